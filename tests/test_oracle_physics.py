@@ -112,3 +112,25 @@ def test_scatter_source(orc):
     out = orc.scatter_source(vol, alb, J)
     np.testing.assert_allclose(out[..., :3], vol[..., :3] + (alb * vol[..., 3])[..., None] * J, rtol=1e-15)
     np.testing.assert_array_equal(out[..., 3], vol[..., 3])
+
+
+def test_scatter_affine_source_without_extinction(orc):
+    """s = 0 and an affine source: each axis sweep is the exact line integral
+    (the segment average is the trapezoid rule, exact for affine q), and the
+    two opposite directions add to (n - 1) q evaluated at the line's midpoint."""
+    shape = (6, 5, 7)
+    nx, ny, nz = shape
+    a = np.array([1.0, 0.5, 0.25])
+    b = np.array([[0.1, -0.05, 0.02], [0.03, 0.04, -0.01], [-0.02, 0.01, 0.05]])  # b[c] . (i, j, k)
+    from oracle_scenes import affine_volume
+    vol = affine_volume(shape, a, b)
+    sc = orc.Scene(shape, (0, 0, 0), 1.0, [one_pixel_camera((0, 0, 0), (1, 0, 0))])
+    J = orc.scatter_J(sc, vol)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+
+    def q(x, y, z):
+        return np.stack([a[c] + b[c][0] * x + b[c][1] * y + b[c][2] * z for c in range(3)], axis=-1)
+
+    expect = ((nx - 1) * q((nx - 1) / 2.0, j, k) + (ny - 1) * q(i, (ny - 1) / 2.0, k)
+              + (nz - 1) * q(i, j, (nz - 1) / 2.0)) / 6.0
+    np.testing.assert_allclose(J, expect, rtol=1e-13)
