@@ -1,0 +1,414 @@
+"""Benchmark of the reconstruction loop (render -> residual -> adjust -> apply).
+
+Workload (default): the full-RTE setting -- a 128^3 float32 volume holding RGB
+emission, extinction and scattering albedo (seeded 8-blob plume with 4-octave
+value noise), 8 ring cameras at 512 x 512, a 0.5-voxel ray step, the paper's
+adjustment rule.  One step is one iteration of the loop: in-scattering source,
+forward march with fused residual, error reduction, adjustment, update.
+
+Metric: ray samples per second, forward + adjustment, i.e. the samples both
+marches process per iteration over the iteration's device time; iterations per
+second are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--storage f32|bf16]
+
+Under torchrun every rank runs an independent replica (the loop does not
+shard within one volume here); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ray samples/s (fwd+adjoint) and recon iters/s at 128^3×8 views; p50/p99 job latency"
+WORKLOAD = dict(name="full_rte_128^3_8x512^2", n=128, views=8, side=512, step=0.5, seed=2,
+                alpha_l=2e-4, noise=1e-3)
+KERNELS_PER_STEP = 8  # 3 sweeps, forward, error reduction, adjustment, apply, rmse
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="one untimed iteration plus one forward and one adjustment launch, for ncu")
+    return ap.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(storage, rank, local):
+    """Seeded ground truth, cameras and targets (rendered on the GPU from the
+    ground truth with in-scattering, plus seeded pixel noise)."""
+    import torch
+    from paper_1809_06417_gb300 import flamerec as fr, synth
+    w = WORKLOAD
+    n = w["n"]
+    shape, origin, h = synth.unit_grid(n)
+    gt, albedo = synth.plume_volume(n, w["seed"] + 1000 * rank)
+    cams = synth.ring_cameras(w["views"], w["side"], w["side"], elevation_jitter_deg=10.0, seed=w["seed"])
+    dt = torch.float32 if storage == "f32" else torch.bfloat16
+    ctx = fr.Context(local)
+    gt_d = torch.as_tensor(gt, dtype=torch.float32, device="cuda").to(dt).contiguous()
+    alb_d = torch.as_tensor(albedo, dtype=torch.float32, device="cuda").contiguous()
+    src = torch.empty_like(gt_d)
+    J = torch.empty((n, n, n, 4), device="cuda")
+    ctx.fr_scatter_source(fr.volume(gt_d, origin, h), alb_d, J, fr.volume(src, origin, h))
+    K, S = w["views"], w["side"]
+    img = torch.empty((K, S, S, 3), device="cuda")
+    fcams = fr.cameras(cams)
+    ctx.fr_render(fr.volume(src, origin, h), fcams, fr.params(step=w["step"]), img)
+    torch.cuda.synchronize()
+    scale = float(img.max())
+    img_np = synth.add_noise(img.cpu().numpy() / scale, w["noise"], w["seed"])
+    targets = torch.as_tensor(img_np, dtype=torch.float32, device="cuda").contiguous()
+    bbox = torch.zeros((K, 4), dtype=torch.int32, device="cuda")
+    ctx.fr_prepare_targets(targets, 30 / 255, bbox)
+    vol0 = gt_d.clone()
+    vol0[..., :3] = 0  # the volume starts at zero (Sec. 3); extinction and albedo known
+    del J, src
+    return ctx, dict(origin=origin, h=h, cams=cams, fcams=fcams, targets=targets, bbox=bbox, albedo=alb_d,
+                     vol0=vol0, gt=gt, gt_albedo=albedo, scale=scale, img_np=img_np)
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+    from paper_1809_06417_gb300 import flamerec as fr
+    torch.cuda.set_device(local)
+    w = WORKLOAD
+    ctx, I = make_inputs(args.storage, rank, local)
+    p = fr.params(step=w["step"], alpha_l=w["alpha_l"])
+    vol = I["vol0"].clone()
+    fv = fr.volume(vol, I["origin"], I["h"])
+    cams = I["fcams"]
+    stream = torch.cuda.current_stream()
+    n_fwd = ctx.fr_count_samples(fv, cams, p)
+    n_adj = ctx.fr_count_samples(fv, cams, p, residual=I["targets"])
+    flush = torch.empty(384 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+
+    def step(it):
+        ctx.fr_reconstruct(fv, cams, I["targets"], I["bbox"], 1, p, albedo=I["albedo"], first_iteration=it)
+
+    for it in range(args.warmup):
+        step(it)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            step(args.warmup + i)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if ws > 1:
+        dist.barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([t_dev], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t)
+
+    # per-kernel timing of the two marches (forward + residual, adjustment)
+    res = torch.empty_like(I["targets"])
+    sq = torch.zeros(4, device="cuda")
+    dV = torch.zeros(vol.shape[:3] + (4,), device="cuda")
+    src = torch.empty_like(vol)
+    J = torch.empty(vol.shape[:3] + (4,), device="cuda")
+    ctx.fr_scatter_source(fv, I["albedo"], J, fr.volume(src, I["origin"], I["h"]))
+    fs = fr.volume(src, I["origin"], I["h"])
+    kf, ka = [], []
+    for i in range(max(5, args.steps // 2)):
+        flush.fill_(float(i))
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        ctx.fr_render_residual(fs, cams, p, I["targets"], I["bbox"], None, res, sq)
+        e1.record(stream)
+        ctx.fr_adjust(fs, cams, p, res, i, dV)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        kf.append(e0.elapsed_time(e1))
+        ka.append(e1.elapsed_time(e2))
+    t_fwd, t_adj = statistics.median(kf) / 1e3, statistics.median(ka) / 1e3
+
+    # end to end through the C ABI with host buffers: pinned targets in, rmse out
+    tgt_host = I["targets"].cpu().pin_memory()
+    rmse_host = np.zeros((1, 3), dtype=np.float32)
+    vol_e2e = I["vol0"].clone()
+    fe = fr.volume(vol_e2e, I["origin"], I["h"])
+    for it in range(2):
+        ctx.fr_reconstruct(fe, cams, tgt_host, I["bbox"], 1, p, albedo=I["albedo"], first_iteration=it,
+                           rmse=rmse_host, targets_are_host=True)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for it in range(args.steps):
+        ctx.fr_reconstruct(fe, cams, tgt_host, I["bbox"], 1, p, albedo=I["albedo"], first_iteration=2 + it,
+                           rmse=rmse_host, targets_are_host=True)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t)
+
+    # reconstruction quality after the timed iterations (context for the number)
+    rmse_now = np.zeros((1, 3), dtype=np.float32)
+    ctx.fr_reconstruct(fv, cams, I["targets"], I["bbox"], 1, p, albedo=I["albedo"],
+                       first_iteration=args.warmup + args.steps, rmse=rmse_now)
+    torch.cuda.synchronize()
+
+    samples_step = n_fwd + n_adj
+    value = ws * samples_step * args.steps / t_dev
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    # dominant kernel and its algorithmic bytes: the forward march reads every
+    # node record once per sample-corner (8 x record bytes per sample)
+    rec_bytes = 16 if args.storage == "f32" else 8
+    dom = "fwd" if t_fwd >= t_adj else "adj"
+    n_dom, t_dom = (n_fwd, t_fwd) if dom == "fwd" else (n_adj, t_adj)
+    gather_bytes = 8 * rec_bytes * n_dom
+    achieved = gather_bytes / t_dom / 1e9
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "samples/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_dev / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "grid": [w["n"]] * 3, "views": w["views"], "image": [w["side"]] * 2,
+                   "step_vox": w["step"], "storage": args.storage, "rule": "paper", "scattering": True,
+                   "l2": "flushed before every timed step (384 MiB write)", "parallelism": f"replicas{ws}"},
+        "recon_iters_per_s": ws * args.steps / t_dev,
+        "samples_per_step": {"fwd": n_fwd, "adj": n_adj},
+        "kernel_ms": {"fwd_residual": 1e3 * t_fwd, "adjust": 1e3 * t_adj},
+        "e2e": {"value": ws * samples_step * args.steps / t_e2e, "unit": "samples/s",
+                "h2d_bytes_per_step": int(I["targets"].numel() * 4), "d2h_bytes_per_step": 12},
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"},
+        "clocks": clk.summary(),
+        "rmse_after": [float(x) for x in rmse_now[0]],
+        "wall_s": t_wall,
+    }
+    ctx.close()
+    return out
+
+
+class OracleSample:
+    """The oracle on bounded samples of the workload: a band of image rows of
+    one view, one iteration (in-scattering source, render of those pixels,
+    residual, adjustment).  The scene, ground truth and the sample's targets
+    are prepared outside the timed region."""
+
+    def __init__(self):
+        import oracle as orc
+        from paper_1809_06417_gb300 import synth
+        self.orc = orc
+        w = WORKLOAD
+        n = w["n"]
+        self.shape, self.origin, self.h = synth.unit_grid(n)
+        self.gt, self.albedo = synth.plume_volume(n, w["seed"])
+        self.cams = synth.ring_cameras(w["views"], w["side"], w["side"], elevation_jitter_deg=10.0, seed=w["seed"])
+        self.P = orc.make_params(step=w["step"], alpha_l=w["alpha_l"])
+        sc = orc.Scene(self.shape, self.origin, self.h, self.cams[:1])
+        self.src_gt = orc.scatter_source(self.gt, self.albedo, orc.scatter_J(sc, self.gt))
+        self.vol0 = self.gt.copy()
+        self.vol0[..., :3] = 0.0
+
+    def run(self, rows, view=0):
+        orc, w = self.orc, WORKLOAD
+        S = w["side"]
+        sc = orc.Scene(self.shape, self.origin, self.h, [self.cams[view]])
+        y0 = S // 2 - rows // 2
+        px = [(0, x, y) for y in range(y0, y0 + rows) for x in range(S)]
+        tgt, _ = orc.render_pixels(sc, self.src_gt, self.P, px)
+        tgt /= max(tgt.max(), 1e-30)
+        t0 = time.perf_counter()
+        src0 = orc.scatter_source(self.vol0, self.albedo, orc.scatter_J(sc, self.vol0))
+        ren, n_f = orc.render_pixels(sc, src0, self.P, px)
+        res = np.zeros((1, S, S, 3))
+        mask = np.zeros((1, S, S), dtype=np.uint8)
+        flame = (tgt.max(axis=1) > 30 / 255).reshape(rows, S)
+        res[0, y0:y0 + rows] = (tgt - ren).reshape(rows, S, 3) * flame[..., None]
+        mask[0, y0:y0 + rows] = flame
+        _, n_a = orc.update_paper(sc, src0, self.P, res, mask, 0)
+        dt = time.perf_counter() - t0
+        return n_f + n_a, dt, f"view {view}, rows {y0}-{y0 + rows - 1} of {S}, one iteration"
+
+
+def cpu_baseline(rows=320):
+    n, dt, what = OracleSample().run(rows)
+    return {"value": n / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": f"{what} (scatter source, render, residual, adjust) of {WORKLOAD['name']}; "
+                      f"{n} samples in {dt:.1f} s"}
+
+
+def run_profile(args):
+    """One warm-up iteration, then one launch each of the forward march
+    (fused residual) and the adjustment, with no timing or L2 flush: the
+    command the ncu captures use."""
+    import torch
+    from paper_1809_06417_gb300 import flamerec as fr
+    w = WORKLOAD
+    ctx, I = make_inputs(args.storage, 0, 0)
+    p = fr.params(step=w["step"], alpha_l=w["alpha_l"])
+    vol = I["vol0"].clone()
+    fv = fr.volume(vol, I["origin"], I["h"])
+    ctx.fr_reconstruct(fv, I["fcams"], I["targets"], I["bbox"], 1, p, albedo=I["albedo"])
+    src = torch.empty_like(vol)
+    J = torch.empty(vol.shape[:3] + (4,), device="cuda")
+    ctx.fr_scatter_source(fv, I["albedo"], J, fr.volume(src, I["origin"], I["h"]))
+    fs = fr.volume(src, I["origin"], I["h"])
+    res = torch.empty_like(I["targets"])
+    sq = torch.zeros(4, device="cuda")
+    dV = torch.zeros(vol.shape[:3] + (4,), device="cuda")
+    ctx.fr_render_residual(fs, I["fcams"], p, I["targets"], I["bbox"], None, res, sq)
+    ctx.fr_adjust(fs, I["fcams"], p, res, 1, dV)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "ok", "sq_err": [float(x) for x in sq.cpu()]}))
+    ctx.close()
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    rows = 8
+    tot_n, tot_t = 0, 0.0
+    sample = OracleSample()
+    for i in range(args.warmup + args.steps):
+        n, dt, what = sample.run(rows, view=i % WORKLOAD["views"])
+        if i >= args.warmup:
+            tot_n += n
+            tot_t += dt
+    v = tot_n / tot_t
+    return {"metric": METRIC, "value": v, "unit": "samples/s", "impl": "reference", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "grid": [WORKLOAD["n"]] * 3, "views": WORKLOAD["views"],
+                       "image": [WORKLOAD["side"]] * 2, "step_vox": WORKLOAD["step"], "storage": "f64",
+                       "rule": "paper", "scattering": True, "parallelism": "cpu1"},
+            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                             "sample": f"per step {rows} rows of one view, one iteration"},
+            "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.profile:
+        run_profile(args)
+        return
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()  # before any GPU work: the oracle never forks after CUDA init
+    out = run_ours(args, ws, rank, local)
+    if rank == 0:
+        out["cpu_baseline"] = cpu
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * flamerec.h -- C ABI of the GB300 flame volume reconstruction library
+ * (render / compare / adjust loop of Shen et al., "Radiative Transport Based
+ * Flame Volume Reconstruction from Videos", arXiv 1809.06417).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Status: every call returns fr_status.  FR_OK is 0.  On failure nothing
+ *    has been launched unless the status is FR_ECUDA, and fr_last_error(ctx)
+ *    returns a message that stays valid until the next call on that context.
+ *    No call aborts, throws across the ABI or traps on the device.
+ *  - Memory: pointers marked "device" are borrowed device pointers owned by
+ *    the caller; they must stay valid until the work queued on the context's
+ *    stream has finished.  Pointers marked "host" are read (or written) before
+ *    the call returns unless stated otherwise.  The library allocates only
+ *    its own scratch, which it owns and frees in fr_destroy.
+ *  - Ordering: all device work is queued on the context's stream, in call
+ *    order.  Calls do not synchronise the host except where stated.
+ *  - Geometry: the volume is a node-centred grid.  Node (i, j, k) is a key
+ *    point (a voxel vertex, Sec. 3.3 definitions) at world position
+ *    origin + h (i, j, k); records are stored x fastest: index
+ *    (k ny + j) nx + i.  Ray arithmetic is done in voxel units (world / h):
+ *    the sampling step, segment lengths, extinction (per voxel length) and
+ *    the key-point distance D of Eq. 10 are all in voxel edge lengths.
+ *  - Images: float32, views concatenated, rows top to bottom, 3 channels
+ *    interleaved: element ((v H + y) W + x) 3 + c.
+ */
+#ifndef FLAMEREC_H
+#define FLAMEREC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FR_ABI_VERSION 1
+#define FR_MAX_VIEWS 32          /* cameras per problem */
+
+typedef enum fr_status {
+    FR_OK = 0,
+    FR_EINVAL = 1,       /* bad argument; nothing launched */
+    FR_ENOMEM = 2,       /* device or host allocation failed, or a job can never fit */
+    FR_ECUDA = 3,        /* a CUDA call failed; see fr_last_error */
+    FR_ETIMEDOUT = 4,    /* a bounded wait ran out */
+    FR_EBUSY = 5,        /* resource in use (e.g. a job table slot) */
+    FR_ECANCELED = 6     /* the job was cancelled */
+} fr_status;
+
+typedef enum fr_dtype { FR_F32 = 0, FR_BF16 = 1, FR_F16 = 2 } fr_dtype;
+
+/* Record kinds.  FR_KIND_RGB: {S_r, S_g, S_b, sigma_t} per node, the
+ * emitted radiance per voxel length of the RTE (Eq. 5, first term) and the
+ * extinction coefficient (Eq. 5, second term).  FR_KIND_TEMP: {T, sigma_t},
+ * temperature in kelvin mapped to RGB through the colour-temperature table
+ * (Sec. 3.3.3). */
+typedef enum fr_kind { FR_KIND_RGB = 0, FR_KIND_TEMP = 1 } fr_kind;
+
+/* A volume: descriptor plus a borrowed device pointer to nx*ny*nz records of
+ * `dtype` with 4 (RGB) or 2 (TEMP) components each.  Every extent >= 2. */
+typedef struct fr_volume {
+    int32_t nx, ny, nz;
+    int32_t kind;        /* fr_kind */
+    int32_t dtype;       /* fr_dtype (storage; all arithmetic is float32) */
+    int32_t pad_;
+    float origin[3];     /* world position of node (0,0,0) */
+    float h;             /* node spacing (world units) */
+    void *data;          /* device */
+} fr_volume;
+
+/* Perspective pinhole camera (world units).  right, up, fwd orthonormal.
+ * Pixel (x, y), row 0 on top, casts the ray through its centre:
+ *   d = normalise(fwd + a right + b up),
+ *   a = (2 (x + 0.5) / width - 1) tan_half_fov width / height,
+ *   b = (1 - 2 (y + 0.5) / height) tan_half_fov. */
+typedef struct fr_camera {
+    float pos[3], right[3], up[3], fwd[3];
+    float tan_half_fov;  /* tangent of half the vertical field of view */
+    int32_t width, height;
+    int32_t pad_;
+} fr_camera;
+
+typedef enum fr_rule {
+    FR_RULE_PAPER = 0,    /* Eqs. 10-11: dV_j += G alpha_l dL T exp(-alpha_d D) */
+    FR_RULE_GRADIENT = 1  /* V -= grad_step * d(0.5 sum m dL^2)/dV (exact adjoint) */
+} fr_rule;
+
+/* Method parameters.  fr_params_default() fills the paper's constants. */
+typedef struct fr_params {
+    float step;          /* sampling step, voxel edge lengths (Sec. 4.2: 1) */
+    float alpha_l;       /* Eq. 10 residual scale (Sec. 5.1: 0.001) */
+    float alpha_d;       /* Eq. 10 distance scale (Sec. 5.1: 1) */
+    float tau;           /* > 0: constant sample opacity, Eqs. 7-8, 12 (Sec. 5.1: 0.05);
+                            <= 0: extinction from the sigma_t field (Eq. 6) */
+    float g_std;         /* spread of G(s), mean 1 (Eq. 11); 0 disables */
+    float flame_thresh;  /* flame-pixel threshold, image units (Sec. 4.1: 30/255) */
+    uint64_t seed;       /* key of the G(s) stream */
+    int32_t clamp_nonneg;/* clamp adjusted values at 0 */
+    int32_t rule;        /* fr_rule used by fr_reconstruct */
+    float grad_step;     /* FR_RULE_GRADIENT step size */
+    int32_t update_sigma;/* FR_RULE_GRADIENT: also step sigma_t */
+    float lut_t_min, lut_t_max; /* colour-temperature table range, kelvin */
+    const float *lut;    /* device, lut_size x 4 {r,g,b,0}, from fr_planck_lut (TEMP only) */
+    int32_t lut_size;
+    int32_t pad_;
+} fr_params;
+
+typedef struct fr_ctx fr_ctx;
+
+/* Library ABI version (FR_ABI_VERSION). */
+int32_t fr_abi_version(void);
+
+/* Fills `p` with the paper's constants (Sec. 4.1, 4.2, 5.1). */
+void fr_params_default(fr_params *p);
+
+/* Create a context on `device`.  stream: the cudaStream_t to queue work on
+ * (borrowed); NULL means CUDA's default stream, as in the runtime API. */
+fr_status fr_create(fr_ctx **out, int device, void *stream);
+fr_status fr_destroy(fr_ctx *ctx);
+/* Replace the context's stream (borrowed; NULL = CUDA's default stream). */
+fr_status fr_set_stream(fr_ctx *ctx, void *stream);
+/* Message of the last failure on this context ("" if none). */
+const char *fr_last_error(const fr_ctx *ctx);
+/* Blocks until the context's queued work is done. */
+fr_status fr_synchronize(fr_ctx *ctx);
+
+/* Sec. 4.1 pre-processing of target frames, in place.  Pixels whose largest
+ * channel exceeds `thresh` are flame pixels; all others are set to black.
+ * bbox (device, ncam x 4 int32: x0, y0, x1, y1 inclusive) receives the tight
+ * box of each view's flame pixels, with x0 > x1 for a view without any.
+ * targets: device, ncam x height x width x 3. */
+fr_status fr_prepare_targets(fr_ctx *ctx, int ncam, int height, int width,
+                             float *targets, float thresh, int32_t *bbox);
+
+/* Sec. 3.3.1 / Eqs. 5-8 (Algorithm 2, rendering half): ray-march every pixel
+ * of every camera through `vol` front to back.  Field mode: a segment of
+ * length l sampled (trilinearly, at its midpoint) at source S and extinction s
+ * adds T S (1 - exp(-s l)) / s and multiplies T by exp(-s l); tau > 0 uses the
+ * constant-opacity blend of Eqs. 7-8.  Background black.  All cameras must
+ * share one image size.  out_rgb: device, ncam x H x W x 3. */
+fr_status fr_render(fr_ctx *ctx, const fr_volume *vol, const fr_camera *cams,
+                    int ncam, const fr_params *p, float *out_rgb);
+
+/* Rendering fused with the colour constraint of Sec. 3.3.2 and the error
+ * measure of Sec. 5.1.  targets (device) must have been through
+ * fr_prepare_targets.  For every pixel dL = target - rendered;
+ *   residual (device, like the image) = dL on flame pixels, 0 elsewhere;
+ *   rendered (device, nullable) = the rendered image;
+ *   sq_err (device, 4 floats, overwritten) = sum over the per-view boxes of
+ *   dL^2 per channel, and the number of boxed pixels.
+ * RMSE on the paper's [0, 255] scale is 255 sqrt(sq_err[c] / sq_err[3]). */
+fr_status fr_render_residual(fr_ctx *ctx, const fr_volume *vol, const fr_camera *cams,
+                             int ncam, const fr_params *p, const float *targets,
+                             const int32_t *bbox, float *rendered, float *residual,
+                             float *sq_err);
+
+/* Eq. 10 (Algorithm 2, adjustment half): for every pixel with a non-zero
+ * residual, every sample s on its ray and each of the sample's eight key
+ * points j, accumulate
+ *   dV[j] += G(s) alpha_l dL T(s, s_e) exp(-alpha_d D(j, s))
+ * with T the transmittance in front of the sample (Eq. 12 when tau > 0) and
+ * G(s) the Gaussian factor of Eq. 11 drawn from the counter-based stream
+ * keyed by (seed, iteration, view, pixel, sample).  Accumulation order is
+ * unspecified (float atomics).  vol supplies sigma_t only (RGB kind).
+ * dV: device, nodes x 4 float32 {r, g, b, unused}, accumulated into. */
+fr_status fr_adjust(fr_ctx *ctx, const fr_volume *vol, const fr_camera *cams, int ncam,
+                    const fr_params *p, const float *residual, int iteration, float *dV);
+
+/* Eq. 11: V <- V + scale dV on the colour components (and on sigma_t when
+ * with_sigma, from dV's fourth component), optional clamp at 0, rounded to
+ * the volume's storage type; dV is zeroed afterwards when zero_dV. */
+fr_status fr_apply_update(fr_ctx *ctx, fr_volume *vol, float *dV, float scale,
+                          int with_sigma, int clamp_nonneg, int zero_dV);
+
+/* Exact gradient of the rendered images (the differentiable variant of the
+ * adjustment): given grad_img = d(loss)/d(pixel) and the radiance L_total the
+ * forward pass rendered, accumulate d(loss)/d(record) into grad (device,
+ * nodes x 4 float32 for RGB {S_r,S_g,S_b,sigma}; nodes x 2 {T, sigma} for
+ * TEMP).  Transmittance is recomputed along each ray, never stored. */
+fr_status fr_render_backward(fr_ctx *ctx, const fr_volume *vol, const fr_camera *cams,
+                             int ncam, const fr_params *p, const float *L_total,
+                             const float *grad_img, float *grad);
+
+/* In-scattering source (Eq. 5, third term, isotropic phase function Eq. 9
+ * with g = 0).  J at each node is the mean over the six axis directions of the
+ * emitted radiance arriving along grid lines (single scattering); the output
+ * records are S = q + albedo sigma_t J with sigma_t copied.  emission: RGB
+ * volume {q, sigma}; albedo: device, nodes float32; out: RGB volume of the
+ * same grid (any storage type); J (device, nodes x 4 float32) is scratch
+ * supplied by the caller. */
+fr_status fr_scatter_source(fr_ctx *ctx, const fr_volume *emission, const float *albedo,
+                            float *J, fr_volume *out);
+
+/* Colour-temperature table (Sec. 3.3.3): Planck's law integrated against
+ * three Gaussian channel responses (centres 600, 540, 460 nm, width 40 nm,
+ * 380-780 nm, trapezoid rule in 1 nm steps), scaled so green(2000 K) = 1.
+ * lut: device, m x 4 float32 {r, g, b, 0} at t_min + i (t_max - t_min)/(m-1). */
+fr_status fr_planck_lut(fr_ctx *ctx, float t_min, float t_max, int m, float *lut);
+
+/* The reconstruction loop (Sec. 3, Algorithm 2 repeated): for `iters`
+ * iterations: [in-scattering source when albedo != NULL] -> render and
+ * residual -> adjust (p->rule) -> apply.  vol is updated in place.
+ * targets_are_host != 0: targets is pinned host memory and is copied to the
+ * device before the loop (the context keeps a device copy).  targets must be
+ * prepared (fr_prepare_targets) and bbox (device) must be its box.
+ * rmse (nullable): iters x 3 float32 on the paper's [0, 255] scale, of the
+ * image rendered at the start of each iteration; rmse_is_host != 0 means a
+ * host array filled before the call returns (the call then synchronises). */
+fr_status fr_reconstruct(fr_ctx *ctx, fr_volume *vol, const float *albedo,
+                         const fr_camera *cams, int ncam, const float *targets,
+                         int targets_are_host, const int32_t *bbox, int iters,
+                         int first_iteration, const fr_params *p, float *rmse,
+                         int rmse_is_host);
+
+/* Number of samples (segments) the rays of `cams` take through the volume's
+ * box: all rays when residual is NULL (one render), else only the rays whose
+ * residual (device, image layout) is non-zero (one adjustment).  Counted by a
+ * device kernel; *samples (host) is written before the call returns (the
+ * call synchronises the stream). */
+fr_status fr_count_samples(fr_ctx *ctx, const fr_volume *vol, const fr_camera *cams,
+                           int ncam, const fr_params *p, const float *residual,
+                           int64_t *samples);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLAMEREC_H */

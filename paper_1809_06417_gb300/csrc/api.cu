@@ -1,0 +1,617 @@
+// api.cu -- the C ABI declared in include/flamerec.h: argument validation,
+// library-owned scratch, kernel launches and the reconstruction loop.
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "flamerec.h"
+#include "fr_internal.h"
+
+using namespace frk;
+
+namespace {
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct fr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;   // where work is queued (borrowed; 0 = default stream)
+    std::string err;
+    Buf partials, counter, residual, rendered, dV, targets, sqerr, rmse, J, src;
+    unsigned long long* host_counter = nullptr;
+};
+
+namespace {
+
+fr_status fail(fr_ctx* c, fr_status s, const char* fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+fr_status cuda_fail(fr_ctx* c, cudaError_t e, const char* what)
+{
+    return fail(c, FR_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define FR_CUDA(ctx, expr)                                 \
+    do {                                                   \
+        cudaError_t e_ = (expr);                           \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
+    } while (0)
+
+// Device-pointer check: the pointer must lie in a device allocation that
+// holds at least `bytes` from it.  Catches host pointers and short buffers
+// before any kernel could touch them.
+PFN_cuMemGetAddressRange_v3020 range_fn()
+{
+    static PFN_cuMemGetAddressRange_v3020 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuMemGetAddressRange_v3020>(f);
+    });
+    return fn;
+}
+
+fr_status check_dev(fr_ctx* c, const void* p, size_t bytes, const char* name)
+{
+    if (!p) return fail(c, FR_EINVAL, "%s is NULL", name);
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, FR_EINVAL, "%s is not a CUDA pointer (%s)", name, cudaGetErrorName(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(c, FR_EINVAL, "%s must be device memory", name);
+    if (at.type == cudaMemoryTypeDevice && at.device != c->device)
+        return fail(c, FR_EINVAL, "%s lives on device %d, context on %d", name, at.device, c->device);
+    if (auto fn = range_fn()) {
+        CUdeviceptr base = 0;
+        size_t size = 0;
+        if (fn(&base, &size, (CUdeviceptr)(uintptr_t)p) == CUDA_SUCCESS) {
+            if ((uintptr_t)p + bytes > (uintptr_t)base + size)
+                return fail(c, FR_EINVAL, "%s: %zu bytes needed but the allocation ends %zu bytes after it",
+                            name, bytes, (size_t)((uintptr_t)base + size - (uintptr_t)p));
+        }
+    }
+    return FR_OK;
+}
+
+fr_status check_align(fr_ctx* c, const void* p, size_t a, const char* name)
+{
+    if ((uintptr_t)p % a) return fail(c, FR_EINVAL, "%s must be %zu-byte aligned", name, a);
+    return FR_OK;
+}
+
+int rec_components(int kind) { return kind == FR_KIND_RGB ? 4 : 2; }
+int dtype_bytes(int dt) { return dt == FR_F32 ? 4 : 2; }
+size_t rec_bytes(const fr_volume* v) { return (size_t)rec_components(v->kind) * dtype_bytes(v->dtype); }
+long long node_count(const fr_volume* v) { return (long long)v->nx * v->ny * v->nz; }
+
+bool finite3(const float* x) { return std::isfinite(x[0]) && std::isfinite(x[1]) && std::isfinite(x[2]); }
+
+fr_status check_volume(fr_ctx* c, const fr_volume* v, const char* name)
+{
+    if (!v) return fail(c, FR_EINVAL, "%s is NULL", name);
+    if (v->nx < 2 || v->ny < 2 || v->nz < 2 || v->nx > 8192 || v->ny > 8192 || v->nz > 8192)
+        return fail(c, FR_EINVAL, "%s: extents must be in [2, 8192], got %d x %d x %d", name, v->nx, v->ny, v->nz);
+    if (node_count(v) > (1LL << 34)) return fail(c, FR_EINVAL, "%s: too many nodes", name);
+    if (v->kind != FR_KIND_RGB && v->kind != FR_KIND_TEMP) return fail(c, FR_EINVAL, "%s: bad kind %d", name, v->kind);
+    if (v->dtype != FR_F32 && v->dtype != FR_BF16 && v->dtype != FR_F16)
+        return fail(c, FR_EINVAL, "%s: bad dtype %d", name, v->dtype);
+    if (!(v->h > 0.0f) || !std::isfinite(v->h) || !finite3(v->origin))
+        return fail(c, FR_EINVAL, "%s: spacing must be positive and origin finite", name);
+    fr_status s = check_align(c, v->data, rec_bytes(v), name);
+    if (s) return s;
+    return check_dev(c, v->data, (size_t)node_count(v) * rec_bytes(v), name);
+}
+
+fr_status check_cams(fr_ctx* c, const fr_camera* cams, int ncam)
+{
+    if (!cams) return fail(c, FR_EINVAL, "cams is NULL");
+    if (ncam < 1 || ncam > kMaxViews) return fail(c, FR_EINVAL, "ncam must be in [1, %d], got %d", kMaxViews, ncam);
+    for (int i = 0; i < ncam; ++i) {
+        const fr_camera& k = cams[i];
+        if (k.width < 1 || k.height < 1 || k.width > 16384 || k.height > 16384)
+            return fail(c, FR_EINVAL, "camera %d: image size must be in [1, 16384]", i);
+        if (k.width != cams[0].width || k.height != cams[0].height)
+            return fail(c, FR_EINVAL, "camera %d: all cameras must share one image size", i);
+        if (!(k.tan_half_fov > 0.0f) || !std::isfinite(k.tan_half_fov))
+            return fail(c, FR_EINVAL, "camera %d: tan_half_fov must be positive", i);
+        if (!finite3(k.pos) || !finite3(k.right) || !finite3(k.up) || !finite3(k.fwd))
+            return fail(c, FR_EINVAL, "camera %d: non-finite vector", i);
+        auto dot = [](const float* a, const float* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
+        if (fabsf(dot(k.fwd, k.fwd) - 1.0f) > 1e-3f || fabsf(dot(k.right, k.right) - 1.0f) > 1e-3f ||
+            fabsf(dot(k.up, k.up) - 1.0f) > 1e-3f || fabsf(dot(k.fwd, k.right)) > 1e-3f ||
+            fabsf(dot(k.fwd, k.up)) > 1e-3f || fabsf(dot(k.right, k.up)) > 1e-3f)
+            return fail(c, FR_EINVAL, "camera %d: right, up, fwd must be orthonormal", i);
+    }
+    return FR_OK;
+}
+
+fr_status check_params(fr_ctx* c, const fr_params* p, const fr_volume* v, const fr_camera* cams)
+{
+    if (!p) return fail(c, FR_EINVAL, "params is NULL");
+    if (!(p->step > 0.0f) || !std::isfinite(p->step)) return fail(c, FR_EINVAL, "step must be positive");
+    double diag = std::sqrt((double)(v->nx - 1) * (v->nx - 1) + (double)(v->ny - 1) * (v->ny - 1) +
+                            (double)(v->nz - 1) * (v->nz - 1));
+    double max_seg = std::ceil(diag / p->step) + 1.0;
+    if (max_seg > 1e6) return fail(c, FR_EINVAL, "step too small: up to %.0f samples per ray", max_seg);
+    if (!std::isfinite(p->alpha_l) || !std::isfinite(p->alpha_d) || p->alpha_d < 0.0f)
+        return fail(c, FR_EINVAL, "alpha_l must be finite and alpha_d finite and >= 0");
+    if (!(p->tau < 1.0f) || !std::isfinite(p->tau)) return fail(c, FR_EINVAL, "tau must be < 1");
+    if (!std::isfinite(p->flame_thresh)) return fail(c, FR_EINVAL, "flame_thresh must be finite");
+    if (!(p->g_std >= 0.0f) || !std::isfinite(p->g_std)) return fail(c, FR_EINVAL, "g_std must be >= 0");
+    if (p->g_std > 0.0f) {
+        // counter layout of the G(s) stream: 20 bits iteration, 8 view, 22 pixel, 14 sample
+        if ((long long)cams[0].width * cams[0].height > (1LL << 22))
+            return fail(c, FR_EINVAL, "g_std > 0 supports at most 2^22 pixels per view");
+        if (max_seg > 16383.0) return fail(c, FR_EINVAL, "g_std > 0 supports at most 16383 samples per ray");
+    }
+    if (v->kind == FR_KIND_TEMP) {
+        if (!p->lut || p->lut_size < 2 || !(p->lut_t_max > p->lut_t_min))
+            return fail(c, FR_EINVAL, "temperature volumes need lut, lut_size >= 2 and lut_t_max > lut_t_min");
+        fr_status s = check_align(c, p->lut, 16, "lut");
+        if (s) return s;
+        return check_dev(c, p->lut, (size_t)p->lut_size * 16, "lut");
+    }
+    return FR_OK;
+}
+
+fr_status ensure(fr_ctx* c, Buf& b, size_t bytes, const char* name)
+{
+    if (b.bytes >= bytes) return FR_OK;
+    if (b.p) {
+        FR_CUDA(c, cudaStreamSynchronize(c->stream));
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    size_t want = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(c, FR_ENOMEM, "cannot allocate %zu bytes of %s scratch", want, name);
+    }
+    b.bytes = want;
+    return FR_OK;
+}
+
+void fill_problem(const fr_volume* v, const fr_camera* cams, int ncam, const fr_params* p, SingleArgs& a)
+{
+    memset(&a, 0, sizeof a);
+    ProbDev& P = a.p;
+    P.vol = v->data;
+    P.nx = v->nx; P.ny = v->ny; P.nz = v->nz;
+    P.ncam = ncam;
+    P.W = cams[0].width;
+    P.H = cams[0].height;
+    P.tiles_x = (P.W + kTileW - 1) / kTileW;
+    P.tiles_y = (P.H + kTileH - 1) / kTileH;
+    P.img_scale = 1.0f;
+    P.step = p->step;
+    P.alpha_l = p->alpha_l;
+    P.alpha_d = p->alpha_d;
+    P.tau = p->tau > 0.0f ? p->tau : 0.0f;
+    P.g_std = p->g_std;
+    P.thresh = p->flame_thresh;
+    P.seed = p->seed;
+    if (v->kind == FR_KIND_TEMP) {
+        P.lut = reinterpret_cast<const float4*>(p->lut);
+        P.lut_m = p->lut_size;
+        P.lut_t0 = p->lut_t_min;
+        P.lut_scale = (float)(p->lut_size - 1) / (p->lut_t_max - p->lut_t_min);
+    }
+    const float inv_h = 1.0f / v->h;
+    for (int i = 0; i < ncam; ++i) {
+        CamDev& d = a.cams[i];
+        const fr_camera& k = cams[i];
+        for (int ax = 0; ax < 3; ++ax) {
+            d.o[ax] = (k.pos[ax] - v->origin[ax]) * inv_h;
+            d.r[ax] = k.right[ax];
+            d.u[ax] = k.up[ax];
+            d.f[ax] = k.fwd[ax];
+        }
+        d.ty = k.tan_half_fov;
+        d.tx = k.tan_half_fov * (float)k.width / (float)k.height;
+        d.W = k.width;
+        d.H = k.height;
+    }
+}
+
+size_t image_bytes(const fr_camera* cams, int ncam)
+{
+    return (size_t)ncam * cams[0].width * cams[0].height * 3 * sizeof(float);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+
+extern "C" int32_t fr_abi_version(void) { return FR_ABI_VERSION; }
+
+extern "C" void fr_params_default(fr_params* p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->step = 1.0f;
+    p->alpha_l = 0.001f;
+    p->alpha_d = 1.0f;
+    p->tau = 0.0f;
+    p->g_std = 0.0f;
+    p->flame_thresh = 30.0f / 255.0f;
+    p->seed = 0;
+    p->clamp_nonneg = 1;
+    p->rule = FR_RULE_PAPER;
+    p->grad_step = 0.0f;
+    p->update_sigma = 0;
+    p->lut_t_min = 800.0f;
+    p->lut_t_max = 2000.0f;
+    p->lut = nullptr;
+    p->lut_size = 0;
+}
+
+extern "C" fr_status fr_create(fr_ctx** out, int device, void* stream)
+{
+    if (!out) return FR_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return FR_ECUDA;
+    }
+    if (device < 0 || device >= n) return FR_EINVAL;
+    fr_ctx* c = new (std::nothrow) fr_ctx();
+    if (!c) return FR_ENOMEM;
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaMallocHost(&c->host_counter, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return FR_ECUDA;
+    }
+    c->stream = static_cast<cudaStream_t>(stream);
+    *out = c;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_destroy(fr_ctx* c)
+{
+    if (!c) return FR_EINVAL;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
+                   &c->rmse, &c->J, &c->src})
+        if (b->p) cudaFree(b->p);
+    if (c->host_counter) cudaFreeHost(c->host_counter);
+    delete c;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_set_stream(fr_ctx* c, void* stream)
+{
+    if (!c) return FR_EINVAL;
+    c->stream = static_cast<cudaStream_t>(stream);
+    return FR_OK;
+}
+
+extern "C" const char* fr_last_error(const fr_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" fr_status fr_synchronize(fr_ctx* c)
+{
+    if (!c) return FR_EINVAL;
+    FR_CUDA(c, cudaStreamSynchronize(c->stream));
+    return FR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Single calls
+// ---------------------------------------------------------------------------
+
+#define FR_TRY(expr)                  \
+    do {                              \
+        fr_status s_ = (expr);        \
+        if (s_ != FR_OK) return s_;   \
+    } while (0)
+
+#define FR_BEGIN(c)                                   \
+    if (!c) return FR_EINVAL;                         \
+    c->err.clear();                                   \
+    FR_CUDA(c, cudaSetDevice(c->device))
+
+extern "C" fr_status fr_prepare_targets(fr_ctx* c, int ncam, int height, int width, float* targets,
+                                        float thresh, int32_t* bbox)
+{
+    FR_BEGIN(c);
+    if (ncam < 1 || ncam > kMaxViews || height < 1 || width < 1 || height > 16384 || width > 16384)
+        return fail(c, FR_EINVAL, "bad image extents");
+    if (!std::isfinite(thresh)) return fail(c, FR_EINVAL, "thresh must be finite");
+    FR_TRY(check_dev(c, targets, (size_t)ncam * height * width * 3 * sizeof(float), "targets"));
+    FR_TRY(check_dev(c, bbox, (size_t)ncam * 4 * sizeof(int32_t), "bbox"));
+    FR_CUDA(c, launch_prepare_targets(targets, ncam, height, width, thresh, bbox, c->stream));
+    return FR_OK;
+}
+
+extern "C" fr_status fr_render(fr_ctx* c, const fr_volume* vol, const fr_camera* cams, int ncam,
+                               const fr_params* p, float* out_rgb)
+{
+    FR_BEGIN(c);
+    FR_TRY(check_volume(c, vol, "vol"));
+    FR_TRY(check_cams(c, cams, ncam));
+    FR_TRY(check_params(c, p, vol, cams));
+    FR_TRY(check_dev(c, out_rgb, image_bytes(cams, ncam), "out_rgb"));
+    static thread_local SingleArgs a;
+    fill_problem(vol, cams, ncam, p, a);
+    a.p.rendered = out_rgb;
+    int nt = tiles_of(a.p.W, a.p.H, ncam);
+    FR_CUDA(c, launch_fwd(a, vol->dtype, vol->kind, nt, c->stream));
+    return FR_OK;
+}
+
+extern "C" fr_status fr_render_residual(fr_ctx* c, const fr_volume* vol, const fr_camera* cams, int ncam,
+                                        const fr_params* p, const float* targets, const int32_t* bbox,
+                                        float* rendered, float* residual, float* sq_err)
+{
+    FR_BEGIN(c);
+    FR_TRY(check_volume(c, vol, "vol"));
+    FR_TRY(check_cams(c, cams, ncam));
+    FR_TRY(check_params(c, p, vol, cams));
+    const size_t ib = image_bytes(cams, ncam);
+    FR_TRY(check_dev(c, targets, ib, "targets"));
+    FR_TRY(check_dev(c, bbox, (size_t)ncam * 4 * sizeof(int32_t), "bbox"));
+    if (rendered) FR_TRY(check_dev(c, rendered, ib, "rendered"));
+    FR_TRY(check_dev(c, residual, ib, "residual"));
+    FR_TRY(check_dev(c, sq_err, 4 * sizeof(float), "sq_err"));
+    static thread_local SingleArgs a;
+    fill_problem(vol, cams, ncam, p, a);
+    int nt = tiles_of(a.p.W, a.p.H, ncam);
+    FR_TRY(ensure(c, c->partials, (size_t)nt * 4 * sizeof(float), "partials"));
+    a.p.targets = targets;
+    a.p.bbox = bbox;
+    a.p.rendered = rendered;
+    a.p.residual = residual;
+    a.p.partials = static_cast<float*>(c->partials.p);
+    FR_CUDA(c, launch_fwd(a, vol->dtype, vol->kind, nt, c->stream));
+    FR_CUDA(c, launch_finalize(a.p.partials, nt, sq_err, c->stream));
+    return FR_OK;
+}
+
+extern "C" fr_status fr_adjust(fr_ctx* c, const fr_volume* vol, const fr_camera* cams, int ncam,
+                               const fr_params* p, const float* residual, int iteration, float* dV)
+{
+    FR_BEGIN(c);
+    FR_TRY(check_volume(c, vol, "vol"));
+    if (vol->kind != FR_KIND_RGB) return fail(c, FR_EINVAL, "fr_adjust needs an RGB volume (for sigma)");
+    FR_TRY(check_cams(c, cams, ncam));
+    FR_TRY(check_params(c, p, vol, cams));
+    if (iteration < 0 || iteration >= (1 << 20)) return fail(c, FR_EINVAL, "iteration must be in [0, 2^20)");
+    FR_TRY(check_dev(c, residual, image_bytes(cams, ncam), "residual"));
+    FR_TRY(check_align(c, dV, 16, "dV"));
+    FR_TRY(check_dev(c, dV, (size_t)node_count(vol) * 16, "dV"));
+    static thread_local SingleArgs a;
+    fill_problem(vol, cams, ncam, p, a);
+    a.p.img_in = residual;
+    a.p.dV = dV;
+    a.p.iteration = iteration;
+    FR_CUDA(c, launch_adjust(a, vol->dtype, tiles_of(a.p.W, a.p.H, ncam), c->stream));
+    return FR_OK;
+}
+
+extern "C" fr_status fr_apply_update(fr_ctx* c, fr_volume* vol, float* dV, float scale, int with_sigma,
+                                     int clamp_nonneg, int zero_dV)
+{
+    FR_BEGIN(c);
+    FR_TRY(check_volume(c, vol, "vol"));
+    if (!std::isfinite(scale)) return fail(c, FR_EINVAL, "scale must be finite");
+    const size_t comp = (size_t)rec_components(vol->kind);
+    FR_TRY(check_align(c, dV, comp * 4, "dV"));
+    FR_TRY(check_dev(c, dV, (size_t)node_count(vol) * comp * 4, "dV"));
+    FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, node_count(vol), dV, scale, with_sigma,
+                            clamp_nonneg, zero_dV, c->stream));
+    return FR_OK;
+}
+
+extern "C" fr_status fr_render_backward(fr_ctx* c, const fr_volume* vol, const fr_camera* cams, int ncam,
+                                        const fr_params* p, const float* L_total, const float* grad_img,
+                                        float* grad)
+{
+    FR_BEGIN(c);
+    FR_TRY(check_volume(c, vol, "vol"));
+    FR_TRY(check_cams(c, cams, ncam));
+    FR_TRY(check_params(c, p, vol, cams));
+    const size_t ib = image_bytes(cams, ncam);
+    FR_TRY(check_dev(c, L_total, ib, "L_total"));
+    FR_TRY(check_dev(c, grad_img, ib, "grad_img"));
+    const size_t comp = (size_t)rec_components(vol->kind);
+    FR_TRY(check_align(c, grad, comp * 4, "grad"));
+    FR_TRY(check_dev(c, grad, (size_t)node_count(vol) * comp * 4, "grad"));
+    static thread_local SingleArgs a;
+    fill_problem(vol, cams, ncam, p, a);
+    a.p.img_in = grad_img;
+    a.p.L_total = L_total;
+    a.p.dV = grad;
+    FR_CUDA(c, launch_backward(a, vol->dtype, vol->kind, tiles_of(a.p.W, a.p.H, ncam), c->stream));
+    return FR_OK;
+}
+
+extern "C" fr_status fr_scatter_source(fr_ctx* c, const fr_volume* em, const float* albedo, float* J,
+                                       fr_volume* out)
+{
+    FR_BEGIN(c);
+    FR_TRY(check_volume(c, em, "emission"));
+    FR_TRY(check_volume(c, out, "out"));
+    if (em->kind != FR_KIND_RGB || out->kind != FR_KIND_RGB)
+        return fail(c, FR_EINVAL, "in-scattering needs RGB volumes");
+    if (em->nx != out->nx || em->ny != out->ny || em->nz != out->nz || em->dtype != out->dtype)
+        return fail(c, FR_EINVAL, "emission and out must share grid and storage type");
+    if (em->data == out->data) return fail(c, FR_EINVAL, "out must not alias emission");
+    const long long n = node_count(em);
+    FR_TRY(check_dev(c, albedo, (size_t)n * 4, "albedo"));
+    FR_TRY(check_align(c, J, 16, "J"));
+    FR_TRY(check_dev(c, J, (size_t)n * 16, "J"));
+    FR_CUDA(c, launch_scatter_source(em->data, em->dtype, albedo, J, out->data, out->dtype, em->nx, em->ny,
+                                     em->nz, c->stream));
+    return FR_OK;
+}
+
+extern "C" fr_status fr_planck_lut(fr_ctx* c, float t_min, float t_max, int m, float* lut)
+{
+    FR_BEGIN(c);
+    if (!(t_min > 0.0f) || !(t_max > t_min) || !std::isfinite(t_max) || m < 2 || m > (1 << 20))
+        return fail(c, FR_EINVAL, "need 0 < t_min < t_max and 2 <= m <= 2^20");
+    FR_TRY(check_align(c, lut, 16, "lut"));
+    FR_TRY(check_dev(c, lut, (size_t)m * 16, "lut"));
+    FR_CUDA(c, launch_planck_lut(t_min, t_max, m, lut, c->stream));
+    return FR_OK;
+}
+
+extern "C" fr_status fr_count_samples(fr_ctx* c, const fr_volume* vol, const fr_camera* cams, int ncam,
+                                      const fr_params* p, const float* residual, int64_t* samples)
+{
+    FR_BEGIN(c);
+    if (!samples) return fail(c, FR_EINVAL, "samples is NULL");
+    FR_TRY(check_volume(c, vol, "vol"));
+    FR_TRY(check_cams(c, cams, ncam));
+    FR_TRY(check_params(c, p, vol, cams));
+    if (residual) FR_TRY(check_dev(c, residual, image_bytes(cams, ncam), "residual"));
+    FR_TRY(ensure(c, c->counter, sizeof(unsigned long long), "counter"));
+    static thread_local SingleArgs a;
+    fill_problem(vol, cams, ncam, p, a);
+    a.p.img_in = residual;
+    a.p.counter = static_cast<unsigned long long*>(c->counter.p);
+    FR_CUDA(c, cudaMemsetAsync(a.p.counter, 0, sizeof(unsigned long long), c->stream));
+    FR_CUDA(c, launch_count(a, tiles_of(a.p.W, a.p.H, ncam), c->stream));
+    FR_CUDA(c, cudaMemcpyAsync(c->host_counter, a.p.counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               c->stream));
+    FR_CUDA(c, cudaStreamSynchronize(c->stream));
+    *samples = (int64_t)*c->host_counter;
+    return FR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The reconstruction loop
+// ---------------------------------------------------------------------------
+
+extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albedo, const fr_camera* cams,
+                                    int ncam, const float* targets, int targets_are_host, const int32_t* bbox,
+                                    int iters, int first_iteration, const fr_params* p, float* rmse,
+                                    int rmse_is_host)
+{
+    FR_BEGIN(c);
+    FR_TRY(check_volume(c, vol, "vol"));
+    FR_TRY(check_cams(c, cams, ncam));
+    FR_TRY(check_params(c, p, vol, cams));
+    if (iters < 0) return fail(c, FR_EINVAL, "iters must be >= 0");
+    if (first_iteration < 0 || (long long)first_iteration + iters > (1 << 20))
+        return fail(c, FR_EINVAL, "iterations must stay below 2^20");
+    if (p->rule != FR_RULE_PAPER && p->rule != FR_RULE_GRADIENT) return fail(c, FR_EINVAL, "bad rule");
+    if (vol->kind == FR_KIND_TEMP && p->rule == FR_RULE_PAPER)
+        return fail(c, FR_EINVAL, "temperature volumes are reconstructed with FR_RULE_GRADIENT");
+    if (albedo && vol->kind != FR_KIND_RGB) return fail(c, FR_EINVAL, "albedo needs an RGB volume");
+    if (p->rule == FR_RULE_GRADIENT && !std::isfinite(p->grad_step))
+        return fail(c, FR_EINVAL, "grad_step must be finite");
+    const long long nodes = node_count(vol);
+    const size_t ib = image_bytes(cams, ncam);
+    if (!targets) return fail(c, FR_EINVAL, "targets is NULL");
+    if (!targets_are_host) FR_TRY(check_dev(c, targets, ib, "targets"));
+    FR_TRY(check_dev(c, bbox, (size_t)ncam * 4 * sizeof(int32_t), "bbox"));
+    if (albedo) FR_TRY(check_dev(c, albedo, (size_t)nodes * 4, "albedo"));
+    if (rmse && !rmse_is_host) FR_TRY(check_dev(c, rmse, (size_t)iters * 3 * sizeof(float), "rmse"));
+    if (iters == 0) return FR_OK;
+
+    const int comp = rec_components(vol->kind);
+    const int nt = tiles_of(cams[0].width, cams[0].height, ncam);
+    FR_TRY(ensure(c, c->residual, ib, "residual"));
+    FR_TRY(ensure(c, c->dV, (size_t)nodes * comp * 4, "dV"));
+    FR_TRY(ensure(c, c->partials, (size_t)nt * 16, "partials"));
+    FR_TRY(ensure(c, c->sqerr, (size_t)iters * 16, "sqerr"));
+    FR_TRY(ensure(c, c->rmse, (size_t)iters * 12, "rmse"));
+    if (targets_are_host) FR_TRY(ensure(c, c->targets, ib, "targets"));
+    if (p->rule == FR_RULE_GRADIENT) FR_TRY(ensure(c, c->rendered, ib, "rendered"));
+    if (albedo) {
+        FR_TRY(ensure(c, c->J, (size_t)nodes * 16, "J"));
+        FR_TRY(ensure(c, c->src, (size_t)nodes * rec_bytes(vol), "source"));
+    }
+    cudaStream_t s = c->stream;
+    const float* tg = targets;
+    if (targets_are_host) {
+        FR_CUDA(c, cudaMemcpyAsync(c->targets.p, targets, ib, cudaMemcpyHostToDevice, s));
+        tg = static_cast<const float*>(c->targets.p);
+    }
+    FR_CUDA(c, cudaMemsetAsync(c->dV.p, 0, (size_t)nodes * comp * 4, s));
+
+    static thread_local SingleArgs f, u;
+    fill_problem(vol, cams, ncam, p, f);
+    const void* render_vol = albedo ? c->src.p : vol->data;
+    f.p.vol = render_vol;
+    f.p.targets = tg;
+    f.p.bbox = bbox;
+    f.p.residual = static_cast<float*>(c->residual.p);
+    f.p.partials = static_cast<float*>(c->partials.p);
+    f.p.rendered = p->rule == FR_RULE_GRADIENT ? static_cast<float*>(c->rendered.p) : nullptr;
+    u = f;
+    u.p.targets = nullptr;
+    u.p.partials = nullptr;
+    u.p.residual = nullptr;
+    u.p.rendered = nullptr;
+    u.p.img_in = static_cast<const float*>(c->residual.p);
+    u.p.dV = static_cast<float*>(c->dV.p);
+    float* sq = static_cast<float*>(c->sqerr.p);
+    for (int it = 0; it < iters; ++it) {
+        if (albedo)
+            FR_CUDA(c, launch_scatter_source(vol->data, vol->dtype, albedo, static_cast<float*>(c->J.p), c->src.p,
+                                             vol->dtype, vol->nx, vol->ny, vol->nz, s));
+        FR_CUDA(c, launch_fwd(f, vol->dtype, vol->kind, nt, s));
+        FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * it, s));
+        if (p->rule == FR_RULE_PAPER) {
+            u.p.iteration = first_iteration + it;
+            FR_CUDA(c, launch_adjust(u, vol->dtype, nt, s));
+            FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg, 1, s));
+        } else {
+            // d(0.5 sum m dL^2)/d(rendered) = -m dL: the residual scaled by -1
+            u.p.img_scale = -1.0f;
+            u.p.L_total = static_cast<const float*>(c->rendered.p);
+            FR_CUDA(c, launch_backward(u, vol->dtype, vol->kind, nt, s));
+            FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, -p->grad_step,
+                                    p->update_sigma, p->clamp_nonneg, 1, s));
+        }
+    }
+    FR_CUDA(c, launch_rmse(sq, iters, static_cast<float*>(c->rmse.p), s));
+    if (rmse) {
+        if (rmse_is_host) {
+            FR_CUDA(c, cudaMemcpyAsync(rmse, c->rmse.p, (size_t)iters * 12, cudaMemcpyDeviceToHost, s));
+            FR_CUDA(c, cudaStreamSynchronize(s));
+        } else {
+            FR_CUDA(c, cudaMemcpyAsync(rmse, c->rmse.p, (size_t)iters * 12, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    return FR_OK;
+}

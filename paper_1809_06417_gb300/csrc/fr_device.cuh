@@ -1,0 +1,503 @@
+// fr_device.cuh -- device-side building blocks of the flame reconstruction
+// kernels: camera rays, box clipping, node-record loads for each storage type,
+// trilinear sampling, the colour-temperature table and the G(s) stream.
+//
+// Conventions (identical to the C ABI, include/flamerec.h): key points are
+// grid nodes (Sec. 3.3 definitions); all ray arithmetic is in voxel units;
+// a ray is cut into segments of length `step` from its box entry point and
+// each segment is sampled at its midpoint.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace frk {
+
+enum { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2 };
+enum { KIND_RGB = 0, KIND_TEMP = 1 };
+
+// Pixel tile of one CTA: 16 x 8 rays, one per thread; each warp marches an
+// 8 x 4 sub-tile so that its rays stay close together inside the volume.
+constexpr int kTileW = 16;
+constexpr int kTileH = 8;
+constexpr int kTileThreads = kTileW * kTileH;
+
+// Camera in voxel coordinates.
+struct CamDev {
+    float o[3];          // pinhole
+    float r[3], u[3], f[3];
+    float tx, ty;        // tan(half fov) * aspect, tan(half fov)
+    int W, H;
+};
+static_assert(sizeof(CamDev) == 64, "CamDev layout");
+
+// One reconstruction problem as the kernels see it.
+struct ProbDev {
+    const void* vol;             // records the rays sample
+    const CamDev* cams;          // ncam cameras (device memory; batched launches only)
+    int nx, ny, nz;
+    int ncam, W, H;
+    int tiles_x, tiles_y;        // tiles per view
+    const float* targets;        // prepared targets (image layout), nullable
+    const int* bbox;             // ncam x 4, nullable
+    float* rendered;             // image layout, nullable
+    float* residual;             // image layout, nullable
+    float* partials;             // 4 floats per CTA (squared-error partials), nullable
+    float* dV;                   // nodes x 4 accumulator (adjust / backward)
+    const float* img_in;         // adjust: residual; backward: d(loss)/d(pixel)
+    const float* L_total;        // backward: rendered radiance
+    float img_scale;             // multiplies img_in
+    const float4* lut;           // colour-temperature table, lut_m rows {r,g,b,0}
+    int lut_m;
+    float lut_t0, lut_scale;     // u = (T - lut_t0) * lut_scale, lut_scale = (m-1)/(t1-t0)
+    float step, alpha_l, alpha_d, tau, g_std, thresh;
+    unsigned long long seed;
+    int iteration;
+    int pad_;
+    unsigned long long* counter; // sample counter, nullable
+};
+
+// ---------------------------------------------------------------------------
+// Rays
+// ---------------------------------------------------------------------------
+
+struct Ray {
+    float p0x, p0y, p0z;   // box entry point (voxel coordinates)
+    float dx, dy, dz;      // unit direction
+    float chord;           // length inside the box
+    int n;                 // number of segments
+};
+
+// Pinhole ray of pixel (px, py) clipped to the node box [0, n-1]^3; returns
+// false when the ray misses it (or only grazes it).
+__device__ __forceinline__ bool make_ray(const CamDev& c, int px, int py, int nx, int ny, int nz,
+                                         float step, Ray& R)
+{
+    float a = (2.0f * (px + 0.5f) / (float)c.W - 1.0f) * c.tx;
+    float b = (1.0f - 2.0f * (py + 0.5f) / (float)c.H) * c.ty;
+    float dx = c.f[0] + a * c.r[0] + b * c.u[0];
+    float dy = c.f[1] + a * c.r[1] + b * c.u[1];
+    float dz = c.f[2] + a * c.r[2] + b * c.u[2];
+    float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= inv; dy *= inv; dz *= inv;
+    float o[3] = {c.o[0], c.o[1], c.o[2]};
+    float d[3] = {dx, dy, dz};
+    float hi[3] = {(float)(nx - 1), (float)(ny - 1), (float)(nz - 1)};
+    float tin = -INFINITY, tout = INFINITY;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (d[ax] == 0.0f) {
+            if (o[ax] < 0.0f || o[ax] > hi[ax]) return false;
+            continue;
+        }
+        float t0 = (0.0f - o[ax]) / d[ax];
+        float t1 = (hi[ax] - o[ax]) / d[ax];
+        tin = fmaxf(tin, fminf(t0, t1));
+        tout = fminf(tout, fmaxf(t0, t1));
+    }
+    tin = fmaxf(tin, 0.0f);
+    if (!(tout > tin)) return false;
+    R.p0x = o[0] + tin * dx;
+    R.p0y = o[1] + tin * dy;
+    R.p0z = o[2] + tin * dz;
+    R.dx = dx; R.dy = dy; R.dz = dz;
+    R.chord = tout - tin;
+    R.n = (int)ceilf(R.chord / step);
+    return R.n > 0;
+}
+
+// Segment k of a ray: its length and midpoint.
+__device__ __forceinline__ void segment(const Ray& R, float step, int k, float& len,
+                                        float& x, float& y, float& z)
+{
+    float ta = (float)k * step;
+    float tb = fminf(ta + step, R.chord);
+    len = tb - ta;
+    float tm = 0.5f * (ta + tb);
+    x = fmaf(tm, R.dx, R.p0x);
+    y = fmaf(tm, R.dy, R.p0y);
+    z = fmaf(tm, R.dz, R.p0z);
+}
+
+// Cell index clamped to [0, n-2] and the fraction inside it, in [0, 1].
+__device__ __forceinline__ void locate(float p, int n, int& i, float& f)
+{
+    int ii = (int)floorf(p);
+    ii = min(max(ii, 0), n - 2);
+    i = ii;
+    f = fminf(fmaxf(p - (float)ii, 0.0f), 1.0f);
+}
+
+struct Cell {
+    long long base;      // index of the lower corner
+    float fx, fy, fz;
+};
+
+__device__ __forceinline__ Cell cell_of(float x, float y, float z, int nx, int ny, int nz)
+{
+    Cell c;
+    int i, j, k;
+    locate(x, nx, i, c.fx);
+    locate(y, ny, j, c.fy);
+    locate(z, nz, k, c.fz);
+    c.base = ((long long)k * ny + j) * nx + i;
+    return c;
+}
+
+// Cell indices of a sample (clamped as in cell_of) and its fractions.
+struct CellIJK {
+    int i, j, k;
+    float fx, fy, fz;
+};
+
+__device__ __forceinline__ CellIJK cell_ijk(float x, float y, float z, int nx, int ny, int nz)
+{
+    CellIJK c;
+    locate(x, nx, c.i, c.fx);
+    locate(y, ny, c.j, c.fy);
+    locate(z, nz, c.k, c.fz);
+    return c;
+}
+
+// A ray's window on the eight key points of the cell it is in.  Slot s holds
+// the key point whose node coordinates have parities (s & 1, (s >> 1) & 1,
+// s >> 2), so that a step across one cell face keeps four key points in their
+// slots and only the four slots of the departing plane change owner: they are
+// released (leave) and refilled for the arriving plane (enter).  Trilinear
+// weights and key-point distances are the usual ones written with the
+// fraction mirrored where the cell index is odd (mirror_frac).
+struct Win {
+    int ci, cj, ck;
+    long long base;   // node index of (ci, cj, ck)
+    bool live;
+};
+
+__device__ __forceinline__ long long slot_node(const Win& W, int s, int nx, long long nxy)
+{
+    const int dx = (s & 1) ^ (W.ci & 1), dy = ((s >> 1) & 1) ^ (W.cj & 1), dz = (s >> 2) ^ (W.ck & 1);
+    return W.base + dx + dy * (long long)nx + dz * nxy;
+}
+
+// op(slot, node) on the four slots whose AX bit equals q
+template <int AX, class Op>
+__device__ __forceinline__ void win_plane(const Win& W, int q, int nx, long long nxy, Op&& op)
+{
+    constexpr int bit = 1 << AX;
+    if (q) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            if (t & bit) op(t, slot_node(W, t, nx, nxy));
+    } else {
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            if (!(t & bit)) op(t, slot_node(W, t, nx, nxy));
+    }
+}
+
+template <class Leave, class Enter>
+__device__ __forceinline__ void win_move(Win& W, int i, int j, int k, int nx, int ny, long long nxy,
+                                         Leave&& leave, Enter&& enter)
+{
+    if (W.live && i == W.ci && j == W.cj && k == W.ck) return;
+    const int di = i - W.ci, dj = j - W.cj, dk = k - W.ck;
+    if (!W.live || abs(di) > 1 || abs(dj) > 1 || abs(dk) > 1) {
+        if (W.live) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) leave(t, slot_node(W, t, nx, nxy));
+        }
+        W.ci = i; W.cj = j; W.ck = k;
+        W.base = ((long long)k * ny + j) * nx + i;
+        W.live = true;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) enter(t, slot_node(W, t, nx, nxy));
+        return;
+    }
+    if (di) {
+        const int q = di > 0 ? (W.ci & 1) : ((W.ci + 1) & 1);
+        win_plane<0>(W, q, nx, nxy, leave);
+        W.ci += di;
+        W.base += di;
+        win_plane<0>(W, q, nx, nxy, enter);
+    }
+    if (dj) {
+        const int q = dj > 0 ? (W.cj & 1) : ((W.cj + 1) & 1);
+        win_plane<1>(W, q, nx, nxy, leave);
+        W.cj += dj;
+        W.base += (long long)dj * nx;
+        win_plane<1>(W, q, nx, nxy, enter);
+    }
+    if (dk) {
+        const int q = dk > 0 ? (W.ck & 1) : ((W.ck + 1) & 1);
+        win_plane<2>(W, q, nx, nxy, leave);
+        W.ck += dk;
+        W.base += (long long)dk * nxy;
+        win_plane<2>(W, q, nx, nxy, enter);
+    }
+}
+
+template <class Leave>
+__device__ __forceinline__ void win_release(const Win& W, int nx, long long nxy, Leave&& leave)
+{
+    if (!W.live) return;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) leave(t, slot_node(W, t, nx, nxy));
+}
+
+// Fraction toward the odd-parity key point along one axis.
+__device__ __forceinline__ float mirror_frac(int cell, float f) { return (cell & 1) ? 1.0f - f : f; }
+
+// ---------------------------------------------------------------------------
+// Node records
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+
+__device__ __forceinline__ float2 f16x2(uint32_t v)
+{
+    __half2 h = *reinterpret_cast<__half2*>(&v);
+    return __half22float2(h);
+}
+
+// RGB record {S_r, S_g, S_b, sigma} of node `idx`.
+template <int DT>
+__device__ __forceinline__ float4 load_rgb(const void* vol, long long idx)
+{
+    if constexpr (DT == DT_F32) {
+        return __ldg(reinterpret_cast<const float4*>(vol) + idx);
+    } else {
+        uint2 u = __ldg(reinterpret_cast<const uint2*>(vol) + idx);
+        if constexpr (DT == DT_BF16) {
+            return make_float4(bf16_lo(u.x), bf16_hi(u.x), bf16_lo(u.y), bf16_hi(u.y));
+        } else {
+            float2 a = f16x2(u.x), b = f16x2(u.y);
+            return make_float4(a.x, a.y, b.x, b.y);
+        }
+    }
+}
+
+// sigma of an RGB record.
+template <int DT>
+__device__ __forceinline__ float load_rgb_sigma(const void* vol, long long idx)
+{
+    if constexpr (DT == DT_F32) {
+        return __ldg(reinterpret_cast<const float*>(vol) + 4 * idx + 3);
+    } else if constexpr (DT == DT_BF16) {
+        return __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(vol) + 4 * idx + 3) << 16);
+    } else {
+        unsigned short h = __ldg(reinterpret_cast<const unsigned short*>(vol) + 4 * idx + 3);
+        return __half2float(__ushort_as_half(h));
+    }
+}
+
+// Temperature record {T, sigma}.
+template <int DT>
+__device__ __forceinline__ float2 load_ts(const void* vol, long long idx)
+{
+    if constexpr (DT == DT_F32) {
+        return __ldg(reinterpret_cast<const float2*>(vol) + idx);
+    } else {
+        uint32_t u = __ldg(reinterpret_cast<const unsigned int*>(vol) + idx);
+        if constexpr (DT == DT_BF16) return make_float2(bf16_lo(u), bf16_hi(u));
+        else return f16x2(u);
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void store_rgb(void* vol, long long idx, float4 v)
+{
+    if constexpr (DT == DT_F32) {
+        reinterpret_cast<float4*>(vol)[idx] = v;
+    } else if constexpr (DT == DT_BF16) {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t*>(&a);
+        u.y = *reinterpret_cast<uint32_t*>(&b);
+        reinterpret_cast<uint2*>(vol)[idx] = u;
+    } else {
+        __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t*>(&a);
+        u.y = *reinterpret_cast<uint32_t*>(&b);
+        reinterpret_cast<uint2*>(vol)[idx] = u;
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void store_ts(void* vol, long long idx, float2 v)
+{
+    if constexpr (DT == DT_F32) {
+        reinterpret_cast<float2*>(vol)[idx] = v;
+    } else if constexpr (DT == DT_BF16) {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+        reinterpret_cast<__nv_bfloat162*>(vol)[idx] = a;
+    } else {
+        reinterpret_cast<__half2*>(vol)[idx] = __floats2half2_rn(v.x, v.y);
+    }
+}
+
+__device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+__device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t)
+{
+    return make_float4(lerpf(a.x, b.x, t), lerpf(a.y, b.y, t), lerpf(a.z, b.z, t), lerpf(a.w, b.w, t));
+}
+
+__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float t)
+{
+    return make_float2(lerpf(a.x, b.x, t), lerpf(a.y, b.y, t));
+}
+
+// Trilinear blend of the eight RGB records around a sample.
+template <int DT>
+__device__ __forceinline__ float4 sample_rgb(const void* vol, const Cell& c, int nx, long long nxy)
+{
+    const long long b = c.base;
+    float4 v000 = load_rgb<DT>(vol, b), v100 = load_rgb<DT>(vol, b + 1);
+    float4 v010 = load_rgb<DT>(vol, b + nx), v110 = load_rgb<DT>(vol, b + nx + 1);
+    float4 v001 = load_rgb<DT>(vol, b + nxy), v101 = load_rgb<DT>(vol, b + nxy + 1);
+    float4 v011 = load_rgb<DT>(vol, b + nxy + nx), v111 = load_rgb<DT>(vol, b + nxy + nx + 1);
+    float4 c00 = lerp4(v000, v100, c.fx), c10 = lerp4(v010, v110, c.fx);
+    float4 c01 = lerp4(v001, v101, c.fx), c11 = lerp4(v011, v111, c.fx);
+    return lerp4(lerp4(c00, c10, c.fy), lerp4(c01, c11, c.fy), c.fz);
+}
+
+template <int DT>
+__device__ __forceinline__ float sample_rgb_sigma(const void* vol, const Cell& c, int nx, long long nxy)
+{
+    const long long b = c.base;
+    float s000 = load_rgb_sigma<DT>(vol, b), s100 = load_rgb_sigma<DT>(vol, b + 1);
+    float s010 = load_rgb_sigma<DT>(vol, b + nx), s110 = load_rgb_sigma<DT>(vol, b + nx + 1);
+    float s001 = load_rgb_sigma<DT>(vol, b + nxy), s101 = load_rgb_sigma<DT>(vol, b + nxy + 1);
+    float s011 = load_rgb_sigma<DT>(vol, b + nxy + nx), s111 = load_rgb_sigma<DT>(vol, b + nxy + nx + 1);
+    float c00 = lerpf(s000, s100, c.fx), c10 = lerpf(s010, s110, c.fx);
+    float c01 = lerpf(s001, s101, c.fx), c11 = lerpf(s011, s111, c.fx);
+    return lerpf(lerpf(c00, c10, c.fy), lerpf(c01, c11, c.fy), c.fz);
+}
+
+template <int DT>
+__device__ __forceinline__ float2 sample_ts(const void* vol, const Cell& c, int nx, long long nxy)
+{
+    const long long b = c.base;
+    float2 v000 = load_ts<DT>(vol, b), v100 = load_ts<DT>(vol, b + 1);
+    float2 v010 = load_ts<DT>(vol, b + nx), v110 = load_ts<DT>(vol, b + nx + 1);
+    float2 v001 = load_ts<DT>(vol, b + nxy), v101 = load_ts<DT>(vol, b + nxy + 1);
+    float2 v011 = load_ts<DT>(vol, b + nxy + nx), v111 = load_ts<DT>(vol, b + nxy + nx + 1);
+    float2 c00 = lerp2(v000, v100, c.fx), c10 = lerp2(v010, v110, c.fx);
+    float2 c01 = lerp2(v001, v101, c.fx), c11 = lerp2(v011, v111, c.fx);
+    return lerp2(lerp2(c00, c10, c.fy), lerp2(c01, c11, c.fy), c.fz);
+}
+
+// Piecewise-linear colour-temperature lookup and the slope of that
+// interpolant (zero outside the table, where the value is clamped).
+__device__ __forceinline__ void lut_eval(const ProbDev& P, float T, float q[3], float dq[3])
+{
+    float u = (T - P.lut_t0) * P.lut_scale;
+    const float umax = (float)(P.lut_m - 1);
+    bool inside = (u >= 0.0f) && (u <= umax);
+    u = fminf(fmaxf(u, 0.0f), umax);
+    int i = min((int)u, P.lut_m - 2);
+    float f = u - (float)i;
+    float4 a = __ldg(P.lut + i), b = __ldg(P.lut + i + 1);
+    q[0] = lerpf(a.x, b.x, f);
+    q[1] = lerpf(a.y, b.y, f);
+    q[2] = lerpf(a.z, b.z, f);
+    float s = inside ? P.lut_scale : 0.0f;
+    dq[0] = (b.x - a.x) * s;
+    dq[1] = (b.y - a.y) * s;
+    dq[2] = (b.z - a.z) * s;
+}
+
+// (1 - exp(-a)) / sigma for a = sigma * len, given e = exp(-a); a Taylor
+// series near a = 0 avoids the cancellation in 1 - e.
+__device__ __forceinline__ float seg_weight(float sig, float len, float e)
+{
+    float a = sig * len;
+    if (fabsf(a) < 0.1f) {
+        return len * (1.0f - a * (0.5f - a * (1.0f / 6.0f - a * (1.0f / 24.0f - a * (1.0f / 120.0f - a * (1.0f / 720.0f))))));
+    }
+    return (1.0f - e) / sig;
+}
+
+// d/dsigma of seg_weight.
+__device__ __forceinline__ float seg_weight_dsigma(float sig, float len, float e, float beta)
+{
+    float a = sig * len;
+    if (fabsf(a) < 0.1f) {
+        return -len * len * (0.5f - a * (1.0f / 3.0f - a * (1.0f / 8.0f - a * (1.0f / 30.0f - a * (1.0f / 144.0f)))));
+    }
+    return (len * e - beta) / sig;
+}
+
+// ---------------------------------------------------------------------------
+// G(s) of Eq. 11: outputs 2c+1 and 2c+2 of the SplitMix64 sequence started at
+// `seed` (Steele, Lea and Flood, OOPSLA 2014), c = (iteration, view, pixel,
+// sample) packed in 64 bits, made Gaussian by the Box-Muller transform.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long splitmix_out(unsigned long long seed, unsigned long long n)
+{
+    unsigned long long z = seed + n * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ float g_draw(unsigned long long seed, float g_std, int iteration, int view,
+                                        int pixel, int k)
+{
+    unsigned long long c = ((unsigned long long)iteration << 44) | ((unsigned long long)view << 36) |
+                           ((unsigned long long)pixel << 14) | (unsigned long long)k;
+    unsigned long long r1 = splitmix_out(seed, 2 * c + 1), r2 = splitmix_out(seed, 2 * c + 2);
+    float u1 = ((float)(r1 >> 40) + 0.5f) * (1.0f / 16777216.0f);
+    float u2 = (float)(r2 >> 40) * (1.0f / 16777216.0f);
+    return 1.0f + g_std * sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+// ---------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};"
+                 :: "l"(addr), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+__device__ __forceinline__ void red_add_v2(float* addr, float a, float b)
+{
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" :: "l"(addr), "f"(a), "f"(b) : "memory");
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// View and pixel of the calling thread's ray in CTA tile `tile`.
+__device__ __forceinline__ void tile_pixel(const ProbDev& P, int tile, int& view, int& px, int& py)
+{
+    const int per_view = P.tiles_x * P.tiles_y;
+    view = tile / per_view;
+    const int t = tile - view * per_view;
+    const int ty = t / P.tiles_x, tx = t - ty * P.tiles_x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    px = tx * kTileW + (w & 1) * 8 + (lane & 7);
+    py = ty * kTileH + (w >> 1) * 4 + (lane >> 3);
+}
+
+__device__ __forceinline__ int find_problem(const int* __restrict__ tile_start, int nprob, int b)
+{
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tile_start + mid) <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace frk

@@ -1,0 +1,48 @@
+// fr_internal.h -- launchers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fr_device.cuh"
+
+namespace frk {
+
+constexpr int kMaxViews = 32;
+
+// Kernel argument block of single-problem launches: the problem and its
+// cameras travel by value in the kernel's parameter space (no device copy).
+struct SingleArgs {
+    ProbDev p;
+    CamDev cams[kMaxViews];
+};
+
+inline int tiles_of(int W, int H, int ncam)
+{
+    return ((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH) * ncam;
+}
+
+// march.cu
+cudaError_t launch_fwd(const SingleArgs& a, int dt, int kind, int ntiles, cudaStream_t s);
+cudaError_t launch_fwd_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
+                             int dt, int kind, bool tau, cudaStream_t s);
+cudaError_t launch_adjust(const SingleArgs& a, int dt, int ntiles, cudaStream_t s);
+cudaError_t launch_adjust_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
+                                int dt, bool tau, cudaStream_t s);
+cudaError_t launch_backward(const SingleArgs& a, int dt, int kind, int ntiles, cudaStream_t s);
+cudaError_t launch_backward_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
+                                  int dt, int kind, bool tau, cudaStream_t s);
+cudaError_t launch_count(const SingleArgs& a, int ntiles, cudaStream_t s);
+cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cudaStream_t s);
+
+// volume.cu
+cudaError_t launch_apply(void* vol, int dt, int kind, long long nodes, float* dV, float scale,
+                         int with_sigma, int clamp_nonneg, int zero_dV, cudaStream_t s);
+cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* albedo, float* J,
+                                  void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s);
+cudaError_t launch_planck_lut(float t_min, float t_max, int m, float* lut, cudaStream_t s);
+cudaError_t launch_prepare_targets(float* targets, int ncam, int H, int W, float thresh, int* bbox,
+                                   cudaStream_t s);
+cudaError_t launch_rmse(const float* sq4, int n, float* rmse3, cudaStream_t s);
+cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t s);
+
+}  // namespace frk

@@ -1,0 +1,512 @@
+// march.cu -- the ray-marching kernels of the reconstruction loop.
+//
+//  * fwd: renders every pixel (Eqs. 5-8; Algorithm 2, rendering half) and, in
+//    the same pass, forms the residual of the colour constraint (Sec. 3.3.2)
+//    and the squared-error partials of the error measure (Sec. 5.1).
+//  * adjust: the paper's adjustment (Eqs. 10-12; Algorithm 2, adjustment half),
+//    one thread per flame ray, accumulated with vector float reductions.
+//  * backward: the exact gradient of the rendered images with the per-segment
+//    transmittance recomputed along each ray.
+//  * count: samples per render / per adjustment (for throughput accounting).
+//
+// One thread marches one ray; a CTA covers a 16 x 8 pixel tile of one view.
+#include "fr_device.cuh"
+#include "fr_internal.h"
+
+// Launch bounds of the march kernels.  Building with -DFR_MARCH_MINB=n asks
+// the compiler for n resident CTAs per SM (capping registers).
+#ifdef FR_MARCH_MINB
+#define FR_MARCH_BOUNDS __launch_bounds__(frk::kTileThreads, FR_MARCH_MINB)
+#else
+#define FR_MARCH_BOUNDS __launch_bounds__(frk::kTileThreads)
+#endif
+
+
+namespace frk {
+
+// ---------------------------------------------------------------------------
+// Shared pieces
+// ---------------------------------------------------------------------------
+
+// Trilinear blend of eight parity slots with mirrored fractions gx, gy, gz.
+template <class R>
+__device__ __forceinline__ R slot_blend(const R* v, float gx, float gy, float gz);
+
+template <>
+__device__ __forceinline__ float4 slot_blend<float4>(const float4* v, float gx, float gy, float gz)
+{
+    float4 a = lerp4(v[0], v[1], gx), b = lerp4(v[2], v[3], gx);
+    float4 c = lerp4(v[4], v[5], gx), d = lerp4(v[6], v[7], gx);
+    return lerp4(lerp4(a, b, gy), lerp4(c, d, gy), gz);
+}
+
+template <>
+__device__ __forceinline__ float2 slot_blend<float2>(const float2* v, float gx, float gy, float gz)
+{
+    float2 a = lerp2(v[0], v[1], gx), b = lerp2(v[2], v[3], gx);
+    float2 c = lerp2(v[4], v[5], gx), d = lerp2(v[6], v[7], gx);
+    return lerp2(lerp2(a, b, gy), lerp2(c, d, gy), gz);
+}
+
+template <>
+__device__ __forceinline__ float slot_blend<float>(const float* v, float gx, float gy, float gz)
+{
+    float a = lerpf(v[0], v[1], gx), b = lerpf(v[2], v[3], gx);
+    float c = lerpf(v[4], v[5], gx), d = lerpf(v[6], v[7], gx);
+    return lerpf(lerpf(a, b, gy), lerpf(c, d, gy), gz);
+}
+
+template <int DT, int KIND>
+struct RecOf;
+template <int DT>
+struct RecOf<DT, KIND_RGB> {
+    using T = float4;
+    static __device__ __forceinline__ float4 load(const void* vol, long long i) { return load_rgb<DT>(vol, i); }
+};
+template <int DT>
+struct RecOf<DT, KIND_TEMP> {
+    using T = float2;
+    static __device__ __forceinline__ float2 load(const void* vol, long long i) { return load_ts<DT>(vol, i); }
+};
+
+// Source and extinction of a blended record (temperature through the table).
+template <int KIND>
+__device__ __forceinline__ void record_source(const ProbDev& P, float4 r, float S[3], float& sig, float dq[3])
+{
+    S[0] = r.x; S[1] = r.y; S[2] = r.z; sig = r.w;
+}
+
+__device__ __forceinline__ void record_source_temp(const ProbDev& P, float2 r, float S[3], float& sig, float dq[3])
+{
+    lut_eval(P, r.x, S, dq);
+    sig = r.y;
+}
+
+// ---------------------------------------------------------------------------
+// Forward render + residual
+// ---------------------------------------------------------------------------
+
+template <int DT, int KIND, bool TAU>
+__device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, int tile)
+{
+    int view, px, py;
+    tile_pixel(P, tile, view, px, py);
+    const bool valid = px < P.W && py < P.H;
+    float L0 = 0.0f, L1 = 0.0f, L2 = 0.0f;
+    if (valid) {
+        Ray R;
+        if (make_ray(cams[view], px, py, P.nx, P.ny, P.nz, P.step, R)) {
+            const long long nxy = (long long)P.nx * P.ny;
+            float T = 1.0f;
+            for (int k = 0; k < R.n; ++k) {
+                float len, x, y, z;
+                segment(R, P.step, k, len, x, y, z);
+                const Cell c = cell_of(x, y, z, P.nx, P.ny, P.nz);
+                float S[3], sig, dq[3];
+                if constexpr (KIND == KIND_RGB) {
+                    record_source<KIND>(P, sample_rgb<DT>(P.vol, c, P.nx, nxy), S, sig, dq);
+                } else {
+                    record_source_temp(P, sample_ts<DT>(P.vol, c, P.nx, nxy), S, sig, dq);
+                }
+                if constexpr (TAU) {
+                    const float w = T * P.tau;
+                    L0 = fmaf(w, S[0], L0); L1 = fmaf(w, S[1], L1); L2 = fmaf(w, S[2], L2);
+                    T *= 1.0f - P.tau;
+                } else {
+                    const float e = __expf(-sig * len);
+                    const float w = T * seg_weight(sig, len, e);
+                    L0 = fmaf(w, S[0], L0); L1 = fmaf(w, S[1], L1); L2 = fmaf(w, S[2], L2);
+                    T *= e;
+                }
+            }
+        }
+    }
+    // pixel epilogue: image, residual of the colour constraint, error sums
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, cnt = 0.0f;
+    if (valid) {
+        const long long pix = ((long long)view * P.H + py) * P.W + px;
+        if (P.rendered) {
+            float* o = P.rendered + 3 * pix;
+            o[0] = L0; o[1] = L1; o[2] = L2;
+        }
+        if (P.targets) {
+            const float* t = P.targets + 3 * pix;
+            const float t0 = t[0], t1 = t[1], t2 = t[2];
+            const float d0 = t0 - L0, d1 = t1 - L1, d2 = t2 - L2;
+            const bool flame = fmaxf(t0, fmaxf(t1, t2)) > P.thresh;
+            float* r = P.residual + 3 * pix;
+            r[0] = flame ? d0 : 0.0f;
+            r[1] = flame ? d1 : 0.0f;
+            r[2] = flame ? d2 : 0.0f;
+            const int* bb = P.bbox + 4 * view;
+            if (px >= bb[0] && px <= bb[2] && py >= bb[1] && py <= bb[3]) {
+                a0 = d0 * d0; a1 = d1 * d1; a2 = d2 * d2; cnt = 1.0f;
+            }
+        }
+    }
+    if (P.partials) {
+        __shared__ float red[4][kTileThreads / 32];
+        a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2); cnt = warp_sum(cnt);
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) { red[0][w] = a0; red[1][w] = a1; red[2][w] = a2; red[3][w] = cnt; }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            float s = 0.0f;
+#pragma unroll
+            for (int i = 0; i < kTileThreads / 32; ++i) s += red[threadIdx.x][i];
+            P.partials[4 * (long long)tile + threadIdx.x] = s;
+        }
+    }
+}
+
+template <int DT, int KIND, bool TAU>
+__global__ void FR_MARCH_BOUNDS fwd_single(const __grid_constant__ SingleArgs a)
+{
+    fwd_body<DT, KIND, TAU>(a.p, a.cams, blockIdx.x);
+}
+
+template <int DT, int KIND, bool TAU>
+__global__ void FR_MARCH_BOUNDS fwd_batch(const ProbDev* __restrict__ probs,
+                                                                          const int* __restrict__ tile_start,
+                                                                          int nprob)
+{
+    const int p = find_problem(tile_start, nprob, blockIdx.x);
+    const ProbDev& P = probs[p];
+    fwd_body<DT, KIND, TAU>(P, P.cams, blockIdx.x - __ldg(tile_start + p));
+}
+
+// ---------------------------------------------------------------------------
+// Adjustment, paper rule (Eqs. 10-12)
+// ---------------------------------------------------------------------------
+
+// dL is constant along a ray, so each key point collects the scalar sum of
+// G alpha_l T exp(-alpha_d D) over the ray's samples in its window slot and
+// receives that sum times dL when the ray leaves it.
+template <int DT, bool TAU>
+__device__ __forceinline__ void adj_body(const ProbDev& P, const CamDev* cams, int tile)
+{
+    int view, px, py;
+    tile_pixel(P, tile, view, px, py);
+    if (px >= P.W || py >= P.H) return;
+    const long long pix = ((long long)view * P.H + py) * P.W + px;
+    const float* g = P.img_in + 3 * pix;
+    const float dl0 = g[0] * P.img_scale, dl1 = g[1] * P.img_scale, dl2 = g[2] * P.img_scale;
+    if (dl0 == 0.0f && dl1 == 0.0f && dl2 == 0.0f) return;
+    Ray R;
+    if (!make_ray(cams[view], px, py, P.nx, P.ny, P.nz, P.step, R)) return;
+    const long long nxy = (long long)P.nx * P.ny;
+    const int pixel = py * P.W + px;
+    float acc[8], sg[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) { acc[t] = 0.0f; sg[t] = 0.0f; }
+    float* dV = P.dV;
+    const void* vol = P.vol;
+    auto leave = [&acc, dV, dl0, dl1, dl2](int t, long long node) {
+        const float w = acc[t];
+        if (w != 0.0f) red_add_v4(dV + 4 * node, w * dl0, w * dl1, w * dl2, 0.0f);
+        acc[t] = 0.0f;
+    };
+    auto enter = [&sg, vol](int t, long long node) {
+        if constexpr (!TAU) sg[t] = load_rgb_sigma<DT>(vol, node);
+    };
+    Win W;
+    W.live = false;
+    float T = 1.0f;
+    for (int k = 0; k < R.n; ++k) {
+        float len, x, y, z;
+        segment(R, P.step, k, len, x, y, z);
+        const CellIJK c = cell_ijk(x, y, z, P.nx, P.ny, P.nz);
+        win_move(W, c.i, c.j, c.k, P.nx, P.ny, nxy, leave, enter);
+        const float gx = mirror_frac(c.i, c.fx), gy = mirror_frac(c.j, c.fy), gz = mirror_frac(c.k, c.fz);
+        const float G = P.g_std > 0.0f ? g_draw(P.seed, P.g_std, P.iteration, view, pixel, k) : 1.0f;
+        const float base = G * P.alpha_l * T;
+        // squared distances (voxel units) from the sample to each slot's key point
+        const float ex[2] = {gx * gx, (1.0f - gx) * (1.0f - gx)};
+        const float ey[2] = {gy * gy, (1.0f - gy) * (1.0f - gy)};
+        const float ez[2] = {gz * gz, (1.0f - gz) * (1.0f - gz)};
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const float D = sqrtf(ex[t & 1] + ey[(t >> 1) & 1] + ez[t >> 2]);
+            acc[t] = fmaf(base, __expf(-P.alpha_d * D), acc[t]);
+        }
+        if constexpr (TAU) T *= 1.0f - P.tau;
+        else T *= __expf(-slot_blend<float>(sg, gx, gy, gz) * len);
+    }
+    win_release(W, P.nx, nxy, leave);
+}
+
+template <int DT, bool TAU>
+__global__ void FR_MARCH_BOUNDS adj_single(const __grid_constant__ SingleArgs a)
+{
+    adj_body<DT, TAU>(a.p, a.cams, blockIdx.x);
+}
+
+template <int DT, bool TAU>
+__global__ void FR_MARCH_BOUNDS adj_batch(const ProbDev* __restrict__ probs,
+                                                                          const int* __restrict__ tile_start,
+                                                                          int nprob)
+{
+    const int p = find_problem(tile_start, nprob, blockIdx.x);
+    const ProbDev& P = probs[p];
+    adj_body<DT, TAU>(P, P.cams, blockIdx.x - __ldg(tile_start + p));
+}
+
+// ---------------------------------------------------------------------------
+// Exact gradient of the rendered images
+// ---------------------------------------------------------------------------
+
+// Along a ray L = sum_k T_k S_k beta_k with T_{k+1} = T_k exp(-sigma_k l_k):
+//   dL/dS_k = T_k beta_k,
+//   dL/dsigma_k = T_k S_k dbeta_k/dsigma - l_k (L_total - sum_{m<=k} T_m S_m beta_m),
+// the suffix sum taken from the rendered L_total.  Per key point the window
+// accumulates {dS_r, dS_g, dS_b, dsigma} (RGB) or {dT, dsigma} (temperature).
+template <int DT, int KIND, bool TAU>
+__device__ __forceinline__ void bwd_body(const ProbDev& P, const CamDev* cams, int tile)
+{
+    int view, px, py;
+    tile_pixel(P, tile, view, px, py);
+    if (px >= P.W || py >= P.H) return;
+    const long long pix = ((long long)view * P.H + py) * P.W + px;
+    const float* gi = P.img_in + 3 * pix;
+    const float g0 = gi[0] * P.img_scale, g1 = gi[1] * P.img_scale, g2 = gi[2] * P.img_scale;
+    if (g0 == 0.0f && g1 == 0.0f && g2 == 0.0f) return;
+    Ray R;
+    if (!make_ray(cams[view], px, py, P.nx, P.ny, P.nz, P.step, R)) return;
+    const float* lt = P.L_total + 3 * pix;
+    const float Lt0 = lt[0], Lt1 = lt[1], Lt2 = lt[2];
+    const long long nxy = (long long)P.nx * P.ny;
+    float4 acc[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) acc[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float* dV = P.dV;
+    auto leave = [&acc, dV](int t, long long node) {
+        const float4 a = acc[t];
+        if (a.x != 0.0f || a.y != 0.0f || a.z != 0.0f || a.w != 0.0f) {
+            if constexpr (KIND == KIND_RGB) red_add_v4(dV + 4 * node, a.x, a.y, a.z, a.w);
+            else red_add_v2(dV + 2 * node, a.x, a.y);
+        }
+        acc[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    };
+    Win W;
+    W.live = false;
+    float T = 1.0f, p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
+    for (int k = 0; k < R.n; ++k) {
+        float len, x, y, z;
+        segment(R, P.step, k, len, x, y, z);
+        const CellIJK ci = cell_ijk(x, y, z, P.nx, P.ny, P.nz);
+        win_move(W, ci.i, ci.j, ci.k, P.nx, P.ny, nxy, leave, [](int, long long) {});
+        Cell c;
+        c.base = W.base; c.fx = ci.fx; c.fy = ci.fy; c.fz = ci.fz;
+        float S[3], sig, dq[3] = {0.0f, 0.0f, 0.0f};
+        if constexpr (KIND == KIND_RGB) record_source<KIND>(P, sample_rgb<DT>(P.vol, c, P.nx, nxy), S, sig, dq);
+        else record_source_temp(P, sample_ts<DT>(P.vol, c, P.nx, nxy), S, sig, dq);
+        float gS0, gS1, gS2, gsig;
+        if constexpr (TAU) {
+            const float w = T * P.tau;
+            gS0 = g0 * w; gS1 = g1 * w; gS2 = g2 * w;
+            gsig = 0.0f;
+            T *= 1.0f - P.tau;
+        } else {
+            const float e = __expf(-sig * len);
+            const float beta = seg_weight(sig, len, e);
+            const float db = seg_weight_dsigma(sig, len, e, beta);
+            const float tb = T * beta;
+            p0 = fmaf(tb, S[0], p0); p1 = fmaf(tb, S[1], p1); p2 = fmaf(tb, S[2], p2);
+            gS0 = g0 * tb; gS1 = g1 * tb; gS2 = g2 * tb;
+            const float tdb = T * db;
+            gsig = g0 * (tdb * S[0] - len * (Lt0 - p0)) + g1 * (tdb * S[1] - len * (Lt1 - p1)) +
+                   g2 * (tdb * S[2] - len * (Lt2 - p2));
+            T *= e;
+        }
+        float4 gv;
+        if constexpr (KIND == KIND_RGB) gv = make_float4(gS0, gS1, gS2, gsig);
+        else gv = make_float4(gS0 * dq[0] + gS1 * dq[1] + gS2 * dq[2], gsig, 0.0f, 0.0f);
+        const float gx = mirror_frac(ci.i, ci.fx), gy = mirror_frac(ci.j, ci.fy), gz = mirror_frac(ci.k, ci.fz);
+        const float wx[2] = {1.0f - gx, gx}, wy[2] = {1.0f - gy, gy}, wz[2] = {1.0f - gz, gz};
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const float w = wx[t & 1] * wy[(t >> 1) & 1] * wz[t >> 2];
+            acc[t].x = fmaf(w, gv.x, acc[t].x);
+            acc[t].y = fmaf(w, gv.y, acc[t].y);
+            acc[t].z = fmaf(w, gv.z, acc[t].z);
+            acc[t].w = fmaf(w, gv.w, acc[t].w);
+        }
+    }
+    win_release(W, P.nx, nxy, leave);
+}
+
+template <int DT, int KIND, bool TAU>
+__global__ void FR_MARCH_BOUNDS bwd_single(const __grid_constant__ SingleArgs a)
+{
+    bwd_body<DT, KIND, TAU>(a.p, a.cams, blockIdx.x);
+}
+
+template <int DT, int KIND, bool TAU>
+__global__ void FR_MARCH_BOUNDS bwd_batch(const ProbDev* __restrict__ probs,
+                                                                          const int* __restrict__ tile_start,
+                                                                          int nprob)
+{
+    const int p = find_problem(tile_start, nprob, blockIdx.x);
+    const ProbDev& P = probs[p];
+    bwd_body<DT, KIND, TAU>(P, P.cams, blockIdx.x - __ldg(tile_start + p));
+}
+
+// ---------------------------------------------------------------------------
+// Sample counting: segments of every ray (or of the rays with a non-zero
+// residual).
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kTileThreads) count_single(const __grid_constant__ SingleArgs a)
+{
+    const ProbDev& P = a.p;
+    int view, px, py;
+    tile_pixel(P, blockIdx.x, view, px, py);
+    unsigned n = 0;
+    if (px < P.W && py < P.H) {
+        bool use = true;
+        if (P.img_in) {
+            const float* g = P.img_in + 3 * (((long long)view * P.H + py) * P.W + px);
+            use = !(g[0] == 0.0f && g[1] == 0.0f && g[2] == 0.0f);
+        }
+        Ray R;
+        if (use && make_ray(a.cams[view], px, py, P.nx, P.ny, P.nz, P.step, R)) n = (unsigned)R.n;
+    }
+    const unsigned s = __reduce_add_sync(0xffffffffu, n);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(P.counter, (unsigned long long)s);
+}
+
+// Deterministic sum of the per-CTA squared-error partials of one problem.
+__global__ void __launch_bounds__(256) finalize_partials(const float* __restrict__ partials, int ntiles,
+                                                         float* __restrict__ out4)
+{
+    __shared__ float red[4][8];
+    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int i = threadIdx.x; i < ntiles; i += blockDim.x) {
+        const float4 v = reinterpret_cast<const float4*>(partials)[i];
+        s[0] += v.x; s[1] += v.y; s[2] += v.z; s[3] += v.w;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s[c] = warp_sum(s[c]);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        for (int c = 0; c < 4; ++c) red[c][w] = s[c];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        float t = 0.0f;
+        for (int i = 0; i < 8; ++i) t += red[threadIdx.x][i];
+        out4[threadIdx.x] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side dispatch
+// ---------------------------------------------------------------------------
+
+#define FR_DISPATCH_DT(dt, DTC, ...)                      \
+    switch (dt) {                                         \
+        case DT_F32: { constexpr int DTC = DT_F32; __VA_ARGS__; break; }   \
+        case DT_BF16: { constexpr int DTC = DT_BF16; __VA_ARGS__; break; } \
+        case DT_F16: { constexpr int DTC = DT_F16; __VA_ARGS__; break; }   \
+        default: return cudaErrorInvalidValue;            \
+    }
+
+cudaError_t launch_fwd(const SingleArgs& a, int dt, int kind, int ntiles, cudaStream_t s)
+{
+    const bool tau = a.p.tau > 0.0f;
+    dim3 grid(ntiles), block(kTileThreads);
+    FR_DISPATCH_DT(dt, D, {
+        if (kind == KIND_RGB) {
+            if (tau) fwd_single<D, KIND_RGB, true><<<grid, block, 0, s>>>(a);
+            else fwd_single<D, KIND_RGB, false><<<grid, block, 0, s>>>(a);
+        } else {
+            if (tau) fwd_single<D, KIND_TEMP, true><<<grid, block, 0, s>>>(a);
+            else fwd_single<D, KIND_TEMP, false><<<grid, block, 0, s>>>(a);
+        }
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
+                             int dt, int kind, bool tau, cudaStream_t s)
+{
+    dim3 grid(total_tiles), block(kTileThreads);
+    FR_DISPATCH_DT(dt, D, {
+        if (kind == KIND_RGB) {
+            if (tau) fwd_batch<D, KIND_RGB, true><<<grid, block, 0, s>>>(probs, tile_start, nprob);
+            else fwd_batch<D, KIND_RGB, false><<<grid, block, 0, s>>>(probs, tile_start, nprob);
+        } else {
+            if (tau) fwd_batch<D, KIND_TEMP, true><<<grid, block, 0, s>>>(probs, tile_start, nprob);
+            else fwd_batch<D, KIND_TEMP, false><<<grid, block, 0, s>>>(probs, tile_start, nprob);
+        }
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjust(const SingleArgs& a, int dt, int ntiles, cudaStream_t s)
+{
+    const bool tau = a.p.tau > 0.0f;
+    dim3 grid(ntiles), block(kTileThreads);
+    FR_DISPATCH_DT(dt, D, {
+        if (tau) adj_single<D, true><<<grid, block, 0, s>>>(a);
+        else adj_single<D, false><<<grid, block, 0, s>>>(a);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjust_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
+                                int dt, bool tau, cudaStream_t s)
+{
+    dim3 grid(total_tiles), block(kTileThreads);
+    FR_DISPATCH_DT(dt, D, {
+        if (tau) adj_batch<D, true><<<grid, block, 0, s>>>(probs, tile_start, nprob);
+        else adj_batch<D, false><<<grid, block, 0, s>>>(probs, tile_start, nprob);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const SingleArgs& a, int dt, int kind, int ntiles, cudaStream_t s)
+{
+    const bool tau = a.p.tau > 0.0f;
+    dim3 grid(ntiles), block(kTileThreads);
+    FR_DISPATCH_DT(dt, D, {
+        if (kind == KIND_RGB) {
+            if (tau) bwd_single<D, KIND_RGB, true><<<grid, block, 0, s>>>(a);
+            else bwd_single<D, KIND_RGB, false><<<grid, block, 0, s>>>(a);
+        } else {
+            if (tau) bwd_single<D, KIND_TEMP, true><<<grid, block, 0, s>>>(a);
+            else bwd_single<D, KIND_TEMP, false><<<grid, block, 0, s>>>(a);
+        }
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
+                                  int dt, int kind, bool tau, cudaStream_t s)
+{
+    dim3 grid(total_tiles), block(kTileThreads);
+    FR_DISPATCH_DT(dt, D, {
+        if (kind == KIND_RGB) {
+            if (tau) bwd_batch<D, KIND_RGB, true><<<grid, block, 0, s>>>(probs, tile_start, nprob);
+            else bwd_batch<D, KIND_RGB, false><<<grid, block, 0, s>>>(probs, tile_start, nprob);
+        } else {
+            if (tau) bwd_batch<D, KIND_TEMP, true><<<grid, block, 0, s>>>(probs, tile_start, nprob);
+            else bwd_batch<D, KIND_TEMP, false><<<grid, block, 0, s>>>(probs, tile_start, nprob);
+        }
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count(const SingleArgs& a, int ntiles, cudaStream_t s)
+{
+    count_single<<<ntiles, kTileThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cudaStream_t s)
+{
+    finalize_partials<<<1, 256, 0, s>>>(partials, ntiles, out4);
+    return cudaGetLastError();
+}
+
+}  // namespace frk

@@ -1,0 +1,292 @@
+// volume.cu -- per-node and per-pixel kernels around the ray marches:
+//  * apply: V <- V + scale dV (Eq. 11), clamp, re-round to the storage type;
+//  * scatter: axis sweeps for the in-scattered radiance (Eq. 5, third term,
+//    isotropic phase) and the source records S = q + albedo sigma J;
+//  * planck_lut: the colour-temperature table (Sec. 3.3.3);
+//  * prepare_targets: flame threshold and flame bounding boxes (Sec. 4.1);
+//  * rmse: the error measure of Sec. 5.1 from squared-error sums.
+#include "fr_device.cuh"
+#include "fr_internal.h"
+
+namespace frk {
+
+// ---------------------------------------------------------------------------
+// Apply the accumulated adjustment
+// ---------------------------------------------------------------------------
+
+template <int DT, int KIND>
+__global__ void __launch_bounds__(256) apply_kernel(void* vol, long long nodes, float* dV, float scale,
+                                                    int with_sigma, int clamp_nonneg, int zero_dV)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+         i += (long long)gridDim.x * blockDim.x) {
+        if constexpr (KIND == KIND_RGB) {
+            float4 v = load_rgb<DT>(vol, i);
+            float4 d = reinterpret_cast<float4*>(dV)[i];
+            v.x = fmaf(scale, d.x, v.x);
+            v.y = fmaf(scale, d.y, v.y);
+            v.z = fmaf(scale, d.z, v.z);
+            if (with_sigma) v.w = fmaf(scale, d.w, v.w);
+            if (clamp_nonneg) {
+                v.x = fmaxf(v.x, 0.0f); v.y = fmaxf(v.y, 0.0f); v.z = fmaxf(v.z, 0.0f);
+                if (with_sigma) v.w = fmaxf(v.w, 0.0f);
+            }
+            store_rgb<DT>(vol, i, v);
+            if (zero_dV) reinterpret_cast<float4*>(dV)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        } else {
+            float2 v = load_ts<DT>(vol, i);
+            float2 d = reinterpret_cast<float2*>(dV)[i];
+            v.x = fmaf(scale, d.x, v.x);
+            if (with_sigma) v.y = fmaf(scale, d.y, v.y);
+            if (clamp_nonneg) {
+                v.x = fmaxf(v.x, 0.0f);
+                if (with_sigma) v.y = fmaxf(v.y, 0.0f);
+            }
+            store_ts<DT>(vol, i, v);
+            if (zero_dV) reinterpret_cast<float2*>(dV)[i] = make_float2(0.0f, 0.0f);
+        }
+    }
+}
+
+static int grid_for(long long n, int block)
+{
+    long long g = (n + block - 1) / block;
+    const long long cap = 152LL * 16;  // enough resident CTAs for every SM
+    return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
+}
+
+cudaError_t launch_apply(void* vol, int dt, int kind, long long nodes, float* dV, float scale,
+                         int with_sigma, int clamp_nonneg, int zero_dV, cudaStream_t s)
+{
+    int g = grid_for(nodes, 256);
+#define FR_APPLY(D, K) apply_kernel<D, K><<<g, 256, 0, s>>>(vol, nodes, dV, scale, with_sigma, clamp_nonneg, zero_dV)
+    if (kind == KIND_RGB) {
+        if (dt == DT_F32) FR_APPLY(DT_F32, KIND_RGB);
+        else if (dt == DT_BF16) FR_APPLY(DT_BF16, KIND_RGB);
+        else FR_APPLY(DT_F16, KIND_RGB);
+    } else {
+        if (dt == DT_F32) FR_APPLY(DT_F32, KIND_TEMP);
+        else if (dt == DT_BF16) FR_APPLY(DT_BF16, KIND_TEMP);
+        else FR_APPLY(DT_F16, KIND_TEMP);
+    }
+#undef FR_APPLY
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// In-scattering: J = (1/6) sum over the six axis directions of the emitted
+// radiance arriving along grid lines; each unit segment between adjacent nodes
+// is sampled at its midpoint (the mean of its two end records).
+// ---------------------------------------------------------------------------
+
+// One thread per grid line along AXIS.  Pass 1 walks the line forward and
+// pass 2 backward; the x sweep initialises J, the z sweep (LAST) finishes it
+// and writes the source records.
+template <int DT, int AXIS, bool LAST>
+__global__ void __launch_bounds__(128) sweep_kernel(const void* em, const float* albedo, float* J,
+                                                    void* out, int nx, int ny, int nz)
+{
+    const int n_line = AXIS == 0 ? nx : (AXIS == 1 ? ny : nz);
+    const long long lines = AXIS == 0 ? (long long)ny * nz : (AXIS == 1 ? (long long)nx * nz : (long long)nx * ny);
+    const long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (line >= lines) return;
+    long long start, stride;
+    if constexpr (AXIS == 0) {
+        start = line * nx;                       // line = z * ny + y
+        stride = 1;
+    } else if constexpr (AXIS == 1) {
+        long long z = line / nx, x = line - z * nx;
+        start = z * (long long)nx * ny + x;
+        stride = nx;
+    } else {
+        start = line;                            // line = y * nx + x
+        stride = (long long)nx * ny;
+    }
+    float4* J4 = reinterpret_cast<float4*>(J);
+    const float sixth = 1.0f / 6.0f;
+    for (int pass = 0; pass < 2; ++pass) {
+        float L0 = 0.0f, L1 = 0.0f, L2 = 0.0f;
+        float4 prev = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int s = 0; s < n_line; ++s) {
+            const int pos = pass == 0 ? s : n_line - 1 - s;
+            const long long node = start + pos * stride;
+            float4 cur = load_rgb<DT>(em, node);
+            if (s > 0) {
+                float sig = 0.5f * (prev.w + cur.w);
+                float e = __expf(-sig);
+                float beta = seg_weight(sig, 1.0f, e);
+                L0 = fmaf(L0, e, 0.5f * (prev.x + cur.x) * beta);
+                L1 = fmaf(L1, e, 0.5f * (prev.y + cur.y) * beta);
+                L2 = fmaf(L2, e, 0.5f * (prev.z + cur.z) * beta);
+            }
+            prev = cur;
+            float4 j;
+            if (AXIS == 0 && pass == 0) {
+                j = make_float4(L0 * sixth, L1 * sixth, L2 * sixth, 0.0f);
+            } else {
+                j = J4[node];
+                j.x = fmaf(L0, sixth, j.x);
+                j.y = fmaf(L1, sixth, j.y);
+                j.z = fmaf(L2, sixth, j.z);
+            }
+            if (LAST && pass == 1) {
+                const float as = __ldg(albedo + node) * cur.w;
+                store_rgb<DT>(out, node, make_float4(fmaf(as, j.x, cur.x), fmaf(as, j.y, cur.y),
+                                                     fmaf(as, j.z, cur.z), cur.w));
+            }
+            J4[node] = j;
+        }
+    }
+}
+
+cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* albedo, float* J,
+                                  void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s)
+{
+    if (dt_in != dt_out) return cudaErrorInvalidValue;
+    const int B = 128;
+    long long lx = (long long)ny * nz, ly = (long long)nx * nz, lz = (long long)nx * ny;
+    unsigned gx = (unsigned)((lx + B - 1) / B), gy = (unsigned)((ly + B - 1) / B), gz = (unsigned)((lz + B - 1) / B);
+#define FR_SWEEPS(D)                                                                         \
+    sweep_kernel<D, 0, false><<<gx, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz);        \
+    sweep_kernel<D, 1, false><<<gy, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz);        \
+    sweep_kernel<D, 2, true><<<gz, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz)
+    if (dt_in == DT_F32) { FR_SWEEPS(DT_F32); }
+    else if (dt_in == DT_BF16) { FR_SWEEPS(DT_BF16); }
+    else { FR_SWEEPS(DT_F16); }
+#undef FR_SWEEPS
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Colour-temperature table: Planck's law (Sec. 3.3.3) integrated against three
+// Gaussian channel responses by the trapezoid rule, 380-780 nm in 1 nm steps,
+// normalised so that green(2000 K) = 1.
+// ---------------------------------------------------------------------------
+
+__device__ float planck_um(float lambda_um, float T)
+{
+    // second radiation constant h c / k in micrometre kelvin; the first
+    // constant cancels in the normalisation
+    const float c2 = 14387.768775f;
+    float l2 = lambda_um * lambda_um;
+    return 1.0f / (l2 * l2 * lambda_um * expm1f(c2 / (lambda_um * T)));
+}
+
+__device__ void channel_sums(float T, float out[3])
+{
+    const float mu[3] = {600.0f, 540.0f, 460.0f};
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+    for (int i = 0; i <= 400; ++i) {
+        float lam = 380.0f + (float)i;
+        float w = (i == 0 || i == 400) ? 0.5f : 1.0f;
+        float b = w * planck_um(lam * 1e-3f, T);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float u = (lam - mu[c]) * (1.0f / 40.0f);
+            acc[c] = fmaf(b, expf(-0.5f * u * u), acc[c]);
+        }
+    }
+    out[0] = acc[0]; out[1] = acc[1]; out[2] = acc[2];
+}
+
+__global__ void planck_lut_kernel(float t_min, float t_max, int m, float4* lut)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    float norm[3], v[3];
+    channel_sums(2000.0f, norm);
+    float T = t_min + (t_max - t_min) * (float)i / (float)(m - 1);
+    channel_sums(T, v);
+    float s = 1.0f / norm[1];
+    lut[i] = make_float4(v[0] * s, v[1] * s, v[2] * s, 0.0f);
+}
+
+cudaError_t launch_planck_lut(float t_min, float t_max, int m, float* lut, cudaStream_t s)
+{
+    planck_lut_kernel<<<(m + 127) / 128, 128, 0, s>>>(t_min, t_max, m, reinterpret_cast<float4*>(lut));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Target pre-processing (Sec. 4.1)
+// ---------------------------------------------------------------------------
+
+__global__ void bbox_init_kernel(int* bbox, int ncam, int W, int H)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < ncam) {
+        bbox[4 * v + 0] = W; bbox[4 * v + 1] = H; bbox[4 * v + 2] = -1; bbox[4 * v + 3] = -1;
+    }
+}
+
+// One thread per pixel; grid.y = view.  Rows of the launch are image rows so
+// a warp never straddles two views.
+__global__ void __launch_bounds__(256) prepare_kernel(float* targets, int W, int H, float thresh, int* bbox)
+{
+    const int v = blockIdx.y;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const bool in = i < (long long)W * H;
+    int px = 0, py = 0;
+    bool flame = false;
+    if (in) {
+        py = (int)(i / W);
+        px = (int)(i - (long long)py * W);
+        float* t = targets + 3 * ((long long)v * W * H + i);
+        flame = fmaxf(t[0], fmaxf(t[1], t[2])) > thresh;
+        if (!flame) { t[0] = 0.0f; t[1] = 0.0f; t[2] = 0.0f; }
+    }
+    const unsigned any = __ballot_sync(0xffffffffu, flame);
+    if (!any) return;
+    int x0 = __reduce_min_sync(0xffffffffu, flame ? px : INT_MAX);
+    int y0 = __reduce_min_sync(0xffffffffu, flame ? py : INT_MAX);
+    int x1 = __reduce_max_sync(0xffffffffu, flame ? px : -1);
+    int y1 = __reduce_max_sync(0xffffffffu, flame ? py : -1);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(bbox + 4 * v + 0, x0);
+        atomicMin(bbox + 4 * v + 1, y0);
+        atomicMax(bbox + 4 * v + 2, x1);
+        atomicMax(bbox + 4 * v + 3, y1);
+    }
+}
+
+cudaError_t launch_prepare_targets(float* targets, int ncam, int H, int W, float thresh, int* bbox,
+                                   cudaStream_t s)
+{
+    bbox_init_kernel<<<(ncam + 31) / 32, 32, 0, s>>>(bbox, ncam, W, H);
+    long long npx = (long long)W * H;
+    dim3 grid((unsigned)((npx + 255) / 256), ncam);
+    prepare_kernel<<<grid, 256, 0, s>>>(targets, W, H, thresh, bbox);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Error measure and fills
+// ---------------------------------------------------------------------------
+
+__global__ void rmse_kernel(const float* sq4, int n, float* rmse3)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float cnt = sq4[4 * i + 3];
+    for (int c = 0; c < 3; ++c) rmse3[3 * i + c] = cnt > 0.0f ? 255.0f * sqrtf(sq4[4 * i + c] / cnt) : 0.0f;
+}
+
+cudaError_t launch_rmse(const float* sq4, int n, float* rmse3, cudaStream_t s)
+{
+    rmse_kernel<<<(n + 127) / 128, 128, 0, s>>>(sq4, n, rmse3);
+    return cudaGetLastError();
+}
+
+__global__ void fill_kernel(float* p, long long n, float v)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t s)
+{
+    fill_kernel<<<grid_for(n, 256), 256, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+}  // namespace frk

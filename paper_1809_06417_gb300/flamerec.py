@@ -1,0 +1,238 @@
+"""Thin ctypes binding of libflamerec.so (include/flamerec.h).
+
+Argument marshalling only: torch tensors supply device memory and the CUDA
+stream; every step of the reconstruction runs in the library's kernels.  There
+is no CPU fallback: loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libflamerec.so")
+
+FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_ETIMEDOUT, FR_EBUSY, FR_ECANCELED = range(7)
+FR_F32, FR_BF16, FR_F16 = 0, 1, 2
+FR_KIND_RGB, FR_KIND_TEMP = 0, 1
+FR_RULE_PAPER, FR_RULE_GRADIENT = 0, 1
+FR_MAX_VIEWS = 32
+
+STATUS_NAMES = {0: "FR_OK", 1: "FR_EINVAL", 2: "FR_ENOMEM", 3: "FR_ECUDA", 4: "FR_ETIMEDOUT",
+                5: "FR_EBUSY", 6: "FR_ECANCELED"}
+
+
+class FrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class fr_volume(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("kind", ctypes.c_int32), ("dtype", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("origin", ctypes.c_float * 3), ("h", ctypes.c_float), ("data", ctypes.c_void_p)]
+
+
+class fr_camera(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_float * 3), ("right", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
+                ("fwd", ctypes.c_float * 3), ("tan_half_fov", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+class fr_params(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_float), ("alpha_l", ctypes.c_float), ("alpha_d", ctypes.c_float),
+                ("tau", ctypes.c_float), ("g_std", ctypes.c_float), ("flame_thresh", ctypes.c_float),
+                ("seed", ctypes.c_uint64), ("clamp_nonneg", ctypes.c_int32), ("rule", ctypes.c_int32),
+                ("grad_step", ctypes.c_float), ("update_sigma", ctypes.c_int32),
+                ("lut_t_min", ctypes.c_float), ("lut_t_max", ctypes.c_float), ("lut", ctypes.c_void_p),
+                ("lut_size", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_F = ctypes.c_float
+_S = ctypes.c_int  # fr_status
+
+# name -> (restype, argtypes), exactly the declarations of include/flamerec.h
+SIGNATURES = {
+    "fr_abi_version": (ctypes.c_int32, []),
+    "fr_params_default": (None, [_P]),
+    "fr_create": (_S, [_P, _I, _P]),
+    "fr_destroy": (_S, [_P]),
+    "fr_set_stream": (_S, [_P, _P]),
+    "fr_last_error": (ctypes.c_char_p, [_P]),
+    "fr_synchronize": (_S, [_P]),
+    "fr_prepare_targets": (_S, [_P, _I, _I, _I, _P, _F, _P]),
+    "fr_render": (_S, [_P, _P, _P, _I, _P, _P]),
+    "fr_render_residual": (_S, [_P, _P, _P, _I, _P, _P, _P, _P, _P, _P]),
+    "fr_adjust": (_S, [_P, _P, _P, _I, _P, _P, _I, _P]),
+    "fr_apply_update": (_S, [_P, _P, _P, _F, _I, _I, _I]),
+    "fr_render_backward": (_S, [_P, _P, _P, _I, _P, _P, _P, _P]),
+    "fr_scatter_source": (_S, [_P, _P, _P, _P, _P]),
+    "fr_planck_lut": (_S, [_P, _F, _F, _I, _P]),
+    "fr_reconstruct": (_S, [_P, _P, _P, _P, _I, _P, _I, _P, _I, _I, _P, _P, _I]),
+    "fr_count_samples": (_S, [_P, _P, _P, _I, _P, _P, _P]),
+}
+
+_lib = None
+
+
+def load():
+    """Load the library (building it first if its sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    path = _build.build()
+    if not os.path.exists(path):
+        raise FrError(FR_ECUDA, f"libflamerec.so missing at {path}")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    """Device (or host) address of a torch tensor or numpy array, or None."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def params(**kw) -> fr_params:
+    p = fr_params()
+    load().fr_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "lut":
+            p.lut = _ptr(v)
+            if v is not None:
+                p.lut_size = int(v.shape[0])
+            continue
+        if not hasattr(p, k):
+            raise AttributeError(f"fr_params has no field {k}")
+        setattr(p, k, v)
+    return p
+
+
+def cameras(cams) -> ctypes.Array:
+    """fr_camera array from dicts with pos, right, up, fwd, tan_half_fov, width, height."""
+    arr = (fr_camera * len(cams))()
+    for c, s in zip(arr, cams):
+        for key in ("pos", "right", "up", "fwd"):
+            setattr(c, key, (ctypes.c_float * 3)(*[float(x) for x in s[key]]))
+        c.tan_half_fov = float(s["tan_half_fov"])
+        c.width, c.height = int(s["width"]), int(s["height"])
+    return arr
+
+
+_DT = {"float32": FR_F32, "bfloat16": FR_BF16, "float16": FR_F16}
+
+
+def volume(t, origin, h, kind=FR_KIND_RGB) -> fr_volume:
+    """Descriptor of a (nz, ny, nx, C) CUDA tensor (C = 4 for RGB, 2 for TEMP)."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise FrError(FR_EINVAL, "volume tensor must be a contiguous CUDA tensor")
+    nz, ny, nx, ncomp = t.shape
+    if ncomp != (4 if kind == FR_KIND_RGB else 2):
+        raise FrError(FR_EINVAL, f"kind {kind} needs {4 if kind == FR_KIND_RGB else 2} components, got {ncomp}")
+    dt = _DT.get(str(t.dtype).replace("torch.", ""))
+    if dt is None:
+        raise FrError(FR_EINVAL, f"unsupported storage dtype {t.dtype}")
+    v = fr_volume()
+    v.nx, v.ny, v.nz, v.kind, v.dtype = nx, ny, nz, kind, dt
+    v.origin = (ctypes.c_float * 3)(*[float(x) for x in origin])
+    v.h = float(h)
+    v.data = t.data_ptr()
+    return v
+
+
+class Context:
+    """An fr_ctx bound to a device and a stream (torch's current one by default)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.lib = load()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self._stream = stream
+        h = ctypes.c_void_p()
+        st = self.lib.fr_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream))
+        if st != FR_OK:
+            raise FrError(st, "fr_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, status):
+        if status != FR_OK:
+            raise FrError(status, self.lib.fr_last_error(self.h).decode())
+
+    # -- the C ABI, one method per entry point ------------------------------
+
+    def fr_prepare_targets(self, targets, thresh, bbox):
+        k, h, w, _ = targets.shape
+        self.check(self.lib.fr_prepare_targets(self.h, k, h, w, _ptr(targets), float(thresh), _ptr(bbox)))
+
+    def fr_render(self, vol: fr_volume, cams, p: fr_params, out):
+        self.check(self.lib.fr_render(self.h, ctypes.byref(vol), cams, len(cams), ctypes.byref(p), _ptr(out)))
+
+    def fr_render_residual(self, vol, cams, p, targets, bbox, rendered, residual, sq_err):
+        self.check(self.lib.fr_render_residual(self.h, ctypes.byref(vol), cams, len(cams), ctypes.byref(p),
+                                               _ptr(targets), _ptr(bbox), _ptr(rendered), _ptr(residual),
+                                               _ptr(sq_err)))
+
+    def fr_adjust(self, vol, cams, p, residual, iteration, dV):
+        self.check(self.lib.fr_adjust(self.h, ctypes.byref(vol), cams, len(cams), ctypes.byref(p),
+                                      _ptr(residual), int(iteration), _ptr(dV)))
+
+    def fr_apply_update(self, vol, dV, scale=1.0, with_sigma=False, clamp_nonneg=True, zero_dV=True):
+        self.check(self.lib.fr_apply_update(self.h, ctypes.byref(vol), _ptr(dV), float(scale), int(with_sigma),
+                                            int(clamp_nonneg), int(zero_dV)))
+
+    def fr_render_backward(self, vol, cams, p, L_total, grad_img, grad):
+        self.check(self.lib.fr_render_backward(self.h, ctypes.byref(vol), cams, len(cams), ctypes.byref(p),
+                                               _ptr(L_total), _ptr(grad_img), _ptr(grad)))
+
+    def fr_scatter_source(self, emission, albedo, J, out):
+        self.check(self.lib.fr_scatter_source(self.h, ctypes.byref(emission), _ptr(albedo), _ptr(J),
+                                              ctypes.byref(out)))
+
+    def fr_planck_lut(self, t_min, t_max, lut):
+        self.check(self.lib.fr_planck_lut(self.h, float(t_min), float(t_max), int(lut.shape[0]), _ptr(lut)))
+
+    def fr_reconstruct(self, vol, cams, targets, bbox, iters, p, albedo=None, first_iteration=0,
+                       rmse=None, targets_are_host=None):
+        if targets_are_host is None:
+            targets_are_host = not getattr(targets, "is_cuda", False)
+        rmse_is_host = rmse is not None and not getattr(rmse, "is_cuda", False)
+        self.check(self.lib.fr_reconstruct(self.h, ctypes.byref(vol), _ptr(albedo), cams, len(cams),
+                                           _ptr(targets), int(bool(targets_are_host)), _ptr(bbox), int(iters),
+                                           int(first_iteration), ctypes.byref(p), _ptr(rmse),
+                                           int(rmse_is_host)))
+
+    def fr_count_samples(self, vol, cams, p, residual=None):
+        n = ctypes.c_int64()
+        self.check(self.lib.fr_count_samples(self.h, ctypes.byref(vol), cams, len(cams), ctypes.byref(p),
+                                             _ptr(residual), ctypes.byref(n)))
+        return n.value
+
+    def fr_synchronize(self):
+        self.check(self.lib.fr_synchronize(self.h))
