@@ -29,7 +29,7 @@ struct Buf {
 struct fr_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;   // where work is queued (borrowed; 0 = default stream)
-    std::string err;
+    char err[512] = {0};             // last failure message
     Buf partials, counter, residual, rendered, dV, targets, sqerr, rmse, J, src;
     unsigned long long* host_counter = nullptr;
 };
@@ -39,12 +39,10 @@ namespace {
 fr_status fail(fr_ctx* c, fr_status s, const char* fmt, ...)
 {
     if (c) {
-        char buf[512];
         va_list ap;
         va_start(ap, fmt);
-        vsnprintf(buf, sizeof buf, fmt, ap);
+        vsnprintf(c->err, sizeof c->err, fmt, ap);
         va_end(ap);
-        c->err = buf;
     }
     return s;
 }
@@ -323,7 +321,7 @@ extern "C" fr_status fr_set_stream(fr_ctx* c, void* stream)
     return FR_OK;
 }
 
-extern "C" const char* fr_last_error(const fr_ctx* c) { return c ? c->err.c_str() : "null context"; }
+extern "C" const char* fr_last_error(const fr_ctx* c) { return c ? c->err : "null context"; }
 
 extern "C" fr_status fr_synchronize(fr_ctx* c)
 {
@@ -344,7 +342,7 @@ extern "C" fr_status fr_synchronize(fr_ctx* c)
 
 #define FR_BEGIN(c)                                   \
     if (!c) return FR_EINVAL;                         \
-    c->err.clear();                                   \
+    c->err[0] = '\0';                                 \
     FR_CUDA(c, cudaSetDevice(c->device))
 
 extern "C" fr_status fr_prepare_targets(fr_ctx* c, int ncam, int height, int width, float* targets,
