@@ -222,6 +222,30 @@ fr_status fr_count_samples(fr_ctx *ctx, const fr_volume *vol, const fr_camera *c
                            int ncam, const fr_params *p, const float *residual,
                            int64_t *samples);
 
+/* fr_render_residual without any allocation.  (The paper has no counterpart:
+ * this is a service for callers that cannot allocate device memory while they
+ * render -- e.g. a process that gives all device memory to its own pool at
+ * start-up, or a latency-critical loop that forbids cudaMalloc/cudaFree after
+ * start-up because they can synchronise the whole device.)
+ * Same results as fr_render_residual; the caller passes every input and
+ * output.  The per-tile squared-error partials live in one fixed device array
+ * compiled into the library (FR_NOALLOC_MAX_TILES tiles of 16 x 8 pixels,
+ * 1 MiB), which every GPU that loads the library holds until the process
+ * exits.  Images of more tiles, ncam * ceil(W/16) * ceil(H/8), are rejected
+ * with FR_EINVAL.  The first call on a device looks up that array's device
+ * address with the device made current (the calling thread's current device is
+ * restored afterwards); make that first call before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU (e.g. on two
+ * streams at once) race; calls queued one after another are safe, since every
+ * tile overwrites its own partials and nothing needs clearing.
+ * stream: cudaStream_t to queue on (NULL = default stream).  err (nullable):
+ * receives the failure message (empty on success), at most err_len bytes. */
+#define FR_NOALLOC_MAX_TILES 65536
+fr_status fr_render_residual_noalloc(int device, void *stream, const fr_volume *vol,
+                                     const fr_camera *cams, int ncam, const fr_params *p,
+                                     const float *targets, const int32_t *bbox, float *rendered,
+                                     float *residual, float *sq_err, char *err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

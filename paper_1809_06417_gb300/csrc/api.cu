@@ -613,3 +613,101 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
     }
     return FR_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Rendering with residual, without any allocation
+// ---------------------------------------------------------------------------
+//
+// fr_render_residual keeps its per-CTA squared-error partials in scratch that
+// the context allocates on first use.  Some callers cannot allocate device
+// memory when they render: a process that hands all device memory to its own
+// pool at start-up (a fresh cudaMalloc would fail or fragment that budget),
+// or a latency-critical loop that forbids cudaMalloc/cudaFree after start-up
+// because they can synchronise the whole device.  This variant keeps the
+// partials in a fixed file-scope device array instead, so it allocates
+// nothing, device or host.
+
+// FR_NOALLOC_MAX_TILES tiles of 16 x 8 pixels (4 floats each, 1 MiB in
+// total), held by every GPU that loads the library until the process exits.
+static __device__ __align__(256) float g_noalloc_partials[4 * FR_NOALLOC_MAX_TILES];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_partials on `device`, looked up once per device
+// with that device current.  In host code the array's name is only a host
+// stand-in: kernels must be given this address.
+fr_status noalloc_scratch(fr_ctx* c, int device, float** out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        int prev = 0;
+        FR_CUDA(c, cudaGetDevice(&prev));
+        FR_CUDA(c, cudaSetDevice(device));
+        void* addr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_partials);
+        cudaSetDevice(prev);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetSymbolAddress(g_noalloc_partials)");
+        g_noalloc_ptr[device] = static_cast<float*>(addr);
+    }
+    *out = g_noalloc_ptr[device];
+    return FR_OK;
+}
+
+}  // namespace
+
+extern "C" fr_status fr_render_residual_noalloc(int device, void* stream, const fr_volume* vol,
+                                                const fr_camera* cams, int ncam, const fr_params* p,
+                                                const float* targets, const int32_t* bbox, float* rendered,
+                                                float* residual, float* sq_err, char* err, size_t err_len)
+{
+    fr_ctx c;  // stack context for validation messages; holds no resources
+    c.device = device;
+    c.stream = static_cast<cudaStream_t>(stream);
+    auto done = [&](fr_status s) {
+        if (err && err_len) snprintf(err, err_len, "%s", s == FR_OK ? "" : c.err);
+        return s;
+    };
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return done(fail(&c, FR_ECUDA, "no CUDA device"));
+    }
+    if (device < 0 || device >= ndev || device >= kNoAllocMaxDevices)
+        return done(fail(&c, FR_EINVAL, "device %d out of range", device));
+    fr_status s;
+    if ((s = check_volume(&c, vol, "vol")) || (s = check_cams(&c, cams, ncam)) ||
+        (s = check_params(&c, p, vol, cams)))
+        return done(s);
+    const int nt = tiles_of(cams[0].width, cams[0].height, ncam);
+    if (nt > FR_NOALLOC_MAX_TILES)
+        return done(fail(&c, FR_EINVAL,
+                         "%d tiles of 16x8 pixels exceed the fixed scratch of %d tiles; use fr_render_residual",
+                         nt, FR_NOALLOC_MAX_TILES));
+    const size_t ib = image_bytes(cams, ncam);
+    if ((s = check_dev(&c, targets, ib, "targets")) ||
+        (s = check_dev(&c, bbox, (size_t)ncam * 4 * sizeof(int32_t), "bbox")) ||
+        (rendered && (s = check_dev(&c, rendered, ib, "rendered"))) ||
+        (s = check_dev(&c, residual, ib, "residual")) || (s = check_dev(&c, sq_err, 4 * sizeof(float), "sq_err")))
+        return done(s);
+    float* partials = nullptr;
+    if ((s = noalloc_scratch(&c, device, &partials))) return done(s);
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess)
+        return done(cuda_fail(&c, cudaGetLastError(), "cudaSetDevice"));
+    SingleArgs a;  // on the stack: no allocation
+    fill_problem(vol, cams, ncam, p, a);
+    a.p.targets = targets;
+    a.p.bbox = bbox;
+    a.p.rendered = rendered;
+    a.p.residual = residual;
+    a.p.partials = partials;  // every tile overwrites its own 4 floats: nothing to clear
+    cudaError_t e = launch_fwd(a, vol->dtype, vol->kind, nt, c.stream);
+    if (e == cudaSuccess) e = launch_finalize(partials, nt, sq_err, c.stream);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) return done(cuda_fail(&c, e, "launch"));
+    return done(FR_OK);
+}

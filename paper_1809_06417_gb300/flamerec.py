@@ -75,6 +75,8 @@ SIGNATURES = {
     "fr_planck_lut": (_S, [_P, _F, _F, _I, _P]),
     "fr_reconstruct": (_S, [_P, _P, _P, _P, _I, _P, _I, _P, _I, _I, _P, _P, _I]),
     "fr_count_samples": (_S, [_P, _P, _P, _I, _P, _P, _P]),
+    "fr_render_residual_noalloc": (_S, [_I, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, ctypes.c_char_p,
+                                        ctypes.c_size_t]),
 }
 
 _lib = None
@@ -131,6 +133,19 @@ def cameras(cams) -> ctypes.Array:
         c.tan_half_fov = float(s["tan_half_fov"])
         c.width, c.height = int(s["width"]), int(s["height"])
     return arr
+
+
+def fr_render_residual_noalloc(device, stream, vol, cams, p, targets, bbox, rendered, residual, sq_err):
+    """fr_render_residual without any allocation (fixed library scratch).
+    stream: a torch.cuda.Stream (or None for the default stream)."""
+    lib = load()
+    err = ctypes.create_string_buffer(512)
+    h = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    st = lib.fr_render_residual_noalloc(int(device), h, ctypes.byref(vol), cams, len(cams), ctypes.byref(p),
+                                        _ptr(targets), _ptr(bbox), _ptr(rendered), _ptr(residual),
+                                        _ptr(sq_err), err, len(err))
+    if st != FR_OK:
+        raise FrError(st, err.value.decode())
 
 
 _DT = {"float32": FR_F32, "bfloat16": FR_BF16, "float16": FR_F16}
