@@ -30,7 +30,7 @@ struct fr_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;   // where work is queued (borrowed; 0 = default stream)
     char err[512] = {0};             // last failure message
-    Buf partials, counter, residual, rendered, dV, targets, sqerr, rmse, J, src;
+    Buf partials, counter, residual, rendered, dV, targets, sqerr, rmse, J, src, flame_off, flame_list;
     unsigned long long* host_counter = nullptr;
 };
 
@@ -307,7 +307,7 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
-                   &c->rmse, &c->J, &c->src})
+                   &c->rmse, &c->J, &c->src, &c->flame_off, &c->flame_list})
         if (b->p) cudaFree(b->p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
     delete c;
@@ -558,6 +558,10 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
         FR_TRY(ensure(c, c->J, (size_t)nodes * 16, "J"));
         FR_TRY(ensure(c, c->src, (size_t)nodes * rec_bytes(vol), "source"));
     }
+    const long long npix = (long long)ncam * cams[0].width * cams[0].height;
+    if (npix >= (1LL << 32)) return fail(c, FR_EINVAL, "at most 2^32 pixels per reconstruction");
+    FR_TRY(ensure(c, c->flame_off, ((size_t)nt * (kTileThreads / 32) + 1) * sizeof(unsigned), "flame offsets"));
+    FR_TRY(ensure(c, c->flame_list, (size_t)npix * sizeof(unsigned), "flame list"));
     cudaStream_t s = c->stream;
     const float* tg = targets;
     if (targets_are_host) {
@@ -583,6 +587,11 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
     u.p.img_in = static_cast<const float*>(c->residual.p);
     u.p.dV = static_cast<float*>(c->dV.p);
     float* sq = static_cast<float*>(c->sqerr.p);
+    // flame rays, once per call: the targets do not change between iterations
+    unsigned* flame_off = static_cast<unsigned*>(c->flame_off.p);
+    unsigned* flame_list = static_cast<unsigned*>(c->flame_list.p);
+    const unsigned* flame_count = flame_off + (size_t)nt * (kTileThreads / 32);
+    FR_CUDA(c, launch_flame_list(f, nt, flame_off, flame_list, s));
     for (int it = 0; it < iters; ++it) {
         if (albedo)
             FR_CUDA(c, launch_scatter_source(vol->data, vol->dtype, albedo, static_cast<float*>(c->J.p), c->src.p,
@@ -591,7 +600,7 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
         FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * it, s));
         if (p->rule == FR_RULE_PAPER) {
             u.p.iteration = first_iteration + it;
-            FR_CUDA(c, launch_adjust(u, vol->dtype, nt, s));
+            FR_CUDA(c, launch_adjust_list(u, vol->dtype, nt, flame_list, flame_count, s));
             FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg, 1, s));
         } else {
             // d(0.5 sum m dL^2)/d(rendered) = -m dL: the residual scaled by -1

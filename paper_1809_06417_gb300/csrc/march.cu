@@ -86,9 +86,29 @@ __device__ __forceinline__ void record_source_temp(const ProbDev& P, float2 r, f
 // Forward render + residual
 // ---------------------------------------------------------------------------
 
+// The eight records of a cell, corner b = dx + 2 dy + 4 dz.
+template <int DT, int KIND>
+__device__ __forceinline__ void load8(const void* vol, long long base, int nx, long long nxy,
+                                      typename RecOf<DT, KIND>::T v[8])
+{
+    using Rec = RecOf<DT, KIND>;
+    v[0] = Rec::load(vol, base);
+    v[1] = Rec::load(vol, base + 1);
+    v[2] = Rec::load(vol, base + nx);
+    v[3] = Rec::load(vol, base + nx + 1);
+    v[4] = Rec::load(vol, base + nxy);
+    v[5] = Rec::load(vol, base + nxy + 1);
+    v[6] = Rec::load(vol, base + nxy + nx);
+    v[7] = Rec::load(vol, base + nxy + nx + 1);
+}
+
+// Forward march of one ray.  Consecutive samples often share a cell (at half a
+// voxel step about 2 in 5 do), so the cell's eight records stay in registers
+// and are reloaded only when the sample enters another cell.
 template <int DT, int KIND, bool TAU>
 __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, int tile)
 {
+    using RT = typename RecOf<DT, KIND>::T;
     int view, px, py;
     tile_pixel(P, tile, view, px, py);
     const bool valid = px < P.W && py < P.H;
@@ -97,17 +117,21 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
         Ray R;
         if (make_ray(cams[view], px, py, P.nx, P.ny, P.nz, P.step, R)) {
             const long long nxy = (long long)P.nx * P.ny;
+            RT v[8];
+            long long vbase = -1;
             float T = 1.0f;
             for (int k = 0; k < R.n; ++k) {
                 float len, x, y, z;
                 segment(R, P.step, k, len, x, y, z);
                 const Cell c = cell_of(x, y, z, P.nx, P.ny, P.nz);
-                float S[3], sig, dq[3];
-                if constexpr (KIND == KIND_RGB) {
-                    record_source<KIND>(P, sample_rgb<DT>(P.vol, c, P.nx, nxy), S, sig, dq);
-                } else {
-                    record_source_temp(P, sample_ts<DT>(P.vol, c, P.nx, nxy), S, sig, dq);
+                if (c.base != vbase) {
+                    vbase = c.base;
+                    load8<DT, KIND>(P.vol, c.base, P.nx, nxy, v);
                 }
+                const RT r = slot_blend<RT>(v, c.fx, c.fy, c.fz);
+                float S[3], sig, dq[3];
+                if constexpr (KIND == KIND_RGB) record_source<KIND>(P, r, S, sig, dq);
+                else record_source_temp(P, r, S, sig, dq);
                 if constexpr (TAU) {
                     const float w = T * P.tau;
                     L0 = fmaf(w, S[0], L0); L1 = fmaf(w, S[1], L1); L2 = fmaf(w, S[2], L2);
@@ -183,11 +207,8 @@ __global__ void FR_MARCH_BOUNDS fwd_batch(const ProbDev* __restrict__ probs,
 // G alpha_l T exp(-alpha_d D) over the ray's samples in its window slot and
 // receives that sum times dL when the ray leaves it.
 template <int DT, bool TAU>
-__device__ __forceinline__ void adj_body(const ProbDev& P, const CamDev* cams, int tile)
+__device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, int view, int px, int py)
 {
-    int view, px, py;
-    tile_pixel(P, tile, view, px, py);
-    if (px >= P.W || py >= P.H) return;
     const long long pix = ((long long)view * P.H + py) * P.W + px;
     const float* g = P.img_in + 3 * pix;
     const float dl0 = g[0] * P.img_scale, dl1 = g[1] * P.img_scale, dl2 = g[2] * P.img_scale;
@@ -233,6 +254,33 @@ __device__ __forceinline__ void adj_body(const ProbDev& P, const CamDev* cams, i
         else T *= __expf(-slot_blend<float>(sg, gx, gy, gz) * len);
     }
     win_release(W, P.nx, nxy, leave);
+}
+
+template <int DT, bool TAU>
+__device__ __forceinline__ void adj_body(const ProbDev& P, const CamDev* cams, int tile)
+{
+    int view, px, py;
+    tile_pixel(P, tile, view, px, py);
+    if (px >= P.W || py >= P.H) return;
+    adj_ray<DT, TAU>(P, cams, view, px, py);
+}
+
+// The same over a compacted list of flame rays (linear pixel indices in tile
+// order, so a warp's 32 rays are neighbours): no lane idles on a non-flame
+// pixel.  CTA b takes list entries [128 b, 128 b + 128).
+template <int DT, bool TAU>
+__global__ void FR_MARCH_BOUNDS adj_list(const __grid_constant__ SingleArgs a, const unsigned* __restrict__ list,
+                                         const unsigned* __restrict__ count)
+{
+    const unsigned i = blockIdx.x * (unsigned)kTileThreads + threadIdx.x;
+    if (i >= __ldg(count)) return;
+    const ProbDev& P = a.p;
+    const unsigned pix = __ldg(list + i);
+    const unsigned per_view = (unsigned)P.W * (unsigned)P.H;
+    const int view = (int)(pix / per_view);
+    const unsigned r = pix - (unsigned)view * per_view;
+    const int py = (int)(r / (unsigned)P.W), px = (int)(r - (unsigned)py * (unsigned)P.W);
+    adj_ray<DT, TAU>(P, a.cams, view, px, py);
 }
 
 template <int DT, bool TAU>
@@ -376,26 +424,98 @@ __global__ void __launch_bounds__(kTileThreads) count_single(const __grid_consta
 }
 
 // Deterministic sum of the per-CTA squared-error partials of one problem.
-__global__ void __launch_bounds__(256) finalize_partials(const float* __restrict__ partials, int ntiles,
-                                                         float* __restrict__ out4)
+__global__ void __launch_bounds__(1024) finalize_partials(const float* __restrict__ partials, int ntiles,
+                                                          float* __restrict__ out4)
 {
-    __shared__ float red[4][8];
-    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    __shared__ float red[4][32];
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    const float4* p4 = reinterpret_cast<const float4*>(partials);
+#pragma unroll 4
     for (int i = threadIdx.x; i < ntiles; i += blockDim.x) {
-        const float4 v = reinterpret_cast<const float4*>(partials)[i];
-        s[0] += v.x; s[1] += v.y; s[2] += v.z; s[3] += v.w;
+        const float4 v = __ldg(p4 + i);
+        s0 += v.x; s1 += v.y; s2 += v.z; s3 += v.w;
     }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) s[c] = warp_sum(s[c]);
+    s0 = warp_sum(s0); s1 = warp_sum(s1); s2 = warp_sum(s2); s3 = warp_sum(s3);
     const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        for (int c = 0; c < 4; ++c) red[c][w] = s[c];
-    }
+    if ((threadIdx.x & 31) == 0) { red[0][w] = s0; red[1][w] = s1; red[2][w] = s2; red[3][w] = s3; }
     __syncthreads();
     if (threadIdx.x < 4) {
         float t = 0.0f;
-        for (int i = 0; i < 8; ++i) t += red[threadIdx.x][i];
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[threadIdx.x][i];
         out4[threadIdx.x] = t;
+    }
+}
+
+// Flame-ray list (pixels whose prepared target is non-zero), in tile order.
+// Pass 1 counts each warp's flame pixels; pass 2 scans the counts; pass 3
+// writes each warp's pixels at its offset.  Warp w of CTA t is entry 4 t + w.
+__device__ __forceinline__ bool is_flame(const ProbDev& P, int view, int px, int py)
+{
+    if (px >= P.W || py >= P.H) return false;
+    const float* t = P.targets + 3 * (((long long)view * P.H + py) * P.W + px);
+    return fmaxf(t[0], fmaxf(t[1], t[2])) > P.thresh;
+}
+
+__global__ void __launch_bounds__(kTileThreads) flame_count_kernel(const __grid_constant__ SingleArgs a,
+                                                                   unsigned* __restrict__ counts)
+{
+    int view, px, py;
+    tile_pixel(a.p, blockIdx.x, view, px, py);
+    const unsigned m = __ballot_sync(0xffffffffu, is_flame(a.p, view, px, py));
+    if ((threadIdx.x & 31) == 0) counts[blockIdx.x * (kTileThreads / 32) + (threadIdx.x >> 5)] = __popc(m);
+}
+
+// Exclusive scan of n counts in place, total at offsets[n]; one CTA.
+__global__ void __launch_bounds__(1024) flame_scan_kernel(unsigned* __restrict__ offsets, int n)
+{
+    __shared__ unsigned wsum[32];
+    __shared__ unsigned carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const unsigned v = i < n ? offsets[i] : 0u;
+        unsigned x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            unsigned s = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;  // inclusive
+        }
+        __syncthreads();
+        const unsigned before = carry + (w > 0 ? wsum[w - 1] : 0u) + x - v;
+        if (i < n) offsets[i] = before;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = before + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) offsets[n] = carry;
+}
+
+__global__ void __launch_bounds__(kTileThreads) flame_list_kernel(const __grid_constant__ SingleArgs a,
+                                                                  const unsigned* __restrict__ offsets,
+                                                                  unsigned* __restrict__ list)
+{
+    const ProbDev& P = a.p;
+    int view, px, py;
+    tile_pixel(P, blockIdx.x, view, px, py);
+    const bool f = is_flame(P, view, px, py);
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (f) {
+        const unsigned below = m & ((1u << (threadIdx.x & 31)) - 1u);
+        const unsigned at = offsets[blockIdx.x * (kTileThreads / 32) + (threadIdx.x >> 5)] + __popc(below);
+        list[at] = (unsigned)(((long long)view * P.H + py) * P.W + px);
     }
 }
 
@@ -505,7 +625,28 @@ cudaError_t launch_count(const SingleArgs& a, int ntiles, cudaStream_t s)
 
 cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cudaStream_t s)
 {
-    finalize_partials<<<1, 256, 0, s>>>(partials, ntiles, out4);
+    finalize_partials<<<1, 1024, 0, s>>>(partials, ntiles, out4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flame_list(const SingleArgs& a, int ntiles, unsigned* offsets, unsigned* list, cudaStream_t s)
+{
+    const int n = ntiles * (kTileThreads / 32);
+    flame_count_kernel<<<ntiles, kTileThreads, 0, s>>>(a, offsets);
+    flame_scan_kernel<<<1, 1024, 0, s>>>(offsets, n);
+    flame_list_kernel<<<ntiles, kTileThreads, 0, s>>>(a, offsets, list);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjust_list(const SingleArgs& a, int dt, int ntiles, const unsigned* list,
+                               const unsigned* count, cudaStream_t s)
+{
+    const bool tau = a.p.tau > 0.0f;
+    dim3 grid(ntiles), block(kTileThreads);
+    FR_DISPATCH_DT(dt, D, {
+        if (tau) adj_list<D, true><<<grid, block, 0, s>>>(a, list, count);
+        else adj_list<D, false><<<grid, block, 0, s>>>(a, list, count);
+    });
     return cudaGetLastError();
 }
 

@@ -79,57 +79,135 @@ cudaError_t launch_apply(void* vol, int dt, int kind, long long nodes, float* dV
 // is sampled at its midpoint (the mean of its two end records).
 // ---------------------------------------------------------------------------
 
-// One thread per grid line along AXIS.  Pass 1 walks the line forward and
-// pass 2 backward; the x sweep initialises J, the z sweep (LAST) finishes it
-// and writes the source records.
-template <int DT, int AXIS, bool LAST>
-__global__ void __launch_bounds__(128) sweep_kernel(const void* em, const float* albedo, float* J,
-                                                    void* out, int nx, int ny, int nz)
+// The recurrence along a line, L(i) = L(i-1) e_i + c_i with e_i = exp(-s) and
+// c_i = q (1 - exp(-s)) / s for the unit segment into node i (s, q the means of
+// its two end records), is an affine map per segment, so a line is scanned in
+// chunks: each chunk composes its segments' maps (forward and backward), the
+// chunks of a line combine their maps through shared memory, and each chunk
+// then walks its nodes again from its incoming radiance.  A CTA holds 32 lines
+// (threadIdx.x, neighbouring lines: coalesced for the y and z sweeps) times
+// kSweepChunks chunks (threadIdx.y).  The x sweep initialises J, the z sweep
+// (LAST) finishes it and writes the source records S = q + albedo sigma J.
+constexpr int kSweepLines = 32;
+constexpr int kSweepChunks = 8;
+
+struct Seg {
+    float e, c0, c1, c2;
+};
+
+template <int DT>
+__device__ __forceinline__ Seg seg_between(float4 a, float4 b)
 {
+    const float sig = 0.5f * (a.w + b.w);
+    const float e = __expf(-sig);
+    const float beta = seg_weight(sig, 1.0f, e);
+    return Seg{e, 0.5f * (a.x + b.x) * beta, 0.5f * (a.y + b.y) * beta, 0.5f * (a.z + b.z) * beta};
+}
+
+template <int DT, int AXIS, bool LAST>
+__global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const void* em, const float* albedo,
+                                                                            float* J, void* out, int nx, int ny,
+                                                                            int nz)
+{
+    __shared__ float4 fwd[kSweepChunks][kSweepLines];   // {E, C0, C1, C2} of each chunk, forward
+    __shared__ float4 bwd[kSweepChunks][kSweepLines];   // and backward
     const int n_line = AXIS == 0 ? nx : (AXIS == 1 ? ny : nz);
     const long long lines = AXIS == 0 ? (long long)ny * nz : (AXIS == 1 ? (long long)nx * nz : (long long)nx * ny);
-    const long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (line >= lines) return;
-    long long start, stride;
-    if constexpr (AXIS == 0) {
-        start = line * nx;                       // line = z * ny + y
-        stride = 1;
-    } else if constexpr (AXIS == 1) {
-        long long z = line / nx, x = line - z * nx;
-        start = z * (long long)nx * ny + x;
-        stride = nx;
-    } else {
-        start = line;                            // line = y * nx + x
-        stride = (long long)nx * ny;
+    const long long line = blockIdx.x * (long long)kSweepLines + threadIdx.x;
+    const int ch = threadIdx.y;
+    const bool live = line < lines;
+    long long start = 0, stride = 1;
+    if (live) {
+        if constexpr (AXIS == 0) {
+            start = line * nx;                       // line = z * ny + y
+            stride = 1;
+        } else if constexpr (AXIS == 1) {
+            const long long z = line / nx, x = line - z * nx;
+            start = z * (long long)nx * ny + x;
+            stride = nx;
+        } else {
+            start = line;                            // line = y * nx + x
+            stride = (long long)nx * ny;
+        }
     }
-    float4* J4 = reinterpret_cast<float4*>(J);
+    const int m = (n_line + kSweepChunks - 1) / kSweepChunks;
+    const int s0 = min(ch * m, n_line), s1 = min(s0 + m, n_line);   // nodes [s0, s1) of this chunk
+
+    // phase 1: compose the forward map of the segments into s0..s1-1 and the
+    // backward map of the segments into s1-1..s0
+    float Ef = 1.0f, F0 = 0.0f, F1 = 0.0f, F2 = 0.0f;
+    float Eb = 1.0f, B0 = 0.0f, B1 = 0.0f, B2 = 0.0f;
+    if (live && s1 > s0) {
+        const int lo = max(s0 - 1, 0), hi = min(s1, n_line - 1);
+        float4 prev = load_rgb<DT>(em, start + lo * stride);
+        for (int i = lo + 1; i <= hi; ++i) {
+            const float4 cur = load_rgb<DT>(em, start + i * stride);
+            const Seg g = seg_between<DT>(prev, cur);
+            if (i >= s0 && i < s1) {   // forward segment into node i
+                F0 = fmaf(F0, g.e, g.c0); F1 = fmaf(F1, g.e, g.c1); F2 = fmaf(F2, g.e, g.c2);
+                Ef *= g.e;
+            }
+            if (i - 1 >= s0 && i - 1 < s1) {   // backward segment into node i - 1
+                B0 = fmaf(Eb, g.c0, B0); B1 = fmaf(Eb, g.c1, B1); B2 = fmaf(Eb, g.c2, B2);
+                Eb *= g.e;
+            }
+            prev = cur;
+        }
+    }
+    fwd[ch][threadIdx.x] = make_float4(Ef, F0, F1, F2);
+    bwd[ch][threadIdx.x] = make_float4(Eb, B0, B1, B2);
+    __syncthreads();
+    if (!live || s1 <= s0) return;
+
+    // phase 2: radiance arriving at the chunk from either side
+    float lf0 = 0.0f, lf1 = 0.0f, lf2 = 0.0f;
+    for (int c = 0; c < ch; ++c) {
+        const float4 f = fwd[c][threadIdx.x];
+        lf0 = fmaf(lf0, f.x, f.y); lf1 = fmaf(lf1, f.x, f.z); lf2 = fmaf(lf2, f.x, f.w);
+    }
+    float lb0 = 0.0f, lb1 = 0.0f, lb2 = 0.0f;
+    for (int c = kSweepChunks - 1; c > ch; --c) {
+        const float4 b = bwd[c][threadIdx.x];
+        lb0 = fmaf(lb0, b.x, b.y); lb1 = fmaf(lb1, b.x, b.z); lb2 = fmaf(lb2, b.x, b.w);
+    }
+
+    // phase 3: walk the chunk forward (J += L_forward / 6) ...
     const float sixth = 1.0f / 6.0f;
-    for (int pass = 0; pass < 2; ++pass) {
-        float L0 = 0.0f, L1 = 0.0f, L2 = 0.0f;
-        float4 prev = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        for (int s = 0; s < n_line; ++s) {
-            const int pos = pass == 0 ? s : n_line - 1 - s;
-            const long long node = start + pos * stride;
-            float4 cur = load_rgb<DT>(em, node);
-            if (s > 0) {
-                float sig = 0.5f * (prev.w + cur.w);
-                float e = __expf(-sig);
-                float beta = seg_weight(sig, 1.0f, e);
-                L0 = fmaf(L0, e, 0.5f * (prev.x + cur.x) * beta);
-                L1 = fmaf(L1, e, 0.5f * (prev.y + cur.y) * beta);
-                L2 = fmaf(L2, e, 0.5f * (prev.z + cur.z) * beta);
+    float4* J4 = reinterpret_cast<float4*>(J);
+    {
+        float4 prev = load_rgb<DT>(em, start + max(s0 - 1, 0) * stride);
+        for (int i = s0; i < s1; ++i) {
+            const long long node = start + i * stride;
+            const float4 cur = load_rgb<DT>(em, node);
+            if (i > 0) {
+                const Seg g = seg_between<DT>(prev, cur);
+                lf0 = fmaf(lf0, g.e, g.c0); lf1 = fmaf(lf1, g.e, g.c1); lf2 = fmaf(lf2, g.e, g.c2);
             }
             prev = cur;
             float4 j;
-            if (AXIS == 0 && pass == 0) {
-                j = make_float4(L0 * sixth, L1 * sixth, L2 * sixth, 0.0f);
+            if constexpr (AXIS == 0) {
+                j = make_float4(lf0 * sixth, lf1 * sixth, lf2 * sixth, 0.0f);
             } else {
                 j = J4[node];
-                j.x = fmaf(L0, sixth, j.x);
-                j.y = fmaf(L1, sixth, j.y);
-                j.z = fmaf(L2, sixth, j.z);
+                j.x = fmaf(lf0, sixth, j.x); j.y = fmaf(lf1, sixth, j.y); j.z = fmaf(lf2, sixth, j.z);
             }
-            if (LAST && pass == 1) {
+            J4[node] = j;
+        }
+    }
+    // ... and backward (J += L_backward / 6; the z sweep then writes S)
+    {
+        float4 next = load_rgb<DT>(em, start + min(s1, n_line - 1) * stride);
+        for (int i = s1 - 1; i >= s0; --i) {
+            const long long node = start + i * stride;
+            const float4 cur = load_rgb<DT>(em, node);
+            if (i < n_line - 1) {
+                const Seg g = seg_between<DT>(cur, next);
+                lb0 = fmaf(lb0, g.e, g.c0); lb1 = fmaf(lb1, g.e, g.c1); lb2 = fmaf(lb2, g.e, g.c2);
+            }
+            next = cur;
+            float4 j = J4[node];
+            j.x = fmaf(lb0, sixth, j.x); j.y = fmaf(lb1, sixth, j.y); j.z = fmaf(lb2, sixth, j.z);
+            if constexpr (LAST) {
                 const float as = __ldg(albedo + node) * cur.w;
                 store_rgb<DT>(out, node, make_float4(fmaf(as, j.x, cur.x), fmaf(as, j.y, cur.y),
                                                      fmaf(as, j.z, cur.z), cur.w));
@@ -143,9 +221,11 @@ cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* 
                                   void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s)
 {
     if (dt_in != dt_out) return cudaErrorInvalidValue;
-    const int B = 128;
-    long long lx = (long long)ny * nz, ly = (long long)nx * nz, lz = (long long)nx * ny;
-    unsigned gx = (unsigned)((lx + B - 1) / B), gy = (unsigned)((ly + B - 1) / B), gz = (unsigned)((lz + B - 1) / B);
+    const long long lx = (long long)ny * nz, ly = (long long)nx * nz, lz = (long long)nx * ny;
+    const unsigned gx = (unsigned)((lx + kSweepLines - 1) / kSweepLines);
+    const unsigned gy = (unsigned)((ly + kSweepLines - 1) / kSweepLines);
+    const unsigned gz = (unsigned)((lz + kSweepLines - 1) / kSweepLines);
+    const dim3 B(kSweepLines, kSweepChunks);
 #define FR_SWEEPS(D)                                                                         \
     sweep_kernel<D, 0, false><<<gx, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz);        \
     sweep_kernel<D, 1, false><<<gy, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz);        \
