@@ -560,7 +560,7 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
     }
     const long long npix = (long long)ncam * cams[0].width * cams[0].height;
     if (npix >= (1LL << 32)) return fail(c, FR_EINVAL, "at most 2^32 pixels per reconstruction");
-    FR_TRY(ensure(c, c->flame_off, ((size_t)nt * (kTileThreads / 32) + 1) * sizeof(unsigned), "flame offsets"));
+    FR_TRY(ensure(c, c->flame_off, flame_list_buf_entries(nt) * sizeof(unsigned), "flame offsets"));
     FR_TRY(ensure(c, c->flame_list, (size_t)npix * sizeof(unsigned), "flame list"));
     cudaStream_t s = c->stream;
     const float* tg = targets;
@@ -590,7 +590,7 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
     // flame rays, once per call: the targets do not change between iterations
     unsigned* flame_off = static_cast<unsigned*>(c->flame_off.p);
     unsigned* flame_list = static_cast<unsigned*>(c->flame_list.p);
-    const unsigned* flame_count = flame_off + (size_t)nt * (kTileThreads / 32);
+    const unsigned* flame_count = flame_off + flame_list_total_at(nt);
     FR_CUDA(c, launch_flame_list(f, nt, flame_off, flame_list, s));
     for (int it = 0; it < iters; ++it) {
         if (albedo)

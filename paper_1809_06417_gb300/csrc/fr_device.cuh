@@ -161,80 +161,66 @@ __device__ __forceinline__ CellIJK cell_ijk(float x, float y, float z, int nx, i
     return c;
 }
 
-// A ray's window on the eight key points of the cell it is in.  Slot s holds
-// the key point whose node coordinates have parities (s & 1, (s >> 1) & 1,
-// s >> 2), so that a step across one cell face keeps four key points in their
-// slots and only the four slots of the departing plane change owner: they are
-// released (leave) and refilled for the arriving plane (enter).  Trilinear
-// weights and key-point distances are the usual ones written with the
-// fraction mirrored where the cell index is odd (mirror_frac).
+// A ray's window on the eight key points of the cell it is in.  Slot t holds
+// the key point whose node coordinates have parities (t & 1, (t >> 1) & 1,
+// t >> 2).  When the ray moves to another cell, a key point shared by both
+// cells keeps its slot, so only the slots whose key point changes are
+// released (leave) and refilled (enter).  Every slot is visited on every move
+// under its own predicate, so lanes of a warp that move differently run the
+// same instructions.  Trilinear weights and key-point distances of slot t are
+// the usual ones written with the fraction mirrored where the cell index is
+// odd (mirror_frac).
 struct Win {
     int ci, cj, ck;
-    long long base;   // node index of (ci, cj, ck)
+    long long base;          // node index of (ci, cj, ck)
     bool live;
 };
 
-__device__ __forceinline__ long long slot_node(const Win& W, int s, int nx, long long nxy)
+__device__ __forceinline__ long long slot_node(const Win& W, int t, int nx, long long nxy)
 {
-    const int dx = (s & 1) ^ (W.ci & 1), dy = ((s >> 1) & 1) ^ (W.cj & 1), dz = (s >> 2) ^ (W.ck & 1);
-    return W.base + dx + dy * (long long)nx + dz * nxy;
+    const int dx = (t & 1) ^ (W.ci & 1), dy = ((t >> 1) & 1) ^ (W.cj & 1), dz = (t >> 2) ^ (W.ck & 1);
+    return W.base + dx + (long long)(dy * nx) + (dz ? nxy : 0LL);
 }
 
-// op(slot, node) on the four slots whose AX bit equals q
-template <int AX, class Op>
-__device__ __forceinline__ void win_plane(const Win& W, int q, int nx, long long nxy, Op&& op)
+__device__ __forceinline__ void win_set(Win& W, int i, int j, int k, int nx, int ny)
 {
-    constexpr int bit = 1 << AX;
-    if (q) {
-#pragma unroll
-        for (int t = 0; t < 8; ++t)
-            if (t & bit) op(t, slot_node(W, t, nx, nxy));
-    } else {
-#pragma unroll
-        for (int t = 0; t < 8; ++t)
-            if (!(t & bit)) op(t, slot_node(W, t, nx, nxy));
-    }
+    W.ci = i; W.cj = j; W.ck = k;
+    W.base = ((long long)k * ny + j) * nx + i;
+    W.live = true;
 }
 
+// Move the window to cell (i, j, k).  leave(t, node) runs for each slot whose
+// key point is not a corner of the new cell (with its old node), then
+// enter(t, node) for the same slots (with the new node); on the first call
+// every slot enters.
 template <class Leave, class Enter>
 __device__ __forceinline__ void win_move(Win& W, int i, int j, int k, int nx, int ny, long long nxy,
                                          Leave&& leave, Enter&& enter)
 {
-    if (W.live && i == W.ci && j == W.cj && k == W.ck) return;
-    const int di = i - W.ci, dj = j - W.cj, dk = k - W.ck;
-    if (!W.live || abs(di) > 1 || abs(dj) > 1 || abs(dk) > 1) {
-        if (W.live) {
-#pragma unroll
-            for (int t = 0; t < 8; ++t) leave(t, slot_node(W, t, nx, nxy));
-        }
-        W.ci = i; W.cj = j; W.ck = k;
-        W.base = ((long long)k * ny + j) * nx + i;
-        W.live = true;
+    if (!W.live) {
+        win_set(W, i, j, k, nx, ny);
 #pragma unroll
         for (int t = 0; t < 8; ++t) enter(t, slot_node(W, t, nx, nxy));
         return;
     }
-    if (di) {
-        const int q = di > 0 ? (W.ci & 1) : ((W.ci + 1) & 1);
-        win_plane<0>(W, q, nx, nxy, leave);
-        W.ci += di;
-        W.base += di;
-        win_plane<0>(W, q, nx, nxy, enter);
+    if (i == W.ci && j == W.cj && k == W.ck) return;
+    // slot bit value v along an axis names the node c_old + (v ^ (c_old & 1));
+    // it stays iff that node is c_new or c_new + 1
+    const int dx = W.ci - i, dy = W.cj - j, dz = W.ck - k;
+    const int px = W.ci & 1, py = W.cj & 1, pz = W.ck & 1;
+    const bool sx[2] = {(unsigned)(dx + px) <= 1u, (unsigned)(dx + 1 - px) <= 1u};
+    const bool sy[2] = {(unsigned)(dy + py) <= 1u, (unsigned)(dy + 1 - py) <= 1u};
+    const bool sz[2] = {(unsigned)(dz + pz) <= 1u, (unsigned)(dz + 1 - pz) <= 1u};
+    bool go[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        go[t] = !(sx[t & 1] && sy[(t >> 1) & 1] && sz[t >> 2]);
+        if (go[t]) leave(t, slot_node(W, t, nx, nxy));
     }
-    if (dj) {
-        const int q = dj > 0 ? (W.cj & 1) : ((W.cj + 1) & 1);
-        win_plane<1>(W, q, nx, nxy, leave);
-        W.cj += dj;
-        W.base += (long long)dj * nx;
-        win_plane<1>(W, q, nx, nxy, enter);
-    }
-    if (dk) {
-        const int q = dk > 0 ? (W.ck & 1) : ((W.ck + 1) & 1);
-        win_plane<2>(W, q, nx, nxy, leave);
-        W.ck += dk;
-        W.base += (long long)dk * nxy;
-        win_plane<2>(W, q, nx, nxy, enter);
-    }
+    win_set(W, i, j, k, nx, ny);
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+        if (go[t]) enter(t, slot_node(W, t, nx, nxy));
 }
 
 template <class Leave>
@@ -247,6 +233,13 @@ __device__ __forceinline__ void win_release(const Win& W, int nx, long long nxy,
 
 // Fraction toward the odd-parity key point along one axis.
 __device__ __forceinline__ float mirror_frac(int cell, float f) { return (cell & 1) ? 1.0f - f : f; }
+
+// exp(-a * |x|) for x = squared distance, with sqrt taken as x rsqrt(x).
+__device__ __forceinline__ float dist_weight(float a, float x)
+{
+    x = fmaxf(x, 1e-30f);
+    return __expf(-a * (x * rsqrtf(x)));
+}
 
 // ---------------------------------------------------------------------------
 // Node records

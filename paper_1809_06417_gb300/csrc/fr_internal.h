@@ -33,10 +33,12 @@ cudaError_t launch_backward_batch(const ProbDev* probs, const int* tile_start, i
                                   int dt, int kind, bool tau, cudaStream_t s);
 cudaError_t launch_count(const SingleArgs& a, int ntiles, cudaStream_t s);
 cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cudaStream_t s);
-// flame-ray list of a problem with prepared targets: offsets needs
-// 4 ntiles + 1 entries (the total lands in offsets[4 ntiles]), list one entry
-// per pixel at most
-cudaError_t launch_flame_list(const SingleArgs& a, int ntiles, unsigned* offsets, unsigned* list, cudaStream_t s);
+// flame-ray list of a problem with prepared targets: buf needs
+// flame_list_buf_entries(ntiles) entries, the total lands at
+// buf[flame_list_total_at(ntiles)]; list needs one entry per pixel at most
+inline size_t flame_list_buf_entries(int ntiles) { return (size_t)ntiles * (kTileThreads / 32 + 1) + 1; }
+inline size_t flame_list_total_at(int ntiles) { return (size_t)ntiles * (kTileThreads / 32 + 1); }
+cudaError_t launch_flame_list(const SingleArgs& a, int ntiles, unsigned* buf, unsigned* list, cudaStream_t s);
 cudaError_t launch_adjust_list(const SingleArgs& a, int dt, int ntiles, const unsigned* list,
                                const unsigned* count, cudaStream_t s);
 

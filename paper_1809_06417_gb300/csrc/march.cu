@@ -104,7 +104,9 @@ __device__ __forceinline__ void load8(const void* vol, long long base, int nx, l
 
 // Forward march of one ray.  Consecutive samples often share a cell (at half a
 // voxel step about 2 in 5 do), so the cell's eight records stay in registers
-// and are reloaded only when the sample enters another cell.
+// and are reloaded only when the sample enters another cell.  (Reloading just
+// the four records of a crossed face costs more instructions than the L1
+// traffic it saves.)
 template <int DT, int KIND, bool TAU>
 __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, int tile)
 {
@@ -246,10 +248,7 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
         const float ey[2] = {gy * gy, (1.0f - gy) * (1.0f - gy)};
         const float ez[2] = {gz * gz, (1.0f - gz) * (1.0f - gz)};
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const float D = sqrtf(ex[t & 1] + ey[(t >> 1) & 1] + ez[t >> 2]);
-            acc[t] = fmaf(base, __expf(-P.alpha_d * D), acc[t]);
-        }
+        for (int t = 0; t < 8; ++t) acc[t] = fmaf(base, dist_weight(P.alpha_d, ex[t & 1] + ey[(t >> 1) & 1] + ez[t >> 2]), acc[t]);
         if constexpr (TAU) T *= 1.0f - P.tau;
         else T *= __expf(-slot_blend<float>(sg, gx, gy, gz) * len);
     }
@@ -323,10 +322,15 @@ __device__ __forceinline__ void bwd_body(const ProbDev& P, const CamDev* cams, i
     const float* lt = P.L_total + 3 * pix;
     const float Lt0 = lt[0], Lt1 = lt[1], Lt2 = lt[2];
     const long long nxy = (long long)P.nx * P.ny;
+    using Rec = RecOf<DT, KIND>;
+    using RT = typename Rec::T;
     float4 acc[8];
+    RT v[8];
+    long long vbase = -1;
 #pragma unroll
     for (int t = 0; t < 8; ++t) acc[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float* dV = P.dV;
+    const void* vol = P.vol;
     auto leave = [&acc, dV](int t, long long node) {
         const float4 a = acc[t];
         if (a.x != 0.0f || a.y != 0.0f || a.z != 0.0f || a.w != 0.0f) {
@@ -343,11 +347,15 @@ __device__ __forceinline__ void bwd_body(const ProbDev& P, const CamDev* cams, i
         segment(R, P.step, k, len, x, y, z);
         const CellIJK ci = cell_ijk(x, y, z, P.nx, P.ny, P.nz);
         win_move(W, ci.i, ci.j, ci.k, P.nx, P.ny, nxy, leave, [](int, long long) {});
-        Cell c;
-        c.base = W.base; c.fx = ci.fx; c.fy = ci.fy; c.fz = ci.fz;
+        if (W.base != vbase) {
+            vbase = W.base;
+            load8<DT, KIND>(vol, W.base, P.nx, nxy, v);
+        }
+        const RT r = slot_blend<RT>(v, ci.fx, ci.fy, ci.fz);
+        const float gx = mirror_frac(ci.i, ci.fx), gy = mirror_frac(ci.j, ci.fy), gz = mirror_frac(ci.k, ci.fz);
         float S[3], sig, dq[3] = {0.0f, 0.0f, 0.0f};
-        if constexpr (KIND == KIND_RGB) record_source<KIND>(P, sample_rgb<DT>(P.vol, c, P.nx, nxy), S, sig, dq);
-        else record_source_temp(P, sample_ts<DT>(P.vol, c, P.nx, nxy), S, sig, dq);
+        if constexpr (KIND == KIND_RGB) record_source<KIND>(P, r, S, sig, dq);
+        else record_source_temp(P, r, S, sig, dq);
         float gS0, gS1, gS2, gsig;
         if constexpr (TAU) {
             const float w = T * P.tau;
@@ -369,7 +377,6 @@ __device__ __forceinline__ void bwd_body(const ProbDev& P, const CamDev* cams, i
         float4 gv;
         if constexpr (KIND == KIND_RGB) gv = make_float4(gS0, gS1, gS2, gsig);
         else gv = make_float4(gS0 * dq[0] + gS1 * dq[1] + gS2 * dq[2], gsig, 0.0f, 0.0f);
-        const float gx = mirror_frac(ci.i, ci.fx), gy = mirror_frac(ci.j, ci.fy), gz = mirror_frac(ci.k, ci.fz);
         const float wx[2] = {1.0f - gx, gx}, wy[2] = {1.0f - gy, gy}, wz[2] = {1.0f - gz, gz};
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
@@ -447,8 +454,10 @@ __global__ void __launch_bounds__(1024) finalize_partials(const float* __restric
 }
 
 // Flame-ray list (pixels whose prepared target is non-zero), in tile order.
-// Pass 1 counts each warp's flame pixels; pass 2 scans the counts; pass 3
-// writes each warp's pixels at its offset.  Warp w of CTA t is entry 4 t + w.
+// Pass 1 counts each warp's flame pixels and each CTA's total; pass 2 scans the
+// CTA totals; pass 3 writes each warp's pixels at the CTA offset plus the
+// counts of the CTA's earlier warps.  Buffer layout: warp counts
+// [0, 4 ntiles), CTA offsets [4 ntiles, 5 ntiles], total at 5 ntiles.
 __device__ __forceinline__ bool is_flame(const ProbDev& P, int view, int px, int py)
 {
     if (px >= P.W || py >= P.H) return false;
@@ -456,16 +465,29 @@ __device__ __forceinline__ bool is_flame(const ProbDev& P, int view, int px, int
     return fmaxf(t[0], fmaxf(t[1], t[2])) > P.thresh;
 }
 
+constexpr int kWarpsPerTile = kTileThreads / 32;
+
 __global__ void __launch_bounds__(kTileThreads) flame_count_kernel(const __grid_constant__ SingleArgs a,
-                                                                   unsigned* __restrict__ counts)
+                                                                   unsigned* __restrict__ buf, int ntiles)
 {
+    __shared__ unsigned wc[kWarpsPerTile];
     int view, px, py;
     tile_pixel(a.p, blockIdx.x, view, px, py);
     const unsigned m = __ballot_sync(0xffffffffu, is_flame(a.p, view, px, py));
-    if ((threadIdx.x & 31) == 0) counts[blockIdx.x * (kTileThreads / 32) + (threadIdx.x >> 5)] = __popc(m);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        wc[w] = __popc(m);
+        buf[blockIdx.x * kWarpsPerTile + w] = __popc(m);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int i = 0; i < kWarpsPerTile; ++i) t += wc[i];
+        buf[(size_t)kWarpsPerTile * ntiles + blockIdx.x] = t;
+    }
 }
 
-// Exclusive scan of n counts in place, total at offsets[n]; one CTA.
+// Exclusive scan of n values in place, total at offsets[n]; one CTA.
 __global__ void __launch_bounds__(1024) flame_scan_kernel(unsigned* __restrict__ offsets, int n)
 {
     __shared__ unsigned wsum[32];
@@ -504,7 +526,7 @@ __global__ void __launch_bounds__(1024) flame_scan_kernel(unsigned* __restrict__
 }
 
 __global__ void __launch_bounds__(kTileThreads) flame_list_kernel(const __grid_constant__ SingleArgs a,
-                                                                  const unsigned* __restrict__ offsets,
+                                                                  const unsigned* __restrict__ buf, int ntiles,
                                                                   unsigned* __restrict__ list)
 {
     const ProbDev& P = a.p;
@@ -513,8 +535,10 @@ __global__ void __launch_bounds__(kTileThreads) flame_list_kernel(const __grid_c
     const bool f = is_flame(P, view, px, py);
     const unsigned m = __ballot_sync(0xffffffffu, f);
     if (f) {
-        const unsigned below = m & ((1u << (threadIdx.x & 31)) - 1u);
-        const unsigned at = offsets[blockIdx.x * (kTileThreads / 32) + (threadIdx.x >> 5)] + __popc(below);
+        const int w = threadIdx.x >> 5;
+        unsigned at = buf[(size_t)kWarpsPerTile * ntiles + blockIdx.x];
+        for (int i = 0; i < w; ++i) at += buf[blockIdx.x * kWarpsPerTile + i];
+        at += __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
         list[at] = (unsigned)(((long long)view * P.H + py) * P.W + px);
     }
 }
@@ -629,12 +653,11 @@ cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_flame_list(const SingleArgs& a, int ntiles, unsigned* offsets, unsigned* list, cudaStream_t s)
+cudaError_t launch_flame_list(const SingleArgs& a, int ntiles, unsigned* buf, unsigned* list, cudaStream_t s)
 {
-    const int n = ntiles * (kTileThreads / 32);
-    flame_count_kernel<<<ntiles, kTileThreads, 0, s>>>(a, offsets);
-    flame_scan_kernel<<<1, 1024, 0, s>>>(offsets, n);
-    flame_list_kernel<<<ntiles, kTileThreads, 0, s>>>(a, offsets, list);
+    flame_count_kernel<<<ntiles, kTileThreads, 0, s>>>(a, buf, ntiles);
+    flame_scan_kernel<<<1, 1024, 0, s>>>(buf + (size_t)kWarpsPerTile * ntiles, ntiles);
+    flame_list_kernel<<<ntiles, kTileThreads, 0, s>>>(a, buf, ntiles, list);
     return cudaGetLastError();
 }
 
