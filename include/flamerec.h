@@ -213,6 +213,28 @@ fr_status fr_reconstruct(fr_ctx *ctx, fr_volume *vol, const float *albedo,
                          int first_iteration, const fr_params *p, float *rmse,
                          int rmse_is_host);
 
+/* One reconstruction problem of a batch (e.g. one video frame, Sec. 5.2, whose
+ * frames the paper reconstructs independently). */
+typedef struct fr_problem {
+    fr_volume vol;             /* RGB records, updated in place */
+    const fr_camera *cams;     /* host, ncam cameras sharing one image size */
+    int32_t ncam;
+    int32_t pad_;
+    const float *targets;      /* device, prepared by fr_prepare_targets */
+    const int32_t *bbox;       /* device, ncam x 4 */
+    float *rmse;               /* device, iters x 3, or NULL */
+} fr_problem;
+
+/* fr_reconstruct with the paper rule over nprob independent problems at
+ * once: each iteration runs one forward launch, one error reduction, one
+ * adjustment launch over the flame rays of all problems and one update
+ * launch, whatever nprob is.  Volumes share one storage type; grids, cameras
+ * and image sizes may differ.  Parameters are shared.  use_graph != 0 captures
+ * the iterations in a CUDA graph and launches it once; the call then returns
+ * after the work is done.  Scratch is sized from all problems at once. */
+fr_status fr_reconstruct_batch(fr_ctx *ctx, const fr_problem *probs, int nprob, int iters,
+                               int first_iteration, const fr_params *p, int use_graph);
+
 /* Number of samples (segments) the rays of `cams` take through the volume's
  * box: all rays when residual is NULL (one render), else only the rays whose
  * residual (device, image layout) is non-zero (one adjustment).  Counted by a

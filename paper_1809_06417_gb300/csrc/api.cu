@@ -1,5 +1,6 @@
 // api.cu -- the C ABI declared in include/flamerec.h: argument validation,
 // library-owned scratch, kernel launches and the reconstruction loop.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -31,7 +32,12 @@ struct fr_ctx {
     cudaStream_t stream = nullptr;   // where work is queued (borrowed; 0 = default stream)
     char err[512] = {0};             // last failure message
     Buf partials, counter, residual, rendered, dV, targets, sqerr, rmse, J, src, flame_off, flame_list;
+    Buf batch;                       // batched reconstruction scratch and tables
     unsigned long long* host_counter = nullptr;
+    void* staging = nullptr;         // pinned host staging of batch tables
+    size_t staging_bytes = 0;
+    cudaEvent_t staging_done = nullptr;
+    cudaStream_t capture = nullptr;  // stream used to capture CUDA graphs
 };
 
 namespace {
@@ -307,9 +313,12 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
-                   &c->rmse, &c->J, &c->src, &c->flame_off, &c->flame_list})
+                   &c->rmse, &c->J, &c->src, &c->flame_off, &c->flame_list, &c->batch})
         if (b->p) cudaFree(b->p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
+    if (c->staging) cudaFreeHost(c->staging);
+    if (c->staging_done) cudaEventDestroy(c->staging_done);
+    if (c->capture) cudaStreamDestroy(c->capture);
     delete c;
     return FR_OK;
 }
@@ -719,4 +728,165 @@ extern "C" fr_status fr_render_residual_noalloc(int device, void* stream, const 
     cudaSetDevice(prev);
     if (e != cudaSuccess) return done(cuda_fail(&c, e, "launch"));
     return done(FR_OK);
+}
+
+// ---------------------------------------------------------------------------
+// Batched reconstruction
+// ---------------------------------------------------------------------------
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, int nprob, int iters,
+                                          int first_iteration, const fr_params* p, int use_graph)
+{
+    FR_BEGIN(c);
+    if (!probs || nprob < 1 || nprob > (1 << 20)) return fail(c, FR_EINVAL, "need 1 <= nprob <= 2^20");
+    if (iters < 0) return fail(c, FR_EINVAL, "iters must be >= 0");
+    if (first_iteration < 0 || (long long)first_iteration + iters > (1 << 20))
+        return fail(c, FR_EINVAL, "iterations must stay below 2^20");
+    if (!p) return fail(c, FR_EINVAL, "params is NULL");
+    if (p->rule != FR_RULE_PAPER) return fail(c, FR_EINVAL, "batched reconstruction uses FR_RULE_PAPER");
+    const int dt = probs[0].vol.dtype;
+    // sizes and validation
+    size_t arena = 0, cams_total = 0;
+    long long tiles_total = 0;
+    for (int i = 0; i < nprob; ++i) {
+        const fr_problem& q = probs[i];
+        char name[48];
+        snprintf(name, sizeof name, "probs[%d].vol", i);
+        FR_TRY(check_volume(c, &q.vol, name));
+        if (q.vol.kind != FR_KIND_RGB || q.vol.dtype != dt)
+            return fail(c, FR_EINVAL, "probs[%d]: batched volumes are RGB records of one storage type", i);
+        FR_TRY(check_cams(c, q.cams, q.ncam));
+        FR_TRY(check_params(c, p, &q.vol, q.cams));
+        const size_t ib = image_bytes(q.cams, q.ncam);
+        FR_TRY(check_dev(c, q.targets, ib, "targets"));
+        FR_TRY(check_dev(c, q.bbox, (size_t)q.ncam * 16, "bbox"));
+        if (q.rmse) FR_TRY(check_dev(c, q.rmse, (size_t)iters * 12, "rmse"));
+        const long long npix = (long long)q.ncam * q.cams[0].width * q.cams[0].height;
+        if (npix >= (1LL << 32)) return fail(c, FR_EINVAL, "probs[%d]: at most 2^32 pixels", i);
+        const int nt = tiles_of(q.cams[0].width, q.cams[0].height, q.ncam);
+        arena += align256(ib) + align256((size_t)node_count(&q.vol) * 16) + align256((size_t)nt * 16) +
+                 align256((size_t)std::max(iters, 1) * 16) + align256(flame_list_buf_entries(nt) * 4) +
+                 align256((size_t)npix * 4);
+        tiles_total += nt;
+        cams_total += (size_t)q.ncam;
+    }
+    if (tiles_total >= (1LL << 31)) return fail(c, FR_EINVAL, "too many tiles in one batch");
+    if (iters == 0) return FR_OK;
+    const size_t tab_probs = align256(sizeof(ProbDev) * nprob);
+    const size_t tab_cams = align256(sizeof(CamDev) * cams_total);
+    const size_t tab_tiles = align256(sizeof(int) * (nprob + 1));
+    const size_t rmse_all = align256(sizeof(float) * 3 * (size_t)nprob * iters);
+    const size_t tables = tab_probs + tab_cams + tab_tiles;
+    FR_TRY(ensure(c, c->batch, arena + tables + rmse_all, "batch"));
+    // host staging (pinned), reused once the previous copy out of it is done
+    if (!c->staging_done) FR_CUDA(c, cudaEventCreateWithFlags(&c->staging_done, cudaEventDisableTiming));
+    FR_CUDA(c, cudaEventSynchronize(c->staging_done));
+    if (c->staging_bytes < tables) {
+        if (c->staging) cudaFreeHost(c->staging);
+        c->staging = nullptr;
+        c->staging_bytes = 0;
+        if (cudaMallocHost(&c->staging, tables) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, FR_ENOMEM, "cannot allocate %zu bytes of pinned staging", tables);
+        }
+        c->staging_bytes = tables;
+    }
+    char* dbase = static_cast<char*>(c->batch.p);
+    ProbDev* d_probs = reinterpret_cast<ProbDev*>(dbase + arena);
+    CamDev* d_cams = reinterpret_cast<CamDev*>(dbase + arena + tab_probs);
+    int* d_tiles = reinterpret_cast<int*>(dbase + arena + tab_probs + tab_cams);
+    float* d_rmse = reinterpret_cast<float*>(dbase + arena + tables);
+    ProbDev* h_probs = reinterpret_cast<ProbDev*>(c->staging);
+    CamDev* h_cams = reinterpret_cast<CamDev*>(static_cast<char*>(c->staging) + tab_probs);
+    int* h_tiles = reinterpret_cast<int*>(static_cast<char*>(c->staging) + tab_probs + tab_cams);
+    cudaStream_t s = c->stream;
+    static thread_local SingleArgs a;
+    size_t off = 0, cam_off = 0;
+    int tile_off = 0;
+    for (int i = 0; i < nprob; ++i) {
+        const fr_problem& q = probs[i];
+        fill_problem(&q.vol, q.cams, q.ncam, p, a);
+        const int nt = tiles_of(q.cams[0].width, q.cams[0].height, q.ncam);
+        const long long nodes = node_count(&q.vol);
+        const long long npix = (long long)q.ncam * q.cams[0].width * q.cams[0].height;
+        const size_t ib = image_bytes(q.cams, q.ncam);
+        float* residual = reinterpret_cast<float*>(dbase + off); off += align256(ib);
+        float* dV = reinterpret_cast<float*>(dbase + off); off += align256((size_t)nodes * 16);
+        float* partials = reinterpret_cast<float*>(dbase + off); off += align256((size_t)nt * 16);
+        float* sqerr = reinterpret_cast<float*>(dbase + off); off += align256((size_t)iters * 16);
+        unsigned* fbuf = reinterpret_cast<unsigned*>(dbase + off); off += align256(flame_list_buf_entries(nt) * 4);
+        unsigned* flist = reinterpret_cast<unsigned*>(dbase + off); off += align256((size_t)npix * 4);
+        ProbDev& P = a.p;
+        P.cams = d_cams + cam_off;
+        P.targets = q.targets;
+        P.bbox = q.bbox;
+        P.residual = residual;
+        P.partials = partials;
+        P.dV = dV;
+        P.img_in = residual;
+        P.img_scale = 1.0f;
+        P.list = flist;
+        P.list_count = fbuf + flame_list_total_at(nt);
+        P.vol_rw = q.vol.data;
+        P.nodes = nodes;
+        P.sqerr = sqerr;
+        P.ntiles = nt;
+        h_probs[i] = P;
+        for (int v = 0; v < q.ncam; ++v) h_cams[cam_off + v] = a.cams[v];
+        h_tiles[i] = tile_off;
+        FR_CUDA(c, cudaMemsetAsync(dV, 0, (size_t)nodes * 16, s));
+        FR_CUDA(c, launch_flame_list(a, nt, fbuf, flist, s));
+        cam_off += (size_t)q.ncam;
+        tile_off += nt;
+    }
+    h_tiles[nprob] = tile_off;
+    FR_CUDA(c, cudaMemcpyAsync(d_probs, h_probs, tables, cudaMemcpyHostToDevice, s));
+    FR_CUDA(c, cudaEventRecord(c->staging_done, s));
+    const bool tau = p->tau > 0.0f;
+
+    auto iterate = [&](cudaStream_t st) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+            e = launch_fwd_batch(d_probs, d_tiles, nprob, tile_off, dt, KIND_RGB, tau, st);
+            if (e == cudaSuccess) e = launch_finalize_batch(d_probs, nprob, it, st);
+            if (e == cudaSuccess)
+                e = launch_adjust_list_batch(d_probs, d_tiles, nprob, tile_off, dt, tau, first_iteration + it, st);
+            if (e == cudaSuccess) e = launch_apply_batch(d_probs, nprob, dt, p->clamp_nonneg, st);
+        }
+        return e;
+    };
+    if (use_graph) {
+        if (!c->capture) FR_CUDA(c, cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        FR_CUDA(c, cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = iterate(c->capture);
+        cudaError_t e2 = cudaStreamEndCapture(c->capture, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(c, e != cudaSuccess ? e : e2, "graph capture");
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+        e = cudaGraphLaunch(exec, s);
+        cudaError_t e3 = cudaStreamSynchronize(s);
+        cudaGraphExecDestroy(exec);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+        if (e3 != cudaSuccess) return cuda_fail(c, e3, "cudaStreamSynchronize");
+    } else {
+        FR_CUDA(c, iterate(s));
+    }
+    FR_CUDA(c, launch_rmse_batch(d_probs, nprob, iters, d_rmse, s));
+    for (int i = 0; i < nprob; ++i)
+        if (probs[i].rmse)
+            FR_CUDA(c, cudaMemcpyAsync(probs[i].rmse, d_rmse + (size_t)3 * iters * i, (size_t)iters * 12,
+                                       cudaMemcpyDeviceToDevice, s));
+    return FR_OK;
 }

@@ -57,6 +57,14 @@ struct ProbDev {
     int iteration;
     int pad_;
     unsigned long long* counter; // sample counter, nullable
+    // batched launches only
+    const unsigned* list;        // flame-ray list (linear pixel indices)
+    const unsigned* list_count;  // its length (device)
+    void* vol_rw;                // volume updated by the apply step
+    long long nodes;
+    float* sqerr;                // 4 floats per iteration
+    int ntiles;
+    int pad2_;
 };
 
 // ---------------------------------------------------------------------------

@@ -26,8 +26,11 @@ cudaError_t launch_fwd(const SingleArgs& a, int dt, int kind, int ntiles, cudaSt
 cudaError_t launch_fwd_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
                              int dt, int kind, bool tau, cudaStream_t s);
 cudaError_t launch_adjust(const SingleArgs& a, int dt, int ntiles, cudaStream_t s);
-cudaError_t launch_adjust_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
-                                int dt, bool tau, cudaStream_t s);
+cudaError_t launch_adjust_list_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
+                                     int dt, bool tau, int iteration, cudaStream_t s);
+cudaError_t launch_finalize_batch(const ProbDev* probs, int nprob, int iteration, cudaStream_t s);
+cudaError_t launch_apply_batch(const ProbDev* probs, int nprob, int dt, int clamp_nonneg, cudaStream_t s);
+cudaError_t launch_rmse_batch(const ProbDev* probs, int nprob, int iters, float* rmse_all, cudaStream_t s);
 cudaError_t launch_backward(const SingleArgs& a, int dt, int kind, int ntiles, cudaStream_t s);
 cudaError_t launch_backward_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
                                   int dt, int kind, bool tau, cudaStream_t s);

@@ -209,7 +209,8 @@ __global__ void FR_MARCH_BOUNDS fwd_batch(const ProbDev* __restrict__ probs,
 // G alpha_l T exp(-alpha_d D) over the ray's samples in its window slot and
 // receives that sum times dL when the ray leaves it.
 template <int DT, bool TAU>
-__device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, int view, int px, int py)
+__device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, int view, int px, int py,
+                                        int iteration)
 {
     const long long pix = ((long long)view * P.H + py) * P.W + px;
     const float* g = P.img_in + 3 * pix;
@@ -241,7 +242,7 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
         const CellIJK c = cell_ijk(x, y, z, P.nx, P.ny, P.nz);
         win_move(W, c.i, c.j, c.k, P.nx, P.ny, nxy, leave, enter);
         const float gx = mirror_frac(c.i, c.fx), gy = mirror_frac(c.j, c.fy), gz = mirror_frac(c.k, c.fz);
-        const float G = P.g_std > 0.0f ? g_draw(P.seed, P.g_std, P.iteration, view, pixel, k) : 1.0f;
+        const float G = P.g_std > 0.0f ? g_draw(P.seed, P.g_std, iteration, view, pixel, k) : 1.0f;
         const float base = G * P.alpha_l * T;
         // squared distances (voxel units) from the sample to each slot's key point
         const float ex[2] = {gx * gx, (1.0f - gx) * (1.0f - gx)};
@@ -261,7 +262,7 @@ __device__ __forceinline__ void adj_body(const ProbDev& P, const CamDev* cams, i
     int view, px, py;
     tile_pixel(P, tile, view, px, py);
     if (px >= P.W || py >= P.H) return;
-    adj_ray<DT, TAU>(P, cams, view, px, py);
+    adj_ray<DT, TAU>(P, cams, view, px, py, P.iteration);
 }
 
 // The same over a compacted list of flame rays (linear pixel indices in tile
@@ -279,23 +280,31 @@ __global__ void FR_MARCH_BOUNDS adj_list(const __grid_constant__ SingleArgs a, c
     const int view = (int)(pix / per_view);
     const unsigned r = pix - (unsigned)view * per_view;
     const int py = (int)(r / (unsigned)P.W), px = (int)(r - (unsigned)py * (unsigned)P.W);
-    adj_ray<DT, TAU>(P, a.cams, view, px, py);
+    adj_ray<DT, TAU>(P, a.cams, view, px, py, P.iteration);
+}
+
+// Batched form: CTA b belongs to the problem whose tile range holds b and
+// takes that problem's list entries [128 (b - start), ...).
+template <int DT, bool TAU>
+__global__ void FR_MARCH_BOUNDS adj_list_batch(const ProbDev* __restrict__ probs, const int* __restrict__ tile_start,
+                                               int nprob, int iteration)
+{
+    const int p = find_problem(tile_start, nprob, blockIdx.x);
+    const ProbDev& P = probs[p];
+    const unsigned i = (unsigned)(blockIdx.x - __ldg(tile_start + p)) * (unsigned)kTileThreads + threadIdx.x;
+    if (i >= __ldg(P.list_count)) return;
+    const unsigned pix = __ldg(P.list + i);
+    const unsigned per_view = (unsigned)P.W * (unsigned)P.H;
+    const int view = (int)(pix / per_view);
+    const unsigned r = pix - (unsigned)view * per_view;
+    const int py = (int)(r / (unsigned)P.W), px = (int)(r - (unsigned)py * (unsigned)P.W);
+    adj_ray<DT, TAU>(P, P.cams, view, px, py, iteration);
 }
 
 template <int DT, bool TAU>
 __global__ void FR_MARCH_BOUNDS adj_single(const __grid_constant__ SingleArgs a)
 {
     adj_body<DT, TAU>(a.p, a.cams, blockIdx.x);
-}
-
-template <int DT, bool TAU>
-__global__ void FR_MARCH_BOUNDS adj_batch(const ProbDev* __restrict__ probs,
-                                                                          const int* __restrict__ tile_start,
-                                                                          int nprob)
-{
-    const int p = find_problem(tile_start, nprob, blockIdx.x);
-    const ProbDev& P = probs[p];
-    adj_body<DT, TAU>(P, P.cams, blockIdx.x - __ldg(tile_start + p));
 }
 
 // ---------------------------------------------------------------------------
@@ -543,6 +552,29 @@ __global__ void __launch_bounds__(kTileThreads) flame_list_kernel(const __grid_c
     }
 }
 
+// Per-problem sums of the squared-error partials (one CTA per problem), into
+// the problem's error slot of iteration `iteration`.
+__global__ void __launch_bounds__(1024) finalize_batch(const ProbDev* __restrict__ probs, int iteration)
+{
+    __shared__ float red[4][32];
+    const ProbDev& P = probs[blockIdx.x];
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    const float4* p4 = reinterpret_cast<const float4*>(P.partials);
+    for (int i = threadIdx.x; i < P.ntiles; i += blockDim.x) {
+        const float4 v = __ldg(p4 + i);
+        s0 += v.x; s1 += v.y; s2 += v.z; s3 += v.w;
+    }
+    s0 = warp_sum(s0); s1 = warp_sum(s1); s2 = warp_sum(s2); s3 = warp_sum(s3);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { red[0][w] = s0; red[1][w] = s1; red[2][w] = s2; red[3][w] = s3; }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        float t = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[threadIdx.x][i];
+        P.sqerr[4 * iteration + threadIdx.x] = t;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host-side dispatch
 // ---------------------------------------------------------------------------
@@ -598,14 +630,20 @@ cudaError_t launch_adjust(const SingleArgs& a, int dt, int ntiles, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjust_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
-                                int dt, bool tau, cudaStream_t s)
+cudaError_t launch_adjust_list_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
+                                     int dt, bool tau, int iteration, cudaStream_t s)
 {
     dim3 grid(total_tiles), block(kTileThreads);
     FR_DISPATCH_DT(dt, D, {
-        if (tau) adj_batch<D, true><<<grid, block, 0, s>>>(probs, tile_start, nprob);
-        else adj_batch<D, false><<<grid, block, 0, s>>>(probs, tile_start, nprob);
+        if (tau) adj_list_batch<D, true><<<grid, block, 0, s>>>(probs, tile_start, nprob, iteration);
+        else adj_list_batch<D, false><<<grid, block, 0, s>>>(probs, tile_start, nprob, iteration);
     });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batch(const ProbDev* probs, int nprob, int iteration, cudaStream_t s)
+{
+    finalize_batch<<<nprob, 1024, 0, s>>>(probs, iteration);
     return cudaGetLastError();
 }
 

@@ -73,6 +73,52 @@ cudaError_t launch_apply(void* vol, int dt, int kind, long long nodes, float* dV
     return cudaGetLastError();
 }
 
+// Batched apply (paper rule, RGB records): blockIdx.y is the problem; each
+// problem's nodes are covered grid-stride.
+template <int DT>
+__global__ void __launch_bounds__(256) apply_batch_kernel(const ProbDev* __restrict__ probs, int clamp_nonneg)
+{
+    const ProbDev& P = probs[blockIdx.y];
+    void* vol = P.vol_rw;
+    float4* dV = reinterpret_cast<float4*>(P.dV);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P.nodes;
+         i += (long long)gridDim.x * blockDim.x) {
+        float4 v = load_rgb<DT>(vol, i);
+        const float4 d = dV[i];
+        v.x += d.x; v.y += d.y; v.z += d.z;
+        if (clamp_nonneg) { v.x = fmaxf(v.x, 0.0f); v.y = fmaxf(v.y, 0.0f); v.z = fmaxf(v.z, 0.0f); }
+        store_rgb<DT>(vol, i, v);
+        dV[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+}
+
+cudaError_t launch_apply_batch(const ProbDev* probs, int nprob, int dt, int clamp_nonneg, cudaStream_t s)
+{
+    const dim3 grid(96, nprob);
+    if (dt == DT_F32) apply_batch_kernel<DT_F32><<<grid, 256, 0, s>>>(probs, clamp_nonneg);
+    else if (dt == DT_BF16) apply_batch_kernel<DT_BF16><<<grid, 256, 0, s>>>(probs, clamp_nonneg);
+    else apply_batch_kernel<DT_F16><<<grid, 256, 0, s>>>(probs, clamp_nonneg);
+    return cudaGetLastError();
+}
+
+// rmse_all[(p * iters + i) * 3 + c] from each problem's error sums.
+__global__ void rmse_batch_kernel(const ProbDev* __restrict__ probs, int nprob, int iters, float* rmse_all)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nprob * iters) return;
+    const int p = t / iters, i = t - p * iters;
+    const float* sq = probs[p].sqerr + 4 * i;
+    const float cnt = sq[3];
+    for (int c = 0; c < 3; ++c) rmse_all[3 * t + c] = cnt > 0.0f ? 255.0f * sqrtf(sq[c] / cnt) : 0.0f;
+}
+
+cudaError_t launch_rmse_batch(const ProbDev* probs, int nprob, int iters, float* rmse_all, cudaStream_t s)
+{
+    const int n = nprob * iters;
+    rmse_batch_kernel<<<(n + 127) / 128, 128, 0, s>>>(probs, nprob, iters, rmse_all);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // In-scattering: J = (1/6) sum over the six axis directions of the emitted
 // radiance arriving along grid lines; each unit segment between adjacent nodes

@@ -42,6 +42,12 @@ class fr_camera(ctypes.Structure):
                 ("height", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
+class fr_problem(ctypes.Structure):
+    _fields_ = [("vol", fr_volume), ("cams", ctypes.c_void_p), ("ncam", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("targets", ctypes.c_void_p), ("bbox", ctypes.c_void_p),
+                ("rmse", ctypes.c_void_p)]
+
+
 class fr_params(ctypes.Structure):
     _fields_ = [("step", ctypes.c_float), ("alpha_l", ctypes.c_float), ("alpha_d", ctypes.c_float),
                 ("tau", ctypes.c_float), ("g_std", ctypes.c_float), ("flame_thresh", ctypes.c_float),
@@ -75,6 +81,7 @@ SIGNATURES = {
     "fr_planck_lut": (_S, [_P, _F, _F, _I, _P]),
     "fr_reconstruct": (_S, [_P, _P, _P, _P, _I, _P, _I, _P, _I, _I, _P, _P, _I]),
     "fr_count_samples": (_S, [_P, _P, _P, _I, _P, _P, _P]),
+    "fr_reconstruct_batch": (_S, [_P, _P, _I, _I, _I, _P, _I]),
     "fr_render_residual_noalloc": (_S, [_I, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, ctypes.c_char_p,
                                         ctypes.c_size_t]),
 }
@@ -248,6 +255,19 @@ class Context:
         self.check(self.lib.fr_count_samples(self.h, ctypes.byref(vol), cams, len(cams), ctypes.byref(p),
                                              _ptr(residual), ctypes.byref(n)))
         return n.value
+
+    def fr_reconstruct_batch(self, problems, iters, p, first_iteration=0, use_graph=True):
+        """problems: sequence of (fr_volume, camera array, targets, bbox, rmse or None)."""
+        arr = (fr_problem * len(problems))()
+        keep = []
+        for q, (vol, cams, targets, bbox, rmse) in zip(arr, problems):
+            q.vol = vol
+            q.cams = ctypes.cast(cams, ctypes.c_void_p)
+            q.ncam = len(cams)
+            q.targets, q.bbox, q.rmse = _ptr(targets), _ptr(bbox), _ptr(rmse)
+            keep.append(cams)
+        self.check(self.lib.fr_reconstruct_batch(self.h, arr, len(problems), int(iters), int(first_iteration),
+                                                 ctypes.byref(p), int(bool(use_graph))))
 
     def fr_synchronize(self):
         self.check(self.lib.fr_synchronize(self.h))

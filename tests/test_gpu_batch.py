@@ -1,0 +1,56 @@
+"""Batched reconstruction (independent problems such as video frames, one
+launch per phase for all of them): each problem's result equals the one it
+gets when reconstructed alone, with and without CUDA-graph capture."""
+import numpy as np
+import pytest
+
+from gpu_cases import rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _problem(fr, ctx, synth, n, views, side, seed, step=0.5):
+    shape, origin, h = synth.unit_grid(n)
+    cams = synth.ring_cameras(views, side, side, elevation_jitter_deg=8.0, seed=seed)
+    gt, _ = synth.plume_volume(n, seed)
+    gt_d = torch.as_tensor(gt, dtype=torch.float32, device="cuda").contiguous()
+    img = torch.zeros((views, side, side, 3), device="cuda")
+    ctx.fr_render(fr.volume(gt_d, origin, h), fr.cameras(cams), fr.params(step=step), img)
+    img /= img.max()
+    bbox = torch.zeros((views, 4), dtype=torch.int32, device="cuda")
+    ctx.fr_prepare_targets(img, 30 / 255, bbox)
+    v0 = gt_d.clone()
+    v0[..., :3] *= 0.2
+    return dict(origin=origin, h=h, cams=cams, targets=img, bbox=bbox, v0=v0)
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_equals_each_problem_alone(use_graph):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_06417_gb300 import flamerec as fr, synth
+    ctx = fr.Context(0)
+    specs = [(24, 3, 40, 11), (32, 5, 56, 12), (20, 4, 33, 13)]
+    probs = [_problem(fr, ctx, synth, *s) for s in specs]
+    iters, p = 4, fr.params(step=0.5, alpha_l=2e-3, g_std=0.05, seed=9)
+    alone = []
+    for q in probs:
+        v = q["v0"].clone()
+        rmse = np.zeros((iters, 3), dtype=np.float32)
+        ctx.fr_reconstruct(fr.volume(v, q["origin"], q["h"]), fr.cameras(q["cams"]), q["targets"], q["bbox"],
+                           iters, p, first_iteration=2, rmse=rmse)
+        alone.append((v, rmse))
+    vols = [q["v0"].clone() for q in probs]
+    rmses = [torch.zeros((iters, 3), device="cuda") for _ in probs]
+    batch = [(fr.volume(v, q["origin"], q["h"]), fr.cameras(q["cams"]), q["targets"], q["bbox"], r)
+             for v, q, r in zip(vols, probs, rmses)]
+    ctx.fr_reconstruct_batch(batch, iters, p, first_iteration=2, use_graph=use_graph)
+    torch.cuda.synchronize()
+    for (va, ra), vb, rb in zip(alone, vols, rmses):
+        e = rel_err(vb.cpu().numpy()[..., :3], va.cpu().numpy()[..., :3].astype(np.float64))
+        print(f"batch vs alone: volume {e.max():.2e}")
+        assert e.max() < 1e-4
+        np.testing.assert_allclose(rb.cpu().numpy(), ra, rtol=1e-4)
+    ctx.close()
