@@ -235,6 +235,66 @@ typedef struct fr_problem {
 fr_status fr_reconstruct_batch(fr_ctx *ctx, const fr_problem *probs, int nprob, int iters,
                                int first_iteration, const fr_params *p, int use_graph);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a continuous-batching reconstruction server (no counterpart in the
+ * paper, which reconstructs one frame at a time).  Jobs are admitted in
+ * arrival order while their device footprint fits the server's memory budget;
+ * every step advances all resident jobs by one iteration of the paper rule in
+ * shared launches (their rays batched together); jobs join and leave at step
+ * boundaries.  Volumes are held in the server's storage type with float32
+ * arithmetic.  Calls on one server must not run concurrently.
+ * ------------------------------------------------------------------------- */
+typedef struct fr_server fr_server;
+typedef struct fr_job fr_job;
+
+typedef enum fr_job_state {
+    FR_JOB_QUEUED = 0, FR_JOB_RUNNING = 1, FR_JOB_DONE = 2, FR_JOB_CANCELED = 3
+} fr_job_state;
+
+/* A job.  Host buffers must stay valid until the job is done or cancelled. */
+typedef struct fr_job_desc {
+    int32_t nx, ny, nz, pad_;
+    float origin[3];
+    float h;
+    const fr_camera *cams;      /* host, ncam cameras sharing one image size (copied) */
+    int32_t ncam;
+    int32_t iters;              /* iterations to run */
+    const void *init_records;   /* host, nodes x 4 records in the server's storage type:
+                                   initial {S_r, S_g, S_b, sigma} */
+    const float *targets;       /* host, ncam x H x W x 3 raw frames (prepared on admission) */
+    void *result_records;       /* host, nodes x 4 records: written when the job completes */
+    float *rmse;                /* host, iters x 3 per-iteration error, or NULL */
+} fr_job_desc;
+
+typedef struct fr_job_info {
+    int32_t state;              /* fr_job_state */
+    int32_t iters_done;
+    double t_submit, t_admit, t_done;  /* seconds on the server's clock (steady) */
+    size_t footprint;           /* device bytes while resident */
+} fr_job_info;
+
+/* budget_bytes: device memory the server may hold for resident jobs; 0 means
+ * 80% of the device's free memory at creation.  dtype: storage type of every
+ * job's volume.  p: shared method parameters (paper rule). */
+fr_status fr_server_create(fr_ctx *ctx, const fr_params *p, int dtype, size_t budget_bytes,
+                           fr_server **out);
+fr_status fr_server_destroy(fr_server *srv);
+/* Queue a job.  FR_ENOMEM if its footprint exceeds the whole budget. */
+fr_status fr_server_submit(fr_server *srv, const fr_job_desc *desc, fr_job **out);
+/* One step: retire finished jobs, admit queued jobs that fit, advance every
+ * resident job by one iteration.  Blocks until the step's device work is done.
+ * running (nullable): resident jobs after the step; queued: jobs waiting. */
+fr_status fr_server_step(fr_server *srv, int *running, int *queued);
+fr_status fr_job_get_info(const fr_job *job, fr_job_info *info);
+/* Step the server until the job is done or timeout_ms passes (FR_ETIMEDOUT). */
+fr_status fr_job_wait(fr_server *srv, fr_job *job, int timeout_ms);
+/* Cancel a queued or running job (its memory is released at the next step). */
+fr_status fr_job_cancel(fr_server *srv, fr_job *job);
+/* Free a finished or cancelled job's handle (FR_EBUSY while it is queued or running). */
+fr_status fr_job_release(fr_server *srv, fr_job *job);
+/* Device bytes currently held for resident jobs. */
+fr_status fr_server_memory(const fr_server *srv, size_t *used, size_t *budget);
+
 /* Number of samples (segments) the rays of `cams` take through the volume's
  * box: all rays when residual is NULL (one render), else only the rays whose
  * residual (device, image layout) is non-zero (one adjustment).  Counted by a

@@ -1,260 +1,8 @@
 // api.cu -- the C ABI declared in include/flamerec.h: argument validation,
 // library-owned scratch, kernel launches and the reconstruction loop.
-#include <algorithm>
-#include <climits>
-#include <cmath>
-#include <cstdarg>
-#include <cstdio>
-#include <cstring>
-#include <mutex>
-#include <new>
 #include <string>
 
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
-#include "flamerec.h"
-#include "fr_internal.h"
-
-using namespace frk;
-
-namespace {
-
-struct Buf {
-    void* p = nullptr;
-    size_t bytes = 0;
-};
-
-}  // namespace
-
-struct fr_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;   // where work is queued (borrowed; 0 = default stream)
-    char err[512] = {0};             // last failure message
-    Buf partials, counter, residual, rendered, dV, targets, sqerr, rmse, J, src, flame_off, flame_list;
-    Buf batch;                       // batched reconstruction scratch and tables
-    unsigned long long* host_counter = nullptr;
-    void* staging = nullptr;         // pinned host staging of batch tables
-    size_t staging_bytes = 0;
-    cudaEvent_t staging_done = nullptr;
-    cudaStream_t capture = nullptr;  // stream used to capture CUDA graphs
-};
-
-namespace {
-
-fr_status fail(fr_ctx* c, fr_status s, const char* fmt, ...)
-{
-    if (c) {
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(c->err, sizeof c->err, fmt, ap);
-        va_end(ap);
-    }
-    return s;
-}
-
-fr_status cuda_fail(fr_ctx* c, cudaError_t e, const char* what)
-{
-    return fail(c, FR_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
-}
-
-#define FR_CUDA(ctx, expr)                                 \
-    do {                                                   \
-        cudaError_t e_ = (expr);                           \
-        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
-    } while (0)
-
-// Device-pointer check: the pointer must lie in a device allocation that
-// holds at least `bytes` from it.  Catches host pointers and short buffers
-// before any kernel could touch them.
-PFN_cuMemGetAddressRange_v3020 range_fn()
-{
-    static PFN_cuMemGetAddressRange_v3020 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess && q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuMemGetAddressRange_v3020>(f);
-    });
-    return fn;
-}
-
-fr_status check_dev(fr_ctx* c, const void* p, size_t bytes, const char* name)
-{
-    if (!p) return fail(c, FR_EINVAL, "%s is NULL", name);
-    cudaPointerAttributes at;
-    cudaError_t e = cudaPointerGetAttributes(&at, p);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(c, FR_EINVAL, "%s is not a CUDA pointer (%s)", name, cudaGetErrorName(e));
-    }
-    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
-        return fail(c, FR_EINVAL, "%s must be device memory", name);
-    if (at.type == cudaMemoryTypeDevice && at.device != c->device)
-        return fail(c, FR_EINVAL, "%s lives on device %d, context on %d", name, at.device, c->device);
-    if (auto fn = range_fn()) {
-        CUdeviceptr base = 0;
-        size_t size = 0;
-        if (fn(&base, &size, (CUdeviceptr)(uintptr_t)p) == CUDA_SUCCESS) {
-            if ((uintptr_t)p + bytes > (uintptr_t)base + size)
-                return fail(c, FR_EINVAL, "%s: %zu bytes needed but the allocation ends %zu bytes after it",
-                            name, bytes, (size_t)((uintptr_t)base + size - (uintptr_t)p));
-        }
-    }
-    return FR_OK;
-}
-
-fr_status check_align(fr_ctx* c, const void* p, size_t a, const char* name)
-{
-    if ((uintptr_t)p % a) return fail(c, FR_EINVAL, "%s must be %zu-byte aligned", name, a);
-    return FR_OK;
-}
-
-int rec_components(int kind) { return kind == FR_KIND_RGB ? 4 : 2; }
-int dtype_bytes(int dt) { return dt == FR_F32 ? 4 : 2; }
-size_t rec_bytes(const fr_volume* v) { return (size_t)rec_components(v->kind) * dtype_bytes(v->dtype); }
-long long node_count(const fr_volume* v) { return (long long)v->nx * v->ny * v->nz; }
-
-bool finite3(const float* x) { return std::isfinite(x[0]) && std::isfinite(x[1]) && std::isfinite(x[2]); }
-
-fr_status check_volume(fr_ctx* c, const fr_volume* v, const char* name)
-{
-    if (!v) return fail(c, FR_EINVAL, "%s is NULL", name);
-    if (v->nx < 2 || v->ny < 2 || v->nz < 2 || v->nx > 8192 || v->ny > 8192 || v->nz > 8192)
-        return fail(c, FR_EINVAL, "%s: extents must be in [2, 8192], got %d x %d x %d", name, v->nx, v->ny, v->nz);
-    if (node_count(v) > (1LL << 34)) return fail(c, FR_EINVAL, "%s: too many nodes", name);
-    if (v->kind != FR_KIND_RGB && v->kind != FR_KIND_TEMP) return fail(c, FR_EINVAL, "%s: bad kind %d", name, v->kind);
-    if (v->dtype != FR_F32 && v->dtype != FR_BF16 && v->dtype != FR_F16)
-        return fail(c, FR_EINVAL, "%s: bad dtype %d", name, v->dtype);
-    if (!(v->h > 0.0f) || !std::isfinite(v->h) || !finite3(v->origin))
-        return fail(c, FR_EINVAL, "%s: spacing must be positive and origin finite", name);
-    fr_status s = check_align(c, v->data, rec_bytes(v), name);
-    if (s) return s;
-    return check_dev(c, v->data, (size_t)node_count(v) * rec_bytes(v), name);
-}
-
-fr_status check_cams(fr_ctx* c, const fr_camera* cams, int ncam)
-{
-    if (!cams) return fail(c, FR_EINVAL, "cams is NULL");
-    if (ncam < 1 || ncam > kMaxViews) return fail(c, FR_EINVAL, "ncam must be in [1, %d], got %d", kMaxViews, ncam);
-    for (int i = 0; i < ncam; ++i) {
-        const fr_camera& k = cams[i];
-        if (k.width < 1 || k.height < 1 || k.width > 16384 || k.height > 16384)
-            return fail(c, FR_EINVAL, "camera %d: image size must be in [1, 16384]", i);
-        if (k.width != cams[0].width || k.height != cams[0].height)
-            return fail(c, FR_EINVAL, "camera %d: all cameras must share one image size", i);
-        if (!(k.tan_half_fov > 0.0f) || !std::isfinite(k.tan_half_fov))
-            return fail(c, FR_EINVAL, "camera %d: tan_half_fov must be positive", i);
-        if (!finite3(k.pos) || !finite3(k.right) || !finite3(k.up) || !finite3(k.fwd))
-            return fail(c, FR_EINVAL, "camera %d: non-finite vector", i);
-        auto dot = [](const float* a, const float* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
-        if (fabsf(dot(k.fwd, k.fwd) - 1.0f) > 1e-3f || fabsf(dot(k.right, k.right) - 1.0f) > 1e-3f ||
-            fabsf(dot(k.up, k.up) - 1.0f) > 1e-3f || fabsf(dot(k.fwd, k.right)) > 1e-3f ||
-            fabsf(dot(k.fwd, k.up)) > 1e-3f || fabsf(dot(k.right, k.up)) > 1e-3f)
-            return fail(c, FR_EINVAL, "camera %d: right, up, fwd must be orthonormal", i);
-    }
-    return FR_OK;
-}
-
-fr_status check_params(fr_ctx* c, const fr_params* p, const fr_volume* v, const fr_camera* cams)
-{
-    if (!p) return fail(c, FR_EINVAL, "params is NULL");
-    if (!(p->step > 0.0f) || !std::isfinite(p->step)) return fail(c, FR_EINVAL, "step must be positive");
-    double diag = std::sqrt((double)(v->nx - 1) * (v->nx - 1) + (double)(v->ny - 1) * (v->ny - 1) +
-                            (double)(v->nz - 1) * (v->nz - 1));
-    double max_seg = std::ceil(diag / p->step) + 1.0;
-    if (max_seg > 1e6) return fail(c, FR_EINVAL, "step too small: up to %.0f samples per ray", max_seg);
-    if (!std::isfinite(p->alpha_l) || !std::isfinite(p->alpha_d) || p->alpha_d < 0.0f)
-        return fail(c, FR_EINVAL, "alpha_l must be finite and alpha_d finite and >= 0");
-    if (!(p->tau < 1.0f) || !std::isfinite(p->tau)) return fail(c, FR_EINVAL, "tau must be < 1");
-    if (!std::isfinite(p->flame_thresh)) return fail(c, FR_EINVAL, "flame_thresh must be finite");
-    if (!(p->g_std >= 0.0f) || !std::isfinite(p->g_std)) return fail(c, FR_EINVAL, "g_std must be >= 0");
-    if (p->g_std > 0.0f) {
-        // counter layout of the G(s) stream: 20 bits iteration, 8 view, 22 pixel, 14 sample
-        if ((long long)cams[0].width * cams[0].height > (1LL << 22))
-            return fail(c, FR_EINVAL, "g_std > 0 supports at most 2^22 pixels per view");
-        if (max_seg > 16383.0) return fail(c, FR_EINVAL, "g_std > 0 supports at most 16383 samples per ray");
-    }
-    if (v->kind == FR_KIND_TEMP) {
-        if (!p->lut || p->lut_size < 2 || !(p->lut_t_max > p->lut_t_min))
-            return fail(c, FR_EINVAL, "temperature volumes need lut, lut_size >= 2 and lut_t_max > lut_t_min");
-        fr_status s = check_align(c, p->lut, 16, "lut");
-        if (s) return s;
-        return check_dev(c, p->lut, (size_t)p->lut_size * 16, "lut");
-    }
-    return FR_OK;
-}
-
-fr_status ensure(fr_ctx* c, Buf& b, size_t bytes, const char* name)
-{
-    if (b.bytes >= bytes) return FR_OK;
-    if (b.p) {
-        FR_CUDA(c, cudaStreamSynchronize(c->stream));
-        cudaFree(b.p);
-        b.p = nullptr;
-        b.bytes = 0;
-    }
-    size_t want = bytes < 256 ? 256 : bytes;
-    cudaError_t e = cudaMalloc(&b.p, want);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        b.p = nullptr;
-        return fail(c, FR_ENOMEM, "cannot allocate %zu bytes of %s scratch", want, name);
-    }
-    b.bytes = want;
-    return FR_OK;
-}
-
-void fill_problem(const fr_volume* v, const fr_camera* cams, int ncam, const fr_params* p, SingleArgs& a)
-{
-    memset(&a, 0, sizeof a);
-    ProbDev& P = a.p;
-    P.vol = v->data;
-    P.nx = v->nx; P.ny = v->ny; P.nz = v->nz;
-    P.ncam = ncam;
-    P.W = cams[0].width;
-    P.H = cams[0].height;
-    P.tiles_x = (P.W + kTileW - 1) / kTileW;
-    P.tiles_y = (P.H + kTileH - 1) / kTileH;
-    P.img_scale = 1.0f;
-    P.step = p->step;
-    P.alpha_l = p->alpha_l;
-    P.alpha_d = p->alpha_d;
-    P.tau = p->tau > 0.0f ? p->tau : 0.0f;
-    P.g_std = p->g_std;
-    P.thresh = p->flame_thresh;
-    P.seed = p->seed;
-    if (v->kind == FR_KIND_TEMP) {
-        P.lut = reinterpret_cast<const float4*>(p->lut);
-        P.lut_m = p->lut_size;
-        P.lut_t0 = p->lut_t_min;
-        P.lut_scale = (float)(p->lut_size - 1) / (p->lut_t_max - p->lut_t_min);
-    }
-    const float inv_h = 1.0f / v->h;
-    for (int i = 0; i < ncam; ++i) {
-        CamDev& d = a.cams[i];
-        const fr_camera& k = cams[i];
-        for (int ax = 0; ax < 3; ++ax) {
-            d.o[ax] = (k.pos[ax] - v->origin[ax]) * inv_h;
-            d.r[ax] = k.right[ax];
-            d.u[ax] = k.up[ax];
-            d.f[ax] = k.fwd[ax];
-        }
-        d.ty = k.tan_half_fov;
-        d.tx = k.tan_half_fov * (float)k.width / (float)k.height;
-        d.W = k.width;
-        d.H = k.height;
-    }
-}
-
-size_t image_bytes(const fr_camera* cams, int ncam)
-{
-    return (size_t)ncam * cams[0].width * cams[0].height * 3 * sizeof(float);
-}
-
-}  // namespace
+#include "abi_common.h"
 
 // ---------------------------------------------------------------------------
 // Context
@@ -342,17 +90,6 @@ extern "C" fr_status fr_synchronize(fr_ctx* c)
 // ---------------------------------------------------------------------------
 // Single calls
 // ---------------------------------------------------------------------------
-
-#define FR_TRY(expr)                  \
-    do {                              \
-        fr_status s_ = (expr);        \
-        if (s_ != FR_OK) return s_;   \
-    } while (0)
-
-#define FR_BEGIN(c)                                   \
-    if (!c) return FR_EINVAL;                         \
-    c->err[0] = '\0';                                 \
-    FR_CUDA(c, cudaSetDevice(c->device))
 
 extern "C" fr_status fr_prepare_targets(fr_ctx* c, int ncam, int height, int width, float* targets,
                                         float thresh, int32_t* bbox)
@@ -734,12 +471,6 @@ extern "C" fr_status fr_render_residual_noalloc(int device, void* stream, const 
 // Batched reconstruction
 // ---------------------------------------------------------------------------
 
-namespace {
-
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-}  // namespace
-
 extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, int nprob, int iters,
                                           int first_iteration, const fr_params* p, int use_graph)
 {
@@ -837,6 +568,8 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         P.nodes = nodes;
         P.sqerr = sqerr;
         P.ntiles = nt;
+        P.iteration = first_iteration;
+        P.sq_slot = 0;
         h_probs[i] = P;
         for (int v = 0; v < q.ncam; ++v) h_cams[cam_off + v] = a.cams[v];
         h_tiles[i] = tile_off;
@@ -856,7 +589,7 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
             e = launch_fwd_batch(d_probs, d_tiles, nprob, tile_off, dt, KIND_RGB, tau, st);
             if (e == cudaSuccess) e = launch_finalize_batch(d_probs, nprob, it, st);
             if (e == cudaSuccess)
-                e = launch_adjust_list_batch(d_probs, d_tiles, nprob, tile_off, dt, tau, first_iteration + it, st);
+                e = launch_adjust_list_batch(d_probs, d_tiles, nprob, tile_off, dt, tau, it, st);
             if (e == cudaSuccess) e = launch_apply_batch(d_probs, nprob, dt, p->clamp_nonneg, st);
         }
         return e;

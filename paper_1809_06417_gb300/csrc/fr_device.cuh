@@ -64,7 +64,7 @@ struct ProbDev {
     long long nodes;
     float* sqerr;                // 4 floats per iteration
     int ntiles;
-    int pad2_;
+    int sq_slot;                 // error slot of the launch's first iteration
 };
 
 // ---------------------------------------------------------------------------

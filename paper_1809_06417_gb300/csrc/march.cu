@@ -284,7 +284,8 @@ __global__ void FR_MARCH_BOUNDS adj_list(const __grid_constant__ SingleArgs a, c
 }
 
 // Batched form: CTA b belongs to the problem whose tile range holds b and
-// takes that problem's list entries [128 (b - start), ...).
+// takes that problem's list entries [128 (b - start), ...).  The G(s) stream
+// index is the problem's own iteration plus `iteration`.
 template <int DT, bool TAU>
 __global__ void FR_MARCH_BOUNDS adj_list_batch(const ProbDev* __restrict__ probs, const int* __restrict__ tile_start,
                                                int nprob, int iteration)
@@ -298,7 +299,7 @@ __global__ void FR_MARCH_BOUNDS adj_list_batch(const ProbDev* __restrict__ probs
     const int view = (int)(pix / per_view);
     const unsigned r = pix - (unsigned)view * per_view;
     const int py = (int)(r / (unsigned)P.W), px = (int)(r - (unsigned)py * (unsigned)P.W);
-    adj_ray<DT, TAU>(P, P.cams, view, px, py, iteration);
+    adj_ray<DT, TAU>(P, P.cams, view, px, py, P.iteration + iteration);
 }
 
 template <int DT, bool TAU>
@@ -553,7 +554,7 @@ __global__ void __launch_bounds__(kTileThreads) flame_list_kernel(const __grid_c
 }
 
 // Per-problem sums of the squared-error partials (one CTA per problem), into
-// the problem's error slot of iteration `iteration`.
+// the problem's error slot sq_slot + iteration.
 __global__ void __launch_bounds__(1024) finalize_batch(const ProbDev* __restrict__ probs, int iteration)
 {
     __shared__ float red[4][32];
@@ -571,7 +572,7 @@ __global__ void __launch_bounds__(1024) finalize_batch(const ProbDev* __restrict
     if (threadIdx.x < 4) {
         float t = 0.0f;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[threadIdx.x][i];
-        P.sqerr[4 * iteration + threadIdx.x] = t;
+        P.sqerr[4 * (P.sq_slot + iteration) + threadIdx.x] = t;
     }
 }
 

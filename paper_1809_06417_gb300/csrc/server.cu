@@ -1,0 +1,427 @@
+// server.cu -- continuous-batching reconstruction server over the batched
+// kernels: admission by device-memory budget, one iteration of every
+// resident job per step in shared launches, retirement at step boundaries.
+#include <chrono>
+#include <deque>
+#include <vector>
+
+#include "abi_common.h"
+
+struct fr_job {
+    fr_job_desc d;
+    std::vector<fr_camera> cams;
+    int state = FR_JOB_QUEUED;
+    int iters_done = 0;
+    bool cancel = false;
+    size_t footprint = 0;
+    double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+    // device memory while resident (one pool allocation)
+    char* mem = nullptr;
+    void* vol = nullptr;
+    float* targets = nullptr;
+    int* bbox = nullptr;
+    float* residual = nullptr;
+    float* dV = nullptr;
+    float* partials = nullptr;
+    float* sqerr = nullptr;
+    unsigned* fbuf = nullptr;
+    unsigned* flist = nullptr;
+    int ntiles = 0;
+};
+
+struct fr_server {
+    fr_ctx* ctx = nullptr;
+    fr_params p{};
+    int dtype = FR_F32;
+    size_t budget = 0, used = 0;
+    cudaMemPool_t pool = nullptr;
+    std::deque<fr_job*> queue;
+    std::vector<fr_job*> resident;
+    Buf tables;                  // device ProbDev / CamDev / tile starts
+    void* staging = nullptr;     // pinned host staging of the tables
+    size_t staging_bytes = 0;
+    cudaEvent_t staging_done = nullptr;
+    std::chrono::steady_clock::time_point t0;
+
+    double now() const
+    {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+struct JobLayout {
+    size_t vol, targets, bbox, residual, dV, partials, sqerr, fbuf, flist, total;
+};
+
+JobLayout job_layout(const fr_job_desc& d, int dtype, const fr_camera* cams)
+{
+    JobLayout L{};
+    const long long nodes = (long long)d.nx * d.ny * d.nz;
+    const size_t ib = image_bytes(cams, d.ncam);
+    const int nt = tiles_of(cams[0].width, cams[0].height, d.ncam);
+    const long long npix = (long long)d.ncam * cams[0].width * cams[0].height;
+    size_t o = 0;
+    L.vol = o; o += align256((size_t)nodes * 4 * dtype_bytes(dtype));
+    L.targets = o; o += align256(ib);
+    L.bbox = o; o += align256((size_t)d.ncam * 16);
+    L.residual = o; o += align256(ib);
+    L.dV = o; o += align256((size_t)nodes * 16);
+    L.partials = o; o += align256((size_t)nt * 16);
+    L.sqerr = o; o += align256((size_t)std::max(d.iters, 1) * 16);
+    L.fbuf = o; o += align256(flame_list_buf_entries(nt) * 4);
+    L.flist = o; o += align256((size_t)npix * 4);
+    L.total = o;
+    return L;
+}
+
+fr_volume job_volume(const fr_job* j, int dtype)
+{
+    fr_volume v{};
+    v.nx = j->d.nx; v.ny = j->d.ny; v.nz = j->d.nz;
+    v.kind = FR_KIND_RGB;
+    v.dtype = dtype;
+    for (int a = 0; a < 3; ++a) v.origin[a] = j->d.origin[a];
+    v.h = j->d.h;
+    v.data = j->vol;
+    return v;
+}
+
+void job_free(fr_server* s, fr_job* j)
+{
+    if (j->mem) {
+        cudaFreeAsync(j->mem, s->ctx->stream);
+        j->mem = nullptr;
+        s->used -= j->footprint;
+    }
+}
+
+// Admission: allocate, upload the initial volume and the frames, prepare the
+// targets and build the flame-ray list.
+fr_status job_admit(fr_server* s, fr_job* j)
+{
+    fr_ctx* c = s->ctx;
+    cudaStream_t st = c->stream;
+    const JobLayout L = job_layout(j->d, s->dtype, j->cams.data());
+    void* mem = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&mem, L.total, s->pool, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, FR_ENOMEM, "job %p: device allocation of %zu bytes failed", (void*)j, L.total);
+    }
+    j->mem = static_cast<char*>(mem);
+    s->used += j->footprint;
+    j->vol = j->mem + L.vol;
+    j->targets = reinterpret_cast<float*>(j->mem + L.targets);
+    j->bbox = reinterpret_cast<int*>(j->mem + L.bbox);
+    j->residual = reinterpret_cast<float*>(j->mem + L.residual);
+    j->dV = reinterpret_cast<float*>(j->mem + L.dV);
+    j->partials = reinterpret_cast<float*>(j->mem + L.partials);
+    j->sqerr = reinterpret_cast<float*>(j->mem + L.sqerr);
+    j->fbuf = reinterpret_cast<unsigned*>(j->mem + L.fbuf);
+    j->flist = reinterpret_cast<unsigned*>(j->mem + L.flist);
+    const long long nodes = (long long)j->d.nx * j->d.ny * j->d.nz;
+    const size_t ib = image_bytes(j->cams.data(), j->d.ncam);
+    const int W = j->cams[0].width, H = j->cams[0].height;
+    j->ntiles = tiles_of(W, H, j->d.ncam);
+    FR_CUDA(c, cudaMemcpyAsync(j->vol, j->d.init_records, (size_t)nodes * 4 * dtype_bytes(s->dtype),
+                               cudaMemcpyHostToDevice, st));
+    FR_CUDA(c, cudaMemcpyAsync(j->targets, j->d.targets, ib, cudaMemcpyHostToDevice, st));
+    FR_CUDA(c, cudaMemsetAsync(j->dV, 0, (size_t)nodes * 16, st));
+    FR_CUDA(c, launch_prepare_targets(j->targets, j->d.ncam, H, W, s->p.flame_thresh, j->bbox, st));
+    static thread_local SingleArgs a;
+    fr_volume v = job_volume(j, s->dtype);
+    fill_problem(&v, j->cams.data(), j->d.ncam, &s->p, a);
+    a.p.targets = j->targets;
+    FR_CUDA(c, launch_flame_list(a, j->ntiles, j->fbuf, j->flist, st));
+    j->state = FR_JOB_RUNNING;
+    j->t_admit = s->now();
+    return FR_OK;
+}
+
+// Completion: per-iteration error and the final volume back to the host.
+fr_status job_complete(fr_server* s, fr_job* j)
+{
+    fr_ctx* c = s->ctx;
+    cudaStream_t st = c->stream;
+    const long long nodes = (long long)j->d.nx * j->d.ny * j->d.nz;
+    if (j->d.rmse) {
+        std::vector<float> sq((size_t)j->d.iters * 4);
+        FR_CUDA(c, cudaMemcpyAsync(sq.data(), j->sqerr, sq.size() * 4, cudaMemcpyDeviceToHost, st));
+        FR_CUDA(c, cudaStreamSynchronize(st));
+        for (int i = 0; i < j->d.iters; ++i)
+            for (int ch = 0; ch < 3; ++ch) {
+                const float cnt = sq[4 * i + 3];
+                j->d.rmse[3 * i + ch] = cnt > 0.0f ? 255.0f * std::sqrt(sq[4 * i + ch] / cnt) : 0.0f;
+            }
+    }
+    FR_CUDA(c, cudaMemcpyAsync(j->d.result_records, j->vol, (size_t)nodes * 4 * dtype_bytes(s->dtype),
+                               cudaMemcpyDeviceToHost, st));
+    FR_CUDA(c, cudaStreamSynchronize(st));
+    job_free(s, j);
+    j->state = FR_JOB_DONE;
+    j->t_done = s->now();
+    return FR_OK;
+}
+
+}  // namespace
+
+extern "C" fr_status fr_server_create(fr_ctx* c, const fr_params* p, int dtype, size_t budget, fr_server** out)
+{
+    FR_BEGIN(c);
+    if (!out || !p) return fail(c, FR_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (dtype != FR_F32 && dtype != FR_BF16 && dtype != FR_F16) return fail(c, FR_EINVAL, "bad dtype");
+    if (p->rule != FR_RULE_PAPER) return fail(c, FR_EINVAL, "the server runs the paper rule");
+    if (!(p->step > 0.0f) || !std::isfinite(p->alpha_l) || !(p->tau < 1.0f))
+        return fail(c, FR_EINVAL, "bad parameters");
+    size_t free_b = 0, total_b = 0;
+    FR_CUDA(c, cudaMemGetInfo(&free_b, &total_b));
+    if (budget == 0) budget = free_b / 10 * 8;
+    if (budget > free_b) return fail(c, FR_ENOMEM, "budget %zu exceeds free device memory %zu", budget, free_b);
+    fr_server* s = new (std::nothrow) fr_server();
+    if (!s) return fail(c, FR_ENOMEM, "host allocation failed");
+    s->ctx = c;
+    s->p = *p;
+    s->dtype = dtype;
+    s->budget = budget;
+    s->t0 = std::chrono::steady_clock::now();
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = c->device;
+    cudaError_t e = cudaMemPoolCreate(&s->pool, &props);
+    if (e == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;  // keep released memory in the pool between jobs
+        e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->staging_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (s->pool) cudaMemPoolDestroy(s->pool);
+        delete s;
+        return cuda_fail(c, e, "server set-up");
+    }
+    *out = s;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_server_destroy(fr_server* s)
+{
+    if (!s) return FR_EINVAL;
+    fr_ctx* c = s->ctx;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (fr_job* j : s->resident) job_free(s, j);
+    cudaStreamSynchronize(c->stream);
+    if (s->tables.p) cudaFree(s->tables.p);
+    if (s->staging) cudaFreeHost(s->staging);
+    if (s->staging_done) cudaEventDestroy(s->staging_done);
+    if (s->pool) cudaMemPoolDestroy(s->pool);
+    delete s;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_server_submit(fr_server* s, const fr_job_desc* d, fr_job** out)
+{
+    if (!s) return FR_EINVAL;
+    fr_ctx* c = s->ctx;
+    FR_BEGIN(c);
+    if (!d || !out) return fail(c, FR_EINVAL, "NULL argument");
+    *out = nullptr;
+    fr_volume v{};
+    v.nx = d->nx; v.ny = d->ny; v.nz = d->nz;
+    v.kind = FR_KIND_RGB;
+    v.dtype = s->dtype;
+    for (int a = 0; a < 3; ++a) v.origin[a] = d->origin[a];
+    v.h = d->h;
+    if (v.nx < 2 || v.ny < 2 || v.nz < 2 || v.nx > 8192 || v.ny > 8192 || v.nz > 8192)
+        return fail(c, FR_EINVAL, "job extents must be in [2, 8192]");
+    if (!(v.h > 0.0f) || !finite3(v.origin)) return fail(c, FR_EINVAL, "job spacing must be positive");
+    FR_TRY(check_cams(c, d->cams, d->ncam));
+    FR_TRY(check_params(c, &s->p, &v, d->cams));
+    if (d->iters < 1 || d->iters > (1 << 20)) return fail(c, FR_EINVAL, "iters must be in [1, 2^20]");
+    if (!d->init_records || !d->targets || !d->result_records) return fail(c, FR_EINVAL, "NULL host buffer");
+    const long long npix = (long long)d->ncam * d->cams[0].width * d->cams[0].height;
+    if (npix >= (1LL << 32)) return fail(c, FR_EINVAL, "at most 2^32 pixels per job");
+    const size_t fp = job_layout(*d, s->dtype, d->cams).total;
+    if (fp > s->budget) return fail(c, FR_ENOMEM, "job needs %zu bytes, the budget is %zu", fp, s->budget);
+    fr_job* j = new (std::nothrow) fr_job();
+    if (!j) return fail(c, FR_ENOMEM, "host allocation failed");
+    j->d = *d;
+    j->cams.assign(d->cams, d->cams + d->ncam);
+    j->d.cams = j->cams.data();
+    j->footprint = fp;
+    j->t_submit = s->now();
+    s->queue.push_back(j);
+    *out = j;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_server_step(fr_server* s, int* running, int* queued)
+{
+    if (!s) return FR_EINVAL;
+    fr_ctx* c = s->ctx;
+    FR_BEGIN(c);
+    cudaStream_t st = c->stream;
+    // retire cancelled jobs
+    for (size_t i = 0; i < s->resident.size();) {
+        fr_job* j = s->resident[i];
+        if (j->cancel) {
+            job_free(s, j);
+            j->state = FR_JOB_CANCELED;
+            j->t_done = s->now();
+            s->resident.erase(s->resident.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+    // admit in arrival order while the budget allows
+    while (!s->queue.empty()) {
+        fr_job* j = s->queue.front();
+        if (j->cancel) {
+            s->queue.pop_front();
+            j->state = FR_JOB_CANCELED;
+            j->t_done = s->now();
+            continue;
+        }
+        if (s->used + j->footprint > s->budget) break;
+        s->queue.pop_front();
+        fr_status r = job_admit(s, j);
+        if (r != FR_OK) {
+            j->state = FR_JOB_CANCELED;
+            j->t_done = s->now();
+            return r;
+        }
+        s->resident.push_back(j);
+    }
+    const int n = (int)s->resident.size();
+    if (n > 0) {
+        // tables of the resident jobs, with each job's own iteration
+        size_t ncam = 0;
+        for (fr_job* j : s->resident) ncam += (size_t)j->d.ncam;
+        const size_t tp = align256(sizeof(ProbDev) * n), tc = align256(sizeof(CamDev) * ncam);
+        const size_t tt = align256(sizeof(int) * (n + 1));
+        const size_t tables = tp + tc + tt;
+        FR_TRY(ensure(c, s->tables, tables, "server tables"));
+        FR_CUDA(c, cudaEventSynchronize(s->staging_done));
+        if (s->staging_bytes < tables) {
+            if (s->staging) cudaFreeHost(s->staging);
+            s->staging = nullptr;
+            s->staging_bytes = 0;
+            if (cudaMallocHost(&s->staging, tables * 2) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(c, FR_ENOMEM, "pinned staging");
+            }
+            s->staging_bytes = tables * 2;
+        }
+        char* hb = static_cast<char*>(s->staging);
+        char* db = static_cast<char*>(s->tables.p);
+        ProbDev* hp = reinterpret_cast<ProbDev*>(hb);
+        CamDev* hc = reinterpret_cast<CamDev*>(hb + tp);
+        int* ht = reinterpret_cast<int*>(hb + tp + tc);
+        ProbDev* dp = reinterpret_cast<ProbDev*>(db);
+        CamDev* dc = reinterpret_cast<CamDev*>(db + tp);
+        int* dtl = reinterpret_cast<int*>(db + tp + tc);
+        static thread_local SingleArgs a;
+        size_t cam_off = 0;
+        int tile_off = 0;
+        for (int i = 0; i < n; ++i) {
+            fr_job* j = s->resident[i];
+            fr_volume v = job_volume(j, s->dtype);
+            fill_problem(&v, j->cams.data(), j->d.ncam, &s->p, a);
+            ProbDev& P = a.p;
+            P.cams = dc + cam_off;
+            P.targets = j->targets;
+            P.bbox = j->bbox;
+            P.residual = j->residual;
+            P.partials = j->partials;
+            P.dV = j->dV;
+            P.img_in = j->residual;
+            P.img_scale = 1.0f;
+            P.list = j->flist;
+            P.list_count = j->fbuf + flame_list_total_at(j->ntiles);
+            P.vol_rw = j->vol;
+            P.nodes = (long long)j->d.nx * j->d.ny * j->d.nz;
+            P.sqerr = j->sqerr;
+            P.ntiles = j->ntiles;
+            P.iteration = j->iters_done;
+            P.sq_slot = j->iters_done;
+            hp[i] = P;
+            for (int k = 0; k < j->d.ncam; ++k) hc[cam_off + k] = a.cams[k];
+            ht[i] = tile_off;
+            cam_off += (size_t)j->d.ncam;
+            tile_off += j->ntiles;
+        }
+        ht[n] = tile_off;
+        FR_CUDA(c, cudaMemcpyAsync(db, hb, tables, cudaMemcpyHostToDevice, st));
+        FR_CUDA(c, cudaEventRecord(s->staging_done, st));
+        const bool tau = s->p.tau > 0.0f;
+        FR_CUDA(c, launch_fwd_batch(dp, dtl, n, tile_off, s->dtype, KIND_RGB, tau, st));
+        FR_CUDA(c, launch_finalize_batch(dp, n, 0, st));
+        FR_CUDA(c, launch_adjust_list_batch(dp, dtl, n, tile_off, s->dtype, tau, 0, st));
+        FR_CUDA(c, launch_apply_batch(dp, n, s->dtype, s->p.clamp_nonneg, st));
+        FR_CUDA(c, cudaStreamSynchronize(st));
+        // advance and retire
+        for (size_t i = 0; i < s->resident.size();) {
+            fr_job* j = s->resident[i];
+            j->iters_done += 1;
+            if (j->iters_done >= j->d.iters) {
+                FR_TRY(job_complete(s, j));
+                s->resident.erase(s->resident.begin() + i);
+            } else {
+                ++i;
+            }
+        }
+    }
+    if (running) *running = (int)s->resident.size();
+    if (queued) *queued = (int)s->queue.size();
+    return FR_OK;
+}
+
+extern "C" fr_status fr_job_get_info(const fr_job* j, fr_job_info* info)
+{
+    if (!j || !info) return FR_EINVAL;
+    info->state = j->state;
+    info->iters_done = j->iters_done;
+    info->t_submit = j->t_submit;
+    info->t_admit = j->t_admit;
+    info->t_done = j->t_done;
+    info->footprint = j->footprint;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_job_wait(fr_server* s, fr_job* j, int timeout_ms)
+{
+    if (!s || !j) return FR_EINVAL;
+    const auto t_end = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+    while (j->state == FR_JOB_QUEUED || j->state == FR_JOB_RUNNING) {
+        if (std::chrono::steady_clock::now() > t_end) return FR_ETIMEDOUT;
+        FR_TRY(fr_server_step(s, nullptr, nullptr));
+    }
+    return j->state == FR_JOB_DONE ? FR_OK : FR_ECANCELED;
+}
+
+extern "C" fr_status fr_job_cancel(fr_server* s, fr_job* j)
+{
+    if (!s || !j) return FR_EINVAL;
+    if (j->state == FR_JOB_QUEUED || j->state == FR_JOB_RUNNING) j->cancel = true;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_job_release(fr_server* s, fr_job* j)
+{
+    if (!s || !j) return FR_EINVAL;
+    if (j->state == FR_JOB_QUEUED || j->state == FR_JOB_RUNNING) return FR_EBUSY;
+    delete j;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_server_memory(const fr_server* s, size_t* used, size_t* budget)
+{
+    if (!s) return FR_EINVAL;
+    if (used) *used = s->used;
+    if (budget) *budget = s->budget;
+    return FR_OK;
+}

@@ -48,6 +48,21 @@ class fr_problem(ctypes.Structure):
                 ("rmse", ctypes.c_void_p)]
 
 
+class fr_job_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("origin", ctypes.c_float * 3), ("h", ctypes.c_float), ("cams", ctypes.c_void_p),
+                ("ncam", ctypes.c_int32), ("iters", ctypes.c_int32), ("init_records", ctypes.c_void_p),
+                ("targets", ctypes.c_void_p), ("result_records", ctypes.c_void_p), ("rmse", ctypes.c_void_p)]
+
+
+class fr_job_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("iters_done", ctypes.c_int32), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("footprint", ctypes.c_size_t)]
+
+
+FR_JOB_QUEUED, FR_JOB_RUNNING, FR_JOB_DONE, FR_JOB_CANCELED = range(4)
+
+
 class fr_params(ctypes.Structure):
     _fields_ = [("step", ctypes.c_float), ("alpha_l", ctypes.c_float), ("alpha_d", ctypes.c_float),
                 ("tau", ctypes.c_float), ("g_std", ctypes.c_float), ("flame_thresh", ctypes.c_float),
@@ -82,6 +97,15 @@ SIGNATURES = {
     "fr_reconstruct": (_S, [_P, _P, _P, _P, _I, _P, _I, _P, _I, _I, _P, _P, _I]),
     "fr_count_samples": (_S, [_P, _P, _P, _I, _P, _P, _P]),
     "fr_reconstruct_batch": (_S, [_P, _P, _I, _I, _I, _P, _I]),
+    "fr_server_create": (_S, [_P, _P, _I, ctypes.c_size_t, _P]),
+    "fr_server_destroy": (_S, [_P]),
+    "fr_server_submit": (_S, [_P, _P, _P]),
+    "fr_server_step": (_S, [_P, _P, _P]),
+    "fr_job_get_info": (_S, [_P, _P]),
+    "fr_job_wait": (_S, [_P, _P, _I]),
+    "fr_job_cancel": (_S, [_P, _P]),
+    "fr_job_release": (_S, [_P, _P]),
+    "fr_server_memory": (_S, [_P, _P, _P]),
     "fr_render_residual_noalloc": (_S, [_I, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, ctypes.c_char_p,
                                         ctypes.c_size_t]),
 }
@@ -271,3 +295,76 @@ class Context:
 
     def fr_synchronize(self):
         self.check(self.lib.fr_synchronize(self.h))
+
+
+class Job:
+    """A submitted job: keeps its host buffers alive until it is released."""
+
+    def __init__(self, server, handle, keep, result, rmse):
+        self.server, self.h, self._keep, self.result, self.rmse = server, handle, keep, result, rmse
+
+    def info(self) -> fr_job_info:
+        info = fr_job_info()
+        self.server.ctx.check(self.server.lib.fr_job_get_info(self.h, ctypes.byref(info)))
+        return info
+
+    def wait(self, timeout_ms=60000):
+        self.server.ctx.check(self.server.lib.fr_job_wait(self.server.h, self.h, int(timeout_ms)))
+
+    def cancel(self):
+        self.server.ctx.check(self.server.lib.fr_job_cancel(self.server.h, self.h))
+
+    def release(self):
+        if self.h:
+            self.server.ctx.check(self.server.lib.fr_job_release(self.server.h, self.h))
+            self.h = None
+
+
+class Server:
+    """fr_server: continuous-batching reconstruction jobs (see include/flamerec.h)."""
+
+    def __init__(self, ctx: Context, p: fr_params, dtype=FR_BF16, budget_bytes=0):
+        self.ctx, self.lib = ctx, ctx.lib
+        self.dtype = dtype
+        self._p = p
+        h = ctypes.c_void_p()
+        ctx.check(self.lib.fr_server_create(ctx.h, ctypes.byref(p), int(dtype), ctypes.c_size_t(budget_bytes),
+                                            ctypes.byref(h)))
+        self.h = h
+
+    def submit(self, shape, origin, h, cams, iters, init_records, targets, want_rmse=True) -> Job:
+        """init_records: host numpy array (nz, ny, nx, 4) in the server's storage type
+        (uint16 bit patterns for bf16/f16, float32 otherwise); targets: host float32
+        (K, H, W, 3).  Returns a Job whose .result receives the reconstruction."""
+        nx, ny, nz = shape
+        init = np.ascontiguousarray(init_records)
+        tgt = np.ascontiguousarray(targets, dtype=np.float32)
+        result = np.empty_like(init)
+        rmse = np.zeros((iters, 3), dtype=np.float32) if want_rmse else None
+        fcams = cameras(cams)
+        d = fr_job_desc()
+        d.nx, d.ny, d.nz = nx, ny, nz
+        d.origin = (ctypes.c_float * 3)(*[float(x) for x in origin])
+        d.h = float(h)
+        d.cams = ctypes.cast(fcams, ctypes.c_void_p)
+        d.ncam, d.iters = len(cams), int(iters)
+        d.init_records, d.targets, d.result_records = init.ctypes.data, tgt.ctypes.data, result.ctypes.data
+        d.rmse = rmse.ctypes.data if rmse is not None else None
+        jh = ctypes.c_void_p()
+        self.ctx.check(self.lib.fr_server_submit(self.h, ctypes.byref(d), ctypes.byref(jh)))
+        return Job(self, jh, (init, tgt, fcams), result, rmse)
+
+    def step(self):
+        running, queued = ctypes.c_int(), ctypes.c_int()
+        self.ctx.check(self.lib.fr_server_step(self.h, ctypes.byref(running), ctypes.byref(queued)))
+        return running.value, queued.value
+
+    def memory(self):
+        used, budget = ctypes.c_size_t(), ctypes.c_size_t()
+        self.ctx.check(self.lib.fr_server_memory(self.h, ctypes.byref(used), ctypes.byref(budget)))
+        return used.value, budget.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fr_server_destroy(self.h)
+            self.h = None
