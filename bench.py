@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the video-batch and serving sections")
+    ap.add_argument("--serving-jobs", type=int, default=40)
     ap.add_argument("--profile", action="store_true",
                     help="one untimed iteration plus one forward and one adjustment launch, for ncu")
     return ap.parse_args()
@@ -105,6 +107,14 @@ class Clocks:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def alpha_for(n, views, side, step):
+    """Paper-rule residual scale giving the same per-iteration gain across
+    geometries: the adjustment gain grows with views x (pixels per voxel)^2 /
+    step x (chord length in voxels), so alpha_l ~ n step / (views side^2),
+    anchored at 2e-4 for 128^3, 8 views of 512^2, step 0.5."""
+    return 2e-4 * (n / 128.0) * (step / 0.5) * (8.0 / views) * (512.0 / side) ** 2
 
 
 def make_inputs(storage, rank, local):
@@ -283,6 +293,133 @@ def run_ours(args, ws, rank, local):
     return out
 
 
+def run_video(fr, ctx, frames=64, n=96, views=8, side=384, iters=20, step=0.5, seed=4, storage="f32"):
+    """Batched video frames: every frame reconstructed from its own targets,
+    all frames in one batched launch per phase, the 20 iterations captured in
+    one CUDA graph."""
+    import torch
+    from paper_1809_06417_gb300 import synth
+    dt = torch.float32 if storage == "f32" else torch.bfloat16
+    shape, origin, h = synth.unit_grid(n)
+    cams = synth.ring_cameras(views, side, side, elevation_jitter_deg=10.0, seed=seed)
+    fcams = fr.cameras(cams)
+    gts = synth.video_frames(frames, n, seed)
+    p = fr.params(step=step, alpha_l=alpha_for(n, views, side, step))
+    probs, vols, n_fwd, n_adj = [], [], 0, 0
+    for f, gt in enumerate(gts):
+        g = torch.as_tensor(gt, dtype=torch.float32, device="cuda").to(dt).contiguous()
+        img = torch.empty((views, side, side, 3), device="cuda")
+        ctx.fr_render(fr.volume(g, origin, h), fcams, fr.params(step=step), img)
+        img /= img.max()
+        bbox = torch.zeros((views, 4), dtype=torch.int32, device="cuda")
+        ctx.fr_prepare_targets(img, 30 / 255, bbox)
+        v = g.clone()
+        v[..., :3] = 0
+        fv = fr.volume(v, origin, h)
+        n_fwd += ctx.fr_count_samples(fv, fcams, p)
+        n_adj += ctx.fr_count_samples(fv, fcams, p, residual=img)
+        rm = torch.zeros((iters, 3), device="cuda")
+        vols.append((v, img, bbox, rm))
+        probs.append((fv, fcams, img, bbox, rm))
+    ctx.fr_reconstruct_batch(probs, 1, p, use_graph=False)  # warm-up (builds scratch)
+    torch.cuda.synchronize()
+    for v, *_ in vols:
+        v[..., :3] = 0
+    flush = torch.empty(384 * 2 ** 20 // 4, device="cuda")
+    flush.fill_(1.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    ctx.fr_reconstruct_batch(probs, iters, p, use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    final = np.stack([rm[-1].cpu().numpy() for *_, rm in vols])
+    return {"workload": f"video_{frames}x{n}^3_{views}x{side}^2", "frames": frames, "iters_per_frame": iters,
+            "seconds": t, "frames_per_s": frames / t, "samples_per_s": (n_fwd + n_adj) * iters / t,
+            "samples_per_iteration": {"fwd": n_fwd, "adj": n_adj}, "graph": True, "storage": storage,
+            "final_rmse_mean": [float(x) for x in final.mean(axis=0)], "launches_per_iteration": 4}
+
+
+def run_serving(fr, ctx, jobs=40, rate=20.0, seed=5, step=0.5):
+    """Serving stream: seeded Poisson arrivals at `rate` jobs/s, mixed grids,
+    views, image sizes and iteration counts, bf16 volumes, through the
+    continuous-batching server (p50 / p99 latency, jobs/s).  The same jobs are
+    then run offline twice to compare throughput at matched error: all at once
+    through the server (bf16) and one after another through fr_reconstruct
+    (float32, the plain single-job path)."""
+    import torch
+    from paper_1809_06417_gb300 import serving, synth
+    stream = synth.serving_stream(jobs, seed=seed, rate=rate)
+    plumes = {}
+    specs = []
+    for js in stream:
+        n, K, side = js["n"], js["views"], js["side"]
+        if n not in plumes:
+            plumes[n] = synth.plume_volume(n, seed + n)[0]
+        gt = plumes[n]
+        shape, origin, h = synth.unit_grid(n)
+        cams = synth.ring_cameras(K, side, side, elevation_jitter_deg=10.0, seed=js["seed"], phase=0.1 * js["id"])
+        g = torch.as_tensor(gt, dtype=torch.float32, device="cuda").contiguous()
+        img = torch.empty((K, side, side, 3), device="cuda")
+        ctx.fr_render(fr.volume(g, origin, h), fr.cameras(cams), fr.params(step=step), img)
+        img /= img.max()
+        init = gt.copy()
+        init[..., :3] = 0.0
+        specs.append(dict(js=js, shape=shape, origin=origin, h=h, cams=cams, targets=img.cpu().numpy(),
+                          init32=init.astype(np.float32),
+                          init16=torch.as_tensor(init, dtype=torch.float32).to(torch.bfloat16)
+                          .view(torch.int16).numpy().view(np.uint16).copy(),
+                          alpha=alpha_for(n, K, side, step)))
+    p = fr.params(step=step, alpha_l=2e-4)
+
+    def submitter(sp):
+        return lambda srv: srv.submit(sp["shape"], sp["origin"], sp["h"], sp["cams"], sp["js"]["iters"],
+                                      sp["init16"], sp["targets"], alpha_l=sp["alpha"])
+
+    # online: Poisson arrivals, continuous batching
+    srv = fr.Server(ctx, p, dtype=fr.FR_BF16)
+    warm = srv.submit(specs[0]["shape"], specs[0]["origin"], specs[0]["h"], specs[0]["cams"], 2,
+                      specs[0]["init16"], specs[0]["targets"], alpha_l=specs[0]["alpha"])
+    warm.wait()
+    reqs = [serving.Request(arrival=sp["js"]["arrival"] - stream[0]["arrival"], submit=submitter(sp)) for sp in specs]
+    res = serving.run_requests(srv, reqs)
+    online_rmse = np.mean([r.job.rmse[-1, 1] for r in reqs])
+    srv.close()
+    # offline: all jobs at once through the server (bf16)
+    srv = fr.Server(ctx, p, dtype=fr.FR_BF16)
+    t0 = time.perf_counter()
+    handles = [submitter(sp)(srv) for sp in specs]
+    for j in handles:
+        j.wait(timeout_ms=600000)
+    t_batched = time.perf_counter() - t0
+    rmse_batched = np.mean([j.rmse[-1, 1] for j in handles])
+    srv.close()
+    # offline: one job after another through fr_reconstruct (float32)
+    t0 = time.perf_counter()
+    rmse_single = []
+    for sp in specs:
+        K, side = len(sp["cams"]), sp["cams"][0]["width"]
+        v = torch.as_tensor(sp["init32"], device="cuda").contiguous()
+        t = torch.as_tensor(sp["targets"], device="cuda").contiguous()
+        bbox = torch.zeros((K, 4), dtype=torch.int32, device="cuda")
+        ctx.fr_prepare_targets(t, 30 / 255, bbox)
+        rm = np.zeros((sp["js"]["iters"], 3), dtype=np.float32)
+        ctx.fr_reconstruct(fr.volume(v, sp["origin"], sp["h"]), fr.cameras(sp["cams"]), t, bbox, sp["js"]["iters"],
+                           fr.params(step=step, alpha_l=sp["alpha"]), rmse=rm)
+        rmse_single.append(rm[-1, 1])
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    return {"workload": f"serving_poisson{rate:g}_jobs{jobs}", "jobs": jobs, "rate_jobs_per_s": rate,
+            "p50_latency_s": res.percentile(50), "p99_latency_s": res.percentile(99),
+            "jobs_per_s": jobs / res.wall, "max_resident": res.max_running, "steps": res.steps,
+            "online_final_rmse_green_mean": float(online_rmse),
+            "offline": {"batched_bf16_jobs_per_s": jobs / t_batched, "single_f32_jobs_per_s": jobs / t_single,
+                        "speedup": t_single / t_batched, "final_rmse_green_mean_batched": float(rmse_batched),
+                        "final_rmse_green_mean_single": float(np.mean(rmse_single))},
+            "storage": "bf16", "mix": "grids {64,96,128,192}^3, 4-12 views, side 256-768, 20-50 iterations"}
+
+
 class OracleSample:
     """The oracle on bounded samples of the workload: a band of image rows of
     one view, one iteration (in-scattering source, render of those pixels,
@@ -402,6 +539,12 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()  # before any GPU work: the oracle never forks after CUDA init
     out = run_ours(args, ws, rank, local)
+    if rank == 0 and not args.no_extras:
+        from paper_1809_06417_gb300 import flamerec as fr
+        ctx = fr.Context(local)
+        out["video"] = run_video(fr, ctx, storage=args.storage)
+        out["serving"] = run_serving(fr, ctx, jobs=args.serving_jobs)
+        ctx.close()
     if rank == 0:
         out["cpu_baseline"] = cpu
         print(json.dumps(out))

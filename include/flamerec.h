@@ -253,7 +253,8 @@ typedef enum fr_job_state {
 
 /* A job.  Host buffers must stay valid until the job is done or cancelled. */
 typedef struct fr_job_desc {
-    int32_t nx, ny, nz, pad_;
+    int32_t nx, ny, nz;
+    float alpha_l;              /* Eq. 10 residual scale of this job; 0 = the server's */
     float origin[3];
     float h;
     const fr_camera *cams;      /* host, ncam cameras sharing one image size (copied) */

@@ -242,6 +242,7 @@ extern "C" fr_status fr_server_submit(fr_server* s, const fr_job_desc* d, fr_job
     FR_TRY(check_cams(c, d->cams, d->ncam));
     FR_TRY(check_params(c, &s->p, &v, d->cams));
     if (d->iters < 1 || d->iters > (1 << 20)) return fail(c, FR_EINVAL, "iters must be in [1, 2^20]");
+    if (!std::isfinite(d->alpha_l)) return fail(c, FR_EINVAL, "alpha_l must be finite");
     if (!d->init_records || !d->targets || !d->result_records) return fail(c, FR_EINVAL, "NULL host buffer");
     const long long npix = (long long)d->ncam * d->cams[0].width * d->cams[0].height;
     if (npix >= (1LL << 32)) return fail(c, FR_EINVAL, "at most 2^32 pixels per job");
@@ -348,6 +349,7 @@ extern "C" fr_status fr_server_step(fr_server* s, int* running, int* queued)
             P.ntiles = j->ntiles;
             P.iteration = j->iters_done;
             P.sq_slot = j->iters_done;
+            if (j->d.alpha_l != 0.0f) P.alpha_l = j->d.alpha_l;
             hp[i] = P;
             for (int k = 0; k < j->d.ncam; ++k) hc[cam_off + k] = a.cams[k];
             ht[i] = tile_off;

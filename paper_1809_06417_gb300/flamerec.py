@@ -49,7 +49,7 @@ class fr_problem(ctypes.Structure):
 
 
 class fr_job_desc(ctypes.Structure):
-    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("pad_", ctypes.c_int32),
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("alpha_l", ctypes.c_float),
                 ("origin", ctypes.c_float * 3), ("h", ctypes.c_float), ("cams", ctypes.c_void_p),
                 ("ncam", ctypes.c_int32), ("iters", ctypes.c_int32), ("init_records", ctypes.c_void_p),
                 ("targets", ctypes.c_void_p), ("result_records", ctypes.c_void_p), ("rmse", ctypes.c_void_p)]
@@ -332,7 +332,7 @@ class Server:
                                             ctypes.byref(h)))
         self.h = h
 
-    def submit(self, shape, origin, h, cams, iters, init_records, targets, want_rmse=True) -> Job:
+    def submit(self, shape, origin, h, cams, iters, init_records, targets, want_rmse=True, alpha_l=0.0) -> Job:
         """init_records: host numpy array (nz, ny, nx, 4) in the server's storage type
         (uint16 bit patterns for bf16/f16, float32 otherwise); targets: host float32
         (K, H, W, 3).  Returns a Job whose .result receives the reconstruction."""
@@ -344,6 +344,7 @@ class Server:
         fcams = cameras(cams)
         d = fr_job_desc()
         d.nx, d.ny, d.nz = nx, ny, nz
+        d.alpha_l = float(alpha_l)
         d.origin = (ctypes.c_float * 3)(*[float(x) for x in origin])
         d.h = float(h)
         d.cams = ctypes.cast(fcams, ctypes.c_void_p)

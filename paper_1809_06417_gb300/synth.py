@@ -173,13 +173,26 @@ def temperature_volume(n: int, seed: int, t_min: float = 800.0, t_max: float = 2
     return vol
 
 
-def video_frames(frames: int, n: int, seed: int):
-    """Batched video case: one plume advected +1 voxel in y per frame plus
-    per-frame noise.  Returns a list of (records, albedo)."""
+def video_frames(frames: int, n: int, seed: int, sigma_peak: float = SIGMA_PAPER,
+                 colour=(1.0, 0.55, 0.15)):
+    """Batched video case: one plume advected +1 voxel in y per frame (its blobs
+    and its noise texture move together) plus a per-frame noise factor.
+    Returns a list of (n,n,n,4) records {q_r, q_g, q_b, sigma}."""
+    rng = np.random.default_rng(seed)
+    base_noise = value_noise(n, rng)
     out = []
     for f in range(frames):
-        vol, alb = plume_volume(n, seed * 1000 + f, shift_y=float(f) - 0.5 * frames * 0.0)
-        out.append((vol, alb))
+        frng = np.random.default_rng(seed * 100003 + f)
+        prof = plume_profile(n, np.random.default_rng(seed), shift_y=float(f) - 0.25 * frames)
+        noise = np.roll(base_noise, f, axis=1)
+        flicker = 1.0 + 0.1 * (value_noise(n, frng, octaves=1, base_cells=3) - 0.5)
+        dens = prof * (0.6 + 0.4 * noise) * flicker
+        vol = np.zeros((n, n, n, 4))
+        vol[..., 3] = sigma_peak * dens / max(dens.max(), 1e-30)
+        heat = np.clip(dens * (1.0 + 0.5 * (noise - 0.5)), 0.0, None)
+        for ch in range(3):
+            vol[..., ch] = colour[ch] * heat
+        out.append(vol)
     return out
 
 
