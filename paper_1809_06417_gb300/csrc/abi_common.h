@@ -31,6 +31,7 @@ struct fr_ctx {
     char err[512] = {0};             // last failure message
     Buf partials, counter, residual, rendered, dV, targets, sqerr, rmse, J, src, flame_off, flame_list;
     Buf batch;                       // batched reconstruction scratch and tables
+    Buf pairs;                       // x-pair records for the forward march
     unsigned long long* host_counter = nullptr;
     void* staging = nullptr;         // pinned host staging of batch tables
     size_t staging_bytes = 0;
@@ -122,7 +123,7 @@ inline fr_status check_volume(fr_ctx* c, const fr_volume* v, const char* name)
     if (!v) return fail(c, FR_EINVAL, "%s is NULL", name);
     if (v->nx < 2 || v->ny < 2 || v->nz < 2 || v->nx > 8192 || v->ny > 8192 || v->nz > 8192)
         return fail(c, FR_EINVAL, "%s: extents must be in [2, 8192], got %d x %d x %d", name, v->nx, v->ny, v->nz);
-    if (node_count(v) > (1LL << 34)) return fail(c, FR_EINVAL, "%s: too many nodes", name);
+    if (node_count(v) >= (1LL << 31)) return fail(c, FR_EINVAL, "%s: at most 2^31 - 1 nodes", name);
     if (v->kind != FR_KIND_RGB && v->kind != FR_KIND_TEMP) return fail(c, FR_EINVAL, "%s: bad kind %d", name, v->kind);
     if (v->dtype != FR_F32 && v->dtype != FR_BF16 && v->dtype != FR_F16)
         return fail(c, FR_EINVAL, "%s: bad dtype %d", name, v->dtype);

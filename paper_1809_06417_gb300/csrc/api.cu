@@ -61,7 +61,7 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
-                   &c->rmse, &c->J, &c->src, &c->flame_off, &c->flame_list, &c->batch})
+                   &c->rmse, &c->J, &c->src, &c->flame_off, &c->flame_list, &c->batch, &c->pairs})
         if (b->p) cudaFree(b->p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
     if (c->staging) cudaFreeHost(c->staging);
@@ -91,6 +91,15 @@ extern "C" fr_status fr_synchronize(fr_ctx* c)
 // Single calls
 // ---------------------------------------------------------------------------
 
+// x-pair copy of the records the forward march will read (library scratch).
+static fr_status attach_pairs(fr_ctx* c, const fr_volume* vol, const void* records, SingleArgs& a)
+{
+    FR_TRY(ensure(c, c->pairs, (size_t)node_count(vol) * 2 * rec_bytes(vol), "pairs"));
+    FR_CUDA(c, launch_pair_pack(records, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, c->stream));
+    a.p.pairs = c->pairs.p;
+    return FR_OK;
+}
+
 extern "C" fr_status fr_prepare_targets(fr_ctx* c, int ncam, int height, int width, float* targets,
                                         float thresh, int32_t* bbox)
 {
@@ -115,6 +124,7 @@ extern "C" fr_status fr_render(fr_ctx* c, const fr_volume* vol, const fr_camera*
     static thread_local SingleArgs a;
     fill_problem(vol, cams, ncam, p, a);
     a.p.rendered = out_rgb;
+    FR_TRY(attach_pairs(c, vol, vol->data, a));
     int nt = tiles_of(a.p.W, a.p.H, ncam);
     FR_CUDA(c, launch_fwd(a, vol->dtype, vol->kind, nt, c->stream));
     return FR_OK;
@@ -143,6 +153,7 @@ extern "C" fr_status fr_render_residual(fr_ctx* c, const fr_volume* vol, const f
     a.p.rendered = rendered;
     a.p.residual = residual;
     a.p.partials = static_cast<float*>(c->partials.p);
+    FR_TRY(attach_pairs(c, vol, vol->data, a));
     FR_CUDA(c, launch_fwd(a, vol->dtype, vol->kind, nt, c->stream));
     FR_CUDA(c, launch_finalize(a.p.partials, nt, sq_err, c->stream));
     return FR_OK;
@@ -308,6 +319,7 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
     if (npix >= (1LL << 32)) return fail(c, FR_EINVAL, "at most 2^32 pixels per reconstruction");
     FR_TRY(ensure(c, c->flame_off, flame_list_buf_entries(nt) * sizeof(unsigned), "flame offsets"));
     FR_TRY(ensure(c, c->flame_list, (size_t)npix * sizeof(unsigned), "flame list"));
+    FR_TRY(ensure(c, c->pairs, (size_t)nodes * 2 * rec_bytes(vol), "pairs"));
     cudaStream_t s = c->stream;
     const float* tg = targets;
     if (targets_are_host) {
@@ -325,7 +337,9 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
     f.p.residual = static_cast<float*>(c->residual.p);
     f.p.partials = static_cast<float*>(c->partials.p);
     f.p.rendered = p->rule == FR_RULE_GRADIENT ? static_cast<float*>(c->rendered.p) : nullptr;
+    f.p.pairs = c->pairs.p;
     u = f;
+    u.p.pairs = nullptr;
     u.p.targets = nullptr;
     u.p.partials = nullptr;
     u.p.residual = nullptr;
@@ -342,6 +356,7 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
         if (albedo)
             FR_CUDA(c, launch_scatter_source(vol->data, vol->dtype, albedo, static_cast<float*>(c->J.p), c->src.p,
                                              vol->dtype, vol->nx, vol->ny, vol->nz, s));
+        FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, s));
         FR_CUDA(c, launch_fwd(f, vol->dtype, vol->kind, nt, s));
         FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * it, s));
         if (p->rule == FR_RULE_PAPER) {

@@ -65,6 +65,9 @@ struct ProbDev {
     float* sqerr;                // 4 floats per iteration
     int ntiles;
     int sq_slot;                 // error slot of the launch's first iteration
+    // x-pair records: pair i = {record i, record of its +x neighbour}; when
+    // set, the forward march gathers a cell's corners two at a time from it
+    const void* pairs;
 };
 
 // ---------------------------------------------------------------------------
@@ -129,13 +132,14 @@ __device__ __forceinline__ void segment(const Ray& R, float step, int k, float& 
     z = fmaf(tm, R.dz, R.p0z);
 }
 
-// Cell index clamped to [0, n-2] and the fraction inside it, in [0, 1].
+// Cell index clamped to [0, n-2] and the fraction inside it.  Sample points
+// lie on the clipped chord, so the fraction is in [0, 1] up to rounding; the
+// clamp keeps every index inside the volume whatever the input.
 __device__ __forceinline__ void locate(float p, int n, int& i, float& f)
 {
-    int ii = (int)floorf(p);
-    ii = min(max(ii, 0), n - 2);
+    const int ii = min(max(__float2int_rd(p), 0), n - 2);
     i = ii;
-    f = fminf(fmaxf(p - (float)ii, 0.0f), 1.0f);
+    f = p - (float)ii;
 }
 
 struct Cell {
@@ -180,20 +184,26 @@ __device__ __forceinline__ CellIJK cell_ijk(float x, float y, float z, int nx, i
 // odd (mirror_frac).
 struct Win {
     int ci, cj, ck;
-    long long base;          // node index of (ci, cj, ck)
+    int base;                // node index of (ci, cj, ck); volumes hold < 2^31 nodes
+    int o0[3], o1[3];        // node offset of slot bit value 0 / 1 along x, y, z
     bool live;
 };
 
-__device__ __forceinline__ long long slot_node(const Win& W, int t, int nx, long long nxy)
+__device__ __forceinline__ int slot_node(const Win& W, int t)
 {
-    const int dx = (t & 1) ^ (W.ci & 1), dy = ((t >> 1) & 1) ^ (W.cj & 1), dz = (t >> 2) ^ (W.ck & 1);
-    return W.base + dx + (long long)(dy * nx) + (dz ? nxy : 0LL);
+    return W.base + ((t & 1) ? W.o1[0] : W.o0[0]) + (((t >> 1) & 1) ? W.o1[1] : W.o0[1]) +
+           ((t >> 2) ? W.o1[2] : W.o0[2]);
 }
 
-__device__ __forceinline__ void win_set(Win& W, int i, int j, int k, int nx, int ny)
+__device__ __forceinline__ void win_set(Win& W, int i, int j, int k, int nx, int ny, int nxy)
 {
     W.ci = i; W.cj = j; W.ck = k;
-    W.base = ((long long)k * ny + j) * nx + i;
+    W.base = (k * ny + j) * nx + i;
+    // slot bit value v along an axis names node c + (v ^ (c & 1))
+    const int px = i & 1, py = j & 1, pz = k & 1;
+    W.o0[0] = px;            W.o1[0] = 1 - px;
+    W.o0[1] = py ? nx : 0;   W.o1[1] = py ? 0 : nx;
+    W.o0[2] = pz ? nxy : 0;  W.o1[2] = pz ? 0 : nxy;
     W.live = true;
 }
 
@@ -202,18 +212,17 @@ __device__ __forceinline__ void win_set(Win& W, int i, int j, int k, int nx, int
 // enter(t, node) for the same slots (with the new node); on the first call
 // every slot enters.
 template <class Leave, class Enter>
-__device__ __forceinline__ void win_move(Win& W, int i, int j, int k, int nx, int ny, long long nxy,
+__device__ __forceinline__ void win_move(Win& W, int i, int j, int k, int nx, int ny, int nxy,
                                          Leave&& leave, Enter&& enter)
 {
     if (!W.live) {
-        win_set(W, i, j, k, nx, ny);
+        win_set(W, i, j, k, nx, ny, nxy);
 #pragma unroll
-        for (int t = 0; t < 8; ++t) enter(t, slot_node(W, t, nx, nxy));
+        for (int t = 0; t < 8; ++t) enter(t, slot_node(W, t));
         return;
     }
     if (i == W.ci && j == W.cj && k == W.ck) return;
-    // slot bit value v along an axis names the node c_old + (v ^ (c_old & 1));
-    // it stays iff that node is c_new or c_new + 1
+    // the key point of slot bit v stays iff c_old + (v ^ p_old) is c_new or c_new + 1
     const int dx = W.ci - i, dy = W.cj - j, dz = W.ck - k;
     const int px = W.ci & 1, py = W.cj & 1, pz = W.ck & 1;
     const bool sx[2] = {(unsigned)(dx + px) <= 1u, (unsigned)(dx + 1 - px) <= 1u};
@@ -223,20 +232,20 @@ __device__ __forceinline__ void win_move(Win& W, int i, int j, int k, int nx, in
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         go[t] = !(sx[t & 1] && sy[(t >> 1) & 1] && sz[t >> 2]);
-        if (go[t]) leave(t, slot_node(W, t, nx, nxy));
+        if (go[t]) leave(t, slot_node(W, t));
     }
-    win_set(W, i, j, k, nx, ny);
+    win_set(W, i, j, k, nx, ny, nxy);
 #pragma unroll
     for (int t = 0; t < 8; ++t)
-        if (go[t]) enter(t, slot_node(W, t, nx, nxy));
+        if (go[t]) enter(t, slot_node(W, t));
 }
 
 template <class Leave>
-__device__ __forceinline__ void win_release(const Win& W, int nx, long long nxy, Leave&& leave)
+__device__ __forceinline__ void win_release(const Win& W, Leave&& leave)
 {
     if (!W.live) return;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) leave(t, slot_node(W, t, nx, nxy));
+    for (int t = 0; t < 8; ++t) leave(t, slot_node(W, t));
 }
 
 // Fraction toward the odd-parity key point along one axis.
@@ -336,6 +345,47 @@ __device__ __forceinline__ void store_ts(void* vol, long long idx, float2 v)
         reinterpret_cast<__nv_bfloat162*>(vol)[idx] = a;
     } else {
         reinterpret_cast<__half2*>(vol)[idx] = __floats2half2_rn(v.x, v.y);
+    }
+}
+
+// x-pair records (record i and its +x neighbour, adjacent in memory).
+template <int DT>
+__device__ __forceinline__ void load_rgb_pair(const void* pairs, long long idx, float4& a, float4& b)
+{
+    if constexpr (DT == DT_F32) {
+        const float* p = reinterpret_cast<const float*>(pairs) + 8 * idx;
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+            : "l"(p));
+    } else {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(pairs) + idx);
+        if constexpr (DT == DT_BF16) {
+            a = make_float4(bf16_lo(u.x), bf16_hi(u.x), bf16_lo(u.y), bf16_hi(u.y));
+            b = make_float4(bf16_lo(u.z), bf16_hi(u.z), bf16_lo(u.w), bf16_hi(u.w));
+        } else {
+            const float2 a0 = f16x2(u.x), a1 = f16x2(u.y), b0 = f16x2(u.z), b1 = f16x2(u.w);
+            a = make_float4(a0.x, a0.y, a1.x, a1.y);
+            b = make_float4(b0.x, b0.y, b1.x, b1.y);
+        }
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void load_ts_pair(const void* pairs, long long idx, float2& a, float2& b)
+{
+    if constexpr (DT == DT_F32) {
+        const float4 f = __ldg(reinterpret_cast<const float4*>(pairs) + idx);
+        a = make_float2(f.x, f.y);
+        b = make_float2(f.z, f.w);
+    } else {
+        const uint2 u = __ldg(reinterpret_cast<const uint2*>(pairs) + idx);
+        if constexpr (DT == DT_BF16) {
+            a = make_float2(bf16_lo(u.x), bf16_hi(u.x));
+            b = make_float2(bf16_lo(u.y), bf16_hi(u.y));
+        } else {
+            a = f16x2(u.x);
+            b = f16x2(u.y);
+        }
     }
 }
 

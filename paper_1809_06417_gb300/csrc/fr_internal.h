@@ -55,5 +55,7 @@ cudaError_t launch_prepare_targets(float* targets, int ncam, int H, int W, float
                                    cudaStream_t s);
 cudaError_t launch_rmse(const float* sq4, int n, float* rmse3, cudaStream_t s);
 cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t s);
+// x-pair records of a volume (2 records per node) for the forward march
+cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int nx, int ny, int nz, cudaStream_t s);
 
 }  // namespace frk

@@ -62,11 +62,19 @@ template <int DT>
 struct RecOf<DT, KIND_RGB> {
     using T = float4;
     static __device__ __forceinline__ float4 load(const void* vol, long long i) { return load_rgb<DT>(vol, i); }
+    static __device__ __forceinline__ void pair(const void* p, long long i, float4& a, float4& b)
+    {
+        load_rgb_pair<DT>(p, i, a, b);
+    }
 };
 template <int DT>
 struct RecOf<DT, KIND_TEMP> {
     using T = float2;
     static __device__ __forceinline__ float2 load(const void* vol, long long i) { return load_ts<DT>(vol, i); }
+    static __device__ __forceinline__ void pair(const void* p, long long i, float2& a, float2& b)
+    {
+        load_ts_pair<DT>(p, i, a, b);
+    }
 };
 
 // Source and extinction of a blended record (temperature through the table).
@@ -102,12 +110,24 @@ __device__ __forceinline__ void load8(const void* vol, long long base, int nx, l
     v[7] = Rec::load(vol, base + nxy + nx + 1);
 }
 
+// The same from x-pair records: corners (0, dy, dz) and (1, dy, dz) in one load.
+template <int DT, int KIND>
+__device__ __forceinline__ void load8_pairs(const void* pairs, long long base, int nx, long long nxy,
+                                            typename RecOf<DT, KIND>::T v[8])
+{
+    using Rec = RecOf<DT, KIND>;
+    Rec::pair(pairs, base, v[0], v[1]);
+    Rec::pair(pairs, base + nx, v[2], v[3]);
+    Rec::pair(pairs, base + nxy, v[4], v[5]);
+    Rec::pair(pairs, base + nxy + nx, v[6], v[7]);
+}
+
 // Forward march of one ray.  Consecutive samples often share a cell (at half a
 // voxel step about 2 in 5 do), so the cell's eight records stay in registers
 // and are reloaded only when the sample enters another cell.  (Reloading just
 // the four records of a crossed face costs more instructions than the L1
 // traffic it saves.)
-template <int DT, int KIND, bool TAU>
+template <int DT, int KIND, bool TAU, bool PAIRS>
 __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, int tile)
 {
     using RT = typename RecOf<DT, KIND>::T;
@@ -128,7 +148,8 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
                 const Cell c = cell_of(x, y, z, P.nx, P.ny, P.nz);
                 if (c.base != vbase) {
                     vbase = c.base;
-                    load8<DT, KIND>(P.vol, c.base, P.nx, nxy, v);
+                    if constexpr (PAIRS) load8_pairs<DT, KIND>(P.pairs, c.base, P.nx, nxy, v);
+                    else load8<DT, KIND>(P.vol, c.base, P.nx, nxy, v);
                 }
                 const RT r = slot_blend<RT>(v, c.fx, c.fy, c.fz);
                 float S[3], sig, dq[3];
@@ -185,10 +206,10 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
     }
 }
 
-template <int DT, int KIND, bool TAU>
+template <int DT, int KIND, bool TAU, bool PAIRS>
 __global__ void FR_MARCH_BOUNDS fwd_single(const __grid_constant__ SingleArgs a)
 {
-    fwd_body<DT, KIND, TAU>(a.p, a.cams, blockIdx.x);
+    fwd_body<DT, KIND, TAU, PAIRS>(a.p, a.cams, blockIdx.x);
 }
 
 template <int DT, int KIND, bool TAU>
@@ -198,7 +219,7 @@ __global__ void FR_MARCH_BOUNDS fwd_batch(const ProbDev* __restrict__ probs,
 {
     const int p = find_problem(tile_start, nprob, blockIdx.x);
     const ProbDev& P = probs[p];
-    fwd_body<DT, KIND, TAU>(P, P.cams, blockIdx.x - __ldg(tile_start + p));
+    fwd_body<DT, KIND, TAU, false>(P, P.cams, blockIdx.x - __ldg(tile_start + p));
 }
 
 // ---------------------------------------------------------------------------
@@ -219,19 +240,20 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
     Ray R;
     if (!make_ray(cams[view], px, py, P.nx, P.ny, P.nz, P.step, R)) return;
     const long long nxy = (long long)P.nx * P.ny;
+    const int nxy32 = P.nx * P.ny;
     const int pixel = py * P.W + px;
     float acc[8], sg[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) { acc[t] = 0.0f; sg[t] = 0.0f; }
     float* dV = P.dV;
     const void* vol = P.vol;
-    auto leave = [&acc, dV, dl0, dl1, dl2](int t, long long node) {
+    auto leave = [&acc, dV, dl0, dl1, dl2](int t, int node) {
         const float w = acc[t];
-        if (w != 0.0f) red_add_v4(dV + 4 * node, w * dl0, w * dl1, w * dl2, 0.0f);
+        if (w != 0.0f) red_add_v4(dV + 4 * (unsigned)node, w * dl0, w * dl1, w * dl2, 0.0f);
         acc[t] = 0.0f;
     };
-    auto enter = [&sg, vol](int t, long long node) {
-        if constexpr (!TAU) sg[t] = load_rgb_sigma<DT>(vol, node);
+    auto enter = [&sg, vol](int t, int node) {
+        if constexpr (!TAU) sg[t] = load_rgb_sigma<DT>(vol, (unsigned)node);
     };
     Win W;
     W.live = false;
@@ -240,7 +262,7 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
         float len, x, y, z;
         segment(R, P.step, k, len, x, y, z);
         const CellIJK c = cell_ijk(x, y, z, P.nx, P.ny, P.nz);
-        win_move(W, c.i, c.j, c.k, P.nx, P.ny, nxy, leave, enter);
+        win_move(W, c.i, c.j, c.k, P.nx, P.ny, nxy32, leave, enter);
         const float gx = mirror_frac(c.i, c.fx), gy = mirror_frac(c.j, c.fy), gz = mirror_frac(c.k, c.fz);
         const float G = P.g_std > 0.0f ? g_draw(P.seed, P.g_std, iteration, view, pixel, k) : 1.0f;
         const float base = G * P.alpha_l * T;
@@ -253,7 +275,8 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
         if constexpr (TAU) T *= 1.0f - P.tau;
         else T *= __expf(-slot_blend<float>(sg, gx, gy, gz) * len);
     }
-    win_release(W, P.nx, nxy, leave);
+    (void)nxy;
+    win_release(W, leave);
 }
 
 template <int DT, bool TAU>
@@ -341,11 +364,11 @@ __device__ __forceinline__ void bwd_body(const ProbDev& P, const CamDev* cams, i
     for (int t = 0; t < 8; ++t) acc[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float* dV = P.dV;
     const void* vol = P.vol;
-    auto leave = [&acc, dV](int t, long long node) {
+    auto leave = [&acc, dV](int t, int node) {
         const float4 a = acc[t];
         if (a.x != 0.0f || a.y != 0.0f || a.z != 0.0f || a.w != 0.0f) {
-            if constexpr (KIND == KIND_RGB) red_add_v4(dV + 4 * node, a.x, a.y, a.z, a.w);
-            else red_add_v2(dV + 2 * node, a.x, a.y);
+            if constexpr (KIND == KIND_RGB) red_add_v4(dV + 4 * (unsigned)node, a.x, a.y, a.z, a.w);
+            else red_add_v2(dV + 2 * (unsigned)node, a.x, a.y);
         }
         acc[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     };
@@ -356,10 +379,10 @@ __device__ __forceinline__ void bwd_body(const ProbDev& P, const CamDev* cams, i
         float len, x, y, z;
         segment(R, P.step, k, len, x, y, z);
         const CellIJK ci = cell_ijk(x, y, z, P.nx, P.ny, P.nz);
-        win_move(W, ci.i, ci.j, ci.k, P.nx, P.ny, nxy, leave, [](int, long long) {});
+        win_move(W, ci.i, ci.j, ci.k, P.nx, P.ny, (int)nxy, leave, [](int, int) {});
         if (W.base != vbase) {
             vbase = W.base;
-            load8<DT, KIND>(vol, W.base, P.nx, nxy, v);
+            load8<DT, KIND>(vol, (long long)W.base, P.nx, nxy, v);
         }
         const RT r = slot_blend<RT>(v, ci.fx, ci.fy, ci.fz);
         const float gx = mirror_frac(ci.i, ci.fx), gy = mirror_frac(ci.j, ci.fy), gz = mirror_frac(ci.k, ci.fz);
@@ -397,7 +420,7 @@ __device__ __forceinline__ void bwd_body(const ProbDev& P, const CamDev* cams, i
             acc[t].w = fmaf(w, gv.w, acc[t].w);
         }
     }
-    win_release(W, P.nx, nxy, leave);
+    win_release(W, leave);
 }
 
 template <int DT, int KIND, bool TAU>
@@ -591,16 +614,19 @@ __global__ void __launch_bounds__(1024) finalize_batch(const ProbDev* __restrict
 cudaError_t launch_fwd(const SingleArgs& a, int dt, int kind, int ntiles, cudaStream_t s)
 {
     const bool tau = a.p.tau > 0.0f;
+    const bool pairs = a.p.pairs != nullptr;
     dim3 grid(ntiles), block(kTileThreads);
+#define FR_FWD(D, K, T)                                                            \
+    if (pairs) fwd_single<D, K, T, true><<<grid, block, 0, s>>>(a);                \
+    else fwd_single<D, K, T, false><<<grid, block, 0, s>>>(a)
     FR_DISPATCH_DT(dt, D, {
         if (kind == KIND_RGB) {
-            if (tau) fwd_single<D, KIND_RGB, true><<<grid, block, 0, s>>>(a);
-            else fwd_single<D, KIND_RGB, false><<<grid, block, 0, s>>>(a);
+            if (tau) { FR_FWD(D, KIND_RGB, true); } else { FR_FWD(D, KIND_RGB, false); }
         } else {
-            if (tau) fwd_single<D, KIND_TEMP, true><<<grid, block, 0, s>>>(a);
-            else fwd_single<D, KIND_TEMP, false><<<grid, block, 0, s>>>(a);
+            if (tau) { FR_FWD(D, KIND_TEMP, true); } else { FR_FWD(D, KIND_TEMP, false); }
         }
     });
+#undef FR_FWD
     return cudaGetLastError();
 }
 

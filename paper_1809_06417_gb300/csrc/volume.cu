@@ -119,6 +119,58 @@ cudaError_t launch_rmse_batch(const ProbDev* probs, int nprob, int iters, float*
     return cudaGetLastError();
 }
 
+// x-pair records: pair i = {record i, record i + 1}, the second copy of the
+// last node of a row repeating it (no cell uses it).  One CTA per row.
+template <int DT, int KIND>
+__global__ void __launch_bounds__(256) pair_pack_kernel(const void* src, void* dst, long long rows, int nx)
+{
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const long long r0 = row * nx;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const long long i = r0 + x, j = x < nx - 1 ? i + 1 : i;
+            if constexpr (KIND == KIND_RGB) {
+                if constexpr (DT == DT_F32) {
+                    const float4* s4 = reinterpret_cast<const float4*>(src);
+                    float4* d4 = reinterpret_cast<float4*>(dst);
+                    d4[2 * i] = __ldg(s4 + i);
+                    d4[2 * i + 1] = __ldg(s4 + j);
+                } else {
+                    const uint2* s2 = reinterpret_cast<const uint2*>(src);
+                    const uint2 a = __ldg(s2 + i), b = __ldg(s2 + j);
+                    reinterpret_cast<uint4*>(dst)[i] = make_uint4(a.x, a.y, b.x, b.y);
+                }
+            } else {
+                if constexpr (DT == DT_F32) {
+                    const float2* s2 = reinterpret_cast<const float2*>(src);
+                    const float2 a = __ldg(s2 + i), b = __ldg(s2 + j);
+                    reinterpret_cast<float4*>(dst)[i] = make_float4(a.x, a.y, b.x, b.y);
+                } else {
+                    const unsigned* s1 = reinterpret_cast<const unsigned*>(src);
+                    reinterpret_cast<uint2*>(dst)[i] = make_uint2(__ldg(s1 + i), __ldg(s1 + j));
+                }
+            }
+        }
+    }
+}
+
+cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int nx, int ny, int nz, cudaStream_t s)
+{
+    const long long rows = (long long)ny * nz;
+    const int g = (int)(rows < 152LL * 32 ? rows : 152LL * 32);
+#define FR_PACK(D, K) pair_pack_kernel<D, K><<<g, 256, 0, s>>>(src, dst, rows, nx)
+    if (kind == KIND_RGB) {
+        if (dt == DT_F32) FR_PACK(DT_F32, KIND_RGB);
+        else if (dt == DT_BF16) FR_PACK(DT_BF16, KIND_RGB);
+        else FR_PACK(DT_F16, KIND_RGB);
+    } else {
+        if (dt == DT_F32) FR_PACK(DT_F32, KIND_TEMP);
+        else if (dt == DT_BF16) FR_PACK(DT_BF16, KIND_TEMP);
+        else FR_PACK(DT_F16, KIND_TEMP);
+    }
+#undef FR_PACK
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // In-scattering: J = (1/6) sum over the six axis directions of the emitted
 // radiance arriving along grid lines; each unit segment between adjacent nodes
