@@ -518,7 +518,7 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         const int nt = tiles_of(q.cams[0].width, q.cams[0].height, q.ncam);
         arena += align256(ib) + align256((size_t)node_count(&q.vol) * 16) + align256((size_t)nt * 16) +
                  align256((size_t)std::max(iters, 1) * 16) + align256(flame_list_buf_entries(nt) * 4) +
-                 align256((size_t)npix * 4);
+                 align256((size_t)npix * 4) + align256((size_t)node_count(&q.vol) * 2 * rec_bytes(&q.vol));
         tiles_total += nt;
         cams_total += (size_t)q.ncam;
     }
@@ -568,6 +568,7 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         float* sqerr = reinterpret_cast<float*>(dbase + off); off += align256((size_t)iters * 16);
         unsigned* fbuf = reinterpret_cast<unsigned*>(dbase + off); off += align256(flame_list_buf_entries(nt) * 4);
         unsigned* flist = reinterpret_cast<unsigned*>(dbase + off); off += align256((size_t)npix * 4);
+        void* pairs = dbase + off; off += align256((size_t)nodes * 2 * rec_bytes(&q.vol));
         ProbDev& P = a.p;
         P.cams = d_cams + cam_off;
         P.targets = q.targets;
@@ -585,6 +586,7 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         P.ntiles = nt;
         P.iteration = first_iteration;
         P.sq_slot = 0;
+        P.pairs = pairs;
         h_probs[i] = P;
         for (int v = 0; v < q.ncam; ++v) h_cams[cam_off + v] = a.cams[v];
         h_tiles[i] = tile_off;
@@ -601,7 +603,8 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
     auto iterate = [&](cudaStream_t st) -> cudaError_t {
         cudaError_t e = cudaSuccess;
         for (int it = 0; it < iters && e == cudaSuccess; ++it) {
-            e = launch_fwd_batch(d_probs, d_tiles, nprob, tile_off, dt, KIND_RGB, tau, st);
+            e = launch_pair_pack_batch(d_probs, nprob, dt, st);
+            if (e == cudaSuccess) e = launch_fwd_batch(d_probs, d_tiles, nprob, tile_off, dt, KIND_RGB, tau, true, st);
             if (e == cudaSuccess) e = launch_finalize_batch(d_probs, nprob, it, st);
             if (e == cudaSuccess)
                 e = launch_adjust_list_batch(d_probs, d_tiles, nprob, tile_off, dt, tau, it, st);

@@ -24,7 +24,9 @@ inline int tiles_of(int W, int H, int ncam)
 // march.cu
 cudaError_t launch_fwd(const SingleArgs& a, int dt, int kind, int ntiles, cudaStream_t s);
 cudaError_t launch_fwd_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
-                             int dt, int kind, bool tau, cudaStream_t s);
+                             int dt, int kind, bool tau, bool pairs, cudaStream_t s);
+// x-pair records of every problem's volume (vol_rw -> pairs), RGB records
+cudaError_t launch_pair_pack_batch(const ProbDev* probs, int nprob, int dt, cudaStream_t s);
 cudaError_t launch_adjust(const SingleArgs& a, int dt, int ntiles, cudaStream_t s);
 cudaError_t launch_adjust_list_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
                                      int dt, bool tau, int iteration, cudaStream_t s);

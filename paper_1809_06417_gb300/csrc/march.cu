@@ -212,14 +212,14 @@ __global__ void FR_MARCH_BOUNDS fwd_single(const __grid_constant__ SingleArgs a)
     fwd_body<DT, KIND, TAU, PAIRS>(a.p, a.cams, blockIdx.x);
 }
 
-template <int DT, int KIND, bool TAU>
+template <int DT, int KIND, bool TAU, bool PAIRS>
 __global__ void FR_MARCH_BOUNDS fwd_batch(const ProbDev* __restrict__ probs,
                                                                           const int* __restrict__ tile_start,
                                                                           int nprob)
 {
     const int p = find_problem(tile_start, nprob, blockIdx.x);
     const ProbDev& P = probs[p];
-    fwd_body<DT, KIND, TAU, false>(P, P.cams, blockIdx.x - __ldg(tile_start + p));
+    fwd_body<DT, KIND, TAU, PAIRS>(P, P.cams, blockIdx.x - __ldg(tile_start + p));
 }
 
 // ---------------------------------------------------------------------------
@@ -631,18 +631,20 @@ cudaError_t launch_fwd(const SingleArgs& a, int dt, int kind, int ntiles, cudaSt
 }
 
 cudaError_t launch_fwd_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
-                             int dt, int kind, bool tau, cudaStream_t s)
+                             int dt, int kind, bool tau, bool pairs, cudaStream_t s)
 {
     dim3 grid(total_tiles), block(kTileThreads);
+#define FR_FWDB(D, K, T)                                                                        \
+    if (pairs) fwd_batch<D, K, T, true><<<grid, block, 0, s>>>(probs, tile_start, nprob);        \
+    else fwd_batch<D, K, T, false><<<grid, block, 0, s>>>(probs, tile_start, nprob)
     FR_DISPATCH_DT(dt, D, {
         if (kind == KIND_RGB) {
-            if (tau) fwd_batch<D, KIND_RGB, true><<<grid, block, 0, s>>>(probs, tile_start, nprob);
-            else fwd_batch<D, KIND_RGB, false><<<grid, block, 0, s>>>(probs, tile_start, nprob);
+            if (tau) { FR_FWDB(D, KIND_RGB, true); } else { FR_FWDB(D, KIND_RGB, false); }
         } else {
-            if (tau) fwd_batch<D, KIND_TEMP, true><<<grid, block, 0, s>>>(probs, tile_start, nprob);
-            else fwd_batch<D, KIND_TEMP, false><<<grid, block, 0, s>>>(probs, tile_start, nprob);
+            if (tau) { FR_FWDB(D, KIND_TEMP, true); } else { FR_FWDB(D, KIND_TEMP, false); }
         }
     });
+#undef FR_FWDB
     return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@ struct fr_job {
     float* sqerr = nullptr;
     unsigned* fbuf = nullptr;
     unsigned* flist = nullptr;
+    void* pairs = nullptr;
     int ntiles = 0;
 };
 
@@ -52,7 +53,7 @@ struct fr_server {
 namespace {
 
 struct JobLayout {
-    size_t vol, targets, bbox, residual, dV, partials, sqerr, fbuf, flist, total;
+    size_t vol, targets, bbox, residual, dV, partials, sqerr, fbuf, flist, pairs, total;
 };
 
 JobLayout job_layout(const fr_job_desc& d, int dtype, const fr_camera* cams)
@@ -72,6 +73,7 @@ JobLayout job_layout(const fr_job_desc& d, int dtype, const fr_camera* cams)
     L.sqerr = o; o += align256((size_t)std::max(d.iters, 1) * 16);
     L.fbuf = o; o += align256(flame_list_buf_entries(nt) * 4);
     L.flist = o; o += align256((size_t)npix * 4);
+    L.pairs = o; o += align256((size_t)nodes * 8 * dtype_bytes(dtype));
     L.total = o;
     return L;
 }
@@ -121,6 +123,7 @@ fr_status job_admit(fr_server* s, fr_job* j)
     j->sqerr = reinterpret_cast<float*>(j->mem + L.sqerr);
     j->fbuf = reinterpret_cast<unsigned*>(j->mem + L.fbuf);
     j->flist = reinterpret_cast<unsigned*>(j->mem + L.flist);
+    j->pairs = j->mem + L.pairs;
     const long long nodes = (long long)j->d.nx * j->d.ny * j->d.nz;
     const size_t ib = image_bytes(j->cams.data(), j->d.ncam);
     const int W = j->cams[0].width, H = j->cams[0].height;
@@ -350,6 +353,7 @@ extern "C" fr_status fr_server_step(fr_server* s, int* running, int* queued)
             P.iteration = j->iters_done;
             P.sq_slot = j->iters_done;
             if (j->d.alpha_l != 0.0f) P.alpha_l = j->d.alpha_l;
+            P.pairs = j->pairs;
             hp[i] = P;
             for (int k = 0; k < j->d.ncam; ++k) hc[cam_off + k] = a.cams[k];
             ht[i] = tile_off;
@@ -360,7 +364,8 @@ extern "C" fr_status fr_server_step(fr_server* s, int* running, int* queued)
         FR_CUDA(c, cudaMemcpyAsync(db, hb, tables, cudaMemcpyHostToDevice, st));
         FR_CUDA(c, cudaEventRecord(s->staging_done, st));
         const bool tau = s->p.tau > 0.0f;
-        FR_CUDA(c, launch_fwd_batch(dp, dtl, n, tile_off, s->dtype, KIND_RGB, tau, st));
+        FR_CUDA(c, launch_pair_pack_batch(dp, n, s->dtype, st));
+        FR_CUDA(c, launch_fwd_batch(dp, dtl, n, tile_off, s->dtype, KIND_RGB, tau, true, st));
         FR_CUDA(c, launch_finalize_batch(dp, n, 0, st));
         FR_CUDA(c, launch_adjust_list_batch(dp, dtl, n, tile_off, s->dtype, tau, 0, st));
         FR_CUDA(c, launch_apply_batch(dp, n, s->dtype, s->p.clamp_nonneg, st));

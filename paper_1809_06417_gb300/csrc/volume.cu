@@ -153,6 +153,42 @@ __global__ void __launch_bounds__(256) pair_pack_kernel(const void* src, void* d
     }
 }
 
+// Batched form: blockIdx.y is the problem, its volume vol_rw packed into pairs.
+template <int DT>
+__global__ void __launch_bounds__(256) pair_pack_batch_kernel(const ProbDev* __restrict__ probs)
+{
+    const ProbDev& P = probs[blockIdx.y];
+    const long long rows = (long long)P.ny * P.nz;
+    const int nx = P.nx;
+    const void* src = P.vol_rw;
+    void* dst = const_cast<void*>(P.pairs);
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const long long r0 = row * nx;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const long long i = r0 + x, j = x < nx - 1 ? i + 1 : i;
+            if constexpr (DT == DT_F32) {
+                const float4* s4 = reinterpret_cast<const float4*>(src);
+                float4* d4 = reinterpret_cast<float4*>(dst);
+                d4[2 * i] = s4[i];
+                d4[2 * i + 1] = s4[j];
+            } else {
+                const uint2* s2 = reinterpret_cast<const uint2*>(src);
+                const uint2 a = s2[i], b = s2[j];
+                reinterpret_cast<uint4*>(dst)[i] = make_uint4(a.x, a.y, b.x, b.y);
+            }
+        }
+    }
+}
+
+cudaError_t launch_pair_pack_batch(const ProbDev* probs, int nprob, int dt, cudaStream_t s)
+{
+    const dim3 grid(256, nprob);
+    if (dt == DT_F32) pair_pack_batch_kernel<DT_F32><<<grid, 256, 0, s>>>(probs);
+    else if (dt == DT_BF16) pair_pack_batch_kernel<DT_BF16><<<grid, 256, 0, s>>>(probs);
+    else pair_pack_batch_kernel<DT_F16><<<grid, 256, 0, s>>>(probs);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int nx, int ny, int nz, cudaStream_t s)
 {
     const long long rows = (long long)ny * nz;
@@ -315,17 +351,107 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const
     }
 }
 
+// The x sweep with one warp per grid line: lane l owns the l-th of 32 chunks
+// of consecutive nodes, so a warp's loads walk along one row of memory.  The
+// chunks' affine maps are combined with warp shuffles: an inclusive prefix
+// (forward maps, composed first-then-next) and an inclusive suffix (backward
+// maps).  It initialises J (the first sweep).
+template <int DT>
+__global__ void __launch_bounds__(256) sweep_x_kernel(const void* em, float* J, int nx, int ny, int nz)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long line = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (line >= (long long)ny * nz) return;   // whole warps leave together
+    const long long start = line * nx;
+    const int m = (nx + 31) / 32;
+    const int s0 = min(lane * m, nx), s1 = min(s0 + m, nx);
+    float Ef = 1.0f, F0 = 0.0f, F1 = 0.0f, F2 = 0.0f;
+    float Eb = 1.0f, B0 = 0.0f, B1 = 0.0f, B2 = 0.0f;
+    if (s1 > s0) {
+        const int lo = max(s0 - 1, 0), hi = min(s1, nx - 1);
+        float4 prev = load_rgb<DT>(em, start + lo);
+        for (int i = lo + 1; i <= hi; ++i) {
+            const float4 cur = load_rgb<DT>(em, start + i);
+            const Seg g = seg_between<DT>(prev, cur);
+            if (i >= s0 && i < s1) {
+                F0 = fmaf(F0, g.e, g.c0); F1 = fmaf(F1, g.e, g.c1); F2 = fmaf(F2, g.e, g.c2);
+                Ef *= g.e;
+            }
+            if (i - 1 >= s0 && i - 1 < s1) {
+                B0 = fmaf(Eb, g.c0, B0); B1 = fmaf(Eb, g.c1, B1); B2 = fmaf(Eb, g.c2, B2);
+                Eb *= g.e;
+            }
+            prev = cur;
+        }
+    }
+    // inclusive prefix of the forward maps: (earlier) then (mine)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float e = __shfl_up_sync(FULL, Ef, o), c0 = __shfl_up_sync(FULL, F0, o);
+        const float c1 = __shfl_up_sync(FULL, F1, o), c2 = __shfl_up_sync(FULL, F2, o);
+        if (lane >= o) {
+            F0 = fmaf(c0, Ef, F0); F1 = fmaf(c1, Ef, F1); F2 = fmaf(c2, Ef, F2);
+            Ef *= e;
+        }
+    }
+    // inclusive suffix of the backward maps: (mine) applied after (later)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float e = __shfl_down_sync(FULL, Eb, o), c0 = __shfl_down_sync(FULL, B0, o);
+        const float c1 = __shfl_down_sync(FULL, B1, o), c2 = __shfl_down_sync(FULL, B2, o);
+        if (lane + o < 32) {
+            B0 = fmaf(c0, Eb, B0); B1 = fmaf(c1, Eb, B1); B2 = fmaf(c2, Eb, B2);
+            Eb *= e;
+        }
+    }
+    // radiance arriving at the chunk: line start / end carry nothing
+    float lf0 = __shfl_up_sync(FULL, F0, 1), lf1 = __shfl_up_sync(FULL, F1, 1), lf2 = __shfl_up_sync(FULL, F2, 1);
+    float lb0 = __shfl_down_sync(FULL, B0, 1), lb1 = __shfl_down_sync(FULL, B1, 1), lb2 = __shfl_down_sync(FULL, B2, 1);
+    if (lane == 0) { lf0 = lf1 = lf2 = 0.0f; }
+    if (lane == 31) { lb0 = lb1 = lb2 = 0.0f; }
+    if (s1 <= s0) return;
+    const float sixth = 1.0f / 6.0f;
+    float4* J4 = reinterpret_cast<float4*>(J);
+    {
+        float4 prev = load_rgb<DT>(em, start + max(s0 - 1, 0));
+        for (int i = s0; i < s1; ++i) {
+            const float4 cur = load_rgb<DT>(em, start + i);
+            if (i > 0) {
+                const Seg g = seg_between<DT>(prev, cur);
+                lf0 = fmaf(lf0, g.e, g.c0); lf1 = fmaf(lf1, g.e, g.c1); lf2 = fmaf(lf2, g.e, g.c2);
+            }
+            prev = cur;
+            J4[start + i] = make_float4(lf0 * sixth, lf1 * sixth, lf2 * sixth, 0.0f);
+        }
+    }
+    {
+        float4 next = load_rgb<DT>(em, start + min(s1, nx - 1));
+        for (int i = s1 - 1; i >= s0; --i) {
+            const float4 cur = load_rgb<DT>(em, start + i);
+            if (i < nx - 1) {
+                const Seg g = seg_between<DT>(cur, next);
+                lb0 = fmaf(lb0, g.e, g.c0); lb1 = fmaf(lb1, g.e, g.c1); lb2 = fmaf(lb2, g.e, g.c2);
+            }
+            next = cur;
+            float4 j = J4[start + i];
+            j.x = fmaf(lb0, sixth, j.x); j.y = fmaf(lb1, sixth, j.y); j.z = fmaf(lb2, sixth, j.z);
+            J4[start + i] = j;
+        }
+    }
+}
+
 cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* albedo, float* J,
                                   void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s)
 {
     if (dt_in != dt_out) return cudaErrorInvalidValue;
     const long long lx = (long long)ny * nz, ly = (long long)nx * nz, lz = (long long)nx * ny;
-    const unsigned gx = (unsigned)((lx + kSweepLines - 1) / kSweepLines);
+    const unsigned gxw = (unsigned)((lx + 7) / 8);  // one warp per x line, 8 warps per CTA
     const unsigned gy = (unsigned)((ly + kSweepLines - 1) / kSweepLines);
     const unsigned gz = (unsigned)((lz + kSweepLines - 1) / kSweepLines);
     const dim3 B(kSweepLines, kSweepChunks);
 #define FR_SWEEPS(D)                                                                         \
-    sweep_kernel<D, 0, false><<<gx, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz);        \
+    sweep_x_kernel<D><<<gxw, 256, 0, s>>>(emission, J, nx, ny, nz);                         \
     sweep_kernel<D, 1, false><<<gy, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz);        \
     sweep_kernel<D, 2, true><<<gz, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz)
     if (dt_in == DT_F32) { FR_SWEEPS(DT_F32); }
