@@ -34,10 +34,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ray samples/s (fwd+adjoint) and recon iters/s at 128^3×8 views; p50/p99 job latency"
 WORKLOAD = dict(name="full_rte_128^3_8x512^2", n=128, views=8, side=512, step=0.5, seed=2,
-                alpha_l=2e-4, noise=1e-3)
+                alpha_l=2e-4, noise=1e-3, hull=True)
 # kernels one step (one fr_reconstruct iteration) launches: flame-ray list (3),
-# in-scatter sweeps (3), pair pack, forward, error reduction, adjustment, apply, rmse
-KERNELS_PER_STEP = 12
+# hull clear, hull bricks, in-scatter sweeps (3), pair pack, forward, error
+# reduction, adjustment, apply, hull clear, rmse
+KERNELS_PER_STEP = 15
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures of
 # the current kernels at this workload (None where the kernel changed since)
 NCU_TRAFFIC = {("fwd", "f32"): 143.05e6 + 25.19e6}
@@ -53,6 +54,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the video-batch and serving sections")
     ap.add_argument("--serving-jobs", type=int, default=40)
+    ap.add_argument("--no-hull", action="store_true",
+                    help="reconstruct the whole box instead of the visual hull (Sec. 4.3.1)")
+    ap.add_argument("--no-skip", action="store_true", help="march empty bricks too (same result, slower)")
     ap.add_argument("--profile", action="store_true",
                     help="one untimed iteration plus one forward and one adjustment launch, for ncu")
     return ap.parse_args()
@@ -170,9 +174,20 @@ def make_inputs(storage, rank, local):
     ctx.fr_prepare_targets(targets, 30 / 255, bbox)
     vol0 = gt_d.clone()
     vol0[..., :3] = 0  # the volume starts at zero (Sec. 3); extinction and albedo known
+    # visual hull tags of the job, computed once from its flame masks (Sec. 4.3.1)
+    tags = torch.zeros((n, n, n), dtype=torch.int32, device="cuda")
+    ctx.fr_visual_hull(fr.volume(vol0, origin, h), fcams, targets, fr.params(), tags)
     del J, src
     return ctx, dict(origin=origin, h=h, cams=cams, fcams=fcams, targets=targets, bbox=bbox, albedo=alb_d,
-                     vol0=vol0, gt=gt, gt_albedo=albedo, scale=scale, img_np=img_np)
+                     vol0=vol0, gt=gt, gt_albedo=albedo, scale=scale, img_np=img_np, tags=tags)
+
+
+def method_params(args, I):
+    from paper_1809_06417_gb300 import flamerec as fr
+    w = WORKLOAD
+    hull = w["hull"] and not args.no_hull
+    return fr.params(step=w["step"], alpha_l=w["alpha_l"], use_hull=int(hull),
+                     hull_tags=I["tags"] if hull else None, skip_empty=int(not args.no_skip))
 
 
 def run_ours(args, ws, rank, local):
@@ -182,12 +197,11 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     w = WORKLOAD
     ctx, I = make_inputs(args.storage, rank, local)
-    p = fr.params(step=w["step"], alpha_l=w["alpha_l"])
+    p = method_params(args, I)
     vol = I["vol0"].clone()
     fv = fr.volume(vol, I["origin"], I["h"])
     cams = I["fcams"]
     stream = torch.cuda.current_stream()
-    n_fwd = ctx.fr_count_samples(fv, cams, p)
     n_adj = ctx.fr_count_samples(fv, cams, p, residual=I["targets"])
     flush = torch.empty(384 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
 
@@ -196,11 +210,17 @@ def run_ours(args, ws, rank, local):
 
     for it in range(args.warmup):
         step(it)
+    # forward samples evaluated (empty bricks of the current volume skipped),
+    # counted before and after the timed steps
+    n_fwd_before = ctx.fr_count_samples(fv, cams, p)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # per-phase device time of the timed steps, from events the library
+    # records on this stream between its launches
+    ctx.fr_trace_phases(True)
     with Clocks(local) as clk:
         t_wall = time.perf_counter()
         for i in range(args.steps):
@@ -214,28 +234,15 @@ def run_ours(args, ws, rank, local):
         dist.barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
     t_dev = dist_max(sum(ms) / 1e3)
+    phase_ms, calls = ctx.fr_phase_times()
+    ctx.fr_trace_phases(False)
+    assert calls == args.steps, (calls, args.steps)
+    phase_ms = {k: v / args.steps for k, v in phase_ms.items()}
+    n_fwd_after = ctx.fr_count_samples(fv, cams, p)
+    n_fwd = (n_fwd_before + n_fwd_after) // 2
+    n_fwd_box = ctx.fr_count_samples(fv, cams, fr.params(step=w["step"], skip_empty=0))
 
-    # per-kernel timing of the two marches (forward + residual, adjustment)
-    res = torch.empty_like(I["targets"])
-    sq = torch.zeros(4, device="cuda")
-    dV = torch.zeros(vol.shape[:3] + (4,), device="cuda")
-    src = torch.empty_like(vol)
-    J = torch.empty(vol.shape[:3] + (4,), device="cuda")
-    ctx.fr_scatter_source(fv, I["albedo"], J, fr.volume(src, I["origin"], I["h"]))
-    fs = fr.volume(src, I["origin"], I["h"])
-    kf, ka = [], []
-    for i in range(max(5, args.steps // 2)):
-        flush.fill_(float(i))
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(stream)
-        ctx.fr_render_residual(fs, cams, p, I["targets"], I["bbox"], None, res, sq)
-        e1.record(stream)
-        ctx.fr_adjust(fs, cams, p, res, i, dV)
-        e2.record(stream)
-        torch.cuda.synchronize()
-        kf.append(e0.elapsed_time(e1))
-        ka.append(e1.elapsed_time(e2))
-    t_fwd, t_adj = statistics.median(kf) / 1e3, statistics.median(ka) / 1e3
+    t_fwd, t_adj = phase_ms["forward"] / 1e3, phase_ms["adjust"] / 1e3
 
     # end to end through the C ABI with host buffers: pinned targets in, rmse out
     tgt_host = I["targets"].cpu().pin_memory()
@@ -296,10 +303,13 @@ def run_ours(args, ws, rank, local):
         "data": "synthetic",
         "config": {"workload": w["name"], "grid": [w["n"]] * 3, "views": w["views"], "image": [w["side"]] * 2,
                    "step_vox": w["step"], "storage": args.storage, "rule": "paper", "scattering": True,
+                   "visual_hull": bool(p.use_hull), "skip_empty_bricks": bool(p.skip_empty),
                    "l2": "flushed before every timed step (384 MiB write)", "parallelism": f"replicas{ws}"},
         "recon_iters_per_s": ws * args.steps / t_dev,
-        "samples_per_step": {"fwd": n_fwd, "adj": n_adj},
+        "samples_per_step": {"fwd": n_fwd, "adj": n_adj, "fwd_before": n_fwd_before, "fwd_after": n_fwd_after,
+                             "fwd_all_in_box": n_fwd_box},
         "kernel_ms": {"fwd_residual": 1e3 * t_fwd, "adjust": 1e3 * t_adj},
+        "phase_ms_per_step": phase_ms,
         "e2e": {"value": weak_value(ws, samples_step, args.steps, t_e2e), "unit": "samples/s",
                 "h2d_bytes_per_step": int(I["targets"].numel() * 4), "d2h_bytes_per_step": 12},
         "gpu_launches": KERNELS_PER_STEP * args.steps,
@@ -503,7 +513,7 @@ def run_profile(args):
     from paper_1809_06417_gb300 import flamerec as fr
     w = WORKLOAD
     ctx, I = make_inputs(args.storage, 0, 0)
-    p = fr.params(step=w["step"], alpha_l=w["alpha_l"])
+    p = method_params(args, I)
     vol = I["vol0"].clone()
     fv = fr.volume(vol, I["origin"], I["h"])
     ctx.fr_reconstruct(fv, I["fcams"], I["targets"], I["bbox"], 1, p, albedo=I["albedo"])

@@ -45,7 +45,8 @@ typedef enum fr_status {
     FR_ECUDA = 3,        /* a CUDA call failed; see fr_last_error */
     FR_ETIMEDOUT = 4,    /* a bounded wait ran out */
     FR_EBUSY = 5,        /* resource in use (e.g. a job table slot) */
-    FR_ECANCELED = 6     /* the job was cancelled */
+    FR_ECANCELED = 6,    /* the job was cancelled */
+    FR_ERANGE = 7        /* a bounded record overflowed (what fits is still returned) */
 } fr_status;
 
 typedef enum fr_dtype { FR_F32 = 0, FR_BF16 = 1, FR_F16 = 2 } fr_dtype;
@@ -103,7 +104,13 @@ typedef struct fr_params {
     float lut_t_min, lut_t_max; /* colour-temperature table range, kelvin */
     const float *lut;    /* device, lut_size x 4 {r,g,b,0}, from fr_planck_lut (TEMP only) */
     int32_t lut_size;
-    int32_t pad_;
+    int32_t use_hull;    /* fr_reconstruct: hold records outside the visual hull at 0 (Sec. 4.3.1) */
+    int32_t skip_empty;  /* forward march of RGB records without tau: skip 8^3-cell bricks whose
+                            records are all zero (exact: the result is bitwise the same); with
+                            use_hull, the paper-rule adjustment also skips bricks with no key point
+                            inside the hull (exact up to the order of its atomic sums) */
+    const uint32_t *hull_tags; /* use_hull: device, one tag per node from fr_visual_hull for the same
+                            cameras and targets; NULL: fr_reconstruct computes them each call */
 } fr_params;
 
 typedef struct fr_ctx fr_ctx;
@@ -197,6 +204,23 @@ fr_status fr_scatter_source(fr_ctx *ctx, const fr_volume *emission, const float 
  * 380-780 nm, trapezoid rule in 1 nm steps), scaled so green(2000 K) = 1.
  * lut: device, m x 4 float32 {r, g, b, 0} at t_min + i (t_max - t_min)/(m-1). */
 fr_status fr_planck_lut(fr_ctx *ctx, float t_min, float t_max, int m, float *lut);
+
+/* Visual hull (Sec. 4.3.1, Algorithm 1).  Bit v of tags[node] is set when the
+ * centre of a flame pixel of view v (prepared target above p->flame_thresh)
+ * lies in the image rectangle bounding the projection of the box of the eight
+ * cells that share the node ([i-1, i+1] x [j-1, j+1] x [k-1, k+1], clipped to
+ * the volume): every ray that samples one of those cells passes through that
+ * rectangle, so the tags are conservative.  The projection is evaluated in
+ * float32 with one rounding per operation (an integer decision):
+ *   o = (pos - origin) * (1/h);  x_c = ((X - o_x) r_x + (Y - o_y) r_y) + (Z - o_z) r_z,
+ *   likewise y_c (up) and z_c (fwd);  u = ((x_c / z_c) / t_x + 1) (W/2) - 1/2,
+ *   t_x = tan_half W / H;  v = (1 - (y_c / z_c) / tan_half) (H/2) - 1/2;
+ *   pixels [ceil(u_min), floor(u_max)] x [ceil(v_min), floor(v_max)] clipped to
+ *   the image, the whole image if a corner has z_c <= 0.
+ * A node is inside the hull when all ncam bits are set.  vol: the grid (its
+ * data is not read).  targets: device, prepared.  tags: device, nodes uint32. */
+fr_status fr_visual_hull(fr_ctx *ctx, const fr_volume *vol, const fr_camera *cams, int ncam,
+                         const float *targets, const fr_params *p, uint32_t *tags);
 
 /* The reconstruction loop (Sec. 3, Algorithm 2 repeated): for `iters`
  * iterations: [in-scattering source when albedo != NULL] -> render and
@@ -296,9 +320,37 @@ fr_status fr_job_release(fr_server *srv, fr_job *job);
 /* Device bytes currently held for resident jobs. */
 fr_status fr_server_memory(const fr_server *srv, size_t *used, size_t *budget);
 
+/* ---- Tracing: device time per phase of fr_reconstruct ---- */
+
+typedef enum {
+    FR_PHASE_SETUP = 0,   /* flame-ray list; visual hull tags, clear and bricks */
+    FR_PHASE_SCATTER = 1, /* in-scattering source (Sec. 3.2) */
+    FR_PHASE_PACK = 2,    /* x-pair records and brick occupancy */
+    FR_PHASE_FORWARD = 3, /* forward march with the residual (Eqs. 5-8) */
+    FR_PHASE_REDUCE = 4,  /* squared-error reduction */
+    FR_PHASE_ADJUST = 5,  /* adjustment (Eqs. 10-12) or the exact gradient */
+    FR_PHASE_APPLY = 6,   /* update of the volume, hull clear */
+    FR_PHASE_FINISH = 7,  /* error measure of the call */
+    FR_PHASE_COUNT = 8
+} fr_phase;
+
+/* on != 0: the following fr_reconstruct calls record a CUDA event on the
+ * context's stream after each phase (a few microseconds of device time per
+ * event); on == 0 stops.  Either way, what was recorded before is dropped. */
+fr_status fr_trace_phases(fr_ctx *ctx, int on);
+/* Waits for the recorded events and writes ms[p] (host, n >= FR_PHASE_COUNT
+ * entries) = milliseconds spent in phase p summed over every call recorded
+ * since tracing was turned on or last read, and *calls (host, nullable) = the
+ * number of those calls; then drops the record.  FR_ERANGE when more than
+ * 65536 events went unread (the later ones were not recorded). */
+fr_status fr_phase_times(fr_ctx *ctx, float *ms, int n, int32_t *calls);
+
 /* Number of samples (segments) the rays of `cams` take through the volume's
- * box: all rays when residual is NULL (one render), else only the rays whose
- * residual (device, image layout) is non-zero (one adjustment).  Counted by a
+ * box: all rays when residual is NULL (one render; when p->skip_empty applies,
+ * the samples in bricks whose records are all zero are skipped by the render
+ * and not counted), else only the rays whose residual (device, image layout)
+ * is non-zero (one adjustment; with p->skip_empty, p->use_hull and
+ * p->hull_tags, the samples fr_reconstruct's adjustment evaluates).  Counted by a
  * device kernel; *samples (host) is written before the call returns (the
  * call synchronises the stream). */
 fr_status fr_count_samples(fr_ctx *ctx, const fr_volume *vol, const fr_camera *cams,

@@ -88,7 +88,8 @@ def _load():
             "orc_scatter_J": (None, [_P, _P, _P]),
             "orc_scatter_source": (None, [_I64, _P, _P, _P, _P]),
             "orc_reconstruct": (None, [_P, _P, _P, _P, ctypes.c_int, _P, _P, _P, _P,
-                                       ctypes.c_int, ctypes.c_int, _P, _P]),
+                                       ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+            "orc_visual_hull": (None, [_P, _P, ctypes.c_int, _P, _P]),
             "orc_planck": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
             "orc_temp_rgb": (None, [ctypes.c_double, _P]),
             "orc_lut_build": (None, [ctypes.c_double, ctypes.c_double, ctypes.c_int, _P]),
@@ -321,9 +322,20 @@ def scatter_source(vol, albedo, J):
     return out
 
 
+def visual_hull(scene: Scene, mask):
+    """Algorithm 1: per-node view bits (uint32, (nz, ny, nx)) from flame masks (K, H, W)."""
+    lib = _load()
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    nx, ny, nz = scene.shape
+    tags = np.zeros((nz, ny, nx), dtype=np.uint32)
+    lib.orc_visual_hull(ctypes.byref(scene.grid), scene.cams, scene.ncam, _ptr(mask), _ptr(tags))
+    return tags
+
+
 def reconstruct(scene: Scene, vol, params: Params, targets, mask, bbox, iters,
-                albedo=None, first_iteration=0):
-    """Algorithm 2 repeated `iters` times with the paper rule.
+                albedo=None, first_iteration=0, hull=None):
+    """Algorithm 2 repeated `iters` times with the paper rule; with `hull`
+    (visual-hull tags) the records outside the hull are held at 0.
     Returns (volume, rmse per iteration (iters x 3), (forward, adjust) samples)."""
     lib = _load()
     vol = _check_vol(vol, scene.shape, 4).copy()
@@ -333,9 +345,11 @@ def reconstruct(scene: Scene, vol, params: Params, targets, mask, bbox, iters,
     rmse = np.zeros((iters, 3))
     samples = np.zeros(2, dtype=np.int64)
     alb = _f64(albedo) if albedo is not None else None
+    hl = np.ascontiguousarray(hull, dtype=np.uint32) if hull is not None else None
     lib.orc_reconstruct(ctypes.byref(scene.grid), _ptr(vol), _ptr(alb) if alb is not None else None,
                         scene.cams, scene.ncam, ctypes.byref(params), _ptr(targets), _ptr(mask),
-                        _ptr(bbox), int(iters), int(first_iteration), _ptr(rmse), _ptr(samples))
+                        _ptr(bbox), int(iters), int(first_iteration), _ptr(rmse), _ptr(samples),
+                        _ptr(hl) if hl is not None else None)
     return vol, rmse, (int(samples[0]), int(samples[1]))
 
 

@@ -725,6 +725,89 @@ void orc_scatter_source(int64_t nodes, const double *vol, const double *albedo,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Visual hull (Sec. 4.3.1, Algorithm 1)                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Algorithm 1 tags the key points "around" every flame ray of view v with bit
+ * v; a key point is inside the hull when all K bits are set.  Reading: key
+ * point j is around a flame ray of view v when the centre of a flame pixel
+ * lies in the image rectangle that bounds the projection of the box of the
+ * eight cells sharing j ([j-1, j+1] per axis, clipped to the volume) -- every
+ * ray that can sample one of those cells passes through that rectangle, so
+ * the tags are conservative.  The projection decides an integer, so it is
+ * evaluated in single precision, one rounding per operation, in this order:
+ *   o = (pos - origin) * (1 / h)                (camera in voxel units)
+ *   x_c = ((X - o_x) r_x + (Y - o_y) r_y) + (Z - o_z) r_z   (same for up, fwd)
+ *   u = ((x_c / z_c) / t_x + 1) (W / 2) - 1/2,  t_x = tan_half W / H
+ *   v = (1 - (y_c / z_c) / t_y) (H / 2) - 1/2,  t_y = tan_half
+ * and the pixel range is [ceil(u_min), floor(u_max)] x [ceil(v_min), floor(v_max)]
+ * clipped to the image; a corner with z_c <= 0 makes it the whole image. */
+static float dot3f(float ax, float ay, float az, const float r[3])
+{
+    float t = ax * r[0];
+    t = t + ay * r[1];
+    t = t + az * r[2];
+    return t;
+}
+
+void orc_visual_hull(const orc_grid *g, const orc_cam *cams, int ncam, const uint8_t *mask,
+                     uint32_t *tags)
+{
+    const int n[3] = {g->nx, g->ny, g->nz};
+    const float inv_h = 1.0f / (float)g->h;
+    for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+            for (int i = 0; i < n[0]; ++i) {
+                uint32_t tag = 0;
+                const int lo[3] = {i > 0 ? i - 1 : 0, j > 0 ? j - 1 : 0, k > 0 ? k - 1 : 0};
+                const int hi[3] = {i < n[0] - 1 ? i + 1 : n[0] - 1, j < n[1] - 1 ? j + 1 : n[1] - 1,
+                                   k < n[2] - 1 ? k + 1 : n[2] - 1};
+                for (int v = 0; v < ncam; ++v) {
+                    const orc_cam *c = cams + v;
+                    float o[3], r[3], u[3], f[3];
+                    for (int a = 0; a < 3; ++a) {
+                        o[a] = ((float)c->pos[a] - (float)g->origin[a]) * inv_h;
+                        r[a] = (float)c->right[a];
+                        u[a] = (float)c->up[a];
+                        f[a] = (float)c->fwd[a];
+                    }
+                    const float ty = (float)c->tan_half_fov;
+                    const float tx = ty * (float)c->width / (float)c->height;
+                    const float hw = 0.5f * (float)c->width, hh = 0.5f * (float)c->height;
+                    float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+                    int behind = 0;
+                    for (int b = 0; b < 8; ++b) {
+                        const float X = (float)((b & 1) ? hi[0] : lo[0]) - o[0];
+                        const float Y = (float)((b & 2) ? hi[1] : lo[1]) - o[1];
+                        const float Z = (float)((b & 4) ? hi[2] : lo[2]) - o[2];
+                        const float xc = dot3f(X, Y, Z, r), yc = dot3f(X, Y, Z, u), zc = dot3f(X, Y, Z, f);
+                        if (!(zc > 0.0f)) { behind = 1; break; }
+                        const float uu = ((xc / zc) / tx + 1.0f) * hw - 0.5f;
+                        const float vv = (1.0f - (yc / zc) / ty) * hh - 0.5f;
+                        if (uu < umin) umin = uu;
+                        if (uu > umax) umax = uu;
+                        if (vv < vmin) vmin = vv;
+                        if (vv > vmax) vmax = vv;
+                    }
+                    int x0 = 0, x1 = c->width - 1, y0 = 0, y1 = c->height - 1;
+                    if (!behind) {
+                        const float cx0 = ceilf(umin), cx1 = floorf(umax), cy0 = ceilf(vmin), cy1 = floorf(vmax);
+                        x0 = cx0 > 0.0f ? (cx0 < (float)c->width ? (int)cx0 : c->width) : 0;
+                        x1 = cx1 < (float)(c->width - 1) ? (cx1 >= -1.0f ? (int)cx1 : -1) : c->width - 1;
+                        y0 = cy0 > 0.0f ? (cy0 < (float)c->height ? (int)cy0 : c->height) : 0;
+                        y1 = cy1 < (float)(c->height - 1) ? (cy1 >= -1.0f ? (int)cy1 : -1) : c->height - 1;
+                    }
+                    int hit = 0;
+                    for (int py = y0; py <= y1 && !hit; ++py)
+                        for (int px = x0; px <= x1; ++px)
+                            if (mask[((int64_t)v * c->height + py) * c->width + px]) { hit = 1; break; }
+                    if (hit) tag |= 1u << v;
+                }
+                tags[node_index(g, i, j, k)] = tag;
+            }
+}
+
+/* ------------------------------------------------------------------------ */
 /* The iteration (Sec. 3, Algorithm 2): render, compare, adjust.             */
 /* ------------------------------------------------------------------------ */
 
@@ -737,7 +820,8 @@ void orc_scatter_source(int64_t nodes, const double *vol, const double *albedo,
 void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
                      const orc_cam *cams, int ncam, const orc_params *P,
                      const double *targets, const uint8_t *mask, const int32_t *bbox,
-                     int iters, int first_iteration, double *rmse, int64_t *samples)
+                     int iters, int first_iteration, double *rmse, int64_t *samples,
+                     const uint32_t *hull)
 {
     int64_t nodes = (int64_t)g->nx * g->ny * g->nz;
     int64_t npix = 0;
@@ -747,6 +831,14 @@ void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
     double *dV = malloc(sizeof(double) * 3 * (size_t)nodes);
     double *J = albedo ? malloc(sizeof(double) * 3 * (size_t)nodes) : NULL;
     double *src = albedo ? malloc(sizeof(double) * 4 * (size_t)nodes) : NULL;
+    /* key points outside the visual hull are not reconstructed: they hold no
+     * flame, so their whole record (emission and extinction) is 0 and stays 0
+     * (Sec. 4.3.1 marks them with a non-flame value, a small negative number;
+     * 0 here, which leaves the rays through them unchanged) */
+    const uint32_t full = ncam >= 32 ? 0xffffffffu : ((1u << ncam) - 1u);
+    if (hull)
+        for (int64_t j = 0; j < nodes; ++j)
+            if (hull[j] != full) vol[4 * j] = vol[4 * j + 1] = vol[4 * j + 2] = vol[4 * j + 3] = 0.0;
     for (int it = 0; it < iters; ++it) {
         const double *rvol = vol;
         if (albedo) {
@@ -759,6 +851,9 @@ void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
         memset(dV, 0, sizeof(double) * 3 * (size_t)nodes);
         samples[1] += orc_update_paper(g, rvol, cams, ncam, P, res, mask, first_iteration + it, dV);
         orc_apply_update(nodes, vol, dV, P->clamp_nonneg);
+        if (hull)
+            for (int64_t j = 0; j < nodes; ++j)
+                if (hull[j] != full) vol[4 * j] = vol[4 * j + 1] = vol[4 * j + 2] = vol[4 * j + 3] = 0.0;
     }
     free(img); free(res); free(dV); free(J); free(src);
 }

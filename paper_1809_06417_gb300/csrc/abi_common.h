@@ -11,6 +11,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -32,11 +33,19 @@ struct fr_ctx {
     Buf partials, counter, residual, rendered, dV, targets, sqerr, rmse, J, src, flame_off, flame_list;
     Buf batch;                       // batched reconstruction scratch and tables
     Buf pairs;                       // x-pair records for the forward march
+    Buf occ;                         // brick occupancy for empty-space skipping
+    Buf hull_bricks;                 // bricks holding a key point inside the visual hull
+    Buf hull, sat;                   // visual hull tags, flame-mask tables
     unsigned long long* host_counter = nullptr;
     void* staging = nullptr;         // pinned host staging of batch tables
     size_t staging_bytes = 0;
     cudaEvent_t staging_done = nullptr;
     cudaStream_t capture = nullptr;  // stream used to capture CUDA graphs
+    // phase tracing: events recorded between the phases of fr_reconstruct
+    bool trace_on = false;
+    bool trace_overflow = false;
+    std::vector<cudaEvent_t> trace_pool;          // created on demand, reused
+    std::vector<int> trace_phase;                 // phase of the interval ending at event i (-1: none)
 };
 
 namespace frabi {
@@ -251,6 +260,29 @@ inline void fill_problem(const fr_volume* v, const fr_camera* cams, int ncam, co
 inline size_t image_bytes(const fr_camera* cams, int ncam)
 {
     return (size_t)ncam * cams[0].width * cams[0].height * 3 * sizeof(float);
+}
+
+constexpr size_t kTraceMaxEvents = 1 << 16;
+
+// Ends the interval of `phase` (-1: an interval that is not counted) with an
+// event on the context's stream, when tracing is on.  Past kTraceMaxEvents
+// unread events, marks are dropped and the overflow is reported on reading.
+inline fr_status trace_mark(fr_ctx* c, int phase)
+{
+    if (!c->trace_on) return FR_OK;
+    const size_t i = c->trace_phase.size();
+    if (i >= kTraceMaxEvents) {
+        c->trace_overflow = true;
+        return FR_OK;
+    }
+    if (i == c->trace_pool.size()) {
+        cudaEvent_t e;
+        FR_CUDA(c, cudaEventCreate(&e));
+        c->trace_pool.push_back(e);
+    }
+    FR_CUDA(c, cudaEventRecord(c->trace_pool[i], c->stream));
+    c->trace_phase.push_back(phase);
+    return FR_OK;
 }
 
 }  // namespace frabi

@@ -29,6 +29,8 @@ extern "C" void fr_params_default(fr_params* p)
     p->lut_t_max = 2000.0f;
     p->lut = nullptr;
     p->lut_size = 0;
+    p->use_hull = 0;
+    p->skip_empty = 1;
 }
 
 extern "C" fr_status fr_create(fr_ctx** out, int device, void* stream)
@@ -61,12 +63,14 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
-                   &c->rmse, &c->J, &c->src, &c->flame_off, &c->flame_list, &c->batch, &c->pairs})
+                   &c->rmse, &c->J, &c->src, &c->flame_off, &c->flame_list, &c->batch, &c->pairs,
+                   &c->hull, &c->sat, &c->occ, &c->hull_bricks})
         if (b->p) cudaFree(b->p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
     if (c->staging) cudaFreeHost(c->staging);
     if (c->staging_done) cudaEventDestroy(c->staging_done);
     if (c->capture) cudaStreamDestroy(c->capture);
+    for (cudaEvent_t e : c->trace_pool) cudaEventDestroy(e);
     delete c;
     return FR_OK;
 }
@@ -91,12 +95,30 @@ extern "C" fr_status fr_synchronize(fr_ctx* c)
 // Single calls
 // ---------------------------------------------------------------------------
 
-// x-pair copy of the records the forward march will read (library scratch).
-static fr_status attach_pairs(fr_ctx* c, const fr_volume* vol, const void* records, SingleArgs& a)
+// Whether the forward march may skip empty bricks (RGB records in field mode).
+static bool skips_empty(const fr_volume* vol, const fr_params* p)
+{
+    return vol->kind == FR_KIND_RGB && p->skip_empty && !(p->tau > 0.0f);
+}
+
+// x-pair copy of the records the forward march will read, and (when it skips
+// empty bricks) the occupancy of their bricks (library scratch).
+static fr_status attach_pairs(fr_ctx* c, const fr_volume* vol, const fr_params* p, const void* records,
+                              SingleArgs& a)
 {
     FR_TRY(ensure(c, c->pairs, (size_t)node_count(vol) * 2 * rec_bytes(vol), "pairs"));
-    FR_CUDA(c, launch_pair_pack(records, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, c->stream));
+    const int nbx = bricks_along(vol->nx), nby = bricks_along(vol->ny), nbz = bricks_along(vol->nz);
+    unsigned char* occ = nullptr;
+    if (skips_empty(vol, p)) {
+        FR_TRY(ensure(c, c->occ, (size_t)nbx * nby * nbz, "brick occupancy"));
+        occ = static_cast<unsigned char*>(c->occ.p);
+    }
+    FR_CUDA(c, launch_pair_pack(records, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, occ,
+                                c->stream));
     a.p.pairs = c->pairs.p;
+    a.p.occ = occ;
+    a.p.nbx = nbx;
+    a.p.nby = nby;
     return FR_OK;
 }
 
@@ -124,7 +146,7 @@ extern "C" fr_status fr_render(fr_ctx* c, const fr_volume* vol, const fr_camera*
     static thread_local SingleArgs a;
     fill_problem(vol, cams, ncam, p, a);
     a.p.rendered = out_rgb;
-    FR_TRY(attach_pairs(c, vol, vol->data, a));
+    FR_TRY(attach_pairs(c, vol, p, vol->data, a));
     int nt = tiles_of(a.p.W, a.p.H, ncam);
     FR_CUDA(c, launch_fwd(a, vol->dtype, vol->kind, nt, c->stream));
     return FR_OK;
@@ -153,7 +175,7 @@ extern "C" fr_status fr_render_residual(fr_ctx* c, const fr_volume* vol, const f
     a.p.rendered = rendered;
     a.p.residual = residual;
     a.p.partials = static_cast<float*>(c->partials.p);
-    FR_TRY(attach_pairs(c, vol, vol->data, a));
+    FR_TRY(attach_pairs(c, vol, p, vol->data, a));
     FR_CUDA(c, launch_fwd(a, vol->dtype, vol->kind, nt, c->stream));
     FR_CUDA(c, launch_finalize(a.p.partials, nt, sq_err, c->stream));
     return FR_OK;
@@ -248,6 +270,42 @@ extern "C" fr_status fr_planck_lut(fr_ctx* c, float t_min, float t_max, int m, f
     return FR_OK;
 }
 
+extern "C" fr_status fr_trace_phases(fr_ctx* c, int on)
+{
+    FR_BEGIN(c);
+    c->trace_on = on != 0;
+    c->trace_overflow = false;
+    c->trace_phase.clear();
+    return FR_OK;
+}
+
+extern "C" fr_status fr_phase_times(fr_ctx* c, float* ms, int n, int32_t* calls)
+{
+    FR_BEGIN(c);
+    if (!ms || n < FR_PHASE_COUNT) return fail(c, FR_EINVAL, "ms must hold %d entries", (int)FR_PHASE_COUNT);
+    for (int i = 0; i < FR_PHASE_COUNT; ++i) ms[i] = 0.0f;
+    int32_t nc = 0;
+    const size_t ne = c->trace_phase.size();
+    if (ne) FR_CUDA(c, cudaEventSynchronize(c->trace_pool[ne - 1]));
+    for (size_t i = 0; i < ne; ++i) {
+        const int ph = c->trace_phase[i];
+        if (ph < 0) {
+            ++nc;
+            continue;
+        }
+        if (i == 0) continue;
+        float t = 0.0f;
+        FR_CUDA(c, cudaEventElapsedTime(&t, c->trace_pool[i - 1], c->trace_pool[i]));
+        ms[ph] += t;
+    }
+    if (calls) *calls = nc;
+    const bool over = c->trace_overflow;
+    c->trace_phase.clear();
+    c->trace_overflow = false;
+    if (over) return fail(c, FR_ERANGE, "more than %zu trace events went unread", kTraceMaxEvents);
+    return FR_OK;
+}
+
 extern "C" fr_status fr_count_samples(fr_ctx* c, const fr_volume* vol, const fr_camera* cams, int ncam,
                                       const fr_params* p, const float* residual, int64_t* samples)
 {
@@ -262,6 +320,22 @@ extern "C" fr_status fr_count_samples(fr_ctx* c, const fr_volume* vol, const fr_
     fill_problem(vol, cams, ncam, p, a);
     a.p.img_in = residual;
     a.p.counter = static_cast<unsigned long long*>(c->counter.p);
+    // forward samples: those the march evaluates, empty bricks skipped
+    if (!residual && skips_empty(vol, p)) FR_TRY(attach_pairs(c, vol, p, vol->data, a));
+    // adjustment samples inside fr_reconstruct with given hull tags: bricks
+    // without a key point inside the hull are skipped
+    if (residual && p->skip_empty && p->use_hull && p->hull_tags && p->rule == FR_RULE_PAPER &&
+        !(p->tau > 0.0f)) {
+        const int nbx = bricks_along(vol->nx), nby = bricks_along(vol->ny), nbz = bricks_along(vol->nz);
+        FR_TRY(check_dev(c, p->hull_tags, (size_t)node_count(vol) * 4, "hull_tags"));
+        FR_TRY(ensure(c, c->hull_bricks, (size_t)nbx * nby * nbz, "hull bricks"));
+        const unsigned full = ncam >= 32 ? 0xffffffffu : ((1u << ncam) - 1u);
+        unsigned char* hb = static_cast<unsigned char*>(c->hull_bricks.p);
+        FR_CUDA(c, launch_hull_bricks(p->hull_tags, full, vol->nx, vol->ny, vol->nz, hb, c->stream));
+        a.p.occ = hb;
+        a.p.nbx = nbx;
+        a.p.nby = nby;
+    }
     FR_CUDA(c, cudaMemsetAsync(a.p.counter, 0, sizeof(unsigned long long), c->stream));
     FR_CUDA(c, launch_count(a, tiles_of(a.p.W, a.p.H, ncam), c->stream));
     FR_CUDA(c, cudaMemcpyAsync(c->host_counter, a.p.counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
@@ -269,6 +343,31 @@ extern "C" fr_status fr_count_samples(fr_ctx* c, const fr_volume* vol, const fr_
     FR_CUDA(c, cudaStreamSynchronize(c->stream));
     *samples = (int64_t)*c->host_counter;
     return FR_OK;
+}
+
+// Hull tags of a problem into `tags` (library scratch for the mask tables; the
+// cameras travel as launch parameters).
+static fr_status hull_tags(fr_ctx* c, const SingleArgs& a, const float* targets, float thresh, unsigned* tags)
+{
+    const ProbDev& P = a.p;
+    FR_TRY(ensure(c, c->sat, (size_t)P.ncam * (P.H + 1) * (P.W + 1) * sizeof(unsigned), "flame-mask tables"));
+    FR_CUDA(c, launch_visual_hull(a.cams, P.ncam, P.W, P.H, P.nx, P.ny, P.nz, targets, thresh,
+                                  static_cast<unsigned*>(c->sat.p), tags, c->stream));
+    return FR_OK;
+}
+
+extern "C" fr_status fr_visual_hull(fr_ctx* c, const fr_volume* vol, const fr_camera* cams, int ncam,
+                                    const float* targets, const fr_params* p, uint32_t* tags)
+{
+    FR_BEGIN(c);
+    FR_TRY(check_volume(c, vol, "vol"));
+    FR_TRY(check_cams(c, cams, ncam));
+    FR_TRY(check_params(c, p, vol, cams));
+    FR_TRY(check_dev(c, targets, image_bytes(cams, ncam), "targets"));
+    FR_TRY(check_dev(c, tags, (size_t)node_count(vol) * 4, "tags"));
+    static thread_local SingleArgs a;
+    fill_problem(vol, cams, ncam, p, a);
+    return hull_tags(c, a, targets, p->flame_thresh, reinterpret_cast<unsigned*>(tags));
 }
 
 // ---------------------------------------------------------------------------
@@ -320,6 +419,18 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
     FR_TRY(ensure(c, c->flame_off, flame_list_buf_entries(nt) * sizeof(unsigned), "flame offsets"));
     FR_TRY(ensure(c, c->flame_list, (size_t)npix * sizeof(unsigned), "flame list"));
     FR_TRY(ensure(c, c->pairs, (size_t)nodes * 2 * rec_bytes(vol), "pairs"));
+    const int nbx = bricks_along(vol->nx), nby = bricks_along(vol->ny), nbz = bricks_along(vol->nz);
+    unsigned char* occ = nullptr;
+    if (skips_empty(vol, p)) {
+        FR_TRY(ensure(c, c->occ, (size_t)nbx * nby * nbz, "brick occupancy"));
+        occ = static_cast<unsigned char*>(c->occ.p);
+    }
+    if (p->use_hull) {
+        if (vol->kind != FR_KIND_RGB) return fail(c, FR_EINVAL, "the visual hull applies to RGB volumes");
+        if (p->hull_tags) FR_TRY(check_dev(c, p->hull_tags, (size_t)nodes * 4, "hull_tags"));
+        else FR_TRY(ensure(c, c->hull, (size_t)nodes * 4, "hull"));
+        FR_TRY(ensure(c, c->hull_bricks, (size_t)nbx * nby * nbz, "hull bricks"));
+    }
     cudaStream_t s = c->stream;
     const float* tg = targets;
     if (targets_are_host) {
@@ -338,8 +449,13 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
     f.p.partials = static_cast<float*>(c->partials.p);
     f.p.rendered = p->rule == FR_RULE_GRADIENT ? static_cast<float*>(c->rendered.p) : nullptr;
     f.p.pairs = c->pairs.p;
+    f.p.occ = occ;
+    f.p.nbx = nbx;
+    f.p.nby = nby;
     u = f;
     u.p.pairs = nullptr;
+    u.p.occ = nullptr;
+    u.p.adj_occ = nullptr;
     u.p.targets = nullptr;
     u.p.partials = nullptr;
     u.p.residual = nullptr;
@@ -351,28 +467,56 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
     unsigned* flame_off = static_cast<unsigned*>(c->flame_off.p);
     unsigned* flame_list = static_cast<unsigned*>(c->flame_list.p);
     const unsigned* flame_count = flame_off + flame_list_total_at(nt);
+    FR_TRY(trace_mark(c, -1));
     FR_CUDA(c, launch_flame_list(f, nt, flame_off, flame_list, s));
+    const unsigned* hull = nullptr;
+    const unsigned full = ncam >= 32 ? 0xffffffffu : ((1u << ncam) - 1u);
+    if (p->use_hull) {
+        if (p->hull_tags) {
+            hull = p->hull_tags;
+        } else {
+            FR_TRY(hull_tags(c, f, tg, p->flame_thresh, static_cast<unsigned*>(c->hull.p)));
+            hull = static_cast<const unsigned*>(c->hull.p);
+        }
+        FR_CUDA(c, launch_hull_clear(vol->data, vol->dtype, nodes, hull, full, s));
+        if (p->skip_empty && p->rule == FR_RULE_PAPER && !(p->tau > 0.0f)) {
+            unsigned char* hb = static_cast<unsigned char*>(c->hull_bricks.p);
+            FR_CUDA(c, launch_hull_bricks(hull, full, vol->nx, vol->ny, vol->nz, hb, s));
+            u.p.adj_occ = hb;
+        }
+    }
+    FR_TRY(trace_mark(c, FR_PHASE_SETUP));
     for (int it = 0; it < iters; ++it) {
-        if (albedo)
+        if (albedo) {
             FR_CUDA(c, launch_scatter_source(vol->data, vol->dtype, albedo, static_cast<float*>(c->J.p), c->src.p,
                                              vol->dtype, vol->nx, vol->ny, vol->nz, s));
-        FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, s));
+            FR_TRY(trace_mark(c, FR_PHASE_SCATTER));
+        }
+        FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, occ, s));
+        FR_TRY(trace_mark(c, FR_PHASE_PACK));
         FR_CUDA(c, launch_fwd(f, vol->dtype, vol->kind, nt, s));
+        FR_TRY(trace_mark(c, FR_PHASE_FORWARD));
         FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * it, s));
+        FR_TRY(trace_mark(c, FR_PHASE_REDUCE));
         if (p->rule == FR_RULE_PAPER) {
             u.p.iteration = first_iteration + it;
             FR_CUDA(c, launch_adjust_list(u, vol->dtype, nt, flame_list, flame_count, s));
+            FR_TRY(trace_mark(c, FR_PHASE_ADJUST));
             FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg, 1, s));
         } else {
             // d(0.5 sum m dL^2)/d(rendered) = -m dL: the residual scaled by -1
             u.p.img_scale = -1.0f;
             u.p.L_total = static_cast<const float*>(c->rendered.p);
             FR_CUDA(c, launch_backward(u, vol->dtype, vol->kind, nt, s));
+            FR_TRY(trace_mark(c, FR_PHASE_ADJUST));
             FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, -p->grad_step,
                                     p->update_sigma, p->clamp_nonneg, 1, s));
         }
+        if (hull) FR_CUDA(c, launch_hull_clear(vol->data, vol->dtype, nodes, hull, full, s));
+        FR_TRY(trace_mark(c, FR_PHASE_APPLY));
     }
     FR_CUDA(c, launch_rmse(sq, iters, static_cast<float*>(c->rmse.p), s));
+    FR_TRY(trace_mark(c, FR_PHASE_FINISH));
     if (rmse) {
         if (rmse_is_host) {
             FR_CUDA(c, cudaMemcpyAsync(rmse, c->rmse.p, (size_t)iters * 12, cudaMemcpyDeviceToHost, s));

@@ -68,7 +68,16 @@ struct ProbDev {
     // x-pair records: pair i = {record i, record of its +x neighbour}; when
     // set, the forward march gathers a cell's corners two at a time from it
     const void* pairs;
+    // occupancy of 8^3-cell bricks (1 = some corner record of the brick is
+    // non-zero); when set, the forward march skips empty bricks
+    const unsigned char* occ;
+    // bricks holding a key point inside the visual hull; when set, the
+    // adjustment skips the others (their key points' updates are discarded)
+    const unsigned char* adj_occ;
+    int nbx, nby;                // bricks along x and y
 };
+
+constexpr int kBrick = 8;        // cells per brick edge
 
 // ---------------------------------------------------------------------------
 // Rays

@@ -127,9 +127,51 @@ __device__ __forceinline__ void load8_pairs(const void* pairs, long long base, i
 // and are reloaded only when the sample enters another cell.  (Reloading just
 // the four records of a crossed face costs more instructions than the L1
 // traffic it saves.)
-template <int DT, int KIND, bool TAU, bool PAIRS>
+// Skipping of flagged-off bricks along one ray.  A brick is the box of 8^3
+// cells [8b, min(8b + 8, n - 1)] per axis; `flags` holds one byte per brick
+// (non-zero: the samples in it are evaluated).
+struct BrickSkip {
+    int brick = -1;
+    bool occupied = true;
+    float idx, idy, idz;    // reciprocal direction
+
+    __device__ __forceinline__ explicit BrickSkip(const Ray& R)
+        : idx(1.0f / R.dx), idy(1.0f / R.dy), idz(1.0f / R.dz) {}
+
+    // True when sample k (midpoint x, y, z) lies in a flagged-off brick.  k
+    // then moves so that the loop's increment lands on the first sample whose
+    // midpoint may lie beyond that brick; a 1e-3 voxel margin on the exit
+    // keeps rounding on the safe side.
+    __device__ __forceinline__ bool empty(const unsigned char* flags, const ProbDev& P, const Ray& R, float step,
+                                          float x, float y, float z, int& k)
+    {
+        const CellIJK c = cell_ijk(x, y, z, P.nx, P.ny, P.nz);
+        const int b = ((c.k >> 3) * P.nby + (c.j >> 3)) * P.nbx + (c.i >> 3);
+        if (b != brick) {
+            brick = b;
+            occupied = __ldg(flags + b) != 0;
+        }
+        if (occupied) return false;
+        const int bx = c.i & ~(kBrick - 1), by = c.j & ~(kBrick - 1), bz = c.k & ~(kBrick - 1);
+        float te = INFINITY;
+        if (R.dx != 0.0f) te = fminf(te, ((R.dx > 0.0f ? (float)min(bx + kBrick, P.nx - 1) : (float)bx) - R.p0x) * idx);
+        if (R.dy != 0.0f) te = fminf(te, ((R.dy > 0.0f ? (float)min(by + kBrick, P.ny - 1) : (float)by) - R.p0y) * idy);
+        if (R.dz != 0.0f) te = fminf(te, ((R.dz > 0.0f ? (float)min(bz + kBrick, P.nz - 1) : (float)bz) - R.p0z) * idz);
+        const int kn = (int)ceilf((te - 1e-3f) / step - 0.5f);
+        k = max(k, kn - 1);
+        return true;
+    }
+};
+
+// MODE 0: records gathered one by one; 1: from x-pair records; 2: x-pair
+// records and exact skipping of empty bricks (RGB field mode only: a sample
+// whose eight corner records are all zero adds exactly nothing and leaves the
+// transmittance unchanged, so skipping it does not change the result).
+template <int DT, int KIND, bool TAU, int MODE>
 __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, int tile)
 {
+    constexpr bool PAIRS = MODE >= 1;
+    constexpr bool SKIP = MODE == 2 && KIND == KIND_RGB && !TAU;
     using RT = typename RecOf<DT, KIND>::T;
     int view, px, py;
     tile_pixel(P, tile, view, px, py);
@@ -142,9 +184,13 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
             RT v[8];
             long long vbase = -1;
             float T = 1.0f;
+            BrickSkip skip(R);
             for (int k = 0; k < R.n; ++k) {
                 float len, x, y, z;
                 segment(R, P.step, k, len, x, y, z);
+                if constexpr (SKIP) {
+                    if (skip.empty(P.occ, P, R, P.step, x, y, z, k)) continue;
+                }
                 const Cell c = cell_of(x, y, z, P.nx, P.ny, P.nz);
                 if (c.base != vbase) {
                     vbase = c.base;
@@ -206,20 +252,20 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
     }
 }
 
-template <int DT, int KIND, bool TAU, bool PAIRS>
+template <int DT, int KIND, bool TAU, int MODE>
 __global__ void FR_MARCH_BOUNDS fwd_single(const __grid_constant__ SingleArgs a)
 {
-    fwd_body<DT, KIND, TAU, PAIRS>(a.p, a.cams, blockIdx.x);
+    fwd_body<DT, KIND, TAU, MODE>(a.p, a.cams, blockIdx.x);
 }
 
-template <int DT, int KIND, bool TAU, bool PAIRS>
+template <int DT, int KIND, bool TAU, int MODE>
 __global__ void FR_MARCH_BOUNDS fwd_batch(const ProbDev* __restrict__ probs,
                                                                           const int* __restrict__ tile_start,
                                                                           int nprob)
 {
     const int p = find_problem(tile_start, nprob, blockIdx.x);
     const ProbDev& P = probs[p];
-    fwd_body<DT, KIND, TAU, PAIRS>(P, P.cams, blockIdx.x - __ldg(tile_start + p));
+    fwd_body<DT, KIND, TAU, MODE>(P, P.cams, blockIdx.x - __ldg(tile_start + p));
 }
 
 // ---------------------------------------------------------------------------
@@ -229,10 +275,14 @@ __global__ void FR_MARCH_BOUNDS fwd_batch(const ProbDev* __restrict__ probs,
 // dL is constant along a ray, so each key point collects the scalar sum of
 // G alpha_l T exp(-alpha_d D) over the ray's samples in its window slot and
 // receives that sum times dL when the ray leaves it.
-template <int DT, bool TAU>
+template <int DT, bool TAU, bool SKIP = false>
 __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, int view, int px, int py,
                                         int iteration)
 {
+    // SKIP: samples in bricks with no key point inside the visual hull are
+    // skipped.  Their records are zero (no extinction: T is unchanged) and
+    // their key points' updates are discarded after the update, so the
+    // result is the same.
     const long long pix = ((long long)view * P.H + py) * P.W + px;
     const float* g = P.img_in + 3 * pix;
     const float dl0 = g[0] * P.img_scale, dl1 = g[1] * P.img_scale, dl2 = g[2] * P.img_scale;
@@ -258,9 +308,13 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
     Win W;
     W.live = false;
     float T = 1.0f;
+    BrickSkip skip(R);
     for (int k = 0; k < R.n; ++k) {
         float len, x, y, z;
         segment(R, P.step, k, len, x, y, z);
+        if constexpr (SKIP) {
+            if (skip.empty(P.adj_occ, P, R, P.step, x, y, z, k)) continue;
+        }
         const CellIJK c = cell_ijk(x, y, z, P.nx, P.ny, P.nz);
         win_move(W, c.i, c.j, c.k, P.nx, P.ny, nxy32, leave, enter);
         const float gx = mirror_frac(c.i, c.fx), gy = mirror_frac(c.j, c.fy), gz = mirror_frac(c.k, c.fz);
@@ -291,7 +345,7 @@ __device__ __forceinline__ void adj_body(const ProbDev& P, const CamDev* cams, i
 // The same over a compacted list of flame rays (linear pixel indices in tile
 // order, so a warp's 32 rays are neighbours): no lane idles on a non-flame
 // pixel.  CTA b takes list entries [128 b, 128 b + 128).
-template <int DT, bool TAU>
+template <int DT, bool TAU, bool SKIP>
 __global__ void FR_MARCH_BOUNDS adj_list(const __grid_constant__ SingleArgs a, const unsigned* __restrict__ list,
                                          const unsigned* __restrict__ count)
 {
@@ -303,7 +357,7 @@ __global__ void FR_MARCH_BOUNDS adj_list(const __grid_constant__ SingleArgs a, c
     const int view = (int)(pix / per_view);
     const unsigned r = pix - (unsigned)view * per_view;
     const int py = (int)(r / (unsigned)P.W), px = (int)(r - (unsigned)py * (unsigned)P.W);
-    adj_ray<DT, TAU>(P, a.cams, view, px, py, P.iteration);
+    adj_ray<DT, TAU, SKIP>(P, a.cams, view, px, py, P.iteration);
 }
 
 // Batched form: CTA b belongs to the problem whose tile range holds b and
@@ -457,7 +511,19 @@ __global__ void __launch_bounds__(kTileThreads) count_single(const __grid_consta
             use = !(g[0] == 0.0f && g[1] == 0.0f && g[2] == 0.0f);
         }
         Ray R;
-        if (use && make_ray(a.cams[view], px, py, P.nx, P.ny, P.nz, P.step, R)) n = (unsigned)R.n;
+        if (use && make_ray(a.cams[view], px, py, P.nx, P.ny, P.nz, P.step, R)) {
+            if (P.occ) {
+                // the samples the forward march evaluates when it skips empty bricks
+                BrickSkip skip(R);
+                for (int k = 0; k < R.n; ++k) {
+                    float len, x, y, z;
+                    segment(R, P.step, k, len, x, y, z);
+                    if (!skip.empty(P.occ, P, R, P.step, x, y, z, k)) ++n;
+                }
+            } else {
+                n = (unsigned)R.n;
+            }
+        }
     }
     const unsigned s = __reduce_add_sync(0xffffffffu, n);
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(P.counter, (unsigned long long)s);
@@ -614,11 +680,12 @@ __global__ void __launch_bounds__(1024) finalize_batch(const ProbDev* __restrict
 cudaError_t launch_fwd(const SingleArgs& a, int dt, int kind, int ntiles, cudaStream_t s)
 {
     const bool tau = a.p.tau > 0.0f;
-    const bool pairs = a.p.pairs != nullptr;
+    const int mode = a.p.pairs == nullptr ? 0 : (a.p.occ != nullptr && kind == KIND_RGB && !tau ? 2 : 1);
     dim3 grid(ntiles), block(kTileThreads);
 #define FR_FWD(D, K, T)                                                            \
-    if (pairs) fwd_single<D, K, T, true><<<grid, block, 0, s>>>(a);                \
-    else fwd_single<D, K, T, false><<<grid, block, 0, s>>>(a)
+    if (mode == 2) fwd_single<D, K, T, 2><<<grid, block, 0, s>>>(a);               \
+    else if (mode == 1) fwd_single<D, K, T, 1><<<grid, block, 0, s>>>(a);          \
+    else fwd_single<D, K, T, 0><<<grid, block, 0, s>>>(a)
     FR_DISPATCH_DT(dt, D, {
         if (kind == KIND_RGB) {
             if (tau) { FR_FWD(D, KIND_RGB, true); } else { FR_FWD(D, KIND_RGB, false); }
@@ -635,8 +702,8 @@ cudaError_t launch_fwd_batch(const ProbDev* probs, const int* tile_start, int np
 {
     dim3 grid(total_tiles), block(kTileThreads);
 #define FR_FWDB(D, K, T)                                                                        \
-    if (pairs) fwd_batch<D, K, T, true><<<grid, block, 0, s>>>(probs, tile_start, nprob);        \
-    else fwd_batch<D, K, T, false><<<grid, block, 0, s>>>(probs, tile_start, nprob)
+    if (pairs) fwd_batch<D, K, T, 1><<<grid, block, 0, s>>>(probs, tile_start, nprob);           \
+    else fwd_batch<D, K, T, 0><<<grid, block, 0, s>>>(probs, tile_start, nprob)
     FR_DISPATCH_DT(dt, D, {
         if (kind == KIND_RGB) {
             if (tau) { FR_FWDB(D, KIND_RGB, true); } else { FR_FWDB(D, KIND_RGB, false); }
@@ -733,9 +800,11 @@ cudaError_t launch_adjust_list(const SingleArgs& a, int dt, int ntiles, const un
 {
     const bool tau = a.p.tau > 0.0f;
     dim3 grid(ntiles), block(kTileThreads);
+    const bool skip = a.p.adj_occ != nullptr && !tau;
     FR_DISPATCH_DT(dt, D, {
-        if (tau) adj_list<D, true><<<grid, block, 0, s>>>(a, list, count);
-        else adj_list<D, false><<<grid, block, 0, s>>>(a, list, count);
+        if (tau) adj_list<D, true, false><<<grid, block, 0, s>>>(a, list, count);
+        else if (skip) adj_list<D, false, true><<<grid, block, 0, s>>>(a, list, count);
+        else adj_list<D, false, false><<<grid, block, 0, s>>>(a, list, count);
     });
     return cudaGetLastError();
 }

@@ -121,8 +121,22 @@ cudaError_t launch_rmse_batch(const ProbDev* probs, int nprob, int iters, float*
 
 // x-pair records: pair i = {record i, record i + 1}, the second copy of the
 // last node of a row repeating it (no cell uses it).  One CTA per row.
+// Marks, for a non-zero record at node (x, y, z), every brick of 8^3 cells
+// whose corner records include it (a node on a brick boundary belongs to the
+// bricks on both sides).  Stores only ones; the flags are cleared beforehand.
+__device__ __forceinline__ void mark_bricks(unsigned char* occ, int x, int y, int z, int nbx, int nby, int nbz)
+{
+    const int bx0 = (x > 0 && (x & 7) == 0) ? (x >> 3) - 1 : (x >> 3);
+    const int by0 = (y > 0 && (y & 7) == 0) ? (y >> 3) - 1 : (y >> 3);
+    const int bz0 = (z > 0 && (z & 7) == 0) ? (z >> 3) - 1 : (z >> 3);
+    for (int bz = bz0; bz <= min(z >> 3, nbz - 1); ++bz)
+        for (int by = by0; by <= min(y >> 3, nby - 1); ++by)
+            for (int bx = bx0; bx <= min(x >> 3, nbx - 1); ++bx) occ[((long long)bz * nby + by) * nbx + bx] = 1;
+}
+
 template <int DT, int KIND>
-__global__ void __launch_bounds__(256) pair_pack_kernel(const void* src, void* dst, long long rows, int nx)
+__global__ void __launch_bounds__(256) pair_pack_kernel(const void* src, void* dst, long long rows, int nx, int ny,
+                                                        unsigned char* occ, int nbx, int nby, int nbz)
 {
     for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
         const long long r0 = row * nx;
@@ -132,12 +146,18 @@ __global__ void __launch_bounds__(256) pair_pack_kernel(const void* src, void* d
                 if constexpr (DT == DT_F32) {
                     const float4* s4 = reinterpret_cast<const float4*>(src);
                     float4* d4 = reinterpret_cast<float4*>(dst);
-                    d4[2 * i] = __ldg(s4 + i);
+                    const float4 a = __ldg(s4 + i);
+                    d4[2 * i] = a;
                     d4[2 * i + 1] = __ldg(s4 + j);
+                    if (occ && (a.x != 0.0f || a.y != 0.0f || a.z != 0.0f || a.w != 0.0f))
+                        mark_bricks(occ, x, (int)(row % ny), (int)(row / ny), nbx, nby, nbz);
                 } else {
                     const uint2* s2 = reinterpret_cast<const uint2*>(src);
                     const uint2 a = __ldg(s2 + i), b = __ldg(s2 + j);
                     reinterpret_cast<uint4*>(dst)[i] = make_uint4(a.x, a.y, b.x, b.y);
+                    // +0 and -0 both read as empty
+                    if (occ && (((a.x | a.y) & 0x7fff7fffu) != 0u))
+                        mark_bricks(occ, x, (int)(row % ny), (int)(row / ny), nbx, nby, nbz);
                 }
             } else {
                 if constexpr (DT == DT_F32) {
@@ -189,11 +209,17 @@ cudaError_t launch_pair_pack_batch(const ProbDev* probs, int nprob, int dt, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int nx, int ny, int nz, cudaStream_t s)
+cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int nx, int ny, int nz,
+                             unsigned char* occ, cudaStream_t s)
 {
     const long long rows = (long long)ny * nz;
     const int g = (int)(rows < 152LL * 32 ? rows : 152LL * 32);
-#define FR_PACK(D, K) pair_pack_kernel<D, K><<<g, 256, 0, s>>>(src, dst, rows, nx)
+    const int nbx = (nx - 2) / kBrick + 1, nby = (ny - 2) / kBrick + 1, nbz = (nz - 2) / kBrick + 1;
+    if (occ) {
+        cudaError_t e = cudaMemsetAsync(occ, 0, (size_t)nbx * nby * nbz, s);
+        if (e != cudaSuccess) return e;
+    }
+#define FR_PACK(D, K) pair_pack_kernel<D, K><<<g, 256, 0, s>>>(src, dst, rows, nx, ny, occ, nbx, nby, nbz)
     if (kind == KIND_RGB) {
         if (dt == DT_F32) FR_PACK(DT_F32, KIND_RGB);
         else if (dt == DT_BF16) FR_PACK(DT_BF16, KIND_RGB);
@@ -560,6 +586,159 @@ cudaError_t launch_prepare_targets(float* targets, int ncam, int H, int W, float
     long long npx = (long long)W * H;
     dim3 grid((unsigned)((npx + 255) / 256), ncam);
     prepare_kernel<<<grid, 256, 0, s>>>(targets, W, H, thresh, bbox);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Visual hull (Sec. 4.3.1, Algorithm 1)
+// ---------------------------------------------------------------------------
+
+// Summed-area table of the flame mask: sat[v][y+1][x+1] = number of flame
+// pixels in [0, x] x [0, y] of view v (row 0 and column 0 are zero).
+__global__ void sat_rows_kernel(const float* targets, int ncam, int W, int H, float thresh, unsigned* sat)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ncam * (H + 1)) return;
+    const int v = r / (H + 1), y = r - v * (H + 1);
+    unsigned* row = sat + (size_t)r * (W + 1);
+    row[0] = 0;
+    unsigned acc = 0;
+    for (int x = 0; x < W; ++x) {
+        if (y > 0) {
+            const float* t = targets + 3 * (((size_t)v * H + (y - 1)) * W + x);
+            acc += fmaxf(t[0], fmaxf(t[1], t[2])) > thresh ? 1u : 0u;
+        }
+        row[x + 1] = acc;
+    }
+}
+
+__global__ void sat_cols_kernel(int ncam, int W, int H, unsigned* sat)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncam * (W + 1)) return;
+    const int v = c / (W + 1), x = c - v * (W + 1);
+    unsigned* base = sat + (size_t)v * (H + 1) * (W + 1) + x;
+    unsigned acc = 0;
+    for (int y = 0; y <= H; ++y) {
+        acc += base[(size_t)y * (W + 1)];
+        base[(size_t)y * (W + 1)] = acc;
+    }
+}
+
+__device__ __forceinline__ float dot3_rn(float x, float y, float z, const float r[3])
+{
+    return __fadd_rn(__fadd_rn(__fmul_rn(x, r[0]), __fmul_rn(y, r[1])), __fmul_rn(z, r[2]));
+}
+
+// One thread per node; `cams` carries o (voxel units), r, u, f, tx, ty, W, H.
+struct HullCams {
+    CamDev c[kMaxViews];
+};
+
+__global__ void __launch_bounds__(256) hull_kernel(const __grid_constant__ HullCams cams, int ncam, int nx, int ny,
+                                                   int nz, const unsigned* __restrict__ sat,
+                                                   unsigned* __restrict__ tags)
+{
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long nodes = (long long)nx * ny * nz;
+    if (idx >= nodes) return;
+    const int i = (int)(idx % nx), j = (int)((idx / nx) % ny), k = (int)(idx / ((long long)nx * ny));
+    const int lo[3] = {max(i - 1, 0), max(j - 1, 0), max(k - 1, 0)};
+    const int hi[3] = {min(i + 1, nx - 1), min(j + 1, ny - 1), min(k + 1, nz - 1)};
+    unsigned tag = 0;
+    size_t sat_off = 0;
+    for (int v = 0; v < ncam; ++v) {
+        const CamDev& c = cams.c[v];
+        const int W = c.W, H = c.H;
+        const float hw = 0.5f * (float)W, hh = 0.5f * (float)H;
+        float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+        bool behind = false;
+        for (int b = 0; b < 8; ++b) {
+            const float X = __fsub_rn((float)((b & 1) ? hi[0] : lo[0]), c.o[0]);
+            const float Y = __fsub_rn((float)((b & 2) ? hi[1] : lo[1]), c.o[1]);
+            const float Z = __fsub_rn((float)((b & 4) ? hi[2] : lo[2]), c.o[2]);
+            const float xc = dot3_rn(X, Y, Z, c.r), yc = dot3_rn(X, Y, Z, c.u), zc = dot3_rn(X, Y, Z, c.f);
+            if (!(zc > 0.0f)) { behind = true; break; }
+            const float uu = __fsub_rn(__fmul_rn(__fadd_rn(__fdiv_rn(__fdiv_rn(xc, zc), c.tx), 1.0f), hw), 0.5f);
+            const float vv = __fsub_rn(__fmul_rn(__fsub_rn(1.0f, __fdiv_rn(__fdiv_rn(yc, zc), c.ty)), hh), 0.5f);
+            umin = fminf(umin, uu); umax = fmaxf(umax, uu);
+            vmin = fminf(vmin, vv); vmax = fmaxf(vmax, vv);
+        }
+        int x0 = 0, x1 = W - 1, y0 = 0, y1 = H - 1;
+        if (!behind) {
+            const float cx0 = ceilf(umin), cx1 = floorf(umax), cy0 = ceilf(vmin), cy1 = floorf(vmax);
+            x0 = cx0 > 0.0f ? (cx0 < (float)W ? (int)cx0 : W) : 0;
+            x1 = cx1 < (float)(W - 1) ? (cx1 >= -1.0f ? (int)cx1 : -1) : W - 1;
+            y0 = cy0 > 0.0f ? (cy0 < (float)H ? (int)cy0 : H) : 0;
+            y1 = cy1 < (float)(H - 1) ? (cy1 >= -1.0f ? (int)cy1 : -1) : H - 1;
+        }
+        if (x0 <= x1 && y0 <= y1) {
+            const unsigned* S = sat + sat_off;
+            const size_t w1 = (size_t)W + 1;
+            const unsigned cnt = S[(size_t)(y1 + 1) * w1 + (x1 + 1)] - S[(size_t)y0 * w1 + (x1 + 1)] -
+                                 S[(size_t)(y1 + 1) * w1 + x0] + S[(size_t)y0 * w1 + x0];
+            if (cnt) tag |= 1u << v;
+        }
+        sat_off += (size_t)(H + 1) * (W + 1);
+    }
+    tags[idx] = tag;
+}
+
+cudaError_t launch_visual_hull(const CamDev* cams, int ncam, int W, int H, int nx, int ny, int nz,
+                               const float* targets, float thresh, unsigned* sat, unsigned* tags, cudaStream_t s)
+{
+    HullCams hc;
+    for (int v = 0; v < ncam; ++v) hc.c[v] = cams[v];
+    const int rows = ncam * (H + 1), cols = ncam * (W + 1);
+    sat_rows_kernel<<<(rows + 127) / 128, 128, 0, s>>>(targets, ncam, W, H, thresh, sat);
+    sat_cols_kernel<<<(cols + 127) / 128, 128, 0, s>>>(ncam, W, H, sat);
+    const long long nodes = (long long)nx * ny * nz;
+    hull_kernel<<<(unsigned)((nodes + 255) / 256), 256, 0, s>>>(hc, ncam, nx, ny, nz, sat, tags);
+    return cudaGetLastError();
+}
+
+// Bricks of 8^3 cells holding at least one key point inside the hull.
+__global__ void __launch_bounds__(256) hull_bricks_kernel(const unsigned* __restrict__ tags, unsigned full, int nx,
+                                                          int ny, int nz, unsigned char* flags, int nbx, int nby,
+                                                          int nbz)
+{
+    const long long nodes = (long long)nx * ny * nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (__ldg(tags + i) != full) continue;
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+        mark_bricks(flags, x, y, z, nbx, nby, nbz);
+    }
+}
+
+cudaError_t launch_hull_bricks(const unsigned* tags, unsigned full, int nx, int ny, int nz, unsigned char* flags,
+                               cudaStream_t s)
+{
+    const int nbx = bricks_along(nx), nby = bricks_along(ny), nbz = bricks_along(nz);
+    cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)nbx * nby * nbz, s);
+    if (e != cudaSuccess) return e;
+    const long long nodes = (long long)nx * ny * nz;
+    hull_bricks_kernel<<<grid_for(nodes, 256), 256, 0, s>>>(tags, full, nx, ny, nz, flags, nbx, nby, nbz);
+    return cudaGetLastError();
+}
+
+// Records outside the hull (tag != full) are set to 0: no emission, no extinction.
+template <int DT>
+__global__ void __launch_bounds__(256) hull_clear_kernel(void* vol, long long nodes, const unsigned* tags,
+                                                         unsigned full)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (tags[i] != full) store_rgb<DT>(vol, i, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+    }
+}
+
+cudaError_t launch_hull_clear(void* vol, int dt, long long nodes, const unsigned* tags, unsigned full, cudaStream_t s)
+{
+    const int g = grid_for(nodes, 256);
+    if (dt == DT_F32) hull_clear_kernel<DT_F32><<<g, 256, 0, s>>>(vol, nodes, tags, full);
+    else if (dt == DT_BF16) hull_clear_kernel<DT_BF16><<<g, 256, 0, s>>>(vol, nodes, tags, full);
+    else hull_clear_kernel<DT_F16><<<g, 256, 0, s>>>(vol, nodes, tags, full);
     return cudaGetLastError();
 }
 

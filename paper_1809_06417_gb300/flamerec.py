@@ -14,14 +14,16 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libflamerec.so")
 
-FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_ETIMEDOUT, FR_EBUSY, FR_ECANCELED = range(7)
+FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_ETIMEDOUT, FR_EBUSY, FR_ECANCELED, FR_ERANGE = range(8)
 FR_F32, FR_BF16, FR_F16 = 0, 1, 2
 FR_KIND_RGB, FR_KIND_TEMP = 0, 1
 FR_RULE_PAPER, FR_RULE_GRADIENT = 0, 1
 FR_MAX_VIEWS = 32
+PHASES = ("setup", "scatter", "pack", "forward", "reduce", "adjust", "apply", "finish")
+FR_PHASE_COUNT = len(PHASES)
 
 STATUS_NAMES = {0: "FR_OK", 1: "FR_EINVAL", 2: "FR_ENOMEM", 3: "FR_ECUDA", 4: "FR_ETIMEDOUT",
-                5: "FR_EBUSY", 6: "FR_ECANCELED"}
+                5: "FR_EBUSY", 6: "FR_ECANCELED", 7: "FR_ERANGE"}
 
 
 class FrError(RuntimeError):
@@ -69,7 +71,8 @@ class fr_params(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("clamp_nonneg", ctypes.c_int32), ("rule", ctypes.c_int32),
                 ("grad_step", ctypes.c_float), ("update_sigma", ctypes.c_int32),
                 ("lut_t_min", ctypes.c_float), ("lut_t_max", ctypes.c_float), ("lut", ctypes.c_void_p),
-                ("lut_size", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("lut_size", ctypes.c_int32), ("use_hull", ctypes.c_int32),
+                ("skip_empty", ctypes.c_int32), ("hull_tags", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p
@@ -97,6 +100,7 @@ SIGNATURES = {
     "fr_reconstruct": (_S, [_P, _P, _P, _P, _I, _P, _I, _P, _I, _I, _P, _P, _I]),
     "fr_count_samples": (_S, [_P, _P, _P, _I, _P, _P, _P]),
     "fr_reconstruct_batch": (_S, [_P, _P, _I, _I, _I, _P, _I]),
+    "fr_visual_hull": (_S, [_P, _P, _P, _I, _P, _P, _P]),
     "fr_server_create": (_S, [_P, _P, _I, ctypes.c_size_t, _P]),
     "fr_server_destroy": (_S, [_P]),
     "fr_server_submit": (_S, [_P, _P, _P]),
@@ -106,6 +110,8 @@ SIGNATURES = {
     "fr_job_cancel": (_S, [_P, _P]),
     "fr_job_release": (_S, [_P, _P]),
     "fr_server_memory": (_S, [_P, _P, _P]),
+    "fr_trace_phases": (_S, [_P, _I]),
+    "fr_phase_times": (_S, [_P, _P, _I, _P]),
     "fr_render_residual_noalloc": (_S, [_I, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, ctypes.c_char_p,
                                         ctypes.c_size_t]),
 }
@@ -148,6 +154,9 @@ def params(**kw) -> fr_params:
             p.lut = _ptr(v)
             if v is not None:
                 p.lut_size = int(v.shape[0])
+            continue
+        if k == "hull_tags":
+            p.hull_tags = _ptr(v)
             continue
         if not hasattr(p, k):
             raise AttributeError(f"fr_params has no field {k}")
@@ -274,6 +283,16 @@ class Context:
                                            int(first_iteration), ctypes.byref(p), _ptr(rmse),
                                            int(rmse_is_host)))
 
+    def fr_trace_phases(self, on=True):
+        self.check(self.lib.fr_trace_phases(self.h, int(bool(on))))
+
+    def fr_phase_times(self):
+        """(dict phase name -> milliseconds summed over the recorded calls, calls)."""
+        ms = (ctypes.c_float * FR_PHASE_COUNT)()
+        calls = ctypes.c_int32()
+        self.check(self.lib.fr_phase_times(self.h, ms, FR_PHASE_COUNT, ctypes.byref(calls)))
+        return dict(zip(PHASES, list(ms))), calls.value
+
     def fr_count_samples(self, vol, cams, p, residual=None):
         n = ctypes.c_int64()
         self.check(self.lib.fr_count_samples(self.h, ctypes.byref(vol), cams, len(cams), ctypes.byref(p),
@@ -292,6 +311,10 @@ class Context:
             keep.append(cams)
         self.check(self.lib.fr_reconstruct_batch(self.h, arr, len(problems), int(iters), int(first_iteration),
                                                  ctypes.byref(p), int(bool(use_graph))))
+
+    def fr_visual_hull(self, vol, cams, targets, p, tags):
+        self.check(self.lib.fr_visual_hull(self.h, ctypes.byref(vol), cams, len(cams), _ptr(targets),
+                                           ctypes.byref(p), _ptr(tags)))
 
     def fr_synchronize(self):
         self.check(self.lib.fr_synchronize(self.h))

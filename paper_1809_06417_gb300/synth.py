@@ -74,8 +74,14 @@ def _node_coords(n: int):
     return a[:, None, None], a[None, :, None], a[None, None, :]
 
 
+# Profiles are cut to zero below this fraction of their peak, so a flame has
+# compact support (empty space around it holds exact zeros).
+SUPPORT_CUT = 1e-3
+
+
 def _gauss(z, y, x, c, s):
-    return np.exp(-((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2) / (2.0 * s * s))
+    g = np.exp(-((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2) / (2.0 * s * s))
+    return np.where(g < SUPPORT_CUT, 0.0, g)
 
 
 def value_noise(n: int, rng: np.random.Generator, octaves: int = 4, base_cells: int = 4):

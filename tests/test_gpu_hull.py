@@ -1,0 +1,132 @@
+"""Visual hull (Sec. 4.3.1, Algorithm 1) on the GPU: tags equal the oracle's bit
+for bit (the projection is a float32 integer decision taken in the same
+precision and order on both sides), at small and full size; the
+reconstruction loop restricted to the hull follows the oracle."""
+import numpy as np
+import pytest
+
+from gpu_cases import plume_case, rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fr_ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_06417_gb300 import flamerec as fr
+    ctx = fr.Context(0)
+    yield fr, ctx
+    torch.cuda.synchronize()
+    ctx.close()
+
+
+def _gpu_tags(fr, ctx, shape, origin, h, cams, targets, thresh):
+    nx, ny, nz = shape
+    vol = torch.zeros((nz, ny, nx, 4), device="cuda")
+    tags = torch.zeros((nz, ny, nx), dtype=torch.int32, device="cuda")
+    t = torch.as_tensor(np.ascontiguousarray(targets), dtype=torch.float32, device="cuda")
+    ctx.fr_visual_hull(fr.volume(vol, origin, h), fr.cameras(cams), t, fr.params(flame_thresh=thresh), tags)
+    torch.cuda.synchronize()
+    return tags.cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_hull_tags_bit_exact_random_masks(orc, fr_ctx, seed):
+    fr, ctx = fr_ctx
+    from paper_1809_06417_gb300 import synth
+    rng = np.random.default_rng(seed)
+    shape = (19, 23, 17)
+    h = 1.0 / 22
+    origin = tuple(-0.5 * (s - 1) * h for s in shape)
+    cams = synth.ring_cameras(7, 45, 38, elevation_jitter_deg=20.0, seed=seed)
+    targets = rng.random((7, 38, 45, 3)) * (rng.random((7, 38, 45, 1)) < 0.2)
+    thresh = 0.3
+    mask = (targets.max(axis=-1) > thresh).astype(np.uint8)
+    ref = orc.visual_hull(orc.Scene(shape, origin, h, cams), mask)
+    got = _gpu_tags(fr, ctx, shape, origin, h, cams, targets.astype(np.float32), thresh)
+    assert np.array_equal(got, ref), np.argwhere(got != ref)[:5]
+
+
+def test_hull_tags_bit_exact_full_size(orc, fr_ctx):
+    fr, ctx = fr_ctx
+    from paper_1809_06417_gb300 import synth
+    n, views, side = 128, 8, 512
+    shape, origin, h = synth.unit_grid(n)
+    cams = synth.ring_cameras(views, side, side, elevation_jitter_deg=10.0, seed=2)
+    gt, _ = synth.plume_volume(n, 2)
+    g = torch.as_tensor(gt, dtype=torch.float32, device="cuda").contiguous()
+    img = torch.zeros((views, side, side, 3), device="cuda")
+    ctx.fr_render(fr.volume(g, origin, h), fr.cameras(cams), fr.params(step=0.5), img)
+    img /= img.max()
+    targets = img.cpu().numpy()
+    thresh = 30 / 255
+    mask = (targets.max(axis=-1) > thresh).astype(np.uint8)
+    ref = orc.visual_hull(orc.Scene(shape, origin, h, cams), mask)
+    got = _gpu_tags(fr, ctx, shape, origin, h, cams, targets, thresh)
+    assert np.array_equal(got, ref)
+    inside = (got == (1 << views) - 1).mean()
+    print(f"hull fraction of the volume: {inside:.3f}")
+    assert 0.01 < inside < 0.6
+
+
+def test_reconstruct_with_hull_follows_oracle(orc, fr_ctx):
+    fr, ctx = fr_ctx
+    case = plume_case(n=36, views=6, side=64)
+    sc = orc.Scene(case.shape, case.origin, case.h, case.cams)
+    P = orc.make_params(step=case.step, alpha_l=3e-3)
+    img, _ = orc.render(sc, case.vol, P)
+    img /= img.max()
+    t_ref, mask, bbox_ref = orc.prepare_targets(img, 30 / 255)
+    hull = orc.visual_hull(sc, mask)
+    v0 = case.vol.copy()
+    v0[..., :3] = 0.01
+    vol_ref, rmse_ref, _ = orc.reconstruct(sc, v0, P, t_ref, mask, bbox_ref, 4, hull=hull)
+    t_dev = torch.as_tensor(img, dtype=torch.float32, device="cuda").contiguous()
+    bbox = torch.zeros((len(case.cams), 4), dtype=torch.int32, device="cuda")
+    ctx.fr_prepare_targets(t_dev, 30 / 255, bbox)
+    v = torch.as_tensor(v0, dtype=torch.float32, device="cuda").contiguous()
+    rmse = np.zeros((4, 3), dtype=np.float32)
+    ctx.fr_reconstruct(fr.volume(v, case.origin, case.h), fr.cameras(case.cams), t_dev, bbox, 4,
+                       fr.params(step=case.step, alpha_l=3e-3, use_hull=1), rmse=rmse)
+    torch.cuda.synchronize()
+    got = v.cpu().numpy()
+    outside = hull != (1 << len(case.cams)) - 1
+    assert np.all(got[outside] == 0.0)                       # no flame outside the hull
+    assert np.array_equal(got[~outside][:, 3], v0[~outside][:, 3].astype(np.float32))
+    np.testing.assert_allclose(rmse, rmse_ref, rtol=1e-3)
+    e = rel_err(got[..., :3], vol_ref[..., :3])
+    print(f"reconstruct with hull: max {e.max():.3e}, outside fraction {outside.mean():.3f}")
+    assert e.max() < 1e-3
+
+
+def test_reconstruct_with_precomputed_tags_is_identical(fr_ctx):
+    """Tags passed in (from fr_visual_hull) give the same iterations as tags
+    fr_reconstruct computes itself (up to the order of the adjustment's
+    atomic sums, which differs from run to run)."""
+    fr, ctx = fr_ctx
+    case = plume_case(n=40, views=5, side=72)
+    img = torch.zeros((5, 72, 72, 3), device="cuda")
+    g = torch.as_tensor(case.vol, dtype=torch.float32, device="cuda").contiguous()
+    fc = fr.cameras(case.cams)
+    ctx.fr_render(fr.volume(g, case.origin, case.h), fc, fr.params(step=case.step), img)
+    img /= img.max()
+    bbox = torch.zeros((5, 4), dtype=torch.int32, device="cuda")
+    ctx.fr_prepare_targets(img, 30 / 255, bbox)
+    tags = torch.zeros(g.shape[:3], dtype=torch.int32, device="cuda")
+    ctx.fr_visual_hull(fr.volume(g, case.origin, case.h), fc, img, fr.params(), tags)
+    out = []
+    for pre in (None, tags):
+        v = g.clone()
+        v[..., :3] = 0.01
+        rmse = np.zeros((3, 3), dtype=np.float32)
+        ctx.fr_reconstruct(fr.volume(v, case.origin, case.h), fc, img, bbox, 3,
+                           fr.params(step=case.step, alpha_l=3e-3, use_hull=1, hull_tags=pre), rmse=rmse)
+        torch.cuda.synchronize()
+        out.append((v, rmse))
+    a, b = (o[0].cpu().numpy() for o in out)
+    assert np.array_equal(a == 0, b == 0)
+    assert np.max(rel_err(a, b)) < 1e-5
+    np.testing.assert_allclose(out[0][1], out[1][1], rtol=1e-5)
