@@ -31,7 +31,9 @@ def nvcc() -> str:
 def _flags(extra=()):
     # FR_NVCC_FLAGS: extra nvcc options (e.g. -DFR_MARCH_MINB=6 to cap march registers)
     user = os.environ.get("FR_NVCC_FLAGS", "").split()
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+    # -ftz=true: single-precision denormals flush to zero (no denormal paths
+    # around the exp / rsqrt of the marches)
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-ftz=true", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                    "-I", CSRC, *user, *extra]
 
 

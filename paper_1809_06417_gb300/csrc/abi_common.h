@@ -30,7 +30,7 @@ struct fr_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;   // where work is queued (borrowed; 0 = default stream)
     char err[512] = {0};             // last failure message
-    Buf partials, counter, residual, rendered, dV, targets, sqerr, rmse, J, src, flame_off, flame_list;
+    Buf partials, counter, residual, rendered, dV, targets, sqerr, rmse, J, src, flame_cnt, flame_list;
     Buf batch;                       // batched reconstruction scratch and tables
     Buf pairs;                       // x-pair records for the forward march
     Buf occ;                         // brick occupancy for empty-space skipping

@@ -63,7 +63,7 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
-                   &c->rmse, &c->J, &c->src, &c->flame_off, &c->flame_list, &c->batch, &c->pairs,
+                   &c->rmse, &c->J, &c->src, &c->flame_cnt, &c->flame_list, &c->batch, &c->pairs,
                    &c->hull, &c->sat, &c->occ, &c->hull_bricks})
         if (b->p) cudaFree(b->p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
@@ -331,7 +331,8 @@ extern "C" fr_status fr_count_samples(fr_ctx* c, const fr_volume* vol, const fr_
         FR_TRY(ensure(c, c->hull_bricks, (size_t)nbx * nby * nbz, "hull bricks"));
         const unsigned full = ncam >= 32 ? 0xffffffffu : ((1u << ncam) - 1u);
         unsigned char* hb = static_cast<unsigned char*>(c->hull_bricks.p);
-        FR_CUDA(c, launch_hull_bricks(p->hull_tags, full, vol->nx, vol->ny, vol->nz, hb, c->stream));
+        FR_CUDA(c, launch_hull_clear(nullptr, vol->dtype, vol->nx, vol->ny, vol->nz, p->hull_tags, full, hb,
+                                     c->stream));
         a.p.occ = hb;
         a.p.nbx = nbx;
         a.p.nby = nby;
@@ -416,7 +417,7 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
     }
     const long long npix = (long long)ncam * cams[0].width * cams[0].height;
     if (npix >= (1LL << 32)) return fail(c, FR_EINVAL, "at most 2^32 pixels per reconstruction");
-    FR_TRY(ensure(c, c->flame_off, flame_list_buf_entries(nt) * sizeof(unsigned), "flame offsets"));
+    FR_TRY(ensure(c, c->flame_cnt, (size_t)iters * sizeof(unsigned), "flame counts"));
     FR_TRY(ensure(c, c->flame_list, (size_t)npix * sizeof(unsigned), "flame list"));
     FR_TRY(ensure(c, c->pairs, (size_t)nodes * 2 * rec_bytes(vol), "pairs"));
     const int nbx = bricks_along(vol->nx), nby = bricks_along(vol->ny), nbz = bricks_along(vol->nz);
@@ -463,12 +464,15 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
     u.p.img_in = static_cast<const float*>(c->residual.p);
     u.p.dV = static_cast<float*>(c->dV.p);
     float* sq = static_cast<float*>(c->sqerr.p);
-    // flame rays, once per call: the targets do not change between iterations
-    unsigned* flame_off = static_cast<unsigned*>(c->flame_off.p);
+    // flame rays: the forward march of iteration `it` lists them, counted at
+    // flame_cnt[it], for the adjustment that follows it
+    unsigned* flame_cnt = static_cast<unsigned*>(c->flame_cnt.p);
     unsigned* flame_list = static_cast<unsigned*>(c->flame_list.p);
-    const unsigned* flame_count = flame_off + flame_list_total_at(nt);
     FR_TRY(trace_mark(c, -1));
-    FR_CUDA(c, launch_flame_list(f, nt, flame_off, flame_list, s));
+    if (p->rule == FR_RULE_PAPER) {
+        FR_CUDA(c, cudaMemsetAsync(flame_cnt, 0, (size_t)iters * sizeof(unsigned), s));
+        f.p.flist = flame_list;
+    }
     const unsigned* hull = nullptr;
     const unsigned full = ncam >= 32 ? 0xffffffffu : ((1u << ncam) - 1u);
     if (p->use_hull) {
@@ -478,12 +482,11 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
             FR_TRY(hull_tags(c, f, tg, p->flame_thresh, static_cast<unsigned*>(c->hull.p)));
             hull = static_cast<const unsigned*>(c->hull.p);
         }
-        FR_CUDA(c, launch_hull_clear(vol->data, vol->dtype, nodes, hull, full, s));
-        if (p->skip_empty && p->rule == FR_RULE_PAPER && !(p->tau > 0.0f)) {
-            unsigned char* hb = static_cast<unsigned char*>(c->hull_bricks.p);
-            FR_CUDA(c, launch_hull_bricks(hull, full, vol->nx, vol->ny, vol->nz, hb, s));
-            u.p.adj_occ = hb;
-        }
+        unsigned char* hb = nullptr;
+        if (p->skip_empty && p->rule == FR_RULE_PAPER && !(p->tau > 0.0f))
+            hb = static_cast<unsigned char*>(c->hull_bricks.p);
+        FR_CUDA(c, launch_hull_clear(vol->data, vol->dtype, vol->nx, vol->ny, vol->nz, hull, full, hb, s));
+        u.p.adj_occ = hb;
     }
     FR_TRY(trace_mark(c, FR_PHASE_SETUP));
     for (int it = 0; it < iters; ++it) {
@@ -494,13 +497,14 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
         }
         FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, occ, s));
         FR_TRY(trace_mark(c, FR_PHASE_PACK));
+        f.p.flist_count = f.p.flist ? flame_cnt + it : nullptr;
         FR_CUDA(c, launch_fwd(f, vol->dtype, vol->kind, nt, s));
         FR_TRY(trace_mark(c, FR_PHASE_FORWARD));
         FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * it, s));
         FR_TRY(trace_mark(c, FR_PHASE_REDUCE));
         if (p->rule == FR_RULE_PAPER) {
             u.p.iteration = first_iteration + it;
-            FR_CUDA(c, launch_adjust_list(u, vol->dtype, nt, flame_list, flame_count, s));
+            FR_CUDA(c, launch_adjust_list(u, vol->dtype, nt, flame_list, flame_cnt + it, s));
             FR_TRY(trace_mark(c, FR_PHASE_ADJUST));
             FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg, 1, s));
         } else {
@@ -512,7 +516,8 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
             FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, -p->grad_step,
                                     p->update_sigma, p->clamp_nonneg, 1, s));
         }
-        if (hull) FR_CUDA(c, launch_hull_clear(vol->data, vol->dtype, nodes, hull, full, s));
+        if (hull)
+            FR_CUDA(c, launch_hull_clear(vol->data, vol->dtype, vol->nx, vol->ny, vol->nz, hull, full, nullptr, s));
         FR_TRY(trace_mark(c, FR_PHASE_APPLY));
     }
     FR_CUDA(c, launch_rmse(sq, iters, static_cast<float*>(c->rmse.p), s));

@@ -71,6 +71,10 @@ struct ProbDev {
     // occupancy of 8^3-cell bricks (1 = some corner record of the brick is
     // non-zero); when set, the forward march skips empty bricks
     const unsigned char* occ;
+    // flame-ray list the forward march writes (when set): flame pixels
+    // appended warp by warp at *flist_count (zero before the launch)
+    unsigned* flist;
+    unsigned* flist_count;
     // bricks holding a key point inside the visual hull; when set, the
     // adjustment skips the others (their key points' updates are discarded)
     const unsigned char* adj_occ;

@@ -60,10 +60,10 @@ cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t s);
 // visual hull: sat needs ncam (H+1)(W+1) uint32, tags one uint32 per node
 cudaError_t launch_visual_hull(const CamDev* cams, int ncam, int W, int H, int nx, int ny, int nz,
                                const float* targets, float thresh, unsigned* sat, unsigned* tags, cudaStream_t s);
-// per brick: 1 when one of its key points is inside the hull (tag == full)
-cudaError_t launch_hull_bricks(const unsigned* tags, unsigned full, int nx, int ny, int nz, unsigned char* flags,
-                               cudaStream_t s);
-cudaError_t launch_hull_clear(void* vol, int dt, long long nodes, const unsigned* tags, unsigned full, cudaStream_t s);
+// Records outside the hull (tag != full) set to 0 (vol null: none); with
+// flags, per brick of 8^3 cells: 1 when one of its key points is inside
+cudaError_t launch_hull_clear(void* vol, int dt, int nx, int ny, int nz, const unsigned* tags, unsigned full,
+                              unsigned char* flags, cudaStream_t s);
 // x-pair records of a volume (2 records per node) for the forward march, and
 // (occ non-null, RGB records) the occupancy of its 8^3-cell bricks
 inline int bricks_along(int n) { return (n - 2) / kBrick + 1; }

@@ -20,6 +20,9 @@
 #else
 #define FR_MARCH_BOUNDS __launch_bounds__(frk::kTileThreads)
 #endif
+// The adjustment over the flame-ray list runs with 8 resident CTAs per SM
+// (64 registers): it gains more from the occupancy than it loses to the cap.
+#define FR_ADJ_LIST_BOUNDS __launch_bounds__(frk::kTileThreads, 8)
 
 
 namespace frk {
@@ -216,8 +219,9 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
     }
     // pixel epilogue: image, residual of the colour constraint, error sums
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, cnt = 0.0f;
+    const long long pix = ((long long)view * P.H + py) * P.W + px;
+    bool flame = false;
     if (valid) {
-        const long long pix = ((long long)view * P.H + py) * P.W + px;
         if (P.rendered) {
             float* o = P.rendered + 3 * pix;
             o[0] = L0; o[1] = L1; o[2] = L2;
@@ -226,7 +230,7 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
             const float* t = P.targets + 3 * pix;
             const float t0 = t[0], t1 = t[1], t2 = t[2];
             const float d0 = t0 - L0, d1 = t1 - L1, d2 = t2 - L2;
-            const bool flame = fmaxf(t0, fmaxf(t1, t2)) > P.thresh;
+            flame = fmaxf(t0, fmaxf(t1, t2)) > P.thresh;
             float* r = P.residual + 3 * pix;
             r[0] = flame ? d0 : 0.0f;
             r[1] = flame ? d1 : 0.0f;
@@ -235,6 +239,29 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
             if (px >= bb[0] && px <= bb[2] && py >= bb[1] && py <= bb[3]) {
                 a0 = d0 * d0; a1 = d1 * d1; a2 = d2 * d2; cnt = 1.0f;
             }
+        }
+    }
+    if (P.flist) {
+        // flame-ray list for the adjustment: each CTA appends the flame
+        // pixels of its tile as one contiguous run in tile order, so the
+        // adjustment's warps take neighbouring rays
+        __shared__ unsigned wcount[kTileThreads / 32];
+        __shared__ unsigned run_at;
+        const unsigned m = __ballot_sync(0xffffffffu, flame);
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 0) wcount[w] = (unsigned)__popc(m);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned total = 0;
+#pragma unroll
+            for (int i = 0; i < kTileThreads / 32; ++i) total += wcount[i];
+            run_at = total ? atomicAdd(P.flist_count, total) : 0u;
+        }
+        __syncthreads();
+        if (flame) {
+            unsigned at = run_at + (unsigned)__popc(m & ((1u << lane) - 1u));
+            for (int i = 0; i < w; ++i) at += wcount[i];
+            P.flist[at] = (unsigned)pix;
         }
     }
     if (P.partials) {
@@ -346,7 +373,7 @@ __device__ __forceinline__ void adj_body(const ProbDev& P, const CamDev* cams, i
 // order, so a warp's 32 rays are neighbours): no lane idles on a non-flame
 // pixel.  CTA b takes list entries [128 b, 128 b + 128).
 template <int DT, bool TAU, bool SKIP>
-__global__ void FR_MARCH_BOUNDS adj_list(const __grid_constant__ SingleArgs a, const unsigned* __restrict__ list,
+__global__ void FR_ADJ_LIST_BOUNDS adj_list(const __grid_constant__ SingleArgs a, const unsigned* __restrict__ list,
                                          const unsigned* __restrict__ count)
 {
     const unsigned i = blockIdx.x * (unsigned)kTileThreads + threadIdx.x;

@@ -697,48 +697,42 @@ cudaError_t launch_visual_hull(const CamDev* cams, int ncam, int W, int H, int n
     return cudaGetLastError();
 }
 
-// Bricks of 8^3 cells holding at least one key point inside the hull.
-__global__ void __launch_bounds__(256) hull_bricks_kernel(const unsigned* __restrict__ tags, unsigned full, int nx,
-                                                          int ny, int nz, unsigned char* flags, int nbx, int nby,
-                                                          int nbz)
+// Records outside the hull (tag != full) are set to 0: no emission, no
+// extinction (vol null: nothing is cleared).  With `flags`, also marks the
+// bricks of 8^3 cells that hold a key point inside the hull (the flags are
+// cleared beforehand).
+template <int DT>
+__global__ void __launch_bounds__(256) hull_clear_kernel(void* vol, int nx, int ny, int nz,
+                                                         const unsigned* __restrict__ tags, unsigned full,
+                                                         unsigned char* flags, int nbx, int nby, int nbz)
 {
     const long long nodes = (long long)nx * ny * nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
          i += (long long)gridDim.x * blockDim.x) {
-        if (__ldg(tags + i) != full) continue;
-        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
-        mark_bricks(flags, x, y, z, nbx, nby, nbz);
+        if (__ldg(tags + i) != full) {
+            if (vol) store_rgb<DT>(vol, i, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+        } else if (flags) {
+            const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+            mark_bricks(flags, x, y, z, nbx, nby, nbz);
+        }
     }
 }
 
-cudaError_t launch_hull_bricks(const unsigned* tags, unsigned full, int nx, int ny, int nz, unsigned char* flags,
-                               cudaStream_t s)
+cudaError_t launch_hull_clear(void* vol, int dt, int nx, int ny, int nz, const unsigned* tags, unsigned full,
+                              unsigned char* flags, cudaStream_t s)
 {
     const int nbx = bricks_along(nx), nby = bricks_along(ny), nbz = bricks_along(nz);
-    cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)nbx * nby * nbz, s);
-    if (e != cudaSuccess) return e;
-    const long long nodes = (long long)nx * ny * nz;
-    hull_bricks_kernel<<<grid_for(nodes, 256), 256, 0, s>>>(tags, full, nx, ny, nz, flags, nbx, nby, nbz);
-    return cudaGetLastError();
-}
-
-// Records outside the hull (tag != full) are set to 0: no emission, no extinction.
-template <int DT>
-__global__ void __launch_bounds__(256) hull_clear_kernel(void* vol, long long nodes, const unsigned* tags,
-                                                         unsigned full)
-{
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
-         i += (long long)gridDim.x * blockDim.x) {
-        if (tags[i] != full) store_rgb<DT>(vol, i, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+    if (flags) {
+        cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)nbx * nby * nbz, s);
+        if (e != cudaSuccess) return e;
     }
-}
-
-cudaError_t launch_hull_clear(void* vol, int dt, long long nodes, const unsigned* tags, unsigned full, cudaStream_t s)
-{
+    const long long nodes = (long long)nx * ny * nz;
     const int g = grid_for(nodes, 256);
-    if (dt == DT_F32) hull_clear_kernel<DT_F32><<<g, 256, 0, s>>>(vol, nodes, tags, full);
-    else if (dt == DT_BF16) hull_clear_kernel<DT_BF16><<<g, 256, 0, s>>>(vol, nodes, tags, full);
-    else hull_clear_kernel<DT_F16><<<g, 256, 0, s>>>(vol, nodes, tags, full);
+#define FR_CLEAR(D) hull_clear_kernel<D><<<g, 256, 0, s>>>(vol, nx, ny, nz, tags, full, flags, nbx, nby, nbz)
+    if (dt == DT_F32) FR_CLEAR(DT_F32);
+    else if (dt == DT_BF16) FR_CLEAR(DT_BF16);
+    else FR_CLEAR(DT_F16);
+#undef FR_CLEAR
     return cudaGetLastError();
 }
 
