@@ -196,61 +196,58 @@ __device__ __forceinline__ CellIJK cell_ijk(float x, float y, float z, int nx, i
 // the usual ones written with the fraction mirrored where the cell index is
 // odd (mirror_frac).
 struct Win {
-    int ci, cj, ck;
-    int base;                // node index of (ci, cj, ck); volumes hold < 2^31 nodes
-    int o0[3], o1[3];        // node offset of slot bit value 0 / 1 along x, y, z
+    int base;                // node index of the cell's lowest corner; volumes hold < 2^31 nodes
+    int nd[8];               // node held by slot t
     bool live;
 };
 
-__device__ __forceinline__ int slot_node(const Win& W, int t)
+// Nodes of the eight slots for the cell whose lowest corner is node `base` at
+// (i, j, k): slot bit value v along an axis names node c + (v ^ (c & 1)).
+__device__ __forceinline__ void win_nodes(int base, int i, int j, int k, int nx, int nxy, int nd[8])
 {
-    return W.base + ((t & 1) ? W.o1[0] : W.o0[0]) + (((t >> 1) & 1) ? W.o1[1] : W.o0[1]) +
-           ((t >> 2) ? W.o1[2] : W.o0[2]);
-}
-
-__device__ __forceinline__ void win_set(Win& W, int i, int j, int k, int nx, int ny, int nxy)
-{
-    W.ci = i; W.cj = j; W.ck = k;
-    W.base = (k * ny + j) * nx + i;
-    // slot bit value v along an axis names node c + (v ^ (c & 1))
     const int px = i & 1, py = j & 1, pz = k & 1;
-    W.o0[0] = px;            W.o1[0] = 1 - px;
-    W.o0[1] = py ? nx : 0;   W.o1[1] = py ? 0 : nx;
-    W.o0[2] = pz ? nxy : 0;  W.o1[2] = pz ? 0 : nxy;
-    W.live = true;
+    const int ox0 = px, ox1 = 1 - px;
+    const int oy0 = py ? nx : 0, oy1 = py ? 0 : nx;
+    const int zb0 = base + (pz ? nxy : 0), zb1 = base + (pz ? 0 : nxy);
+    const int xy[4] = {ox0 + oy0, ox1 + oy0, ox0 + oy1, ox1 + oy1};
+#pragma unroll
+    for (int t = 0; t < 8; ++t) nd[t] = ((t >> 2) ? zb1 : zb0) + xy[t & 3];
 }
 
 // Move the window to cell (i, j, k).  leave(t, node) runs for each slot whose
 // key point is not a corner of the new cell (with its old node), then
 // enter(t, node) for the same slots (with the new node); on the first call
-// every slot enters.
+// every slot enters.  A key point shared by both cells has the same parities
+// in both, so it keeps its slot.
 template <class Leave, class Enter>
 __device__ __forceinline__ void win_move(Win& W, int i, int j, int k, int nx, int ny, int nxy,
                                          Leave&& leave, Enter&& enter)
 {
+    const int base = (k * ny + j) * nx + i;
+    if (W.live && base == W.base) return;
+    int nn[8];
+    win_nodes(base, i, j, k, nx, nxy, nn);
+    W.base = base;
     if (!W.live) {
-        win_set(W, i, j, k, nx, ny, nxy);
+        W.live = true;
 #pragma unroll
-        for (int t = 0; t < 8; ++t) enter(t, slot_node(W, t));
+        for (int t = 0; t < 8; ++t) {
+            W.nd[t] = nn[t];
+            enter(t, nn[t]);
+        }
         return;
     }
-    if (i == W.ci && j == W.cj && k == W.ck) return;
-    // the key point of slot bit v stays iff c_old + (v ^ p_old) is c_new or c_new + 1
-    const int dx = W.ci - i, dy = W.cj - j, dz = W.ck - k;
-    const int px = W.ci & 1, py = W.cj & 1, pz = W.ck & 1;
-    const bool sx[2] = {(unsigned)(dx + px) <= 1u, (unsigned)(dx + 1 - px) <= 1u};
-    const bool sy[2] = {(unsigned)(dy + py) <= 1u, (unsigned)(dy + 1 - py) <= 1u};
-    const bool sz[2] = {(unsigned)(dz + pz) <= 1u, (unsigned)(dz + 1 - pz) <= 1u};
     bool go[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-        go[t] = !(sx[t & 1] && sy[(t >> 1) & 1] && sz[t >> 2]);
-        if (go[t]) leave(t, slot_node(W, t));
+        go[t] = nn[t] != W.nd[t];
+        if (go[t]) leave(t, W.nd[t]);
     }
-    win_set(W, i, j, k, nx, ny, nxy);
 #pragma unroll
-    for (int t = 0; t < 8; ++t)
-        if (go[t]) enter(t, slot_node(W, t));
+    for (int t = 0; t < 8; ++t) {
+        W.nd[t] = nn[t];
+        if (go[t]) enter(t, nn[t]);
+    }
 }
 
 template <class Leave>
@@ -258,17 +255,29 @@ __device__ __forceinline__ void win_release(const Win& W, Leave&& leave)
 {
     if (!W.live) return;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) leave(t, slot_node(W, t));
+    for (int t = 0; t < 8; ++t) leave(t, W.nd[t]);
 }
 
 // Fraction toward the odd-parity key point along one axis.
 __device__ __forceinline__ float mirror_frac(int cell, float f) { return (cell & 1) ? 1.0f - f : f; }
 
-// exp(-a * |x|) for x = squared distance, with sqrt taken as x rsqrt(x).
-__device__ __forceinline__ float dist_weight(float a, float x)
+// 2^x on the special-function unit (flush-to-zero, about 2 ulp).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// log2(e), to write exp(x) as 2^(x log2 e)
+constexpr float kLog2e = 1.4426950408889634f;
+
+// exp(-a |x|) for x = squared distance, given c = -a log2(e); the square
+// root is taken as x rsqrt(x).
+__device__ __forceinline__ float dist_weight(float c, float x)
 {
     x = fmaxf(x, 1e-30f);
-    return __expf(-a * (x * rsqrtf(x)));
+    return ex2_approx(c * (x * rsqrtf(x)));
 }
 
 // ---------------------------------------------------------------------------

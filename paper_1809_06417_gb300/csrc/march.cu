@@ -20,9 +20,11 @@
 #else
 #define FR_MARCH_BOUNDS __launch_bounds__(frk::kTileThreads)
 #endif
-// The adjustment over the flame-ray list runs with 8 resident CTAs per SM
-// (64 registers): it gains more from the occupancy than it loses to the cap.
-#define FR_ADJ_LIST_BOUNDS __launch_bounds__(frk::kTileThreads, 8)
+// Resident CTAs per SM asked for the adjustment over the flame-ray list.
+#ifndef FR_ADJ_MINB
+#define FR_ADJ_MINB 6
+#endif
+#define FR_ADJ_LIST_BOUNDS __launch_bounds__(frk::kTileThreads, FR_ADJ_MINB)
 
 
 namespace frk {
@@ -319,6 +321,7 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
     const long long nxy = (long long)P.nx * P.ny;
     const int nxy32 = P.nx * P.ny;
     const int pixel = py * P.W + px;
+    const float dcoef = -P.alpha_d * kLog2e;
     float acc[8], sg[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) { acc[t] = 0.0f; sg[t] = 0.0f; }
@@ -351,8 +354,9 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
         const float ex[2] = {gx * gx, (1.0f - gx) * (1.0f - gx)};
         const float ey[2] = {gy * gy, (1.0f - gy) * (1.0f - gy)};
         const float ez[2] = {gz * gz, (1.0f - gz) * (1.0f - gz)};
+        const float exy[4] = {ex[0] + ey[0], ex[1] + ey[0], ex[0] + ey[1], ex[1] + ey[1]};
 #pragma unroll
-        for (int t = 0; t < 8; ++t) acc[t] = fmaf(base, dist_weight(P.alpha_d, ex[t & 1] + ey[(t >> 1) & 1] + ez[t >> 2]), acc[t]);
+        for (int t = 0; t < 8; ++t) acc[t] = fmaf(base, dist_weight(dcoef, exy[t & 3] + ez[t >> 2]), acc[t]);
         if constexpr (TAU) T *= 1.0f - P.tau;
         else T *= __expf(-slot_blend<float>(sg, gx, gy, gz) * len);
     }
