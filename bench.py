@@ -35,10 +35,11 @@ sys.path.insert(0, ROOT)
 METRIC = "ray samples/s (fwd+adjoint) and recon iters/s at 128^3×8 views; p50/p99 job latency"
 WORKLOAD = dict(name="full_rte_128^3_8x512^2", n=128, views=8, side=512, step=0.5, seed=2,
                 alpha_l=2e-4, noise=1e-3, hull=True)
-# kernels one step (one fr_reconstruct iteration) launches: flame-ray list (3),
-# hull clear, hull bricks, in-scatter sweeps (3), pair pack, forward, error
-# reduction, adjustment, apply, hull clear, rmse
-KERNELS_PER_STEP = 15
+# kernels one step (one fr_reconstruct iteration) launches: hull clear with
+# brick marks and its brick box, in-scatter sweeps (3), pair pack and its brick
+# box, forward (which lists the flame rays), error reduction, adjustment, apply,
+# hull clear, rmse
+KERNELS_PER_STEP = 13
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures of
 # the current kernels at this workload (None where the kernel changed since)
 NCU_TRAFFIC = {("fwd", "f32"): 143.05e6 + 25.19e6}

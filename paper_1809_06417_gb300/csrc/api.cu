@@ -110,15 +110,17 @@ static fr_status attach_pairs(fr_ctx* c, const fr_volume* vol, const fr_params* 
     const int nbx = bricks_along(vol->nx), nby = bricks_along(vol->ny), nbz = bricks_along(vol->nz);
     unsigned char* occ = nullptr;
     if (skips_empty(vol, p)) {
-        FR_TRY(ensure(c, c->occ, (size_t)nbx * nby * nbz, "brick occupancy"));
+        FR_TRY(ensure(c, c->occ, brick_table_bytes(vol->nx, vol->ny, vol->nz), "brick occupancy"));
         occ = static_cast<unsigned char*>(c->occ.p);
     }
     FR_CUDA(c, launch_pair_pack(records, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, occ,
                                 c->stream));
     a.p.pairs = c->pairs.p;
     a.p.occ = occ;
+    a.p.occ_box = occ ? brick_box(occ, nbx, nby, nbz) : nullptr;
     a.p.nbx = nbx;
     a.p.nby = nby;
+    a.p.nbz = nbz;
     return FR_OK;
 }
 
@@ -328,7 +330,7 @@ extern "C" fr_status fr_count_samples(fr_ctx* c, const fr_volume* vol, const fr_
         !(p->tau > 0.0f)) {
         const int nbx = bricks_along(vol->nx), nby = bricks_along(vol->ny), nbz = bricks_along(vol->nz);
         FR_TRY(check_dev(c, p->hull_tags, (size_t)node_count(vol) * 4, "hull_tags"));
-        FR_TRY(ensure(c, c->hull_bricks, (size_t)nbx * nby * nbz, "hull bricks"));
+        FR_TRY(ensure(c, c->hull_bricks, brick_table_bytes(vol->nx, vol->ny, vol->nz), "hull bricks"));
         const unsigned full = ncam >= 32 ? 0xffffffffu : ((1u << ncam) - 1u);
         unsigned char* hb = static_cast<unsigned char*>(c->hull_bricks.p);
         FR_CUDA(c, launch_hull_clear(nullptr, vol->dtype, vol->nx, vol->ny, vol->nz, p->hull_tags, full, hb,
@@ -336,6 +338,7 @@ extern "C" fr_status fr_count_samples(fr_ctx* c, const fr_volume* vol, const fr_
         a.p.occ = hb;
         a.p.nbx = nbx;
         a.p.nby = nby;
+        a.p.nbz = nbz;
     }
     FR_CUDA(c, cudaMemsetAsync(a.p.counter, 0, sizeof(unsigned long long), c->stream));
     FR_CUDA(c, launch_count(a, tiles_of(a.p.W, a.p.H, ncam), c->stream));
@@ -423,14 +426,14 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
     const int nbx = bricks_along(vol->nx), nby = bricks_along(vol->ny), nbz = bricks_along(vol->nz);
     unsigned char* occ = nullptr;
     if (skips_empty(vol, p)) {
-        FR_TRY(ensure(c, c->occ, (size_t)nbx * nby * nbz, "brick occupancy"));
+        FR_TRY(ensure(c, c->occ, brick_table_bytes(vol->nx, vol->ny, vol->nz), "brick occupancy"));
         occ = static_cast<unsigned char*>(c->occ.p);
     }
     if (p->use_hull) {
         if (vol->kind != FR_KIND_RGB) return fail(c, FR_EINVAL, "the visual hull applies to RGB volumes");
         if (p->hull_tags) FR_TRY(check_dev(c, p->hull_tags, (size_t)nodes * 4, "hull_tags"));
         else FR_TRY(ensure(c, c->hull, (size_t)nodes * 4, "hull"));
-        FR_TRY(ensure(c, c->hull_bricks, (size_t)nbx * nby * nbz, "hull bricks"));
+        FR_TRY(ensure(c, c->hull_bricks, brick_table_bytes(vol->nx, vol->ny, vol->nz), "hull bricks"));
     }
     cudaStream_t s = c->stream;
     const float* tg = targets;
@@ -451,11 +454,14 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
     f.p.rendered = p->rule == FR_RULE_GRADIENT ? static_cast<float*>(c->rendered.p) : nullptr;
     f.p.pairs = c->pairs.p;
     f.p.occ = occ;
+    f.p.occ_box = occ ? brick_box(occ, nbx, nby, nbz) : nullptr;
     f.p.nbx = nbx;
     f.p.nby = nby;
+    f.p.nbz = nbz;
     u = f;
     u.p.pairs = nullptr;
     u.p.occ = nullptr;
+    u.p.occ_box = nullptr;
     u.p.adj_occ = nullptr;
     u.p.targets = nullptr;
     u.p.partials = nullptr;
@@ -487,6 +493,7 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
             hb = static_cast<unsigned char*>(c->hull_bricks.p);
         FR_CUDA(c, launch_hull_clear(vol->data, vol->dtype, vol->nx, vol->ny, vol->nz, hull, full, hb, s));
         u.p.adj_occ = hb;
+        u.p.adj_box = hb ? brick_box(hb, nbx, nby, nbz) : nullptr;
     }
     FR_TRY(trace_mark(c, FR_PHASE_SETUP));
     for (int it = 0; it < iters; ++it) {

@@ -71,6 +71,7 @@ struct ProbDev {
     // occupancy of 8^3-cell bricks (1 = some corner record of the brick is
     // non-zero); when set, the forward march skips empty bricks
     const unsigned char* occ;
+    const unsigned* occ_box;     // box of the non-empty bricks (brick-table layout)
     // flame-ray list the forward march writes (when set): flame pixels
     // appended warp by warp at *flist_count (zero before the launch)
     unsigned* flist;
@@ -78,7 +79,8 @@ struct ProbDev {
     // bricks holding a key point inside the visual hull; when set, the
     // adjustment skips the others (their key points' updates are discarded)
     const unsigned char* adj_occ;
-    int nbx, nby;                // bricks along x and y
+    const unsigned* adj_box;     // box of those bricks
+    int nbx, nby, nbz;           // bricks along x, y and z
 };
 
 constexpr int kBrick = 8;        // cells per brick edge

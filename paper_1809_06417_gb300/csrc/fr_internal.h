@@ -61,12 +61,26 @@ cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t s);
 cudaError_t launch_visual_hull(const CamDev* cams, int ncam, int W, int H, int nx, int ny, int nz,
                                const float* targets, float thresh, unsigned* sat, unsigned* tags, cudaStream_t s);
 // Records outside the hull (tag != full) set to 0 (vol null: none); with
-// flags, per brick of 8^3 cells: 1 when one of its key points is inside
+// flags, the brick table of the key points inside the hull
 cudaError_t launch_hull_clear(void* vol, int dt, int nx, int ny, int nz, const unsigned* tags, unsigned full,
                               unsigned char* flags, cudaStream_t s);
-// x-pair records of a volume (2 records per node) for the forward march, and
-// (occ non-null, RGB records) the occupancy of its 8^3-cell bricks
+// Brick tables: one flag per brick of 8^3 cells (x fastest), then, at the
+// next 16-byte boundary, the box of the flagged bricks as six unsigned
+// values {nbx - lo_x, nby - lo_y, nbz - lo_z, hi_x + 1, hi_y + 1, hi_z + 1}
+// (all 0 when no brick is flagged).
 inline int bricks_along(int n) { return (n - 2) / kBrick + 1; }
+inline size_t brick_count(int nx, int ny, int nz)
+{
+    return (size_t)bricks_along(nx) * bricks_along(ny) * bricks_along(nz);
+}
+inline size_t brick_box_offset(int nx, int ny, int nz) { return (brick_count(nx, ny, nz) + 15) & ~(size_t)15; }
+inline size_t brick_table_bytes(int nx, int ny, int nz) { return brick_box_offset(nx, ny, nz) + 32; }
+__host__ __device__ inline unsigned* brick_box(unsigned char* table, int nbx, int nby, int nbz)
+{
+    return reinterpret_cast<unsigned*>(table + (((size_t)nbx * nby * nbz + 15) & ~(size_t)15));
+}
+// x-pair records of a volume (2 records per node) for the forward march, and
+// (occ non-null, RGB records) the brick table of its non-zero records
 cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int nx, int ny, int nz,
                              unsigned char* occ, cudaStream_t s);
 

@@ -143,6 +143,36 @@ struct BrickSkip {
     __device__ __forceinline__ explicit BrickSkip(const Ray& R)
         : idx(1.0f / R.dx), idy(1.0f / R.dy), idz(1.0f / R.dz) {}
 
+    // Samples [k0, k1) of the ray that can lie in the box of the flagged-on
+    // bricks (box: brick-table layout); false when there are none.  Samples
+    // outside the range have their midpoint (their start, for the last,
+    // shorter segment) beyond the box by more than a 1e-3 voxel margin.
+    static __device__ __forceinline__ bool box_range(const ProbDev& P, const unsigned* box, const Ray& R,
+                                                     float step, int& k0, int& k1)
+    {
+        const unsigned hx = __ldg(box + 3), hy = __ldg(box + 4), hz = __ldg(box + 5);
+        if (hx == 0u) return false;
+        const float lo[3] = {(float)((P.nbx - (int)__ldg(box)) * kBrick), (float)((P.nby - (int)__ldg(box + 1)) * kBrick),
+                             (float)((P.nbz - (int)__ldg(box + 2)) * kBrick)};
+        const float hi[3] = {(float)min((int)hx * kBrick, P.nx - 1), (float)min((int)hy * kBrick, P.ny - 1),
+                             (float)min((int)hz * kBrick, P.nz - 1)};
+        const float o[3] = {R.p0x, R.p0y, R.p0z}, d[3] = {R.dx, R.dy, R.dz};
+        float tin = 0.0f, tout = R.chord;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (d[a] == 0.0f) {
+                if (o[a] < lo[a] - 1e-3f || o[a] > hi[a] + 1e-3f) return false;
+                continue;
+            }
+            const float t0 = (lo[a] - o[a]) / d[a], t1 = (hi[a] - o[a]) / d[a];
+            tin = fmaxf(tin, fminf(t0, t1));
+            tout = fminf(tout, fmaxf(t0, t1));
+        }
+        k0 = max(0, (int)ceilf((tin - 1e-3f) / step - 0.5f));
+        k1 = min(R.n, (int)floorf((tout + 1e-3f) / step) + 1);
+        return k0 < k1;
+    }
+
     // True when sample k (midpoint x, y, z) lies in a flagged-off brick.  k
     // then moves so that the loop's increment lands on the first sample whose
     // midpoint may lie beyond that brick; a 1e-3 voxel margin on the exit
@@ -190,7 +220,11 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
             long long vbase = -1;
             float T = 1.0f;
             BrickSkip skip(R);
-            for (int k = 0; k < R.n; ++k) {
+            int k0 = 0, k1 = R.n;
+            if constexpr (SKIP) {
+                if (!BrickSkip::box_range(P, P.occ_box, R, P.step, k0, k1)) k1 = 0;
+            }
+            for (int k = k0; k < k1; ++k) {
                 float len, x, y, z;
                 segment(R, P.step, k, len, x, y, z);
                 if constexpr (SKIP) {
@@ -339,7 +373,11 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
     W.live = false;
     float T = 1.0f;
     BrickSkip skip(R);
-    for (int k = 0; k < R.n; ++k) {
+    int k0 = 0, k1 = R.n;
+    if constexpr (SKIP) {
+        if (!BrickSkip::box_range(P, P.adj_box, R, P.step, k0, k1)) return;
+    }
+    for (int k = k0; k < k1; ++k) {
         float len, x, y, z;
         segment(R, P.step, k, len, x, y, z);
         if constexpr (SKIP) {

@@ -134,6 +134,50 @@ __device__ __forceinline__ void mark_bricks(unsigned char* occ, int x, int y, in
             for (int bx = bx0; bx <= min(x >> 3, nbx - 1); ++bx) occ[((long long)bz * nby + by) * nbx + bx] = 1;
 }
 
+// The box of the flagged bricks of a brick table (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024) brick_box_kernel(unsigned char* table, int nbx, int nby, int nbz)
+{
+    __shared__ unsigned red[6][32];
+    const int nb = nbx * nby * nbz;
+    unsigned lo[3] = {UINT_MAX, UINT_MAX, UINT_MAX}, hi[3] = {0u, 0u, 0u};
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        if (!table[b]) continue;
+        const unsigned c[3] = {(unsigned)(b % nbx), (unsigned)((b / nbx) % nby), (unsigned)(b / (nbx * nby))};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = min(lo[a], c[a]);
+            hi[a] = max(hi[a], c[a] + 1u);
+        }
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const unsigned l = __reduce_min_sync(0xffffffffu, lo[a]), h = __reduce_max_sync(0xffffffffu, hi[a]);
+        if (lane == 0) { red[a][w] = l; red[3 + a][w] = h; }
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        unsigned* box = brick_box(table, nbx, nby, nbz);
+        const int nbs[3] = {nbx, nby, nbz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const unsigned l = __reduce_min_sync(0xffffffffu, lane < nw ? red[a][lane] : UINT_MAX);
+            const unsigned h = __reduce_max_sync(0xffffffffu, lane < nw ? red[3 + a][lane] : 0u);
+            if (lane == 0) {
+                box[a] = h ? (unsigned)nbs[a] - l : 0u;
+                box[3 + a] = h;
+            }
+        }
+    }
+}
+
+static cudaError_t launch_brick_box(unsigned char* table, int nx, int ny, int nz, cudaStream_t s)
+{
+    brick_box_kernel<<<1, 1024, 0, s>>>(table, bricks_along(nx), bricks_along(ny), bricks_along(nz));
+    return cudaGetLastError();
+}
+
 template <int DT, int KIND>
 __global__ void __launch_bounds__(256) pair_pack_kernel(const void* src, void* dst, long long rows, int nx, int ny,
                                                         unsigned char* occ, int nbx, int nby, int nbz)
@@ -216,7 +260,7 @@ cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int n
     const int g = (int)(rows < 152LL * 32 ? rows : 152LL * 32);
     const int nbx = (nx - 2) / kBrick + 1, nby = (ny - 2) / kBrick + 1, nbz = (nz - 2) / kBrick + 1;
     if (occ) {
-        cudaError_t e = cudaMemsetAsync(occ, 0, (size_t)nbx * nby * nbz, s);
+        cudaError_t e = cudaMemsetAsync(occ, 0, brick_table_bytes(nx, ny, nz), s);
         if (e != cudaSuccess) return e;
     }
 #define FR_PACK(D, K) pair_pack_kernel<D, K><<<g, 256, 0, s>>>(src, dst, rows, nx, ny, occ, nbx, nby, nbz)
@@ -230,6 +274,11 @@ cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int n
         else FR_PACK(DT_F16, KIND_TEMP);
     }
 #undef FR_PACK
+    if (occ) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_brick_box(occ, nx, ny, nz, s);
+    }
     return cudaGetLastError();
 }
 
@@ -723,7 +772,7 @@ cudaError_t launch_hull_clear(void* vol, int dt, int nx, int ny, int nz, const u
 {
     const int nbx = bricks_along(nx), nby = bricks_along(ny), nbz = bricks_along(nz);
     if (flags) {
-        cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)nbx * nby * nbz, s);
+        cudaError_t e = cudaMemsetAsync(flags, 0, brick_table_bytes(nx, ny, nz), s);
         if (e != cudaSuccess) return e;
     }
     const long long nodes = (long long)nx * ny * nz;
@@ -733,6 +782,11 @@ cudaError_t launch_hull_clear(void* vol, int dt, int nx, int ny, int nz, const u
     else if (dt == DT_BF16) FR_CLEAR(DT_BF16);
     else FR_CLEAR(DT_F16);
 #undef FR_CLEAR
+    if (flags) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_brick_box(flags, nx, ny, nz, s);
+    }
     return cudaGetLastError();
 }
 
