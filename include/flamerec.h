@@ -237,6 +237,22 @@ fr_status fr_reconstruct(fr_ctx *ctx, fr_volume *vol, const float *albedo,
                          int first_iteration, const fr_params *p, float *rmse,
                          int rmse_is_host);
 
+/* The reconstruction loop with the stop criterion of Sec. 3: iterations as in
+ * fr_reconstruct until the image error (the rmse rows below) changes by less
+ * than stop_delta (>= 0, on the [0, 255] scale) in every channel between two
+ * consecutive iterations, or max_iters (>= 1) iterations have run; the paper
+ * stops at 0.01.  The iterations run as one CUDA graph whose conditional while
+ * node the device ends, so the host does not wait on each iteration.  rmse
+ * (nullable; host when rmse_is_host, else device): room for max_iters x 3,
+ * the first *iters_done rows written.  *iters_done (host, required): the
+ * iterations run; the call synchronises the context's stream.  Phase tracing
+ * does not see inside the graph. */
+fr_status fr_reconstruct_until(fr_ctx *ctx, fr_volume *vol, const float *albedo,
+                               const fr_camera *cams, int ncam, const float *targets,
+                               int targets_are_host, const int32_t *bbox, int max_iters,
+                               float stop_delta, int first_iteration, const fr_params *p,
+                               float *rmse, int rmse_is_host, int32_t *iters_done);
+
 /* One reconstruction problem of a batch (e.g. one video frame, Sec. 5.2, whose
  * frames the paper reconstructs independently). */
 typedef struct fr_problem {

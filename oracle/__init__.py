@@ -88,7 +88,7 @@ def _load():
             "orc_scatter_J": (None, [_P, _P, _P]),
             "orc_scatter_source": (None, [_I64, _P, _P, _P, _P]),
             "orc_reconstruct": (None, [_P, _P, _P, _P, ctypes.c_int, _P, _P, _P, _P,
-                                       ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+                                       ctypes.c_int, ctypes.c_int, _P, _P, _P, ctypes.c_double, _P]),
             "orc_visual_hull": (None, [_P, _P, ctypes.c_int, _P, _P]),
             "orc_planck": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
             "orc_temp_rgb": (None, [ctypes.c_double, _P]),
@@ -333,10 +333,11 @@ def visual_hull(scene: Scene, mask):
 
 
 def reconstruct(scene: Scene, vol, params: Params, targets, mask, bbox, iters,
-                albedo=None, first_iteration=0, hull=None):
+                albedo=None, first_iteration=0, hull=None, stop_delta=None):
     """Algorithm 2 repeated `iters` times with the paper rule; with `hull`
-    (visual-hull tags) the records outside the hull are held at 0.
-    Returns (volume, rmse per iteration (iters x 3), (forward, adjust) samples)."""
+    (visual-hull tags) the records outside the hull are held at 0; with
+    stop_delta, stops once the image error changes by less than it (Sec. 3).
+    Returns (volume, rmse per iteration run (rows x 3), (forward, adjust) samples)."""
     lib = _load()
     vol = _check_vol(vol, scene.shape, 4).copy()
     targets = _f64(targets)
@@ -346,11 +347,13 @@ def reconstruct(scene: Scene, vol, params: Params, targets, mask, bbox, iters,
     samples = np.zeros(2, dtype=np.int64)
     alb = _f64(albedo) if albedo is not None else None
     hl = np.ascontiguousarray(hull, dtype=np.uint32) if hull is not None else None
+    done = ctypes.c_int(0)
     lib.orc_reconstruct(ctypes.byref(scene.grid), _ptr(vol), _ptr(alb) if alb is not None else None,
                         scene.cams, scene.ncam, ctypes.byref(params), _ptr(targets), _ptr(mask),
                         _ptr(bbox), int(iters), int(first_iteration), _ptr(rmse), _ptr(samples),
-                        _ptr(hl) if hl is not None else None)
-    return vol, rmse, (int(samples[0]), int(samples[1]))
+                        _ptr(hl) if hl is not None else None,
+                        float(stop_delta) if stop_delta is not None else -1.0, ctypes.byref(done))
+    return vol, rmse[:done.value], (int(samples[0]), int(samples[1]))
 
 
 def planck(lambda_m, temp_k):

@@ -812,7 +812,10 @@ void orc_visual_hull(const orc_grid *g, const orc_cam *cams, int ncam, const uin
 /* ------------------------------------------------------------------------ */
 
 /* Runs `iters` iterations of the paper rule on vol (N^3 x 4, colour updated
- * in place).  albedo (nullable) turns on the in-scattering source, recomputed
+ * in place); with stop_delta >= 0, stops earlier after the first iteration
+ * k >= 1 whose image error differs from iteration k-1's by less than
+ * stop_delta in every channel (Sec. 3 stop criterion), and *iters_done
+ * (nullable) gets the iterations run.  albedo (nullable) turns on the in-scattering source, recomputed
  * from the current volume at the start of each iteration.  targets must have
  * been through orc_prepare_targets (mask, bbox).  rmse (iters x 3) gets the
  * error of the images rendered at the start of each iteration.  samples[0..1]
@@ -821,7 +824,7 @@ void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
                      const orc_cam *cams, int ncam, const orc_params *P,
                      const double *targets, const uint8_t *mask, const int32_t *bbox,
                      int iters, int first_iteration, double *rmse, int64_t *samples,
-                     const uint32_t *hull)
+                     const uint32_t *hull, double stop_delta, int *iters_done)
 {
     int64_t nodes = (int64_t)g->nx * g->ny * g->nz;
     int64_t npix = 0;
@@ -854,6 +857,13 @@ void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
         if (hull)
             for (int64_t j = 0; j < nodes; ++j)
                 if (hull[j] != full) vol[4 * j] = vol[4 * j + 1] = vol[4 * j + 2] = vol[4 * j + 3] = 0.0;
+        if (iters_done) *iters_done = it + 1;
+        if (stop_delta >= 0.0 && it >= 1) {
+            int small = 1;
+            for (int ch = 0; ch < 3; ++ch)
+                if (!(fabs(rmse[3 * it + ch] - rmse[3 * (it - 1) + ch]) < stop_delta)) small = 0;
+            if (small) break;
+        }
     }
     free(img); free(res); free(dV); free(J); free(src);
 }

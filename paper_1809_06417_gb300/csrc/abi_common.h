@@ -35,6 +35,7 @@ struct fr_ctx {
     Buf pairs;                       // x-pair records for the forward march
     Buf occ;                         // brick occupancy for empty-space skipping
     Buf hull_bricks;                 // bricks holding a key point inside the visual hull
+    Buf loop;                        // device iteration counter of fr_reconstruct_until
     Buf hull, sat;                   // visual hull tags, flame-mask tables
     unsigned long long* host_counter = nullptr;
     void* staging = nullptr;         // pinned host staging of batch tables

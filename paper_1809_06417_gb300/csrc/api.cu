@@ -64,7 +64,7 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     cudaStreamSynchronize(c->stream);
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
                    &c->rmse, &c->J, &c->src, &c->flame_cnt, &c->flame_list, &c->batch, &c->pairs,
-                   &c->hull, &c->sat, &c->occ, &c->hull_bricks})
+                   &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop})
         if (b->p) cudaFree(b->p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
     if (c->staging) cudaFreeHost(c->staging);
@@ -378,12 +378,16 @@ extern "C" fr_status fr_visual_hull(fr_ctx* c, const fr_volume* vol, const fr_ca
 // The reconstruction loop
 // ---------------------------------------------------------------------------
 
-extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albedo, const fr_camera* cams,
-                                    int ncam, const float* targets, int targets_are_host, const int32_t* bbox,
-                                    int iters, int first_iteration, const fr_params* p, float* rmse,
-                                    int rmse_is_host)
+// The loop of fr_reconstruct (stop_delta < 0: exactly `iters` iterations) and
+// of fr_reconstruct_until (stop_delta >= 0: at most `iters` iterations, ended
+// on the device by the stop criterion inside a conditional CUDA graph).
+static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo, const fr_camera* cams, int ncam,
+                                  const float* targets, int targets_are_host, const int32_t* bbox, int iters,
+                                  int first_iteration, const fr_params* p, float* rmse, int rmse_is_host,
+                                  float stop_delta, int32_t* iters_done)
 {
     FR_BEGIN(c);
+    const bool until = stop_delta >= 0.0f;
     FR_TRY(check_volume(c, vol, "vol"));
     FR_TRY(check_cams(c, cams, ncam));
     FR_TRY(check_params(c, p, vol, cams));
@@ -421,6 +425,7 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
     const long long npix = (long long)ncam * cams[0].width * cams[0].height;
     if (npix >= (1LL << 32)) return fail(c, FR_EINVAL, "at most 2^32 pixels per reconstruction");
     FR_TRY(ensure(c, c->flame_cnt, (size_t)iters * sizeof(unsigned), "flame counts"));
+    if (until) FR_TRY(ensure(c, c->loop, 16, "loop counter"));
     FR_TRY(ensure(c, c->flame_list, (size_t)npix * sizeof(unsigned), "flame list"));
     FR_TRY(ensure(c, c->pairs, (size_t)nodes * 2 * rec_bytes(vol), "pairs"));
     const int nbx = bricks_along(vol->nx), nby = bricks_along(vol->ny), nbz = bricks_along(vol->nz);
@@ -496,48 +501,151 @@ extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albe
         u.p.adj_box = hb ? brick_box(hb, nbx, nby, nbz) : nullptr;
     }
     FR_TRY(trace_mark(c, FR_PHASE_SETUP));
-    for (int it = 0; it < iters; ++it) {
+    // One iteration on stream st.  it >= 0: per-iteration slots it; it < 0:
+    // slot 0 and the iteration index read on the device (graph body).
+    auto one_iteration = [&](cudaStream_t st, int it) -> fr_status {
+        const int slot = it < 0 ? 0 : it;
         if (albedo) {
             FR_CUDA(c, launch_scatter_source(vol->data, vol->dtype, albedo, static_cast<float*>(c->J.p), c->src.p,
-                                             vol->dtype, vol->nx, vol->ny, vol->nz, s));
+                                             vol->dtype, vol->nx, vol->ny, vol->nz, st));
             FR_TRY(trace_mark(c, FR_PHASE_SCATTER));
         }
-        FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, occ, s));
+        FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, occ,
+                                    st));
         FR_TRY(trace_mark(c, FR_PHASE_PACK));
-        f.p.flist_count = f.p.flist ? flame_cnt + it : nullptr;
-        FR_CUDA(c, launch_fwd(f, vol->dtype, vol->kind, nt, s));
+        f.p.flist_count = f.p.flist ? flame_cnt + slot : nullptr;
+        FR_CUDA(c, launch_fwd(f, vol->dtype, vol->kind, nt, st));
         FR_TRY(trace_mark(c, FR_PHASE_FORWARD));
-        FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * it, s));
+        FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * slot, st));
         FR_TRY(trace_mark(c, FR_PHASE_REDUCE));
         if (p->rule == FR_RULE_PAPER) {
-            u.p.iteration = first_iteration + it;
-            FR_CUDA(c, launch_adjust_list(u, vol->dtype, nt, flame_list, flame_cnt + it, s));
+            u.p.iteration = first_iteration + slot;
+            FR_CUDA(c, launch_adjust_list(u, vol->dtype, nt, flame_list, flame_cnt + slot, st));
             FR_TRY(trace_mark(c, FR_PHASE_ADJUST));
-            FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg, 1, s));
+            FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg, 1,
+                                    st));
         } else {
             // d(0.5 sum m dL^2)/d(rendered) = -m dL: the residual scaled by -1
             u.p.img_scale = -1.0f;
             u.p.L_total = static_cast<const float*>(c->rendered.p);
-            FR_CUDA(c, launch_backward(u, vol->dtype, vol->kind, nt, s));
+            FR_CUDA(c, launch_backward(u, vol->dtype, vol->kind, nt, st));
             FR_TRY(trace_mark(c, FR_PHASE_ADJUST));
             FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, -p->grad_step,
-                                    p->update_sigma, p->clamp_nonneg, 1, s));
+                                    p->update_sigma, p->clamp_nonneg, 1, st));
         }
         if (hull)
-            FR_CUDA(c, launch_hull_clear(vol->data, vol->dtype, vol->nx, vol->ny, vol->nz, hull, full, nullptr, s));
+            FR_CUDA(c, launch_hull_clear(vol->data, vol->dtype, vol->nx, vol->ny, vol->nz, hull, full, nullptr, st));
         FR_TRY(trace_mark(c, FR_PHASE_APPLY));
-    }
-    FR_CUDA(c, launch_rmse(sq, iters, static_cast<float*>(c->rmse.p), s));
-    FR_TRY(trace_mark(c, FR_PHASE_FINISH));
-    if (rmse) {
-        if (rmse_is_host) {
-            FR_CUDA(c, cudaMemcpyAsync(rmse, c->rmse.p, (size_t)iters * 12, cudaMemcpyDeviceToHost, s));
-            FR_CUDA(c, cudaStreamSynchronize(s));
-        } else {
-            FR_CUDA(c, cudaMemcpyAsync(rmse, c->rmse.p, (size_t)iters * 12, cudaMemcpyDeviceToDevice, s));
+        return FR_OK;
+    };
+    if (!until) {
+        for (int it = 0; it < iters; ++it) FR_TRY(one_iteration(s, it));
+        FR_CUDA(c, launch_rmse(sq, iters, static_cast<float*>(c->rmse.p), s));
+        FR_TRY(trace_mark(c, FR_PHASE_FINISH));
+        if (rmse) {
+            if (rmse_is_host) {
+                FR_CUDA(c, cudaMemcpyAsync(rmse, c->rmse.p, (size_t)iters * 12, cudaMemcpyDeviceToHost, s));
+                FR_CUDA(c, cudaStreamSynchronize(s));
+            } else {
+                FR_CUDA(c, cudaMemcpyAsync(rmse, c->rmse.p, (size_t)iters * 12, cudaMemcpyDeviceToDevice, s));
+            }
         }
+        return FR_OK;
+    }
+
+    // Until the stop criterion: a graph whose conditional while node runs the
+    // iteration body; the body's last kernel records the iteration's error,
+    // advances the device iteration counter and ends the loop.  Graph bodies
+    // hold no event records, so tracing pauses during the capture.
+    int* loop_iter = static_cast<int*>(c->loop.p);
+    FR_CUDA(c, cudaMemsetAsync(loop_iter, 0, sizeof(int), s));
+    u.p.iter_dev = loop_iter;
+    if (!c->capture) FR_CUDA(c, cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    FR_CUDA(c, cudaGraphCreate(&graph, 0));
+    auto fail_graph = [&](cudaError_t e, const char* what) {
+        if (exec) cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return cuda_fail(c, e, what);
+    };
+    cudaGraphConditionalHandle handle;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return fail_graph(e, "cudaGraphConditionalHandleCreate");
+    // (the parameter union has members without default constructors: zeroed raw storage)
+    alignas(cudaGraphNodeParams) unsigned char np_bytes[sizeof(cudaGraphNodeParams)];
+    memset(np_bytes, 0, sizeof np_bytes);
+    cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(np_bytes);
+    np->type = cudaGraphNodeTypeConditional;
+    np->conditional.handle = handle;
+    np->conditional.type = cudaGraphCondTypeWhile;
+    np->conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, np);
+    if (e != cudaSuccess) return fail_graph(e, "cudaGraphAddNode (conditional)");
+    cudaGraph_t body = np->conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c->capture, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail_graph(e, "cudaStreamBeginCaptureToGraph");
+    const bool tracing = c->trace_on;
+    c->trace_on = false;
+    fr_status st = one_iteration(c->capture, -1);
+    if (st == FR_OK) {
+        cudaError_t ek = launch_converge(sq, static_cast<float*>(c->rmse.p), loop_iter,
+                                         p->rule == FR_RULE_PAPER ? flame_cnt : nullptr, iters, stop_delta, handle,
+                                         c->capture);
+        if (ek != cudaSuccess) st = cuda_fail(c, ek, "converge kernel");
+    }
+    c->trace_on = tracing;
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(c->capture, &captured);
+    if (st != FR_OK) {
+        cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return fail_graph(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) return fail_graph(e, "cudaGraphInstantiate");
+    e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) return fail_graph(e, "cudaGraphLaunch");
+    int done = 0;
+    e = cudaMemcpyAsync(c->host_counter, loop_iter, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_graph(e, "loop counter");
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    memcpy(&done, c->host_counter, sizeof(int));
+    if (iters_done) *iters_done = done;
+    if (rmse && done > 0) {
+        FR_CUDA(c, cudaMemcpyAsync(rmse, c->rmse.p, (size_t)done * 12,
+                                   rmse_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+        if (rmse_is_host) FR_CUDA(c, cudaStreamSynchronize(s));
     }
     return FR_OK;
+}
+
+extern "C" fr_status fr_reconstruct(fr_ctx* c, fr_volume* vol, const float* albedo, const fr_camera* cams,
+                                    int ncam, const float* targets, int targets_are_host, const int32_t* bbox,
+                                    int iters, int first_iteration, const fr_params* p, float* rmse,
+                                    int rmse_is_host)
+{
+    return reconstruct_impl(c, vol, albedo, cams, ncam, targets, targets_are_host, bbox, iters, first_iteration, p,
+                            rmse, rmse_is_host, -1.0f, nullptr);
+}
+
+extern "C" fr_status fr_reconstruct_until(fr_ctx* c, fr_volume* vol, const float* albedo, const fr_camera* cams,
+                                          int ncam, const float* targets, int targets_are_host,
+                                          const int32_t* bbox, int max_iters, float stop_delta,
+                                          int first_iteration, const fr_params* p, float* rmse, int rmse_is_host,
+                                          int32_t* iters_done)
+{
+    if (!c) return FR_EINVAL;
+    if (!(stop_delta >= 0.0f) || !std::isfinite(stop_delta))
+        return fail(c, FR_EINVAL, "stop_delta must be finite and >= 0");
+    if (!iters_done) return fail(c, FR_EINVAL, "iters_done is NULL");
+    if (max_iters < 1) return fail(c, FR_EINVAL, "max_iters must be >= 1");
+    *iters_done = 0;
+    return reconstruct_impl(c, vol, albedo, cams, ncam, targets, targets_are_host, bbox, max_iters,
+                            first_iteration, p, rmse, rmse_is_host, stop_delta, iters_done);
 }
 
 // ---------------------------------------------------------------------------

@@ -72,6 +72,9 @@ struct ProbDev {
     // non-zero); when set, the forward march skips empty bricks
     const unsigned char* occ;
     const unsigned* occ_box;     // box of the non-empty bricks (brick-table layout)
+    // when set, the adjustment's iteration index is iteration + *iter_dev
+    // (loops whose iterations are counted on the device)
+    const int* iter_dev;
     // flame-ray list the forward march writes (when set): flame pixels
     // appended warp by warp at *flist_count (zero before the launch)
     unsigned* flist;

@@ -55,6 +55,9 @@ cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* 
 cudaError_t launch_planck_lut(float t_min, float t_max, int m, float* lut, cudaStream_t s);
 cudaError_t launch_prepare_targets(float* targets, int ncam, int H, int W, float thresh, int* bbox,
                                    cudaStream_t s);
+// end of an iteration of a loop counted on the device (conditional graph body)
+cudaError_t launch_converge(const float* sq4, float* hist3, int* iter, unsigned* flame_count, int max_iters,
+                            float stop_delta, cudaGraphConditionalHandle handle, cudaStream_t s);
 cudaError_t launch_rmse(const float* sq4, int n, float* rmse3, cudaStream_t s);
 cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t s);
 // visual hull: sat needs ncam (H+1)(W+1) uint32, tags one uint32 per node

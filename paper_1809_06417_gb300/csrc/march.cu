@@ -426,7 +426,7 @@ __global__ void FR_ADJ_LIST_BOUNDS adj_list(const __grid_constant__ SingleArgs a
     const int view = (int)(pix / per_view);
     const unsigned r = pix - (unsigned)view * per_view;
     const int py = (int)(r / (unsigned)P.W), px = (int)(r - (unsigned)py * (unsigned)P.W);
-    adj_ray<DT, TAU, SKIP>(P, a.cams, view, px, py, P.iteration);
+    adj_ray<DT, TAU, SKIP>(P, a.cams, view, px, py, P.iteration + (P.iter_dev ? __ldg(P.iter_dev) : 0));
 }
 
 // Batched form: CTA b belongs to the problem whose tile range holds b and

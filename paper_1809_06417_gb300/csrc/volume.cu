@@ -802,6 +802,45 @@ __global__ void rmse_kernel(const float* sq4, int n, float* rmse3)
     for (int c = 0; c < 3; ++c) rmse3[3 * i + c] = cnt > 0.0f ? 255.0f * sqrtf(sq4[4 * i + c] / cnt) : 0.0f;
 }
 
+// End of one iteration of a device-counted loop (one thread): the image error
+// of iteration it = *iter from its squared-error sums (as rmse_kernel), the
+// stop criterion |E_it - E_it-1| < stop_delta in every channel (or the last
+// allowed iteration) ending the conditional loop, the counter advanced and the
+// flame-ray count cleared for the next forward march.
+__global__ void converge_kernel(const float* __restrict__ sq4, float* hist3, int* iter, unsigned* flame_count,
+                                int max_iters, float stop_delta, cudaGraphConditionalHandle handle)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int it = *iter;
+    if (it < 0 || it >= max_iters) {   // never expected: end the loop rather than write out of range
+        cudaGraphSetConditional(handle, 0u);
+        return;
+    }
+    const float cnt = sq4[3];
+    float r[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) r[c] = cnt > 0.0f ? 255.0f * sqrtf(sq4[c] / cnt) : 0.0f;
+    bool stop = it + 1 >= max_iters;
+    if (it >= 1) {
+        bool small = true;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) small = small && fabsf(r[c] - hist3[3 * (it - 1) + c]) < stop_delta;
+        stop = stop || small;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) hist3[3 * it + c] = r[c];
+    *iter = it + 1;
+    if (flame_count) *flame_count = 0u;
+    if (stop) cudaGraphSetConditional(handle, 0u);
+}
+
+cudaError_t launch_converge(const float* sq4, float* hist3, int* iter, unsigned* flame_count, int max_iters,
+                            float stop_delta, cudaGraphConditionalHandle handle, cudaStream_t s)
+{
+    converge_kernel<<<1, 32, 0, s>>>(sq4, hist3, iter, flame_count, max_iters, stop_delta, handle);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rmse(const float* sq4, int n, float* rmse3, cudaStream_t s)
 {
     rmse_kernel<<<(n + 127) / 128, 128, 0, s>>>(sq4, n, rmse3);

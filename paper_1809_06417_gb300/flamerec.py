@@ -98,6 +98,7 @@ SIGNATURES = {
     "fr_scatter_source": (_S, [_P, _P, _P, _P, _P]),
     "fr_planck_lut": (_S, [_P, _F, _F, _I, _P]),
     "fr_reconstruct": (_S, [_P, _P, _P, _P, _I, _P, _I, _P, _I, _I, _P, _P, _I]),
+    "fr_reconstruct_until": (_S, [_P, _P, _P, _P, _I, _P, _I, _P, _I, _F, _I, _P, _P, _I, _P]),
     "fr_count_samples": (_S, [_P, _P, _P, _I, _P, _P, _P]),
     "fr_reconstruct_batch": (_S, [_P, _P, _I, _I, _I, _P, _I]),
     "fr_visual_hull": (_S, [_P, _P, _P, _I, _P, _P, _P]),
@@ -282,6 +283,20 @@ class Context:
                                            _ptr(targets), int(bool(targets_are_host)), _ptr(bbox), int(iters),
                                            int(first_iteration), ctypes.byref(p), _ptr(rmse),
                                            int(rmse_is_host)))
+
+    def fr_reconstruct_until(self, vol, cams, targets, bbox, max_iters, stop_delta, p, albedo=None,
+                             first_iteration=0, rmse=None, targets_are_host=None):
+        """Iterates until the image error changes by less than stop_delta; returns the iterations run."""
+        if targets_are_host is None:
+            targets_are_host = not getattr(targets, "is_cuda", False)
+        rmse_is_host = rmse is not None and not getattr(rmse, "is_cuda", False)
+        done = ctypes.c_int32()
+        self.check(self.lib.fr_reconstruct_until(self.h, ctypes.byref(vol), _ptr(albedo), cams, len(cams),
+                                                 _ptr(targets), int(bool(targets_are_host)), _ptr(bbox),
+                                                 int(max_iters), float(stop_delta), int(first_iteration),
+                                                 ctypes.byref(p), _ptr(rmse), int(rmse_is_host),
+                                                 ctypes.byref(done)))
+        return done.value
 
     def fr_trace_phases(self, on=True):
         self.check(self.lib.fr_trace_phases(self.h, int(bool(on))))

@@ -150,3 +150,24 @@ def test_reconstruct_with_hull_keeps_outside_empty(orc):
             sq += (t ** 2).sum(axis=(0, 1))
             cnt += t.shape[0] * t.shape[1]
     np.testing.assert_allclose(rmse0[0], 255.0 * np.sqrt(sq / cnt), rtol=1e-12)
+
+
+def test_stop_criterion(orc):
+    """Sec. 3 stop criterion: the loop ends after the first iteration whose
+    image error differs from the previous one's by less than stop_delta in
+    every channel; an infinite threshold stops after two iterations, a zero
+    threshold never stops early, and a stopped run is a prefix of the full run."""
+    sc, P, v0, targets, mask, bbox, views = _recon_case(orc)
+    full, r_full, _ = orc.reconstruct(sc, v0, P, targets, mask, bbox, 8)
+    assert r_full.shape == (8, 3)
+    _, r_inf, _ = orc.reconstruct(sc, v0, P, targets, mask, bbox, 8, stop_delta=1e30)
+    assert r_inf.shape == (2, 3) and np.array_equal(r_inf, r_full[:2])
+    _, r_zero, _ = orc.reconstruct(sc, v0, P, targets, mask, bbox, 8, stop_delta=0.0)
+    assert np.array_equal(r_zero, r_full)
+    step = np.abs(np.diff(r_full, axis=0)).max(axis=1)   # largest channel change per iteration
+    assert np.all(np.diff(step) < 0)                      # shrinking steps on this case
+    delta = 0.5 * (step[2] + step[3])                     # first met at iteration 4 (index 3 + 1)
+    vol, r_mid, _ = orc.reconstruct(sc, v0, P, targets, mask, bbox, 8, stop_delta=delta)
+    assert r_mid.shape == (5, 3) and np.array_equal(r_mid, r_full[:5])
+    part, _, _ = orc.reconstruct(sc, v0, P, targets, mask, bbox, 5)
+    assert np.array_equal(vol, part)
