@@ -336,6 +336,17 @@ fr_status fr_job_release(fr_server *srv, fr_job *job);
 /* Device bytes currently held for resident jobs. */
 fr_status fr_server_memory(const fr_server *srv, size_t *used, size_t *budget);
 
+/* Volume data error (Sec. 5.1): per colour channel, the root mean square of
+ * the difference between the emission of two RGB volumes on the same grid
+ * (any storage types), over the key points whose tag equals full_mask (the
+ * visual hull's key points when tags come from fr_visual_hull and full_mask =
+ * 2^ncam - 1), or over all key points when tags is NULL; in the volumes' own
+ * units.  tags: device, one per node, nullable.  rmse3 (host, 3 floats) and
+ * *count (host, nullable: the key points compared) are written before the call
+ * returns (it synchronises the stream); rmse3 is 0 when none is compared. */
+fr_status fr_volume_rmse(fr_ctx *ctx, const fr_volume *a, const fr_volume *b, const uint32_t *tags,
+                         uint32_t full_mask, float *rmse3, int64_t *count);
+
 /* ---- Tracing: device time per phase of fr_reconstruct ---- */
 
 typedef enum {

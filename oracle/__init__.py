@@ -90,6 +90,7 @@ def _load():
             "orc_reconstruct": (None, [_P, _P, _P, _P, ctypes.c_int, _P, _P, _P, _P,
                                        ctypes.c_int, ctypes.c_int, _P, _P, _P, ctypes.c_double, _P]),
             "orc_visual_hull": (None, [_P, _P, ctypes.c_int, _P, _P]),
+            "orc_volume_rmse": (_I64, [_I64, _P, _P, _P, ctypes.c_uint32, _P]),
             "orc_planck": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
             "orc_temp_rgb": (None, [ctypes.c_double, _P]),
             "orc_lut_build": (None, [ctypes.c_double, ctypes.c_double, ctypes.c_int, _P]),
@@ -354,6 +355,23 @@ def reconstruct(scene: Scene, vol, params: Params, targets, mask, bbox, iters,
                         _ptr(hl) if hl is not None else None,
                         float(stop_delta) if stop_delta is not None else -1.0, ctypes.byref(done))
     return vol, rmse[:done.value], (int(samples[0]), int(samples[1]))
+
+
+def volume_rmse(a, b, tags=None, full=None):
+    """Volume data error (Sec. 5.1) of the emission channels over the key points
+    whose tag equals `full` (all key points without tags).  Returns (rmse3, count)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    if a.shape != b.shape or a.shape[-1] != 4:
+        raise ValueError("volumes must share a (..., 4) shape")
+    nodes = a.size // 4
+    tg = np.ascontiguousarray(tags, dtype=np.uint32) if tags is not None else None
+    if tg is not None and tg.size != nodes:
+        raise ValueError("one tag per node")
+    out = np.zeros(3)
+    n = _load().orc_volume_rmse(nodes, _ptr(a), _ptr(b), _ptr(tg) if tg is not None else None,
+                                int(full or 0), _ptr(out))
+    return out, int(n)
 
 
 def planck(lambda_m, temp_k):

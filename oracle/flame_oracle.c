@@ -807,6 +807,28 @@ void orc_visual_hull(const orc_grid *g, const orc_cam *cams, int ncam, const uin
             }
 }
 
+/* Volume data error (Sec. 5.1): per colour channel, the root mean square of
+ * the difference between two volumes' emission over the key points inside the
+ * visual hull (tags == full; every key point when tags is NULL), in the
+ * volumes' own units.  Returns the number of key points compared (rmse3 = 0
+ * when there are none). */
+int64_t orc_volume_rmse(int64_t nodes, const double *a, const double *b, const uint32_t *tags,
+                        uint32_t full, double *rmse3)
+{
+    double acc[3] = {0.0, 0.0, 0.0};
+    int64_t count = 0;
+    for (int64_t j = 0; j < nodes; ++j) {
+        if (tags && tags[j] != full) continue;
+        for (int ch = 0; ch < 3; ++ch) {
+            const double d = a[4 * j + ch] - b[4 * j + ch];
+            acc[ch] += d * d;
+        }
+        ++count;
+    }
+    for (int ch = 0; ch < 3; ++ch) rmse3[ch] = count ? sqrt(acc[ch] / (double)count) : 0.0;
+    return count;
+}
+
 /* ------------------------------------------------------------------------ */
 /* The iteration (Sec. 3, Algorithm 2): render, compare, adjust.             */
 /* ------------------------------------------------------------------------ */

@@ -26,6 +26,8 @@ struct Buf {
     size_t bytes = 0;
 };
 
+constexpr size_t kHostScratchBytes = 64;
+
 struct fr_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;   // where work is queued (borrowed; 0 = default stream)
@@ -36,8 +38,9 @@ struct fr_ctx {
     Buf occ;                         // brick occupancy for empty-space skipping
     Buf hull_bricks;                 // bricks holding a key point inside the visual hull
     Buf loop;                        // device iteration counter of fr_reconstruct_until
+    Buf verr;                        // volume-error partials and result
     Buf hull, sat;                   // visual hull tags, flame-mask tables
-    unsigned long long* host_counter = nullptr;
+    unsigned long long* host_counter = nullptr;  // pinned host scratch of kHostScratchBytes
     void* staging = nullptr;         // pinned host staging of batch tables
     size_t staging_bytes = 0;
     cudaEvent_t staging_done = nullptr;

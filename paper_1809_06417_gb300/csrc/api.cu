@@ -47,7 +47,7 @@ extern "C" fr_status fr_create(fr_ctx** out, int device, void* stream)
     if (!c) return FR_ENOMEM;
     c->device = device;
     if (cudaSetDevice(device) != cudaSuccess ||
-        cudaMallocHost(&c->host_counter, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMallocHost(&c->host_counter, kHostScratchBytes) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return FR_ECUDA;
@@ -64,7 +64,7 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     cudaStreamSynchronize(c->stream);
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
                    &c->rmse, &c->J, &c->src, &c->flame_cnt, &c->flame_list, &c->batch, &c->pairs,
-                   &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop})
+                   &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr})
         if (b->p) cudaFree(b->p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
     if (c->staging) cudaFreeHost(c->staging);
@@ -269,6 +269,32 @@ extern "C" fr_status fr_planck_lut(fr_ctx* c, float t_min, float t_max, int m, f
     FR_TRY(check_align(c, lut, 16, "lut"));
     FR_TRY(check_dev(c, lut, (size_t)m * 16, "lut"));
     FR_CUDA(c, launch_planck_lut(t_min, t_max, m, lut, c->stream));
+    return FR_OK;
+}
+
+extern "C" fr_status fr_volume_rmse(fr_ctx* c, const fr_volume* a, const fr_volume* b, const uint32_t* tags,
+                                    uint32_t full_mask, float* rmse3, int64_t* count)
+{
+    FR_BEGIN(c);
+    if (!rmse3) return fail(c, FR_EINVAL, "rmse3 is NULL");
+    FR_TRY(check_volume(c, a, "a"));
+    FR_TRY(check_volume(c, b, "b"));
+    if (a->kind != FR_KIND_RGB || b->kind != FR_KIND_RGB) return fail(c, FR_EINVAL, "RGB volumes are compared");
+    if (a->nx != b->nx || a->ny != b->ny || a->nz != b->nz) return fail(c, FR_EINVAL, "the grids differ");
+    const long long nodes = node_count(a);
+    if (tags) FR_TRY(check_dev(c, tags, (size_t)nodes * 4, "tags"));
+    const int g = volume_err_blocks(nodes);
+    FR_TRY(ensure(c, c->verr, align256((size_t)g * 16) + 32, "volume error"));
+    float* out = reinterpret_cast<float*>(static_cast<char*>(c->verr.p) + align256((size_t)g * 16));
+    FR_CUDA(c, launch_volume_err(a->data, a->dtype, b->data, b->dtype, nodes, tags, full_mask, c->verr.p, out,
+                                 c->stream));
+    FR_CUDA(c, cudaMemcpyAsync(c->host_counter, out, 24, cudaMemcpyDeviceToHost, c->stream));
+    FR_CUDA(c, cudaStreamSynchronize(c->stream));
+    const char* hs = reinterpret_cast<const char*>(c->host_counter);
+    unsigned long long n = 0;
+    memcpy(rmse3, hs, 12);
+    memcpy(&n, hs + 16, 8);
+    if (count) *count = (int64_t)n;
     return FR_OK;
 }
 

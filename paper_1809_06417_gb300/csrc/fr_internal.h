@@ -55,6 +55,12 @@ cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* 
 cudaError_t launch_planck_lut(float t_min, float t_max, int m, float* lut, cudaStream_t s);
 cudaError_t launch_prepare_targets(float* targets, int ncam, int H, int W, float thresh, int* bbox,
                                    cudaStream_t s);
+// volume data error of two RGB volumes' emission inside the hull: partials
+// (volume_err_blocks(nodes) x 16 bytes), out = rmse3, then the count as a
+// 64-bit integer at float offset 4
+int volume_err_blocks(long long nodes);
+cudaError_t launch_volume_err(const void* a, int dta, const void* b, int dtb, long long nodes, const unsigned* tags,
+                              unsigned full, void* partials, float* out, cudaStream_t s);
 // end of an iteration of a loop counted on the device (conditional graph body)
 cudaError_t launch_converge(const float* sq4, float* hist3, int* iter, unsigned* flame_count, int max_iters,
                             float stop_delta, cudaGraphConditionalHandle handle, cudaStream_t s);

@@ -802,6 +802,94 @@ __global__ void rmse_kernel(const float* sq4, int n, float* rmse3)
     for (int c = 0; c < 3; ++c) rmse3[3 * i + c] = cnt > 0.0f ? 255.0f * sqrtf(sq4[4 * i + c] / cnt) : 0.0f;
 }
 
+// Volume data error (Sec. 5.1): squared emission differences of two volumes
+// summed per CTA over the key points inside the hull (tags == full; all when
+// tags is null), then summed over the CTAs in a fixed order.
+struct ErrPartial {
+    float s[3];
+    unsigned n;
+};
+
+template <int DA, int DB>
+__global__ void __launch_bounds__(256) volume_err_kernel(const void* a, const void* b, long long nodes,
+                                                         const unsigned* __restrict__ tags, unsigned full,
+                                                         ErrPartial* partials)
+{
+    __shared__ float red[3][8];
+    __shared__ unsigned redn[8];
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    unsigned n = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (tags && __ldg(tags + i) != full) continue;
+        const float4 va = load_rgb<DA>(a, i), vb = load_rgb<DB>(b, i);
+        const float d0 = va.x - vb.x, d1 = va.y - vb.y, d2 = va.z - vb.z;
+        s0 = fmaf(d0, d0, s0); s1 = fmaf(d1, d1, s1); s2 = fmaf(d2, d2, s2);
+        ++n;
+    }
+    s0 = warp_sum(s0); s1 = warp_sum(s1); s2 = warp_sum(s2);
+    n = __reduce_add_sync(0xffffffffu, n);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { red[0][w] = s0; red[1][w] = s1; red[2][w] = s2; redn[w] = n; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ErrPartial p{{0.0f, 0.0f, 0.0f}, 0u};
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            p.s[0] += red[0][i]; p.s[1] += red[1][i]; p.s[2] += red[2][i]; p.n += redn[i];
+        }
+        partials[blockIdx.x] = p;
+    }
+}
+
+// out: rmse3 (3 floats) then the count (unsigned long long at byte 16).
+__global__ void __launch_bounds__(1024) volume_err_finish(const ErrPartial* partials, int np, float* out)
+{
+    __shared__ float red[3][32];
+    __shared__ unsigned long long redn[32];
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    unsigned long long n = 0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const ErrPartial p = partials[i];
+        s0 += p.s[0]; s1 += p.s[1]; s2 += p.s[2]; n += p.n;
+    }
+    s0 = warp_sum(s0); s1 = warp_sum(s1); s2 = warp_sum(s2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { red[0][w] = s0; red[1][w] = s1; red[2][w] = s2; redn[w] = n; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t[3] = {0.0f, 0.0f, 0.0f};
+        unsigned long long tn = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            t[0] += red[0][i]; t[1] += red[1][i]; t[2] += red[2][i]; tn += redn[i];
+        }
+        for (int c = 0; c < 3; ++c) out[c] = tn ? sqrtf(t[c] / (float)tn) : 0.0f;
+        *reinterpret_cast<unsigned long long*>(out + 4) = tn;
+    }
+}
+
+int volume_err_blocks(long long nodes) { return grid_for(nodes, 256); }
+
+cudaError_t launch_volume_err(const void* a, int dta, const void* b, int dtb, long long nodes, const unsigned* tags,
+                              unsigned full, void* partials, float* out, cudaStream_t s)
+{
+    const int g = grid_for(nodes, 256);
+    ErrPartial* pp = static_cast<ErrPartial*>(partials);
+#define FR_ERR(DA, DB) volume_err_kernel<DA, DB><<<g, 256, 0, s>>>(a, b, nodes, tags, full, pp)
+#define FR_ERR_B(DA)                              \
+    if (dtb == DT_F32) FR_ERR(DA, DT_F32);        \
+    else if (dtb == DT_BF16) FR_ERR(DA, DT_BF16); \
+    else FR_ERR(DA, DT_F16)
+    if (dta == DT_F32) { FR_ERR_B(DT_F32); }
+    else if (dta == DT_BF16) { FR_ERR_B(DT_BF16); }
+    else { FR_ERR_B(DT_F16); }
+#undef FR_ERR_B
+#undef FR_ERR
+    volume_err_finish<<<1, 1024, 0, s>>>(pp, g, out);
+    return cudaGetLastError();
+}
+
 // End of one iteration of a device-counted loop (one thread): the image error
 // of iteration it = *iter from its squared-error sums (as rmse_kernel), the
 // stop criterion |E_it - E_it-1| < stop_delta in every channel (or the last

@@ -111,6 +111,7 @@ SIGNATURES = {
     "fr_job_cancel": (_S, [_P, _P]),
     "fr_job_release": (_S, [_P, _P]),
     "fr_server_memory": (_S, [_P, _P, _P]),
+    "fr_volume_rmse": (_S, [_P, _P, _P, _P, ctypes.c_uint32, _P, _P]),
     "fr_trace_phases": (_S, [_P, _I]),
     "fr_phase_times": (_S, [_P, _P, _I, _P]),
     "fr_render_residual_noalloc": (_S, [_I, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, ctypes.c_char_p,
@@ -297,6 +298,14 @@ class Context:
                                                  ctypes.byref(p), _ptr(rmse), int(rmse_is_host),
                                                  ctypes.byref(done)))
         return done.value
+
+    def fr_volume_rmse(self, a, b, tags=None, full_mask=0):
+        """(rmse per colour channel, key points compared) of two RGB volumes (fr_volume)."""
+        out = (ctypes.c_float * 3)()
+        n = ctypes.c_int64()
+        self.check(self.lib.fr_volume_rmse(self.h, ctypes.byref(a), ctypes.byref(b), _ptr(tags), int(full_mask),
+                                           out, ctypes.byref(n)))
+        return np.array(list(out), dtype=np.float64), n.value
 
     def fr_trace_phases(self, on=True):
         self.check(self.lib.fr_trace_phases(self.h, int(bool(on))))

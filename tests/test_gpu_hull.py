@@ -130,3 +130,30 @@ def test_reconstruct_with_precomputed_tags_is_identical(fr_ctx):
     assert np.array_equal(a == 0, b == 0)
     assert np.max(rel_err(a, b)) < 1e-5
     np.testing.assert_allclose(out[0][1], out[1][1], rtol=1e-5)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_volume_rmse_follows_oracle(orc, fr_ctx, dtype):
+    """Volume data error in the hull (Sec. 5.1): GPU against the oracle fed the
+    same (rounded) records, with random tags, with no tags, and at full size."""
+    fr, ctx = fr_ctx
+    rng = np.random.default_rng(11)
+    for shape in ((13, 17, 11), (128, 128, 128)):
+        a = rng.random(shape[::-1] + (4,)).astype(np.float32)
+        b = (a + rng.normal(scale=0.1, size=a.shape)).astype(np.float32)
+        tags = rng.integers(0, 4, size=shape[::-1]).astype(np.uint32)
+        ta = torch.as_tensor(a, device="cuda").to(dtype).contiguous()
+        tb = torch.as_tensor(b, device="cuda").to(dtype).contiguous()
+        ra, rb = ta.float().cpu().numpy(), tb.float().cpu().numpy()
+        tt = torch.as_tensor(tags.view(np.int32), device="cuda")
+        h = 1.0 / (max(shape) - 1)
+        origin = tuple(-0.5 * (n - 1) * h for n in shape)
+        va, vb = fr.volume(ta, origin, h), fr.volume(tb, origin, h)
+        for tg, full in ((tt, 3), (None, 0)):
+            got, n = ctx.fr_volume_rmse(va, vb, tg, full)
+            ref, n_ref = orc.volume_rmse(ra, rb, tags if tg is not None else None, full)
+            assert n == n_ref
+            np.testing.assert_allclose(got, ref, rtol=1e-5)
+    # no key point compared
+    got, n = ctx.fr_volume_rmse(va, vb, torch.zeros_like(tt), 3)
+    assert n == 0 and np.all(got == 0.0)

@@ -171,3 +171,28 @@ def test_stop_criterion(orc):
     assert r_mid.shape == (5, 3) and np.array_equal(r_mid, r_full[:5])
     part, _, _ = orc.reconstruct(sc, v0, P, targets, mask, bbox, 5)
     assert np.array_equal(vol, part)
+
+
+def test_volume_rmse_in_hull(orc):
+    """Volume data error (Sec. 5.1) inside the hull: zero for equal volumes, |c|
+    for a constant offset c of one channel, blind to any difference outside
+    the hull, and taken over every key point without tags."""
+    rng = np.random.default_rng(4)
+    a = rng.random((6, 7, 5, 4))
+    tags = rng.integers(0, 8, size=(6, 7, 5)).astype(np.uint32)
+    full = 7
+    inside = tags == full
+    r, n = orc.volume_rmse(a, a, tags, full)
+    assert n == inside.sum() and np.all(r == 0.0)
+    b = a.copy()
+    b[..., 1] += 0.25
+    b[~inside] += rng.normal(size=(np.count_nonzero(~inside), 4)) * 100.0
+    r, n = orc.volume_rmse(a, b, tags, full)
+    assert np.allclose(r, [0.0, 0.25, 0.0], atol=1e-15)
+    b[..., 3] += 5.0                                     # extinction is not compared
+    r2, _ = orc.volume_rmse(a, b, tags, full)
+    assert np.array_equal(r, r2)
+    r3, n3 = orc.volume_rmse(a, a + 0.5, None)
+    assert n3 == a.size // 4 and np.allclose(r3, 0.5, atol=1e-15)
+    r4, n4 = orc.volume_rmse(a, b, np.zeros_like(tags), full)
+    assert n4 == 0 and np.all(r4 == 0.0)
