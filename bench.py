@@ -486,6 +486,60 @@ def run_serving(fr, ctx, jobs=40, rate=20.0, seed=5, step=0.5):
             "storage": "bf16", "mix": "grids {64,96,128,192}^3, 4-12 views, side 256-768, 20-50 iterations"}
 
 
+def run_temperature_views(fr, ctx, n=128, side=512, step=0.5, iters=50, seed=3, view_counts=(4, 16, 28)):
+    """Paper-literal temperature path (Sec. 3.3.3) against the number of cameras:
+    targets rendered from a seeded temperature field through the colour-
+    temperature table, the green channel reconstructed with the paper rule
+    inside the visual hull, the temperature read off the table; errors inside
+    the hull (Sec. 5.1), and on the key points inside every camera set's hull."""
+    import torch
+    from paper_1809_06417_gb300 import synth
+    t_min, t_max = 800.0, 2000.0
+    lut = torch.zeros((1024, 4), device="cuda")
+    ctx.fr_planck_lut(t_min, t_max, lut)
+    pt = dict(lut=lut, lut_t_min=t_min, lut_t_max=t_max)
+    gt = synth.temperature_volume(n, seed)
+    shape, origin, h = synth.unit_grid(n)
+    g = torch.as_tensor(gt, dtype=torch.float32, device="cuda").contiguous()
+    out, temps, hulls = {}, {}, {}
+    for views in view_counts:
+        cams = synth.ring_cameras(views, side, side, elevation_jitter_deg=10.0, seed=seed)
+        fc = fr.cameras(cams)
+        img = torch.zeros((views, side, side, 3), device="cuda")
+        ctx.fr_render(fr.volume(g, origin, h, kind=fr.FR_KIND_TEMP), fc, fr.params(step=step, **pt), img)
+        thresh = 30 / 255 * float(img.max())
+        bbox = torch.zeros((views, 4), dtype=torch.int32, device="cuda")
+        ctx.fr_prepare_targets(img, thresh, bbox)
+        rec = torch.zeros((n, n, n, 4), device="cuda")
+        rec[..., 3] = g[..., 1]
+        fv = fr.volume(rec, origin, h)
+        tags = torch.zeros((n, n, n), dtype=torch.int32, device="cuda")
+        ctx.fr_visual_hull(fv, fc, img, fr.params(flame_thresh=thresh), tags)
+        p = fr.params(step=step, alpha_l=alpha_for(n, views, side, step), flame_thresh=thresh, use_hull=1,
+                      hull_tags=tags)
+        rmse = np.zeros((iters, 3), dtype=np.float32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.fr_reconstruct(fv, fc, img, bbox, iters, p, rmse=rmse)
+        temp = torch.zeros((n, n, n, 2), device="cuda")
+        ctx.fr_temperature_from_green(fv, fr.params(**pt), fr.volume(temp, origin, h, kind=fr.FR_KIND_TEMP))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        temps[views] = temp.cpu().numpy()[..., 0]
+        hulls[views] = tags.cpu().numpy().view(np.uint32) == (1 << views) - 1
+        inside = hulls[views]
+        out[views] = {"seconds": dt, "hull_key_points": int(inside.sum()),
+                      "temperature_rmse_in_hull_K": float(np.sqrt(np.mean((temps[views][inside] -
+                                                                             gt[..., 0][inside]) ** 2))),
+                      "green_image_rmse_first_last": [float(rmse[0, 1]), float(rmse[-1, 1])]}
+    common = np.logical_and.reduce([hulls[v] for v in view_counts])
+    for views in view_counts:
+        out[views]["temperature_rmse_in_all_hulls_K"] = float(
+            np.sqrt(np.mean((temps[views][common] - gt[..., 0][common]) ** 2)))
+    return {"workload": f"temperature_green_{n}^3_{side}^2_{iters}it", "common_key_points": int(common.sum()),
+            "views": {str(k): v for k, v in out.items()}}
+
+
 class OracleSample:
     """The oracle on bounded samples of the workload: a band of image rows of
     one view, one iteration (in-scattering source, render of those pixels,
@@ -617,6 +671,7 @@ def main():
         ctx = fr.Context(local)
         out["video"] = run_video(fr, ctx, storage=args.storage)
         out["serving"] = run_serving(fr, ctx, jobs=args.serving_jobs)
+        out["temperature_views"] = run_temperature_views(fr, ctx)
         ctx.close()
     if rank == 0:
         out["cpu_baseline"] = cpu

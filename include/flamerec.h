@@ -336,6 +336,16 @@ fr_status fr_job_release(fr_server *srv, fr_job *job);
 /* Device bytes currently held for resident jobs. */
 fr_status fr_server_memory(const fr_server *srv, size_t *used, size_t *budget);
 
+/* Temperature from the green channel (Sec. 3.3.3): the paper reconstructs the
+ * green channel and reads the temperature off the colour-temperature mapping.
+ * Per node, T = the inverse of the table's piecewise-linear green column
+ * (p->lut, lut_size x {r, g, b, 0} float32 from fr_planck_lut over
+ * [p->lut_t_min, p->lut_t_max]; its green column must increase strictly, which
+ * it does over 800-2000 K) at the record's green value, clamped to the range;
+ * the record's extinction is copied.  rgb: RGB records; temp: temperature
+ * records on the same grid (any storage types).  Asynchronous. */
+fr_status fr_temperature_from_green(fr_ctx *ctx, const fr_volume *rgb, const fr_params *p, fr_volume *temp);
+
 /* Volume data error (Sec. 5.1): per colour channel, the root mean square of
  * the difference between the emission of two RGB volumes on the same grid
  * (any storage types), over the key points whose tag equals full_mask (the

@@ -94,6 +94,7 @@ def _load():
             "orc_planck": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
             "orc_temp_rgb": (None, [ctypes.c_double, _P]),
             "orc_lut_build": (None, [ctypes.c_double, ctypes.c_double, ctypes.c_int, _P]),
+            "orc_green_to_temp": (ctypes.c_double, [_P, ctypes.c_double]),
             "orc_hg_phase": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
             "orc_g_draw": (ctypes.c_double, [ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
                                              ctypes.c_int, _I64, _I64]),
@@ -226,6 +227,16 @@ def _lut_struct(lut, t_min, t_max):
     L.lut = lut.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     L.m, L.t_min, L.t_max = lut.shape[0], float(t_min), float(t_max)
     return L, lut
+
+
+def green_to_temp(green, lut, t_min, t_max):
+    """Sec. 3.3.3: temperatures whose table green value is `green` (array)."""
+    lib = _load()
+    L, keep = _lut_struct(lut, t_min, t_max)
+    g = np.asarray(green, dtype=np.float64)
+    out = np.array([lib.orc_green_to_temp(ctypes.byref(L), float(x)) for x in g.ravel()])
+    del keep
+    return out.reshape(g.shape)
 
 
 def render_temp(scene: Scene, vol_ts, lut, t_min, t_max, params: Params):

@@ -240,6 +240,29 @@ static void lut_eval(const orc_lut *L, double t, double q[3], double dq[3])
     }
 }
 
+/* Temperature from a green value (Sec. 3.3.3: the temperature is recovered
+ * through the green channel, which grows with temperature over the table's
+ * range): the inverse of the table's piecewise-linear green interpolant.  The
+ * segment i with g_i <= g <= g_{i+1} is found by bisection; values below the
+ * first entry give t_min, above the last t_max.  The green column must be
+ * strictly increasing. */
+double orc_green_to_temp(const orc_lut *L, double green)
+{
+    const double *lut = L->lut;
+    const int m = L->m;
+    if (!(green > lut[1])) return L->t_min;
+    if (!(green < lut[3 * (int64_t)(m - 1) + 1])) return L->t_max;
+    int lo = 0, hi = m - 1;   /* lut_g[lo] < green < lut_g[hi] */
+    while (hi - lo > 1) {
+        const int mid = lo + (hi - lo) / 2;
+        if (lut[3 * (int64_t)mid + 1] <= green) lo = mid;
+        else hi = mid;
+    }
+    const double a = lut[3 * (int64_t)lo + 1], b = lut[3 * (int64_t)hi + 1];
+    const double f = (green - a) / (b - a);
+    return L->t_min + ((double)lo + f) * (L->t_max - L->t_min) / (double)(m - 1);
+}
+
 /* Henyey-Greenstein phase function, Eq. 9; cos_wi = omega . omega_i. */
 double orc_hg_phase(double g, double cos_wi)
 {

@@ -272,6 +272,26 @@ extern "C" fr_status fr_planck_lut(fr_ctx* c, float t_min, float t_max, int m, f
     return FR_OK;
 }
 
+extern "C" fr_status fr_temperature_from_green(fr_ctx* c, const fr_volume* rgb, const fr_params* p,
+                                               fr_volume* temp)
+{
+    FR_BEGIN(c);
+    if (!p) return fail(c, FR_EINVAL, "p is NULL");
+    FR_TRY(check_volume(c, rgb, "rgb"));
+    FR_TRY(check_volume(c, temp, "temp"));
+    if (rgb->kind != FR_KIND_RGB || temp->kind != FR_KIND_TEMP)
+        return fail(c, FR_EINVAL, "rgb must hold RGB records and temp temperature records");
+    if (rgb->nx != temp->nx || rgb->ny != temp->ny || rgb->nz != temp->nz)
+        return fail(c, FR_EINVAL, "the grids differ");
+    if (!p->lut || p->lut_size < 2 || !(p->lut_t_max > p->lut_t_min))
+        return fail(c, FR_EINVAL, "needs lut, lut_size >= 2 and lut_t_max > lut_t_min");
+    FR_TRY(check_align(c, p->lut, 16, "lut"));
+    FR_TRY(check_dev(c, p->lut, (size_t)p->lut_size * 16, "lut"));
+    FR_CUDA(c, launch_green_to_temp(rgb->data, rgb->dtype, temp->data, temp->dtype, node_count(rgb), p->lut,
+                                    p->lut_size, p->lut_t_min, p->lut_t_max, c->stream));
+    return FR_OK;
+}
+
 extern "C" fr_status fr_volume_rmse(fr_ctx* c, const fr_volume* a, const fr_volume* b, const uint32_t* tags,
                                     uint32_t full_mask, float* rmse3, int64_t* count)
 {

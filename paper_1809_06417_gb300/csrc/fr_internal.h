@@ -55,6 +55,9 @@ cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* 
 cudaError_t launch_planck_lut(float t_min, float t_max, int m, float* lut, cudaStream_t s);
 cudaError_t launch_prepare_targets(float* targets, int ncam, int H, int W, float thresh, int* bbox,
                                    cudaStream_t s);
+// temperature records {T, sigma} from the green channel of RGB records
+cudaError_t launch_green_to_temp(const void* rgb, int dt_rgb, void* temp, int dt_temp, long long nodes,
+                                 const float* lut, int m, float t_min, float t_max, cudaStream_t s);
 // volume data error of two RGB volumes' emission inside the hull: partials
 // (volume_err_blocks(nodes) x 16 bytes), out = rmse3, then the count as a
 // 64-bit integer at float offset 4

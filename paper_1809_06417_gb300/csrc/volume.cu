@@ -802,6 +802,57 @@ __global__ void rmse_kernel(const float* sq4, int n, float* rmse3)
     for (int c = 0; c < 3; ++c) rmse3[3 * i + c] = cnt > 0.0f ? 255.0f * sqrtf(sq4[4 * i + c] / cnt) : 0.0f;
 }
 
+// Temperature from the green channel (Sec. 3.3.3): per node, the inverse of
+// the table's piecewise-linear green column (bisection over its m entries,
+// strictly increasing), clamped to [t_min, t_max]; the extinction is copied.
+template <int DR, int DT>
+__global__ void __launch_bounds__(256) green_to_temp_kernel(const void* rgb, void* temp, long long nodes,
+                                                            const float4* __restrict__ lut, int m, float t_min,
+                                                            float t_max)
+{
+    const float g_lo = __ldg(&lut[0].y), g_hi = __ldg(&lut[m - 1].y);
+    const float dt = (t_max - t_min) / (float)(m - 1);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 r = load_rgb<DR>(rgb, i);
+        const float g = r.y;
+        float t;
+        if (!(g > g_lo)) {
+            t = t_min;
+        } else if (!(g < g_hi)) {
+            t = t_max;
+        } else {
+            int lo = 0, hi = m - 1;   // lut[lo].y < g < lut[hi].y
+            while (hi - lo > 1) {
+                const int mid = lo + ((hi - lo) >> 1);
+                if (__ldg(&lut[mid].y) <= g) lo = mid;
+                else hi = mid;
+            }
+            const float a = __ldg(&lut[lo].y), b = __ldg(&lut[hi].y);
+            t = t_min + ((float)lo + (g - a) / (b - a)) * dt;
+        }
+        store_ts<DT>(temp, i, make_float2(t, r.w));
+    }
+}
+
+cudaError_t launch_green_to_temp(const void* rgb, int dt_rgb, void* temp, int dt_temp, long long nodes,
+                                 const float* lut, int m, float t_min, float t_max, cudaStream_t s)
+{
+    const int g = grid_for(nodes, 256);
+    const float4* l4 = reinterpret_cast<const float4*>(lut);
+#define FR_G2T(DR, DT) green_to_temp_kernel<DR, DT><<<g, 256, 0, s>>>(rgb, temp, nodes, l4, m, t_min, t_max)
+#define FR_G2T_T(DR)                                \
+    if (dt_temp == DT_F32) FR_G2T(DR, DT_F32);      \
+    else if (dt_temp == DT_BF16) FR_G2T(DR, DT_BF16); \
+    else FR_G2T(DR, DT_F16)
+    if (dt_rgb == DT_F32) { FR_G2T_T(DT_F32); }
+    else if (dt_rgb == DT_BF16) { FR_G2T_T(DT_BF16); }
+    else { FR_G2T_T(DT_F16); }
+#undef FR_G2T_T
+#undef FR_G2T
+    return cudaGetLastError();
+}
+
 // Volume data error (Sec. 5.1): squared emission differences of two volumes
 // summed per CTA over the key points inside the hull (tags == full; all when
 // tags is null), then summed over the CTAs in a fixed order.

@@ -112,6 +112,7 @@ SIGNATURES = {
     "fr_job_release": (_S, [_P, _P]),
     "fr_server_memory": (_S, [_P, _P, _P]),
     "fr_volume_rmse": (_S, [_P, _P, _P, _P, ctypes.c_uint32, _P, _P]),
+    "fr_temperature_from_green": (_S, [_P, _P, _P, _P]),
     "fr_trace_phases": (_S, [_P, _I]),
     "fr_phase_times": (_S, [_P, _P, _I, _P]),
     "fr_render_residual_noalloc": (_S, [_I, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, ctypes.c_char_p,
@@ -298,6 +299,10 @@ class Context:
                                                  ctypes.byref(p), _ptr(rmse), int(rmse_is_host),
                                                  ctypes.byref(done)))
         return done.value
+
+    def fr_temperature_from_green(self, rgb, p, temp):
+        self.check(self.lib.fr_temperature_from_green(self.h, ctypes.byref(rgb), ctypes.byref(p),
+                                                      ctypes.byref(temp)))
 
     def fr_volume_rmse(self, a, b, tags=None, full_mask=0):
         """(rmse per colour channel, key points compared) of two RGB volumes (fr_volume)."""
