@@ -486,19 +486,20 @@ def run_serving(fr, ctx, jobs=40, rate=20.0, seed=5, step=0.5):
             "storage": "bf16", "mix": "grids {64,96,128,192}^3, 4-12 views, side 256-768, 20-50 iterations"}
 
 
-def run_temperature_views(fr, ctx, n=128, side=512, step=0.5, iters=50, seed=3, view_counts=(4, 16, 28)):
-    """Paper-literal temperature path (Sec. 3.3.3) against the number of cameras:
+def run_temperature_views(fr, ctx, n=128, side=512, step=0.5, iters=50, seed=3, view_counts=(4, 16, 28),
+                          t_min=1000.0, t_max=2300.0):
+    """Paper-literal temperature path (Sec. 3.3.3) against the number of cameras
+    (Sec. 5.2: 4, 16 and 28 cameras, temperatures in 1000-2300 K):
     targets rendered from a seeded temperature field through the colour-
     temperature table, the green channel reconstructed with the paper rule
     inside the visual hull, the temperature read off the table; errors inside
     the hull (Sec. 5.1), and on the key points inside every camera set's hull."""
     import torch
     from paper_1809_06417_gb300 import synth
-    t_min, t_max = 800.0, 2000.0
     lut = torch.zeros((1024, 4), device="cuda")
     ctx.fr_planck_lut(t_min, t_max, lut)
     pt = dict(lut=lut, lut_t_min=t_min, lut_t_max=t_max)
-    gt = synth.temperature_volume(n, seed)
+    gt = synth.temperature_volume(n, seed, t_min=t_min, t_max=t_max)
     shape, origin, h = synth.unit_grid(n)
     g = torch.as_tensor(gt, dtype=torch.float32, device="cuda").contiguous()
     out, temps, hulls = {}, {}, {}
@@ -536,8 +537,58 @@ def run_temperature_views(fr, ctx, n=128, side=512, step=0.5, iters=50, seed=3, 
     for views in view_counts:
         out[views]["temperature_rmse_in_all_hulls_K"] = float(
             np.sqrt(np.mean((temps[views][common] - gt[..., 0][common]) ** 2)))
-    return {"workload": f"temperature_green_{n}^3_{side}^2_{iters}it", "common_key_points": int(common.sum()),
+    return {"workload": f"temperature_green_{n}^3_{side}^2_{iters}it", "range_K": [t_min, t_max],
+            "common_key_points": int(common.sum()),
             "views": {str(k): v for k, v in out.items()}}
+
+
+def run_held_out(fr, ctx, n=128, views=10, side=512, step=0.5, iters=50, seed=2):
+    """The paper's extra evaluation: reconstruct from nine of ten views (full
+    RTE, visual hull) and render the tenth, which the reconstruction never saw."""
+    import torch
+    from paper_1809_06417_gb300 import synth
+    shape, origin, h = synth.unit_grid(n)
+    gt, albedo = synth.plume_volume(n, seed)
+    cams = synth.ring_cameras(views, side, side, elevation_jitter_deg=10.0, seed=seed)
+    g = torch.as_tensor(gt, dtype=torch.float32, device="cuda").contiguous()
+    alb = torch.as_tensor(albedo, dtype=torch.float32, device="cuda").contiguous()
+    src = torch.empty_like(g)
+    J = torch.empty((n, n, n, 4), device="cuda")
+    ctx.fr_scatter_source(fr.volume(g, origin, h), alb, J, fr.volume(src, origin, h))
+    img = torch.zeros((views, side, side, 3), device="cuda")
+    ctx.fr_render(fr.volume(src, origin, h), fr.cameras(cams), fr.params(step=step), img)
+    img /= img.max()
+    k = views - 1
+    t_in, t_out = img[:k].contiguous(), img[k:].contiguous()
+    b_in = torch.zeros((k, 4), dtype=torch.int32, device="cuda")
+    b_out = torch.zeros((1, 4), dtype=torch.int32, device="cuda")
+    ctx.fr_prepare_targets(t_in, 30 / 255, b_in)
+    ctx.fr_prepare_targets(t_out, 30 / 255, b_out)
+    c_in, c_out = fr.cameras(cams[:k]), fr.cameras(cams[k:])
+    v = g.clone()
+    v[..., :3] = 0.0
+    fv = fr.volume(v, origin, h)
+
+    def view_rmse(cams_, targets, bbox):
+        s_ = torch.empty((4,), device="cuda")
+        res = torch.empty_like(targets)
+        ren = torch.empty_like(targets)
+        s_.zero_()
+        # the test view is rendered with in-scattering from the current volume
+        ctx.fr_scatter_source(fv, alb, J, fr.volume(src, origin, h))
+        ctx.fr_render_residual(fr.volume(src, origin, h), cams_, fr.params(step=step), targets, bbox, ren, res, s_)
+        q = s_.cpu().numpy().astype(np.float64)
+        return [float(x) for x in 255.0 * np.sqrt(q[:3] / max(q[3], 1.0))]
+
+    before = view_rmse(c_out, t_out, b_out)
+    p = fr.params(step=step, alpha_l=alpha_for(n, k, side, step), use_hull=1)
+    rmse = np.zeros((iters, 3), dtype=np.float32)
+    ctx.fr_reconstruct(fv, c_in, t_in, b_in, iters, p, albedo=alb, rmse=rmse)
+    after = view_rmse(c_out, t_out, b_out)
+    fit = view_rmse(c_in, t_in, b_in)
+    return {"workload": f"held_out_{n}^3_{k}+1x{side}^2_{iters}it", "test_view_rmse_before": before,
+            "test_view_rmse_after": after, "input_views_rmse_after": fit,
+            "input_views_rmse_first": [float(x) for x in rmse[0]]}
 
 
 class OracleSample:
@@ -672,6 +723,7 @@ def main():
         out["video"] = run_video(fr, ctx, storage=args.storage)
         out["serving"] = run_serving(fr, ctx, jobs=args.serving_jobs)
         out["temperature_views"] = run_temperature_views(fr, ctx)
+        out["held_out_view"] = run_held_out(fr, ctx)
         ctx.close()
     if rank == 0:
         out["cpu_baseline"] = cpu

@@ -357,6 +357,31 @@ fr_status fr_temperature_from_green(fr_ctx *ctx, const fr_volume *rgb, const fr_
 fr_status fr_volume_rmse(fr_ctx *ctx, const fr_volume *a, const fr_volume *b, const uint32_t *tags,
                          uint32_t full_mask, float *rmse3, int64_t *count);
 
+/* ---- Cameras and grids (host arithmetic, no context, no device) ---- */
+
+/* A pinhole camera from a 3x4 projection P (row-major, double), pixel
+ * coordinates [u, v, w] = P [X, Y, Z, 1] with pixel centres at integers, u to
+ * the right and v down: P = K [R | -R C], K = [[f, s, c_u], [0, f_v, c_v],
+ * [0, 0, 1]], found by an RQ decomposition of P's left 3x3 block.  The model of
+ * fr_camera has square pixels, no skew and the principal point at the image
+ * centre: FR_EINVAL unless |s| and |f - f_v| are below 1e-6 f and the principal
+ * point is within 1e-3 pixel of ((width - 1) / 2, (height - 1) / 2).  Output:
+ * pos = C, right = R row 0, up = -R row 1, fwd = R row 2,
+ * tan_half_fov = height / (2 f_v). */
+fr_status fr_camera_from_projection(const double P[12], int width, int height, fr_camera *out);
+
+/* Volume dimensions (Sec. 4.2): for the world box [box_min, box_max] and the
+ * cameras, each of the box's 12 edges is projected into every image; the
+ * largest number of pixels an edge along axis d spans in u or v over all
+ * images is n_d, and the voxel edge that rule asks for along d is
+ * alpha l_d / n_d (l_d the box length, alpha = 1.5 in the paper).  The grid
+ * here has cubic voxels, so h = the smallest of the three edges and
+ * dims[d] = ceil(l_d / h) + 1 nodes, from origin box_min.  FR_EINVAL when a
+ * box corner is not in front of a camera (z_c <= 0) or the box is empty.
+ * n (nullable): the three n_d. */
+fr_status fr_volume_dims(const fr_camera *cams, int ncam, const float box_min[3], const float box_max[3],
+                         float alpha, int32_t dims[3], float *h, float n[3]);
+
 /* ---- Tracing: device time per phase of fr_reconstruct ---- */
 
 typedef enum {

@@ -91,6 +91,7 @@ def _load():
                                        ctypes.c_int, ctypes.c_int, _P, _P, _P, ctypes.c_double, _P]),
             "orc_visual_hull": (None, [_P, _P, ctypes.c_int, _P, _P]),
             "orc_volume_rmse": (_I64, [_I64, _P, _P, _P, ctypes.c_uint32, _P]),
+            "orc_volume_dims": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_double, _P, _P, _P]),
             "orc_planck": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
             "orc_temp_rgb": (None, [ctypes.c_double, _P]),
             "orc_lut_build": (None, [ctypes.c_double, ctypes.c_double, ctypes.c_int, _P]),
@@ -366,6 +367,21 @@ def reconstruct(scene: Scene, vol, params: Params, targets, mask, bbox, iters,
                         _ptr(hl) if hl is not None else None,
                         float(stop_delta) if stop_delta is not None else -1.0, ctypes.byref(done))
     return vol, rmse[:done.value], (int(samples[0]), int(samples[1]))
+
+
+def volume_dims(cams, box_min, box_max, alpha=1.5):
+    """Sec. 4.2 volume dimensions: (dims, h, n per axis); ValueError when a box
+    corner is behind a camera."""
+    sc = Scene((2, 2, 2), (0.0, 0.0, 0.0), 1.0, cams)
+    lo = np.ascontiguousarray(box_min, dtype=np.float64)
+    ln = np.ascontiguousarray(np.asarray(box_max, dtype=np.float64) - lo)
+    dims = np.zeros(3, dtype=np.int32)
+    h = ctypes.c_double()
+    n = np.zeros(3)
+    if _load().orc_volume_dims(sc.cams, sc.ncam, _ptr(lo), _ptr(ln), float(alpha), _ptr(dims),
+                               ctypes.byref(h), _ptr(n)) != 0:
+        raise ValueError("a box corner is not in front of a camera")
+    return tuple(int(x) for x in dims), h.value, tuple(n)
 
 
 def volume_rmse(a, b, tags=None, full=None):

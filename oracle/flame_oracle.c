@@ -830,6 +830,50 @@ void orc_visual_hull(const orc_grid *g, const orc_cam *cams, int ncam, const uin
             }
 }
 
+/* Volume dimensions (Sec. 4.2): project the 8 corners of the world box
+ * [lo, lo + len] into every image; for each of the 12 edges (along axis d) the
+ * pixels it spans are the larger of |du| and |dv|; n_d is the largest over
+ * edges and images; the voxel edge along d is alpha len_d / n_d.  Reading for
+ * cubic voxels: h = the smallest of the three, dims_d = ceil(len_d / h) + 1
+ * nodes.  Returns 0, or -1 when a corner is not in front of a camera. */
+int orc_volume_dims(const orc_cam *cams, int ncam, const double lo[3], const double len[3], double alpha,
+                    int dims[3], double *h, double nmax[3])
+{
+    for (int d = 0; d < 3; ++d) nmax[d] = 0.0;
+    for (int v = 0; v < ncam; ++v) {
+        const orc_cam *c = cams + v;
+        const double ty = c->tan_half_fov, tx = ty * (double)c->width / (double)c->height;
+        double u[8], w[8];
+        for (int b = 0; b < 8; ++b) {
+            double rel[3];
+            for (int d = 0; d < 3; ++d) rel[d] = lo[d] + (((b >> d) & 1) ? len[d] : 0.0) - c->pos[d];
+            const double xc = rel[0] * c->right[0] + rel[1] * c->right[1] + rel[2] * c->right[2];
+            const double yc = rel[0] * c->up[0] + rel[1] * c->up[1] + rel[2] * c->up[2];
+            const double zc = rel[0] * c->fwd[0] + rel[1] * c->fwd[1] + rel[2] * c->fwd[2];
+            if (!(zc > 0.0)) return -1;
+            u[b] = (xc / zc / tx + 1.0) * 0.5 * c->width - 0.5;
+            w[b] = (1.0 - yc / zc / ty) * 0.5 * c->height - 0.5;
+        }
+        for (int b = 0; b < 8; ++b)
+            for (int d = 0; d < 3; ++d) {
+                if ((b >> d) & 1) continue;
+                const int e = b | (1 << d);
+                double span = fabs(u[e] - u[b]);
+                if (fabs(w[e] - w[b]) > span) span = fabs(w[e] - w[b]);
+                if (span > nmax[d]) nmax[d] = span;
+            }
+    }
+    double best = INFINITY;
+    for (int d = 0; d < 3; ++d) {
+        if (!(nmax[d] > 0.0)) return -1;
+        const double e = alpha * len[d] / nmax[d];
+        if (e < best) best = e;
+    }
+    *h = best;
+    for (int d = 0; d < 3; ++d) dims[d] = (int)ceil(len[d] / best - 1e-9) + 1;
+    return 0;
+}
+
 /* Volume data error (Sec. 5.1): per colour channel, the root mean square of
  * the difference between two volumes' emission over the key points inside the
  * visual hull (tags == full; every key point when tags is NULL), in the

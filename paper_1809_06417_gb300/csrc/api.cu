@@ -272,6 +272,133 @@ extern "C" fr_status fr_planck_lut(fr_ctx* c, float t_min, float t_max, int m, f
     return FR_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Cameras and grids (host arithmetic)
+// ---------------------------------------------------------------------------
+
+extern "C" fr_status fr_camera_from_projection(const double P[12], int width, int height, fr_camera* out)
+{
+    if (!P || !out || width < 1 || height < 1) return FR_EINVAL;
+    // RQ decomposition of M = P[:, :3] = K R by Givens rotations: zero M[2][1],
+    // then M[2][0], then M[1][0] with rotations about x, y, z applied on the right.
+    // P and -P are the same camera: take the sign that gives det(M) > 0, so
+    // that R is a proper rotation
+    double Pm[12];
+    for (int i = 0; i < 12; ++i) Pm[i] = P[i];
+    const double detM = Pm[0] * (Pm[5] * Pm[10] - Pm[6] * Pm[9]) - Pm[1] * (Pm[4] * Pm[10] - Pm[6] * Pm[8]) +
+                        Pm[2] * (Pm[4] * Pm[9] - Pm[5] * Pm[8]);
+    if (!(detM != 0.0) || !std::isfinite(detM)) return FR_EINVAL;
+    if (detM < 0.0)
+        for (int i = 0; i < 12; ++i) Pm[i] = -Pm[i];
+    double M[3][3], Q[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) M[r][c] = Pm[4 * r + c];
+    auto rotate = [&](int a, int b, double cth, double sth) {
+        // M <- M G, Q <- G^T Q with G the rotation in the (a, b) plane
+        for (int r = 0; r < 3; ++r) {
+            const double ma = M[r][a], mb = M[r][b];
+            M[r][a] = ma * cth + mb * sth;
+            M[r][b] = -ma * sth + mb * cth;
+        }
+        for (int c = 0; c < 3; ++c) {
+            const double qa = Q[a][c], qb = Q[b][c];
+            Q[a][c] = cth * qa + sth * qb;
+            Q[b][c] = -sth * qa + cth * qb;
+        }
+    };
+    auto zero = [&](int row, int a, int b) {   // zero M[row][a] using column b
+        const double x = M[row][a], y = M[row][b], r = std::hypot(x, y);
+        if (r == 0.0) return;
+        rotate(a, b, y / r, -x / r);
+    };
+    zero(2, 1, 2);
+    zero(2, 0, 2);
+    zero(1, 0, 1);
+    // make K's diagonal positive: flip signs of K's columns and R's rows
+    for (int d = 0; d < 3; ++d)
+        if (M[d][d] < 0.0) {
+            for (int r = 0; r < 3; ++r) M[r][d] = -M[r][d];
+            for (int c = 0; c < 3; ++c) Q[d][c] = -Q[d][c];
+        }
+    if (!(M[2][2] > 0.0)) return FR_EINVAL;
+    double K[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) K[r][c] = M[r][c] / M[2][2];
+    const double f = K[0][0], fv = K[1][1], sk = K[0][1], cu = K[0][2], cv = K[1][2];
+    if (!(f > 0.0) || std::fabs(sk) > 1e-6 * f || std::fabs(f - fv) > 1e-6 * f) return FR_EINVAL;
+    if (std::fabs(cu - 0.5 * (width - 1)) > 1e-3 || std::fabs(cv - 0.5 * (height - 1)) > 1e-3) return FR_EINVAL;
+    // centre: the left block is now K' R with K' = M (upper triangular, K
+    // scaled by M[2][2]), and p4 = -K' R C, so C = -R^T K'^-1 p4 (back substitution)
+    const double p4[3] = {Pm[3], Pm[7], Pm[11]};
+    double y[3];
+    y[2] = p4[2] / M[2][2];
+    y[1] = (p4[1] - M[1][2] * y[2]) / M[1][1];
+    y[0] = (p4[0] - M[0][1] * y[1] - M[0][2] * y[2]) / M[0][0];
+    fr_camera cam;
+    memset(&cam, 0, sizeof cam);
+    for (int a = 0; a < 3; ++a) {
+        cam.pos[a] = (float)(-(Q[0][a] * y[0] + Q[1][a] * y[1] + Q[2][a] * y[2]));
+        cam.right[a] = (float)Q[0][a];
+        cam.up[a] = (float)(-Q[1][a]);
+        cam.fwd[a] = (float)Q[2][a];
+    }
+    cam.tan_half_fov = (float)(height / (2.0 * fv));
+    cam.width = width;
+    cam.height = height;
+    *out = cam;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_volume_dims(const fr_camera* cams, int ncam, const float box_min[3], const float box_max[3],
+                                    float alpha, int32_t dims[3], float* h, float n[3])
+{
+    if (!cams || ncam < 1 || !box_min || !box_max || !dims || !h || !(alpha > 0.0f)) return FR_EINVAL;
+    double lo[3], len[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = box_min[d];
+        len[d] = (double)box_max[d] - box_min[d];
+        if (!(len[d] > 0.0)) return FR_EINVAL;
+    }
+    double nmax[3] = {0.0, 0.0, 0.0};
+    for (int v = 0; v < ncam; ++v) {
+        const fr_camera& c = cams[v];
+        const double ty = c.tan_half_fov, tx = ty * c.width / c.height;
+        double uv[8][2];
+        for (int b = 0; b < 8; ++b) {
+            double X[3], xc = 0.0, yc = 0.0, zc = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                X[d] = (((b >> d) & 1) ? lo[d] + len[d] : lo[d]) - c.pos[d];
+                xc += X[d] * c.right[d];
+                yc += X[d] * c.up[d];
+                zc += X[d] * c.fwd[d];
+            }
+            if (!(zc > 0.0)) return FR_EINVAL;
+            uv[b][0] = (xc / zc / tx + 1.0) * 0.5 * c.width - 0.5;
+            uv[b][1] = (1.0 - yc / zc / ty) * 0.5 * c.height - 0.5;
+        }
+        for (int b = 0; b < 8; ++b)
+            for (int d = 0; d < 3; ++d) {
+                if ((b >> d) & 1) continue;   // edge from corner b to b + (1 << d), along axis d
+                const int e = b | (1 << d);
+                const double du = std::fabs(uv[e][0] - uv[b][0]), dv = std::fabs(uv[e][1] - uv[b][1]);
+                nmax[d] = std::max(nmax[d], std::max(du, dv));
+            }
+    }
+    double hh = INFINITY;
+    for (int d = 0; d < 3; ++d) {
+        if (!(nmax[d] > 0.0)) return FR_EINVAL;
+        hh = std::min(hh, alpha * len[d] / nmax[d]);
+    }
+    for (int d = 0; d < 3; ++d) {
+        const double cells = std::ceil(len[d] / hh - 1e-9);
+        if (cells + 1 > (double)INT_MAX) return FR_EINVAL;
+        dims[d] = (int32_t)cells + 1;
+        if (n) n[d] = (float)nmax[d];
+    }
+    *h = (float)hh;
+    return FR_OK;
+}
+
 extern "C" fr_status fr_temperature_from_green(fr_ctx* c, const fr_volume* rgb, const fr_params* p,
                                                fr_volume* temp)
 {

@@ -113,6 +113,8 @@ SIGNATURES = {
     "fr_server_memory": (_S, [_P, _P, _P]),
     "fr_volume_rmse": (_S, [_P, _P, _P, _P, ctypes.c_uint32, _P, _P]),
     "fr_temperature_from_green": (_S, [_P, _P, _P, _P]),
+    "fr_camera_from_projection": (_S, [_P, _I, _I, _P]),
+    "fr_volume_dims": (_S, [_P, _I, _P, _P, _F, _P, _P, _P]),
     "fr_trace_phases": (_S, [_P, _I]),
     "fr_phase_times": (_S, [_P, _P, _I, _P]),
     "fr_render_residual_noalloc": (_S, [_I, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, ctypes.c_char_p,
@@ -210,6 +212,32 @@ def volume(t, origin, h, kind=FR_KIND_RGB) -> fr_volume:
     v.h = float(h)
     v.data = t.data_ptr()
     return v
+
+
+def camera_from_projection(P, width, height):
+    """fr_camera (as a dict like synth's cameras) from a 3x4 projection matrix."""
+    arr = np.ascontiguousarray(P, dtype=np.float64).reshape(12)
+    cam = fr_camera()
+    st = load().fr_camera_from_projection(arr.ctypes.data, int(width), int(height), ctypes.byref(cam))
+    if st != FR_OK:
+        raise FrError(st, "projection not representable by the pinhole model (square pixels, no skew, "
+                          "centred principal point)")
+    return dict(pos=list(cam.pos), right=list(cam.right), up=list(cam.up), fwd=list(cam.fwd),
+                tan_half_fov=cam.tan_half_fov, width=cam.width, height=cam.height)
+
+
+def volume_dims(cams, box_min, box_max, alpha=1.5):
+    """Sec. 4.2 volume dimensions: (dims (nx, ny, nz), voxel edge h, pixels per edge n)."""
+    fc = cameras(cams)
+    lo = (ctypes.c_float * 3)(*box_min)
+    hi = (ctypes.c_float * 3)(*box_max)
+    dims = (ctypes.c_int32 * 3)()
+    h = ctypes.c_float()
+    n = (ctypes.c_float * 3)()
+    st = load().fr_volume_dims(fc, len(cams), lo, hi, float(alpha), dims, ctypes.byref(h), n)
+    if st != FR_OK:
+        raise FrError(st, "no volume dimensions (box behind a camera or empty)")
+    return tuple(dims), h.value, tuple(n)
 
 
 class Context:
