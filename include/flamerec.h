@@ -111,6 +111,12 @@ typedef struct fr_params {
                             inside the hull (exact up to the order of its atomic sums) */
     const uint32_t *hull_tags; /* use_hull: device, one tag per node from fr_visual_hull for the same
                             cameras and targets; NULL: fr_reconstruct computes them each call */
+    float hg_g;          /* in-scattering phase: Henyey-Greenstein asymmetry in (-1, 1) (Eq. 9);
+                            0: isotropic, as in the paper.  g != 0: each view renders its own
+                            source, the six directional radiances weighted towards the direction
+                            from the volume's centre to its camera */
+    int32_t sequential_views; /* fr_reconstruct: 1 = update the volume after each view in turn
+                            (Kaczmarz order; the source is recomputed before each view) */
 } fr_params;
 
 typedef struct fr_ctx fr_ctx;

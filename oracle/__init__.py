@@ -55,7 +55,8 @@ class Params(ctypes.Structure):
                 ("alpha_d", ctypes.c_double), ("tau", ctypes.c_double),
                 ("g_std", ctypes.c_double), ("flame_thresh", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("clamp_nonneg", ctypes.c_int32),
-                ("pad_", ctypes.c_int32)]
+                ("pad_", ctypes.c_int32), ("hg_g", ctypes.c_double), ("sequential", ctypes.c_int32),
+                ("pad2_", ctypes.c_int32)]
 
 
 class Lut(ctypes.Structure):
@@ -92,6 +93,9 @@ def _load():
             "orc_visual_hull": (None, [_P, _P, ctypes.c_int, _P, _P]),
             "orc_volume_rmse": (_I64, [_I64, _P, _P, _P, ctypes.c_uint32, _P]),
             "orc_volume_dims": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_double, _P, _P, _P]),
+            "orc_scatter_L6": (None, [_P, _P, _P]),
+            "orc_hg_weights": (None, [ctypes.c_double, _P, _P]),
+            "orc_scatter_source_hg": (None, [_I64, _P, _P, _P, _P, _P]),
             "orc_planck": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
             "orc_temp_rgb": (None, [ctypes.c_double, _P]),
             "orc_lut_build": (None, [ctypes.c_double, ctypes.c_double, ctypes.c_int, _P]),
@@ -136,10 +140,11 @@ def make_cams(cams) -> ctypes.Array:
 
 
 def make_params(step=1.0, alpha_l=0.001, alpha_d=1.0, tau=0.0, g_std=0.0,
-                flame_thresh=30.0 / 255.0, seed=0, clamp_nonneg=1) -> Params:
+                flame_thresh=30.0 / 255.0, seed=0, clamp_nonneg=1, hg_g=0.0, sequential=0) -> Params:
     p = Params()
     p.step, p.alpha_l, p.alpha_d, p.tau = float(step), float(alpha_l), float(alpha_d), float(tau)
     p.g_std, p.flame_thresh, p.seed, p.clamp_nonneg = float(g_std), float(flame_thresh), int(seed), int(clamp_nonneg)
+    p.hg_g, p.sequential = float(hg_g), int(sequential)
     return p
 
 
@@ -367,6 +372,29 @@ def reconstruct(scene: Scene, vol, params: Params, targets, mask, bbox, iters,
                         _ptr(hl) if hl is not None else None,
                         float(stop_delta) if stop_delta is not None else -1.0, ctypes.byref(done))
     return vol, rmse[:done.value], (int(samples[0]), int(samples[1]))
+
+
+def scatter_L6(scene: Scene, vol):
+    """The six directional radiances (nz,ny,nx,6,3), d = 2 axis + (0: +axis, 1: -axis)."""
+    vol = _check_vol(vol, scene.shape, 4)
+    nx, ny, nz = scene.shape
+    out = np.zeros((nz, ny, nx, 6, 3))
+    _load().orc_scatter_L6(ctypes.byref(scene.grid), _ptr(vol), _ptr(out))
+    return out
+
+
+def hg_weights(g, omega):
+    w = np.zeros(6)
+    _load().orc_hg_weights(float(g), _ptr(np.ascontiguousarray(omega, dtype=np.float64)), _ptr(w))
+    return w
+
+
+def scatter_source_hg(vol, albedo, L6, w):
+    vol = _f64(vol)
+    out = np.zeros_like(vol)
+    _load().orc_scatter_source_hg(vol.size // 4, _ptr(vol), _ptr(_f64(albedo)), _ptr(_f64(L6)),
+                                  _ptr(np.ascontiguousarray(w, dtype=np.float64)), _ptr(out))
+    return out
 
 
 def volume_dims(cams, box_min, box_max, alpha=1.5):

@@ -62,6 +62,9 @@ typedef struct {
     uint64_t seed;       /* key of the G(s) stream */
     int32_t clamp_nonneg;/* clamp updated values at 0 */
     int32_t pad_;
+    double hg_g;         /* Henyey-Greenstein asymmetry of the in-scattering (Eq. 9); 0: isotropic */
+    int32_t sequential;  /* 1: views update the volume one after another (Kaczmarz order) */
+    int32_t pad2_;
 } orc_params;
 
 /* Temperature-to-RGB table (Sec. 3.3.3): m entries over [t_min, t_max]. */
@@ -547,9 +550,22 @@ void orc_residual(int ncam, int height, int width, const double *rendered,
  * in constant-tau mode, exp(-sum of preceding optical depths) in field mode)
  * and D the Euclidean key-point distance in voxel edge lengths.  All views
  * accumulate into one dV (N^3 x 3).  Returns the number of samples visited. */
+static int64_t update_paper_views(const orc_grid *g, const double *vol, const orc_cam *cams,
+                                  int ncam, const orc_params *P, const double *residual,
+                                  const uint8_t *mask, int iteration, int view_base, double *dV);
+
 int64_t orc_update_paper(const orc_grid *g, const double *vol, const orc_cam *cams,
                          int ncam, const orc_params *P, const double *residual,
                          const uint8_t *mask, int iteration, double *dV)
+{
+    return update_paper_views(g, vol, cams, ncam, P, residual, mask, iteration, 0, dV);
+}
+
+/* The views of cams are views view_base, view_base + 1, ... of the problem:
+ * their index keys the G(s) stream. */
+static int64_t update_paper_views(const orc_grid *g, const double *vol, const orc_cam *cams,
+                                  int ncam, const orc_params *P, const double *residual,
+                                  const uint8_t *mask, int iteration, int view_base, double *dV)
 {
     orc_field F = {ORC_RGB, vol, NULL};
     int64_t total = 0, off = 0;
@@ -571,7 +587,7 @@ int64_t orc_update_paper(const orc_grid *g, const double *vol, const orc_cam *ca
                     orc_sample s;
                     segment(o, d, t0, t1, P->step, k, &len, p);
                     sample_field(g, &F, p, &s);
-                    double G = orc_g_draw(P->seed, P->g_std, iteration, v,
+                    double G = orc_g_draw(P->seed, P->g_std, iteration, view_base + v,
                                           (int64_t)py * c->width + px, k);
                     for (int b = 0; b < 8; ++b) {
                         int64_t j = s.idx[b];
@@ -747,6 +763,90 @@ void orc_scatter_source(int64_t nodes, const double *vol, const double *albedo,
     }
 }
 
+/* The six directional radiances of orc_scatter_J kept apart: L6 (N^3 x 6 x 3)
+ * holds, for propagation direction d = 2 axis + dir (dir 0: towards +axis,
+ * 1: towards -axis), the radiance arriving at each node along the grid line
+ * (same recurrence, L = 0 at the line's first node). */
+void orc_scatter_L6(const orc_grid *g, const double *vol, double *L6)
+{
+    const int n[3] = {g->nx, g->ny, g->nz};
+    int64_t nodes = (int64_t)n[0] * n[1] * n[2];
+    memset(L6, 0, sizeof(double) * 18 * (size_t)nodes);
+    for (int axis = 0; axis < 3; ++axis) {
+        int a1 = (axis + 1) % 3, a2 = (axis + 2) % 3;
+        for (int u = 0; u < n[a1]; ++u)
+            for (int w = 0; w < n[a2]; ++w)
+                for (int dir = 0; dir < 2; ++dir) {
+                    double L[3] = {0.0, 0.0, 0.0};
+                    int64_t prev = -1;
+                    for (int s = 0; s < n[axis]; ++s) {
+                        int pos = dir == 0 ? s : n[axis] - 1 - s;
+                        int ijk[3];
+                        ijk[axis] = pos; ijk[a1] = u; ijk[a2] = w;
+                        int64_t j = node_index(g, ijk[0], ijk[1], ijk[2]);
+                        if (prev >= 0) {
+                            const double *r0 = vol + 4 * prev, *r1 = vol + 4 * j;
+                            double sig = 0.5 * (r0[3] + r1[3]);
+                            double beta, dbeta;
+                            segment_weight(sig, 1.0, &beta, &dbeta);
+                            double att = exp(-sig);
+                            for (int ch = 0; ch < 3; ++ch)
+                                L[ch] = L[ch] * att + 0.5 * (r0[ch] + r1[ch]) * beta;
+                        }
+                        for (int ch = 0; ch < 3; ++ch) L6[18 * j + 3 * (2 * axis + dir) + ch] = L[ch];
+                        prev = j;
+                    }
+                }
+    }
+}
+
+/* Weights of the six directional radiances in the light scattered towards
+ * unit direction omega (Eq. 9): light propagating along direction d arrives
+ * from omega_i = -e_d, so w_d is proportional to p(omega, -e_d); the six
+ * weights are normalised to sum to 1 (each direction stands for a sixth of the
+ * sphere).  g = 0 gives 1/6 each. */
+void orc_hg_weights(double g, const double omega[3], double w[6])
+{
+    double sum = 0.0;
+    for (int d = 0; d < 6; ++d) {
+        const int axis = d / 2;
+        const double sign = (d & 1) ? -1.0 : 1.0;   /* e_d along +axis for dir 0 */
+        const double cos_wi = -sign * omega[axis];  /* omega . (-e_d) */
+        w[d] = orc_hg_phase(g, cos_wi);
+        sum += w[d];
+    }
+    for (int d = 0; d < 6; ++d) w[d] /= sum;
+}
+
+/* Source records towards one view: S = q + albedo sigma sum_d w_d L_d. */
+void orc_scatter_source_hg(int64_t nodes, const double *vol, const double *albedo, const double *L6,
+                           const double w[6], double *out)
+{
+    for (int64_t j = 0; j < nodes; ++j) {
+        double s = vol[4 * j + 3];
+        for (int ch = 0; ch < 3; ++ch) {
+            double in = 0.0;
+            for (int d = 0; d < 6; ++d) in += w[d] * L6[18 * j + 3 * d + ch];
+            out[4 * j + ch] = vol[4 * j + ch] + albedo[j] * s * in;
+        }
+        out[4 * j + 3] = s;
+    }
+}
+
+/* Unit direction from the volume's centre to camera c, in world axes (the
+ * grid's axes): the direction towards which view c sees scattered light. */
+static void view_direction(const orc_grid *g, const orc_cam *c, double omega[3])
+{
+    double d[3], len = 0.0;
+    const int n[3] = {g->nx, g->ny, g->nz};
+    for (int a = 0; a < 3; ++a) {
+        d[a] = c->pos[a] - (g->origin[a] + 0.5 * (double)(n[a] - 1) * g->h);
+        len += d[a] * d[a];
+    }
+    len = sqrt(len);
+    for (int a = 0; a < 3; ++a) omega[a] = d[a] / len;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Visual hull (Sec. 4.3.1, Algorithm 1)                                     */
 /* ------------------------------------------------------------------------ */
@@ -900,15 +1000,45 @@ int64_t orc_volume_rmse(int64_t nodes, const double *a, const double *b, const u
 /* The iteration (Sec. 3, Algorithm 2): render, compare, adjust.             */
 /* ------------------------------------------------------------------------ */
 
+/* Squared residual sums of one view inside its flame box: residual =
+ * target - rendered everywhere, acc[0..2] += the squares in the box, returns
+ * the number of box pixels (Sec. 5.1). */
+static int64_t view_residual(int height, int width, const double *rendered, const double *targets,
+                             const int32_t *bb, double *residual, double acc[3])
+{
+    int64_t count = 0;
+    for (int py = 0; py < height; ++py)
+        for (int px = 0; px < width; ++px) {
+            int64_t pix = (int64_t)py * width + px;
+            int in_box = px >= bb[0] && px <= bb[2] && py >= bb[1] && py <= bb[3];
+            for (int ch = 0; ch < 3; ++ch) {
+                double r = targets[3 * pix + ch] - rendered[3 * pix + ch];
+                residual[3 * pix + ch] = r;
+                if (in_box) acc[ch] += r * r;
+            }
+            count += in_box;
+        }
+    return count;
+}
+
 /* Runs `iters` iterations of the paper rule on vol (N^3 x 4, colour updated
  * in place); with stop_delta >= 0, stops earlier after the first iteration
  * k >= 1 whose image error differs from iteration k-1's by less than
  * stop_delta in every channel (Sec. 3 stop criterion), and *iters_done
- * (nullable) gets the iterations run.  albedo (nullable) turns on the in-scattering source, recomputed
- * from the current volume at the start of each iteration.  targets must have
- * been through orc_prepare_targets (mask, bbox).  rmse (iters x 3) gets the
- * error of the images rendered at the start of each iteration.  samples[0..1]
- * accumulate forward and adjustment sample counts. */
+ * (nullable) gets the iterations run.  albedo (nullable) turns on the
+ * in-scattering source, recomputed from the current volume at the start of
+ * each iteration.  targets must have been through orc_prepare_targets (mask,
+ * bbox).  rmse (iters x 3) gets the error of the images rendered in each
+ * iteration.  samples[0..1] accumulate forward and adjustment sample counts.
+ *
+ * Variants the paper mentions without using (Sec. 3.3.1, Eq. 9; Sec. 3.3.2):
+ * P->hg_g != 0 scatters with the Henyey-Greenstein phase function: each view
+ * renders its own source, with the six directional radiances weighted
+ * towards the direction from the volume's centre to its camera;
+ * P->sequential = 1 updates the volume after each view in turn (Kaczmarz
+ * order), the source recomputed from the current volume before each view.
+ * Either way the views are rendered and adjusted one at a time and the
+ * iteration's error pools every view's box. */
 void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
                      const orc_cam *cams, int ncam, const orc_params *P,
                      const double *targets, const uint8_t *mask, const int32_t *bbox,
@@ -918,10 +1048,11 @@ void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
     int64_t nodes = (int64_t)g->nx * g->ny * g->nz;
     int64_t npix = 0;
     for (int v = 0; v < ncam; ++v) npix += (int64_t)cams[v].width * cams[v].height;
+    const int per_view = P->hg_g != 0.0 || P->sequential;
     double *img = malloc(sizeof(double) * 3 * (size_t)npix);
     double *res = malloc(sizeof(double) * 3 * (size_t)npix);
     double *dV = malloc(sizeof(double) * 3 * (size_t)nodes);
-    double *J = albedo ? malloc(sizeof(double) * 3 * (size_t)nodes) : NULL;
+    double *J = albedo ? malloc(sizeof(double) * 18 * (size_t)nodes) : NULL;   /* J or L6 */
     double *src = albedo ? malloc(sizeof(double) * 4 * (size_t)nodes) : NULL;
     /* key points outside the visual hull are not reconstructed: they hold no
      * flame, so their whole record (emission and extinction) is 0 and stays 0
@@ -932,20 +1063,63 @@ void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
         for (int64_t j = 0; j < nodes; ++j)
             if (hull[j] != full) vol[4 * j] = vol[4 * j + 1] = vol[4 * j + 2] = vol[4 * j + 3] = 0.0;
     for (int it = 0; it < iters; ++it) {
-        const double *rvol = vol;
-        if (albedo) {
-            orc_scatter_J(g, vol, J);
-            orc_scatter_source(nodes, vol, albedo, J, src);
-            rvol = src;
+        if (!per_view) {
+            const double *rvol = vol;
+            if (albedo) {
+                orc_scatter_J(g, vol, J);
+                orc_scatter_source(nodes, vol, albedo, J, src);
+                rvol = src;
+            }
+            samples[0] += orc_render(g, rvol, cams, ncam, P, img, NULL);
+            orc_residual(ncam, cams[0].height, cams[0].width, img, targets, bbox, res, rmse + 3 * it);
+            memset(dV, 0, sizeof(double) * 3 * (size_t)nodes);
+            samples[1] += orc_update_paper(g, rvol, cams, ncam, P, res, mask, first_iteration + it, dV);
+            orc_apply_update(nodes, vol, dV, P->clamp_nonneg);
+            if (hull)
+                for (int64_t j = 0; j < nodes; ++j)
+                    if (hull[j] != full) vol[4 * j] = vol[4 * j + 1] = vol[4 * j + 2] = vol[4 * j + 3] = 0.0;
+        } else {
+            double acc[3] = {0.0, 0.0, 0.0};
+            int64_t count = 0, off = 0;
+            memset(dV, 0, sizeof(double) * 3 * (size_t)nodes);
+            for (int v = 0; v < ncam; ++v) {
+                const orc_cam *c = cams + v;
+                const double *rvol = vol;
+                if (albedo) {
+                    if (P->hg_g != 0.0) {
+                        if (v == 0 || P->sequential) orc_scatter_L6(g, vol, J);
+                        double omega[3], w[6];
+                        view_direction(g, c, omega);
+                        orc_hg_weights(P->hg_g, omega, w);
+                        orc_scatter_source_hg(nodes, vol, albedo, J, w, src);
+                    } else if (v == 0 || P->sequential) {
+                        orc_scatter_J(g, vol, J);
+                        orc_scatter_source(nodes, vol, albedo, J, src);
+                    }
+                    rvol = src;
+                }
+                samples[0] += orc_render(g, rvol, c, 1, P, img + 3 * off, NULL);
+                count += view_residual(c->height, c->width, img + 3 * off, targets + 3 * off, bbox + 4 * v,
+                                       res + 3 * off, acc);
+                samples[1] += update_paper_views(g, rvol, c, 1, P, res + 3 * off, mask + off,
+                                                 first_iteration + it, v, dV);
+                if (P->sequential) {
+                    orc_apply_update(nodes, vol, dV, P->clamp_nonneg);
+                    memset(dV, 0, sizeof(double) * 3 * (size_t)nodes);
+                    if (hull)
+                        for (int64_t j = 0; j < nodes; ++j)
+                            if (hull[j] != full) vol[4 * j] = vol[4 * j + 1] = vol[4 * j + 2] = vol[4 * j + 3] = 0.0;
+                }
+                off += (int64_t)c->width * c->height;
+            }
+            if (!P->sequential) {
+                orc_apply_update(nodes, vol, dV, P->clamp_nonneg);
+                if (hull)
+                    for (int64_t j = 0; j < nodes; ++j)
+                        if (hull[j] != full) vol[4 * j] = vol[4 * j + 1] = vol[4 * j + 2] = vol[4 * j + 3] = 0.0;
+            }
+            for (int ch = 0; ch < 3; ++ch) rmse[3 * it + ch] = count ? 255.0 * sqrt(acc[ch] / (double)count) : 0.0;
         }
-        samples[0] += orc_render(g, rvol, cams, ncam, P, img, NULL);
-        orc_residual(ncam, cams[0].height, cams[0].width, img, targets, bbox, res, rmse + 3 * it);
-        memset(dV, 0, sizeof(double) * 3 * (size_t)nodes);
-        samples[1] += orc_update_paper(g, rvol, cams, ncam, P, res, mask, first_iteration + it, dV);
-        orc_apply_update(nodes, vol, dV, P->clamp_nonneg);
-        if (hull)
-            for (int64_t j = 0; j < nodes; ++j)
-                if (hull[j] != full) vol[4 * j] = vol[4 * j + 1] = vol[4 * j + 2] = vol[4 * j + 3] = 0.0;
         if (iters_done) *iters_done = it + 1;
         if (stop_delta >= 0.0 && it >= 1) {
             int small = 1;

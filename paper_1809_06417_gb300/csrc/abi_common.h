@@ -39,6 +39,7 @@ struct fr_ctx {
     Buf hull_bricks;                 // bricks holding a key point inside the visual hull
     Buf loop;                        // device iteration counter of fr_reconstruct_until
     Buf verr;                        // volume-error partials and result
+    Buf L6;                          // directional radiances for anisotropic in-scattering
     Buf hull, sat;                   // visual hull tags, flame-mask tables
     unsigned long long* host_counter = nullptr;  // pinned host scratch of kHostScratchBytes
     void* staging = nullptr;         // pinned host staging of batch tables

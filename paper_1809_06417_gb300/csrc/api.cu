@@ -64,7 +64,7 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     cudaStreamSynchronize(c->stream);
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
                    &c->rmse, &c->J, &c->src, &c->flame_cnt, &c->flame_list, &c->batch, &c->pairs,
-                   &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr})
+                   &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr, &c->L6})
         if (b->p) cudaFree(b->p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
     if (c->staging) cudaFreeHost(c->staging);
@@ -573,6 +573,12 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     if (albedo && vol->kind != FR_KIND_RGB) return fail(c, FR_EINVAL, "albedo needs an RGB volume");
     if (p->rule == FR_RULE_GRADIENT && !std::isfinite(p->grad_step))
         return fail(c, FR_EINVAL, "grad_step must be finite");
+    if (!(p->hg_g > -1.0f && p->hg_g < 1.0f)) return fail(c, FR_EINVAL, "hg_g must lie in (-1, 1)");
+    if (p->sequential_views != 0 && p->sequential_views != 1)
+        return fail(c, FR_EINVAL, "sequential_views must be 0 or 1");
+    // views rendered and adjusted one at a time: anisotropic scattering (each
+    // view its own source) or the sequential order
+    const bool per_view = (p->hg_g != 0.0f && albedo) || p->sequential_views;
     const long long nodes = node_count(vol);
     const size_t ib = image_bytes(cams, ncam);
     if (!targets) return fail(c, FR_EINVAL, "targets is NULL");
@@ -597,7 +603,10 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     }
     const long long npix = (long long)ncam * cams[0].width * cams[0].height;
     if (npix >= (1LL << 32)) return fail(c, FR_EINVAL, "at most 2^32 pixels per reconstruction");
-    FR_TRY(ensure(c, c->flame_cnt, (size_t)iters * sizeof(unsigned), "flame counts"));
+    const int count_slots = per_view ? ncam : 1;   // flame-ray counts per iteration
+    FR_TRY(ensure(c, c->flame_cnt, (size_t)iters * count_slots * sizeof(unsigned), "flame counts"));
+    const bool hg = per_view && p->hg_g != 0.0f && albedo;
+    if (hg) FR_TRY(ensure(c, c->L6, (size_t)nodes * 6 * 16, "directional radiances"));
     if (until) FR_TRY(ensure(c, c->loop, 16, "loop counter"));
     FR_TRY(ensure(c, c->flame_list, (size_t)npix * sizeof(unsigned), "flame list"));
     FR_TRY(ensure(c, c->pairs, (size_t)nodes * 2 * rec_bytes(vol), "pairs"));
@@ -654,7 +663,7 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     unsigned* flame_list = static_cast<unsigned*>(c->flame_list.p);
     FR_TRY(trace_mark(c, -1));
     if (p->rule == FR_RULE_PAPER) {
-        FR_CUDA(c, cudaMemsetAsync(flame_cnt, 0, (size_t)iters * sizeof(unsigned), s));
+        FR_CUDA(c, cudaMemsetAsync(flame_cnt, 0, (size_t)iters * count_slots * sizeof(unsigned), s));
         f.p.flist = flame_list;
     }
     const unsigned* hull = nullptr;
@@ -676,7 +685,104 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     FR_TRY(trace_mark(c, FR_PHASE_SETUP));
     // One iteration on stream st.  it >= 0: per-iteration slots it; it < 0:
     // slot 0 and the iteration index read on the device (graph body).
+    // Per-view problems: view v of the call as a one-view problem over the
+    // same volume, its targets, box, residual and image slices, its own flame
+    // count, and its index v in the G(s) stream.
+    const size_t view_px = (size_t)cams[0].width * cams[0].height;
+    const int nt1 = tiles_of(cams[0].width, cams[0].height, 1);
+    static thread_local SingleArgs fv, uv;
+    auto view_problem = [&](int v, int slot) {
+        fv = f;
+        fv.p.ncam = 1;
+        fv.cams[0] = f.cams[v];
+        fv.p.targets = tg + 3 * view_px * v;
+        fv.p.bbox = bbox + 4 * v;
+        fv.p.residual = f.p.residual + 3 * view_px * v;
+        if (f.p.rendered) fv.p.rendered = f.p.rendered + 3 * view_px * v;
+        fv.p.flist_count = f.p.flist ? flame_cnt + (size_t)slot * count_slots + v : nullptr;
+        uv = u;
+        uv.p.ncam = 1;
+        uv.cams[0] = u.cams[v];
+        uv.p.img_in = u.p.img_in + 3 * view_px * v;
+        if (p->rule == FR_RULE_GRADIENT) uv.p.L_total = static_cast<const float*>(c->rendered.p) + 3 * view_px * v;
+        uv.p.view_base = v;
+    };
+    // Henyey-Greenstein weights towards each camera (Eq. 9): light travelling
+    // along axis direction d comes from -e_d, weight ~ p(omega, -e_d),
+    // normalised to sum to 1; omega from the volume's centre to the camera.
+    auto hg_weights = [&](int v) {
+        HgWeights w;
+        const double g = p->hg_g;
+        double om[3], len = 0.0;
+        const int n[3] = {vol->nx, vol->ny, vol->nz};
+        for (int a = 0; a < 3; ++a) {
+            om[a] = (double)cams[v].pos[a] - ((double)vol->origin[a] + 0.5 * (n[a] - 1) * (double)vol->h);
+            len += om[a] * om[a];
+        }
+        len = std::sqrt(len);
+        double pw[6], sum = 0.0;
+        for (int d = 0; d < 6; ++d) {
+            const double e = (d & 1) ? -1.0 : 1.0;
+            const double cos_wi = -e * om[d / 2] / len;
+            const double den = 1.0 + g * g + 2.0 * g * cos_wi;
+            pw[d] = (1.0 - g * g) / (den * std::sqrt(den));   // the 1/(4 pi) cancels
+            sum += pw[d];
+        }
+        for (int d = 0; d < 6; ++d) w.w[d] = (float)(pw[d] / sum);
+        return w;
+    };
+    auto per_view_iteration = [&](cudaStream_t st, int it) -> fr_status {
+        const int slot = it < 0 ? 0 : it;
+        const bool seq = p->sequential_views != 0;
+        for (int v = 0; v < ncam; ++v) {
+            if (albedo) {
+                if (hg) {
+                    if (v == 0 || seq)
+                        FR_CUDA(c, launch_scatter_L6(vol->data, vol->dtype, static_cast<float*>(c->L6.p), vol->nx,
+                                                     vol->ny, vol->nz, st));
+                    FR_CUDA(c, launch_source_hg(vol->data, vol->dtype, albedo, static_cast<const float*>(c->L6.p),
+                                                hg_weights(v), c->src.p, nodes, st));
+                } else if (v == 0 || seq) {
+                    FR_CUDA(c, launch_scatter_source(vol->data, vol->dtype, albedo, static_cast<float*>(c->J.p),
+                                                     c->src.p, vol->dtype, vol->nx, vol->ny, vol->nz, st));
+                }
+                FR_TRY(trace_mark(c, FR_PHASE_SCATTER));
+            }
+            if (v == 0 || seq || hg) {
+                FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz,
+                                            occ, st));
+                FR_TRY(trace_mark(c, FR_PHASE_PACK));
+            }
+            view_problem(v, slot);
+            FR_CUDA(c, launch_fwd(fv, vol->dtype, vol->kind, nt1, st));
+            FR_TRY(trace_mark(c, FR_PHASE_FORWARD));
+            FR_CUDA(c, launch_finalize(fv.p.partials, nt1, sq + 4 * slot, st, v > 0));
+            FR_TRY(trace_mark(c, FR_PHASE_REDUCE));
+            if (p->rule == FR_RULE_PAPER) {
+                uv.p.iteration = first_iteration + slot;
+                FR_CUDA(c, launch_adjust_list(uv, vol->dtype, nt1, flame_list, fv.p.flist_count, st));
+            } else {
+                uv.p.img_scale = -1.0f;
+                FR_CUDA(c, launch_backward(uv, vol->dtype, vol->kind, nt1, st));
+            }
+            FR_TRY(trace_mark(c, FR_PHASE_ADJUST));
+            if (seq || v == ncam - 1) {
+                if (p->rule == FR_RULE_PAPER)
+                    FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg,
+                                            1, st));
+                else
+                    FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, -p->grad_step,
+                                            p->update_sigma, p->clamp_nonneg, 1, st));
+                if (hull)
+                    FR_CUDA(c, launch_hull_clear(vol->data, vol->dtype, vol->nx, vol->ny, vol->nz, hull, full,
+                                                 nullptr, st));
+                FR_TRY(trace_mark(c, FR_PHASE_APPLY));
+            }
+        }
+        return FR_OK;
+    };
     auto one_iteration = [&](cudaStream_t st, int it) -> fr_status {
+        if (per_view) return per_view_iteration(st, it);
         const int slot = it < 0 ? 0 : it;
         if (albedo) {
             FR_CUDA(c, launch_scatter_source(vol->data, vol->dtype, albedo, static_cast<float*>(c->J.p), c->src.p,
@@ -764,8 +870,8 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     fr_status st = one_iteration(c->capture, -1);
     if (st == FR_OK) {
         cudaError_t ek = launch_converge(sq, static_cast<float*>(c->rmse.p), loop_iter,
-                                         p->rule == FR_RULE_PAPER ? flame_cnt : nullptr, iters, stop_delta, handle,
-                                         c->capture);
+                                         p->rule == FR_RULE_PAPER ? flame_cnt : nullptr, count_slots, iters,
+                                         stop_delta, handle, c->capture);
         if (ek != cudaSuccess) st = cuda_fail(c, ek, "converge kernel");
     }
     c->trace_on = tracing;

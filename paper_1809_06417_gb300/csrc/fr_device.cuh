@@ -72,6 +72,9 @@ struct ProbDev {
     // non-zero); when set, the forward march skips empty bricks
     const unsigned char* occ;
     const unsigned* occ_box;     // box of the non-empty bricks (brick-table layout)
+    // index of this problem's first view in its G(s) stream (views rendered
+    // one problem at a time keep their own index)
+    int view_base;
     // when set, the adjustment's iteration index is iteration + *iter_dev
     // (loops whose iterations are counted on the device)
     const int* iter_dev;

@@ -37,7 +37,7 @@ cudaError_t launch_backward(const SingleArgs& a, int dt, int kind, int ntiles, c
 cudaError_t launch_backward_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
                                   int dt, int kind, bool tau, cudaStream_t s);
 cudaError_t launch_count(const SingleArgs& a, int ntiles, cudaStream_t s);
-cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cudaStream_t s);
+cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cudaStream_t s, int accumulate = 0);
 // flame-ray list of a problem with prepared targets: buf needs
 // flame_list_buf_entries(ntiles) entries, the total lands at
 // buf[flame_list_total_at(ntiles)]; list needs one entry per pixel at most
@@ -64,9 +64,19 @@ cudaError_t launch_green_to_temp(const void* rgb, int dt_rgb, void* temp, int dt
 int volume_err_blocks(long long nodes);
 cudaError_t launch_volume_err(const void* a, int dta, const void* b, int dtb, long long nodes, const unsigned* tags,
                               unsigned full, void* partials, float* out, cudaStream_t s);
-// end of an iteration of a loop counted on the device (conditional graph body)
-cudaError_t launch_converge(const float* sq4, float* hist3, int* iter, unsigned* flame_count, int max_iters,
-                            float stop_delta, cudaGraphConditionalHandle handle, cudaStream_t s);
+// end of an iteration of a loop counted on the device (conditional graph body);
+// clears flame_count[0 .. n_counts)
+cudaError_t launch_converge(const float* sq4, float* hist3, int* iter, unsigned* flame_count, int n_counts,
+                            int max_iters, float stop_delta, cudaGraphConditionalHandle handle, cudaStream_t s);
+// In-scattering with a Henyey-Greenstein phase function: the six directional
+// radiances per node (L6, nodes x 6 float4, d = 2 axis + (0: +axis, 1: -axis)),
+// and the source towards one view, S = q + albedo sigma sum_d w_d L_d.
+cudaError_t launch_scatter_L6(const void* emission, int dt, float* L6, int nx, int ny, int nz, cudaStream_t s);
+struct HgWeights {
+    float w[6];
+};
+cudaError_t launch_source_hg(const void* emission, int dt, const float* albedo, const float* L6, HgWeights w,
+                             void* out, long long nodes, cudaStream_t s);
 cudaError_t launch_rmse(const float* sq4, int n, float* rmse3, cudaStream_t s);
 cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t s);
 // visual hull: sat needs ncam (H+1)(W+1) uint32, tags one uint32 per node

@@ -386,7 +386,7 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
         const CellIJK c = cell_ijk(x, y, z, P.nx, P.ny, P.nz);
         win_move(W, c.i, c.j, c.k, P.nx, P.ny, nxy32, leave, enter);
         const float gx = mirror_frac(c.i, c.fx), gy = mirror_frac(c.j, c.fy), gz = mirror_frac(c.k, c.fz);
-        const float G = P.g_std > 0.0f ? g_draw(P.seed, P.g_std, iteration, view, pixel, k) : 1.0f;
+        const float G = P.g_std > 0.0f ? g_draw(P.seed, P.g_std, iteration, view + P.view_base, pixel, k) : 1.0f;
         const float base = G * P.alpha_l * T;
         // squared distances (voxel units) from the sample to each slot's key point
         const float ex[2] = {gx * gx, (1.0f - gx) * (1.0f - gx)};
@@ -599,8 +599,9 @@ __global__ void __launch_bounds__(kTileThreads) count_single(const __grid_consta
 }
 
 // Deterministic sum of the per-CTA squared-error partials of one problem.
+// accumulate != 0: adds to out4 (several views of one pooled error measure).
 __global__ void __launch_bounds__(1024) finalize_partials(const float* __restrict__ partials, int ntiles,
-                                                          float* __restrict__ out4)
+                                                          float* __restrict__ out4, int accumulate)
 {
     __shared__ float red[4][32];
     float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
@@ -617,7 +618,7 @@ __global__ void __launch_bounds__(1024) finalize_partials(const float* __restric
     if (threadIdx.x < 4) {
         float t = 0.0f;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[threadIdx.x][i];
-        out4[threadIdx.x] = t;
+        out4[threadIdx.x] = accumulate ? out4[threadIdx.x] + t : t;
     }
 }
 
@@ -850,9 +851,9 @@ cudaError_t launch_count(const SingleArgs& a, int ntiles, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cudaStream_t s)
+cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cudaStream_t s, int accumulate)
 {
-    finalize_partials<<<1, 1024, 0, s>>>(partials, ntiles, out4);
+    finalize_partials<<<1, 1024, 0, s>>>(partials, ntiles, out4, accumulate);
     return cudaGetLastError();
 }
 

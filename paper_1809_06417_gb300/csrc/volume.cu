@@ -313,10 +313,12 @@ __device__ __forceinline__ Seg seg_between(float4 a, float4 b)
     return Seg{e, 0.5f * (a.x + b.x) * beta, 0.5f * (a.y + b.y) * beta, 0.5f * (a.z + b.z) * beta};
 }
 
+// L6 (nullable): store each direction's radiance there (nodes x 6 float4)
+// instead of accumulating J and writing the source.
 template <int DT, int AXIS, bool LAST>
 __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const void* em, const float* albedo,
                                                                             float* J, void* out, int nx, int ny,
-                                                                            int nz)
+                                                                            int nz, float4* L6)
 {
     __shared__ float4 fwd[kSweepChunks][kSweepLines];   // {E, C0, C1, C2} of each chunk, forward
     __shared__ float4 bwd[kSweepChunks][kSweepLines];   // and backward
@@ -393,6 +395,10 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const
                 lf0 = fmaf(lf0, g.e, g.c0); lf1 = fmaf(lf1, g.e, g.c1); lf2 = fmaf(lf2, g.e, g.c2);
             }
             prev = cur;
+            if (L6) {
+                L6[6 * node + 2 * AXIS] = make_float4(lf0, lf1, lf2, 0.0f);
+                continue;
+            }
             float4 j;
             if constexpr (AXIS == 0) {
                 j = make_float4(lf0 * sixth, lf1 * sixth, lf2 * sixth, 0.0f);
@@ -414,6 +420,10 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const
                 lb0 = fmaf(lb0, g.e, g.c0); lb1 = fmaf(lb1, g.e, g.c1); lb2 = fmaf(lb2, g.e, g.c2);
             }
             next = cur;
+            if (L6) {
+                L6[6 * node + 2 * AXIS + 1] = make_float4(lb0, lb1, lb2, 0.0f);
+                continue;
+            }
             float4 j = J4[node];
             j.x = fmaf(lb0, sixth, j.x); j.y = fmaf(lb1, sixth, j.y); j.z = fmaf(lb2, sixth, j.z);
             if constexpr (LAST) {
@@ -432,7 +442,7 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const
 // (forward maps, composed first-then-next) and an inclusive suffix (backward
 // maps).  It initialises J (the first sweep).
 template <int DT>
-__global__ void __launch_bounds__(256) sweep_x_kernel(const void* em, float* J, int nx, int ny, int nz)
+__global__ void __launch_bounds__(256) sweep_x_kernel(const void* em, float* J, int nx, int ny, int nz, float4* L6)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -497,7 +507,8 @@ __global__ void __launch_bounds__(256) sweep_x_kernel(const void* em, float* J, 
                 lf0 = fmaf(lf0, g.e, g.c0); lf1 = fmaf(lf1, g.e, g.c1); lf2 = fmaf(lf2, g.e, g.c2);
             }
             prev = cur;
-            J4[start + i] = make_float4(lf0 * sixth, lf1 * sixth, lf2 * sixth, 0.0f);
+            if (L6) L6[6 * (start + i)] = make_float4(lf0, lf1, lf2, 0.0f);
+            else J4[start + i] = make_float4(lf0 * sixth, lf1 * sixth, lf2 * sixth, 0.0f);
         }
     }
     {
@@ -509,6 +520,10 @@ __global__ void __launch_bounds__(256) sweep_x_kernel(const void* em, float* J, 
                 lb0 = fmaf(lb0, g.e, g.c0); lb1 = fmaf(lb1, g.e, g.c1); lb2 = fmaf(lb2, g.e, g.c2);
             }
             next = cur;
+            if (L6) {
+                L6[6 * (start + i) + 1] = make_float4(lb0, lb1, lb2, 0.0f);
+                continue;
+            }
             float4 j = J4[start + i];
             j.x = fmaf(lb0, sixth, j.x); j.y = fmaf(lb1, sixth, j.y); j.z = fmaf(lb2, sixth, j.z);
             J4[start + i] = j;
@@ -526,13 +541,64 @@ cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* 
     const unsigned gz = (unsigned)((lz + kSweepLines - 1) / kSweepLines);
     const dim3 B(kSweepLines, kSweepChunks);
 #define FR_SWEEPS(D)                                                                         \
-    sweep_x_kernel<D><<<gxw, 256, 0, s>>>(emission, J, nx, ny, nz);                         \
-    sweep_kernel<D, 1, false><<<gy, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz);        \
-    sweep_kernel<D, 2, true><<<gz, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz)
+    sweep_x_kernel<D><<<gxw, 256, 0, s>>>(emission, J, nx, ny, nz, nullptr);                \
+    sweep_kernel<D, 1, false><<<gy, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz, nullptr); \
+    sweep_kernel<D, 2, true><<<gz, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz, nullptr)
     if (dt_in == DT_F32) { FR_SWEEPS(DT_F32); }
     else if (dt_in == DT_BF16) { FR_SWEEPS(DT_BF16); }
     else { FR_SWEEPS(DT_F16); }
 #undef FR_SWEEPS
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_L6(const void* emission, int dt, float* L6, int nx, int ny, int nz, cudaStream_t s)
+{
+    const long long lx = (long long)ny * nz, ly = (long long)nx * nz, lz = (long long)nx * ny;
+    const unsigned gxw = (unsigned)((lx + 7) / 8);
+    const unsigned gy = (unsigned)((ly + kSweepLines - 1) / kSweepLines);
+    const unsigned gz = (unsigned)((lz + kSweepLines - 1) / kSweepLines);
+    const dim3 B(kSweepLines, kSweepChunks);
+    float4* L = reinterpret_cast<float4*>(L6);
+#define FR_SWEEPS6(D)                                                                            \
+    sweep_x_kernel<D><<<gxw, 256, 0, s>>>(emission, nullptr, nx, ny, nz, L);                    \
+    sweep_kernel<D, 1, false><<<gy, B, 0, s>>>(emission, nullptr, nullptr, nullptr, nx, ny, nz, L); \
+    sweep_kernel<D, 2, false><<<gz, B, 0, s>>>(emission, nullptr, nullptr, nullptr, nx, ny, nz, L)
+    if (dt == DT_F32) { FR_SWEEPS6(DT_F32); }
+    else if (dt == DT_BF16) { FR_SWEEPS6(DT_BF16); }
+    else { FR_SWEEPS6(DT_F16); }
+#undef FR_SWEEPS6
+    return cudaGetLastError();
+}
+
+// Source records towards one view: S = q + albedo sigma sum_d w_d L_d (Eq. 9
+// phase weights), sigma unchanged.
+template <int DT>
+__global__ void __launch_bounds__(256) source_hg_kernel(const void* em, const float* __restrict__ albedo,
+                                                        const float4* __restrict__ L6, HgWeights w, void* out,
+                                                        long long nodes)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 r = load_rgb<DT>(em, i);
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            const float4 l = __ldg(L6 + 6 * i + d);
+            s0 = fmaf(w.w[d], l.x, s0); s1 = fmaf(w.w[d], l.y, s1); s2 = fmaf(w.w[d], l.z, s2);
+        }
+        const float as = __ldg(albedo + i) * r.w;
+        store_rgb<DT>(out, i, make_float4(fmaf(as, s0, r.x), fmaf(as, s1, r.y), fmaf(as, s2, r.z), r.w));
+    }
+}
+
+cudaError_t launch_source_hg(const void* emission, int dt, const float* albedo, const float* L6, HgWeights w,
+                             void* out, long long nodes, cudaStream_t s)
+{
+    const int g = grid_for(nodes, 256);
+    const float4* L = reinterpret_cast<const float4*>(L6);
+    if (dt == DT_F32) source_hg_kernel<DT_F32><<<g, 256, 0, s>>>(emission, albedo, L, w, out, nodes);
+    else if (dt == DT_BF16) source_hg_kernel<DT_BF16><<<g, 256, 0, s>>>(emission, albedo, L, w, out, nodes);
+    else source_hg_kernel<DT_F16><<<g, 256, 0, s>>>(emission, albedo, L, w, out, nodes);
     return cudaGetLastError();
 }
 
@@ -947,7 +1013,7 @@ cudaError_t launch_volume_err(const void* a, int dta, const void* b, int dtb, lo
 // allowed iteration) ending the conditional loop, the counter advanced and the
 // flame-ray count cleared for the next forward march.
 __global__ void converge_kernel(const float* __restrict__ sq4, float* hist3, int* iter, unsigned* flame_count,
-                                int max_iters, float stop_delta, cudaGraphConditionalHandle handle)
+                                int n_counts, int max_iters, float stop_delta, cudaGraphConditionalHandle handle)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int it = *iter;
@@ -969,14 +1035,15 @@ __global__ void converge_kernel(const float* __restrict__ sq4, float* hist3, int
 #pragma unroll
     for (int c = 0; c < 3; ++c) hist3[3 * it + c] = r[c];
     *iter = it + 1;
-    if (flame_count) *flame_count = 0u;
+    if (flame_count)
+        for (int i = 0; i < n_counts; ++i) flame_count[i] = 0u;
     if (stop) cudaGraphSetConditional(handle, 0u);
 }
 
-cudaError_t launch_converge(const float* sq4, float* hist3, int* iter, unsigned* flame_count, int max_iters,
-                            float stop_delta, cudaGraphConditionalHandle handle, cudaStream_t s)
+cudaError_t launch_converge(const float* sq4, float* hist3, int* iter, unsigned* flame_count, int n_counts,
+                            int max_iters, float stop_delta, cudaGraphConditionalHandle handle, cudaStream_t s)
 {
-    converge_kernel<<<1, 32, 0, s>>>(sq4, hist3, iter, flame_count, max_iters, stop_delta, handle);
+    converge_kernel<<<1, 32, 0, s>>>(sq4, hist3, iter, flame_count, n_counts, max_iters, stop_delta, handle);
     return cudaGetLastError();
 }
 

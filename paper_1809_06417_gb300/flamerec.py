@@ -72,7 +72,8 @@ class fr_params(ctypes.Structure):
                 ("grad_step", ctypes.c_float), ("update_sigma", ctypes.c_int32),
                 ("lut_t_min", ctypes.c_float), ("lut_t_max", ctypes.c_float), ("lut", ctypes.c_void_p),
                 ("lut_size", ctypes.c_int32), ("use_hull", ctypes.c_int32),
-                ("skip_empty", ctypes.c_int32), ("hull_tags", ctypes.c_void_p)]
+                ("skip_empty", ctypes.c_int32), ("hull_tags", ctypes.c_void_p), ("hg_g", ctypes.c_float),
+                ("sequential_views", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
