@@ -393,7 +393,8 @@ def run_video(fr, ctx, frames=64, n=96, views=8, side=384, iters=20, step=0.5, s
     cams = synth.ring_cameras(views, side, side, elevation_jitter_deg=10.0, seed=seed)
     fcams = fr.cameras(cams)
     gts = synth.video_frames(frames, n, seed)
-    p = fr.params(step=step, alpha_l=alpha_for(n, views, side, step))
+    # each frame restricted to its own visual hull (Sec. 4.3.1), empty bricks skipped
+    p = fr.params(step=step, alpha_l=alpha_for(n, views, side, step), use_hull=1)
     probs, vols, n_fwd, n_adj = [], [], 0, 0
     for f, gt in enumerate(gts):
         g = torch.as_tensor(gt, dtype=torch.float32, device="cuda").to(dt).contiguous()
@@ -405,7 +406,7 @@ def run_video(fr, ctx, frames=64, n=96, views=8, side=384, iters=20, step=0.5, s
         v = g.clone()
         v[..., :3] = 0
         fv = fr.volume(v, origin, h)
-        n_fwd += ctx.fr_count_samples(fv, fcams, p)
+        n_fwd += ctx.fr_count_samples(fv, fcams, fr.params(step=step, skip_empty=0))
         n_adj += ctx.fr_count_samples(fv, fcams, p, residual=img)
         rm = torch.zeros((iters, 3), device="cuda")
         vols.append((v, img, bbox, rm))
@@ -425,9 +426,11 @@ def run_video(fr, ctx, frames=64, n=96, views=8, side=384, iters=20, step=0.5, s
     t = e0.elapsed_time(e1) / 1e3
     final = np.stack([rm[-1].cpu().numpy() for *_, rm in vols])
     return {"workload": f"video_{frames}x{n}^3_{views}x{side}^2", "frames": frames, "iters_per_frame": iters,
-            "seconds": t, "frames_per_s": frames / t, "samples_per_s": (n_fwd + n_adj) * iters / t,
-            "samples_per_iteration": {"fwd": n_fwd, "adj": n_adj}, "graph": True, "storage": storage,
-            "final_rmse_mean": [float(x) for x in final.mean(axis=0)], "launches_per_iteration": 4}
+            "seconds": t, "frames_per_s": frames / t,
+            "nominal_samples_per_s": (n_fwd + n_adj) * iters / t,   # every in-box sample, skipped ones included
+            "samples_per_iteration": {"fwd_all_in_box": n_fwd, "adj_flame_rays": n_adj}, "graph": True,
+            "storage": storage, "visual_hull": True,
+            "final_rmse_mean": [float(x) for x in final.mean(axis=0)], "launches_per_iteration": 8}
 
 
 def run_serving(fr, ctx, jobs=40, rate=20.0, seed=5, step=0.5):
@@ -460,7 +463,7 @@ def run_serving(fr, ctx, jobs=40, rate=20.0, seed=5, step=0.5):
                           init16=torch.as_tensor(init, dtype=torch.float32).to(torch.bfloat16)
                           .view(torch.int16).numpy().view(np.uint16).copy(),
                           alpha=alpha_for(n, K, side, step)))
-    p = fr.params(step=step, alpha_l=2e-4)
+    p = fr.params(step=step, alpha_l=2e-4, use_hull=1)   # each job in its own visual hull
 
     def submitter(sp):
         return lambda srv: srv.submit(sp["shape"], sp["origin"], sp["h"], sp["cams"], sp["js"]["iters"],
@@ -495,7 +498,7 @@ def run_serving(fr, ctx, jobs=40, rate=20.0, seed=5, step=0.5):
         ctx.fr_prepare_targets(t, 30 / 255, bbox)
         rm = np.zeros((sp["js"]["iters"], 3), dtype=np.float32)
         ctx.fr_reconstruct(fr.volume(v, sp["origin"], sp["h"]), fr.cameras(sp["cams"]), t, bbox, sp["js"]["iters"],
-                           fr.params(step=step, alpha_l=sp["alpha"]), rmse=rm)
+                           fr.params(step=step, alpha_l=sp["alpha"], use_hull=1), rmse=rm)
         rmse_single.append(rm[-1, 1])
     torch.cuda.synchronize()
     t_single = time.perf_counter() - t0
@@ -506,7 +509,8 @@ def run_serving(fr, ctx, jobs=40, rate=20.0, seed=5, step=0.5):
             "offline": {"batched_bf16_jobs_per_s": jobs / t_batched, "single_f32_jobs_per_s": jobs / t_single,
                         "speedup": t_single / t_batched, "final_rmse_green_mean_batched": float(rmse_batched),
                         "final_rmse_green_mean_single": float(np.mean(rmse_single))},
-            "storage": "bf16", "mix": "grids {64,96,128,192}^3, 4-12 views, side 256-768, 20-50 iterations"}
+            "storage": "bf16", "visual_hull": True,
+            "mix": "grids {64,96,128,192}^3, 4-12 views, side 256-768, 20-50 iterations"}
 
 
 def run_temperature_views(fr, ctx, n=128, side=512, step=0.5, iters=50, seed=3, view_counts=(4, 16, 28),

@@ -275,9 +275,12 @@ typedef struct fr_problem {
  * once: each iteration runs one forward launch, one error reduction, one
  * adjustment launch over the flame rays of all problems and one update
  * launch, whatever nprob is.  Volumes share one storage type; grids, cameras
- * and image sizes may differ.  Parameters are shared.  use_graph != 0 captures
- * the iterations in a CUDA graph and launches it once; the call then returns
- * after the work is done.  Scratch is sized from all problems at once. */
+ * and image sizes may differ.  Parameters are shared.  p->use_hull: each
+ * problem's visual hull is computed from its own targets (p->hull_tags is not
+ * read) and its records outside it are held at 0; p->skip_empty: empty bricks
+ * are skipped as in fr_reconstruct.  use_graph != 0 captures the iterations in
+ * a CUDA graph and launches it once; the call then returns after the work is
+ * done.  Scratch is sized from all problems at once. */
 fr_status fr_reconstruct_batch(fr_ctx *ctx, const fr_problem *probs, int nprob, int iters,
                                int first_iteration, const fr_params *p, int use_graph);
 
@@ -322,7 +325,9 @@ typedef struct fr_job_info {
 
 /* budget_bytes: device memory the server may hold for resident jobs; 0 means
  * 80% of the device's free memory at creation.  dtype: storage type of every
- * job's volume.  p: shared method parameters (paper rule). */
+ * job's volume.  p: shared method parameters (paper rule); with p->use_hull
+ * each job's visual hull is computed from its frames at admission, and
+ * p->skip_empty skips empty bricks, as in fr_reconstruct_batch. */
 fr_status fr_server_create(fr_ctx *ctx, const fr_params *p, int dtype, size_t budget_bytes,
                            fr_server **out);
 fr_status fr_server_destroy(fr_server *srv);

@@ -306,3 +306,7 @@ using namespace frabi;
     FR_CUDA(c, cudaSetDevice(c->device))
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Visual hull tags of one problem (api.cu): flame-mask tables in the
+// context's scratch, one tag per node into `tags` (device).
+fr_status hull_tags(fr_ctx* c, const SingleArgs& a, const float* targets, float thresh, unsigned* tags);

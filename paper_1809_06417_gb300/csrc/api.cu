@@ -524,7 +524,7 @@ extern "C" fr_status fr_count_samples(fr_ctx* c, const fr_volume* vol, const fr_
 
 // Hull tags of a problem into `tags` (library scratch for the mask tables; the
 // cameras travel as launch parameters).
-static fr_status hull_tags(fr_ctx* c, const SingleArgs& a, const float* targets, float thresh, unsigned* tags)
+fr_status hull_tags(fr_ctx* c, const SingleArgs& a, const float* targets, float thresh, unsigned* tags)
 {
     const ProbDev& P = a.p;
     FR_TRY(ensure(c, c->sat, (size_t)P.ncam * (P.H + 1) * (P.W + 1) * sizeof(unsigned), "flame-mask tables"));
@@ -1040,6 +1040,9 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
     if (!p) return fail(c, FR_EINVAL, "params is NULL");
     if (p->rule != FR_RULE_PAPER) return fail(c, FR_EINVAL, "batched reconstruction uses FR_RULE_PAPER");
     const int dt = probs[0].vol.dtype;
+    // visual hull per problem (from its own targets) and exact empty-brick skipping
+    const bool hull = p->use_hull != 0;
+    const bool skip = p->skip_empty && !(p->tau > 0.0f);
     // sizes and validation
     size_t arena = 0, cams_total = 0;
     long long tiles_total = 0;
@@ -1062,6 +1065,10 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         arena += align256(ib) + align256((size_t)node_count(&q.vol) * 16) + align256((size_t)nt * 16) +
                  align256((size_t)std::max(iters, 1) * 16) + align256(flame_list_buf_entries(nt) * 4) +
                  align256((size_t)npix * 4) + align256((size_t)node_count(&q.vol) * 2 * rec_bytes(&q.vol));
+        const size_t tb = align256(brick_table_bytes(q.vol.nx, q.vol.ny, q.vol.nz));
+        if (hull) arena += align256((size_t)node_count(&q.vol) * 4);
+        if (skip) arena += tb;
+        if (hull && skip) arena += tb;
         tiles_total += nt;
         cams_total += (size_t)q.ncam;
     }
@@ -1112,7 +1119,28 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         unsigned* fbuf = reinterpret_cast<unsigned*>(dbase + off); off += align256(flame_list_buf_entries(nt) * 4);
         unsigned* flist = reinterpret_cast<unsigned*>(dbase + off); off += align256((size_t)npix * 4);
         void* pairs = dbase + off; off += align256((size_t)nodes * 2 * rec_bytes(&q.vol));
+        const size_t tb = align256(brick_table_bytes(q.vol.nx, q.vol.ny, q.vol.nz));
+        unsigned* tags = nullptr;
+        unsigned char *occ = nullptr, *hb = nullptr;
+        if (hull) { tags = reinterpret_cast<unsigned*>(dbase + off); off += align256((size_t)nodes * 4); }
+        if (skip) { occ = reinterpret_cast<unsigned char*>(dbase + off); off += tb; }
+        if (hull && skip) { hb = reinterpret_cast<unsigned char*>(dbase + off); off += tb; }
+        const int nbx = bricks_along(q.vol.nx), nby = bricks_along(q.vol.ny), nbz = bricks_along(q.vol.nz);
+        const unsigned full = q.ncam >= 32 ? 0xffffffffu : ((1u << q.ncam) - 1u);
+        if (hull) {
+            FR_TRY(hull_tags(c, a, q.targets, p->flame_thresh, tags));
+            FR_CUDA(c, launch_hull_clear(q.vol.data, dt, q.vol.nx, q.vol.ny, q.vol.nz, tags, full, hb, s));
+        }
         ProbDev& P = a.p;
+        P.nbx = nbx;
+        P.nby = nby;
+        P.nbz = nbz;
+        P.occ = occ;
+        P.occ_box = occ ? brick_box(occ, nbx, nby, nbz) : nullptr;
+        P.hull = tags;
+        P.hull_full = full;
+        P.adj_occ = hb;
+        P.adj_box = hb ? brick_box(hb, nbx, nby, nbz) : nullptr;
         P.cams = d_cams + cam_off;
         P.targets = q.targets;
         P.bbox = q.bbox;
@@ -1146,12 +1174,16 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
     auto iterate = [&](cudaStream_t st) -> cudaError_t {
         cudaError_t e = cudaSuccess;
         for (int it = 0; it < iters && e == cudaSuccess; ++it) {
-            e = launch_pair_pack_batch(d_probs, nprob, dt, st);
-            if (e == cudaSuccess) e = launch_fwd_batch(d_probs, d_tiles, nprob, tile_off, dt, KIND_RGB, tau, true, st);
+            if (skip) e = launch_brick_reset_batch(d_probs, nprob, st);
+            if (e == cudaSuccess) e = launch_pair_pack_batch(d_probs, nprob, dt, st);
+            if (e == cudaSuccess && skip) e = launch_brick_box_batch(d_probs, nprob, st);
+            if (e == cudaSuccess)
+                e = launch_fwd_batch(d_probs, d_tiles, nprob, tile_off, dt, KIND_RGB, tau, true, st, skip);
             if (e == cudaSuccess) e = launch_finalize_batch(d_probs, nprob, it, st);
             if (e == cudaSuccess)
-                e = launch_adjust_list_batch(d_probs, d_tiles, nprob, tile_off, dt, tau, it, st);
+                e = launch_adjust_list_batch(d_probs, d_tiles, nprob, tile_off, dt, tau, it, st, hull && skip);
             if (e == cudaSuccess) e = launch_apply_batch(d_probs, nprob, dt, p->clamp_nonneg, st);
+            if (e == cudaSuccess && hull) e = launch_hull_clear_batch(d_probs, nprob, dt, st);
         }
         return e;
     };

@@ -75,6 +75,10 @@ struct ProbDev {
     // index of this problem's first view in its G(s) stream (views rendered
     // one problem at a time keep their own index)
     int view_base;
+    // visual hull tags of this problem (batched hull clear): key points whose
+    // tag differs from hull_full are held at 0
+    const unsigned* hull;
+    unsigned hull_full;
     // when set, the adjustment's iteration index is iteration + *iter_dev
     // (loops whose iterations are counted on the device)
     const int* iter_dev;

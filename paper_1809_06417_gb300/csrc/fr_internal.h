@@ -24,14 +24,18 @@ inline int tiles_of(int W, int H, int ncam)
 // march.cu
 cudaError_t launch_fwd(const SingleArgs& a, int dt, int kind, int ntiles, cudaStream_t s);
 cudaError_t launch_fwd_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
-                             int dt, int kind, bool tau, bool pairs, cudaStream_t s);
+                             int dt, int kind, bool tau, bool pairs, cudaStream_t s, bool skip = false);
 // x-pair records of every problem's volume (vol_rw -> pairs), RGB records
 cudaError_t launch_pair_pack_batch(const ProbDev* probs, int nprob, int dt, cudaStream_t s);
 cudaError_t launch_adjust(const SingleArgs& a, int dt, int ntiles, cudaStream_t s);
 cudaError_t launch_adjust_list_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
-                                     int dt, bool tau, int iteration, cudaStream_t s);
+                                     int dt, bool tau, int iteration, cudaStream_t s, bool skip = false);
 cudaError_t launch_finalize_batch(const ProbDev* probs, int nprob, int iteration, cudaStream_t s);
 cudaError_t launch_apply_batch(const ProbDev* probs, int nprob, int dt, int clamp_nonneg, cudaStream_t s);
+// batched brick tables (P.occ: flags cleared, then their box) and hull clear (P.hull)
+cudaError_t launch_brick_reset_batch(const ProbDev* probs, int nprob, cudaStream_t s);
+cudaError_t launch_brick_box_batch(const ProbDev* probs, int nprob, cudaStream_t s);
+cudaError_t launch_hull_clear_batch(const ProbDev* probs, int nprob, int dt, cudaStream_t s);
 cudaError_t launch_rmse_batch(const ProbDev* probs, int nprob, int iters, float* rmse_all, cudaStream_t s);
 cudaError_t launch_backward(const SingleArgs& a, int dt, int kind, int ntiles, cudaStream_t s);
 cudaError_t launch_backward_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
@@ -90,13 +94,16 @@ cudaError_t launch_hull_clear(void* vol, int dt, int nx, int ny, int nz, const u
 // next 16-byte boundary, the box of the flagged bricks as six unsigned
 // values {nbx - lo_x, nby - lo_y, nbz - lo_z, hi_x + 1, hi_y + 1, hi_z + 1}
 // (all 0 when no brick is flagged).
-inline int bricks_along(int n) { return (n - 2) / kBrick + 1; }
-inline size_t brick_count(int nx, int ny, int nz)
+__host__ __device__ inline int bricks_along(int n) { return (n - 2) / kBrick + 1; }
+__host__ __device__ inline size_t brick_count(int nx, int ny, int nz)
 {
     return (size_t)bricks_along(nx) * bricks_along(ny) * bricks_along(nz);
 }
-inline size_t brick_box_offset(int nx, int ny, int nz) { return (brick_count(nx, ny, nz) + 15) & ~(size_t)15; }
-inline size_t brick_table_bytes(int nx, int ny, int nz) { return brick_box_offset(nx, ny, nz) + 32; }
+__host__ __device__ inline size_t brick_box_offset(int nx, int ny, int nz)
+{
+    return (brick_count(nx, ny, nz) + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t brick_table_bytes(int nx, int ny, int nz) { return brick_box_offset(nx, ny, nz) + 32; }
 __host__ __device__ inline unsigned* brick_box(unsigned char* table, int nbx, int nby, int nbz)
 {
     return reinterpret_cast<unsigned*>(table + (((size_t)nbx * nby * nbz + 15) & ~(size_t)15));

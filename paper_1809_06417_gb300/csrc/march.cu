@@ -432,7 +432,7 @@ __global__ void FR_ADJ_LIST_BOUNDS adj_list(const __grid_constant__ SingleArgs a
 // Batched form: CTA b belongs to the problem whose tile range holds b and
 // takes that problem's list entries [128 (b - start), ...).  The G(s) stream
 // index is the problem's own iteration plus `iteration`.
-template <int DT, bool TAU>
+template <int DT, bool TAU, bool SKIP>
 __global__ void FR_MARCH_BOUNDS adj_list_batch(const ProbDev* __restrict__ probs, const int* __restrict__ tile_start,
                                                int nprob, int iteration)
 {
@@ -445,7 +445,7 @@ __global__ void FR_MARCH_BOUNDS adj_list_batch(const ProbDev* __restrict__ probs
     const int view = (int)(pix / per_view);
     const unsigned r = pix - (unsigned)view * per_view;
     const int py = (int)(r / (unsigned)P.W), px = (int)(r - (unsigned)py * (unsigned)P.W);
-    adj_ray<DT, TAU>(P, P.cams, view, px, py, P.iteration + iteration);
+    adj_ray<DT, TAU, SKIP>(P, P.cams, view, px, py, P.iteration + iteration);
 }
 
 template <int DT, bool TAU>
@@ -768,11 +768,13 @@ cudaError_t launch_fwd(const SingleArgs& a, int dt, int kind, int ntiles, cudaSt
 }
 
 cudaError_t launch_fwd_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
-                             int dt, int kind, bool tau, bool pairs, cudaStream_t s)
+                             int dt, int kind, bool tau, bool pairs, cudaStream_t s, bool skip)
 {
     dim3 grid(total_tiles), block(kTileThreads);
+    skip = skip && pairs && kind == KIND_RGB && !tau;
 #define FR_FWDB(D, K, T)                                                                        \
-    if (pairs) fwd_batch<D, K, T, 1><<<grid, block, 0, s>>>(probs, tile_start, nprob);           \
+    if (skip) fwd_batch<D, K, T, 2><<<grid, block, 0, s>>>(probs, tile_start, nprob);            \
+    else if (pairs) fwd_batch<D, K, T, 1><<<grid, block, 0, s>>>(probs, tile_start, nprob);      \
     else fwd_batch<D, K, T, 0><<<grid, block, 0, s>>>(probs, tile_start, nprob)
     FR_DISPATCH_DT(dt, D, {
         if (kind == KIND_RGB) {
@@ -797,12 +799,13 @@ cudaError_t launch_adjust(const SingleArgs& a, int dt, int ntiles, cudaStream_t 
 }
 
 cudaError_t launch_adjust_list_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
-                                     int dt, bool tau, int iteration, cudaStream_t s)
+                                     int dt, bool tau, int iteration, cudaStream_t s, bool skip)
 {
     dim3 grid(total_tiles), block(kTileThreads);
     FR_DISPATCH_DT(dt, D, {
-        if (tau) adj_list_batch<D, true><<<grid, block, 0, s>>>(probs, tile_start, nprob, iteration);
-        else adj_list_batch<D, false><<<grid, block, 0, s>>>(probs, tile_start, nprob, iteration);
+        if (tau) adj_list_batch<D, true, false><<<grid, block, 0, s>>>(probs, tile_start, nprob, iteration);
+        else if (skip) adj_list_batch<D, false, true><<<grid, block, 0, s>>>(probs, tile_start, nprob, iteration);
+        else adj_list_batch<D, false, false><<<grid, block, 0, s>>>(probs, tile_start, nprob, iteration);
     });
     return cudaGetLastError();
 }

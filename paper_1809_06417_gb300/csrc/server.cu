@@ -27,6 +27,9 @@ struct fr_job {
     unsigned* fbuf = nullptr;
     unsigned* flist = nullptr;
     void* pairs = nullptr;
+    unsigned* tags = nullptr;           // visual hull tags (server with use_hull)
+    unsigned char* occ = nullptr;       // brick table of the non-empty records (skip_empty)
+    unsigned char* hull_bricks = nullptr;  // brick table of the hull (both)
     int ntiles = 0;
 };
 
@@ -53,10 +56,13 @@ struct fr_server {
 namespace {
 
 struct JobLayout {
-    size_t vol, targets, bbox, residual, dV, partials, sqerr, fbuf, flist, pairs, total;
+    size_t vol, targets, bbox, residual, dV, partials, sqerr, fbuf, flist, pairs, tags, occ, hull_bricks, total;
 };
 
-JobLayout job_layout(const fr_job_desc& d, int dtype, const fr_camera* cams)
+bool server_hull(const fr_server* s) { return s->p.use_hull != 0; }
+bool server_skip(const fr_server* s) { return s->p.skip_empty && !(s->p.tau > 0.0f); }
+
+JobLayout job_layout(const fr_job_desc& d, int dtype, const fr_camera* cams, bool hull, bool skip)
 {
     JobLayout L{};
     const long long nodes = (long long)d.nx * d.ny * d.nz;
@@ -74,6 +80,10 @@ JobLayout job_layout(const fr_job_desc& d, int dtype, const fr_camera* cams)
     L.fbuf = o; o += align256(flame_list_buf_entries(nt) * 4);
     L.flist = o; o += align256((size_t)npix * 4);
     L.pairs = o; o += align256((size_t)nodes * 8 * dtype_bytes(dtype));
+    const size_t tb = align256(brick_table_bytes(d.nx, d.ny, d.nz));
+    L.tags = o; if (hull) o += align256((size_t)nodes * 4);
+    L.occ = o; if (skip) o += tb;
+    L.hull_bricks = o; if (hull && skip) o += tb;
     L.total = o;
     return L;
 }
@@ -105,7 +115,8 @@ fr_status job_admit(fr_server* s, fr_job* j)
 {
     fr_ctx* c = s->ctx;
     cudaStream_t st = c->stream;
-    const JobLayout L = job_layout(j->d, s->dtype, j->cams.data());
+    const bool hull = server_hull(s), skip = server_skip(s);
+    const JobLayout L = job_layout(j->d, s->dtype, j->cams.data(), hull, skip);
     void* mem = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync(&mem, L.total, s->pool, st);
     if (e != cudaSuccess) {
@@ -124,6 +135,9 @@ fr_status job_admit(fr_server* s, fr_job* j)
     j->fbuf = reinterpret_cast<unsigned*>(j->mem + L.fbuf);
     j->flist = reinterpret_cast<unsigned*>(j->mem + L.flist);
     j->pairs = j->mem + L.pairs;
+    j->tags = hull ? reinterpret_cast<unsigned*>(j->mem + L.tags) : nullptr;
+    j->occ = skip ? reinterpret_cast<unsigned char*>(j->mem + L.occ) : nullptr;
+    j->hull_bricks = hull && skip ? reinterpret_cast<unsigned char*>(j->mem + L.hull_bricks) : nullptr;
     const long long nodes = (long long)j->d.nx * j->d.ny * j->d.nz;
     const size_t ib = image_bytes(j->cams.data(), j->d.ncam);
     const int W = j->cams[0].width, H = j->cams[0].height;
@@ -138,6 +152,12 @@ fr_status job_admit(fr_server* s, fr_job* j)
     fill_problem(&v, j->cams.data(), j->d.ncam, &s->p, a);
     a.p.targets = j->targets;
     FR_CUDA(c, launch_flame_list(a, j->ntiles, j->fbuf, j->flist, st));
+    if (hull) {
+        // the job's visual hull from its prepared frames; records outside it cleared
+        const unsigned full = j->d.ncam >= 32 ? 0xffffffffu : ((1u << j->d.ncam) - 1u);
+        FR_TRY(hull_tags(c, a, j->targets, s->p.flame_thresh, j->tags));
+        FR_CUDA(c, launch_hull_clear(j->vol, s->dtype, j->d.nx, j->d.ny, j->d.nz, j->tags, full, j->hull_bricks, st));
+    }
     j->state = FR_JOB_RUNNING;
     j->t_admit = s->now();
     return FR_OK;
@@ -249,7 +269,7 @@ extern "C" fr_status fr_server_submit(fr_server* s, const fr_job_desc* d, fr_job
     if (!d->init_records || !d->targets || !d->result_records) return fail(c, FR_EINVAL, "NULL host buffer");
     const long long npix = (long long)d->ncam * d->cams[0].width * d->cams[0].height;
     if (npix >= (1LL << 32)) return fail(c, FR_EINVAL, "at most 2^32 pixels per job");
-    const size_t fp = job_layout(*d, s->dtype, d->cams).total;
+    const size_t fp = job_layout(*d, s->dtype, d->cams, server_hull(s), server_skip(s)).total;
     if (fp > s->budget) return fail(c, FR_ENOMEM, "job needs %zu bytes, the budget is %zu", fp, s->budget);
     fr_job* j = new (std::nothrow) fr_job();
     if (!j) return fail(c, FR_ENOMEM, "host allocation failed");
@@ -354,6 +374,15 @@ extern "C" fr_status fr_server_step(fr_server* s, int* running, int* queued)
             P.sq_slot = j->iters_done;
             if (j->d.alpha_l != 0.0f) P.alpha_l = j->d.alpha_l;
             P.pairs = j->pairs;
+            P.nbx = bricks_along(j->d.nx);
+            P.nby = bricks_along(j->d.ny);
+            P.nbz = bricks_along(j->d.nz);
+            P.occ = j->occ;
+            P.occ_box = j->occ ? brick_box(j->occ, P.nbx, P.nby, P.nbz) : nullptr;
+            P.hull = j->tags;
+            P.hull_full = j->d.ncam >= 32 ? 0xffffffffu : ((1u << j->d.ncam) - 1u);
+            P.adj_occ = j->hull_bricks;
+            P.adj_box = j->hull_bricks ? brick_box(j->hull_bricks, P.nbx, P.nby, P.nbz) : nullptr;
             hp[i] = P;
             for (int k = 0; k < j->d.ncam; ++k) hc[cam_off + k] = a.cams[k];
             ht[i] = tile_off;
@@ -364,11 +393,15 @@ extern "C" fr_status fr_server_step(fr_server* s, int* running, int* queued)
         FR_CUDA(c, cudaMemcpyAsync(db, hb, tables, cudaMemcpyHostToDevice, st));
         FR_CUDA(c, cudaEventRecord(s->staging_done, st));
         const bool tau = s->p.tau > 0.0f;
+        const bool hull = server_hull(s), skip = server_skip(s);
+        if (skip) FR_CUDA(c, launch_brick_reset_batch(dp, n, st));
         FR_CUDA(c, launch_pair_pack_batch(dp, n, s->dtype, st));
-        FR_CUDA(c, launch_fwd_batch(dp, dtl, n, tile_off, s->dtype, KIND_RGB, tau, true, st));
+        if (skip) FR_CUDA(c, launch_brick_box_batch(dp, n, st));
+        FR_CUDA(c, launch_fwd_batch(dp, dtl, n, tile_off, s->dtype, KIND_RGB, tau, true, st, skip));
         FR_CUDA(c, launch_finalize_batch(dp, n, 0, st));
-        FR_CUDA(c, launch_adjust_list_batch(dp, dtl, n, tile_off, s->dtype, tau, 0, st));
+        FR_CUDA(c, launch_adjust_list_batch(dp, dtl, n, tile_off, s->dtype, tau, 0, st, hull && skip));
         FR_CUDA(c, launch_apply_batch(dp, n, s->dtype, s->p.clamp_nonneg, st));
+        if (hull) FR_CUDA(c, launch_hull_clear_batch(dp, n, s->dtype, st));
         FR_CUDA(c, cudaStreamSynchronize(st));
         // advance and retire
         for (size_t i = 0; i < s->resident.size();) {

@@ -134,8 +134,8 @@ __device__ __forceinline__ void mark_bricks(unsigned char* occ, int x, int y, in
             for (int bx = bx0; bx <= min(x >> 3, nbx - 1); ++bx) occ[((long long)bz * nby + by) * nbx + bx] = 1;
 }
 
-// The box of the flagged bricks of a brick table (one CTA of 1024 threads).
-__global__ void __launch_bounds__(1024) brick_box_kernel(unsigned char* table, int nbx, int nby, int nbz)
+// The box of the flagged bricks of a brick table (one CTA).
+__device__ __forceinline__ void brick_box_cta(unsigned char* table, int nbx, int nby, int nbz)
 {
     __shared__ unsigned red[6][32];
     const int nb = nbx * nby * nbz;
@@ -170,6 +170,61 @@ __global__ void __launch_bounds__(1024) brick_box_kernel(unsigned char* table, i
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(1024) brick_box_kernel(unsigned char* table, int nbx, int nby, int nbz)
+{
+    brick_box_cta(table, nbx, nby, nbz);
+}
+
+// Batched forms, one problem per blockIdx.y (reset, box) or per CTA (box).
+__global__ void __launch_bounds__(256) brick_reset_batch_kernel(const ProbDev* __restrict__ probs)
+{
+    const ProbDev& P = probs[blockIdx.y];
+    if (!P.occ) return;
+    unsigned char* t = const_cast<unsigned char*>(P.occ);
+    const size_t n = brick_table_bytes(P.nx, P.ny, P.nz);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        t[i] = 0;
+}
+
+__global__ void __launch_bounds__(1024) brick_box_batch_kernel(const ProbDev* __restrict__ probs)
+{
+    const ProbDev& P = probs[blockIdx.x];
+    if (!P.occ) return;
+    brick_box_cta(const_cast<unsigned char*>(P.occ), P.nbx, P.nby, P.nbz);
+}
+
+cudaError_t launch_brick_reset_batch(const ProbDev* probs, int nprob, cudaStream_t s)
+{
+    brick_reset_batch_kernel<<<dim3(8, nprob), 256, 0, s>>>(probs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_brick_box_batch(const ProbDev* probs, int nprob, cudaStream_t s)
+{
+    brick_box_batch_kernel<<<nprob, 1024, 0, s>>>(probs);
+    return cudaGetLastError();
+}
+
+// Records outside each problem's hull (hull tag != hull_full) set to 0.
+template <int DT>
+__global__ void __launch_bounds__(256) hull_clear_batch_kernel(const ProbDev* __restrict__ probs)
+{
+    const ProbDev& P = probs[blockIdx.y];
+    if (!P.hull) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P.nodes;
+         i += (long long)gridDim.x * blockDim.x)
+        if (__ldg(P.hull + i) != P.hull_full) store_rgb<DT>(P.vol_rw, i, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+}
+
+cudaError_t launch_hull_clear_batch(const ProbDev* probs, int nprob, int dt, cudaStream_t s)
+{
+    const dim3 grid(128, nprob);
+    if (dt == DT_F32) hull_clear_batch_kernel<DT_F32><<<grid, 256, 0, s>>>(probs);
+    else if (dt == DT_BF16) hull_clear_batch_kernel<DT_BF16><<<grid, 256, 0, s>>>(probs);
+    else hull_clear_batch_kernel<DT_F16><<<grid, 256, 0, s>>>(probs);
+    return cudaGetLastError();
 }
 
 static cudaError_t launch_brick_box(unsigned char* table, int nx, int ny, int nz, cudaStream_t s)
@@ -226,20 +281,26 @@ __global__ void __launch_bounds__(256) pair_pack_batch_kernel(const ProbDev* __r
     const int nx = P.nx;
     const void* src = P.vol_rw;
     void* dst = const_cast<void*>(P.pairs);
+    unsigned char* occ = const_cast<unsigned char*>(P.occ);   // brick flags (cleared beforehand), or null
     for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
         const long long r0 = row * nx;
         for (int x = threadIdx.x; x < nx; x += blockDim.x) {
             const long long i = r0 + x, j = x < nx - 1 ? i + 1 : i;
+            bool nonzero;
             if constexpr (DT == DT_F32) {
                 const float4* s4 = reinterpret_cast<const float4*>(src);
                 float4* d4 = reinterpret_cast<float4*>(dst);
-                d4[2 * i] = s4[i];
+                const float4 a = s4[i];
+                d4[2 * i] = a;
                 d4[2 * i + 1] = s4[j];
+                nonzero = a.x != 0.0f || a.y != 0.0f || a.z != 0.0f || a.w != 0.0f;
             } else {
                 const uint2* s2 = reinterpret_cast<const uint2*>(src);
                 const uint2 a = s2[i], b = s2[j];
                 reinterpret_cast<uint4*>(dst)[i] = make_uint4(a.x, a.y, b.x, b.y);
+                nonzero = ((a.x | a.y) & 0x7fff7fffu) != 0u;
             }
+            if (occ && nonzero) mark_bricks(occ, x, (int)(row % P.ny), (int)(row / P.ny), P.nbx, P.nby, P.nbz);
         }
     }
 }

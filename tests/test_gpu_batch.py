@@ -26,15 +26,15 @@ def _problem(fr, ctx, synth, n, views, side, seed, step=0.5):
     return dict(origin=origin, h=h, cams=cams, targets=img, bbox=bbox, v0=v0)
 
 
-@pytest.mark.parametrize("use_graph", [False, True])
-def test_batch_equals_each_problem_alone(use_graph):
+@pytest.mark.parametrize("use_graph,use_hull", [(False, 0), (True, 0), (True, 1)])
+def test_batch_equals_each_problem_alone(use_graph, use_hull):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1809_06417_gb300 import flamerec as fr, synth
     ctx = fr.Context(0)
     specs = [(24, 3, 40, 11), (32, 5, 56, 12), (20, 4, 33, 13)]
     probs = [_problem(fr, ctx, synth, *s) for s in specs]
-    iters, p = 4, fr.params(step=0.5, alpha_l=2e-3, g_std=0.05, seed=9)
+    iters, p = 4, fr.params(step=0.5, alpha_l=2e-3, g_std=0.05, seed=9, use_hull=use_hull)
     alone = []
     for q in probs:
         v = q["v0"].clone()

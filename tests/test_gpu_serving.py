@@ -80,10 +80,11 @@ def test_same_result_alone_and_in_the_mix(env, dtype, tol):
     srv.close()
 
 
-def test_server_matches_reconstruct(env):
+@pytest.mark.parametrize("use_hull", [0, 1])
+def test_server_matches_reconstruct(env, use_hull):
     fr, ctx, jobs = env
     q = jobs[1]
-    p = fr.params(step=0.5, alpha_l=2e-3)
+    p = fr.params(step=0.5, alpha_l=2e-3, use_hull=use_hull)
     srv = fr.Server(ctx, p, dtype=fr.FR_F32)
     job = _submit(srv, q, 6, "f32")
     job.wait()
