@@ -739,12 +739,13 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
                 if (hg) {
                     if (v == 0 || seq)
                         FR_CUDA(c, launch_scatter_L6(vol->data, vol->dtype, static_cast<float*>(c->L6.p), vol->nx,
-                                                     vol->ny, vol->nz, st));
+                                                     vol->ny, vol->nz, st, p->skip_empty != 0));
                     FR_CUDA(c, launch_source_hg(vol->data, vol->dtype, albedo, static_cast<const float*>(c->L6.p),
                                                 hg_weights(v), c->src.p, nodes, st));
                 } else if (v == 0 || seq) {
                     FR_CUDA(c, launch_scatter_source(vol->data, vol->dtype, albedo, static_cast<float*>(c->J.p),
-                                                     c->src.p, vol->dtype, vol->nx, vol->ny, vol->nz, st));
+                                                     c->src.p, vol->dtype, vol->nx, vol->ny, vol->nz, st,
+                                                     p->skip_empty != 0));
                 }
                 FR_TRY(trace_mark(c, FR_PHASE_SCATTER));
             }
@@ -786,7 +787,7 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
         const int slot = it < 0 ? 0 : it;
         if (albedo) {
             FR_CUDA(c, launch_scatter_source(vol->data, vol->dtype, albedo, static_cast<float*>(c->J.p), c->src.p,
-                                             vol->dtype, vol->nx, vol->ny, vol->nz, st));
+                                             vol->dtype, vol->nx, vol->ny, vol->nz, st, p->skip_empty != 0));
             FR_TRY(trace_mark(c, FR_PHASE_SCATTER));
         }
         FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, occ,

@@ -54,8 +54,12 @@ cudaError_t launch_adjust_list(const SingleArgs& a, int dt, int ntiles, const un
 // volume.cu
 cudaError_t launch_apply(void* vol, int dt, int kind, long long nodes, float* dV, float scale,
                          int with_sigma, int clamp_nonneg, int zero_dV, cudaStream_t s);
+// skip_empty: chunks of a grid line whose records are all zero skip their
+// walks; J is then left undefined at their nodes (their source is 0 anyway),
+// so only the reconstruction loop, which reads the source alone, asks for it.
 cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* albedo, float* J,
-                                  void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s);
+                                  void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s,
+                                  bool skip_empty = false);
 cudaError_t launch_planck_lut(float t_min, float t_max, int m, float* lut, cudaStream_t s);
 cudaError_t launch_prepare_targets(float* targets, int ncam, int H, int W, float thresh, int* bbox,
                                    cudaStream_t s);
@@ -75,7 +79,8 @@ cudaError_t launch_converge(const float* sq4, float* hist3, int* iter, unsigned*
 // In-scattering with a Henyey-Greenstein phase function: the six directional
 // radiances per node (L6, nodes x 6 float4, d = 2 axis + (0: +axis, 1: -axis)),
 // and the source towards one view, S = q + albedo sigma sum_d w_d L_d.
-cudaError_t launch_scatter_L6(const void* emission, int dt, float* L6, int nx, int ny, int nz, cudaStream_t s);
+cudaError_t launch_scatter_L6(const void* emission, int dt, float* L6, int nx, int ny, int nz, cudaStream_t s,
+                              bool skip_empty = false);
 struct HgWeights {
     float w[6];
 };

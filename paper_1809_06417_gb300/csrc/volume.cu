@@ -365,6 +365,11 @@ struct Seg {
     float e, c0, c1, c2;
 };
 
+__device__ __forceinline__ bool nonzero_record(float4 r)
+{
+    return r.x != 0.0f || r.y != 0.0f || r.z != 0.0f || r.w != 0.0f;
+}
+
 template <int DT>
 __device__ __forceinline__ Seg seg_between(float4 a, float4 b)
 {
@@ -379,7 +384,7 @@ __device__ __forceinline__ Seg seg_between(float4 a, float4 b)
 template <int DT, int AXIS, bool LAST>
 __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const void* em, const float* albedo,
                                                                             float* J, void* out, int nx, int ny,
-                                                                            int nz, float4* L6)
+                                                                            int nz, float4* L6, bool skip_empty)
 {
     __shared__ float4 fwd[kSweepChunks][kSweepLines];   // {E, C0, C1, C2} of each chunk, forward
     __shared__ float4 bwd[kSweepChunks][kSweepLines];   // and backward
@@ -409,11 +414,14 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const
     // backward map of the segments into s1-1..s0
     float Ef = 1.0f, F0 = 0.0f, F1 = 0.0f, F2 = 0.0f;
     float Eb = 1.0f, B0 = 0.0f, B1 = 0.0f, B2 = 0.0f;
+    bool occupied = false;   // some record of the chunk's nodes is non-zero
     if (live && s1 > s0) {
         const int lo = max(s0 - 1, 0), hi = min(s1, n_line - 1);
         float4 prev = load_rgb<DT>(em, start + lo * stride);
+        if (lo == s0) occupied = nonzero_record(prev);
         for (int i = lo + 1; i <= hi; ++i) {
             const float4 cur = load_rgb<DT>(em, start + i * stride);
+            if (i < s1) occupied |= nonzero_record(cur);
             const Seg g = seg_between<DT>(prev, cur);
             if (i >= s0 && i < s1) {   // forward segment into node i
                 F0 = fmaf(F0, g.e, g.c0); F1 = fmaf(F1, g.e, g.c1); F2 = fmaf(F2, g.e, g.c2);
@@ -430,6 +438,22 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const
     bwd[ch][threadIdx.x] = make_float4(Eb, B0, B1, B2);
     __syncthreads();
     if (!live || s1 <= s0) return;
+    if (skip_empty && !occupied) {
+        // every record of the chunk is zero: no extinction, so J at its nodes
+        // is never used (S = q + albedo sigma J = 0 there); the light crossing
+        // it is carried by the chunk maps.  Only the stores the next steps
+        // read are made: zero directional radiances, or the zero source.
+        for (int i = s0; i < s1; ++i) {
+            const long long node = start + i * stride;
+            if (L6) {
+                L6[6 * node + 2 * AXIS] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                L6[6 * node + 2 * AXIS + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            } else if constexpr (LAST) {
+                store_rgb<DT>(out, node, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+            }
+        }
+        return;
+    }
 
     // phase 2: radiance arriving at the chunk from either side
     float lf0 = 0.0f, lf1 = 0.0f, lf2 = 0.0f;
@@ -503,7 +527,8 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const
 // (forward maps, composed first-then-next) and an inclusive suffix (backward
 // maps).  It initialises J (the first sweep).
 template <int DT>
-__global__ void __launch_bounds__(256) sweep_x_kernel(const void* em, float* J, int nx, int ny, int nz, float4* L6)
+__global__ void __launch_bounds__(256) sweep_x_kernel(const void* em, float* J, int nx, int ny, int nz, float4* L6,
+                                                      bool skip_empty)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -514,11 +539,14 @@ __global__ void __launch_bounds__(256) sweep_x_kernel(const void* em, float* J, 
     const int s0 = min(lane * m, nx), s1 = min(s0 + m, nx);
     float Ef = 1.0f, F0 = 0.0f, F1 = 0.0f, F2 = 0.0f;
     float Eb = 1.0f, B0 = 0.0f, B1 = 0.0f, B2 = 0.0f;
+    bool occupied = false;   // some record of the chunk's nodes is non-zero
     if (s1 > s0) {
         const int lo = max(s0 - 1, 0), hi = min(s1, nx - 1);
         float4 prev = load_rgb<DT>(em, start + lo);
+        if (lo == s0) occupied = nonzero_record(prev);
         for (int i = lo + 1; i <= hi; ++i) {
             const float4 cur = load_rgb<DT>(em, start + i);
+            if (i < s1) occupied |= nonzero_record(cur);
             const Seg g = seg_between<DT>(prev, cur);
             if (i >= s0 && i < s1) {
                 F0 = fmaf(F0, g.e, g.c0); F1 = fmaf(F1, g.e, g.c1); F2 = fmaf(F2, g.e, g.c2);
@@ -559,6 +587,19 @@ __global__ void __launch_bounds__(256) sweep_x_kernel(const void* em, float* J, 
     if (s1 <= s0) return;
     const float sixth = 1.0f / 6.0f;
     float4* J4 = reinterpret_cast<float4*>(J);
+    if (skip_empty && !occupied) {
+        // an empty chunk (see sweep_kernel): J = 0 so that later sweeps add to
+        // a defined value, zero directional radiances in L6 mode
+        for (int i = s0; i < s1; ++i) {
+            if (L6) {
+                L6[6 * (start + i)] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                L6[6 * (start + i) + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            } else {
+                J4[start + i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+        }
+        return;
+    }
     {
         float4 prev = load_rgb<DT>(em, start + max(s0 - 1, 0));
         for (int i = s0; i < s1; ++i) {
@@ -593,7 +634,7 @@ __global__ void __launch_bounds__(256) sweep_x_kernel(const void* em, float* J, 
 }
 
 cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* albedo, float* J,
-                                  void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s)
+                                  void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s, bool skip_empty)
 {
     if (dt_in != dt_out) return cudaErrorInvalidValue;
     const long long lx = (long long)ny * nz, ly = (long long)nx * nz, lz = (long long)nx * ny;
@@ -602,9 +643,9 @@ cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* 
     const unsigned gz = (unsigned)((lz + kSweepLines - 1) / kSweepLines);
     const dim3 B(kSweepLines, kSweepChunks);
 #define FR_SWEEPS(D)                                                                         \
-    sweep_x_kernel<D><<<gxw, 256, 0, s>>>(emission, J, nx, ny, nz, nullptr);                \
-    sweep_kernel<D, 1, false><<<gy, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz, nullptr); \
-    sweep_kernel<D, 2, true><<<gz, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz, nullptr)
+    sweep_x_kernel<D><<<gxw, 256, 0, s>>>(emission, J, nx, ny, nz, nullptr, skip_empty);                \
+    sweep_kernel<D, 1, false><<<gy, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz, nullptr, skip_empty); \
+    sweep_kernel<D, 2, true><<<gz, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz, nullptr, skip_empty)
     if (dt_in == DT_F32) { FR_SWEEPS(DT_F32); }
     else if (dt_in == DT_BF16) { FR_SWEEPS(DT_BF16); }
     else { FR_SWEEPS(DT_F16); }
@@ -612,7 +653,8 @@ cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_L6(const void* emission, int dt, float* L6, int nx, int ny, int nz, cudaStream_t s)
+cudaError_t launch_scatter_L6(const void* emission, int dt, float* L6, int nx, int ny, int nz, cudaStream_t s,
+                              bool skip_empty)
 {
     const long long lx = (long long)ny * nz, ly = (long long)nx * nz, lz = (long long)nx * ny;
     const unsigned gxw = (unsigned)((lx + 7) / 8);
@@ -621,9 +663,9 @@ cudaError_t launch_scatter_L6(const void* emission, int dt, float* L6, int nx, i
     const dim3 B(kSweepLines, kSweepChunks);
     float4* L = reinterpret_cast<float4*>(L6);
 #define FR_SWEEPS6(D)                                                                            \
-    sweep_x_kernel<D><<<gxw, 256, 0, s>>>(emission, nullptr, nx, ny, nz, L);                    \
-    sweep_kernel<D, 1, false><<<gy, B, 0, s>>>(emission, nullptr, nullptr, nullptr, nx, ny, nz, L); \
-    sweep_kernel<D, 2, false><<<gz, B, 0, s>>>(emission, nullptr, nullptr, nullptr, nx, ny, nz, L)
+    sweep_x_kernel<D><<<gxw, 256, 0, s>>>(emission, nullptr, nx, ny, nz, L, skip_empty);                    \
+    sweep_kernel<D, 1, false><<<gy, B, 0, s>>>(emission, nullptr, nullptr, nullptr, nx, ny, nz, L, skip_empty); \
+    sweep_kernel<D, 2, false><<<gz, B, 0, s>>>(emission, nullptr, nullptr, nullptr, nx, ny, nz, L, skip_empty)
     if (dt == DT_F32) { FR_SWEEPS6(DT_F32); }
     else if (dt == DT_BF16) { FR_SWEEPS6(DT_BF16); }
     else { FR_SWEEPS6(DT_F16); }
