@@ -618,6 +618,42 @@ def run_held_out(fr, ctx, n=128, views=10, side=512, step=0.5, iters=50, seed=2)
             "input_views_rmse_first": [float(x) for x in rmse[0]]}
 
 
+def run_differentiable(fr, ctx, n=128, views=8, side=512, step=0.5, seed=3, reps=5):
+    """The differentiable temperature path (C3): forward render through the
+    colour-temperature table and the exact backward through
+    torch.autograd.Function, timed with CUDA events (median of reps)."""
+    import torch
+    from paper_1809_06417_gb300 import autograd as ag, synth
+    shape, origin, h = synth.unit_grid(n)
+    lut = torch.zeros((4096, 4), device="cuda")
+    ctx.fr_planck_lut(800.0, 2000.0, lut)
+    cams = synth.ring_cameras(views, side, side, elevation_jitter_deg=10.0, seed=seed)
+    scene = ag.RenderScene(ctx, cams, origin, h, kind=fr.FR_KIND_TEMP, step=step, lut=lut,
+                           lut_t_min=800.0, lut_t_max=2000.0)
+    vol = torch.as_tensor(synth.temperature_volume(n, seed), dtype=torch.float32,
+                          device="cuda").requires_grad_(True)
+    w = torch.randn(scene.image_shape, device="cuda")
+    stream = torch.cuda.current_stream()
+    fwd_ms, bwd_ms = [], []
+    for i in range(reps + 1):
+        vol.grad = None
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        img = ag.render(vol, scene)
+        e1.record(stream)
+        (img * w).sum().backward()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        if i:
+            fwd_ms.append(e0.elapsed_time(e1))
+            bwd_ms.append(e1.elapsed_time(e2))
+    n_fwd = ctx.fr_count_samples(scene.volume(vol.detach()), scene.fcams, scene.params)
+    return {"workload": f"temperature_autograd_{n}^3_{views}x{side}^2", "forward_ms": statistics.median(fwd_ms),
+            "backward_ms": statistics.median(bwd_ms), "samples_per_pass": n_fwd,
+            "backward_samples_per_s": n_fwd / (statistics.median(bwd_ms) / 1e3),
+            "note": "backward includes the loss and torch's reduction kernels around fr_render_backward"}
+
+
 class OracleSample:
     """The oracle on bounded samples of the workload: a band of image rows of
     one view, one iteration (in-scattering source, render of those pixels,
@@ -751,6 +787,7 @@ def main():
         out["serving"] = run_serving(fr, ctx, jobs=args.serving_jobs)
         out["temperature_views"] = run_temperature_views(fr, ctx)
         out["held_out_view"] = run_held_out(fr, ctx)
+        out["differentiable"] = run_differentiable(fr, ctx)
         ctx.close()
     if rank == 0:
         out["cpu_baseline"] = cpu

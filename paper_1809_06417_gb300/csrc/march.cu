@@ -480,20 +480,27 @@ __device__ __forceinline__ void bwd_body(const ProbDev& P, const CamDev* cams, i
     const long long nxy = (long long)P.nx * P.ny;
     using Rec = RecOf<DT, KIND>;
     using RT = typename Rec::T;
-    float4 acc[8];
+    // per key point: {dS_r, dS_g, dS_b, dsigma} (RGB) or {dT, dsigma} (TEMP)
+    constexpr int NA = KIND == KIND_RGB ? 4 : 2;
+    float acc[8][NA];
     RT v[8];
     long long vbase = -1;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) acc[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int t = 0; t < 8; ++t)
+#pragma unroll
+        for (int q = 0; q < NA; ++q) acc[t][q] = 0.0f;
     float* dV = P.dV;
     const void* vol = P.vol;
     auto leave = [&acc, dV](int t, int node) {
-        const float4 a = acc[t];
-        if (a.x != 0.0f || a.y != 0.0f || a.z != 0.0f || a.w != 0.0f) {
-            if constexpr (KIND == KIND_RGB) red_add_v4(dV + 4 * (unsigned)node, a.x, a.y, a.z, a.w);
-            else red_add_v2(dV + 2 * (unsigned)node, a.x, a.y);
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < NA; ++q) any = any || acc[t][q] != 0.0f;
+        if (any) {
+            if constexpr (KIND == KIND_RGB) red_add_v4(dV + 4 * (unsigned)node, acc[t][0], acc[t][1], acc[t][2], acc[t][3]);
+            else red_add_v2(dV + 2 * (unsigned)node, acc[t][0], acc[t][1]);
         }
-        acc[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int q = 0; q < NA; ++q) acc[t][q] = 0.0f;
     };
     Win W;
     W.live = false;
@@ -530,24 +537,35 @@ __device__ __forceinline__ void bwd_body(const ProbDev& P, const CamDev* cams, i
                    g2 * (tdb * S[2] - len * (Lt2 - p2));
             T *= e;
         }
-        float4 gv;
-        if constexpr (KIND == KIND_RGB) gv = make_float4(gS0, gS1, gS2, gsig);
-        else gv = make_float4(gS0 * dq[0] + gS1 * dq[1] + gS2 * dq[2], gsig, 0.0f, 0.0f);
+        float gv[NA];
+        if constexpr (KIND == KIND_RGB) {
+            gv[0] = gS0; gv[1] = gS1; gv[2] = gS2; gv[3] = gsig;
+        } else {
+            gv[0] = gS0 * dq[0] + gS1 * dq[1] + gS2 * dq[2];
+            gv[1] = gsig;
+        }
         const float wx[2] = {1.0f - gx, gx}, wy[2] = {1.0f - gy, gy}, wz[2] = {1.0f - gz, gz};
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
             const float w = wx[t & 1] * wy[(t >> 1) & 1] * wz[t >> 2];
-            acc[t].x = fmaf(w, gv.x, acc[t].x);
-            acc[t].y = fmaf(w, gv.y, acc[t].y);
-            acc[t].z = fmaf(w, gv.z, acc[t].z);
-            acc[t].w = fmaf(w, gv.w, acc[t].w);
+#pragma unroll
+            for (int q = 0; q < NA; ++q) acc[t][q] = fmaf(w, gv[q], acc[t][q]);
         }
     }
     win_release(W, leave);
 }
 
+// Resident CTAs per SM asked for the backward march: 4 with temperature
+// records (128 registers), 3 with RGB records (168).
+#ifndef FR_BWD_MINB_RGB
+#define FR_BWD_MINB_RGB 3
+#endif
+#ifndef FR_BWD_MINB_TEMP
+#define FR_BWD_MINB_TEMP 4
+#endif
 template <int DT, int KIND, bool TAU>
-__global__ void FR_MARCH_BOUNDS bwd_single(const __grid_constant__ SingleArgs a)
+__global__ void __launch_bounds__(kTileThreads, KIND == KIND_RGB ? FR_BWD_MINB_RGB : FR_BWD_MINB_TEMP)
+    bwd_single(const __grid_constant__ SingleArgs a)
 {
     bwd_body<DT, KIND, TAU>(a.p, a.cams, blockIdx.x);
 }
