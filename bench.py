@@ -37,9 +37,9 @@ WORKLOAD = dict(name="full_rte_128^3_8x512^2", n=128, views=8, side=512, step=0.
                 alpha_l=2e-4, noise=1e-3, hull=True)
 # kernels one step (one fr_reconstruct iteration) launches: hull clear with
 # brick marks and its brick box, in-scatter sweeps (3), pair pack and its brick
-# box, forward (which lists the flame rays), error reduction, adjustment, apply,
-# hull clear, rmse
-KERNELS_PER_STEP = 13
+# box, forward (which lists the flame rays), error reduction, adjustment, update
+# (with the hull clear), rmse
+KERNELS_PER_STEP = 12
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures of
 # the current kernels at this workload (None where the kernel changed since)
 NCU_TRAFFIC = {("fwd", "f32"): 41.62e6 + 2.68e6, ("adj", "f32"): 20.92e6 + 0.0}
@@ -430,7 +430,7 @@ def run_video(fr, ctx, frames=64, n=96, views=8, side=384, iters=20, step=0.5, s
             "nominal_samples_per_s": (n_fwd + n_adj) * iters / t,   # every in-box sample, skipped ones included
             "samples_per_iteration": {"fwd_all_in_box": n_fwd, "adj_flame_rays": n_adj}, "graph": True,
             "storage": storage, "visual_hull": True,
-            "final_rmse_mean": [float(x) for x in final.mean(axis=0)], "launches_per_iteration": 8}
+            "final_rmse_mean": [float(x) for x in final.mean(axis=0)], "launches_per_iteration": 7}
 
 
 def run_serving(fr, ctx, jobs=40, rate=20.0, seed=5, step=0.5):

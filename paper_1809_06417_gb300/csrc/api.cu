@@ -768,15 +768,13 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
             }
             FR_TRY(trace_mark(c, FR_PHASE_ADJUST));
             if (seq || v == ncam - 1) {
+                // the update, with the hull clear fused in
                 if (p->rule == FR_RULE_PAPER)
                     FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg,
-                                            1, st));
+                                            1, st, hull, full));
                 else
                     FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, -p->grad_step,
-                                            p->update_sigma, p->clamp_nonneg, 1, st));
-                if (hull)
-                    FR_CUDA(c, launch_hull_clear(vol->data, vol->dtype, vol->nx, vol->ny, vol->nz, hull, full,
-                                                 nullptr, st));
+                                            p->update_sigma, p->clamp_nonneg, 1, st, hull, full));
                 FR_TRY(trace_mark(c, FR_PHASE_APPLY));
             }
         }
@@ -803,7 +801,7 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
             FR_CUDA(c, launch_adjust_list(u, vol->dtype, nt, flame_list, flame_cnt + slot, st));
             FR_TRY(trace_mark(c, FR_PHASE_ADJUST));
             FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg, 1,
-                                    st));
+                                    st, hull, full));
         } else {
             // d(0.5 sum m dL^2)/d(rendered) = -m dL: the residual scaled by -1
             u.p.img_scale = -1.0f;
@@ -811,10 +809,8 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
             FR_CUDA(c, launch_backward(u, vol->dtype, vol->kind, nt, st));
             FR_TRY(trace_mark(c, FR_PHASE_ADJUST));
             FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, -p->grad_step,
-                                    p->update_sigma, p->clamp_nonneg, 1, st));
+                                    p->update_sigma, p->clamp_nonneg, 1, st, hull, full));
         }
-        if (hull)
-            FR_CUDA(c, launch_hull_clear(vol->data, vol->dtype, vol->nx, vol->ny, vol->nz, hull, full, nullptr, st));
         FR_TRY(trace_mark(c, FR_PHASE_APPLY));
         return FR_OK;
     };
@@ -1183,8 +1179,7 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
             if (e == cudaSuccess) e = launch_finalize_batch(d_probs, nprob, it, st);
             if (e == cudaSuccess)
                 e = launch_adjust_list_batch(d_probs, d_tiles, nprob, tile_off, dt, tau, it, st, hull && skip);
-            if (e == cudaSuccess) e = launch_apply_batch(d_probs, nprob, dt, p->clamp_nonneg, st);
-            if (e == cudaSuccess && hull) e = launch_hull_clear_batch(d_probs, nprob, dt, st);
+            if (e == cudaSuccess) e = launch_apply_batch(d_probs, nprob, dt, p->clamp_nonneg, st);   // + hull clear
         }
         return e;
     };

@@ -32,10 +32,10 @@ cudaError_t launch_adjust_list_batch(const ProbDev* probs, const int* tile_start
                                      int dt, bool tau, int iteration, cudaStream_t s, bool skip = false);
 cudaError_t launch_finalize_batch(const ProbDev* probs, int nprob, int iteration, cudaStream_t s);
 cudaError_t launch_apply_batch(const ProbDev* probs, int nprob, int dt, int clamp_nonneg, cudaStream_t s);
-// batched brick tables (P.occ: flags cleared, then their box) and hull clear (P.hull)
+// batched brick tables (P.occ: flags cleared, then their box); the batched
+// update clears the records outside each problem's hull (P.hull)
 cudaError_t launch_brick_reset_batch(const ProbDev* probs, int nprob, cudaStream_t s);
 cudaError_t launch_brick_box_batch(const ProbDev* probs, int nprob, cudaStream_t s);
-cudaError_t launch_hull_clear_batch(const ProbDev* probs, int nprob, int dt, cudaStream_t s);
 cudaError_t launch_rmse_batch(const ProbDev* probs, int nprob, int iters, float* rmse_all, cudaStream_t s);
 cudaError_t launch_backward(const SingleArgs& a, int dt, int kind, int ntiles, cudaStream_t s);
 cudaError_t launch_backward_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
@@ -53,7 +53,8 @@ cudaError_t launch_adjust_list(const SingleArgs& a, int dt, int ntiles, const un
 
 // volume.cu
 cudaError_t launch_apply(void* vol, int dt, int kind, long long nodes, float* dV, float scale,
-                         int with_sigma, int clamp_nonneg, int zero_dV, cudaStream_t s);
+                         int with_sigma, int clamp_nonneg, int zero_dV, cudaStream_t s,
+                         const unsigned* hull = nullptr, unsigned hull_full = 0);
 // skip_empty: chunks of a grid line whose records are all zero skip their
 // walks; J is then left undefined at their nodes (their source is 0 anyway),
 // so only the reconstruction loop, which reads the source alone, asks for it.

@@ -20,6 +20,11 @@
 #else
 #define FR_MARCH_BOUNDS __launch_bounds__(frk::kTileThreads)
 #endif
+// Resident CTAs per SM asked for the forward march.
+#ifndef FR_FWD_MINB
+#define FR_FWD_MINB 1
+#endif
+#define FR_FWD_BOUNDS __launch_bounds__(frk::kTileThreads, FR_FWD_MINB)
 // Resident CTAs per SM asked for the adjustment over the flame-ray list.
 #ifndef FR_ADJ_MINB
 #define FR_ADJ_MINB 6
@@ -316,7 +321,7 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
 }
 
 template <int DT, int KIND, bool TAU, int MODE>
-__global__ void FR_MARCH_BOUNDS fwd_single(const __grid_constant__ SingleArgs a)
+__global__ void FR_FWD_BOUNDS fwd_single(const __grid_constant__ SingleArgs a)
 {
     fwd_body<DT, KIND, TAU, MODE>(a.p, a.cams, blockIdx.x);
 }

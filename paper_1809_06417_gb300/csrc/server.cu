@@ -400,8 +400,7 @@ extern "C" fr_status fr_server_step(fr_server* s, int* running, int* queued)
         FR_CUDA(c, launch_fwd_batch(dp, dtl, n, tile_off, s->dtype, KIND_RGB, tau, true, st, skip));
         FR_CUDA(c, launch_finalize_batch(dp, n, 0, st));
         FR_CUDA(c, launch_adjust_list_batch(dp, dtl, n, tile_off, s->dtype, tau, 0, st, hull && skip));
-        FR_CUDA(c, launch_apply_batch(dp, n, s->dtype, s->p.clamp_nonneg, st));
-        if (hull) FR_CUDA(c, launch_hull_clear_batch(dp, n, s->dtype, st));
+        FR_CUDA(c, launch_apply_batch(dp, n, s->dtype, s->p.clamp_nonneg, st));   // with the hull clear
         FR_CUDA(c, cudaStreamSynchronize(st));
         // advance and retire
         for (size_t i = 0; i < s->resident.size();) {

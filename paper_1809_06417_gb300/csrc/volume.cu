@@ -14,12 +14,25 @@ namespace frk {
 // Apply the accumulated adjustment
 // ---------------------------------------------------------------------------
 
+// hull (nullable): records of key points whose tag differs from hull_full
+// are set to 0 instead (the hull clear fused into the update).
 template <int DT, int KIND>
 __global__ void __launch_bounds__(256) apply_kernel(void* vol, long long nodes, float* dV, float scale,
-                                                    int with_sigma, int clamp_nonneg, int zero_dV)
+                                                    int with_sigma, int clamp_nonneg, int zero_dV,
+                                                    const unsigned* __restrict__ hull, unsigned hull_full)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
          i += (long long)gridDim.x * blockDim.x) {
+        if (hull && __ldg(hull + i) != hull_full) {
+            if constexpr (KIND == KIND_RGB) {
+                store_rgb<DT>(vol, i, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+                if (zero_dV) reinterpret_cast<float4*>(dV)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            } else {
+                store_ts<DT>(vol, i, make_float2(0.0f, 0.0f));
+                if (zero_dV) reinterpret_cast<float2*>(dV)[i] = make_float2(0.0f, 0.0f);
+            }
+            continue;
+        }
         if constexpr (KIND == KIND_RGB) {
             float4 v = load_rgb<DT>(vol, i);
             float4 d = reinterpret_cast<float4*>(dV)[i];
@@ -56,10 +69,12 @@ static int grid_for(long long n, int block)
 }
 
 cudaError_t launch_apply(void* vol, int dt, int kind, long long nodes, float* dV, float scale,
-                         int with_sigma, int clamp_nonneg, int zero_dV, cudaStream_t s)
+                         int with_sigma, int clamp_nonneg, int zero_dV, cudaStream_t s, const unsigned* hull,
+                         unsigned hull_full)
 {
     int g = grid_for(nodes, 256);
-#define FR_APPLY(D, K) apply_kernel<D, K><<<g, 256, 0, s>>>(vol, nodes, dV, scale, with_sigma, clamp_nonneg, zero_dV)
+#define FR_APPLY(D, K) \
+    apply_kernel<D, K><<<g, 256, 0, s>>>(vol, nodes, dV, scale, with_sigma, clamp_nonneg, zero_dV, hull, hull_full)
     if (kind == KIND_RGB) {
         if (dt == DT_F32) FR_APPLY(DT_F32, KIND_RGB);
         else if (dt == DT_BF16) FR_APPLY(DT_BF16, KIND_RGB);
@@ -83,6 +98,11 @@ __global__ void __launch_bounds__(256) apply_batch_kernel(const ProbDev* __restr
     float4* dV = reinterpret_cast<float4*>(P.dV);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P.nodes;
          i += (long long)gridDim.x * blockDim.x) {
+        if (P.hull && __ldg(P.hull + i) != P.hull_full) {   // outside the problem's hull: held at 0
+            store_rgb<DT>(vol, i, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+            dV[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            continue;
+        }
         float4 v = load_rgb<DT>(vol, i);
         const float4 d = dV[i];
         v.x += d.x; v.y += d.y; v.z += d.z;
@@ -204,26 +224,6 @@ cudaError_t launch_brick_reset_batch(const ProbDev* probs, int nprob, cudaStream
 cudaError_t launch_brick_box_batch(const ProbDev* probs, int nprob, cudaStream_t s)
 {
     brick_box_batch_kernel<<<nprob, 1024, 0, s>>>(probs);
-    return cudaGetLastError();
-}
-
-// Records outside each problem's hull (hull tag != hull_full) set to 0.
-template <int DT>
-__global__ void __launch_bounds__(256) hull_clear_batch_kernel(const ProbDev* __restrict__ probs)
-{
-    const ProbDev& P = probs[blockIdx.y];
-    if (!P.hull) return;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P.nodes;
-         i += (long long)gridDim.x * blockDim.x)
-        if (__ldg(P.hull + i) != P.hull_full) store_rgb<DT>(P.vol_rw, i, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
-}
-
-cudaError_t launch_hull_clear_batch(const ProbDev* probs, int nprob, int dt, cudaStream_t s)
-{
-    const dim3 grid(128, nprob);
-    if (dt == DT_F32) hull_clear_batch_kernel<DT_F32><<<grid, 256, 0, s>>>(probs);
-    else if (dt == DT_BF16) hull_clear_batch_kernel<DT_BF16><<<grid, 256, 0, s>>>(probs);
-    else hull_clear_batch_kernel<DT_F16><<<grid, 256, 0, s>>>(probs);
     return cudaGetLastError();
 }
 
