@@ -131,6 +131,15 @@ void fr_params_default(fr_params *p);
  * (borrowed); NULL means CUDA's default stream, as in the runtime API. */
 fr_status fr_create(fr_ctx **out, int device, void *stream);
 fr_status fr_destroy(fr_ctx *ctx);
+/* Device scratch the context allocates on first use and keeps (residuals,
+ * accumulators, tables): at most `bytes` in all (0: no limit).  A call that
+ * would need more fails with FR_ENOMEM, launches nothing and leaves the
+ * context usable; raising the limit lets the next call proceed.  Scratch
+ * already held is kept. */
+fr_status fr_set_scratch_limit(fr_ctx *ctx, size_t bytes);
+/* Device scratch the context holds now, in bytes (host output). */
+fr_status fr_scratch_bytes(const fr_ctx *ctx, size_t *held);
+
 /* Replace the context's stream (borrowed; NULL = CUDA's default stream). */
 fr_status fr_set_stream(fr_ctx *ctx, void *stream);
 /* Message of the last failure on this context ("" if none). */

@@ -46,6 +46,9 @@ struct fr_ctx {
     size_t staging_bytes = 0;
     cudaEvent_t staging_done = nullptr;
     cudaStream_t capture = nullptr;  // stream used to capture CUDA graphs
+    // device scratch held in Bufs, and the most the context may hold
+    size_t scratch_bytes = 0;
+    size_t scratch_limit = SIZE_MAX;
     // phase tracing: events recorded between the phases of fr_reconstruct
     bool trace_on = false;
     bool trace_overflow = false;
@@ -203,13 +206,17 @@ inline fr_status check_params(fr_ctx* c, const fr_params* p, const fr_volume* v,
 inline fr_status ensure(fr_ctx* c, Buf& b, size_t bytes, const char* name)
 {
     if (b.bytes >= bytes) return FR_OK;
+    size_t want = bytes < 256 ? 256 : bytes;
+    if (c->scratch_bytes - b.bytes + want > c->scratch_limit)
+        return fail(c, FR_ENOMEM, "%s scratch of %zu bytes would exceed the context's limit of %zu bytes", name,
+                    want, c->scratch_limit);
     if (b.p) {
         FR_CUDA(c, cudaStreamSynchronize(c->stream));
         cudaFree(b.p);
+        c->scratch_bytes -= b.bytes;
         b.p = nullptr;
         b.bytes = 0;
     }
-    size_t want = bytes < 256 ? 256 : bytes;
     cudaError_t e = cudaMalloc(&b.p, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -217,6 +224,7 @@ inline fr_status ensure(fr_ctx* c, Buf& b, size_t bytes, const char* name)
         return fail(c, FR_ENOMEM, "cannot allocate %zu bytes of %s scratch", want, name);
     }
     b.bytes = want;
+    c->scratch_bytes += want;
     return FR_OK;
 }
 

@@ -75,6 +75,20 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     return FR_OK;
 }
 
+extern "C" fr_status fr_set_scratch_limit(fr_ctx* c, size_t bytes)
+{
+    if (!c) return FR_EINVAL;
+    c->scratch_limit = bytes ? bytes : SIZE_MAX;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_scratch_bytes(const fr_ctx* c, size_t* held)
+{
+    if (!c || !held) return FR_EINVAL;
+    *held = c->scratch_bytes;
+    return FR_OK;
+}
+
 extern "C" fr_status fr_set_stream(fr_ctx* c, void* stream)
 {
     if (!c) return FR_EINVAL;

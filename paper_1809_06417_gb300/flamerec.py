@@ -117,6 +117,8 @@ SIGNATURES = {
     "fr_camera_from_projection": (_S, [_P, _I, _I, _P]),
     "fr_volume_dims": (_S, [_P, _I, _P, _P, _F, _P, _P, _P]),
     "fr_trace_phases": (_S, [_P, _I]),
+    "fr_set_scratch_limit": (_S, [_P, ctypes.c_size_t]),
+    "fr_scratch_bytes": (_S, [_P, _P]),
     "fr_phase_times": (_S, [_P, _P, _I, _P]),
     "fr_render_residual_noalloc": (_S, [_I, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, ctypes.c_char_p,
                                         ctypes.c_size_t]),
@@ -241,6 +243,38 @@ def volume_dims(cams, box_min, box_max, alpha=1.5):
     return tuple(dims), h.value, tuple(n)
 
 
+def _nvtx(fn):
+    """NVTX range named after the entry point around the call (visible in
+    Nsight timelines), when torch's CUDA NVTX bindings are present."""
+    import functools
+    name = fn.__name__
+
+    @functools.wraps(fn)
+    def wrapper(*a, **k):
+        nv = _nvtx_module()
+        if nv is None:
+            return fn(*a, **k)
+        nv.range_push(name)
+        try:
+            return fn(*a, **k)
+        finally:
+            nv.range_pop()
+    return wrapper
+
+
+_NVTX = []
+
+
+def _nvtx_module():
+    if not _NVTX:
+        try:
+            import torch
+            _NVTX.append(torch.cuda.nvtx if torch.cuda.is_available() else None)
+        except Exception:  # torch absent or without CUDA: no ranges
+            _NVTX.append(None)
+    return _NVTX[0]
+
+
 class Context:
     """An fr_ctx bound to a device and a stream (torch's current one by default)."""
 
@@ -278,14 +312,17 @@ class Context:
         k, h, w, _ = targets.shape
         self.check(self.lib.fr_prepare_targets(self.h, k, h, w, _ptr(targets), float(thresh), _ptr(bbox)))
 
+    @_nvtx
     def fr_render(self, vol: fr_volume, cams, p: fr_params, out):
         self.check(self.lib.fr_render(self.h, ctypes.byref(vol), cams, len(cams), ctypes.byref(p), _ptr(out)))
 
+    @_nvtx
     def fr_render_residual(self, vol, cams, p, targets, bbox, rendered, residual, sq_err):
         self.check(self.lib.fr_render_residual(self.h, ctypes.byref(vol), cams, len(cams), ctypes.byref(p),
                                                _ptr(targets), _ptr(bbox), _ptr(rendered), _ptr(residual),
                                                _ptr(sq_err)))
 
+    @_nvtx
     def fr_adjust(self, vol, cams, p, residual, iteration, dV):
         self.check(self.lib.fr_adjust(self.h, ctypes.byref(vol), cams, len(cams), ctypes.byref(p),
                                       _ptr(residual), int(iteration), _ptr(dV)))
@@ -294,10 +331,12 @@ class Context:
         self.check(self.lib.fr_apply_update(self.h, ctypes.byref(vol), _ptr(dV), float(scale), int(with_sigma),
                                             int(clamp_nonneg), int(zero_dV)))
 
+    @_nvtx
     def fr_render_backward(self, vol, cams, p, L_total, grad_img, grad):
         self.check(self.lib.fr_render_backward(self.h, ctypes.byref(vol), cams, len(cams), ctypes.byref(p),
                                                _ptr(L_total), _ptr(grad_img), _ptr(grad)))
 
+    @_nvtx
     def fr_scatter_source(self, emission, albedo, J, out):
         self.check(self.lib.fr_scatter_source(self.h, ctypes.byref(emission), _ptr(albedo), _ptr(J),
                                               ctypes.byref(out)))
@@ -305,6 +344,7 @@ class Context:
     def fr_planck_lut(self, t_min, t_max, lut):
         self.check(self.lib.fr_planck_lut(self.h, float(t_min), float(t_max), int(lut.shape[0]), _ptr(lut)))
 
+    @_nvtx
     def fr_reconstruct(self, vol, cams, targets, bbox, iters, p, albedo=None, first_iteration=0,
                        rmse=None, targets_are_host=None):
         if targets_are_host is None:
@@ -315,6 +355,7 @@ class Context:
                                            int(first_iteration), ctypes.byref(p), _ptr(rmse),
                                            int(rmse_is_host)))
 
+    @_nvtx
     def fr_reconstruct_until(self, vol, cams, targets, bbox, max_iters, stop_delta, p, albedo=None,
                              first_iteration=0, rmse=None, targets_are_host=None):
         """Iterates until the image error changes by less than stop_delta; returns the iterations run."""
@@ -341,6 +382,14 @@ class Context:
                                            out, ctypes.byref(n)))
         return np.array(list(out), dtype=np.float64), n.value
 
+    def fr_set_scratch_limit(self, nbytes):
+        self.check(self.lib.fr_set_scratch_limit(self.h, int(nbytes)))
+
+    def fr_scratch_bytes(self):
+        n = ctypes.c_size_t()
+        self.check(self.lib.fr_scratch_bytes(self.h, ctypes.byref(n)))
+        return n.value
+
     def fr_trace_phases(self, on=True):
         self.check(self.lib.fr_trace_phases(self.h, int(bool(on))))
 
@@ -357,6 +406,7 @@ class Context:
                                              _ptr(residual), ctypes.byref(n)))
         return n.value
 
+    @_nvtx
     def fr_reconstruct_batch(self, problems, iters, p, first_iteration=0, use_graph=True):
         """problems: sequence of (fr_volume, camera array, targets, bbox, rmse or None)."""
         arr = (fr_problem * len(problems))()
@@ -370,6 +420,7 @@ class Context:
         self.check(self.lib.fr_reconstruct_batch(self.h, arr, len(problems), int(iters), int(first_iteration),
                                                  ctypes.byref(p), int(bool(use_graph))))
 
+    @_nvtx
     def fr_visual_hull(self, vol, cams, targets, p, tags):
         self.check(self.lib.fr_visual_hull(self.h, ctypes.byref(vol), cams, len(cams), _ptr(targets),
                                            ctypes.byref(p), _ptr(tags)))
@@ -436,6 +487,7 @@ class Server:
         self.ctx.check(self.lib.fr_server_submit(self.h, ctypes.byref(d), ctypes.byref(jh)))
         return Job(self, jh, (init, tgt, fcams), result, rmse)
 
+    @_nvtx
     def step(self):
         running, queued = ctypes.c_int(), ctypes.c_int()
         self.ctx.check(self.lib.fr_server_step(self.h, ctypes.byref(running), ctypes.byref(queued)))
