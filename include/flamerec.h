@@ -131,6 +131,17 @@ void fr_params_default(fr_params *p);
  * (borrowed); NULL means CUDA's default stream, as in the runtime API. */
 fr_status fr_create(fr_ctx **out, int device, void *stream);
 fr_status fr_destroy(fr_ctx *ctx);
+/* Bounds checks.  A library built with -DFR_CHECKED (build.py --checked)
+ * checks the indices its kernels compute before every access (record
+ * gathers, update reductions, pixels, flame-ray list entries, bricks, nodes
+ * of the volume passes); an index out of range sets a bit in a device check
+ * word (1 gather, 2 reduction, 4 pixel, 8 list entry, 16 brick, 32 volume
+ * node) and is replaced by 0, never trapping.  fr_checks_enabled() tells the
+ * build; fr_check_word synchronises the context's stream and returns the
+ * word (0 in the normal build), clearing it when reset != 0. */
+int32_t fr_checks_enabled(void);
+fr_status fr_check_word(fr_ctx *ctx, uint32_t *word, int reset);
+
 /* Device scratch the context allocates on first use and keeps (residuals,
  * accumulators, tables): at most `bytes` in all (0: no limit).  A call that
  * would need more fails with FR_ENOMEM, launches nothing and leaves the

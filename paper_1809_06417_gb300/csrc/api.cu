@@ -75,6 +75,27 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     return FR_OK;
 }
 
+extern "C" int32_t fr_checks_enabled(void)
+{
+#ifdef FR_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+extern "C" fr_status fr_check_word(fr_ctx* c, uint32_t* word, int reset)
+{
+    FR_BEGIN(c);
+    if (!word) return fail(c, FR_EINVAL, "word is NULL");
+    FR_CUDA(c, cudaStreamSynchronize(c->stream));
+    unsigned a = 0, b = 0;
+    FR_CUDA(c, check_word_march(&a, reset != 0));
+    FR_CUDA(c, check_word_volume(&b, reset != 0));
+    *word = a | b;
+    return FR_OK;
+}
+
 extern "C" fr_status fr_set_scratch_limit(fr_ctx* c, size_t bytes)
 {
     if (!c) return FR_EINVAL;

@@ -95,6 +95,26 @@ struct ProbDev {
 
 constexpr int kBrick = 8;        // cells per brick edge
 
+// Bounds checks of the checked build (-DFR_CHECKED): an index outside [0, n)
+// is recorded in the translation unit's check word (bit `code`) and replaced
+// by 0, so the access stays inside its buffer; the normal build compiles the
+// checks away.  Codes: 1 record gather, 2 update reduction, 4 pixel,
+// 8 flame-ray list entry, 16 brick, 32 node of a volume pass.
+#ifdef FR_CHECKED
+static __device__ unsigned g_fr_check_word;
+__device__ __forceinline__ long long fr_checked(long long i, long long n, unsigned code)
+{
+    if (i < 0 || i >= n) {
+        atomicOr(&g_fr_check_word, code);
+        return 0;
+    }
+    return i;
+}
+#define FR_CHK(i, n, code) fr_checked((long long)(i), (long long)(n), (code))
+#else
+#define FR_CHK(i, n, code) (i)
+#endif
+
 // ---------------------------------------------------------------------------
 // Rays
 // ---------------------------------------------------------------------------

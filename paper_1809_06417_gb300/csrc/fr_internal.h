@@ -73,6 +73,9 @@ cudaError_t launch_green_to_temp(const void* rgb, int dt_rgb, void* temp, int dt
 int volume_err_blocks(long long nodes);
 cudaError_t launch_volume_err(const void* a, int dta, const void* b, int dtb, long long nodes, const unsigned* tags,
                               unsigned full, void* partials, float* out, cudaStream_t s);
+// bounds-check words of the checked build (0 otherwise), per translation unit
+cudaError_t check_word_march(unsigned* word, bool reset);
+cudaError_t check_word_volume(unsigned* word, bool reset);
 // end of an iteration of a loop counted on the device (conditional graph body);
 // clears flame_count[0 .. n_counts)
 cudaError_t launch_converge(const float* sq4, float* hist3, int* iter, unsigned* flame_count, int n_counts,

@@ -189,7 +189,7 @@ struct BrickSkip {
         const int b = ((c.k >> 3) * P.nby + (c.j >> 3)) * P.nbx + (c.i >> 3);
         if (b != brick) {
             brick = b;
-            occupied = __ldg(flags + b) != 0;
+            occupied = __ldg(flags + FR_CHK(b, (long long)P.nbx * P.nby * P.nbz, 16u)) != 0;
         }
         if (occupied) return false;
         const int bx = c.i & ~(kBrick - 1), by = c.j & ~(kBrick - 1), bz = c.k & ~(kBrick - 1);
@@ -238,8 +238,10 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
                 const Cell c = cell_of(x, y, z, P.nx, P.ny, P.nz);
                 if (c.base != vbase) {
                     vbase = c.base;
-                    if constexpr (PAIRS) load8_pairs<DT, KIND>(P.pairs, c.base, P.nx, nxy, v);
-                    else load8<DT, KIND>(P.vol, c.base, P.nx, nxy, v);
+                    // the cell's far corner, base + nxy + nx + 1, must be a node
+                    const long long b = FR_CHK(c.base, nxy * P.nz - nxy - P.nx - 1, 1u);
+                    if constexpr (PAIRS) load8_pairs<DT, KIND>(P.pairs, b, P.nx, nxy, v);
+                    else load8<DT, KIND>(P.vol, b, P.nx, nxy, v);
                 }
                 const RT r = slot_blend<RT>(v, c.fx, c.fy, c.fz);
                 float S[3], sig, dq[3];
@@ -260,7 +262,8 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
     }
     // pixel epilogue: image, residual of the colour constraint, error sums
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, cnt = 0.0f;
-    const long long pix = ((long long)view * P.H + py) * P.W + px;
+    const long long pix = valid ? FR_CHK(((long long)view * P.H + py) * P.W + px, (long long)P.ncam * P.H * P.W, 4u)
+                                : 0;
     bool flame = false;
     if (valid) {
         if (P.rendered) {
@@ -366,13 +369,15 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
     for (int t = 0; t < 8; ++t) { acc[t] = 0.0f; sg[t] = 0.0f; }
     float* dV = P.dV;
     const void* vol = P.vol;
-    auto leave = [&acc, dV, dl0, dl1, dl2](int t, int node) {
+    const long long nodes = nxy * P.nz;
+    (void)nodes;
+    auto leave = [&acc, dV, dl0, dl1, dl2, nodes](int t, int node) {
         const float w = acc[t];
-        if (w != 0.0f) red_add_v4(dV + 4 * (unsigned)node, w * dl0, w * dl1, w * dl2, 0.0f);
+        if (w != 0.0f) red_add_v4(dV + 4 * (unsigned)FR_CHK(node, nodes, 2u), w * dl0, w * dl1, w * dl2, 0.0f);
         acc[t] = 0.0f;
     };
-    auto enter = [&sg, vol](int t, int node) {
-        if constexpr (!TAU) sg[t] = load_rgb_sigma<DT>(vol, (unsigned)node);
+    auto enter = [&sg, vol, nodes](int t, int node) {
+        if constexpr (!TAU) sg[t] = load_rgb_sigma<DT>(vol, (unsigned)FR_CHK(node, nodes, 1u));
     };
     Win W;
     W.live = false;
@@ -426,7 +431,7 @@ __global__ void FR_ADJ_LIST_BOUNDS adj_list(const __grid_constant__ SingleArgs a
     const unsigned i = blockIdx.x * (unsigned)kTileThreads + threadIdx.x;
     if (i >= __ldg(count)) return;
     const ProbDev& P = a.p;
-    const unsigned pix = __ldg(list + i);
+    const unsigned pix = (unsigned)FR_CHK(__ldg(list + i), (long long)P.ncam * P.W * P.H, 8u);
     const unsigned per_view = (unsigned)P.W * (unsigned)P.H;
     const int view = (int)(pix / per_view);
     const unsigned r = pix - (unsigned)view * per_view;
@@ -496,13 +501,16 @@ __device__ __forceinline__ void bwd_body(const ProbDev& P, const CamDev* cams, i
         for (int q = 0; q < NA; ++q) acc[t][q] = 0.0f;
     float* dV = P.dV;
     const void* vol = P.vol;
-    auto leave = [&acc, dV](int t, int node) {
+    const long long nodes = nxy * P.nz;
+    (void)nodes;
+    auto leave = [&acc, dV, nodes](int t, int node) {
         bool any = false;
 #pragma unroll
         for (int q = 0; q < NA; ++q) any = any || acc[t][q] != 0.0f;
         if (any) {
-            if constexpr (KIND == KIND_RGB) red_add_v4(dV + 4 * (unsigned)node, acc[t][0], acc[t][1], acc[t][2], acc[t][3]);
-            else red_add_v2(dV + 2 * (unsigned)node, acc[t][0], acc[t][1]);
+            const unsigned nd = (unsigned)FR_CHK(node, nodes, 2u);
+            if constexpr (KIND == KIND_RGB) red_add_v4(dV + 4 * nd, acc[t][0], acc[t][1], acc[t][2], acc[t][3]);
+            else red_add_v2(dV + 2 * nd, acc[t][0], acc[t][1]);
         }
 #pragma unroll
         for (int q = 0; q < NA; ++q) acc[t][q] = 0.0f;
@@ -517,7 +525,7 @@ __device__ __forceinline__ void bwd_body(const ProbDev& P, const CamDev* cams, i
         win_move(W, ci.i, ci.j, ci.k, P.nx, P.ny, (int)nxy, leave, [](int, int) {});
         if (W.base != vbase) {
             vbase = W.base;
-            load8<DT, KIND>(vol, (long long)W.base, P.nx, nxy, v);
+            load8<DT, KIND>(vol, FR_CHK((long long)W.base, nxy * P.nz - nxy - P.nx - 1, 1u), P.nx, nxy, v);
         }
         const RT r = slot_blend<RT>(v, ci.fx, ci.fy, ci.fz);
         const float gx = mirror_frac(ci.i, ci.fx), gy = mirror_frac(ci.j, ci.fy), gz = mirror_frac(ci.k, ci.fz);
@@ -903,6 +911,23 @@ cudaError_t launch_adjust_list(const SingleArgs& a, int dt, int ntiles, const un
         else adj_list<D, false, false><<<grid, block, 0, s>>>(a, list, count);
     });
     return cudaGetLastError();
+}
+
+// The check word of this translation unit (0 in the normal build).
+cudaError_t check_word_march(unsigned* word, bool reset)
+{
+#ifdef FR_CHECKED
+    cudaError_t e = cudaMemcpyFromSymbol(word, g_fr_check_word, sizeof(unsigned));
+    if (e == cudaSuccess && reset) {
+        const unsigned zero = 0;
+        e = cudaMemcpyToSymbol(g_fr_check_word, &zero, sizeof(unsigned));
+    }
+    return e;
+#else
+    (void)reset;
+    *word = 0;
+    return cudaSuccess;
+#endif
 }
 
 }  // namespace frk

@@ -151,7 +151,8 @@ __device__ __forceinline__ void mark_bricks(unsigned char* occ, int x, int y, in
     const int bz0 = (z > 0 && (z & 7) == 0) ? (z >> 3) - 1 : (z >> 3);
     for (int bz = bz0; bz <= min(z >> 3, nbz - 1); ++bz)
         for (int by = by0; by <= min(y >> 3, nby - 1); ++by)
-            for (int bx = bx0; bx <= min(x >> 3, nbx - 1); ++bx) occ[((long long)bz * nby + by) * nbx + bx] = 1;
+            for (int bx = bx0; bx <= min(x >> 3, nbx - 1); ++bx)
+                occ[FR_CHK(((long long)bz * nby + by) * nbx + bx, (long long)nbx * nby * nbz, 16u)] = 1;
 }
 
 // The box of the flagged bricks of a brick table (one CTA).
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const
         // it is carried by the chunk maps.  Only the stores the next steps
         // read are made: zero directional radiances, or the zero source.
         for (int i = s0; i < s1; ++i) {
-            const long long node = start + i * stride;
+            const long long node = FR_CHK(start + i * stride, (long long)nx * ny * nz, 32u);
             if (L6) {
                 L6[6 * node + 2 * AXIS] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 L6[6 * node + 2 * AXIS + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -473,7 +474,7 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const
     {
         float4 prev = load_rgb<DT>(em, start + max(s0 - 1, 0) * stride);
         for (int i = s0; i < s1; ++i) {
-            const long long node = start + i * stride;
+            const long long node = FR_CHK(start + i * stride, (long long)nx * ny * nz, 32u);
             const float4 cur = load_rgb<DT>(em, node);
             if (i > 0) {
                 const Seg g = seg_between<DT>(prev, cur);
@@ -498,7 +499,7 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const
     {
         float4 next = load_rgb<DT>(em, start + min(s1, n_line - 1) * stride);
         for (int i = s1 - 1; i >= s0; --i) {
-            const long long node = start + i * stride;
+            const long long node = FR_CHK(start + i * stride, (long long)nx * ny * nz, 32u);
             const float4 cur = load_rgb<DT>(em, node);
             if (i < n_line - 1) {
                 const Seg g = seg_between<DT>(cur, next);
@@ -1166,6 +1167,22 @@ cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t s)
 {
     fill_kernel<<<grid_for(n, 256), 256, 0, s>>>(p, n, v);
     return cudaGetLastError();
+}
+
+cudaError_t check_word_volume(unsigned* word, bool reset)
+{
+#ifdef FR_CHECKED
+    cudaError_t e = cudaMemcpyFromSymbol(word, g_fr_check_word, sizeof(unsigned));
+    if (e == cudaSuccess && reset) {
+        const unsigned zero = 0;
+        e = cudaMemcpyToSymbol(g_fr_check_word, &zero, sizeof(unsigned));
+    }
+    return e;
+#else
+    (void)reset;
+    *word = 0;
+    return cudaSuccess;
+#endif
 }
 
 }  // namespace frk

@@ -117,6 +117,8 @@ SIGNATURES = {
     "fr_camera_from_projection": (_S, [_P, _I, _I, _P]),
     "fr_volume_dims": (_S, [_P, _I, _P, _P, _F, _P, _P, _P]),
     "fr_trace_phases": (_S, [_P, _I]),
+    "fr_checks_enabled": (ctypes.c_int32, []),
+    "fr_check_word": (_S, [_P, _P, _I]),
     "fr_set_scratch_limit": (_S, [_P, ctypes.c_size_t]),
     "fr_scratch_bytes": (_S, [_P, _P]),
     "fr_phase_times": (_S, [_P, _P, _I, _P]),
@@ -128,12 +130,13 @@ _lib = None
 
 
 def load():
-    """Load the library (building it first if its sources are newer)."""
+    """Load the library (building it first if its sources are newer).  With
+    FR_LIBRARY_VARIANT=checked in the environment, the bounds-checked build."""
     global _lib
     if _lib is not None:
         return _lib
     from . import build as _build
-    path = _build.build()
+    path = _build.build(checked=os.environ.get("FR_LIBRARY_VARIANT") == "checked")
     if not os.path.exists(path):
         raise FrError(FR_ECUDA, f"libflamerec.so missing at {path}")
     lib = ctypes.CDLL(path)
@@ -381,6 +384,11 @@ class Context:
         self.check(self.lib.fr_volume_rmse(self.h, ctypes.byref(a), ctypes.byref(b), _ptr(tags), int(full_mask),
                                            out, ctypes.byref(n)))
         return np.array(list(out), dtype=np.float64), n.value
+
+    def fr_check_word(self, reset=False):
+        w = ctypes.c_uint32()
+        self.check(self.lib.fr_check_word(self.h, ctypes.byref(w), int(bool(reset))))
+        return w.value
 
     def fr_set_scratch_limit(self, nbytes):
         self.check(self.lib.fr_set_scratch_limit(self.h, int(nbytes)))

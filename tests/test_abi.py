@@ -51,3 +51,14 @@ def test_create_fails_cleanly_without_gpu():
     h = ctypes.c_void_p()
     assert lib.fr_create(ctypes.byref(h), 0, None) == flamerec.FR_ECUDA
     assert not h.value
+
+
+def test_host_only_entry_points_without_a_gpu():
+    """The normal build has its bounds checks compiled out; the host-arithmetic
+    entry points answer without a device."""
+    from paper_1809_06417_gb300 import flamerec
+    lib = flamerec.load()
+    assert lib.fr_checks_enabled() == 0
+    P = (ctypes.c_double * 12)(*([0.0] * 12))
+    cam = flamerec.fr_camera()
+    assert lib.fr_camera_from_projection(P, 8, 8, ctypes.byref(cam)) == flamerec.FR_EINVAL
