@@ -160,7 +160,7 @@ static void locate(const orc_grid *g, const double p[3], int c[3], double f[3])
     }
 }
 
-/* The eight key points around a sample (Sec. 3.3 "sample points"): node
+/* The eight key points around a sample (Sec. 3.3, sample points): node
  * indices and trilinear weights, corner b = dx + 2 dy + 4 dz. */
 static void corners(const orc_grid *g, const int c[3], const double f[3],
                     int64_t idx[8], double w[8])
@@ -851,9 +851,9 @@ static void view_direction(const orc_grid *g, const orc_cam *c, double omega[3])
 /* Visual hull (Sec. 4.3.1, Algorithm 1)                                     */
 /* ------------------------------------------------------------------------ */
 
-/* Algorithm 1 tags the key points "around" every flame ray of view v with bit
+/* Algorithm 1 tags the key points near every flame ray of view v with bit
  * v; a key point is inside the hull when all K bits are set.  Reading: key
- * point j is around a flame ray of view v when the centre of a flame pixel
+ * point j is near a flame ray of view v when the centre of a flame pixel
  * lies in the image rectangle that bounds the projection of the box of the
  * eight cells sharing j ([j-1, j+1] per axis, clipped to the volume) -- every
  * ray that can sample one of those cells passes through that rectangle, so
@@ -1056,7 +1056,7 @@ void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
     double *src = albedo ? malloc(sizeof(double) * 4 * (size_t)nodes) : NULL;
     /* key points outside the visual hull are not reconstructed: they hold no
      * flame, so their whole record (emission and extinction) is 0 and stays 0
-     * (Sec. 4.3.1 marks them with a non-flame value, a small negative number;
+     * (Sec. 4.3.1 marks them with a non-flame value, slightly below zero;
      * 0 here, which leaves the rays through them unchanged) */
     const uint32_t full = ncam >= 32 ? 0xffffffffu : ((1u << ncam) - 1u);
     if (hull)
