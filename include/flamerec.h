@@ -105,7 +105,7 @@ typedef struct fr_params {
     const float *lut;    /* device, lut_size x 4 {r,g,b,0}, from fr_planck_lut (TEMP only) */
     int32_t lut_size;
     int32_t use_hull;    /* fr_reconstruct: hold records outside the visual hull at 0 (Sec. 4.3.1) */
-    int32_t skip_empty;  /* forward march of RGB records without tau: skip 8^3-cell bricks whose
+    int32_t skip_empty;  /* forward march of RGB records without tau: skip bricks (fr_brick_cells()^3 cells) whose
                             records are all zero (exact: the result is bitwise the same); with
                             use_hull, the paper-rule adjustment also skips bricks with no key point
                             inside the hull (exact up to the order of its atomic sums) */
@@ -140,6 +140,8 @@ fr_status fr_destroy(fr_ctx *ctx);
  * build; fr_check_word synchronises the context's stream and returns the
  * word (0 in the normal build), clearing it when reset != 0. */
 int32_t fr_checks_enabled(void);
+/* Edge of the bricks the marches skip, in cells (the skipping granularity). */
+int32_t fr_brick_cells(void);
 fr_status fr_check_word(fr_ctx *ctx, uint32_t *word, int reset);
 
 /* Device scratch the context allocates on first use and keeps (residuals,

@@ -84,6 +84,8 @@ extern "C" int32_t fr_checks_enabled(void)
 #endif
 }
 
+extern "C" int32_t fr_brick_cells(void) { return kBrick; }
+
 extern "C" fr_status fr_check_word(fr_ctx* c, uint32_t* word, int reset)
 {
     FR_BEGIN(c);

@@ -99,7 +99,7 @@ cudaError_t launch_visual_hull(const CamDev* cams, int ncam, int W, int H, int n
 // flags, the brick table of the key points inside the hull
 cudaError_t launch_hull_clear(void* vol, int dt, int nx, int ny, int nz, const unsigned* tags, unsigned full,
                               unsigned char* flags, cudaStream_t s);
-// Brick tables: one flag per brick of 8^3 cells (x fastest), then, at the
+// Brick tables: one flag per brick of kBrick^3 cells (x fastest), then, at the
 // next 16-byte boundary, the box of the flagged bricks as six unsigned
 // values {nbx - lo_x, nby - lo_y, nbz - lo_z, hi_x + 1, hi_y + 1, hi_z + 1}
 // (all 0 when no brick is flagged).

@@ -137,8 +137,8 @@ __device__ __forceinline__ void load8_pairs(const void* pairs, long long base, i
 // and are reloaded only when the sample enters another cell.  (Reloading just
 // the four records of a crossed face costs more instructions than the L1
 // traffic it saves.)
-// Skipping of flagged-off bricks along one ray.  A brick is the box of 8^3
-// cells [8b, min(8b + 8, n - 1)] per axis; `flags` holds one byte per brick
+// Skipping of flagged-off bricks along one ray.  A brick is the box of kBrick^3
+// cells [B b, min(B b + B, n - 1)] per axis (B = kBrick); `flags` holds one byte per brick
 // (non-zero: the samples in it are evaluated).
 struct BrickSkip {
     int brick = -1;
@@ -186,7 +186,7 @@ struct BrickSkip {
                                           float x, float y, float z, int& k)
     {
         const CellIJK c = cell_ijk(x, y, z, P.nx, P.ny, P.nz);
-        const int b = ((c.k >> 3) * P.nby + (c.j >> 3)) * P.nbx + (c.i >> 3);
+        const int b = ((c.k >> kBrickShift) * P.nby + (c.j >> kBrickShift)) * P.nbx + (c.i >> kBrickShift);
         if (b != brick) {
             brick = b;
             occupied = __ldg(flags + FR_CHK(b, (long long)P.nbx * P.nby * P.nbz, 16u)) != 0;

@@ -141,27 +141,32 @@ cudaError_t launch_rmse_batch(const ProbDev* probs, int nprob, int iters, float*
 
 // x-pair records: pair i = {record i, record i + 1}, the second copy of the
 // last node of a row repeating it (no cell uses it).  One CTA per row.
-// Marks, for a non-zero record at node (x, y, z), every brick of 8^3 cells
+// Marks, for a non-zero record at node (x, y, z), every brick of kBrick^3 cells
 // whose corner records include it (a node on a brick boundary belongs to the
 // bricks on both sides).  Stores only ones; the flags are cleared beforehand.
 __device__ __forceinline__ void mark_bricks(unsigned char* occ, int x, int y, int z, int nbx, int nby, int nbz)
 {
-    const int bx0 = (x > 0 && (x & 7) == 0) ? (x >> 3) - 1 : (x >> 3);
-    const int by0 = (y > 0 && (y & 7) == 0) ? (y >> 3) - 1 : (y >> 3);
-    const int bz0 = (z > 0 && (z & 7) == 0) ? (z >> 3) - 1 : (z >> 3);
-    for (int bz = bz0; bz <= min(z >> 3, nbz - 1); ++bz)
-        for (int by = by0; by <= min(y >> 3, nby - 1); ++by)
-            for (int bx = bx0; bx <= min(x >> 3, nbx - 1); ++bx)
+    constexpr int S = kBrickShift, M = kBrick - 1;
+    const int bx0 = (x > 0 && (x & M) == 0) ? (x >> S) - 1 : (x >> S);
+    const int by0 = (y > 0 && (y & M) == 0) ? (y >> S) - 1 : (y >> S);
+    const int bz0 = (z > 0 && (z & M) == 0) ? (z >> S) - 1 : (z >> S);
+    for (int bz = bz0; bz <= min(z >> S, nbz - 1); ++bz)
+        for (int by = by0; by <= min(y >> S, nby - 1); ++by)
+            for (int bx = bx0; bx <= min(x >> S, nbx - 1); ++bx)
                 occ[FR_CHK(((long long)bz * nby + by) * nbx + bx, (long long)nbx * nby * nbz, 16u)] = 1;
 }
 
-// The box of the flagged bricks of a brick table (one CTA).
-__device__ __forceinline__ void brick_box_cta(unsigned char* table, int nbx, int nby, int nbz)
+// The box of the flagged bricks of a brick table: CTA `part` of `nparts`
+// scans its share of the flags and merges its box into the table's with
+// atomicMax on the encoded values {nb - lo, hi + 1} (the table, box included,
+// is zeroed beforehand).
+__device__ __forceinline__ void brick_box_part(unsigned char* table, int nbx, int nby, int nbz, int part,
+                                               int nparts)
 {
     __shared__ unsigned red[6][32];
     const int nb = nbx * nby * nbz;
     unsigned lo[3] = {UINT_MAX, UINT_MAX, UINT_MAX}, hi[3] = {0u, 0u, 0u};
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    for (int b = part * blockDim.x + threadIdx.x; b < nb; b += nparts * blockDim.x) {
         if (!table[b]) continue;
         const unsigned c[3] = {(unsigned)(b % nbx), (unsigned)((b / nbx) % nby), (unsigned)(b / (nbx * nby))};
 #pragma unroll
@@ -185,17 +190,19 @@ __device__ __forceinline__ void brick_box_cta(unsigned char* table, int nbx, int
         for (int a = 0; a < 3; ++a) {
             const unsigned l = __reduce_min_sync(0xffffffffu, lane < nw ? red[a][lane] : UINT_MAX);
             const unsigned h = __reduce_max_sync(0xffffffffu, lane < nw ? red[3 + a][lane] : 0u);
-            if (lane == 0) {
-                box[a] = h ? (unsigned)nbs[a] - l : 0u;
-                box[3 + a] = h;
+            if (lane == 0 && h) {
+                atomicMax(box + a, (unsigned)nbs[a] - l);
+                atomicMax(box + 3 + a, h);
             }
         }
     }
 }
 
-__global__ void __launch_bounds__(1024) brick_box_kernel(unsigned char* table, int nbx, int nby, int nbz)
+constexpr int kBoxParts = 16;   // CTAs per brick table
+
+__global__ void __launch_bounds__(256) brick_box_kernel(unsigned char* table, int nbx, int nby, int nbz)
 {
-    brick_box_cta(table, nbx, nby, nbz);
+    brick_box_part(table, nbx, nby, nbz, blockIdx.x, gridDim.x);
 }
 
 // Batched forms, one problem per blockIdx.y (reset, box) or per CTA (box).
@@ -209,11 +216,11 @@ __global__ void __launch_bounds__(256) brick_reset_batch_kernel(const ProbDev* _
         t[i] = 0;
 }
 
-__global__ void __launch_bounds__(1024) brick_box_batch_kernel(const ProbDev* __restrict__ probs)
+__global__ void __launch_bounds__(256) brick_box_batch_kernel(const ProbDev* __restrict__ probs)
 {
-    const ProbDev& P = probs[blockIdx.x];
+    const ProbDev& P = probs[blockIdx.y];
     if (!P.occ) return;
-    brick_box_cta(const_cast<unsigned char*>(P.occ), P.nbx, P.nby, P.nbz);
+    brick_box_part(const_cast<unsigned char*>(P.occ), P.nbx, P.nby, P.nbz, blockIdx.x, gridDim.x);
 }
 
 cudaError_t launch_brick_reset_batch(const ProbDev* probs, int nprob, cudaStream_t s)
@@ -224,13 +231,13 @@ cudaError_t launch_brick_reset_batch(const ProbDev* probs, int nprob, cudaStream
 
 cudaError_t launch_brick_box_batch(const ProbDev* probs, int nprob, cudaStream_t s)
 {
-    brick_box_batch_kernel<<<nprob, 1024, 0, s>>>(probs);
+    brick_box_batch_kernel<<<dim3(kBoxParts, nprob), 256, 0, s>>>(probs);
     return cudaGetLastError();
 }
 
 static cudaError_t launch_brick_box(unsigned char* table, int nx, int ny, int nz, cudaStream_t s)
 {
-    brick_box_kernel<<<1, 1024, 0, s>>>(table, bricks_along(nx), bricks_along(ny), bricks_along(nz));
+    brick_box_kernel<<<kBoxParts, 256, 0, s>>>(table, bricks_along(nx), bricks_along(ny), bricks_along(nz));
     return cudaGetLastError();
 }
 
@@ -918,7 +925,7 @@ cudaError_t launch_visual_hull(const CamDev* cams, int ncam, int W, int H, int n
 
 // Records outside the hull (tag != full) are set to 0: no emission, no
 // extinction (vol null: nothing is cleared).  With `flags`, also marks the
-// bricks of 8^3 cells that hold a key point inside the hull (the flags are
+// bricks of kBrick^3 cells that hold a key point inside the hull (the flags are
 // cleared beforehand).
 template <int DT>
 __global__ void __launch_bounds__(256) hull_clear_kernel(void* vol, int nx, int ny, int nz,

@@ -118,6 +118,7 @@ SIGNATURES = {
     "fr_volume_dims": (_S, [_P, _I, _P, _P, _F, _P, _P, _P]),
     "fr_trace_phases": (_S, [_P, _I]),
     "fr_checks_enabled": (ctypes.c_int32, []),
+    "fr_brick_cells": (ctypes.c_int32, []),
     "fr_check_word": (_S, [_P, _P, _I]),
     "fr_set_scratch_limit": (_S, [_P, ctypes.c_size_t]),
     "fr_scratch_bytes": (_S, [_P, _P]),

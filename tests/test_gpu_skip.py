@@ -2,7 +2,7 @@
 with and without it are bitwise identical -- a sample whose eight corner
 records are all zero adds exactly nothing and leaves the transmittance
 unchanged -- and the samples it evaluates are those whose cell lies in a brick
-of 8^3 cells holding a non-zero record (counted on the host in float64)."""
+(of fr_brick_cells()^3 cells) holding a non-zero record (counted on the host in float64)."""
 import numpy as np
 import pytest
 
@@ -24,11 +24,11 @@ def fr_ctx():
     ctx.close()
 
 
-def _host_count(vol, cams, origin, h, step):
-    """Samples of all pixel rays whose cell is in an occupied brick."""
+def _host_count(vol, cams, origin, h, step, B):
+    """Samples of all pixel rays whose cell is in an occupied brick of B^3 cells."""
     nz, ny, nx = vol.shape[:3]
     occ_node = np.any(vol != 0, axis=-1)
-    nb = [(n - 2) // 8 + 1 for n in (nx, ny, nz)]
+    nb = [(n - 2) // B + 1 for n in (nx, ny, nz)]
     occ = np.zeros((nb[2], nb[1], nb[0]), dtype=bool)
     k, j, i = np.nonzero(occ_node)
     for dk in (-1, 0):
@@ -36,7 +36,7 @@ def _host_count(vol, cams, origin, h, step):
             for di in (-1, 0):
                 ci, cj, ck = i + di, j + dj, k + dk
                 ok = (ci >= 0) & (ci <= nx - 2) & (cj >= 0) & (cj <= ny - 2) & (ck >= 0) & (ck <= nz - 2)
-                occ[ck[ok] // 8, cj[ok] // 8, ci[ok] // 8] = True
+                occ[ck[ok] // B, cj[ok] // B, ci[ok] // B] = True
     total = evaluated = 0
     hi = np.array([nx - 1, ny - 1, nz - 1], dtype=np.float64)
     for cam in cams:
@@ -66,7 +66,7 @@ def _host_count(vol, cams, origin, h, step):
             tm = 0.5 * (ta + tb)
             p = p0[live] + tm[:, None] * dd[live]
             c = np.clip(np.floor(p), 0, hi - 1).astype(np.int64)
-            evaluated += int(occ[c[:, 2] // 8, c[:, 1] // 8, c[:, 0] // 8].sum())
+            evaluated += int(occ[c[:, 2] // B, c[:, 1] // B, c[:, 0] // B].sum())
     return total, evaluated
 
 
@@ -107,7 +107,7 @@ def test_skip_is_bitwise_exact_and_counts_occupied_samples(fr_ctx, n, views, sid
     s_all = ctx.fr_count_samples(fv, cams, fr.params(step=case.step, skip_empty=0))
     s_eval = ctx.fr_count_samples(fv, cams, fr.params(step=case.step, skip_empty=1))
     stored = vt.float().cpu().numpy()
-    h_all, h_eval = _host_count(stored, case.cams, case.origin, case.h, case.step)
+    h_all, h_eval = _host_count(stored, case.cams, case.origin, case.h, case.step, fr.load().fr_brick_cells())
     print(f"n={n}: samples {s_all}, evaluated {s_eval} ({s_eval / s_all:.3f}); host {h_all}, {h_eval}")
     assert s_eval < s_all
     assert abs(s_all - h_all) <= 1e-4 * h_all
