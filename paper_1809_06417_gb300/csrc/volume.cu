@@ -367,7 +367,12 @@ cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int n
 // kSweepChunks chunks (threadIdx.y).  The x sweep initialises J, the z sweep
 // (LAST) finishes it and writes the source records S = q + albedo sigma J.
 constexpr int kSweepLines = 32;
-constexpr int kSweepChunks = 8;
+// 16 chunks per line (8 nodes each at 128^3): twice the threads of 8 chunks
+// and half the serial walk, measured 10% faster; 32 chunks gained nothing more.
+#ifndef FR_SWEEP_CHUNKS
+#define FR_SWEEP_CHUNKS 16
+#endif
+constexpr int kSweepChunks = FR_SWEEP_CHUNKS;
 
 struct Seg {
     float e, c0, c1, c2;
