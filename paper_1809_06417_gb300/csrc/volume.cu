@@ -241,40 +241,42 @@ static cudaError_t launch_brick_box(unsigned char* table, int nx, int ny, int nz
     return cudaGetLastError();
 }
 
+// Flat over the nodes (every thread busy whatever nx is): pair i = {record i,
+// record of its +x neighbour} (itself on the last x), and the brick marks of
+// the non-zero records.
 template <int DT, int KIND>
-__global__ void __launch_bounds__(256) pair_pack_kernel(const void* src, void* dst, long long rows, int nx, int ny,
+__global__ void __launch_bounds__(256) pair_pack_kernel(const void* src, void* dst, long long nodes, int nx, int ny,
                                                         unsigned char* occ, int nbx, int nby, int nbz)
 {
-    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-        const long long r0 = row * nx;
-        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-            const long long i = r0 + x, j = x < nx - 1 ? i + 1 : i;
-            if constexpr (KIND == KIND_RGB) {
-                if constexpr (DT == DT_F32) {
-                    const float4* s4 = reinterpret_cast<const float4*>(src);
-                    float4* d4 = reinterpret_cast<float4*>(dst);
-                    const float4 a = __ldg(s4 + i);
-                    d4[2 * i] = a;
-                    d4[2 * i + 1] = __ldg(s4 + j);
-                    if (occ && (a.x != 0.0f || a.y != 0.0f || a.z != 0.0f || a.w != 0.0f))
-                        mark_bricks(occ, x, (int)(row % ny), (int)(row / ny), nbx, nby, nbz);
-                } else {
-                    const uint2* s2 = reinterpret_cast<const uint2*>(src);
-                    const uint2 a = __ldg(s2 + i), b = __ldg(s2 + j);
-                    reinterpret_cast<uint4*>(dst)[i] = make_uint4(a.x, a.y, b.x, b.y);
-                    // +0 and -0 both read as empty
-                    if (occ && (((a.x | a.y) & 0x7fff7fffu) != 0u))
-                        mark_bricks(occ, x, (int)(row % ny), (int)(row / ny), nbx, nby, nbz);
-                }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long row = i / nx;
+        const int x = (int)(i - row * nx);
+        const long long j = x < nx - 1 ? i + 1 : i;
+        if constexpr (KIND == KIND_RGB) {
+            bool nonzero;
+            if constexpr (DT == DT_F32) {
+                const float4* s4 = reinterpret_cast<const float4*>(src);
+                float4* d4 = reinterpret_cast<float4*>(dst);
+                const float4 a = __ldg(s4 + i);
+                d4[2 * i] = a;
+                d4[2 * i + 1] = __ldg(s4 + j);
+                nonzero = a.x != 0.0f || a.y != 0.0f || a.z != 0.0f || a.w != 0.0f;
             } else {
-                if constexpr (DT == DT_F32) {
-                    const float2* s2 = reinterpret_cast<const float2*>(src);
-                    const float2 a = __ldg(s2 + i), b = __ldg(s2 + j);
-                    reinterpret_cast<float4*>(dst)[i] = make_float4(a.x, a.y, b.x, b.y);
-                } else {
-                    const unsigned* s1 = reinterpret_cast<const unsigned*>(src);
-                    reinterpret_cast<uint2*>(dst)[i] = make_uint2(__ldg(s1 + i), __ldg(s1 + j));
-                }
+                const uint2* s2 = reinterpret_cast<const uint2*>(src);
+                const uint2 a = __ldg(s2 + i), b = __ldg(s2 + j);
+                reinterpret_cast<uint4*>(dst)[i] = make_uint4(a.x, a.y, b.x, b.y);
+                nonzero = ((a.x | a.y) & 0x7fff7fffu) != 0u;   // +0 and -0 both read as empty
+            }
+            if (occ && nonzero) mark_bricks(occ, x, (int)(row % ny), (int)(row / ny), nbx, nby, nbz);
+        } else {
+            if constexpr (DT == DT_F32) {
+                const float2* s2 = reinterpret_cast<const float2*>(src);
+                const float2 a = __ldg(s2 + i), b = __ldg(s2 + j);
+                reinterpret_cast<float4*>(dst)[i] = make_float4(a.x, a.y, b.x, b.y);
+            } else {
+                const unsigned* s1 = reinterpret_cast<const unsigned*>(src);
+                reinterpret_cast<uint2*>(dst)[i] = make_uint2(__ldg(s1 + i), __ldg(s1 + j));
             }
         }
     }
@@ -325,14 +327,14 @@ cudaError_t launch_pair_pack_batch(const ProbDev* probs, int nprob, int dt, cuda
 cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int nx, int ny, int nz,
                              unsigned char* occ, cudaStream_t s)
 {
-    const long long rows = (long long)ny * nz;
-    const int g = (int)(rows < 152LL * 32 ? rows : 152LL * 32);
+    const long long nodes = (long long)nx * ny * nz;
+    const int g = grid_for(nodes, 256);
     const int nbx = (nx - 2) / kBrick + 1, nby = (ny - 2) / kBrick + 1, nbz = (nz - 2) / kBrick + 1;
     if (occ) {
         cudaError_t e = cudaMemsetAsync(occ, 0, brick_table_bytes(nx, ny, nz), s);
         if (e != cudaSuccess) return e;
     }
-#define FR_PACK(D, K) pair_pack_kernel<D, K><<<g, 256, 0, s>>>(src, dst, rows, nx, ny, occ, nbx, nby, nbz)
+#define FR_PACK(D, K) pair_pack_kernel<D, K><<<g, 256, 0, s>>>(src, dst, nodes, nx, ny, occ, nbx, nby, nbz)
     if (kind == KIND_RGB) {
         if (dt == DT_F32) FR_PACK(DT_F32, KIND_RGB);
         else if (dt == DT_BF16) FR_PACK(DT_BF16, KIND_RGB);
