@@ -645,7 +645,8 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     const bool hg = per_view && p->hg_g != 0.0f && albedo;
     if (hg) FR_TRY(ensure(c, c->L6, (size_t)nodes * 6 * 16, "directional radiances"));
     if (until) FR_TRY(ensure(c, c->loop, 16, "loop counter"));
-    FR_TRY(ensure(c, c->flame_list, (size_t)npix * sizeof(unsigned), "flame list"));
+    // (runs may be padded to whole warps: at most one tile's worth per tile)
+    FR_TRY(ensure(c, c->flame_list, (size_t)nt * kTileThreads * sizeof(unsigned), "flame list"));
     FR_TRY(ensure(c, c->pairs, (size_t)nodes * 2 * rec_bytes(vol), "pairs"));
     const int nbx = bricks_along(vol->nx), nby = bricks_along(vol->ny), nbz = bricks_along(vol->nz);
     unsigned char* occ = nullptr;
@@ -719,6 +720,12 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
         u.p.adj_occ = hb;
         u.p.adj_box = hb ? brick_box(hb, nbx, nby, nbz) : nullptr;
     }
+    // With the hull's brick table, records outside its flagged bricks are
+    // zero: the pack skips their nodes and the forward clips its rays to the
+    // table's box (which holds every brick with a non-zero record), so the
+    // box of the non-zero bricks is not recomputed every iteration.
+    const unsigned char* pack_keep = occ ? u.p.adj_occ : nullptr;
+    if (pack_keep) f.p.occ_box = u.p.adj_box;
     FR_TRY(trace_mark(c, FR_PHASE_SETUP));
     // One iteration on stream st.  it >= 0: per-iteration slots it; it < 0:
     // slot 0 and the iteration index read on the device (graph body).
@@ -788,7 +795,7 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
             }
             if (v == 0 || seq || hg) {
                 FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz,
-                                            occ, st));
+                                            occ, st, pack_keep));
                 FR_TRY(trace_mark(c, FR_PHASE_PACK));
             }
             view_problem(v, slot);
@@ -826,7 +833,7 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
             FR_TRY(trace_mark(c, FR_PHASE_SCATTER));
         }
         FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, occ,
-                                    st));
+                                    st, pack_keep));
         FR_TRY(trace_mark(c, FR_PHASE_PACK));
         f.p.flist_count = f.p.flist ? flame_cnt + slot : nullptr;
         FR_CUDA(c, launch_fwd(f, vol->dtype, vol->kind, nt, st));

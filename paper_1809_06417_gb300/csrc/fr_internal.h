@@ -118,8 +118,11 @@ __host__ __device__ inline unsigned* brick_box(unsigned char* table, int nbx, in
     return reinterpret_cast<unsigned*>(table + (((size_t)nbx * nby * nbz + 15) & ~(size_t)15));
 }
 // x-pair records of a volume (2 records per node) for the forward march, and
-// (occ non-null, RGB records) the brick table of its non-zero records
+// (occ non-null, RGB records) the brick table of its non-zero records.  keep
+// (nullable, brick-table layout): only nodes of flagged bricks are packed and
+// their box is the one the forward clips to, so occ's own box is not computed
+// (for the visual hull's table, whose flagged-off bricks hold zero records).
 cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int nx, int ny, int nz,
-                             unsigned char* occ, cudaStream_t s);
+                             unsigned char* occ, cudaStream_t s, const unsigned char* keep = nullptr);
 
 }  // namespace frk

@@ -20,16 +20,25 @@
 #else
 #define FR_MARCH_BOUNDS __launch_bounds__(frk::kTileThreads)
 #endif
-// Resident CTAs per SM asked for the forward march.
+// Resident CTAs per SM asked for the forward march: 6 caps it at 80
+// registers without spills (20% more warps than the 96 it takes unbounded;
+// measured 3% faster; 7 or 8 spill and are slower).
 #ifndef FR_FWD_MINB
-#define FR_FWD_MINB 1
+#define FR_FWD_MINB 6
 #endif
 #define FR_FWD_BOUNDS __launch_bounds__(frk::kTileThreads, FR_FWD_MINB)
-// Resident CTAs per SM asked for the adjustment over the flame-ray list.
-#ifndef FR_ADJ_MINB
-#define FR_ADJ_MINB 6
+// The adjustment over the flame-ray list runs one warp per CTA: a CTA's
+// resources return as soon as its 32 rays end, where a 4-warp CTA waits for
+// its longest ray (measured 6% faster).  FR_ADJ_MINB resident CTAs per SM
+// leave the compiler 96 registers (20 warps per SM); asking for 24 (80
+// registers) measured 2% slower.
+#ifndef FR_ADJ_THREADS
+#define FR_ADJ_THREADS 32
 #endif
-#define FR_ADJ_LIST_BOUNDS __launch_bounds__(frk::kTileThreads, FR_ADJ_MINB)
+#ifndef FR_ADJ_MINB
+#define FR_ADJ_MINB 20
+#endif
+#define FR_ADJ_LIST_BOUNDS __launch_bounds__(FR_ADJ_THREADS, FR_ADJ_MINB)
 
 
 namespace frk {
@@ -132,11 +141,6 @@ __device__ __forceinline__ void load8_pairs(const void* pairs, long long base, i
     Rec::pair(pairs, base + nxy + nx, v[6], v[7]);
 }
 
-// Forward march of one ray.  Consecutive samples often share a cell (at half a
-// voxel step about 2 in 5 do), so the cell's eight records stay in registers
-// and are reloaded only when the sample enters another cell.  (Reloading just
-// the four records of a crossed face costs more instructions than the L1
-// traffic it saves.)
 // Skipping of flagged-off bricks along one ray.  A brick is the box of kBrick^3
 // cells [B b, min(B b + B, n - 1)] per axis (B = kBrick); `flags` holds one byte per brick
 // (non-zero: the samples in it are evaluated).
@@ -203,6 +207,11 @@ struct BrickSkip {
     }
 };
 
+// Forward march of one ray.  Consecutive samples often share a cell (at half a
+// voxel step about 2 in 5 do), so the cell's eight records stay in registers
+// and are reloaded only when the sample enters another cell.  (Reloading just
+// the four records of a crossed face costs more instructions than the L1
+// traffic it saves.)
 // MODE 0: records gathered one by one; 1: from x-pair records; 2: x-pair
 // records and exact skipping of empty bricks (RGB field mode only: a sample
 // whose eight corner records are all zero adds exactly nothing and leaves the
@@ -287,10 +296,12 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
     }
     if (P.flist) {
         // flame-ray list for the adjustment: each CTA appends the flame
-        // pixels of its tile as one contiguous run in tile order, so the
-        // adjustment's warps take neighbouring rays
+        // pixels of its tile as one contiguous run in tile order, padded to
+        // whole warps, so each of the adjustment's warps takes neighbouring
+        // rays of one tile (measured 3% faster than unpadded runs, whose
+        // warps straddle two unrelated tiles)
         __shared__ unsigned wcount[kTileThreads / 32];
-        __shared__ unsigned run_at;
+        __shared__ unsigned run_at, run_len;
         const unsigned m = __ballot_sync(0xffffffffu, flame);
         const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
         if (lane == 0) wcount[w] = (unsigned)__popc(m);
@@ -299,6 +310,8 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
             unsigned total = 0;
 #pragma unroll
             for (int i = 0; i < kTileThreads / 32; ++i) total += wcount[i];
+            run_len = total;
+            total = (total + 31u) & ~31u;
             run_at = total ? atomicAdd(P.flist_count, total) : 0u;
         }
         __syncthreads();
@@ -307,6 +320,9 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
             for (int i = 0; i < w; ++i) at += wcount[i];
             P.flist[at] = (unsigned)pix;
         }
+        // the run is padded to whole warps with entries that name no pixel
+        if ((unsigned)threadIdx.x >= run_len && (unsigned)threadIdx.x < ((run_len + 31u) & ~31u))
+            P.flist[run_at + threadIdx.x] = kNoPixel;
     }
     if (P.partials) {
         __shared__ float red[4][kTileThreads / 32];
@@ -371,11 +387,16 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
     const void* vol = P.vol;
     const long long nodes = nxy * P.nz;
     (void)nodes;
+    // every slot that leaves has collected at least one sample, so its
+    // reduction is issued without testing the weight (a zero test per slot
+    // measured 5% slower)
     auto leave = [&acc, dV, dl0, dl1, dl2, nodes](int t, int node) {
         const float w = acc[t];
-        if (w != 0.0f) red_add_v4(dV + 4 * (unsigned)FR_CHK(node, nodes, 2u), w * dl0, w * dl1, w * dl2, 0.0f);
+        red_add_v4(dV + 4 * (unsigned)FR_CHK(node, nodes, 2u), w * dl0, w * dl1, w * dl2, 0.0f);
         acc[t] = 0.0f;
     };
+    // (reloading all eight corner sigmas on every cell change instead of the
+    // entering slots' measured 16% slower)
     auto enter = [&sg, vol, nodes](int t, int node) {
         if constexpr (!TAU) sg[t] = load_rgb_sigma<DT>(vol, (unsigned)FR_CHK(node, nodes, 1u));
     };
@@ -423,15 +444,17 @@ __device__ __forceinline__ void adj_body(const ProbDev& P, const CamDev* cams, i
 
 // The same over a compacted list of flame rays (linear pixel indices in tile
 // order, so a warp's 32 rays are neighbours): no lane idles on a non-flame
-// pixel.  CTA b takes list entries [128 b, 128 b + 128).
+// pixel.  CTA b takes list entries [n b, n b + n), n = FR_ADJ_THREADS.
 template <int DT, bool TAU, bool SKIP>
 __global__ void FR_ADJ_LIST_BOUNDS adj_list(const __grid_constant__ SingleArgs a, const unsigned* __restrict__ list,
                                          const unsigned* __restrict__ count)
 {
-    const unsigned i = blockIdx.x * (unsigned)kTileThreads + threadIdx.x;
+    const unsigned i = blockIdx.x * (unsigned)FR_ADJ_THREADS + threadIdx.x;
     if (i >= __ldg(count)) return;
     const ProbDev& P = a.p;
-    const unsigned pix = (unsigned)FR_CHK(__ldg(list + i), (long long)P.ncam * P.W * P.H, 8u);
+    const unsigned e = __ldg(list + i);
+    if (e == kNoPixel) return;
+    const unsigned pix = (unsigned)FR_CHK(e, (long long)P.ncam * P.W * P.H, 8u);
     const unsigned per_view = (unsigned)P.W * (unsigned)P.H;
     const int view = (int)(pix / per_view);
     const unsigned r = pix - (unsigned)view * per_view;
@@ -503,15 +526,11 @@ __device__ __forceinline__ void bwd_body(const ProbDev& P, const CamDev* cams, i
     const void* vol = P.vol;
     const long long nodes = nxy * P.nz;
     (void)nodes;
+    // (reductions of all-zero sums are issued too, as in the adjustment)
     auto leave = [&acc, dV, nodes](int t, int node) {
-        bool any = false;
-#pragma unroll
-        for (int q = 0; q < NA; ++q) any = any || acc[t][q] != 0.0f;
-        if (any) {
-            const unsigned nd = (unsigned)FR_CHK(node, nodes, 2u);
-            if constexpr (KIND == KIND_RGB) red_add_v4(dV + 4 * nd, acc[t][0], acc[t][1], acc[t][2], acc[t][3]);
-            else red_add_v2(dV + 2 * nd, acc[t][0], acc[t][1]);
-        }
+        const unsigned nd = (unsigned)FR_CHK(node, nodes, 2u);
+        if constexpr (KIND == KIND_RGB) red_add_v4(dV + 4 * nd, acc[t][0], acc[t][1], acc[t][2], acc[t][3]);
+        else red_add_v2(dV + 2 * nd, acc[t][0], acc[t][1]);
 #pragma unroll
         for (int q = 0; q < NA; ++q) acc[t][q] = 0.0f;
     };
@@ -902,8 +921,9 @@ cudaError_t launch_flame_list(const SingleArgs& a, int ntiles, unsigned* buf, un
 cudaError_t launch_adjust_list(const SingleArgs& a, int dt, int ntiles, const unsigned* list,
                                const unsigned* count, cudaStream_t s)
 {
+    static_assert(FR_ADJ_THREADS % 32 == 0 && kTileThreads % FR_ADJ_THREADS == 0, "adjustment CTA size");
     const bool tau = a.p.tau > 0.0f;
-    dim3 grid(ntiles), block(kTileThreads);
+    dim3 grid((unsigned)ntiles * (kTileThreads / FR_ADJ_THREADS)), block(FR_ADJ_THREADS);
     const bool skip = a.p.adj_occ != nullptr && !tau;
     FR_DISPATCH_DT(dt, D, {
         if (tau) adj_list<D, true, false><<<grid, block, 0, s>>>(a, list, count);

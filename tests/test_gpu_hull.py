@@ -72,7 +72,10 @@ def test_hull_tags_bit_exact_full_size(orc, fr_ctx):
     assert 0.01 < inside < 0.6
 
 
-def test_reconstruct_with_hull_follows_oracle(orc, fr_ctx):
+@pytest.mark.parametrize("scatter", [False, True])
+def test_reconstruct_with_hull_follows_oracle(orc, fr_ctx, scatter):
+    """The hull-restricted loop follows the oracle; with in-scattering its
+    sweeps also skip the loads of line chunks in bricks outside the hull."""
     fr, ctx = fr_ctx
     case = plume_case(n=36, views=6, side=64)
     sc = orc.Scene(case.shape, case.origin, case.h, case.cams)
@@ -83,14 +86,16 @@ def test_reconstruct_with_hull_follows_oracle(orc, fr_ctx):
     hull = orc.visual_hull(sc, mask)
     v0 = case.vol.copy()
     v0[..., :3] = 0.01
-    vol_ref, rmse_ref, _ = orc.reconstruct(sc, v0, P, t_ref, mask, bbox_ref, 4, hull=hull)
+    alb_np = case.albedo if scatter else None
+    vol_ref, rmse_ref, _ = orc.reconstruct(sc, v0, P, t_ref, mask, bbox_ref, 4, hull=hull, albedo=alb_np)
     t_dev = torch.as_tensor(img, dtype=torch.float32, device="cuda").contiguous()
     bbox = torch.zeros((len(case.cams), 4), dtype=torch.int32, device="cuda")
     ctx.fr_prepare_targets(t_dev, 30 / 255, bbox)
     v = torch.as_tensor(v0, dtype=torch.float32, device="cuda").contiguous()
     rmse = np.zeros((4, 3), dtype=np.float32)
+    alb = torch.as_tensor(case.albedo, dtype=torch.float32, device="cuda").contiguous() if scatter else None
     ctx.fr_reconstruct(fr.volume(v, case.origin, case.h), fr.cameras(case.cams), t_dev, bbox, 4,
-                       fr.params(step=case.step, alpha_l=3e-3, use_hull=1), rmse=rmse)
+                       fr.params(step=case.step, alpha_l=3e-3, use_hull=1), albedo=alb, rmse=rmse)
     torch.cuda.synchronize()
     got = v.cpu().numpy()
     outside = hull != (1 << len(case.cams)) - 1
@@ -98,7 +103,7 @@ def test_reconstruct_with_hull_follows_oracle(orc, fr_ctx):
     assert np.array_equal(got[~outside][:, 3], v0[~outside][:, 3].astype(np.float32))
     np.testing.assert_allclose(rmse, rmse_ref, rtol=1e-3)
     e = rel_err(got[..., :3], vol_ref[..., :3])
-    print(f"reconstruct with hull: max {e.max():.3e}, outside fraction {outside.mean():.3f}")
+    print(f"reconstruct with hull (scatter={scatter}): max {e.max():.3e}, outside fraction {outside.mean():.3f}")
     assert e.max() < 1e-3
 
 
