@@ -38,6 +38,7 @@ struct fr_ctx {
     Buf occ;                         // brick occupancy for empty-space skipping
     Buf hull_bricks;                 // bricks holding a key point inside the visual hull
     Buf loop;                        // device iteration counter of fr_reconstruct_until
+    Buf fin;                         // multi-CTA error reduction: part sums and its counter (kept 0)
     Buf verr;                        // volume-error partials and result
     Buf L6;                          // directional radiances for anisotropic in-scattering
     Buf hull, sat;                   // visual hull tags, flame-mask tables

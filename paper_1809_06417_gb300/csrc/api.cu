@@ -64,7 +64,7 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     cudaStreamSynchronize(c->stream);
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
                    &c->rmse, &c->J, &c->src, &c->flame_cnt, &c->flame_list, &c->batch, &c->pairs,
-                   &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr, &c->L6})
+                   &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr, &c->L6, &c->fin})
         if (b->p) cudaFree(b->p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
     if (c->staging) cudaFreeHost(c->staging);
@@ -136,6 +136,17 @@ extern "C" fr_status fr_synchronize(fr_ctx* c)
 static bool skips_empty(const fr_volume* vol, const fr_params* p)
 {
     return vol->kind == FR_KIND_RGB && p->skip_empty && !(p->tau > 0.0f);
+}
+
+// Scratch of the multi-CTA error reduction, its counter zeroed once.
+static fr_status fin_scratch(fr_ctx* c, void** out)
+{
+    if (!c->fin.p) {
+        FR_TRY(ensure(c, c->fin, kFinScratchBytes, "error reduction"));
+        FR_CUDA(c, cudaMemsetAsync(c->fin.p, 0, kFinScratchBytes, c->stream));
+    }
+    *out = c->fin.p;
+    return FR_OK;
 }
 
 // x-pair copy of the records the forward march will read, and (when it skips
@@ -215,8 +226,10 @@ extern "C" fr_status fr_render_residual(fr_ctx* c, const fr_volume* vol, const f
     a.p.residual = residual;
     a.p.partials = static_cast<float*>(c->partials.p);
     FR_TRY(attach_pairs(c, vol, p, vol->data, a));
+    void* fin = nullptr;
+    FR_TRY(fin_scratch(c, &fin));
     FR_CUDA(c, launch_fwd(a, vol->dtype, vol->kind, nt, c->stream));
-    FR_CUDA(c, launch_finalize(a.p.partials, nt, sq_err, c->stream));
+    FR_CUDA(c, launch_finalize(a.p.partials, nt, sq_err, c->stream, 0, fin));
     return FR_OK;
 }
 
@@ -726,6 +739,8 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     // box of the non-zero bricks is not recomputed every iteration.
     const unsigned char* pack_keep = occ ? u.p.adj_occ : nullptr;
     if (pack_keep) f.p.occ_box = u.p.adj_box;
+    void* fin = nullptr;
+    FR_TRY(fin_scratch(c, &fin));
     FR_TRY(trace_mark(c, FR_PHASE_SETUP));
     // One iteration on stream st.  it >= 0: per-iteration slots it; it < 0:
     // slot 0 and the iteration index read on the device (graph body).
@@ -801,7 +816,7 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
             view_problem(v, slot);
             FR_CUDA(c, launch_fwd(fv, vol->dtype, vol->kind, nt1, st));
             FR_TRY(trace_mark(c, FR_PHASE_FORWARD));
-            FR_CUDA(c, launch_finalize(fv.p.partials, nt1, sq + 4 * slot, st, v > 0));
+            FR_CUDA(c, launch_finalize(fv.p.partials, nt1, sq + 4 * slot, st, v > 0, fin));
             FR_TRY(trace_mark(c, FR_PHASE_REDUCE));
             if (p->rule == FR_RULE_PAPER) {
                 uv.p.iteration = first_iteration + slot;
@@ -838,7 +853,7 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
         f.p.flist_count = f.p.flist ? flame_cnt + slot : nullptr;
         FR_CUDA(c, launch_fwd(f, vol->dtype, vol->kind, nt, st));
         FR_TRY(trace_mark(c, FR_PHASE_FORWARD));
-        FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * slot, st));
+        FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * slot, st, 0, fin));
         FR_TRY(trace_mark(c, FR_PHASE_REDUCE));
         if (p->rule == FR_RULE_PAPER) {
             u.p.iteration = first_iteration + slot;

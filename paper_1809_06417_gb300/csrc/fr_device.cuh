@@ -131,6 +131,7 @@ __device__ __forceinline__ long long fr_checked(long long i, long long n, unsign
 struct Ray {
     float p0x, p0y, p0z;   // box entry point (voxel coordinates)
     float dx, dy, dz;      // unit direction
+    float idx, idy, idz;   // 1 / direction (infinite along an axis the ray does not move on)
     float chord;           // length inside the box
     int n;                 // number of segments
 };
@@ -149,6 +150,13 @@ __device__ __forceinline__ bool make_ray(const CamDev& c, int px, int py, int nx
     dx *= inv; dy *= inv; dz *= inv;
     float o[3] = {c.o[0], c.o[1], c.o[2]};
     float d[3] = {dx, dy, dz};
+    // The entry point and chord come from correctly rounded quotients: they
+    // fix the sample positions, hence each sample's cell and key points
+    // (Eq. 10), and a sample within rounding of a cell face may land on
+    // either side (products by the reciprocals would widen that window to
+    // about 1.5 ulp).  The reciprocals serve the brick and box clipping,
+    // whose 1e-3 voxel margins absorb their rounding.
+    float id[3] = {1.0f / dx, 1.0f / dy, 1.0f / dz};
     float hi[3] = {(float)(nx - 1), (float)(ny - 1), (float)(nz - 1)};
     float tin = -INFINITY, tout = INFINITY;
 #pragma unroll
@@ -168,6 +176,7 @@ __device__ __forceinline__ bool make_ray(const CamDev& c, int px, int py, int nx
     R.p0y = o[1] + tin * dy;
     R.p0z = o[2] + tin * dz;
     R.dx = dx; R.dy = dy; R.dz = dz;
+    R.idx = id[0]; R.idy = id[1]; R.idz = id[2];
     R.chord = tout - tin;
     R.n = (int)ceilf(R.chord / step);
     return R.n > 0;

@@ -147,10 +147,8 @@ __device__ __forceinline__ void load8_pairs(const void* pairs, long long base, i
 struct BrickSkip {
     int brick = -1;
     bool occupied = true;
-    float idx, idy, idz;    // reciprocal direction
 
-    __device__ __forceinline__ explicit BrickSkip(const Ray& R)
-        : idx(1.0f / R.dx), idy(1.0f / R.dy), idz(1.0f / R.dz) {}
+    __device__ __forceinline__ explicit BrickSkip(const Ray&) {}
 
     // Samples [k0, k1) of the ray that can lie in the box of the flagged-on
     // bricks (box: brick-table layout); false when there are none.  Samples
@@ -165,7 +163,7 @@ struct BrickSkip {
                              (float)((P.nbz - (int)__ldg(box + 2)) * kBrick)};
         const float hi[3] = {(float)min((int)hx * kBrick, P.nx - 1), (float)min((int)hy * kBrick, P.ny - 1),
                              (float)min((int)hz * kBrick, P.nz - 1)};
-        const float o[3] = {R.p0x, R.p0y, R.p0z}, d[3] = {R.dx, R.dy, R.dz};
+        const float o[3] = {R.p0x, R.p0y, R.p0z}, d[3] = {R.dx, R.dy, R.dz}, id[3] = {R.idx, R.idy, R.idz};
         float tin = 0.0f, tout = R.chord;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -173,12 +171,15 @@ struct BrickSkip {
                 if (o[a] < lo[a] - 1e-3f || o[a] > hi[a] + 1e-3f) return false;
                 continue;
             }
-            const float t0 = (lo[a] - o[a]) / d[a], t1 = (hi[a] - o[a]) / d[a];
+            const float t0 = (lo[a] - o[a]) * id[a], t1 = (hi[a] - o[a]) * id[a];
             tin = fmaxf(tin, fminf(t0, t1));
             tout = fminf(tout, fmaxf(t0, t1));
         }
-        k0 = max(0, (int)ceilf((tin - 1e-3f) / step - 0.5f));
-        k1 = min(R.n, (int)floorf((tout + 1e-3f) / step) + 1);
+        // (the 1e-3 voxel margins cover the rounding of the products by
+        // 1 / step, a few ulp of at most a few hundred sample lengths)
+        const float is = 1.0f / step;
+        k0 = max(0, (int)ceilf((tin - 1e-3f) * is - 0.5f));
+        k1 = min(R.n, (int)floorf((tout + 1e-3f) * is) + 1);
         return k0 < k1;
     }
 
@@ -198,9 +199,9 @@ struct BrickSkip {
         if (occupied) return false;
         const int bx = c.i & ~(kBrick - 1), by = c.j & ~(kBrick - 1), bz = c.k & ~(kBrick - 1);
         float te = INFINITY;
-        if (R.dx != 0.0f) te = fminf(te, ((R.dx > 0.0f ? (float)min(bx + kBrick, P.nx - 1) : (float)bx) - R.p0x) * idx);
-        if (R.dy != 0.0f) te = fminf(te, ((R.dy > 0.0f ? (float)min(by + kBrick, P.ny - 1) : (float)by) - R.p0y) * idy);
-        if (R.dz != 0.0f) te = fminf(te, ((R.dz > 0.0f ? (float)min(bz + kBrick, P.nz - 1) : (float)bz) - R.p0z) * idz);
+        if (R.dx != 0.0f) te = fminf(te, ((R.dx > 0.0f ? (float)min(bx + kBrick, P.nx - 1) : (float)bx) - R.p0x) * R.idx);
+        if (R.dy != 0.0f) te = fminf(te, ((R.dy > 0.0f ? (float)min(by + kBrick, P.ny - 1) : (float)by) - R.p0y) * R.idy);
+        if (R.dz != 0.0f) te = fminf(te, ((R.dz > 0.0f ? (float)min(bz + kBrick, P.nz - 1) : (float)bz) - R.p0z) * R.idz);
         const int kn = (int)ceilf((te - 1e-3f) / step - 0.5f);
         k = max(k, kn - 1);
         return true;
@@ -672,6 +673,51 @@ __global__ void __launch_bounds__(1024) finalize_partials(const float* __restric
     }
 }
 
+// The same sum over kFinParts CTAs: CTA b sums its share of the tiles into
+// part_sums[b]; the last CTA to finish (counted in *done, which it resets to 0)
+// adds the shares in order, so the result does not depend on which CTA ends
+// last.  part_sums: kFinParts float4; *done must be 0 before the first launch.
+
+__global__ void __launch_bounds__(256) finalize_parts(const float* __restrict__ partials, int ntiles,
+                                                      float* __restrict__ out4, int accumulate,
+                                                      float4* part_sums, unsigned* done)
+{
+    __shared__ float red[4][8];
+    __shared__ bool last;
+    const int per = (ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int b0 = blockIdx.x * per, b1 = min(b0 + per, ntiles);
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    const float4* p4 = reinterpret_cast<const float4*>(partials);
+#pragma unroll 4
+    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        const float4 v = __ldg(p4 + i);
+        s0 += v.x; s1 += v.y; s2 += v.z; s3 += v.w;
+    }
+    s0 = warp_sum(s0); s1 = warp_sum(s1); s2 = warp_sum(s2); s3 = warp_sum(s3);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { red[0][w] = s0; red[1][w] = s1; red[2][w] = s2; red[3][w] = s3; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float4 t = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            t.x += red[0][i]; t.y += red[1][i]; t.z += red[2][i]; t.w += red[3][i];
+        }
+        part_sums[blockIdx.x] = t;
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    if (threadIdx.x < 4) {
+        __threadfence();
+        const volatile float* ps = reinterpret_cast<const volatile float*>(part_sums);
+        float t = 0.0f;
+        for (int i = 0; i < (int)gridDim.x; ++i) t += ps[4 * i + threadIdx.x];
+        out4[threadIdx.x] = accumulate ? out4[threadIdx.x] + t : t;
+    }
+    if (threadIdx.x == 0) *done = 0u;
+}
+
 // Flame-ray list (pixels whose prepared target is non-zero), in tile order.
 // Pass 1 counts each warp's flame pixels and each CTA's total; pass 2 scans the
 // CTA totals; pass 3 writes each warp's pixels at the CTA offset plus the
@@ -904,9 +950,16 @@ cudaError_t launch_count(const SingleArgs& a, int ntiles, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cudaStream_t s, int accumulate)
+cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cudaStream_t s, int accumulate,
+                            void* scratch)
 {
-    finalize_partials<<<1, 1024, 0, s>>>(partials, ntiles, out4, accumulate);
+    if (scratch) {
+        float4* part_sums = reinterpret_cast<float4*>(scratch);
+        unsigned* done = reinterpret_cast<unsigned*>(part_sums + kFinParts);
+        finalize_parts<<<kFinParts, 256, 0, s>>>(partials, ntiles, out4, accumulate, part_sums, done);
+    } else {
+        finalize_partials<<<1, 1024, 0, s>>>(partials, ntiles, out4, accumulate);
+    }
     return cudaGetLastError();
 }
 

@@ -558,6 +558,145 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const
     }
 }
 
+// The y / z sweep with a chunk of at most CM nodes held in registers: the
+// chunk's records (and its nodes' J, albedo) are loaded together at the start,
+// where the kernel above reloads them in three dependent walks; J is stored
+// once per node.  The arithmetic and its order are the same, so the results
+// are bitwise equal.  rec[0] is node max(s0 - 1, 0), rec[1 + q] node s0 + q,
+// rec[cnt + 1] node min(s1, n - 1); segment j joins rec[j] and rec[j + 1] and
+// leads into node s0 + j.
+template <int DT, int AXIS, bool LAST, int CM>
+__global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_reg_kernel(const void* em, const float* albedo,
+                                                                                float* J, void* out, int nx, int ny,
+                                                                                int nz, bool skip_empty)
+{
+    __shared__ float4 fwd[kSweepChunks][kSweepLines];
+    __shared__ float4 bwd[kSweepChunks][kSweepLines];
+    const int n_line = AXIS == 1 ? ny : nz;
+    const long long lines = AXIS == 1 ? (long long)nx * nz : (long long)nx * ny;
+    const long long line = blockIdx.x * (long long)kSweepLines + threadIdx.x;
+    const int ch = threadIdx.y;
+    const bool live = line < lines;
+    long long start = 0, stride = 1;
+    if (live) {
+        if constexpr (AXIS == 1) {
+            const long long z = line / nx, x = line - z * nx;
+            start = z * (long long)nx * ny + x;
+            stride = nx;
+        } else {
+            start = line;                            // line = y * nx + x
+            stride = (long long)nx * ny;
+        }
+    }
+    const long long nodes = (long long)nx * ny * nz;
+    const int m = (n_line + kSweepChunks - 1) / kSweepChunks;
+    const int s0 = min(ch * m, n_line), s1 = min(s0 + m, n_line), cnt = s1 - s0;   // cnt <= CM
+    float4 rec[CM + 2];
+    float Ef = 1.0f, F0 = 0.0f, F1 = 0.0f, F2 = 0.0f;
+    float Eb = 1.0f, B0 = 0.0f, B1 = 0.0f, B2 = 0.0f;
+    bool occupied = false;
+    float3 jv[CM];   // J of the chunk's nodes (earlier sweeps), then J + L_forward / 6
+    float alb[CM];
+    if (live && cnt > 0) {
+#pragma unroll
+        for (int j = 0; j < CM + 2; ++j) {
+            if (j <= cnt + 1) {
+                const int i = j == 0 ? max(s0 - 1, 0) : (j <= cnt ? s0 + j - 1 : min(s1, n_line - 1));
+                rec[j] = load_rgb<DT>(em, FR_CHK(start + i * stride, nodes, 35u));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < CM; ++q)
+            if (q < cnt) occupied |= nonzero_record(rec[q + 1]);
+        if (!skip_empty || occupied) {
+            float4* J4 = reinterpret_cast<float4*>(J);
+#pragma unroll
+            for (int q = 0; q < CM; ++q) {
+                if (q < cnt) {
+                    const long long node = start + (s0 + q) * stride;
+                    const float4 t = J4[node];
+                    jv[q] = make_float3(t.x, t.y, t.z);
+                    if constexpr (LAST) alb[q] = __ldg(albedo + node);
+                }
+            }
+        }
+        // phase 1: the chunk's forward and backward maps
+#pragma unroll
+        for (int j = 0; j <= CM; ++j) {
+            const int i = s0 + j;
+            if (j <= cnt && i >= 1 && i <= n_line - 1) {
+                const Seg g = seg_between<DT>(rec[j], rec[j + 1]);
+                if (j < cnt) {
+                    F0 = fmaf(F0, g.e, g.c0); F1 = fmaf(F1, g.e, g.c1); F2 = fmaf(F2, g.e, g.c2);
+                    Ef *= g.e;
+                }
+                if (j >= 1) {
+                    B0 = fmaf(Eb, g.c0, B0); B1 = fmaf(Eb, g.c1, B1); B2 = fmaf(Eb, g.c2, B2);
+                    Eb *= g.e;
+                }
+            }
+        }
+    }
+    fwd[ch][threadIdx.x] = make_float4(Ef, F0, F1, F2);
+    bwd[ch][threadIdx.x] = make_float4(Eb, B0, B1, B2);
+    __syncthreads();
+    if (!live || cnt <= 0) return;
+    if (skip_empty && !occupied) {
+        if constexpr (LAST) {
+            for (int q = 0; q < cnt; ++q)
+                store_rgb<DT>(out, FR_CHK(start + (s0 + q) * stride, nodes, 36u), make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+        }
+        return;
+    }
+    // phase 2: radiance arriving at the chunk from either side
+    float lf0 = 0.0f, lf1 = 0.0f, lf2 = 0.0f;
+    for (int c = 0; c < ch; ++c) {
+        const float4 f = fwd[c][threadIdx.x];
+        lf0 = fmaf(lf0, f.x, f.y); lf1 = fmaf(lf1, f.x, f.z); lf2 = fmaf(lf2, f.x, f.w);
+    }
+    float lb0 = 0.0f, lb1 = 0.0f, lb2 = 0.0f;
+    for (int c = kSweepChunks - 1; c > ch; --c) {
+        const float4 b = bwd[c][threadIdx.x];
+        lb0 = fmaf(lb0, b.x, b.y); lb1 = fmaf(lb1, b.x, b.z); lb2 = fmaf(lb2, b.x, b.w);
+    }
+    // phase 3: forward walk (J += L_forward / 6, in registers) ...
+    const float sixth = 1.0f / 6.0f;
+#pragma unroll
+    for (int q = 0; q < CM; ++q) {
+        if (q < cnt) {
+            if (s0 + q > 0) {
+                const Seg g = seg_between<DT>(rec[q], rec[q + 1]);
+                lf0 = fmaf(lf0, g.e, g.c0); lf1 = fmaf(lf1, g.e, g.c1); lf2 = fmaf(lf2, g.e, g.c2);
+            }
+            jv[q].x = fmaf(lf0, sixth, jv[q].x); jv[q].y = fmaf(lf1, sixth, jv[q].y);
+            jv[q].z = fmaf(lf2, sixth, jv[q].z);
+        }
+    }
+    // ... and backward walk (J += L_backward / 6; stored, or the source written)
+    float4* J4 = reinterpret_cast<float4*>(J);
+#pragma unroll
+    for (int q = CM - 1; q >= 0; --q) {
+        if (q < cnt) {
+            const int i = s0 + q;
+            if (i < n_line - 1) {
+                const Seg g = seg_between<DT>(rec[q + 1], rec[q + 2]);
+                lb0 = fmaf(lb0, g.e, g.c0); lb1 = fmaf(lb1, g.e, g.c1); lb2 = fmaf(lb2, g.e, g.c2);
+            }
+            const float jx = fmaf(lb0, sixth, jv[q].x), jy = fmaf(lb1, sixth, jv[q].y), jz = fmaf(lb2, sixth, jv[q].z);
+            const long long node = FR_CHK(start + i * stride, nodes, 37u);
+            if constexpr (LAST) {
+                const float4 cur = rec[q + 1];
+                const float as = alb[q] * cur.w;
+                store_rgb<DT>(out, node, make_float4(fmaf(as, jx, cur.x), fmaf(as, jy, cur.y), fmaf(as, jz, cur.z),
+                                                     cur.w));
+                if (!skip_empty) J4[node] = make_float4(jx, jy, jz, 0.0f);
+            } else {
+                J4[node] = make_float4(jx, jy, jz, 0.0f);
+            }
+        }
+    }
+}
+
 // The x sweep with one warp per grid line: lane l owns the l-th of 32 chunks
 // of consecutive nodes, so a warp's loads walk along one row of memory.  The
 // chunks' affine maps are combined with warp shuffles: an inclusive prefix
@@ -670,23 +809,152 @@ __global__ void __launch_bounds__(256) sweep_x_kernel(const void* em, float* J, 
     }
 }
 
-cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* albedo, float* J,
-                                  void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s, bool skip_empty)
+// The x sweep with a chunk of at most CM nodes held in registers (see
+// sweep_reg_kernel; the same arithmetic as sweep_x_kernel in the same order).
+template <int DT, int CM>
+__global__ void __launch_bounds__(256) sweep_x_reg_kernel(const void* em, float* J, int nx, int ny, int nz,
+                                                          bool skip_empty)
 {
-    if (dt_in != dt_out) return cudaErrorInvalidValue;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long line = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (line >= (long long)ny * nz) return;   // whole warps leave together
+    const long long start = line * nx;
+    const long long nodes = (long long)nx * ny * nz;
+    const int m = (nx + 31) / 32;
+    const int s0 = min(lane * m, nx), s1 = min(s0 + m, nx), cnt = s1 - s0;   // cnt <= CM
+    float4 rec[CM + 2];
+    float Ef = 1.0f, F0 = 0.0f, F1 = 0.0f, F2 = 0.0f;
+    float Eb = 1.0f, B0 = 0.0f, B1 = 0.0f, B2 = 0.0f;
+    bool occupied = false;
+    if (cnt > 0) {
+#pragma unroll
+        for (int j = 0; j < CM + 2; ++j) {
+            if (j <= cnt + 1) {
+                const int i = j == 0 ? max(s0 - 1, 0) : (j <= cnt ? s0 + j - 1 : min(s1, nx - 1));
+                rec[j] = load_rgb<DT>(em, FR_CHK(start + i, nodes, 38u));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < CM; ++q)
+            if (q < cnt) occupied |= nonzero_record(rec[q + 1]);
+#pragma unroll
+        for (int j = 0; j <= CM; ++j) {
+            const int i = s0 + j;
+            if (j <= cnt && i >= 1 && i <= nx - 1) {
+                const Seg g = seg_between<DT>(rec[j], rec[j + 1]);
+                if (j < cnt) {
+                    F0 = fmaf(F0, g.e, g.c0); F1 = fmaf(F1, g.e, g.c1); F2 = fmaf(F2, g.e, g.c2);
+                    Ef *= g.e;
+                }
+                if (j >= 1) {
+                    B0 = fmaf(Eb, g.c0, B0); B1 = fmaf(Eb, g.c1, B1); B2 = fmaf(Eb, g.c2, B2);
+                    Eb *= g.e;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float e = __shfl_up_sync(FULL, Ef, o), c0 = __shfl_up_sync(FULL, F0, o);
+        const float c1 = __shfl_up_sync(FULL, F1, o), c2 = __shfl_up_sync(FULL, F2, o);
+        if (lane >= o) {
+            F0 = fmaf(c0, Ef, F0); F1 = fmaf(c1, Ef, F1); F2 = fmaf(c2, Ef, F2);
+            Ef *= e;
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float e = __shfl_down_sync(FULL, Eb, o), c0 = __shfl_down_sync(FULL, B0, o);
+        const float c1 = __shfl_down_sync(FULL, B1, o), c2 = __shfl_down_sync(FULL, B2, o);
+        if (lane + o < 32) {
+            B0 = fmaf(c0, Eb, B0); B1 = fmaf(c1, Eb, B1); B2 = fmaf(c2, Eb, B2);
+            Eb *= e;
+        }
+    }
+    float lf0 = __shfl_up_sync(FULL, F0, 1), lf1 = __shfl_up_sync(FULL, F1, 1), lf2 = __shfl_up_sync(FULL, F2, 1);
+    float lb0 = __shfl_down_sync(FULL, B0, 1), lb1 = __shfl_down_sync(FULL, B1, 1), lb2 = __shfl_down_sync(FULL, B2, 1);
+    if (lane == 0) { lf0 = lf1 = lf2 = 0.0f; }
+    if (lane == 31) { lb0 = lb1 = lb2 = 0.0f; }
+    if (cnt <= 0) return;
+    const float sixth = 1.0f / 6.0f;
+    float4* J4 = reinterpret_cast<float4*>(J);
+    if (skip_empty && !occupied) {
+        for (int q = 0; q < cnt; ++q) J4[start + s0 + q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        return;
+    }
+    float3 jv[CM];
+#pragma unroll
+    for (int q = 0; q < CM; ++q) {
+        if (q < cnt) {
+            if (s0 + q > 0) {
+                const Seg g = seg_between<DT>(rec[q], rec[q + 1]);
+                lf0 = fmaf(lf0, g.e, g.c0); lf1 = fmaf(lf1, g.e, g.c1); lf2 = fmaf(lf2, g.e, g.c2);
+            }
+            jv[q] = make_float3(lf0 * sixth, lf1 * sixth, lf2 * sixth);
+        }
+    }
+#pragma unroll
+    for (int q = CM - 1; q >= 0; --q) {
+        if (q < cnt) {
+            const int i = s0 + q;
+            if (i < nx - 1) {
+                const Seg g = seg_between<DT>(rec[q + 1], rec[q + 2]);
+                lb0 = fmaf(lb0, g.e, g.c0); lb1 = fmaf(lb1, g.e, g.c1); lb2 = fmaf(lb2, g.e, g.c2);
+            }
+            J4[FR_CHK(start + i, nodes, 39u)] =
+                make_float4(fmaf(lb0, sixth, jv[q].x), fmaf(lb1, sixth, jv[q].y), fmaf(lb2, sixth, jv[q].z), 0.0f);
+        }
+    }
+}
+
+// Chunks of up to FR_SWEEP_REG_MAX (4 or 8; 0: none) nodes run the
+// register-held sweep kernels.
+#ifndef FR_SWEEP_REG_MAX
+#define FR_SWEEP_REG_MAX 8
+#endif
+
+template <int DT, int AXIS, bool LAST>
+static void launch_sweep_yz(int m, unsigned grid, const void* em, const float* albedo, float* J, void* out, int nx,
+                            int ny, int nz, cudaStream_t s, bool skip_empty)
+{
+    const dim3 B(kSweepLines, kSweepChunks);
+    if (FR_SWEEP_REG_MAX >= 4 && m <= 4)
+        sweep_reg_kernel<DT, AXIS, LAST, 4><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, skip_empty);
+    else if (FR_SWEEP_REG_MAX >= 8 && m <= 8)
+        sweep_reg_kernel<DT, AXIS, LAST, 8><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, skip_empty);
+    else
+        sweep_kernel<DT, AXIS, LAST><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, nullptr, skip_empty);
+}
+
+template <int DT>
+static void launch_sweeps(const void* em, const float* albedo, float* J, void* out, int nx, int ny, int nz,
+                          cudaStream_t s, bool skip_empty)
+{
     const long long lx = (long long)ny * nz, ly = (long long)nx * nz, lz = (long long)nx * ny;
     const unsigned gxw = (unsigned)((lx + 7) / 8);  // one warp per x line, 8 warps per CTA
     const unsigned gy = (unsigned)((ly + kSweepLines - 1) / kSweepLines);
     const unsigned gz = (unsigned)((lz + kSweepLines - 1) / kSweepLines);
-    const dim3 B(kSweepLines, kSweepChunks);
-#define FR_SWEEPS(D)                                                                         \
-    sweep_x_kernel<D><<<gxw, 256, 0, s>>>(emission, J, nx, ny, nz, nullptr, skip_empty);                \
-    sweep_kernel<D, 1, false><<<gy, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz, nullptr, skip_empty); \
-    sweep_kernel<D, 2, true><<<gz, B, 0, s>>>(emission, albedo, J, out, nx, ny, nz, nullptr, skip_empty)
-    if (dt_in == DT_F32) { FR_SWEEPS(DT_F32); }
-    else if (dt_in == DT_BF16) { FR_SWEEPS(DT_BF16); }
-    else { FR_SWEEPS(DT_F16); }
-#undef FR_SWEEPS
+    const int mx = (nx + 31) / 32;
+    if (FR_SWEEP_REG_MAX >= 4 && mx <= 4)
+        sweep_x_reg_kernel<DT, 4><<<gxw, 256, 0, s>>>(em, J, nx, ny, nz, skip_empty);
+    else if (FR_SWEEP_REG_MAX >= 8 && mx <= 8)
+        sweep_x_reg_kernel<DT, 8><<<gxw, 256, 0, s>>>(em, J, nx, ny, nz, skip_empty);
+    else
+        sweep_x_kernel<DT><<<gxw, 256, 0, s>>>(em, J, nx, ny, nz, nullptr, skip_empty);
+    launch_sweep_yz<DT, 1, false>((ny + kSweepChunks - 1) / kSweepChunks, gy, em, albedo, J, out, nx, ny, nz, s,
+                                  skip_empty);
+    launch_sweep_yz<DT, 2, true>((nz + kSweepChunks - 1) / kSweepChunks, gz, em, albedo, J, out, nx, ny, nz, s,
+                                 skip_empty);
+}
+
+cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* albedo, float* J,
+                                  void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s, bool skip_empty)
+{
+    if (dt_in != dt_out) return cudaErrorInvalidValue;
+    if (dt_in == DT_F32) launch_sweeps<DT_F32>(emission, albedo, J, out, nx, ny, nz, s, skip_empty);
+    else if (dt_in == DT_BF16) launch_sweeps<DT_BF16>(emission, albedo, J, out, nx, ny, nz, s, skip_empty);
+    else launch_sweeps<DT_F16>(emission, albedo, J, out, nx, ny, nz, s, skip_empty);
     return cudaGetLastError();
 }
 
