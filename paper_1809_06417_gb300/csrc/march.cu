@@ -212,7 +212,8 @@ struct BrickSkip {
 // voxel step about 2 in 5 do), so the cell's eight records stay in registers
 // and are reloaded only when the sample enters another cell.  (Reloading just
 // the four records of a crossed face costs more instructions than the L1
-// traffic it saves.)
+// traffic it saves; prefetching the next sample's cell into L1 measured 8%
+// slower.)
 // MODE 0: records gathered one by one; 1: from x-pair records; 2: x-pair
 // records and exact skipping of empty bricks (RGB field mode only: a sample
 // whose eight corner records are all zero adds exactly nothing and leaves the
