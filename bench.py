@@ -36,13 +36,19 @@ METRIC = "ray samples/s (fwd+adjoint) and recon iters/s at 128^3×8 views; p50/p
 WORKLOAD = dict(name="full_rte_128^3_8x512^2", n=128, views=8, side=512, step=0.5, seed=2,
                 alpha_l=2e-4, noise=1e-3, hull=True)
 # kernels one step (one fr_reconstruct iteration) launches: hull clear with
-# brick marks and its brick box, in-scatter sweeps (3), pair pack (inside the
+# brick marks and their box, in-scatter sweeps (3), pair pack (inside the
 # hull's bricks; the forward clips to their box), forward (which lists the
-# flame rays), error reduction, adjustment, update (with the hull clear), rmse
-KERNELS_PER_STEP = 11
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures of
-# the current kernels at this workload (None where the kernel changed since)
-NCU_TRAFFIC = {("fwd", "f32"): None, ("adj", "f32"): None}
+# flame rays), error reduction (which also writes the rmse), adjustment,
+# update (with the hull clear)
+KERNELS_PER_STEP = 9
+# dram__bytes_read.sum + dram__bytes_write.sum and smsp__inst_executed.sum
+# (warp instructions) per launch from ncu captures of the current kernels at
+# this workload (None where the kernel changed since)
+NCU_TRAFFIC = {("fwd", "f32"): 38.96e6 + 1.93e6, ("adj", "f32"): 18.26e6 + 0.0}
+NCU_INST = {("fwd", "f32"): 164.12e6, ("adj", "f32"): 217.51e6}
+# instruction issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock
+# at the 2070 MHz maximum SM clock, in warp instructions per second
+ISSUE_PEAK = 152 * 4 * 2.07e9
 
 
 def parse():
@@ -330,9 +336,9 @@ def run_ours(args, ws, rank, local):
     rec = 16 if args.storage == "f32" else 8
     sig = 4 if args.storage == "f32" else 2
     kernels = {"fwd": dict(per_sample=8 * rec, samples=n_fwd, seconds=t_fwd,
-                           traffic=NCU_TRAFFIC.get(("fwd", args.storage))),
+                           traffic=NCU_TRAFFIC.get(("fwd", args.storage)), inst=NCU_INST.get(("fwd", args.storage))),
                "adj": dict(per_sample=8 * sig + 8 * 16, samples=n_adj, seconds=t_adj,
-                           traffic=NCU_TRAFFIC.get(("adj", args.storage)))}
+                           traffic=NCU_TRAFFIC.get(("adj", args.storage)), inst=NCU_INST.get(("adj", args.storage)))}
     dom = max(kernels, key=lambda k: kernels[k]["seconds"])
     K = kernels[dom]
     achieved = K["per_sample"] * K["samples"] / K["seconds"] / 1e9
@@ -367,8 +373,15 @@ def run_ours(args, ws, rank, local):
                      "bytes_per_sample": K["per_sample"], "samples_per_launch": K["samples"],
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
                      else "fallback 6.8 TB/s",
-                     "note": "gather bytes are served by L1/L2 (the volume stays in the 129 MB L2); "
-                             "DRAM traffic per launch is `traffic`, far below the gather bytes"},
+                     "note": "gather bytes are served by L1/L2 (the volume stays in the 129 MB L2; DRAM "
+                             "traffic per launch is `traffic`, far below them) and the adjustment's key-point "
+                             "window issues one reduction per key point a ray leaves, not one per sample-corner, "
+                             "so frac can exceed 1; the binding limit is instruction issue (`issue`)",
+                     "issue": None if K["inst"] is None else {
+                         "warp_instructions_per_launch": K["inst"], "achieved_per_s": K["inst"] / K["seconds"],
+                         "peak_per_s": ISSUE_PEAK, "frac": K["inst"] / K["seconds"] / ISSUE_PEAK,
+                         "source": "smsp__inst_executed.sum of one ncu capture; peak 152 SMs x 4 schedulers x "
+                                   "2070 MHz"}},
         "clocks": clk.summary(),
         "rmse_after": [float(x) for x in rmse_now[0]],
         "until_converged": until,

@@ -39,6 +39,10 @@ struct fr_ctx {
     Buf hull_bricks;                 // bricks holding a key point inside the visual hull
     Buf loop;                        // device iteration counter of fr_reconstruct_until
     Buf fin;                         // multi-CTA error reduction: part sums and its counter (kept 0)
+    // dV holds zeros over its first dV_zero_bytes when dV.p == dV_zero_at: a
+    // completed reconstruction leaves it so (each update zeroes what it adds)
+    const void* dV_zero_at = nullptr;
+    size_t dV_zero_bytes = 0;
     Buf verr;                        // volume-error partials and result
     Buf L6;                          // directional radiances for anisotropic in-scattering
     Buf hull, sat;                   // visual hull tags, flame-mask tables

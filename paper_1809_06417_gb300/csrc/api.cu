@@ -679,7 +679,13 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
         FR_CUDA(c, cudaMemcpyAsync(c->targets.p, targets, ib, cudaMemcpyHostToDevice, s));
         tg = static_cast<const float*>(c->targets.p);
     }
-    FR_CUDA(c, cudaMemsetAsync(c->dV.p, 0, (size_t)nodes * comp * 4, s));
+    const size_t dv_bytes = (size_t)nodes * comp * 4;
+    if (c->dV_zero_at != c->dV.p || c->dV_zero_bytes < dv_bytes) FR_CUDA(c, cudaMemsetAsync(c->dV.p, 0, dv_bytes, s));
+    c->dV_zero_at = nullptr;   // until this call completes
+    auto loop_done = [&]() {
+        c->dV_zero_at = c->dV.p;
+        c->dV_zero_bytes = dv_bytes;
+    };
 
     static thread_local SingleArgs f, u;
     fill_problem(vol, cams, ncam, p, f);
@@ -741,6 +747,7 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     if (pack_keep) f.p.occ_box = u.p.adj_box;
     void* fin = nullptr;
     FR_TRY(fin_scratch(c, &fin));
+    float* rmse_dev = static_cast<float*>(c->rmse.p);
     FR_TRY(trace_mark(c, FR_PHASE_SETUP));
     // One iteration on stream st.  it >= 0: per-iteration slots it; it < 0:
     // slot 0 and the iteration index read on the device (graph body).
@@ -816,7 +823,8 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
             view_problem(v, slot);
             FR_CUDA(c, launch_fwd(fv, vol->dtype, vol->kind, nt1, st));
             FR_TRY(trace_mark(c, FR_PHASE_FORWARD));
-            FR_CUDA(c, launch_finalize(fv.p.partials, nt1, sq + 4 * slot, st, v > 0, fin));
+            FR_CUDA(c, launch_finalize(fv.p.partials, nt1, sq + 4 * slot, st, v > 0, fin,
+                                       it < 0 ? nullptr : rmse_dev + 3 * slot));
             FR_TRY(trace_mark(c, FR_PHASE_REDUCE));
             if (p->rule == FR_RULE_PAPER) {
                 uv.p.iteration = first_iteration + slot;
@@ -853,7 +861,10 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
         f.p.flist_count = f.p.flist ? flame_cnt + slot : nullptr;
         FR_CUDA(c, launch_fwd(f, vol->dtype, vol->kind, nt, st));
         FR_TRY(trace_mark(c, FR_PHASE_FORWARD));
-        FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * slot, st, 0, fin));
+        // the error sums and (outside the graph loop, whose converge kernel
+        // records it) the error measure of this iteration
+        FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * slot, st, 0, fin,
+                                   it < 0 ? nullptr : rmse_dev + 3 * slot));
         FR_TRY(trace_mark(c, FR_PHASE_REDUCE));
         if (p->rule == FR_RULE_PAPER) {
             u.p.iteration = first_iteration + slot;
@@ -875,7 +886,7 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     };
     if (!until) {
         for (int it = 0; it < iters; ++it) FR_TRY(one_iteration(s, it));
-        FR_CUDA(c, launch_rmse(sq, iters, static_cast<float*>(c->rmse.p), s));
+        loop_done();
         FR_TRY(trace_mark(c, FR_PHASE_FINISH));
         if (rmse) {
             if (rmse_is_host) {
@@ -948,6 +959,7 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     if (e != cudaSuccess) return fail_graph(e, "loop counter");
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
+    loop_done();
     memcpy(&done, c->host_counter, sizeof(int));
     if (iters_done) *iters_done = done;
     if (rmse && done > 0) {

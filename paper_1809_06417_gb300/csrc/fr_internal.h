@@ -43,11 +43,13 @@ cudaError_t launch_backward_batch(const ProbDev* probs, const int* tile_start, i
 cudaError_t launch_count(const SingleArgs& a, int ntiles, cudaStream_t s);
 // scratch (nullable): kFinScratchBytes of device memory, kFinParts float4 and
 // then a counter word that is 0 before the first launch (every launch leaves
-// it 0); with it the sum runs over kFinParts CTAs, without it in one
+// it 0); with it the sum runs over kFinParts CTAs, without it in one.  rmse3
+// (nullable, with scratch only): the error measure of the final sums, as
+// launch_rmse writes it.
 constexpr int kFinParts = 32;
 constexpr size_t kFinScratchBytes = kFinParts * 16 + 16;
 cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cudaStream_t s, int accumulate = 0,
-                            void* scratch = nullptr);
+                            void* scratch = nullptr, float* rmse3 = nullptr);
 // flame-ray list of a problem with prepared targets: buf needs
 // flame_list_buf_entries(ntiles) entries, the total lands at
 // buf[flame_list_total_at(ntiles)]; list needs one entry per pixel at most

@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(1024) finalize_partials(const float* __restric
 
 __global__ void __launch_bounds__(256) finalize_parts(const float* __restrict__ partials, int ntiles,
                                                       float* __restrict__ out4, int accumulate,
-                                                      float4* part_sums, unsigned* done)
+                                                      float4* part_sums, unsigned* done, float* rmse3)
 {
     __shared__ float red[4][8];
     __shared__ bool last;
@@ -709,14 +709,25 @@ __global__ void __launch_bounds__(256) finalize_parts(const float* __restrict__ 
     }
     __syncthreads();
     if (!last) return;
+    __shared__ float sum4[4];
     if (threadIdx.x < 4) {
         __threadfence();
         const volatile float* ps = reinterpret_cast<const volatile float*>(part_sums);
         float t = 0.0f;
         for (int i = 0; i < (int)gridDim.x; ++i) t += ps[4 * i + threadIdx.x];
-        out4[threadIdx.x] = accumulate ? out4[threadIdx.x] + t : t;
+        t = accumulate ? out4[threadIdx.x] + t : t;
+        out4[threadIdx.x] = t;
+        sum4[threadIdx.x] = t;
     }
     if (threadIdx.x == 0) *done = 0u;
+    if (rmse3) {
+        // the error measure (as rmse_kernel computes it)
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            const float cnt = sum4[3];
+            rmse3[threadIdx.x] = cnt > 0.0f ? 255.0f * sqrtf(sum4[threadIdx.x] / cnt) : 0.0f;
+        }
+    }
 }
 
 // Flame-ray list (pixels whose prepared target is non-zero), in tile order.
@@ -952,12 +963,12 @@ cudaError_t launch_count(const SingleArgs& a, int ntiles, cudaStream_t s)
 }
 
 cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cudaStream_t s, int accumulate,
-                            void* scratch)
+                            void* scratch, float* rmse3)
 {
     if (scratch) {
         float4* part_sums = reinterpret_cast<float4*>(scratch);
         unsigned* done = reinterpret_cast<unsigned*>(part_sums + kFinParts);
-        finalize_parts<<<kFinParts, 256, 0, s>>>(partials, ntiles, out4, accumulate, part_sums, done);
+        finalize_parts<<<kFinParts, 256, 0, s>>>(partials, ntiles, out4, accumulate, part_sums, done, rmse3);
     } else {
         finalize_partials<<<1, 1024, 0, s>>>(partials, ntiles, out4, accumulate);
     }

@@ -14,51 +14,61 @@ namespace frk {
 // Apply the accumulated adjustment
 // ---------------------------------------------------------------------------
 
+// The update of node i (hull: the hull clear fused into it, see apply_kernel).
+template <int DT, int KIND>
+__device__ __forceinline__ void apply_node(void* vol, long long i, float* dV, float scale, int with_sigma,
+                                           int clamp_nonneg, int zero_dV, const unsigned* __restrict__ hull,
+                                           unsigned hull_full)
+{
+    if (hull && __ldg(hull + i) != hull_full) {
+        if constexpr (KIND == KIND_RGB) {
+            store_rgb<DT>(vol, i, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+            if (zero_dV) reinterpret_cast<float4*>(dV)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        } else {
+            store_ts<DT>(vol, i, make_float2(0.0f, 0.0f));
+            if (zero_dV) reinterpret_cast<float2*>(dV)[i] = make_float2(0.0f, 0.0f);
+        }
+        return;
+    }
+    if constexpr (KIND == KIND_RGB) {
+        float4 v = load_rgb<DT>(vol, i);
+        float4 d = reinterpret_cast<float4*>(dV)[i];
+        v.x = fmaf(scale, d.x, v.x);
+        v.y = fmaf(scale, d.y, v.y);
+        v.z = fmaf(scale, d.z, v.z);
+        if (with_sigma) v.w = fmaf(scale, d.w, v.w);
+        if (clamp_nonneg) {
+            v.x = fmaxf(v.x, 0.0f); v.y = fmaxf(v.y, 0.0f); v.z = fmaxf(v.z, 0.0f);
+            if (with_sigma) v.w = fmaxf(v.w, 0.0f);
+        }
+        store_rgb<DT>(vol, i, v);
+        if (zero_dV) reinterpret_cast<float4*>(dV)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    } else {
+        float2 v = load_ts<DT>(vol, i);
+        float2 d = reinterpret_cast<float2*>(dV)[i];
+        v.x = fmaf(scale, d.x, v.x);
+        if (with_sigma) v.y = fmaf(scale, d.y, v.y);
+        if (clamp_nonneg) {
+            v.x = fmaxf(v.x, 0.0f);
+            if (with_sigma) v.y = fmaxf(v.y, 0.0f);
+        }
+        store_ts<DT>(vol, i, v);
+        if (zero_dV) reinterpret_cast<float2*>(dV)[i] = make_float2(0.0f, 0.0f);
+    }
+}
+
 // hull (nullable): records of key points whose tag differs from hull_full
-// are set to 0 instead (the hull clear fused into the update).
+// are set to 0 instead (the hull clear fused into the update).  (A pass over
+// the visual hull's bricks only measured slower than this flat one, which
+// streams at close to the L2 bandwidth.)
 template <int DT, int KIND>
 __global__ void __launch_bounds__(256) apply_kernel(void* vol, long long nodes, float* dV, float scale,
                                                     int with_sigma, int clamp_nonneg, int zero_dV,
                                                     const unsigned* __restrict__ hull, unsigned hull_full)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
-         i += (long long)gridDim.x * blockDim.x) {
-        if (hull && __ldg(hull + i) != hull_full) {
-            if constexpr (KIND == KIND_RGB) {
-                store_rgb<DT>(vol, i, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
-                if (zero_dV) reinterpret_cast<float4*>(dV)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            } else {
-                store_ts<DT>(vol, i, make_float2(0.0f, 0.0f));
-                if (zero_dV) reinterpret_cast<float2*>(dV)[i] = make_float2(0.0f, 0.0f);
-            }
-            continue;
-        }
-        if constexpr (KIND == KIND_RGB) {
-            float4 v = load_rgb<DT>(vol, i);
-            float4 d = reinterpret_cast<float4*>(dV)[i];
-            v.x = fmaf(scale, d.x, v.x);
-            v.y = fmaf(scale, d.y, v.y);
-            v.z = fmaf(scale, d.z, v.z);
-            if (with_sigma) v.w = fmaf(scale, d.w, v.w);
-            if (clamp_nonneg) {
-                v.x = fmaxf(v.x, 0.0f); v.y = fmaxf(v.y, 0.0f); v.z = fmaxf(v.z, 0.0f);
-                if (with_sigma) v.w = fmaxf(v.w, 0.0f);
-            }
-            store_rgb<DT>(vol, i, v);
-            if (zero_dV) reinterpret_cast<float4*>(dV)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        } else {
-            float2 v = load_ts<DT>(vol, i);
-            float2 d = reinterpret_cast<float2*>(dV)[i];
-            v.x = fmaf(scale, d.x, v.x);
-            if (with_sigma) v.y = fmaf(scale, d.y, v.y);
-            if (clamp_nonneg) {
-                v.x = fmaxf(v.x, 0.0f);
-                if (with_sigma) v.y = fmaxf(v.y, 0.0f);
-            }
-            store_ts<DT>(vol, i, v);
-            if (zero_dV) reinterpret_cast<float2*>(dV)[i] = make_float2(0.0f, 0.0f);
-        }
-    }
+         i += (long long)gridDim.x * blockDim.x)
+        apply_node<DT, KIND>(vol, i, dV, scale, with_sigma, clamp_nonneg, zero_dV, hull, hull_full);
 }
 
 static int grid_for(long long n, int block)
@@ -73,8 +83,8 @@ cudaError_t launch_apply(void* vol, int dt, int kind, long long nodes, float* dV
                          unsigned hull_full)
 {
     int g = grid_for(nodes, 256);
-#define FR_APPLY(D, K) \
-    apply_kernel<D, K><<<g, 256, 0, s>>>(vol, nodes, dV, scale, with_sigma, clamp_nonneg, zero_dV, hull, hull_full)
+#define FR_APPLY(D, KD) \
+    apply_kernel<D, KD><<<g, 256, 0, s>>>(vol, nodes, dV, scale, with_sigma, clamp_nonneg, zero_dV, hull, hull_full)
     if (kind == KIND_RGB) {
         if (dt == DT_F32) FR_APPLY(DT_F32, KIND_RGB);
         else if (dt == DT_BF16) FR_APPLY(DT_BF16, KIND_RGB);
@@ -156,41 +166,15 @@ __device__ __forceinline__ void mark_bricks(unsigned char* occ, int x, int y, in
                 occ[FR_CHK(((long long)bz * nby + by) * nbx + bx, (long long)nbx * nby * nbz, 16u)] = 1;
 }
 
-// True when some brick whose corner records include node (x, y, z) is flagged.
-__device__ __forceinline__ bool node_in_flagged_brick(const unsigned char* flags, int x, int y, int z, int nbx,
-                                                      int nby, int nbz)
-{
-    constexpr int S = kBrickShift, M = kBrick - 1;
-    const int bx0 = (x > 0 && (x & M) == 0) ? (x >> S) - 1 : (x >> S);
-    const int by0 = (y > 0 && (y & M) == 0) ? (y >> S) - 1 : (y >> S);
-    const int bz0 = (z > 0 && (z & M) == 0) ? (z >> S) - 1 : (z >> S);
-    for (int bz = bz0; bz <= min(z >> S, nbz - 1); ++bz)
-        for (int by = by0; by <= min(y >> S, nby - 1); ++by)
-            for (int bx = bx0; bx <= min(x >> S, nbx - 1); ++bx)
-                if (__ldg(flags + FR_CHK(((long long)bz * nby + by) * nbx + bx, (long long)nbx * nby * nbz, 34u)))
-                    return true;
-    return false;
-}
 
-// The box of the flagged bricks of a brick table: CTA `part` of `nparts`
-// scans its share of the flags and merges its box into the table's with
-// atomicMax on the encoded values {nb - lo, hi + 1} (the table, box included,
-// is zeroed beforehand).
-__device__ __forceinline__ void brick_box_part(unsigned char* table, int nbx, int nby, int nbz, int part,
-                                               int nparts)
+// Merges the box [lo, hi) of brick coordinates seen by the CTA's threads (hi 0:
+// none) into the table's box, encoded {nb - lo, hi} per axis and merged with
+// atomicMax (the table, box included, is zeroed beforehand).  Every thread of
+// the CTA calls it.
+__device__ __forceinline__ void merge_box(unsigned char* table, int nbx, int nby, int nbz, const unsigned lo[3],
+                                          const unsigned hi[3])
 {
     __shared__ unsigned red[6][32];
-    const int nb = nbx * nby * nbz;
-    unsigned lo[3] = {UINT_MAX, UINT_MAX, UINT_MAX}, hi[3] = {0u, 0u, 0u};
-    for (int b = part * blockDim.x + threadIdx.x; b < nb; b += nparts * blockDim.x) {
-        if (!table[b]) continue;
-        const unsigned c[3] = {(unsigned)(b % nbx), (unsigned)((b / nbx) % nby), (unsigned)(b / (nbx * nby))};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = min(lo[a], c[a]);
-            hi[a] = max(hi[a], c[a] + 1u);
-        }
-    }
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -212,6 +196,27 @@ __device__ __forceinline__ void brick_box_part(unsigned char* table, int nbx, in
             }
         }
     }
+}
+
+// The box of the flagged bricks of a brick table: CTA `part` of `nparts`
+// scans its share of the flags and merges its box into the table's with
+// atomicMax on the encoded values {nb - lo, hi + 1} (the table, box included,
+// is zeroed beforehand).
+__device__ __forceinline__ void brick_box_part(unsigned char* table, int nbx, int nby, int nbz, int part,
+                                               int nparts)
+{
+    const int nb = nbx * nby * nbz;
+    unsigned lo[3] = {UINT_MAX, UINT_MAX, UINT_MAX}, hi[3] = {0u, 0u, 0u};
+    for (int b = part * blockDim.x + threadIdx.x; b < nb; b += nparts * blockDim.x) {
+        if (!table[b]) continue;
+        const unsigned c[3] = {(unsigned)(b % nbx), (unsigned)((b / nbx) % nby), (unsigned)(b / (nbx * nby))};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = min(lo[a], c[a]);
+            hi[a] = max(hi[a], c[a] + 1u);
+        }
+    }
+    merge_box(table, nbx, nby, nbz, lo, hi);
 }
 
 constexpr int kBoxParts = 16;   // CTAs per brick table
@@ -257,47 +262,107 @@ static cudaError_t launch_brick_box(unsigned char* table, int nx, int ny, int nz
     return cudaGetLastError();
 }
 
-// Flat over the nodes (every thread busy whatever nx is): pair i = {record i,
-// record of its +x neighbour} (itself on the last x), and the brick marks of
-// the non-zero records.
+// A brick table whose flagged-off bricks hold zero records (flags nullable:
+// none): the nodes of those bricks are read by no forward sample.
+struct KeepBricks {
+    const unsigned char* flags;
+    int nx, ny, nbx, nby, nbz;
+};
+
+// Nodes owned by brick (bx, by, bz): [B b, B b + B) along each axis, the last
+// brick along an axis owning the nodes up to n - 1 as well (B = kBrick).  The
+// bricks that hold an owned node are the brick itself and its lower
+// neighbours, so when none of those is flagged in a table whose flagged-off
+// bricks hold zero records, the owned nodes need no pass.
+struct OwnedNodes {
+    int x0, y0, z0, ex, ey, ez;
+    bool active;
+};
+
+__device__ __forceinline__ OwnedNodes owned_nodes(const KeepBricks& K, int nz, int b)
+{
+    OwnedNodes o;
+    const int bx = b % K.nbx, r = b / K.nbx, by = r % K.nby, bz = r / K.nby;
+    o.active = false;
+    for (int cz = max(bz - 1, 0); cz <= bz; ++cz)
+        for (int cy = max(by - 1, 0); cy <= by; ++cy)
+            for (int cx = max(bx - 1, 0); cx <= bx; ++cx)
+                o.active |= __ldg(K.flags + FR_CHK(((long long)cz * K.nby + cy) * K.nbx + cx,
+                                                   (long long)K.nbx * K.nby * K.nbz, 40u)) != 0;
+    o.x0 = bx * kBrick; o.y0 = by * kBrick; o.z0 = bz * kBrick;
+    o.ex = bx == K.nbx - 1 ? K.nx - o.x0 : kBrick;
+    o.ey = by == K.nby - 1 ? K.ny - o.y0 : kBrick;
+    o.ez = bz == K.nbz - 1 ? nz - o.z0 : kBrick;
+    return o;
+}
+
+// Pair i = {record i, record of its +x neighbour} (itself on the last x) of
+// node (x, y, z), and the brick marks of the non-zero records.
+template <int DT, int KIND>
+__device__ __forceinline__ void pack_node(const void* src, void* dst, long long i, int x, int y, int z, int nx,
+                                          unsigned char* occ, int nbx, int nby, int nbz)
+{
+    const long long j = x < nx - 1 ? i + 1 : i;
+    if constexpr (KIND == KIND_RGB) {
+        bool nonzero;
+        if constexpr (DT == DT_F32) {
+            const float4* s4 = reinterpret_cast<const float4*>(src);
+            float4* d4 = reinterpret_cast<float4*>(dst);
+            const float4 a = __ldg(s4 + i);
+            d4[2 * i] = a;
+            d4[2 * i + 1] = __ldg(s4 + j);
+            nonzero = a.x != 0.0f || a.y != 0.0f || a.z != 0.0f || a.w != 0.0f;
+        } else {
+            const uint2* s2 = reinterpret_cast<const uint2*>(src);
+            const uint2 a = __ldg(s2 + i), b = __ldg(s2 + j);
+            reinterpret_cast<uint4*>(dst)[i] = make_uint4(a.x, a.y, b.x, b.y);
+            nonzero = ((a.x | a.y) & 0x7fff7fffu) != 0u;   // +0 and -0 both read as empty
+        }
+        if (occ && nonzero) mark_bricks(occ, x, y, z, nbx, nby, nbz);
+    } else {
+        if constexpr (DT == DT_F32) {
+            const float2* s2 = reinterpret_cast<const float2*>(src);
+            const float2 a = __ldg(s2 + i), b = __ldg(s2 + j);
+            reinterpret_cast<float4*>(dst)[i] = make_float4(a.x, a.y, b.x, b.y);
+        } else {
+            const unsigned* s1 = reinterpret_cast<const unsigned*>(src);
+            reinterpret_cast<uint2*>(dst)[i] = make_uint2(__ldg(s1 + i), __ldg(s1 + j));
+        }
+    }
+}
+
+// Flat over the nodes (every thread busy whatever nx is).
 template <int DT, int KIND>
 __global__ void __launch_bounds__(256) pair_pack_kernel(const void* src, void* dst, long long nodes, int nx, int ny,
-                                                        unsigned char* occ, int nbx, int nby, int nbz,
-                                                        const unsigned char* keep)
+                                                        unsigned char* occ, int nbx, int nby, int nbz)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
          i += (long long)gridDim.x * blockDim.x) {
-        const long long row = i / nx;
-        const int x = (int)(i - row * nx);
-        // a node of no kept brick is read by no forward sample
-        if (keep && !node_in_flagged_brick(keep, x, (int)(row % ny), (int)(row / ny), nbx, nby, nbz)) continue;
-        const long long j = x < nx - 1 ? i + 1 : i;
-        if constexpr (KIND == KIND_RGB) {
-            bool nonzero;
-            if constexpr (DT == DT_F32) {
-                const float4* s4 = reinterpret_cast<const float4*>(src);
-                float4* d4 = reinterpret_cast<float4*>(dst);
-                const float4 a = __ldg(s4 + i);
-                d4[2 * i] = a;
-                d4[2 * i + 1] = __ldg(s4 + j);
-                nonzero = a.x != 0.0f || a.y != 0.0f || a.z != 0.0f || a.w != 0.0f;
-            } else {
-                const uint2* s2 = reinterpret_cast<const uint2*>(src);
-                const uint2 a = __ldg(s2 + i), b = __ldg(s2 + j);
-                reinterpret_cast<uint4*>(dst)[i] = make_uint4(a.x, a.y, b.x, b.y);
-                nonzero = ((a.x | a.y) & 0x7fff7fffu) != 0u;   // +0 and -0 both read as empty
-            }
-            if (occ && nonzero) mark_bricks(occ, x, (int)(row % ny), (int)(row / ny), nbx, nby, nbz);
-        } else {
-            if constexpr (DT == DT_F32) {
-                const float2* s2 = reinterpret_cast<const float2*>(src);
-                const float2 a = __ldg(s2 + i), b = __ldg(s2 + j);
-                reinterpret_cast<float4*>(dst)[i] = make_float4(a.x, a.y, b.x, b.y);
-            } else {
-                const unsigned* s1 = reinterpret_cast<const unsigned*>(src);
-                reinterpret_cast<uint2*>(dst)[i] = make_uint2(__ldg(s1 + i), __ldg(s1 + j));
-            }
-        }
+        // node coordinates in 32-bit arithmetic (volumes hold < 2^31 nodes)
+        const unsigned row = (unsigned)i / (unsigned)nx;
+        const int x = (int)((unsigned)i - row * (unsigned)nx);
+        const unsigned z = row / (unsigned)ny;
+        const int y = (int)(row - z * (unsigned)ny);
+        pack_node<DT, KIND>(src, dst, i, x, y, (int)z, nx, occ, nbx, nby, nbz);
+    }
+}
+
+// Over the owned nodes of the active bricks of `keep` only, one warp per brick
+// (a node of an inactive brick is read by no forward sample).
+template <int DT, int KIND>
+__global__ void __launch_bounds__(256) pair_pack_bricks_kernel(const void* src, void* dst, int nz, unsigned char* occ,
+                                                               KeepBricks keep)
+{
+    const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (b >= keep.nbx * keep.nby * keep.nbz) return;
+    const OwnedNodes o = owned_nodes(keep, nz, b);
+    if (!o.active) return;
+    const int exy = o.ex * o.ey, cnt = exy * o.ez;
+    for (int t = lane; t < cnt; t += 32) {
+        const int dz = t / exy, r = t - dz * exy, dy = r / o.ex, dx = r - dy * o.ex;
+        const int x = o.x0 + dx, y = o.y0 + dy, z = o.z0 + dz;
+        const long long i = ((long long)z * keep.ny + y) * keep.nx + x;
+        pack_node<DT, KIND>(src, dst, i, x, y, z, keep.nx, occ, keep.nbx, keep.nby, keep.nbz);
     }
 }
 
@@ -353,7 +418,11 @@ cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int n
         cudaError_t e = cudaMemsetAsync(occ, 0, brick_table_bytes(nx, ny, nz), s);
         if (e != cudaSuccess) return e;
     }
-#define FR_PACK(D, K) pair_pack_kernel<D, K><<<g, 256, 0, s>>>(src, dst, nodes, nx, ny, occ, nbx, nby, nbz, keep)
+    const KeepBricks KB{keep, nx, ny, nbx, nby, nbz};
+    const unsigned gb = (unsigned)(((long long)nbx * nby * nbz * 32 + 255) / 256);
+#define FR_PACK(D, K)                                                                        \
+    if (keep) pair_pack_bricks_kernel<D, K><<<gb, 256, 0, s>>>(src, dst, nz, occ, KB);      \
+    else pair_pack_kernel<D, K><<<g, 256, 0, s>>>(src, dst, nodes, nx, ny, occ, nbx, nby, nbz)
     if (kind == KIND_RGB) {
         if (dt == DT_F32) FR_PACK(DT_F32, KIND_RGB);
         else if (dt == DT_BF16) FR_PACK(DT_BF16, KIND_RGB);
@@ -1230,15 +1299,27 @@ __global__ void __launch_bounds__(256) hull_clear_kernel(void* vol, int nx, int 
                                                          unsigned char* flags, int nbx, int nby, int nbz)
 {
     const long long nodes = (long long)nx * ny * nz;
+    // box of the bricks this thread flags (merged into the table's box below)
+    unsigned lo[3] = {UINT_MAX, UINT_MAX, UINT_MAX}, hi[3] = {0u, 0u, 0u};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
          i += (long long)gridDim.x * blockDim.x) {
         if (__ldg(tags + i) != full) {
             if (vol) store_rgb<DT>(vol, i, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
         } else if (flags) {
-            const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+            const unsigned row = (unsigned)i / (unsigned)nx, zu = row / (unsigned)ny;
+            const int x = (int)((unsigned)i - row * (unsigned)nx), y = (int)(row - zu * (unsigned)ny), z = (int)zu;
             mark_bricks(flags, x, y, z, nbx, nby, nbz);
+            const int c[3] = {x, y, z}, nb[3] = {nbx, nby, nbz};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                constexpr int S = kBrickShift, M = kBrick - 1;
+                const int b0 = (c[a] > 0 && (c[a] & M) == 0) ? (c[a] >> S) - 1 : (c[a] >> S);
+                lo[a] = min(lo[a], (unsigned)b0);
+                hi[a] = max(hi[a], (unsigned)min(c[a] >> S, nb[a] - 1) + 1u);
+            }
         }
     }
+    if (flags) merge_box(flags, nbx, nby, nbz, lo, hi);
 }
 
 cudaError_t launch_hull_clear(void* vol, int dt, int nx, int ny, int nz, const unsigned* tags, unsigned full,
@@ -1256,11 +1337,6 @@ cudaError_t launch_hull_clear(void* vol, int dt, int nx, int ny, int nz, const u
     else if (dt == DT_BF16) FR_CLEAR(DT_BF16);
     else FR_CLEAR(DT_F16);
 #undef FR_CLEAR
-    if (flags) {
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        return launch_brick_box(flags, nx, ny, nz, s);
-    }
     return cudaGetLastError();
 }
 
