@@ -284,6 +284,20 @@ def run_ours(args, ws, rank, local):
     ref_max = float(ref[..., :3].max())
     del ref
 
+    # the visual hull of the job (Sec. 4.3.1, Algorithm 1): the flame masks'
+    # summed-area tables and the per-node tags, event-timed over 10 calls
+    tags_h = torch.empty_like(I["tags"])
+    ctx.fr_visual_hull(fv, cams, I["targets"], fr.params(), tags_h)
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    for _ in range(10):
+        ctx.fr_visual_hull(fv, cams, I["targets"], fr.params(), tags_h)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    hull_ms = h0.elapsed_time(h1) / 10
+    hull_same = bool(torch.equal(tags_h, I["tags"]))
+    del tags_h
+
     # the variants the paper mentions without using, on the same workload:
     # anisotropic in-scattering (Eq. 9) and sequential per-view updates
     variants = {}
@@ -385,6 +399,8 @@ def run_ours(args, ws, rank, local):
         "clocks": clk.summary(),
         "rmse_after": [float(x) for x in rmse_now[0]],
         "until_converged": until,
+        "visual_hull": {"ms": hull_ms, "views": w["views"], "grid": [w["n"]] * 3, "image": [w["side"]] * 2,
+                        "same_tags_as_setup": hull_same},
         "variants": variants,
         "volume_rmse_in_hull": {"rmse": [float(x) for x in v_rmse], "key_points": v_n,
                                 "relative_to_max": [float(x) / ref_max for x in v_rmse],

@@ -878,6 +878,150 @@ __global__ void __launch_bounds__(256) sweep_x_kernel(const void* em, float* J, 
     }
 }
 
+// The y / z sweep with the CTA's 32 lines staged in shared memory: one
+// coalesced pass loads every record of the lines (n_line x 32 float4), so the
+// chunks' walks read shared memory instead of waiting on global loads, and the
+// kernel holds few registers (two CTAs per SM).  J of a chunk of at most CM
+// nodes stays in registers.  The arithmetic and its order are those of
+// sweep_reg_kernel.
+#ifndef FR_SWEEP_SMEM_MINB
+#define FR_SWEEP_SMEM_MINB 2
+#endif
+template <int DT, int AXIS, bool LAST, int CM>
+__global__ void __launch_bounds__(kSweepLines * kSweepChunks, FR_SWEEP_SMEM_MINB) sweep_smem_kernel(const void* em,
+                                                                                   const float* albedo, float* J,
+                                                                                   void* out, int nx, int ny, int nz,
+                                                                                   bool skip_empty)
+{
+    extern __shared__ float4 recs[];   // [node along the line][line of the CTA]
+    __shared__ float4 fwd[kSweepChunks][kSweepLines];
+    __shared__ float4 bwd[kSweepChunks][kSweepLines];
+    const int n_line = AXIS == 1 ? ny : nz;
+    const long long lines = AXIS == 1 ? (long long)nx * nz : (long long)nx * ny;
+    const long long stride = AXIS == 1 ? (long long)nx : (long long)nx * ny;
+    const long long nodes = (long long)nx * ny * nz;
+    auto line_start = [&](long long ln) -> long long {
+        if constexpr (AXIS == 1) {
+            const long long z = ln / nx;
+            return z * (long long)nx * ny + (ln - z * nx);   // line = z * nx + x
+        } else {
+            return ln;                                       // line = y * nx + x
+        }
+    };
+    const int tid = threadIdx.y * kSweepLines + threadIdx.x;
+    const long long line0 = blockIdx.x * (long long)kSweepLines;
+    for (int e = tid; e < n_line * kSweepLines; e += kSweepLines * kSweepChunks) {
+        const int i = e / kSweepLines, l = e - i * kSweepLines;
+        float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (line0 + l < lines) r = load_rgb<DT>(em, FR_CHK(line_start(line0 + l) + i * stride, nodes, 41u));
+        recs[e] = r;
+    }
+    const long long line = line0 + threadIdx.x;
+    const int ch = threadIdx.y;
+    const bool live = line < lines;
+    const long long start = live ? line_start(line) : 0;
+    const int m = (n_line + kSweepChunks - 1) / kSweepChunks;
+    const int s0 = min(ch * m, n_line), s1 = min(s0 + m, n_line), cnt = s1 - s0;   // cnt <= CM
+    auto rec = [&](int i) -> float4 { return recs[i * kSweepLines + threadIdx.x]; };
+    float3 jv[CM];
+    float alb[CM];
+    if (live && cnt > 0) {
+        // J (earlier sweeps) and albedo of the chunk's nodes, in flight during the staging
+        float4* J4 = reinterpret_cast<float4*>(J);
+#pragma unroll
+        for (int q = 0; q < CM; ++q) {
+            if (q < cnt) {
+                const long long node = start + (s0 + q) * stride;
+                const float4 t = J4[node];
+                jv[q] = make_float3(t.x, t.y, t.z);
+                if constexpr (LAST) alb[q] = __ldg(albedo + node);
+            }
+        }
+    }
+    __syncthreads();
+    float Ef = 1.0f, F0 = 0.0f, F1 = 0.0f, F2 = 0.0f;
+    float Eb = 1.0f, B0 = 0.0f, B1 = 0.0f, B2 = 0.0f;
+    bool occupied = false;
+    if (live && cnt > 0) {
+        for (int q = 0; q < cnt; ++q) occupied |= nonzero_record(rec(s0 + q));
+        // phase 1: the chunk's forward and backward maps; segment j joins
+        // nodes s0 - 1 + j and s0 + j
+        for (int j = 0; j <= cnt; ++j) {
+            const int i = s0 + j;
+            if (i >= 1 && i <= n_line - 1) {
+                const Seg g = seg_between<DT>(rec(i - 1), rec(i));
+                if (j < cnt) {
+                    F0 = fmaf(F0, g.e, g.c0); F1 = fmaf(F1, g.e, g.c1); F2 = fmaf(F2, g.e, g.c2);
+                    Ef *= g.e;
+                }
+                if (j >= 1) {
+                    B0 = fmaf(Eb, g.c0, B0); B1 = fmaf(Eb, g.c1, B1); B2 = fmaf(Eb, g.c2, B2);
+                    Eb *= g.e;
+                }
+            }
+        }
+    }
+    fwd[ch][threadIdx.x] = make_float4(Ef, F0, F1, F2);
+    bwd[ch][threadIdx.x] = make_float4(Eb, B0, B1, B2);
+    __syncthreads();
+    if (!live || cnt <= 0) return;
+    if (skip_empty && !occupied) {
+        if constexpr (LAST) {
+            for (int q = 0; q < cnt; ++q)
+                store_rgb<DT>(out, FR_CHK(start + (s0 + q) * stride, nodes, 42u), make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+        }
+        return;
+    }
+    // phase 2: radiance arriving at the chunk from either side
+    float lf0 = 0.0f, lf1 = 0.0f, lf2 = 0.0f;
+    for (int c = 0; c < ch; ++c) {
+        const float4 f = fwd[c][threadIdx.x];
+        lf0 = fmaf(lf0, f.x, f.y); lf1 = fmaf(lf1, f.x, f.z); lf2 = fmaf(lf2, f.x, f.w);
+    }
+    float lb0 = 0.0f, lb1 = 0.0f, lb2 = 0.0f;
+    for (int c = kSweepChunks - 1; c > ch; --c) {
+        const float4 b = bwd[c][threadIdx.x];
+        lb0 = fmaf(lb0, b.x, b.y); lb1 = fmaf(lb1, b.x, b.z); lb2 = fmaf(lb2, b.x, b.w);
+    }
+    // phase 3: forward walk (J += L_forward / 6, in registers) ...
+    const float sixth = 1.0f / 6.0f;
+#pragma unroll
+    for (int q = 0; q < CM; ++q) {
+        if (q < cnt) {
+            const int i = s0 + q;
+            if (i > 0) {
+                const Seg g = seg_between<DT>(rec(i - 1), rec(i));
+                lf0 = fmaf(lf0, g.e, g.c0); lf1 = fmaf(lf1, g.e, g.c1); lf2 = fmaf(lf2, g.e, g.c2);
+            }
+            jv[q].x = fmaf(lf0, sixth, jv[q].x); jv[q].y = fmaf(lf1, sixth, jv[q].y);
+            jv[q].z = fmaf(lf2, sixth, jv[q].z);
+        }
+    }
+    // ... and backward walk (J += L_backward / 6; stored, or the source written)
+    float4* J4 = reinterpret_cast<float4*>(J);
+#pragma unroll
+    for (int q = CM - 1; q >= 0; --q) {
+        if (q < cnt) {
+            const int i = s0 + q;
+            if (i < n_line - 1) {
+                const Seg g = seg_between<DT>(rec(i), rec(i + 1));
+                lb0 = fmaf(lb0, g.e, g.c0); lb1 = fmaf(lb1, g.e, g.c1); lb2 = fmaf(lb2, g.e, g.c2);
+            }
+            const float jx = fmaf(lb0, sixth, jv[q].x), jy = fmaf(lb1, sixth, jv[q].y), jz = fmaf(lb2, sixth, jv[q].z);
+            const long long node = FR_CHK(start + i * stride, nodes, 43u);
+            if constexpr (LAST) {
+                const float4 cur = rec(i);
+                const float as = alb[q] * cur.w;
+                store_rgb<DT>(out, node, make_float4(fmaf(as, jx, cur.x), fmaf(as, jy, cur.y), fmaf(as, jz, cur.z),
+                                                     cur.w));
+                if (!skip_empty) J4[node] = make_float4(jx, jy, jz, 0.0f);
+            } else {
+                J4[node] = make_float4(jx, jy, jz, 0.0f);
+            }
+        }
+    }
+}
+
 // The x sweep with a chunk of at most CM nodes held in registers (see
 // sweep_reg_kernel; the same arithmetic as sweep_x_kernel in the same order).
 template <int DT, int CM>
@@ -983,12 +1127,37 @@ __global__ void __launch_bounds__(256) sweep_x_reg_kernel(const void* em, float*
 #define FR_SWEEP_REG_MAX 8
 #endif
 
+// Lines whose records fit in kSweepSmemMax bytes of shared memory per CTA run
+// the staged kernel (0: never).
+#ifndef FR_SWEEP_SMEM_MAX
+#define FR_SWEEP_SMEM_MAX 0
+#endif
+
+template <int DT, int AXIS, bool LAST, int CM>
+static void launch_sweep_smem(unsigned grid, size_t smem, const void* em, const float* albedo, float* J, void* out,
+                              int nx, int ny, int nz, cudaStream_t s, bool skip_empty)
+{
+    static bool attr = false;   // the shared-memory opt-in, set once per instantiation
+    if (!attr && smem > 48 * 1024) {
+        cudaFuncSetAttribute(sweep_smem_kernel<DT, AXIS, LAST, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             FR_SWEEP_SMEM_MAX);
+        attr = true;
+    }
+    sweep_smem_kernel<DT, AXIS, LAST, CM><<<grid, dim3(kSweepLines, kSweepChunks), smem, s>>>(em, albedo, J, out, nx,
+                                                                                            ny, nz, skip_empty);
+}
+
 template <int DT, int AXIS, bool LAST>
 static void launch_sweep_yz(int m, unsigned grid, const void* em, const float* albedo, float* J, void* out, int nx,
                             int ny, int nz, cudaStream_t s, bool skip_empty)
 {
     const dim3 B(kSweepLines, kSweepChunks);
-    if (FR_SWEEP_REG_MAX >= 4 && m <= 4)
+    const int n_line = AXIS == 1 ? ny : nz;
+    const size_t smem = (size_t)n_line * kSweepLines * sizeof(float4);
+    if (smem <= (size_t)FR_SWEEP_SMEM_MAX && m <= 8) {
+        if (m <= 4) launch_sweep_smem<DT, AXIS, LAST, 4>(grid, smem, em, albedo, J, out, nx, ny, nz, s, skip_empty);
+        else launch_sweep_smem<DT, AXIS, LAST, 8>(grid, smem, em, albedo, J, out, nx, ny, nz, s, skip_empty);
+    } else if (FR_SWEEP_REG_MAX >= 4 && m <= 4)
         sweep_reg_kernel<DT, AXIS, LAST, 4><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, skip_empty);
     else if (FR_SWEEP_REG_MAX >= 8 && m <= 8)
         sweep_reg_kernel<DT, AXIS, LAST, 8><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, skip_empty);
@@ -1187,33 +1356,66 @@ cudaError_t launch_prepare_targets(float* targets, int ncam, int H, int W, float
 
 // Summed-area table of the flame mask: sat[v][y+1][x+1] = number of flame
 // pixels in [0, x] x [0, y] of view v (row 0 and column 0 are zero).
-__global__ void sat_rows_kernel(const float* targets, int ncam, int W, int H, float thresh, unsigned* sat)
+// Summed-area table of each view's flame mask, (H + 1) x (W + 1) per view:
+// entry (y, x) counts the flame pixels in image rows < y and columns < x.
+// Pass 1: row prefix sums, one warp per table row, 32 columns per step with a
+// shuffle scan.
+__global__ void __launch_bounds__(256) sat_rows_kernel(const float* targets, int ncam, int W, int H, float thresh,
+                                                       unsigned* sat)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= ncam * (H + 1)) return;
+    const unsigned FULL = 0xffffffffu;
+    const int r = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (r >= ncam * (H + 1)) return;   // whole warps leave together
     const int v = r / (H + 1), y = r - v * (H + 1);
     unsigned* row = sat + (size_t)r * (W + 1);
-    row[0] = 0;
-    unsigned acc = 0;
-    for (int x = 0; x < W; ++x) {
-        if (y > 0) {
+    if (lane == 0) row[0] = 0;
+    unsigned carry = 0;
+    for (int x0 = 0; x0 < W; x0 += 32) {
+        const int x = x0 + lane;
+        unsigned f = 0;
+        if (y > 0 && x < W) {
             const float* t = targets + 3 * (((size_t)v * H + (y - 1)) * W + x);
-            acc += fmaxf(t[0], fmaxf(t[1], t[2])) > thresh ? 1u : 0u;
+            f = fmaxf(t[0], fmaxf(t[1], t[2])) > thresh ? 1u : 0u;
         }
-        row[x + 1] = acc;
+        unsigned incl = f;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned n = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += n;
+        }
+        if (x < W) row[x + 1] = carry + incl;
+        carry += __shfl_sync(FULL, incl, 31);
     }
 }
 
-__global__ void sat_cols_kernel(int ncam, int W, int H, unsigned* sat)
+// Pass 2: column prefix sums.  A CTA takes 32 neighbouring columns of one view
+// (threadIdx.x) in kSatChunks row chunks (threadIdx.y): each chunk sums its
+// rows, the chunks' sums are combined in shared memory, then each chunk
+// rewrites its rows from its offset.
+constexpr int kSatChunks = 16;
+
+__global__ void __launch_bounds__(32 * kSatChunks) sat_cols_kernel(int ncam, int W, int H, unsigned* sat)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncam * (W + 1)) return;
-    const int v = c / (W + 1), x = c - v * (W + 1);
-    unsigned* base = sat + (size_t)v * (H + 1) * (W + 1) + x;
+    __shared__ unsigned part[kSatChunks][32];
+    const int tiles = (W + 1 + 31) / 32;
+    const int v = blockIdx.x / tiles, tile = blockIdx.x - v * tiles;
+    const int x = tile * 32 + threadIdx.x, ch = threadIdx.y;
+    const bool live = v < ncam && x <= W;
+    const int rows = H + 1, m = (rows + kSatChunks - 1) / kSatChunks;
+    const int y0 = min(ch * m, rows), y1 = min(y0 + m, rows);
+    const size_t w1 = (size_t)W + 1;
+    unsigned* base = sat + (size_t)v * rows * w1 + x;
+    unsigned sum = 0;
+    if (live)
+        for (int y = y0; y < y1; ++y) sum += base[y * w1];
+    part[ch][threadIdx.x] = sum;
+    __syncthreads();
+    if (!live) return;
     unsigned acc = 0;
-    for (int y = 0; y <= H; ++y) {
-        acc += base[(size_t)y * (W + 1)];
-        base[(size_t)y * (W + 1)] = acc;
+    for (int c = 0; c < ch; ++c) acc += part[c][threadIdx.x];
+    for (int y = y0; y < y1; ++y) {
+        acc += base[y * w1];
+        base[y * w1] = acc;
     }
 }
 
@@ -1222,58 +1424,96 @@ __device__ __forceinline__ float dot3_rn(float x, float y, float z, const float 
     return __fadd_rn(__fadd_rn(__fmul_rn(x, r[0]), __fmul_rn(y, r[1])), __fmul_rn(z, r[2]));
 }
 
-// One thread per node; `cams` carries o (voxel units), r, u, f, tx, ty, W, H.
+// `cams` carries o (voxel units), r, u, f, tx, ty, W, H.
 struct HullCams {
     CamDev c[kMaxViews];
 };
 
-__global__ void __launch_bounds__(256) hull_kernel(const __grid_constant__ HullCams cams, int ncam, int nx, int ny,
-                                                   int nz, const unsigned* __restrict__ sat,
-                                                   unsigned* __restrict__ tags)
+// Pixel coordinates of lattice point (gx, gy, gz) in view c (float32, the
+// rounding of each step fixed); false when it is not in front of the camera.
+__device__ __forceinline__ bool hull_project(const CamDev& c, int gx, int gy, int gz, float& uu, float& vv)
 {
-    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long nodes = (long long)nx * ny * nz;
-    if (idx >= nodes) return;
-    const int i = (int)(idx % nx), j = (int)((idx / nx) % ny), k = (int)(idx / ((long long)nx * ny));
-    const int lo[3] = {max(i - 1, 0), max(j - 1, 0), max(k - 1, 0)};
-    const int hi[3] = {min(i + 1, nx - 1), min(j + 1, ny - 1), min(k + 1, nz - 1)};
+    const float X = __fsub_rn((float)gx, c.o[0]), Y = __fsub_rn((float)gy, c.o[1]), Z = __fsub_rn((float)gz, c.o[2]);
+    const float xc = dot3_rn(X, Y, Z, c.r), yc = dot3_rn(X, Y, Z, c.u), zc = dot3_rn(X, Y, Z, c.f);
+    if (!(zc > 0.0f)) return false;
+    const float hw = 0.5f * (float)c.W, hh = 0.5f * (float)c.H;
+    uu = __fsub_rn(__fmul_rn(__fadd_rn(__fdiv_rn(__fdiv_rn(xc, zc), c.tx), 1.0f), hw), 0.5f);
+    vv = __fsub_rn(__fmul_rn(__fsub_rn(1.0f, __fdiv_rn(__fdiv_rn(yc, zc), c.ty)), hh), 0.5f);
+    return true;
+}
+
+// One thread per node, a CTA per tile of kHullTX x kHullTY x kHullTZ nodes.
+// Node (i, j, k)'s box has its corners on the lattice points {max(i-1, 0),
+// min(i+1, n-1)} per axis, so the tile's nodes share the corners of a
+// (kHullTX + 2) x (kHullTY + 2) x (kHullTZ + 2) lattice block: per view the CTA
+// projects that block once into shared memory (about 2.3 projections per node
+// instead of 8), and each node takes the bounding rectangle of its 8 corners'
+// projections and counts the flame pixels in it with 4 table reads.
+constexpr int kHullTX = 8, kHullTY = 8, kHullTZ = 4;
+constexpr int kHullLX = kHullTX + 2, kHullLY = kHullTY + 2, kHullLZ = kHullTZ + 2;
+constexpr int kHullLattice = kHullLX * kHullLY * kHullLZ;
+
+__global__ void __launch_bounds__(kHullTX * kHullTY * kHullTZ) hull_kernel(const __grid_constant__ HullCams cams,
+                                                                          int ncam, int nx, int ny, int nz,
+                                                                          const unsigned* __restrict__ sat,
+                                                                          unsigned* __restrict__ tags)
+{
+    __shared__ float2 proj[kHullLattice];
+    __shared__ unsigned char front[kHullLattice];
+    const int tiles_x = (nx + kHullTX - 1) / kHullTX, tiles_y = (ny + kHullTY - 1) / kHullTY;
+    const int tb = blockIdx.x, tile_x = tb % tiles_x, tr = tb / tiles_x, tile_y = tr % tiles_y,
+              tile_z = tr / tiles_y;
+    const int x0 = tile_x * kHullTX, y0 = tile_y * kHullTY, z0 = tile_z * kHullTZ;
+    const int t = threadIdx.x;
+    const int i = x0 + t % kHullTX, j = y0 + (t / kHullTX) % kHullTY, k = z0 + t / (kHullTX * kHullTY);
+    const bool live = i < nx && j < ny && k < nz;
+    // lattice indices of the node's box corners within the block (origin x0 - 1, y0 - 1, z0 - 1)
+    const int lo[3] = {max(i - 1, 0) - (x0 - 1), max(j - 1, 0) - (y0 - 1), max(k - 1, 0) - (z0 - 1)};
+    const int hi[3] = {min(i + 1, nx - 1) - (x0 - 1), min(j + 1, ny - 1) - (y0 - 1), min(k + 1, nz - 1) - (z0 - 1)};
     unsigned tag = 0;
     size_t sat_off = 0;
     for (int v = 0; v < ncam; ++v) {
         const CamDev& c = cams.c[v];
         const int W = c.W, H = c.H;
-        const float hw = 0.5f * (float)W, hh = 0.5f * (float)H;
-        float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
-        bool behind = false;
-        for (int b = 0; b < 8; ++b) {
-            const float X = __fsub_rn((float)((b & 1) ? hi[0] : lo[0]), c.o[0]);
-            const float Y = __fsub_rn((float)((b & 2) ? hi[1] : lo[1]), c.o[1]);
-            const float Z = __fsub_rn((float)((b & 4) ? hi[2] : lo[2]), c.o[2]);
-            const float xc = dot3_rn(X, Y, Z, c.r), yc = dot3_rn(X, Y, Z, c.u), zc = dot3_rn(X, Y, Z, c.f);
-            if (!(zc > 0.0f)) { behind = true; break; }
-            const float uu = __fsub_rn(__fmul_rn(__fadd_rn(__fdiv_rn(__fdiv_rn(xc, zc), c.tx), 1.0f), hw), 0.5f);
-            const float vv = __fsub_rn(__fmul_rn(__fsub_rn(1.0f, __fdiv_rn(__fdiv_rn(yc, zc), c.ty)), hh), 0.5f);
-            umin = fminf(umin, uu); umax = fmaxf(umax, uu);
-            vmin = fminf(vmin, vv); vmax = fmaxf(vmax, vv);
+        for (int p = t; p < kHullLattice; p += blockDim.x) {
+            const int pi = p % kHullLX, pr = p / kHullLX, pj = pr % kHullLY, pk = pr / kHullLY;
+            float uu = 0.0f, vv = 0.0f;
+            front[p] = hull_project(c, x0 - 1 + pi, y0 - 1 + pj, z0 - 1 + pk, uu, vv) ? 1 : 0;
+            proj[p] = make_float2(uu, vv);
         }
-        int x0 = 0, x1 = W - 1, y0 = 0, y1 = H - 1;
-        if (!behind) {
-            const float cx0 = ceilf(umin), cx1 = floorf(umax), cy0 = ceilf(vmin), cy1 = floorf(vmax);
-            x0 = cx0 > 0.0f ? (cx0 < (float)W ? (int)cx0 : W) : 0;
-            x1 = cx1 < (float)(W - 1) ? (cx1 >= -1.0f ? (int)cx1 : -1) : W - 1;
-            y0 = cy0 > 0.0f ? (cy0 < (float)H ? (int)cy0 : H) : 0;
-            y1 = cy1 < (float)(H - 1) ? (cy1 >= -1.0f ? (int)cy1 : -1) : H - 1;
+        __syncthreads();
+        if (live) {
+            float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+            bool behind = false;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const int q = (((b & 4) ? hi[2] : lo[2]) * kHullLY + ((b & 2) ? hi[1] : lo[1])) * kHullLX +
+                              ((b & 1) ? hi[0] : lo[0]);
+                behind |= front[q] == 0;
+                const float2 uv = proj[q];
+                umin = fminf(umin, uv.x); umax = fmaxf(umax, uv.x);
+                vmin = fminf(vmin, uv.y); vmax = fmaxf(vmax, uv.y);
+            }
+            int x0p = 0, x1p = W - 1, y0p = 0, y1p = H - 1;
+            if (!behind) {
+                const float cx0 = ceilf(umin), cx1 = floorf(umax), cy0 = ceilf(vmin), cy1 = floorf(vmax);
+                x0p = cx0 > 0.0f ? (cx0 < (float)W ? (int)cx0 : W) : 0;
+                x1p = cx1 < (float)(W - 1) ? (cx1 >= -1.0f ? (int)cx1 : -1) : W - 1;
+                y0p = cy0 > 0.0f ? (cy0 < (float)H ? (int)cy0 : H) : 0;
+                y1p = cy1 < (float)(H - 1) ? (cy1 >= -1.0f ? (int)cy1 : -1) : H - 1;
+            }
+            if (x0p <= x1p && y0p <= y1p) {
+                const unsigned* S = sat + sat_off;
+                const size_t w1 = (size_t)W + 1;
+                const unsigned cnt = S[(size_t)(y1p + 1) * w1 + (x1p + 1)] - S[(size_t)y0p * w1 + (x1p + 1)] -
+                                     S[(size_t)(y1p + 1) * w1 + x0p] + S[(size_t)y0p * w1 + x0p];
+                if (cnt) tag |= 1u << v;
+            }
         }
-        if (x0 <= x1 && y0 <= y1) {
-            const unsigned* S = sat + sat_off;
-            const size_t w1 = (size_t)W + 1;
-            const unsigned cnt = S[(size_t)(y1 + 1) * w1 + (x1 + 1)] - S[(size_t)y0 * w1 + (x1 + 1)] -
-                                 S[(size_t)(y1 + 1) * w1 + x0] + S[(size_t)y0 * w1 + x0];
-            if (cnt) tag |= 1u << v;
-        }
+        __syncthreads();
         sat_off += (size_t)(H + 1) * (W + 1);
     }
-    tags[idx] = tag;
+    if (live) tags[((long long)k * ny + j) * nx + i] = tag;
 }
 
 cudaError_t launch_visual_hull(const CamDev* cams, int ncam, int W, int H, int nx, int ny, int nz,
@@ -1281,11 +1521,12 @@ cudaError_t launch_visual_hull(const CamDev* cams, int ncam, int W, int H, int n
 {
     HullCams hc;
     for (int v = 0; v < ncam; ++v) hc.c[v] = cams[v];
-    const int rows = ncam * (H + 1), cols = ncam * (W + 1);
-    sat_rows_kernel<<<(rows + 127) / 128, 128, 0, s>>>(targets, ncam, W, H, thresh, sat);
-    sat_cols_kernel<<<(cols + 127) / 128, 128, 0, s>>>(ncam, W, H, sat);
-    const long long nodes = (long long)nx * ny * nz;
-    hull_kernel<<<(unsigned)((nodes + 255) / 256), 256, 0, s>>>(hc, ncam, nx, ny, nz, sat, tags);
+    const int rows = ncam * (H + 1), tiles = (W + 1 + 31) / 32;
+    sat_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(targets, ncam, W, H, thresh, sat);
+    sat_cols_kernel<<<(unsigned)(ncam * tiles), dim3(32, kSatChunks), 0, s>>>(ncam, W, H, sat);
+    const long long node_tiles = (long long)((nx + kHullTX - 1) / kHullTX) * ((ny + kHullTY - 1) / kHullTY) *
+                                 ((nz + kHullTZ - 1) / kHullTZ);
+    hull_kernel<<<(unsigned)node_tiles, kHullTX * kHullTY * kHullTZ, 0, s>>>(hc, ncam, nx, ny, nz, sat, tags);
     return cudaGetLastError();
 }
 
