@@ -456,6 +456,8 @@ cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int n
 // (threadIdx.x, neighbouring lines: coalesced for the y and z sweeps) times
 // kSweepChunks chunks (threadIdx.y).  The x sweep initialises J, the z sweep
 // (LAST) finishes it and writes the source records S = q + albedo sigma J.
+// (Staging a CTA's 32 lines in shared memory, one coalesced load pass and two
+// CTAs per SM, measured 15% slower than holding each chunk in registers.)
 // (Testing the visual hull's brick table first, so that chunks in bricks
 // known to be zero skip their loads, measured 15% slower: the flag load adds
 // a dependent round trip to every chunk of these latency-bound sweeps.)
@@ -878,150 +880,6 @@ __global__ void __launch_bounds__(256) sweep_x_kernel(const void* em, float* J, 
     }
 }
 
-// The y / z sweep with the CTA's 32 lines staged in shared memory: one
-// coalesced pass loads every record of the lines (n_line x 32 float4), so the
-// chunks' walks read shared memory instead of waiting on global loads, and the
-// kernel holds few registers (two CTAs per SM).  J of a chunk of at most CM
-// nodes stays in registers.  The arithmetic and its order are those of
-// sweep_reg_kernel.
-#ifndef FR_SWEEP_SMEM_MINB
-#define FR_SWEEP_SMEM_MINB 2
-#endif
-template <int DT, int AXIS, bool LAST, int CM>
-__global__ void __launch_bounds__(kSweepLines * kSweepChunks, FR_SWEEP_SMEM_MINB) sweep_smem_kernel(const void* em,
-                                                                                   const float* albedo, float* J,
-                                                                                   void* out, int nx, int ny, int nz,
-                                                                                   bool skip_empty)
-{
-    extern __shared__ float4 recs[];   // [node along the line][line of the CTA]
-    __shared__ float4 fwd[kSweepChunks][kSweepLines];
-    __shared__ float4 bwd[kSweepChunks][kSweepLines];
-    const int n_line = AXIS == 1 ? ny : nz;
-    const long long lines = AXIS == 1 ? (long long)nx * nz : (long long)nx * ny;
-    const long long stride = AXIS == 1 ? (long long)nx : (long long)nx * ny;
-    const long long nodes = (long long)nx * ny * nz;
-    auto line_start = [&](long long ln) -> long long {
-        if constexpr (AXIS == 1) {
-            const long long z = ln / nx;
-            return z * (long long)nx * ny + (ln - z * nx);   // line = z * nx + x
-        } else {
-            return ln;                                       // line = y * nx + x
-        }
-    };
-    const int tid = threadIdx.y * kSweepLines + threadIdx.x;
-    const long long line0 = blockIdx.x * (long long)kSweepLines;
-    for (int e = tid; e < n_line * kSweepLines; e += kSweepLines * kSweepChunks) {
-        const int i = e / kSweepLines, l = e - i * kSweepLines;
-        float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (line0 + l < lines) r = load_rgb<DT>(em, FR_CHK(line_start(line0 + l) + i * stride, nodes, 41u));
-        recs[e] = r;
-    }
-    const long long line = line0 + threadIdx.x;
-    const int ch = threadIdx.y;
-    const bool live = line < lines;
-    const long long start = live ? line_start(line) : 0;
-    const int m = (n_line + kSweepChunks - 1) / kSweepChunks;
-    const int s0 = min(ch * m, n_line), s1 = min(s0 + m, n_line), cnt = s1 - s0;   // cnt <= CM
-    auto rec = [&](int i) -> float4 { return recs[i * kSweepLines + threadIdx.x]; };
-    float3 jv[CM];
-    float alb[CM];
-    if (live && cnt > 0) {
-        // J (earlier sweeps) and albedo of the chunk's nodes, in flight during the staging
-        float4* J4 = reinterpret_cast<float4*>(J);
-#pragma unroll
-        for (int q = 0; q < CM; ++q) {
-            if (q < cnt) {
-                const long long node = start + (s0 + q) * stride;
-                const float4 t = J4[node];
-                jv[q] = make_float3(t.x, t.y, t.z);
-                if constexpr (LAST) alb[q] = __ldg(albedo + node);
-            }
-        }
-    }
-    __syncthreads();
-    float Ef = 1.0f, F0 = 0.0f, F1 = 0.0f, F2 = 0.0f;
-    float Eb = 1.0f, B0 = 0.0f, B1 = 0.0f, B2 = 0.0f;
-    bool occupied = false;
-    if (live && cnt > 0) {
-        for (int q = 0; q < cnt; ++q) occupied |= nonzero_record(rec(s0 + q));
-        // phase 1: the chunk's forward and backward maps; segment j joins
-        // nodes s0 - 1 + j and s0 + j
-        for (int j = 0; j <= cnt; ++j) {
-            const int i = s0 + j;
-            if (i >= 1 && i <= n_line - 1) {
-                const Seg g = seg_between<DT>(rec(i - 1), rec(i));
-                if (j < cnt) {
-                    F0 = fmaf(F0, g.e, g.c0); F1 = fmaf(F1, g.e, g.c1); F2 = fmaf(F2, g.e, g.c2);
-                    Ef *= g.e;
-                }
-                if (j >= 1) {
-                    B0 = fmaf(Eb, g.c0, B0); B1 = fmaf(Eb, g.c1, B1); B2 = fmaf(Eb, g.c2, B2);
-                    Eb *= g.e;
-                }
-            }
-        }
-    }
-    fwd[ch][threadIdx.x] = make_float4(Ef, F0, F1, F2);
-    bwd[ch][threadIdx.x] = make_float4(Eb, B0, B1, B2);
-    __syncthreads();
-    if (!live || cnt <= 0) return;
-    if (skip_empty && !occupied) {
-        if constexpr (LAST) {
-            for (int q = 0; q < cnt; ++q)
-                store_rgb<DT>(out, FR_CHK(start + (s0 + q) * stride, nodes, 42u), make_float4(0.0f, 0.0f, 0.0f, 0.0f));
-        }
-        return;
-    }
-    // phase 2: radiance arriving at the chunk from either side
-    float lf0 = 0.0f, lf1 = 0.0f, lf2 = 0.0f;
-    for (int c = 0; c < ch; ++c) {
-        const float4 f = fwd[c][threadIdx.x];
-        lf0 = fmaf(lf0, f.x, f.y); lf1 = fmaf(lf1, f.x, f.z); lf2 = fmaf(lf2, f.x, f.w);
-    }
-    float lb0 = 0.0f, lb1 = 0.0f, lb2 = 0.0f;
-    for (int c = kSweepChunks - 1; c > ch; --c) {
-        const float4 b = bwd[c][threadIdx.x];
-        lb0 = fmaf(lb0, b.x, b.y); lb1 = fmaf(lb1, b.x, b.z); lb2 = fmaf(lb2, b.x, b.w);
-    }
-    // phase 3: forward walk (J += L_forward / 6, in registers) ...
-    const float sixth = 1.0f / 6.0f;
-#pragma unroll
-    for (int q = 0; q < CM; ++q) {
-        if (q < cnt) {
-            const int i = s0 + q;
-            if (i > 0) {
-                const Seg g = seg_between<DT>(rec(i - 1), rec(i));
-                lf0 = fmaf(lf0, g.e, g.c0); lf1 = fmaf(lf1, g.e, g.c1); lf2 = fmaf(lf2, g.e, g.c2);
-            }
-            jv[q].x = fmaf(lf0, sixth, jv[q].x); jv[q].y = fmaf(lf1, sixth, jv[q].y);
-            jv[q].z = fmaf(lf2, sixth, jv[q].z);
-        }
-    }
-    // ... and backward walk (J += L_backward / 6; stored, or the source written)
-    float4* J4 = reinterpret_cast<float4*>(J);
-#pragma unroll
-    for (int q = CM - 1; q >= 0; --q) {
-        if (q < cnt) {
-            const int i = s0 + q;
-            if (i < n_line - 1) {
-                const Seg g = seg_between<DT>(rec(i), rec(i + 1));
-                lb0 = fmaf(lb0, g.e, g.c0); lb1 = fmaf(lb1, g.e, g.c1); lb2 = fmaf(lb2, g.e, g.c2);
-            }
-            const float jx = fmaf(lb0, sixth, jv[q].x), jy = fmaf(lb1, sixth, jv[q].y), jz = fmaf(lb2, sixth, jv[q].z);
-            const long long node = FR_CHK(start + i * stride, nodes, 43u);
-            if constexpr (LAST) {
-                const float4 cur = rec(i);
-                const float as = alb[q] * cur.w;
-                store_rgb<DT>(out, node, make_float4(fmaf(as, jx, cur.x), fmaf(as, jy, cur.y), fmaf(as, jz, cur.z),
-                                                     cur.w));
-                if (!skip_empty) J4[node] = make_float4(jx, jy, jz, 0.0f);
-            } else {
-                J4[node] = make_float4(jx, jy, jz, 0.0f);
-            }
-        }
-    }
-}
-
 // The x sweep with a chunk of at most CM nodes held in registers (see
 // sweep_reg_kernel; the same arithmetic as sweep_x_kernel in the same order).
 template <int DT, int CM>
@@ -1127,47 +985,23 @@ __global__ void __launch_bounds__(256) sweep_x_reg_kernel(const void* em, float*
 #define FR_SWEEP_REG_MAX 8
 #endif
 
-// Lines whose records fit in kSweepSmemMax bytes of shared memory per CTA run
-// the staged kernel (0: never).
-#ifndef FR_SWEEP_SMEM_MAX
-#define FR_SWEEP_SMEM_MAX 0
-#endif
-
-template <int DT, int AXIS, bool LAST, int CM>
-static void launch_sweep_smem(unsigned grid, size_t smem, const void* em, const float* albedo, float* J, void* out,
-                              int nx, int ny, int nz, cudaStream_t s, bool skip_empty)
-{
-    static bool attr = false;   // the shared-memory opt-in, set once per instantiation
-    if (!attr && smem > 48 * 1024) {
-        cudaFuncSetAttribute(sweep_smem_kernel<DT, AXIS, LAST, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             FR_SWEEP_SMEM_MAX);
-        attr = true;
-    }
-    sweep_smem_kernel<DT, AXIS, LAST, CM><<<grid, dim3(kSweepLines, kSweepChunks), smem, s>>>(em, albedo, J, out, nx,
-                                                                                            ny, nz, skip_empty);
-}
-
 template <int DT, int AXIS, bool LAST>
-static void launch_sweep_yz(int m, unsigned grid, const void* em, const float* albedo, float* J, void* out, int nx,
-                            int ny, int nz, cudaStream_t s, bool skip_empty)
+static cudaError_t launch_sweep_yz(int m, unsigned grid, const void* em, const float* albedo, float* J, void* out,
+                                   int nx, int ny, int nz, cudaStream_t s, bool skip_empty)
 {
     const dim3 B(kSweepLines, kSweepChunks);
-    const int n_line = AXIS == 1 ? ny : nz;
-    const size_t smem = (size_t)n_line * kSweepLines * sizeof(float4);
-    if (smem <= (size_t)FR_SWEEP_SMEM_MAX && m <= 8) {
-        if (m <= 4) launch_sweep_smem<DT, AXIS, LAST, 4>(grid, smem, em, albedo, J, out, nx, ny, nz, s, skip_empty);
-        else launch_sweep_smem<DT, AXIS, LAST, 8>(grid, smem, em, albedo, J, out, nx, ny, nz, s, skip_empty);
-    } else if (FR_SWEEP_REG_MAX >= 4 && m <= 4)
+    if (FR_SWEEP_REG_MAX >= 4 && m <= 4)
         sweep_reg_kernel<DT, AXIS, LAST, 4><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, skip_empty);
     else if (FR_SWEEP_REG_MAX >= 8 && m <= 8)
         sweep_reg_kernel<DT, AXIS, LAST, 8><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, skip_empty);
     else
         sweep_kernel<DT, AXIS, LAST><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, nullptr, skip_empty);
+    return cudaSuccess;
 }
 
 template <int DT>
-static void launch_sweeps(const void* em, const float* albedo, float* J, void* out, int nx, int ny, int nz,
-                          cudaStream_t s, bool skip_empty)
+static cudaError_t launch_sweeps(const void* em, const float* albedo, float* J, void* out, int nx, int ny, int nz,
+                                 cudaStream_t s, bool skip_empty)
 {
     const long long lx = (long long)ny * nz, ly = (long long)nx * nz, lz = (long long)nx * ny;
     const unsigned gxw = (unsigned)((lx + 7) / 8);  // one warp per x line, 8 warps per CTA
@@ -1180,19 +1014,22 @@ static void launch_sweeps(const void* em, const float* albedo, float* J, void* o
         sweep_x_reg_kernel<DT, 8><<<gxw, 256, 0, s>>>(em, J, nx, ny, nz, skip_empty);
     else
         sweep_x_kernel<DT><<<gxw, 256, 0, s>>>(em, J, nx, ny, nz, nullptr, skip_empty);
-    launch_sweep_yz<DT, 1, false>((ny + kSweepChunks - 1) / kSweepChunks, gy, em, albedo, J, out, nx, ny, nz, s,
-                                  skip_empty);
-    launch_sweep_yz<DT, 2, true>((nz + kSweepChunks - 1) / kSweepChunks, gz, em, albedo, J, out, nx, ny, nz, s,
-                                 skip_empty);
+    cudaError_t e = launch_sweep_yz<DT, 1, false>((ny + kSweepChunks - 1) / kSweepChunks, gy, em, albedo, J, out, nx,
+                                                  ny, nz, s, skip_empty);
+    if (e != cudaSuccess) return e;
+    return launch_sweep_yz<DT, 2, true>((nz + kSweepChunks - 1) / kSweepChunks, gz, em, albedo, J, out, nx, ny, nz,
+                                        s, skip_empty);
 }
 
 cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* albedo, float* J,
                                   void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s, bool skip_empty)
 {
     if (dt_in != dt_out) return cudaErrorInvalidValue;
-    if (dt_in == DT_F32) launch_sweeps<DT_F32>(emission, albedo, J, out, nx, ny, nz, s, skip_empty);
-    else if (dt_in == DT_BF16) launch_sweeps<DT_BF16>(emission, albedo, J, out, nx, ny, nz, s, skip_empty);
-    else launch_sweeps<DT_F16>(emission, albedo, J, out, nx, ny, nz, s, skip_empty);
+    cudaError_t e;
+    if (dt_in == DT_F32) e = launch_sweeps<DT_F32>(emission, albedo, J, out, nx, ny, nz, s, skip_empty);
+    else if (dt_in == DT_BF16) e = launch_sweeps<DT_BF16>(emission, albedo, J, out, nx, ny, nz, s, skip_empty);
+    else e = launch_sweeps<DT_F16>(emission, albedo, J, out, nx, ny, nz, s, skip_empty);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
