@@ -1132,7 +1132,7 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         const int nt = tiles_of(q.cams[0].width, q.cams[0].height, q.ncam);
         arena += align256(ib) + align256((size_t)node_count(&q.vol) * 16) + align256((size_t)nt * 16) +
                  align256((size_t)std::max(iters, 1) * 16) + align256(flame_list_buf_entries(nt) * 4) +
-                 align256((size_t)npix * 4) + align256((size_t)node_count(&q.vol) * 2 * rec_bytes(&q.vol));
+                 align256((size_t)nt * kTileThreads * 4) + align256((size_t)node_count(&q.vol) * 2 * rec_bytes(&q.vol));
         const size_t tb = align256(brick_table_bytes(q.vol.nx, q.vol.ny, q.vol.nz));
         if (hull) arena += align256((size_t)node_count(&q.vol) * 4);
         if (skip) arena += tb;
@@ -1178,14 +1178,14 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         fill_problem(&q.vol, q.cams, q.ncam, p, a);
         const int nt = tiles_of(q.cams[0].width, q.cams[0].height, q.ncam);
         const long long nodes = node_count(&q.vol);
-        const long long npix = (long long)q.ncam * q.cams[0].width * q.cams[0].height;
         const size_t ib = image_bytes(q.cams, q.ncam);
         float* residual = reinterpret_cast<float*>(dbase + off); off += align256(ib);
         float* dV = reinterpret_cast<float*>(dbase + off); off += align256((size_t)nodes * 16);
         float* partials = reinterpret_cast<float*>(dbase + off); off += align256((size_t)nt * 16);
         float* sqerr = reinterpret_cast<float*>(dbase + off); off += align256((size_t)iters * 16);
         unsigned* fbuf = reinterpret_cast<unsigned*>(dbase + off); off += align256(flame_list_buf_entries(nt) * 4);
-        unsigned* flist = reinterpret_cast<unsigned*>(dbase + off); off += align256((size_t)npix * 4);
+        // (runs padded to whole warps: at most a tile's worth of entries per tile)
+        unsigned* flist = reinterpret_cast<unsigned*>(dbase + off); off += align256((size_t)nt * kTileThreads * 4);
         void* pairs = dbase + off; off += align256((size_t)nodes * 2 * rec_bytes(&q.vol));
         const size_t tb = align256(brick_table_bytes(q.vol.nx, q.vol.ny, q.vol.nz));
         unsigned* tags = nullptr;

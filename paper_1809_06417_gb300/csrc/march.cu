@@ -190,7 +190,13 @@ struct BrickSkip {
     __device__ __forceinline__ bool empty(const unsigned char* flags, const ProbDev& P, const Ray& R, float step,
                                           float x, float y, float z, int& k)
     {
-        const CellIJK c = cell_ijk(x, y, z, P.nx, P.ny, P.nz);
+        return empty_at(flags, P, R, step, cell_ijk(x, y, z, P.nx, P.ny, P.nz), k);
+    }
+
+    // The same for the sample's cell c.
+    __device__ __forceinline__ bool empty_at(const unsigned char* flags, const ProbDev& P, const Ray& R, float step,
+                                             const CellIJK& c, int& k)
+    {
         const int b = ((c.k >> kBrickShift) * P.nby + (c.j >> kBrickShift)) * P.nbx + (c.i >> kBrickShift);
         if (b != brick) {
             brick = b;
@@ -347,10 +353,20 @@ __global__ void FR_FWD_BOUNDS fwd_single(const __grid_constant__ SingleArgs a)
     fwd_body<DT, KIND, TAU, MODE>(a.p, a.cams, blockIdx.x);
 }
 
+// (Batched forward: capped at 80 registers like fwd_single it spills 40 bytes
+// and is still 3% faster on the video batch than with 96 registers;
+// FR_FWD_BATCH_CAP=0 leaves the registers unbounded.)
+#ifndef FR_FWD_BATCH_CAP
+#define FR_FWD_BATCH_CAP 1
+#endif
+#if FR_FWD_BATCH_CAP
+#define FR_FWD_BATCH_BOUNDS FR_FWD_BOUNDS
+#else
+#define FR_FWD_BATCH_BOUNDS FR_MARCH_BOUNDS
+#endif
 template <int DT, int KIND, bool TAU, int MODE>
-__global__ void FR_MARCH_BOUNDS fwd_batch(const ProbDev* __restrict__ probs,
-                                                                          const int* __restrict__ tile_start,
-                                                                          int nprob)
+__global__ void FR_FWD_BATCH_BOUNDS fwd_batch(const ProbDev* __restrict__ probs, const int* __restrict__ tile_start,
+                                              int nprob)
 {
     const int p = find_problem(tile_start, nprob, blockIdx.x);
     const ProbDev& P = probs[p];
@@ -364,7 +380,9 @@ __global__ void FR_MARCH_BOUNDS fwd_batch(const ProbDev* __restrict__ probs,
 // dL is constant along a ray, so each key point collects the scalar sum of
 // G alpha_l T exp(-alpha_d D) over the ray's samples in its window slot and
 // receives that sum times dL when the ray leaves it.
-template <int DT, bool TAU, bool SKIP = false>
+// RG: G(s) drawn per sample (g_std > 0); false: G = 1 (a compile-time
+// constant, 1.6% faster than a per-sample test of g_std).
+template <int DT, bool TAU, bool SKIP, bool RG>
 __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, int view, int px, int py,
                                         int iteration)
 {
@@ -413,13 +431,15 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
     for (int k = k0; k < k1; ++k) {
         float len, x, y, z;
         segment(R, P.step, k, len, x, y, z);
-        if constexpr (SKIP) {
-            if (skip.empty(P.adj_occ, P, R, P.step, x, y, z, k)) continue;
-        }
         const CellIJK c = cell_ijk(x, y, z, P.nx, P.ny, P.nz);
+        // (testing the brick only when the cell changes measured 5% slower)
+        if constexpr (SKIP) {
+            if (skip.empty_at(P.adj_occ, P, R, P.step, c, k)) continue;
+        }
         win_move(W, c.i, c.j, c.k, P.nx, P.ny, nxy32, leave, enter);
         const float gx = mirror_frac(c.i, c.fx), gy = mirror_frac(c.j, c.fy), gz = mirror_frac(c.k, c.fz);
-        const float G = P.g_std > 0.0f ? g_draw(P.seed, P.g_std, iteration, view + P.view_base, pixel, k) : 1.0f;
+        float G = 1.0f;
+        if constexpr (RG) G = g_draw(P.seed, P.g_std, iteration, view + P.view_base, pixel, k);
         const float base = G * P.alpha_l * T;
         // squared distances (voxel units) from the sample to each slot's key point
         const float ex[2] = {gx * gx, (1.0f - gx) * (1.0f - gx)};
@@ -441,7 +461,8 @@ __device__ __forceinline__ void adj_body(const ProbDev& P, const CamDev* cams, i
     int view, px, py;
     tile_pixel(P, tile, view, px, py);
     if (px >= P.W || py >= P.H) return;
-    adj_ray<DT, TAU>(P, cams, view, px, py, P.iteration);
+    if (P.g_std > 0.0f) adj_ray<DT, TAU, false, true>(P, cams, view, px, py, P.iteration);
+    else adj_ray<DT, TAU, false, false>(P, cams, view, px, py, P.iteration);
 }
 
 // The same over a compacted list of flame rays (linear pixel indices in tile
@@ -461,26 +482,32 @@ __global__ void FR_ADJ_LIST_BOUNDS adj_list(const __grid_constant__ SingleArgs a
     const int view = (int)(pix / per_view);
     const unsigned r = pix - (unsigned)view * per_view;
     const int py = (int)(r / (unsigned)P.W), px = (int)(r - (unsigned)py * (unsigned)P.W);
-    adj_ray<DT, TAU, SKIP>(P, a.cams, view, px, py, P.iteration + (P.iter_dev ? __ldg(P.iter_dev) : 0));
+    const int it = P.iteration + (P.iter_dev ? __ldg(P.iter_dev) : 0);
+    if (P.g_std > 0.0f) adj_ray<DT, TAU, SKIP, true>(P, a.cams, view, px, py, it);
+    else adj_ray<DT, TAU, SKIP, false>(P, a.cams, view, px, py, it);
 }
 
-// Batched form: CTA b belongs to the problem whose tile range holds b and
-// takes that problem's list entries [128 (b - start), ...).  The G(s) stream
-// index is the problem's own iteration plus `iteration`.
+// Batched form, one warp per CTA like adj_list: CTA b covers list entries
+// [n b', n b' + n) of the problem whose tile range holds tile b / (128 / n),
+// b' counted from that problem's first CTA (n = FR_ADJ_THREADS).  The G(s)
+// stream index is the problem's own iteration plus `iteration`.
 template <int DT, bool TAU, bool SKIP>
-__global__ void FR_MARCH_BOUNDS adj_list_batch(const ProbDev* __restrict__ probs, const int* __restrict__ tile_start,
-                                               int nprob, int iteration)
+__global__ void FR_ADJ_LIST_BOUNDS adj_list_batch(const ProbDev* __restrict__ probs,
+                                                  const int* __restrict__ tile_start, int nprob, int iteration)
 {
-    const int p = find_problem(tile_start, nprob, blockIdx.x);
+    constexpr unsigned kPer = kTileThreads / FR_ADJ_THREADS;   // CTAs per tile
+    const int p = find_problem(tile_start, nprob, (int)(blockIdx.x / kPer));
     const ProbDev& P = probs[p];
-    const unsigned i = (unsigned)(blockIdx.x - __ldg(tile_start + p)) * (unsigned)kTileThreads + threadIdx.x;
+    const unsigned i = (blockIdx.x - (unsigned)__ldg(tile_start + p) * kPer) * (unsigned)FR_ADJ_THREADS + threadIdx.x;
     if (i >= __ldg(P.list_count)) return;
     const unsigned pix = __ldg(P.list + i);
+    if (pix == kNoPixel) return;
     const unsigned per_view = (unsigned)P.W * (unsigned)P.H;
     const int view = (int)(pix / per_view);
     const unsigned r = pix - (unsigned)view * per_view;
     const int py = (int)(r / (unsigned)P.W), px = (int)(r - (unsigned)py * (unsigned)P.W);
-    adj_ray<DT, TAU, SKIP>(P, P.cams, view, px, py, P.iteration + iteration);
+    if (P.g_std > 0.0f) adj_ray<DT, TAU, SKIP, true>(P, P.cams, view, px, py, P.iteration + iteration);
+    else adj_ray<DT, TAU, SKIP, false>(P, P.cams, view, px, py, P.iteration + iteration);
 }
 
 template <int DT, bool TAU>
@@ -730,11 +757,13 @@ __global__ void __launch_bounds__(256) finalize_parts(const float* __restrict__ 
     }
 }
 
-// Flame-ray list (pixels whose prepared target is non-zero), in tile order.
-// Pass 1 counts each warp's flame pixels and each CTA's total; pass 2 scans the
-// CTA totals; pass 3 writes each warp's pixels at the CTA offset plus the
-// counts of the CTA's earlier warps.  Buffer layout: warp counts
-// [0, 4 ntiles), CTA offsets [4 ntiles, 5 ntiles], total at 5 ntiles.
+// Flame-ray list (pixels whose prepared target is non-zero), in tile order,
+// each tile's run padded to whole warps with entries that name no pixel.
+// Pass 1 counts each warp's flame pixels and each CTA's padded total; pass 2
+// scans the CTA totals; pass 3 writes each warp's pixels at the CTA offset
+// plus the counts of the CTA's earlier warps, and the padding.  Buffer layout:
+// warp counts [0, 4 ntiles), CTA offsets [4 ntiles, 5 ntiles], total at
+// 5 ntiles (the list holds at most 128 entries per tile).
 __device__ __forceinline__ bool is_flame(const ProbDev& P, int view, int px, int py)
 {
     if (px >= P.W || py >= P.H) return false;
@@ -760,7 +789,7 @@ __global__ void __launch_bounds__(kTileThreads) flame_count_kernel(const __grid_
     if (threadIdx.x == 0) {
         unsigned t = 0;
         for (int i = 0; i < kWarpsPerTile; ++i) t += wc[i];
-        buf[(size_t)kWarpsPerTile * ntiles + blockIdx.x] = t;
+        buf[(size_t)kWarpsPerTile * ntiles + blockIdx.x] = (t + 31u) & ~31u;   // the run padded to whole warps
     }
 }
 
@@ -811,13 +840,18 @@ __global__ void __launch_bounds__(kTileThreads) flame_list_kernel(const __grid_c
     tile_pixel(P, blockIdx.x, view, px, py);
     const bool f = is_flame(P, view, px, py);
     const unsigned m = __ballot_sync(0xffffffffu, f);
+    const unsigned run_at = buf[(size_t)kWarpsPerTile * ntiles + blockIdx.x];
     if (f) {
         const int w = threadIdx.x >> 5;
-        unsigned at = buf[(size_t)kWarpsPerTile * ntiles + blockIdx.x];
+        unsigned at = run_at;
         for (int i = 0; i < w; ++i) at += buf[blockIdx.x * kWarpsPerTile + i];
         at += __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
         list[at] = (unsigned)(((long long)view * P.H + py) * P.W + px);
     }
+    // the run's padding to whole warps names no pixel
+    unsigned len = 0;
+    for (int i = 0; i < kWarpsPerTile; ++i) len += buf[blockIdx.x * kWarpsPerTile + i];
+    if ((unsigned)threadIdx.x >= len && (unsigned)threadIdx.x < ((len + 31u) & ~31u)) list[run_at + threadIdx.x] = kNoPixel;
 }
 
 // Per-problem sums of the squared-error partials (one CTA per problem), into
@@ -909,7 +943,7 @@ cudaError_t launch_adjust(const SingleArgs& a, int dt, int ntiles, cudaStream_t 
 cudaError_t launch_adjust_list_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
                                      int dt, bool tau, int iteration, cudaStream_t s, bool skip)
 {
-    dim3 grid(total_tiles), block(kTileThreads);
+    dim3 grid((unsigned)total_tiles * (kTileThreads / FR_ADJ_THREADS)), block(FR_ADJ_THREADS);
     FR_DISPATCH_DT(dt, D, {
         if (tau) adj_list_batch<D, true, false><<<grid, block, 0, s>>>(probs, tile_start, nprob, iteration);
         else if (skip) adj_list_batch<D, false, true><<<grid, block, 0, s>>>(probs, tile_start, nprob, iteration);

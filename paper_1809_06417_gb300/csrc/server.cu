@@ -68,7 +68,6 @@ JobLayout job_layout(const fr_job_desc& d, int dtype, const fr_camera* cams, boo
     const long long nodes = (long long)d.nx * d.ny * d.nz;
     const size_t ib = image_bytes(cams, d.ncam);
     const int nt = tiles_of(cams[0].width, cams[0].height, d.ncam);
-    const long long npix = (long long)d.ncam * cams[0].width * cams[0].height;
     size_t o = 0;
     L.vol = o; o += align256((size_t)nodes * 4 * dtype_bytes(dtype));
     L.targets = o; o += align256(ib);
@@ -78,7 +77,7 @@ JobLayout job_layout(const fr_job_desc& d, int dtype, const fr_camera* cams, boo
     L.partials = o; o += align256((size_t)nt * 16);
     L.sqerr = o; o += align256((size_t)std::max(d.iters, 1) * 16);
     L.fbuf = o; o += align256(flame_list_buf_entries(nt) * 4);
-    L.flist = o; o += align256((size_t)npix * 4);
+    L.flist = o; o += align256((size_t)nt * kTileThreads * 4);   // runs padded to whole warps
     L.pairs = o; o += align256((size_t)nodes * 8 * dtype_bytes(dtype));
     const size_t tb = align256(brick_table_bytes(d.nx, d.ny, d.nz));
     L.tags = o; if (hull) o += align256((size_t)nodes * 4);

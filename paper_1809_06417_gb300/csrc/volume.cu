@@ -659,7 +659,8 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_reg_kernel(c
             stride = (long long)nx * ny;
         }
     }
-    const long long nodes = (long long)nx * ny * nz;
+    const long long nodes = (long long)nx * ny * nz;   // bounds of the checked build
+    (void)nodes;
     const int m = (n_line + kSweepChunks - 1) / kSweepChunks;
     const int s0 = min(ch * m, n_line), s1 = min(s0 + m, n_line), cnt = s1 - s0;   // cnt <= CM
     float4 rec[CM + 2];
@@ -891,7 +892,8 @@ __global__ void __launch_bounds__(256) sweep_x_reg_kernel(const void* em, float*
     const long long line = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (line >= (long long)ny * nz) return;   // whole warps leave together
     const long long start = line * nx;
-    const long long nodes = (long long)nx * ny * nz;
+    const long long nodes = (long long)nx * ny * nz;   // bounds of the checked build
+    (void)nodes;
     const int m = (nx + 31) / 32;
     const int s0 = min(lane * m, nx), s1 = min(s0 + m, nx), cnt = s1 - s0;   // cnt <= CM
     float4 rec[CM + 2];
