@@ -44,8 +44,8 @@ cudaError_t launch_count(const SingleArgs& a, int ntiles, cudaStream_t s);
 // scratch (nullable): kFinScratchBytes of device memory, kFinParts float4 and
 // then a counter word that is 0 before the first launch (every launch leaves
 // it 0); with it the sum runs over kFinParts CTAs, without it in one.  rmse3
-// (nullable, with scratch only): the error measure of the final sums, as
-// launch_rmse writes it.
+// (nullable, with scratch only): the error measure of the final sums (Sec.
+// 5.1), 255 sqrt(sum / count) per channel, 0 without counted pixels.
 constexpr int kFinParts = 32;
 constexpr size_t kFinScratchBytes = kFinParts * 16 + 16;
 cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cudaStream_t s, int accumulate = 0,
@@ -98,7 +98,6 @@ struct HgWeights {
 };
 cudaError_t launch_source_hg(const void* emission, int dt, const float* albedo, const float* L6, HgWeights w,
                              void* out, long long nodes, cudaStream_t s);
-cudaError_t launch_rmse(const float* sq4, int n, float* rmse3, cudaStream_t s);
 cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t s);
 // visual hull: sat needs ncam (H+1)(W+1) uint32, tags one uint32 per node
 cudaError_t launch_visual_hull(const CamDev* cams, int ncam, int W, int H, int nx, int ny, int nz,

@@ -145,10 +145,8 @@ __device__ __forceinline__ void load8_pairs(const void* pairs, long long base, i
 // cells [B b, min(B b + B, n - 1)] per axis (B = kBrick); `flags` holds one byte per brick
 // (non-zero: the samples in it are evaluated).
 struct BrickSkip {
-    int brick = -1;
-    bool occupied = true;
-
-    __device__ __forceinline__ explicit BrickSkip(const Ray&) {}
+    int brick = -1;         // the brick of the last tested sample
+    bool occupied = true;   // and its flag
 
     // Samples [k0, k1) of the ray that can lie in the box of the flagged-on
     // bricks (box: brick-table layout); false when there are none.  Samples
@@ -241,7 +239,7 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
             RT v[8];
             long long vbase = -1;
             float T = 1.0f;
-            BrickSkip skip(R);
+            BrickSkip skip;
             int k0 = 0, k1 = R.n;
             if constexpr (SKIP) {
                 if (!BrickSkip::box_range(P, P.occ_box, R, P.step, k0, k1)) k1 = 0;
@@ -423,7 +421,7 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
     Win W;
     W.live = false;
     float T = 1.0f;
-    BrickSkip skip(R);
+    BrickSkip skip;
     int k0 = 0, k1 = R.n;
     if constexpr (SKIP) {
         if (!BrickSkip::box_range(P, P.adj_box, R, P.step, k0, k1)) return;
@@ -662,7 +660,7 @@ __global__ void __launch_bounds__(kTileThreads) count_single(const __grid_consta
         if (use && make_ray(a.cams[view], px, py, P.nx, P.ny, P.nz, P.step, R)) {
             if (P.occ) {
                 // the samples the forward march evaluates when it skips empty bricks
-                BrickSkip skip(R);
+                BrickSkip skip;
                 for (int k = 0; k < R.n; ++k) {
                     float len, x, y, z;
                     segment(R, P.step, k, len, x, y, z);
@@ -748,7 +746,7 @@ __global__ void __launch_bounds__(256) finalize_parts(const float* __restrict__ 
     }
     if (threadIdx.x == 0) *done = 0u;
     if (rmse3) {
-        // the error measure (as rmse_kernel computes it)
+        // the error measure of Sec. 5.1, 255 sqrt(sum / count) per channel
         __syncthreads();
         if (threadIdx.x < 3) {
             const float cnt = sum4[3];

@@ -4,7 +4,8 @@
 //    isotropic phase) and the source records S = q + albedo sigma J;
 //  * planck_lut: the colour-temperature table (Sec. 3.3.3);
 //  * prepare_targets: flame threshold and flame bounding boxes (Sec. 4.1);
-//  * rmse: the error measure of Sec. 5.1 from squared-error sums.
+//  * the error of the reconstruction: the volume data error of Sec. 5.1 and the
+//    stop criterion's iteration end.
 #include "fr_device.cuh"
 #include "fr_internal.h"
 
@@ -1424,14 +1425,6 @@ cudaError_t launch_hull_clear(void* vol, int dt, int nx, int ny, int nz, const u
 // Error measure and fills
 // ---------------------------------------------------------------------------
 
-__global__ void rmse_kernel(const float* sq4, int n, float* rmse3)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float cnt = sq4[4 * i + 3];
-    for (int c = 0; c < 3; ++c) rmse3[3 * i + c] = cnt > 0.0f ? 255.0f * sqrtf(sq4[4 * i + c] / cnt) : 0.0f;
-}
-
 // Temperature from the green channel (Sec. 3.3.3): per node, the inverse of
 // the table's piecewise-linear green column (bisection over its m entries,
 // strictly increasing), clamped to [t_min, t_max]; the extinction is copied.
@@ -1572,7 +1565,7 @@ cudaError_t launch_volume_err(const void* a, int dta, const void* b, int dtb, lo
 }
 
 // End of one iteration of a device-counted loop (one thread): the image error
-// of iteration it = *iter from its squared-error sums (as rmse_kernel), the
+// of iteration it = *iter from its squared-error sums (255 sqrt(sum / count)), the
 // stop criterion |E_it - E_it-1| < stop_delta in every channel (or the last
 // allowed iteration) ending the conditional loop, the counter advanced and the
 // flame-ray count cleared for the next forward march.
@@ -1608,12 +1601,6 @@ cudaError_t launch_converge(const float* sq4, float* hist3, int* iter, unsigned*
                             int max_iters, float stop_delta, cudaGraphConditionalHandle handle, cudaStream_t s)
 {
     converge_kernel<<<1, 32, 0, s>>>(sq4, hist3, iter, flame_count, n_counts, max_iters, stop_delta, handle);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_rmse(const float* sq4, int n, float* rmse3, cudaStream_t s)
-{
-    rmse_kernel<<<(n + 127) / 128, 128, 0, s>>>(sq4, n, rmse3);
     return cudaGetLastError();
 }
 
