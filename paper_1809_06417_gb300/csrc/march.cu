@@ -251,6 +251,25 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
                     if (skip.empty(P.occ, P, R, P.step, x, y, z, k)) continue;
                 }
                 const Cell c = cell_of(x, y, z, P.nx, P.ny, P.nz);
+#ifdef FR_FWD_PRED_LOAD
+                if constexpr (PAIRS && DT == DT_F32 && KIND == KIND_RGB) {
+                    // the four pair loads predicated on a cell change, no branch
+                    const unsigned need = c.base != vbase ? 1u : 0u;
+                    vbase = c.base;
+                    const long long b = FR_CHK(c.base, nxy * P.nz - nxy - P.nx - 1, 1u);
+                    const long long idx[4] = {b, b + P.nx, b + nxy, b + nxy + P.nx};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float* pp = reinterpret_cast<const float*>(P.pairs) + 8 * idx[q];
+                        float4& a = v[2 * q];
+                        float4& bb = v[2 * q + 1];
+                        asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %9, 0;\n\t"
+                            "@p ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t}"
+                            : "+f"(a.x), "+f"(a.y), "+f"(a.z), "+f"(a.w), "+f"(bb.x), "+f"(bb.y), "+f"(bb.z), "+f"(bb.w)
+                            : "l"(pp), "r"(need));
+                    }
+                } else
+#endif
                 if (c.base != vbase) {
                     vbase = c.base;
                     // the cell's far corner, base + nxy + nx + 1, must be a node
