@@ -433,6 +433,18 @@ __device__ __forceinline__ void store_ts(void* vol, long long idx, float2 v)
 }
 
 // x-pair records (record i and its +x neighbour, adjacent in memory).
+// The FP32 x-pair record load of load_rgb_pair when need != 0; a and b keep
+// their values otherwise (one predicated load, no branch).
+__device__ __forceinline__ void load_rgb_pair_f32_if(const void* pairs, long long idx, unsigned need, float4& a,
+                                                     float4& b)
+{
+    const float* p = reinterpret_cast<const float*>(pairs) + 8 * idx;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %9, 0;\n\t"
+        "@q ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t}"
+        : "+f"(a.x), "+f"(a.y), "+f"(a.z), "+f"(a.w), "+f"(b.x), "+f"(b.y), "+f"(b.z), "+f"(b.w)
+        : "l"(p), "r"(need));
+}
+
 template <int DT>
 __device__ __forceinline__ void load_rgb_pair(const void* pairs, long long idx, float4& a, float4& b)
 {

