@@ -270,42 +270,31 @@ __device__ __forceinline__ void win_nodes(int base, int i, int j, int k, int nx,
     for (int t = 0; t < 8; ++t) nd[t] = ((t >> 2) ? zb1 : zb0) + xy[t & 3];
 }
 
-// Move the window to cell (i, j, k).  leave(t, node) runs for each slot whose
-// key point is not a corner of the new cell (with its old node), then
-// enter(t, node) for the same slots (with the new node); on the first call
-// every slot enters.  A key point shared by both cells has the same parities
-// in both, so it keeps its slot.
+// Move the window to cell (i, j, k).  leave(t, node, p) and then
+// enter(t, node, p) run for every slot, p telling whether the slot's key point
+// changes (leave with its old node, enter with its new one); the callbacks
+// predicate their memory operations on p.  On the first call every slot
+// enters.  A key point shared by both cells has the same parities in both, so
+// it keeps its slot.  No branch depends on the cell: a warp's lanes, which
+// enter cells at different samples, stay converged (the adjustment measured
+// 3.7% faster than with a branch on the cell change and 2.6% more than with a
+// branch per slot).
 template <class Leave, class Enter>
-__device__ __forceinline__ void win_move(Win& W, int i, int j, int k, int nx, int ny, int nxy,
-                                         Leave&& leave, Enter&& enter)
+__device__ __forceinline__ void win_move_pred(Win& W, int i, int j, int k, int nx, int ny, int nxy, Leave&& leave,
+                                              Enter&& enter)
 {
-    // No early return when the cell is unchanged: every slot then compares
-    // equal and nothing moves, and the warp's lanes, which change cells at
-    // different samples, stay converged (measured 3.7% faster in the
-    // adjustment than a branch on the cell).
     const int base = (k * ny + j) * nx + i;
     int nn[8];
     win_nodes(base, i, j, k, nx, nxy, nn);
     W.base = base;
-    if (!W.live) {
-        W.live = true;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            W.nd[t] = nn[t];
-            enter(t, nn[t]);
-        }
-        return;
-    }
-    bool go[8];
+    const bool first = !W.live;
+    W.live = true;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-        go[t] = nn[t] != W.nd[t];
-        if (go[t]) leave(t, W.nd[t]);
-    }
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
+        const bool go = first || nn[t] != W.nd[t];
+        leave(t, first ? nn[t] : W.nd[t], go && !first);   // (a valid node even when nothing leaves)
         W.nd[t] = nn[t];
-        if (go[t]) enter(t, nn[t]);
+        enter(t, nn[t], go);
     }
 }
 
@@ -616,6 +605,41 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
 __device__ __forceinline__ void red_add_v2(float* addr, float a, float b)
 {
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" :: "l"(addr), "f"(a), "f"(b) : "memory");
+}
+
+__device__ __forceinline__ void red_add_v4_if(float* addr, float a, float b, float c, float d, bool p)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t"
+                 "@q red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n\t}"
+                 :: "l"(addr), "f"(a), "f"(b), "f"(c), "f"(d), "r"((unsigned)p) : "memory");
+}
+
+__device__ __forceinline__ void red_add_v2_if(float* addr, float a, float b, bool p)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q red.global.add.v2.f32 [%0], {%1, %2};\n\t}"
+                 :: "l"(addr), "f"(a), "f"(b), "r"((unsigned)p) : "memory");
+}
+
+__device__ __forceinline__ void load_f32_if(const float* addr, bool p, float& v)
+{
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.f32 %0, [%1];\n\t}"
+        : "+f"(v) : "l"(addr), "r"((unsigned)p));
+}
+
+// A BF16 value loaded and widened to FP32 when p (v kept otherwise).
+__device__ __forceinline__ void load_bf16_if(const unsigned short* addr, bool p, float& v)
+{
+    asm("{\n\t.reg .pred q;\n\t.reg .b32 r;\n\tsetp.ne.u32 q, %2, 0;\n\t"
+        "@q ld.global.nc.u16 r, [%1];\n\t@q shl.b32 r, r, 16;\n\t@q mov.b32 %0, r;\n\t}"
+        : "+f"(v) : "l"(addr), "r"((unsigned)p));
+}
+
+// An FP16 value loaded and widened to FP32 when p (v kept otherwise).
+__device__ __forceinline__ void load_f16_if(const unsigned short* addr, bool p, float& v)
+{
+    asm("{\n\t.reg .pred q;\n\t.reg .b16 h;\n\tsetp.ne.u32 q, %2, 0;\n\t"
+        "@q ld.global.nc.b16 h, [%1];\n\t@q cvt.f32.f16 %0, h;\n\t}"
+        : "+f"(v) : "l"(addr), "r"((unsigned)p));
 }
 
 __device__ __forceinline__ float warp_sum(float v)

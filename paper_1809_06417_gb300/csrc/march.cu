@@ -196,9 +196,16 @@ struct BrickSkip {
                                              const CellIJK& c, int& k)
     {
         const int b = ((c.k >> kBrickShift) * P.nby + (c.j >> kBrickShift)) * P.nbx + (c.i >> kBrickShift);
-        if (b != brick) {
+        {
+            // the flag reloaded by a predicated load when the brick changes
+            // (no branch: 0.5-2% faster in the marches)
+            unsigned f = occupied ? 1u : 0u;
+            const unsigned need = b != brick ? 1u : 0u;
+            const unsigned char* fp = flags + FR_CHK(b, (long long)P.nbx * P.nby * P.nbz, 16u);
+            asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.u8 %0, [%1];\n\t}"
+                : "+r"(f) : "l"(fp), "r"(need));
             brick = b;
-            occupied = __ldg(flags + FR_CHK(b, (long long)P.nbx * P.nby * P.nbz, 16u)) != 0;
+            occupied = f != 0u;
         }
         if (occupied) return false;
         const int bx = c.i & ~(kBrick - 1), by = c.j & ~(kBrick - 1), bz = c.k & ~(kBrick - 1);
@@ -419,18 +426,27 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
     const void* vol = P.vol;
     const long long nodes = nxy * P.nz;
     (void)nodes;
-    // every slot that leaves has collected at least one sample, so its
-    // reduction is issued without testing the weight (a zero test per slot
-    // measured 5% slower)
-    auto leave = [&acc, dV, dl0, dl1, dl2, nodes](int t, int node) {
+    // The window's callbacks run for every slot at every sample with p telling
+    // whether the slot moves, and predicate their memory operations on it: no
+    // branch, so the warp's lanes, which change cells at different samples,
+    // stay converged (2.6% faster than branching per slot).  Every slot that
+    // leaves has collected at least one sample, so its reduction is issued
+    // without testing the weight (a zero test per slot measured 5% slower).
+    // (Reloading all eight corner sigmas on every cell change instead of the
+    // entering slots' measured 16% slower.)
+    auto leave = [&acc, dV, dl0, dl1, dl2, nodes](int t, int node, bool p) {
         const float w = acc[t];
-        red_add_v4(dV + 4 * (unsigned)FR_CHK(node, nodes, 2u), w * dl0, w * dl1, w * dl2, 0.0f);
-        acc[t] = 0.0f;
+        red_add_v4_if(dV + 4 * (unsigned)FR_CHK(node, nodes, 2u), w * dl0, w * dl1, w * dl2, 0.0f, p);
+        acc[t] = p ? 0.0f : w;
     };
-    // (reloading all eight corner sigmas on every cell change instead of the
-    // entering slots' measured 16% slower)
-    auto enter = [&sg, vol, nodes](int t, int node) {
-        if constexpr (!TAU) sg[t] = load_rgb_sigma<DT>(vol, (unsigned)FR_CHK(node, nodes, 1u));
+    auto enter = [&sg, vol, nodes](int t, int node, bool p) {
+        if constexpr (!TAU) {
+            // sigma is the record's fourth component
+            const long long at = 4 * (long long)(unsigned)FR_CHK(node, nodes, 1u) + 3;
+            if constexpr (DT == DT_F32) load_f32_if(reinterpret_cast<const float*>(vol) + at, p, sg[t]);
+            else if constexpr (DT == DT_BF16) load_bf16_if(reinterpret_cast<const unsigned short*>(vol) + at, p, sg[t]);
+            else load_f16_if(reinterpret_cast<const unsigned short*>(vol) + at, p, sg[t]);
+        }
     };
     Win W;
     W.live = false;
@@ -448,7 +464,7 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
         if constexpr (SKIP) {
             if (skip.empty_at(P.adj_occ, P, R, P.step, c, k)) continue;
         }
-        win_move(W, c.i, c.j, c.k, P.nx, P.ny, nxy32, leave, enter);
+        win_move_pred(W, c.i, c.j, c.k, P.nx, P.ny, nxy32, leave, enter);
         const float gx = mirror_frac(c.i, c.fx), gy = mirror_frac(c.j, c.fy), gz = mirror_frac(c.k, c.fz);
         float G = 1.0f;
         if constexpr (RG) G = g_draw(P.seed, P.g_std, iteration, view + P.view_base, pixel, k);
@@ -464,7 +480,7 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
         else T *= __expf(-slot_blend<float>(sg, gx, gy, gz) * len);
     }
     (void)nxy;
-    win_release(W, leave);
+    win_release(W, [&leave](int t, int node) { leave(t, node, true); });
 }
 
 template <int DT, bool TAU>
@@ -567,13 +583,14 @@ __device__ __forceinline__ void bwd_body(const ProbDev& P, const CamDev* cams, i
     const void* vol = P.vol;
     const long long nodes = nxy * P.nz;
     (void)nodes;
-    // (reductions of all-zero sums are issued too, as in the adjustment)
-    auto leave = [&acc, dV, nodes](int t, int node) {
+    // (predicated per slot as in the adjustment; reductions of all-zero sums
+    // are issued too)
+    auto leave = [&acc, dV, nodes](int t, int node, bool p) {
         const unsigned nd = (unsigned)FR_CHK(node, nodes, 2u);
-        if constexpr (KIND == KIND_RGB) red_add_v4(dV + 4 * nd, acc[t][0], acc[t][1], acc[t][2], acc[t][3]);
-        else red_add_v2(dV + 2 * nd, acc[t][0], acc[t][1]);
+        if constexpr (KIND == KIND_RGB) red_add_v4_if(dV + 4 * nd, acc[t][0], acc[t][1], acc[t][2], acc[t][3], p);
+        else red_add_v2_if(dV + 2 * nd, acc[t][0], acc[t][1], p);
 #pragma unroll
-        for (int q = 0; q < NA; ++q) acc[t][q] = 0.0f;
+        for (int q = 0; q < NA; ++q) acc[t][q] = p ? 0.0f : acc[t][q];
     };
     Win W;
     W.live = false;
@@ -582,7 +599,7 @@ __device__ __forceinline__ void bwd_body(const ProbDev& P, const CamDev* cams, i
         float len, x, y, z;
         segment(R, P.step, k, len, x, y, z);
         const CellIJK ci = cell_ijk(x, y, z, P.nx, P.ny, P.nz);
-        win_move(W, ci.i, ci.j, ci.k, P.nx, P.ny, (int)nxy, leave, [](int, int) {});
+        win_move_pred(W, ci.i, ci.j, ci.k, P.nx, P.ny, (int)nxy, leave, [](int, int, bool) {});
         if (W.base != vbase) {
             vbase = W.base;
             load8<DT, KIND>(vol, FR_CHK((long long)W.base, nxy * P.nz - nxy - P.nx - 1, 1u), P.nx, nxy, v);
@@ -625,7 +642,7 @@ __device__ __forceinline__ void bwd_body(const ProbDev& P, const CamDev* cams, i
             for (int q = 0; q < NA; ++q) acc[t][q] = fmaf(w, gv[q], acc[t][q]);
         }
     }
-    win_release(W, leave);
+    win_release(W, [&leave](int t, int node) { leave(t, node, true); });
 }
 
 // Resident CTAs per SM asked for the backward march: 4 with temperature
