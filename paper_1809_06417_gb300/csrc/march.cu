@@ -224,7 +224,8 @@ struct BrickSkip {
 // and are reloaded only when the sample enters another cell.  (Reloading just
 // the four records of a crossed face costs more instructions than the L1
 // traffic it saves; prefetching the next sample's cell into L1 measured 8%
-// slower.)
+// slower; one-warp CTAs, the tile's epilogue done by its last warp, 19% slower:
+// a tile's four warps no longer share an SM's L1.)
 // MODE 0: records gathered one by one; 1: from x-pair records; 2: x-pair
 // records and exact skipping of empty bricks (RGB field mode only: a sample
 // whose eight corner records are all zero adds exactly nothing and leaves the
