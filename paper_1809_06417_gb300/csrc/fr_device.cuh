@@ -24,9 +24,10 @@ constexpr int kTileW = 16;
 #ifndef FR_TILE_H
 #define FR_TILE_H 8
 #endif
-// 8 or 4 rows (one warp per 8 x 4 pixels); 16 x 4 tiles measured 5% slower in
-// the forward (more, smaller CTAs) and 1% in the adjustment (more padding in
-// the flame-ray runs)
+// 8 rows (4 or 16 also work: one warp per 8 x 4 pixels); 16 x 4 tiles
+// measured 5% slower in the forward (more, smaller CTAs) and 1% in the
+// adjustment (more padding in the flame-ray runs), 16 x 16 tiles (with 3 CTAs
+// per SM) 7% slower in the forward
 constexpr int kTileH = FR_TILE_H;
 constexpr int kTileThreads = kTileW * kTileH;
 // flame-list entry that names no pixel (padding)
