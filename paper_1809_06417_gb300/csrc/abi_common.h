@@ -39,6 +39,7 @@ struct fr_ctx {
     Buf hull_bricks;                 // bricks holding a key point inside the visual hull
     Buf loop;                        // device iteration counter of fr_reconstruct_until
     Buf fin;                         // multi-CTA error reduction: part sums and its counter (kept 0)
+    Buf flame_tm;                    // transmittance at the split of each listed flame ray's second half
     // dV holds zeros over its first dV_zero_bytes when dV.p == dV_zero_at: a
     // completed reconstruction leaves it so (each update zeroes what it adds)
     const void* dV_zero_at = nullptr;

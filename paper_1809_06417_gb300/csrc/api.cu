@@ -64,7 +64,7 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     cudaStreamSynchronize(c->stream);
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
                    &c->rmse, &c->J, &c->src, &c->flame_cnt, &c->flame_list, &c->batch, &c->pairs,
-                   &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr, &c->L6, &c->fin})
+                   &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr, &c->L6, &c->fin, &c->flame_tm})
         if (b->p) cudaFree(b->p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
     if (c->staging) cudaFreeHost(c->staging);
@@ -659,7 +659,16 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     if (hg) FR_TRY(ensure(c, c->L6, (size_t)nodes * 6 * 16, "directional radiances"));
     if (until) FR_TRY(ensure(c, c->loop, 16, "loop counter"));
     // (runs may be padded to whole warps: at most one tile's worth per tile)
-    FR_TRY(ensure(c, c->flame_list, (size_t)nt * kTileThreads * sizeof(unsigned), "flame list"));
+#if FR_ADJ_SPLIT > 1
+    // every part of every flame ray (the part index in an entry's top two bits)
+    const bool split = p->rule == FR_RULE_PAPER && npix < (1LL << 30) - 1;
+    const int parts = split ? FR_ADJ_SPLIT : 1;
+#else
+    const bool split = false;
+    const int parts = 1;
+#endif
+    FR_TRY(ensure(c, c->flame_list, (size_t)nt * kTileThreads * parts * sizeof(unsigned), "flame list"));
+    if (split) FR_TRY(ensure(c, c->flame_tm, (size_t)nt * kTileThreads * parts * sizeof(float), "flame list"));
     FR_TRY(ensure(c, c->pairs, (size_t)nodes * 2 * rec_bytes(vol), "pairs"));
     const int nbx = bricks_along(vol->nx), nby = bricks_along(vol->ny), nbz = bricks_along(vol->nz);
     unsigned char* occ = nullptr;
@@ -722,7 +731,9 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     if (p->rule == FR_RULE_PAPER) {
         FR_CUDA(c, cudaMemsetAsync(flame_cnt, 0, (size_t)iters * count_slots * sizeof(unsigned), s));
         f.p.flist = flame_list;
+        f.p.flist_tm = split ? static_cast<float*>(c->flame_tm.p) : nullptr;
     }
+    const float* flame_tm = split ? static_cast<const float*>(c->flame_tm.p) : nullptr;
     const unsigned* hull = nullptr;
     const unsigned full = ncam >= 32 ? 0xffffffffu : ((1u << ncam) - 1u);
     if (p->use_hull) {
@@ -828,7 +839,7 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
             FR_TRY(trace_mark(c, FR_PHASE_REDUCE));
             if (p->rule == FR_RULE_PAPER) {
                 uv.p.iteration = first_iteration + slot;
-                FR_CUDA(c, launch_adjust_list(uv, vol->dtype, nt1, flame_list, fv.p.flist_count, st));
+                FR_CUDA(c, launch_adjust_list(uv, vol->dtype, nt1, flame_list, fv.p.flist_count, st, flame_tm));
             } else {
                 uv.p.img_scale = -1.0f;
                 FR_CUDA(c, launch_backward(uv, vol->dtype, vol->kind, nt1, st));
@@ -868,7 +879,7 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
         FR_TRY(trace_mark(c, FR_PHASE_REDUCE));
         if (p->rule == FR_RULE_PAPER) {
             u.p.iteration = first_iteration + slot;
-            FR_CUDA(c, launch_adjust_list(u, vol->dtype, nt, flame_list, flame_cnt + slot, st));
+            FR_CUDA(c, launch_adjust_list(u, vol->dtype, nt, flame_list, flame_cnt + slot, st, flame_tm));
             FR_TRY(trace_mark(c, FR_PHASE_ADJUST));
             FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg, 1,
                                     st, hull, full));

@@ -56,8 +56,9 @@ cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cuda
 inline size_t flame_list_buf_entries(int ntiles) { return (size_t)ntiles * (kTileThreads / 32 + 1) + 1; }
 inline size_t flame_list_total_at(int ntiles) { return (size_t)ntiles * (kTileThreads / 32 + 1); }
 cudaError_t launch_flame_list(const SingleArgs& a, int ntiles, unsigned* buf, unsigned* list, cudaStream_t s);
+// tm (nullable): the list holds both halves of every flame ray (ProbDev::flist_tm)
 cudaError_t launch_adjust_list(const SingleArgs& a, int dt, int ntiles, const unsigned* list,
-                               const unsigned* count, cudaStream_t s);
+                               const unsigned* count, cudaStream_t s, const float* tm = nullptr);
 
 // volume.cu
 cudaError_t launch_apply(void* vol, int dt, int kind, long long nodes, float* dV, float scale,

@@ -230,7 +230,9 @@ struct BrickSkip {
 // records and exact skipping of empty bricks (RGB field mode only: a sample
 // whose eight corner records are all zero adds exactly nothing and leaves the
 // transmittance unchanged, so skipping it does not change the result).
-template <int DT, int KIND, bool TAU, int MODE>
+// SPLIT: track the transmittance at the ray's part boundaries for a flame list
+// of ray parts (the single-problem forward; the batched one lists no rays).
+template <int DT, int KIND, bool TAU, int MODE, bool SPLIT = false>
 __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, int tile)
 {
     constexpr bool PAIRS = MODE >= 1;
@@ -240,6 +242,11 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
     tile_pixel(P, tile, view, px, py);
     const bool valid = px < P.W && py < P.H;
     float L0 = 0.0f, L1 = 0.0f, L2 = 0.0f;
+    // transmittance after the samples of the ray's first j + 1 parts
+    constexpr int kTm = SPLIT && FR_ADJ_SPLIT > 1 ? FR_ADJ_SPLIT - 1 : 1;
+    float Tm[kTm];
+#pragma unroll
+    for (int j = 0; j < kTm; ++j) Tm[j] = 1.0f;
     if (valid) {
         Ray R;
         if (make_ray(cams[view], px, py, P.nx, P.ny, P.nz, P.step, R)) {
@@ -254,6 +261,9 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
             if constexpr (SKIP) {
                 if (!BrickSkip::box_range(P, P.occ_box, R, P.step, k0, k1)) k1 = 0;
             }
+            int kb[kTm];
+#pragma unroll
+            for (int j = 0; j < kTm; ++j) kb[j] = R.n * (j + 1) / FR_ADJ_SPLIT;
             for (int k = k0; k < k1; ++k) {
                 float len, x, y, z;
                 segment(R, P.step, k, len, x, y, z);
@@ -294,6 +304,10 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
                     L0 = fmaf(w, S[0], L0); L1 = fmaf(w, S[1], L1); L2 = fmaf(w, S[2], L2);
                     T *= e;
                 }
+                if constexpr (SPLIT && FR_ADJ_SPLIT > 1) {
+#pragma unroll
+                    for (int j = 0; j < kTm; ++j) Tm[j] = k < kb[j] ? T : Tm[j];
+                }
             }
         }
     }
@@ -327,30 +341,42 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
         // pixels of its tile as one contiguous run in tile order, padded to
         // whole warps, so each of the adjustment's warps takes neighbouring
         // rays of one tile (measured 3% faster than unpadded runs, whose
-        // warps straddle two unrelated tiles)
+        // warps straddle two unrelated tiles).  With flist_tm the run holds
+        // one such block per part of the rays, part j's entries tagged j in
+        // their top two bits and carrying the transmittance Tm[j - 1].
         __shared__ unsigned wcount[kTileThreads / 32];
         __shared__ unsigned run_at, run_len;
         const unsigned m = __ballot_sync(0xffffffffu, flame);
         const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
         if (lane == 0) wcount[w] = (unsigned)__popc(m);
         __syncthreads();
+        const unsigned parts = SPLIT && FR_ADJ_SPLIT > 1 && P.flist_tm ? (unsigned)FR_ADJ_SPLIT : 1u;
         if (threadIdx.x == 0) {
             unsigned total = 0;
 #pragma unroll
             for (int i = 0; i < kTileThreads / 32; ++i) total += wcount[i];
             run_len = total;
             total = (total + 31u) & ~31u;
-            run_at = total ? atomicAdd(P.flist_count, total) : 0u;
+            run_at = total ? atomicAdd(P.flist_count, parts * total) : 0u;
         }
         __syncthreads();
+        const unsigned padded = (run_len + 31u) & ~31u;
         if (flame) {
             unsigned at = run_at + (unsigned)__popc(m & ((1u << lane) - 1u));
             for (int i = 0; i < w; ++i) at += wcount[i];
             P.flist[at] = (unsigned)pix;
+            if (parts > 1u) {
+#pragma unroll
+                for (int j = 1; j <= kTm; ++j) {
+                    P.flist[at + j * padded] = (unsigned)pix | ((unsigned)j << 30);
+                    P.flist_tm[at + j * padded] = Tm[j - 1];
+                }
+            }
         }
         // the run is padded to whole warps with entries that name no pixel
-        if ((unsigned)threadIdx.x >= run_len && (unsigned)threadIdx.x < ((run_len + 31u) & ~31u))
-            P.flist[run_at + threadIdx.x] = kNoPixel;
+        if ((unsigned)threadIdx.x >= run_len && (unsigned)threadIdx.x < padded) {
+            for (unsigned j = 0; j < parts; ++j) P.flist[run_at + j * padded + threadIdx.x] = kNoPixel;
+        }
     }
     if (P.partials) {
         __shared__ float red[4][kTileThreads / 32];
@@ -370,7 +396,7 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
 template <int DT, int KIND, bool TAU, int MODE>
 __global__ void FR_FWD_BOUNDS fwd_single(const __grid_constant__ SingleArgs a)
 {
-    fwd_body<DT, KIND, TAU, MODE>(a.p, a.cams, blockIdx.x);
+    fwd_body<DT, KIND, TAU, MODE, true>(a.p, a.cams, blockIdx.x);
 }
 
 // (Batched forward: capped at 80 registers like fwd_single it spills 40 bytes
@@ -404,7 +430,7 @@ __global__ void FR_FWD_BATCH_BOUNDS fwd_batch(const ProbDev* __restrict__ probs,
 // constant, 1.6% faster than a per-sample test of g_std).
 template <int DT, bool TAU, bool SKIP, bool RG>
 __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, int view, int px, int py,
-                                        int iteration)
+                                        int iteration, int part = -1, float T0 = 1.0f)
 {
     // SKIP: samples in bricks with no key point inside the visual hull are
     // skipped.  Their records are zero (no extinction: T is unchanged) and
@@ -454,12 +480,20 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
     };
     Win W;
     W.live = false;
-    float T = 1.0f;
+    float T = T0;
     BrickSkip skip;
     int k0 = 0, k1 = R.n;
     if constexpr (SKIP) {
         if (!BrickSkip::box_range(P, P.adj_box, R, P.step, k0, k1)) return;
     }
+#if FR_ADJ_SPLIT > 1
+    // part j: samples [R.n j / n, R.n (j + 1) / n) of the ray, starting from the
+    // transmittance the forward march reached there
+    if (part >= 0) {
+        k0 = max(k0, R.n * part / FR_ADJ_SPLIT);
+        k1 = min(k1, R.n * (part + 1) / FR_ADJ_SPLIT);
+    }
+#endif
     for (int k = k0; k < k1; ++k) {
         float len, x, y, z;
         segment(R, P.step, k, len, x, y, z);
@@ -499,7 +533,11 @@ __device__ __forceinline__ void adj_body(const ProbDev& P, const CamDev* cams, i
 
 // The same over a compacted list of flame rays (linear pixel indices in tile
 // order, so a warp's 32 rays are neighbours): no lane idles on a non-flame
-// pixel.  CTA b takes list entries [n b, n b + n), n = FR_ADJ_THREADS.
+// pixel.  CTA b takes list entries [n b, n b + n), n = FR_ADJ_THREADS.  With
+// tm, an entry names one part of a ray (its top two bits) and the part starts
+// from the transmittance tm holds at the entry's position; the parts'
+// contributions add up to the whole ray's, the key points at a part boundary
+// receiving one reduction from each side.
 // (A persistent grid whose warps take the list's 32-entry runs from a
 // segment owned by their SM, so that one SM marches neighbouring rays and
 // shares their records in L1, stealing from the fullest segment at the end,
@@ -510,21 +548,28 @@ __device__ __forceinline__ void adj_body(const ProbDev& P, const CamDev* cams, i
 // its next chunk.)
 template <int DT, bool TAU, bool SKIP>
 __global__ void FR_ADJ_LIST_BOUNDS adj_list(const __grid_constant__ SingleArgs a, const unsigned* __restrict__ list,
-                                         const unsigned* __restrict__ count)
+                                         const unsigned* __restrict__ count, const float* __restrict__ tm)
 {
     const unsigned i = blockIdx.x * (unsigned)FR_ADJ_THREADS + threadIdx.x;
     if (i >= __ldg(count)) return;
     const ProbDev& P = a.p;
-    const unsigned e = __ldg(list + i);
+    unsigned e = __ldg(list + i);
     if (e == kNoPixel) return;
+    int part = -1;
+    float T0 = 1.0f;
+    if (tm) {
+        part = (int)(e >> 30);
+        e &= 0x3fffffffu;
+        if (part) T0 = __ldg(tm + i);
+    }
     const unsigned pix = (unsigned)FR_CHK(e, (long long)P.ncam * P.W * P.H, 8u);
     const unsigned per_view = (unsigned)P.W * (unsigned)P.H;
     const int view = (int)(pix / per_view);
     const unsigned r = pix - (unsigned)view * per_view;
     const int py = (int)(r / (unsigned)P.W), px = (int)(r - (unsigned)py * (unsigned)P.W);
     const int it = P.iteration + (P.iter_dev ? __ldg(P.iter_dev) : 0);
-    if (P.g_std > 0.0f) adj_ray<DT, TAU, SKIP, true>(P, a.cams, view, px, py, it);
-    else adj_ray<DT, TAU, SKIP, false>(P, a.cams, view, px, py, it);
+    if (P.g_std > 0.0f) adj_ray<DT, TAU, SKIP, true>(P, a.cams, view, px, py, it, part, T0);
+    else adj_ray<DT, TAU, SKIP, false>(P, a.cams, view, px, py, it, part, T0);
 }
 
 // Batched form, one warp per CTA like adj_list: CTA b covers list entries
@@ -1059,16 +1104,21 @@ cudaError_t launch_flame_list(const SingleArgs& a, int ntiles, unsigned* buf, un
 }
 
 cudaError_t launch_adjust_list(const SingleArgs& a, int dt, int ntiles, const unsigned* list,
-                               const unsigned* count, cudaStream_t s)
+                               const unsigned* count, cudaStream_t s, const float* tm)
 {
     static_assert(FR_ADJ_THREADS % 32 == 0 && kTileThreads % FR_ADJ_THREADS == 0, "adjustment CTA size");
     const bool tau = a.p.tau > 0.0f;
-    dim3 grid((unsigned)ntiles * (kTileThreads / FR_ADJ_THREADS)), block(FR_ADJ_THREADS);
+#if FR_ADJ_SPLIT > 1
+    const unsigned parts = tm ? (unsigned)FR_ADJ_SPLIT : 1u;
+#else
+    const unsigned parts = 1u;
+#endif
+    dim3 grid((unsigned)ntiles * (kTileThreads / FR_ADJ_THREADS) * parts), block(FR_ADJ_THREADS);
     const bool skip = a.p.adj_occ != nullptr && !tau;
     FR_DISPATCH_DT(dt, D, {
-        if (tau) adj_list<D, true, false><<<grid, block, 0, s>>>(a, list, count);
-        else if (skip) adj_list<D, false, true><<<grid, block, 0, s>>>(a, list, count);
-        else adj_list<D, false, false><<<grid, block, 0, s>>>(a, list, count);
+        if (tau) adj_list<D, true, false><<<grid, block, 0, s>>>(a, list, count, tm);
+        else if (skip) adj_list<D, false, true><<<grid, block, 0, s>>>(a, list, count, tm);
+        else adj_list<D, false, false><<<grid, block, 0, s>>>(a, list, count, tm);
     });
     return cudaGetLastError();
 }
