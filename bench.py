@@ -397,7 +397,7 @@ def run_ours(args, ws, rank, local):
                      "note": "gather bytes are served by L1/L2 (the volume stays in the 129 MB L2; DRAM "
                              "traffic per launch is `traffic`, far below them) and the adjustment's key-point "
                              "window issues one reduction per key point a ray leaves, not one per sample-corner, "
-                             "so frac can exceed 1; the binding limit is instruction issue (`issue`)",
+                             "so frac can exceed 1; the binding limit is instruction issue (`issue`, null while the kernel has changed since its ncu capture)",
                      "issue": None if K["inst"] is None else {
                          "warp_instructions_per_launch": K["inst"], "achieved_per_s": K["inst"] / K["seconds"],
                          "peak_per_s": ISSUE_PEAK, "frac": K["inst"] / K["seconds"] / ISSUE_PEAK,
