@@ -658,9 +658,11 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     const bool hg = per_view && p->hg_g != 0.0f && albedo;
     if (hg) FR_TRY(ensure(c, c->L6, (size_t)nodes * 6 * 16, "directional radiances"));
     if (until) FR_TRY(ensure(c, c->loop, 16, "loop counter"));
-    // (runs may be padded to whole warps: at most one tile's worth per tile)
+    // Flame-ray list: one entry per flame pixel and part of its ray, each part's
+    // block of a tile's run padded to whole warps (at most one tile's worth per
+    // tile and part); the part index sits in an entry's top two bits, so larger
+    // reconstructions list whole rays.
 #if FR_ADJ_SPLIT > 1
-    // every part of every flame ray (the part index in an entry's top two bits)
     const bool split = p->rule == FR_RULE_PAPER && npix < (1LL << 30) - 1;
     const int parts = split ? FR_ADJ_SPLIT : 1;
 #else
