@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define FR_ABI_VERSION 1
+#define FR_ABI_VERSION 2
 #define FR_MAX_VIEWS 32          /* cameras per problem */
 
 typedef enum fr_status {
@@ -291,6 +291,9 @@ typedef struct fr_problem {
     const float *targets;      /* device, prepared by fr_prepare_targets */
     const int32_t *bbox;       /* device, ncam x 4 */
     float *rmse;               /* device, iters x 3, or NULL */
+    const uint32_t *hull_tags; /* device, one tag per node, or NULL; with p->use_hull these tags
+                                  (e.g. from fr_visual_hull, kept across calls) are used instead
+                                  of computing the problem's hull from its targets */
 } fr_problem;
 
 /* fr_reconstruct with the paper rule over nprob independent problems at
@@ -298,9 +301,9 @@ typedef struct fr_problem {
  * adjustment launch over the flame rays of all problems and one update
  * launch, whatever nprob is.  Volumes share one storage type; grids, cameras
  * and image sizes may differ.  Parameters are shared.  p->use_hull: each
- * problem's visual hull is computed from its own targets (p->hull_tags is not
- * read) and its records outside it are held at 0; p->skip_empty: empty bricks
- * are skipped as in fr_reconstruct.  use_graph != 0 captures the iterations in
+ * problem's visual hull is its hull_tags, or else computed from its own
+ * targets (p->hull_tags is not read), and its records outside it are held at
+ * 0; p->skip_empty: empty bricks are skipped as in fr_reconstruct.  use_graph != 0 captures the iterations in
  * a CUDA graph and launches it once; the call then returns after the work is
  * done.  Scratch is sized from all problems at once. */
 fr_status fr_reconstruct_batch(fr_ctx *ctx, const fr_problem *probs, int nprob, int iters,
@@ -336,6 +339,9 @@ typedef struct fr_job_desc {
     const float *targets;       /* host, ncam x H x W x 3 raw frames (prepared on admission) */
     void *result_records;       /* host, nodes x 4 records: written when the job completes */
     float *rmse;                /* host, iters x 3 per-iteration error, or NULL */
+    const uint32_t *hull_tags;  /* host, one tag per node, or NULL; with the server's use_hull
+                                   these tags are copied at admission instead of computing the
+                                   job's hull from its frames */
 } fr_job_desc;
 
 typedef struct fr_job_info {
@@ -457,17 +463,24 @@ fr_status fr_count_samples(fr_ctx *ctx, const fr_volume *vol, const fr_camera *c
  * render -- e.g. a process that gives all device memory to its own pool at
  * start-up, or a latency-critical loop that forbids cudaMalloc/cudaFree after
  * start-up because they can synchronise the whole device.)
- * Same results as fr_render_residual; the caller passes every input and
- * output.  The per-tile squared-error partials live in one fixed device array
- * compiled into the library (FR_NOALLOC_MAX_TILES tiles of 16 x 8 pixels,
- * 1 MiB), which every GPU that loads the library holds until the process
- * exits.  Images of more tiles, ncam * ceil(W/16) * ceil(H/8), are rejected
- * with FR_EINVAL.  The first call on a device looks up that array's device
- * address with the device made current (the calling thread's current device is
- * restored afterwards); make that first call before any stream capture.  All
- * calls share the array: calls whose work overlaps on the GPU (e.g. on two
- * streams at once) race; calls queued one after another are safe, since every
- * tile overwrites its own partials and nothing needs clearing.
+ * The same results as fr_render_residual within float32 rounding (the records
+ * are gathered one by one rather than in x-pairs and the error sums are added
+ * in another order); the caller passes every input and output.  The per-tile
+ * squared-error partials live in one fixed device array compiled into the
+ * library (FR_NOALLOC_MAX_TILES tiles of 16 x 8 pixels, 1 MiB), which every GPU
+ * that loads the library holds until the process exits.  Images of more
+ * tiles, ncam * ceil(W/16) * ceil(H/8), are rejected with FR_EINVAL.  The first
+ * call on a device, with the device made current (the calling thread's current
+ * device is restored afterwards), looks up that array's device address and
+ * loads the array and every kernel this entry point launches -- the module
+ * loading that CUDA would otherwise do lazily at a first launch, which takes
+ * device memory.  Make that first call before the caller's pool takes the
+ * device's memory and before any stream capture; after a cudaDeviceReset in
+ * the same process the looked-up address is stale, so the entry point must not
+ * be called again on that device.  All calls share the array: calls whose work
+ * overlaps on the GPU (e.g. on two streams at once) race; calls queued one
+ * after another are safe, since every tile overwrites its own partials and
+ * nothing needs clearing.
  * stream: cudaStream_t to queue on (NULL = default stream).  err (nullable):
  * receives the failure message (empty on success), at most err_len bytes. */
 #define FR_NOALLOC_MAX_TILES 65536

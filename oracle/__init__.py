@@ -25,15 +25,18 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no target-specific flags)."""
+    """Compile the oracle with gcc (plain -O2, no target-specific flags), with
+    OpenMP when the compiler has it (the pixel loops can then run on several
+    threads, see set_threads), else without."""
     os.makedirs(_BUILD, exist_ok=True)
     fresh = os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)
     if fresh and not force:
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
-           "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off"]
+    r = subprocess.run(base + ["-fopenmp", _SRC, "-o", tmp, "-lm"], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run(base + [_SRC, "-o", tmp, "-lm"], check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -56,7 +59,19 @@ class Params(ctypes.Structure):
                 ("g_std", ctypes.c_double), ("flame_thresh", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("clamp_nonneg", ctypes.c_int32),
                 ("pad_", ctypes.c_int32), ("hg_g", ctypes.c_double), ("sequential", ctypes.c_int32),
-                ("pad2_", ctypes.c_int32)]
+                ("storage", ctypes.c_int32)]
+
+# 16-bit storage types of orc_round_storage / Params.storage
+STORAGE = {None: 0, "f64": 0, "bf16": 1, "f16": 2}
+# visual hull: margin (pixels) within which a rectangle edge near a pixel
+# centre leaves a tag bit undecided, and the same for a corner near the camera
+# plane (voxels).  A float32 evaluation of the projection, one rounding per
+# operation, stays within 1.4e-4 pixels and 1e-4 voxels of the double-precision
+# one on ring cameras up to 192^3 grids and 768-pixel images
+# (tests/test_oracle_hull.py measures it), so decisions outside these margins
+# are the same in both precisions.
+HULL_EPS = 1e-3
+HULL_EPS_Z = 1e-3
 
 
 class Lut(ctypes.Structure):
@@ -90,7 +105,10 @@ def _load():
             "orc_scatter_source": (None, [_I64, _P, _P, _P, _P]),
             "orc_reconstruct": (None, [_P, _P, _P, _P, ctypes.c_int, _P, _P, _P, _P,
                                        ctypes.c_int, ctypes.c_int, _P, _P, _P, ctypes.c_double, _P]),
-            "orc_visual_hull": (None, [_P, _P, ctypes.c_int, _P, _P]),
+            "orc_visual_hull": (None, [_P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_double, ctypes.c_double]),
+            "orc_set_threads": (None, [ctypes.c_int]),
+            "orc_threads": (ctypes.c_int, []),
+            "orc_round_storage": (None, [_I64, _P, ctypes.c_int]),
             "orc_volume_rmse": (_I64, [_I64, _P, _P, _P, ctypes.c_uint32, _P]),
             "orc_volume_dims": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_double, _P, _P, _P]),
             "orc_scatter_L6": (None, [_P, _P, _P]),
@@ -140,12 +158,31 @@ def make_cams(cams) -> ctypes.Array:
 
 
 def make_params(step=1.0, alpha_l=0.001, alpha_d=1.0, tau=0.0, g_std=0.0,
-                flame_thresh=30.0 / 255.0, seed=0, clamp_nonneg=1, hg_g=0.0, sequential=0) -> Params:
+                flame_thresh=30.0 / 255.0, seed=0, clamp_nonneg=1, hg_g=0.0, sequential=0,
+                storage=None) -> Params:
+    """storage: None / "f64" (records held in double), "bf16" or "f16" (the
+    loop's stored records rounded to that type, as in 16-bit storage)."""
     p = Params()
     p.step, p.alpha_l, p.alpha_d, p.tau = float(step), float(alpha_l), float(alpha_d), float(tau)
     p.g_std, p.flame_thresh, p.seed, p.clamp_nonneg = float(g_std), float(flame_thresh), int(seed), int(clamp_nonneg)
     p.hg_g, p.sequential = float(hg_g), int(sequential)
+    p.storage = STORAGE[storage]
     return p
+
+
+def set_threads(n: int) -> int:
+    """Threads for the oracle's pixel and node loops (1 by default); returns
+    the count it will use (1 without OpenMP)."""
+    lib = _load()
+    lib.orc_set_threads(int(n))
+    return int(lib.orc_threads())
+
+
+def round_storage(x, storage):
+    """x (float64 array) rounded to a 16-bit storage type ("bf16" or "f16")."""
+    a = _f64(x).copy()
+    _load().orc_round_storage(a.size, _ptr(a), STORAGE[storage])
+    return a
 
 
 def _npix(cams) -> int:
@@ -340,14 +377,18 @@ def scatter_source(vol, albedo, J):
     return out
 
 
-def visual_hull(scene: Scene, mask):
-    """Algorithm 1: per-node view bits (uint32, (nz, ny, nx)) from flame masks (K, H, W)."""
+def visual_hull(scene: Scene, mask, with_undecided=False, eps=HULL_EPS, eps_z=HULL_EPS_Z):
+    """Algorithm 1: per-node view bits (uint32, (nz, ny, nx)) from flame masks
+    (K, H, W).  with_undecided: also the bits that are not fixed to a margin of
+    eps pixels (rectangle edges) and eps_z voxels (camera plane)."""
     lib = _load()
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
     nx, ny, nz = scene.shape
     tags = np.zeros((nz, ny, nx), dtype=np.uint32)
-    lib.orc_visual_hull(ctypes.byref(scene.grid), scene.cams, scene.ncam, _ptr(mask), _ptr(tags))
-    return tags
+    amb = np.zeros((nz, ny, nx), dtype=np.uint32)
+    lib.orc_visual_hull(ctypes.byref(scene.grid), scene.cams, scene.ncam, _ptr(mask), _ptr(tags), _ptr(amb),
+                        float(eps), float(eps_z))
+    return (tags, amb) if with_undecided else tags
 
 
 def reconstruct(scene: Scene, vol, params: Params, targets, mask, bbox, iters,

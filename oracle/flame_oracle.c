@@ -37,6 +37,12 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_THREAD() omp_get_thread_num()
+#else
+#define ORC_THREAD() 0
+#endif
 
 #define ORC_PI 3.14159265358979323846
 
@@ -64,8 +70,12 @@ typedef struct {
     int32_t pad_;
     double hg_g;         /* Henyey-Greenstein asymmetry of the in-scattering (Eq. 9); 0: isotropic */
     int32_t sequential;  /* 1: views update the volume one after another (Kaczmarz order) */
-    int32_t pad2_;
+    int32_t storage;     /* orc_reconstruct: 0 records held in double; ORC_BF16 / ORC_F16: every
+                            record the loop stores (volume, in-scattering source) is rounded to
+                            that type, as a volume kept in 16-bit storage is */
 } orc_params;
+
+enum { ORC_STORE_F64 = 0, ORC_BF16 = 1, ORC_F16 = 2 };
 
 /* Temperature-to-RGB table (Sec. 3.3.3): m entries over [t_min, t_max]. */
 typedef struct {
@@ -171,6 +181,55 @@ static void corners(const orc_grid *g, const int c[3], const double f[3],
         w[b] = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) *
                (dz ? f[2] : 1.0 - f[2]);
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Threads and storage types                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Threads the pixel loops of rendering and adjustment and the node loop of
+ * the visual hull run on (1 unless set; OpenMP builds only).  Pixels are
+ * independent, so renders do not depend on it; the adjustment sums each
+ * thread's share in its own buffer and adds the buffers in thread order, so
+ * its sums are regrouped (FP64 rounding only) when the count changes. */
+static int g_threads = 1;
+
+void orc_set_threads(int n) { g_threads = n > 1 ? n : 1; }
+
+/* Threads the next parallel loop can use (1 in a build without OpenMP). */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return g_threads;
+#else
+    return 1;
+#endif
+}
+
+/* x rounded to the nearest value with `bits` significant binary digits
+ * (ties to even), whose exponent is at least e_min (below it, numbers are
+ * spaced 2^(e_min - bits + 1) apart, the subnormals of the type): the
+ * rounding of a binary floating-point type with that many digits and that
+ * smallest normal exponent.  Overflow is not handled (the fields here stay
+ * far below the types' largest values). */
+static double round_digits(double x, int bits, int e_min)
+{
+    if (x == 0.0 || !isfinite(x)) return x;
+    int e;
+    frexp(x, &e);                    /* |x| in [2^(e-1), 2^e) */
+    if (e - 1 < e_min) e = e_min + 1;
+    const double q = ldexp(1.0, e - bits);   /* spacing of the representable values there */
+    return nearbyint(x / q) * q;     /* the default rounding mode: to nearest, ties to even */
+}
+
+/* Round n values to a 16-bit storage type: bfloat16 (8 significant digits,
+ * the exponent range of float32, smallest normal 2^-126) or IEEE binary16
+ * (11 digits, smallest normal 2^-14).  mode 0 leaves them. */
+void orc_round_storage(int64_t n, double *x, int mode)
+{
+    if (mode == ORC_STORE_F64) return;
+    const int bits = mode == ORC_BF16 ? 8 : 11, e_min = mode == ORC_BF16 ? -126 : -14;
+    for (int64_t i = 0; i < n; ++i) x[i] = round_digits(x[i], bits, e_min);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -410,12 +469,15 @@ static int64_t render_views(const orc_grid *g, const orc_field *F, const orc_cam
     int64_t total = 0, off = 0;
     for (int v = 0; v < ncam; ++v) {
         const orc_cam *c = cams + v;
+        int64_t view_total = 0;
+#pragma omp parallel for num_threads(g_threads) schedule(static, 1) reduction(+ : view_total)
         for (int py = 0; py < c->height; ++py)
             for (int px = 0; px < c->width; ++px) {
                 int64_t pix = off + (int64_t)py * c->width + px;
-                total += render_pixel(g, F, c, P, px, py, out + 3 * pix,
-                                      t_out ? t_out + pix : NULL);
+                view_total += render_pixel(g, F, c, P, px, py, out + 3 * pix,
+                                           t_out ? t_out + pix : NULL);
             }
+        total += view_total;
         off += (int64_t)c->width * c->height;
     }
     return total;
@@ -568,10 +630,26 @@ static int64_t update_paper_views(const orc_grid *g, const double *vol, const or
                                   const uint8_t *mask, int iteration, int view_base, double *dV)
 {
     orc_field F = {ORC_RGB, vol, NULL};
+    const int64_t nodes = (int64_t)g->nx * g->ny * g->nz;
+    /* one accumulator per thread (the first is dV itself), added in thread
+     * order at the end */
+    int nt = orc_threads();
+    double **acc = malloc(sizeof(double *) * (size_t)nt);
+    acc[0] = dV;
+    for (int t = 1; t < nt; ++t) {
+        acc[t] = calloc((size_t)(3 * nodes), sizeof(double));
+        if (!acc[t]) {   /* out of memory: the remaining work runs on fewer threads */
+            nt = t;
+            break;
+        }
+    }
     int64_t total = 0, off = 0;
     for (int v = 0; v < ncam; ++v) {
         const orc_cam *c = cams + v;
-        for (int py = 0; py < c->height; ++py)
+        int64_t view_total = 0;
+#pragma omp parallel for num_threads(nt) schedule(static, 1) reduction(+ : view_total)
+        for (int py = 0; py < c->height; ++py) {
+            double *dst = acc[ORC_THREAD()];
             for (int px = 0; px < c->width; ++px) {
                 int64_t pix = off + (int64_t)py * c->width + px;
                 if (!mask[pix]) continue;
@@ -580,7 +658,7 @@ static int64_t update_paper_views(const orc_grid *g, const double *vol, const or
                 camera_ray(g, c, px, py, o, d);
                 if (!clip_ray(g, o, d, &t0, &t1)) continue;
                 int64_t n = segment_count(t0, t1, P->step);
-                total += n;
+                view_total += n;
                 double T = 1.0;
                 for (int64_t k = 0; k < n; ++k) {
                     double len, p[3];
@@ -595,7 +673,7 @@ static int64_t update_paper_views(const orc_grid *g, const double *vol, const or
                         double dx = p[0] - (double)ji, dy = p[1] - (double)jj, dz = p[2] - (double)jk;
                         double D = sqrt(dx * dx + dy * dy + dz * dz);
                         double a = G * P->alpha_l * T * exp(-P->alpha_d * D);
-                        for (int ch = 0; ch < 3; ++ch) dV[3 * j + ch] += a * dL[ch];
+                        for (int ch = 0; ch < 3; ++ch) dst[3 * j + ch] += a * dL[ch];
                     }
                     if (P->tau > 0.0)
                         T *= 1.0 - P->tau;
@@ -603,8 +681,15 @@ static int64_t update_paper_views(const orc_grid *g, const double *vol, const or
                         T *= exp(-s.sigma * len);
                 }
             }
+        }
+        total += view_total;
         off += (int64_t)c->width * c->height;
     }
+    for (int t = 1; t < nt; ++t) {
+        for (int64_t i = 0; i < 3 * nodes; ++i) dV[i] += acc[t][i];
+        free(acc[t]);
+    }
+    free(acc);
     return total;
 }
 
@@ -857,76 +942,91 @@ static void view_direction(const orc_grid *g, const orc_cam *c, double omega[3])
  * lies in the image rectangle that bounds the projection of the box of the
  * eight cells sharing j ([j-1, j+1] per axis, clipped to the volume) -- every
  * ray that can sample one of those cells passes through that rectangle, so
- * the tags are conservative.  The projection decides an integer, so it is
- * evaluated in single precision, one rounding per operation, in this order:
- *   o = (pos - origin) * (1 / h)                (camera in voxel units)
- *   x_c = ((X - o_x) r_x + (Y - o_y) r_y) + (Z - o_z) r_z   (same for up, fwd)
- *   u = ((x_c / z_c) / t_x + 1) (W / 2) - 1/2,  t_x = tan_half W / H
- *   v = (1 - (y_c / z_c) / t_y) (H / 2) - 1/2,  t_y = tan_half
- * and the pixel range is [ceil(u_min), floor(u_max)] x [ceil(v_min), floor(v_max)]
- * clipped to the image; a corner with z_c <= 0 makes it the whole image. */
-static float dot3f(float ax, float ay, float az, const float r[3])
+ * the tags are conservative.  The corners are projected in double precision:
+ *   u = (x_c / z_c / t_x + 1) W / 2 - 1/2,  t_x = tan_half W / H,
+ *   v = (1 - y_c / z_c / t_y) H / 2 - 1/2,  t_y = tan_half,
+ * (x_c, y_c, z_c) the corner relative to the camera along right, up, fwd, in
+ * voxel units; the pixel centres inside are columns ceil(u_min)..floor(u_max)
+ * and rows ceil(v_min)..floor(v_max), clipped to the image; a corner with
+ * z_c <= 0 (beside or behind the camera) makes it the whole image.
+ *
+ * Whether a pixel centre lies in the rectangle is an integer decision, which
+ * an evaluation in another precision may take differently when a rectangle
+ * edge lies within its rounding error of a pixel centre.  amb (nullable)
+ * receives, per node, the views whose bit changes when every edge of the
+ * rectangle moves in or out by eps pixels, or when a corner lies within eps_z
+ * voxels of the camera plane: the decisions that are not fixed to that
+ * margin. */
+
+/* 1 when a flame pixel of view v has its centre in [u0, u1] x [w0, w1]. */
+static int flame_in_rect(const uint8_t *mask, const orc_cam *c, int v, double u0, double u1,
+                         double w0, double w1)
 {
-    float t = ax * r[0];
-    t = t + ay * r[1];
-    t = t + az * r[2];
-    return t;
+    double x0 = ceil(u0), x1 = floor(u1), y0 = ceil(w0), y1 = floor(w1);
+    if (x0 < 0.0) x0 = 0.0;
+    if (y0 < 0.0) y0 = 0.0;
+    if (x1 > (double)(c->width - 1)) x1 = (double)(c->width - 1);
+    if (y1 > (double)(c->height - 1)) y1 = (double)(c->height - 1);
+    if (!(x0 <= x1) || !(y0 <= y1)) return 0;
+    for (int py = (int)y0; py <= (int)y1; ++py)
+        for (int px = (int)x0; px <= (int)x1; ++px)
+            if (mask[((int64_t)v * c->height + py) * c->width + px]) return 1;
+    return 0;
 }
 
 void orc_visual_hull(const orc_grid *g, const orc_cam *cams, int ncam, const uint8_t *mask,
-                     uint32_t *tags)
+                     uint32_t *tags, uint32_t *amb, double eps, double eps_z)
 {
     const int n[3] = {g->nx, g->ny, g->nz};
-    const float inv_h = 1.0f / (float)g->h;
+#pragma omp parallel for num_threads(g_threads) schedule(static, 1)
     for (int k = 0; k < n[2]; ++k)
         for (int j = 0; j < n[1]; ++j)
             for (int i = 0; i < n[0]; ++i) {
-                uint32_t tag = 0;
+                uint32_t tag = 0, unsure = 0;
                 const int lo[3] = {i > 0 ? i - 1 : 0, j > 0 ? j - 1 : 0, k > 0 ? k - 1 : 0};
                 const int hi[3] = {i < n[0] - 1 ? i + 1 : n[0] - 1, j < n[1] - 1 ? j + 1 : n[1] - 1,
                                    k < n[2] - 1 ? k + 1 : n[2] - 1};
                 for (int v = 0; v < ncam; ++v) {
                     const orc_cam *c = cams + v;
-                    float o[3], r[3], u[3], f[3];
-                    for (int a = 0; a < 3; ++a) {
-                        o[a] = ((float)c->pos[a] - (float)g->origin[a]) * inv_h;
-                        r[a] = (float)c->right[a];
-                        u[a] = (float)c->up[a];
-                        f[a] = (float)c->fwd[a];
-                    }
-                    const float ty = (float)c->tan_half_fov;
-                    const float tx = ty * (float)c->width / (float)c->height;
-                    const float hw = 0.5f * (float)c->width, hh = 0.5f * (float)c->height;
-                    float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
-                    int behind = 0;
+                    const double ty = c->tan_half_fov;
+                    const double tx = ty * (double)c->width / (double)c->height;
+                    double umin = INFINITY, umax = -INFINITY, wmin = INFINITY, wmax = -INFINITY;
+                    int behind = 0, near_plane = 0;
                     for (int b = 0; b < 8; ++b) {
-                        const float X = (float)((b & 1) ? hi[0] : lo[0]) - o[0];
-                        const float Y = (float)((b & 2) ? hi[1] : lo[1]) - o[1];
-                        const float Z = (float)((b & 4) ? hi[2] : lo[2]) - o[2];
-                        const float xc = dot3f(X, Y, Z, r), yc = dot3f(X, Y, Z, u), zc = dot3f(X, Y, Z, f);
-                        if (!(zc > 0.0f)) { behind = 1; break; }
-                        const float uu = ((xc / zc) / tx + 1.0f) * hw - 0.5f;
-                        const float vv = (1.0f - (yc / zc) / ty) * hh - 0.5f;
-                        if (uu < umin) umin = uu;
-                        if (uu > umax) umax = uu;
-                        if (vv < vmin) vmin = vv;
-                        if (vv > vmax) vmax = vv;
+                        const int corner[3] = {(b & 1) ? hi[0] : lo[0], (b & 2) ? hi[1] : lo[1],
+                                               (b & 4) ? hi[2] : lo[2]};
+                        double xc = 0.0, yc = 0.0, zc = 0.0;
+                        for (int a = 0; a < 3; ++a) {
+                            const double X = (double)corner[a] - (c->pos[a] - g->origin[a]) / g->h;
+                            xc += X * c->right[a];
+                            yc += X * c->up[a];
+                            zc += X * c->fwd[a];
+                        }
+                        if (fabs(zc) <= eps_z) near_plane = 1;
+                        if (!(zc > 0.0)) {
+                            behind = 1;
+                            continue;
+                        }
+                        const double u = (xc / zc / tx + 1.0) * 0.5 * (double)c->width - 0.5;
+                        const double w = (1.0 - yc / zc / ty) * 0.5 * (double)c->height - 0.5;
+                        if (u < umin) umin = u;
+                        if (u > umax) umax = u;
+                        if (w < wmin) wmin = w;
+                        if (w > wmax) wmax = w;
                     }
-                    int x0 = 0, x1 = c->width - 1, y0 = 0, y1 = c->height - 1;
-                    if (!behind) {
-                        const float cx0 = ceilf(umin), cx1 = floorf(umax), cy0 = ceilf(vmin), cy1 = floorf(vmax);
-                        x0 = cx0 > 0.0f ? (cx0 < (float)c->width ? (int)cx0 : c->width) : 0;
-                        x1 = cx1 < (float)(c->width - 1) ? (cx1 >= -1.0f ? (int)cx1 : -1) : c->width - 1;
-                        y0 = cy0 > 0.0f ? (cy0 < (float)c->height ? (int)cy0 : c->height) : 0;
-                        y1 = cy1 < (float)(c->height - 1) ? (cy1 >= -1.0f ? (int)cy1 : -1) : c->height - 1;
+                    int hit, shrunk, grown;
+                    if (behind) {
+                        hit = shrunk = grown = flame_in_rect(mask, c, v, -INFINITY, INFINITY, -INFINITY, INFINITY);
+                    } else {
+                        hit = flame_in_rect(mask, c, v, umin, umax, wmin, wmax);
+                        shrunk = flame_in_rect(mask, c, v, umin + eps, umax - eps, wmin + eps, wmax - eps);
+                        grown = flame_in_rect(mask, c, v, umin - eps, umax + eps, wmin - eps, wmax + eps);
                     }
-                    int hit = 0;
-                    for (int py = y0; py <= y1 && !hit; ++py)
-                        for (int px = x0; px <= x1; ++px)
-                            if (mask[((int64_t)v * c->height + py) * c->width + px]) { hit = 1; break; }
                     if (hit) tag |= 1u << v;
+                    if (shrunk != grown || near_plane) unsure |= 1u << v;
                 }
                 tags[node_index(g, i, j, k)] = tag;
+                if (amb) amb[node_index(g, i, j, k)] = unsure;
             }
 }
 
@@ -1030,6 +1130,9 @@ static int64_t view_residual(int height, int width, const double *rendered, cons
  * each iteration.  targets must have been through orc_prepare_targets (mask,
  * bbox).  rmse (iters x 3) gets the error of the images rendered in each
  * iteration.  samples[0..1] accumulate forward and adjustment sample counts.
+ * P->storage != 0 keeps the records in a 16-bit type: the volume is rounded
+ * to it on entry and after every update, the in-scattering source each time it
+ * is formed (orc_round_storage).
  *
  * Variants the paper mentions without using (Sec. 3.3.1, Eq. 9; Sec. 3.3.2):
  * P->hg_g != 0 scatters with the Henyey-Greenstein phase function: each view
@@ -1062,12 +1165,17 @@ void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
     if (hull)
         for (int64_t j = 0; j < nodes; ++j)
             if (hull[j] != full) vol[4 * j] = vol[4 * j + 1] = vol[4 * j + 2] = vol[4 * j + 3] = 0.0;
+    /* a volume in 16-bit storage holds only values of that type: the records
+     * the loop keeps (the volume after each update and the source records it
+     * renders) are rounded to it */
+    orc_round_storage(4 * nodes, vol, P->storage);
     for (int it = 0; it < iters; ++it) {
         if (!per_view) {
             const double *rvol = vol;
             if (albedo) {
                 orc_scatter_J(g, vol, J);
                 orc_scatter_source(nodes, vol, albedo, J, src);
+                orc_round_storage(4 * nodes, src, P->storage);
                 rvol = src;
             }
             samples[0] += orc_render(g, rvol, cams, ncam, P, img, NULL);
@@ -1075,6 +1183,7 @@ void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
             memset(dV, 0, sizeof(double) * 3 * (size_t)nodes);
             samples[1] += orc_update_paper(g, rvol, cams, ncam, P, res, mask, first_iteration + it, dV);
             orc_apply_update(nodes, vol, dV, P->clamp_nonneg);
+            orc_round_storage(4 * nodes, vol, P->storage);
             if (hull)
                 for (int64_t j = 0; j < nodes; ++j)
                     if (hull[j] != full) vol[4 * j] = vol[4 * j + 1] = vol[4 * j + 2] = vol[4 * j + 3] = 0.0;
@@ -1092,9 +1201,11 @@ void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
                         view_direction(g, c, omega);
                         orc_hg_weights(P->hg_g, omega, w);
                         orc_scatter_source_hg(nodes, vol, albedo, J, w, src);
+                        orc_round_storage(4 * nodes, src, P->storage);
                     } else if (v == 0 || P->sequential) {
                         orc_scatter_J(g, vol, J);
                         orc_scatter_source(nodes, vol, albedo, J, src);
+                        orc_round_storage(4 * nodes, src, P->storage);
                     }
                     rvol = src;
                 }
@@ -1105,6 +1216,7 @@ void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
                                                  first_iteration + it, v, dV);
                 if (P->sequential) {
                     orc_apply_update(nodes, vol, dV, P->clamp_nonneg);
+                    orc_round_storage(4 * nodes, vol, P->storage);
                     memset(dV, 0, sizeof(double) * 3 * (size_t)nodes);
                     if (hull)
                         for (int64_t j = 0; j < nodes; ++j)
@@ -1114,6 +1226,7 @@ void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
             }
             if (!P->sequential) {
                 orc_apply_update(nodes, vol, dV, P->clamp_nonneg);
+                orc_round_storage(4 * nodes, vol, P->storage);
                 if (hull)
                     for (int64_t j = 0; j < nodes; ++j)
                         if (hull[j] != full) vol[4 * j] = vol[4 * j + 1] = vol[4 * j + 2] = vol[4 * j + 3] = 0.0;

@@ -1033,7 +1033,11 @@ float* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
 // Device address of g_noalloc_partials on `device`, looked up once per device
 // with that device current.  In host code the array's name is only a host
-// stand-in: kernels must be given this address.
+// stand-in: kernels must be given this address.  The same one-time set-up
+// loads every kernel the entry point launches: with lazy module loading (the
+// default since CUDA 12) the array, the module and each kernel would
+// otherwise be loaded -- taking device memory -- at their first use, which
+// could fail in a process whose pool already holds all device memory.
 fr_status noalloc_scratch(fr_ctx* c, int device, float** out)
 {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -1043,8 +1047,13 @@ fr_status noalloc_scratch(fr_ctx* c, int device, float** out)
         FR_CUDA(c, cudaSetDevice(device));
         void* addr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_partials);
+        const char* what = "cudaGetSymbolAddress(g_noalloc_partials)";
+        if (e == cudaSuccess) {
+            e = preload_noalloc_kernels();
+            what = "loading the render kernels";
+        }
         cudaSetDevice(prev);
-        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetSymbolAddress(g_noalloc_partials)");
+        if (e != cudaSuccess) return cuda_fail(c, e, what);
         g_noalloc_ptr[device] = static_cast<float*>(addr);
     }
     *out = g_noalloc_ptr[device];
@@ -1140,6 +1149,7 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         FR_TRY(check_dev(c, q.targets, ib, "targets"));
         FR_TRY(check_dev(c, q.bbox, (size_t)q.ncam * 16, "bbox"));
         if (q.rmse) FR_TRY(check_dev(c, q.rmse, (size_t)iters * 12, "rmse"));
+        if (hull && q.hull_tags) FR_TRY(check_dev(c, q.hull_tags, (size_t)node_count(&q.vol) * 4, "hull_tags"));
         const long long npix = (long long)q.ncam * q.cams[0].width * q.cams[0].height;
         if (npix >= (1LL << 32)) return fail(c, FR_EINVAL, "probs[%d]: at most 2^32 pixels", i);
         const int nt = tiles_of(q.cams[0].width, q.cams[0].height, q.ncam);
@@ -1209,7 +1219,9 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         const int nbx = bricks_along(q.vol.nx), nby = bricks_along(q.vol.ny), nbz = bricks_along(q.vol.nz);
         const unsigned full = q.ncam >= 32 ? 0xffffffffu : ((1u << q.ncam) - 1u);
         if (hull) {
-            FR_TRY(hull_tags(c, a, q.targets, p->flame_thresh, tags));
+            // the problem's own tags when given, else its hull from its targets
+            if (q.hull_tags) tags = const_cast<unsigned*>(reinterpret_cast<const unsigned*>(q.hull_tags));
+            else FR_TRY(hull_tags(c, a, q.targets, p->flame_thresh, tags));
             FR_CUDA(c, launch_hull_clear(q.vol.data, dt, q.vol.nx, q.vol.ny, q.vol.nz, tags, full, hb, s));
         }
         ProbDev& P = a.p;

@@ -23,6 +23,11 @@ inline int tiles_of(int W, int H, int ncam)
 
 // march.cu
 cudaError_t launch_fwd(const SingleArgs& a, int dt, int kind, int ntiles, cudaStream_t s);
+// Loads the kernels the allocation-free render launches (the forward march
+// gathering records one by one, every storage type, kind and opacity mode,
+// and the one-CTA error reduction) on the current device, so that their first
+// launch needs no module loading.
+cudaError_t preload_noalloc_kernels();
 cudaError_t launch_fwd_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
                              int dt, int kind, bool tau, bool pairs, cudaStream_t s, bool skip = false);
 // x-pair records of every problem's volume (vol_rw -> pairs), RGB records

@@ -995,6 +995,25 @@ cudaError_t launch_fwd(const SingleArgs& a, int dt, int kind, int ntiles, cudaSt
     return cudaGetLastError();
 }
 
+cudaError_t preload_noalloc_kernels()
+{
+    // cudaFuncGetAttributes loads a kernel's module code (lazy loading
+    // otherwise loads it, and allocates for it, at the first launch)
+    cudaFuncAttributes attr;
+    cudaError_t e = cudaFuncGetAttributes(&attr, finalize_partials);
+#define FR_PRELOAD(D, K, T) \
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&attr, fwd_single<D, K, T, 0>)
+#define FR_PRELOAD_DT(D)                                                                      \
+    FR_PRELOAD(D, KIND_RGB, false); FR_PRELOAD(D, KIND_RGB, true); FR_PRELOAD(D, KIND_TEMP, false); \
+    FR_PRELOAD(D, KIND_TEMP, true)
+    FR_PRELOAD_DT(DT_F32);
+    FR_PRELOAD_DT(DT_BF16);
+    FR_PRELOAD_DT(DT_F16);
+#undef FR_PRELOAD_DT
+#undef FR_PRELOAD
+    return e;
+}
+
 cudaError_t launch_fwd_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
                              int dt, int kind, bool tau, bool pairs, cudaStream_t s, bool skip)
 {

@@ -154,7 +154,10 @@ fr_status job_admit(fr_server* s, fr_job* j)
     if (hull) {
         // the job's visual hull from its prepared frames; records outside it cleared
         const unsigned full = j->d.ncam >= 32 ? 0xffffffffu : ((1u << j->d.ncam) - 1u);
-        FR_TRY(hull_tags(c, a, j->targets, s->p.flame_thresh, j->tags));
+        if (j->d.hull_tags)
+            FR_CUDA(c, cudaMemcpyAsync(j->tags, j->d.hull_tags, (size_t)nodes * 4, cudaMemcpyHostToDevice, st));
+        else
+            FR_TRY(hull_tags(c, a, j->targets, s->p.flame_thresh, j->tags));
         FR_CUDA(c, launch_hull_clear(j->vol, s->dtype, j->d.nx, j->d.ny, j->d.nz, j->tags, full, j->hull_bricks, st));
     }
     j->state = FR_JOB_RUNNING;

@@ -47,14 +47,15 @@ class fr_camera(ctypes.Structure):
 class fr_problem(ctypes.Structure):
     _fields_ = [("vol", fr_volume), ("cams", ctypes.c_void_p), ("ncam", ctypes.c_int32),
                 ("pad_", ctypes.c_int32), ("targets", ctypes.c_void_p), ("bbox", ctypes.c_void_p),
-                ("rmse", ctypes.c_void_p)]
+                ("rmse", ctypes.c_void_p), ("hull_tags", ctypes.c_void_p)]
 
 
 class fr_job_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("alpha_l", ctypes.c_float),
                 ("origin", ctypes.c_float * 3), ("h", ctypes.c_float), ("cams", ctypes.c_void_p),
                 ("ncam", ctypes.c_int32), ("iters", ctypes.c_int32), ("init_records", ctypes.c_void_p),
-                ("targets", ctypes.c_void_p), ("result_records", ctypes.c_void_p), ("rmse", ctypes.c_void_p)]
+                ("targets", ctypes.c_void_p), ("result_records", ctypes.c_void_p), ("rmse", ctypes.c_void_p),
+                ("hull_tags", ctypes.c_void_p)]
 
 
 class fr_job_info(ctypes.Structure):
@@ -417,14 +418,16 @@ class Context:
 
     @_nvtx
     def fr_reconstruct_batch(self, problems, iters, p, first_iteration=0, use_graph=True):
-        """problems: sequence of (fr_volume, camera array, targets, bbox, rmse or None)."""
+        """problems: sequence of (fr_volume, camera array, targets, bbox, rmse or None[, hull tags or None])."""
         arr = (fr_problem * len(problems))()
         keep = []
-        for q, (vol, cams, targets, bbox, rmse) in zip(arr, problems):
+        for q, prob in zip(arr, problems):
+            vol, cams, targets, bbox, rmse = prob[:5]
             q.vol = vol
             q.cams = ctypes.cast(cams, ctypes.c_void_p)
             q.ncam = len(cams)
             q.targets, q.bbox, q.rmse = _ptr(targets), _ptr(bbox), _ptr(rmse)
+            q.hull_tags = _ptr(prob[5]) if len(prob) > 5 else None
             keep.append(cams)
         self.check(self.lib.fr_reconstruct_batch(self.h, arr, len(problems), int(iters), int(first_iteration),
                                                  ctypes.byref(p), int(bool(use_graph))))
@@ -473,10 +476,13 @@ class Server:
                                             ctypes.byref(h)))
         self.h = h
 
-    def submit(self, shape, origin, h, cams, iters, init_records, targets, want_rmse=True, alpha_l=0.0) -> Job:
+    def submit(self, shape, origin, h, cams, iters, init_records, targets, want_rmse=True, alpha_l=0.0,
+               hull_tags=None) -> Job:
         """init_records: host numpy array (nz, ny, nx, 4) in the server's storage type
         (uint16 bit patterns for bf16/f16, float32 otherwise); targets: host float32
-        (K, H, W, 3).  Returns a Job whose .result receives the reconstruction."""
+        (K, H, W, 3); hull_tags: host uint32 (nz, ny, nx) tags used instead of the
+        job's own hull (servers with use_hull).  Returns a Job whose .result
+        receives the reconstruction."""
         nx, ny, nz = shape
         init = np.ascontiguousarray(init_records)
         tgt = np.ascontiguousarray(targets, dtype=np.float32)
@@ -492,9 +498,11 @@ class Server:
         d.ncam, d.iters = len(cams), int(iters)
         d.init_records, d.targets, d.result_records = init.ctypes.data, tgt.ctypes.data, result.ctypes.data
         d.rmse = rmse.ctypes.data if rmse is not None else None
+        tags = np.ascontiguousarray(hull_tags, dtype=np.uint32) if hull_tags is not None else None
+        d.hull_tags = tags.ctypes.data if tags is not None else None
         jh = ctypes.c_void_p()
         self.ctx.check(self.lib.fr_server_submit(self.h, ctypes.byref(d), ctypes.byref(jh)))
-        return Job(self, jh, (init, tgt, fcams), result, rmse)
+        return Job(self, jh, (init, tgt, fcams, tags), result, rmse)
 
     @_nvtx
     def step(self):

@@ -37,6 +37,8 @@ def main():
         ctx.fr_adjust(fv, fc, fr.params(step=case.step), res, 0, dV)
         grad = torch.zeros(v.shape[:3] + (4,), device="cuda")
         ctx.fr_render_backward(fv, fc, fr.params(step=case.step), img, res, grad)
+        fr.fr_render_residual_noalloc(0, torch.cuda.current_stream(), fv, fc, fr.params(step=case.step), t, bbox,
+                                      None, res, sq)
     words["render_adjust_backward"] = ctx.fr_check_word(reset=True)
     # the loop: hull, skipping, scattering, variants, stop criterion
     case = plume_case(n=36, views=5, side=56)

@@ -50,3 +50,35 @@ def rel_err(gpu, ref):
     """Element-wise error relative to the largest reference magnitude."""
     scale = float(np.max(np.abs(ref)))
     return np.abs(np.asarray(gpu, dtype=np.float64) - ref) / (scale if scale > 0 else 1.0)
+
+
+def oracle_targets(orc, case, albedo=None, noise=0.0, seed=11, thresh=30 / 255, P=None):
+    """Targets rendered by the oracle from the case's ground truth (through its
+    in-scattering source when albedo is given), normalised to max 1, plus
+    seeded noise; and the oracle's preparation of them.  Returns
+    (scene, raw images, prepared targets, mask, bbox)."""
+    from paper_1809_06417_gb300 import synth
+    sc = orc.Scene(case.shape, case.origin, case.h, case.cams)
+    P = P if P is not None else orc.make_params(step=case.step)
+    src = case.vol if albedo is None else orc.scatter_source(case.vol, albedo, orc.scatter_J(sc, case.vol))
+    img, _ = orc.render(sc, src, P)
+    img = img / img.max()
+    if noise:
+        img = synth.add_noise(img, noise, seed)
+    t_ref, mask, bbox = orc.prepare_targets(img, thresh)
+    return sc, img, t_ref, mask, bbox
+
+
+def tags_on_device(torch, tags):
+    """uint32 hull tags (nz, ny, nx) as the int32 CUDA tensor fr_params.hull_tags takes."""
+    return torch.as_tensor(np.ascontiguousarray(tags, dtype=np.uint32).view(np.int32), device="cuda")
+
+
+def oracle_lut(orc, torch, t_min, t_max, m):
+    """The oracle's colour-temperature table rounded to float32, as the device
+    table the library reads (m x 4, fourth column 0) and as the float64 table
+    the oracle is given: both sides then interpolate the same values."""
+    ref = orc.lut_build(t_min, t_max, m).astype(np.float32)
+    dev = torch.zeros((m, 4), device="cuda")
+    dev[:, :3] = torch.as_tensor(ref, device="cuda")
+    return dev, ref.astype(np.float64)

@@ -28,7 +28,7 @@ def test_library_exports_every_declared_symbol():
 def test_abi_version_and_defaults():
     from paper_1809_06417_gb300 import flamerec
     lib = flamerec.load()
-    assert lib.fr_abi_version() == 1
+    assert lib.fr_abi_version() == 2
     p = flamerec.params()
     # the paper's constants (Sec. 4.1, 4.2, 5.1)
     assert p.step == 1.0 and abs(p.alpha_l - 0.001) < 1e-9 and p.alpha_d == 1.0
@@ -36,10 +36,35 @@ def test_abi_version_and_defaults():
 
 
 def test_struct_layouts():
-    from paper_1809_06417_gb300 import flamerec
-    assert ctypes.sizeof(flamerec.fr_camera) == 64
-    assert ctypes.sizeof(flamerec.fr_volume) == 48
-    assert flamerec.fr_params.lut.offset % 8 == 0
+    """The binding's structures have the header's sizes and field offsets (a C
+    program compiled against include/flamerec.h prints them)."""
+    import subprocess
+    import tempfile
+    from paper_1809_06417_gb300 import flamerec as fr
+    assert ctypes.sizeof(fr.fr_camera) == 64
+    assert ctypes.sizeof(fr.fr_volume) == 48
+    assert fr.fr_params.lut.offset % 8 == 0
+    fields = {"fr_params": ["lut", "hull_tags", "hg_g", "sequential_views"],
+              "fr_problem": ["targets", "rmse", "hull_tags"],
+              "fr_job_desc": ["cams", "init_records", "rmse", "hull_tags"],
+              "fr_job_info": ["t_submit", "footprint"]}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "flamerec.h"', "int main(void) {"]
+    for st, names in fields.items():
+        lines.append(f'printf("{st} %zu\\n", sizeof({st}));')
+        for f in names:
+            lines.append(f'printf("{st}.{f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["return 0; }"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines))
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    got = dict(zip(out[0::2], (int(x) for x in out[1::2])))
+    for st, names in fields.items():
+        cls = getattr(fr, st)
+        assert ctypes.sizeof(cls) == got[st], st
+        for f in names:
+            assert getattr(cls, f).offset == got[f"{st}.{f}"], (st, f)
 
 
 def test_create_fails_cleanly_without_gpu():

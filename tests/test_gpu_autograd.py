@@ -5,7 +5,7 @@ differences at 64 random voxels and against the FP64 oracle gradient."""
 import numpy as np
 import pytest
 
-from gpu_cases import rel_err
+from gpu_cases import oracle_lut, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -72,7 +72,8 @@ def test_autograd_matches_finite_differences_at_full_size(setup):
 
 
 def test_autograd_matches_oracle_gradient(setup, orc):
-    fr, ag, synth, ctx, lut = setup
+    fr, ag, synth, ctx, _ = setup
+    lut, lut_ref = oracle_lut(orc, torch, 800.0, 2000.0, 4096)   # one table for both sides
     n, views, side, step = 32, 3, 48, 0.5
     scene, cams, (shape, origin, h) = _scene(ag, fr, ctx, lut, n, views, side, step, 5)
     vol_np = synth.temperature_volume(n, 5)
@@ -81,7 +82,6 @@ def test_autograd_matches_oracle_gradient(setup, orc):
     img = ag.render(vol, scene)
     gimg = np.random.default_rng(2).normal(size=scene.image_shape)
     img.backward(torch.as_tensor(gimg, dtype=torch.float32, device="cuda"))
-    lut_ref = lut.cpu().numpy()[:, :3].astype(np.float64)
     sc = orc.Scene(shape, origin, h, cams)
     P = orc.make_params(step=step)
     ref_img, _ = orc.render_temp(sc, vol_np, lut_ref, 800.0, 2000.0, P)

@@ -54,3 +54,48 @@ def test_batch_equals_each_problem_alone(use_graph, use_hull):
         assert e.max() < 1e-4
         np.testing.assert_allclose(rb.cpu().numpy(), ra, rtol=1e-4)
     ctx.close()
+
+
+@pytest.mark.parametrize("use_hull", [0, 1])
+def test_batch_follows_oracle(orc, use_hull):
+    """Each problem of a batch (grids, views and image sizes differing; G(s)
+    drawn; the iteration index starting at 2) against orc.reconstruct on the
+    same targets, rendered by the oracle; with the hull, each problem carries
+    the oracle's tags, so both sides use one tag set."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_cases import Case, oracle_targets, tags_on_device
+    from paper_1809_06417_gb300 import flamerec as fr, synth
+    ctx = fr.Context(0)
+    specs = [(24, 3, 40, 11), (32, 5, 56, 12), (20, 4, 33, 13)]
+    iters = 4
+    P = orc.make_params(step=0.5, alpha_l=2e-3, g_std=0.05, seed=9)
+    p = fr.params(step=0.5, alpha_l=2e-3, g_std=0.05, seed=9, use_hull=use_hull)
+    refs, batch, keep = [], [], []
+    for n, views, side, seed in specs:
+        shape, origin, h = synth.unit_grid(n)
+        cams = synth.ring_cameras(views, side, side, elevation_jitter_deg=8.0, seed=seed)
+        case = Case(shape, cams, synth.plume_volume(n, seed)[0], 0.5)
+        sc, img, t_ref, mask, bbox_ref = oracle_targets(orc, case)
+        tags = orc.visual_hull(sc, mask) if use_hull else None
+        v0 = case.vol.copy()
+        v0[..., :3] *= 0.2
+        refs.append(orc.reconstruct(sc, v0, P, t_ref, mask, bbox_ref, iters, first_iteration=2, hull=tags)[:2])
+        v = torch.as_tensor(v0, dtype=torch.float32, device="cuda").contiguous()
+        t_dev = torch.as_tensor(img, dtype=torch.float32, device="cuda").contiguous()
+        bbox = torch.zeros((views, 4), dtype=torch.int32, device="cuda")
+        ctx.fr_prepare_targets(t_dev, 30 / 255, bbox)
+        rm = torch.zeros((iters, 3), device="cuda")
+        tg = tags_on_device(torch, tags) if use_hull else None
+        keep.append((v, rm, t_dev, bbox, tg))
+        batch.append((fr.volume(v, origin, h), fr.cameras(cams), t_dev, bbox, rm, tg))
+    ctx.fr_reconstruct_batch(batch, iters, p, first_iteration=2, use_graph=True)
+    torch.cuda.synchronize()
+    for (vol_ref, rmse_ref), (v, rm, *_) in zip(refs, keep):
+        got = v.cpu().numpy().astype(np.float64)
+        e = rel_err(got[..., :3], vol_ref[..., :3])
+        print(f"batch vs oracle (hull={use_hull}): volume {e.max():.2e}, rmse {rm.cpu().numpy()[-1]} "
+              f"vs {rmse_ref[-1]}")
+        assert e.max() < 1e-3
+        np.testing.assert_allclose(rm.cpu().numpy(), rmse_ref, rtol=1e-3)
+    ctx.close()

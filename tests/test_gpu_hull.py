@@ -1,11 +1,18 @@
-"""Visual hull (Sec. 4.3.1, Algorithm 1) on the GPU: tags equal the oracle's bit
-for bit (the projection is a float32 integer decision taken in the same
-precision and order on both sides), at small and full size; the
-reconstruction loop restricted to the hull follows the oracle."""
+"""Visual hull (Sec. 4.3.1, Algorithm 1) on the GPU against the FP64 oracle.
+
+The kernel projects in float32, the oracle in double precision.  Whether a
+pixel centre lies inside a node's rectangle is an integer decision, so the two
+agree exactly on every tag bit that the oracle reports as decided (no
+rectangle edge within 1e-3 pixel of a pixel centre whose flame decides the
+bit); the undecided bits are counted and bounded, and the GPU's bit there must
+be one of the two answers.  The reconstruction loop restricted to the hull is
+compared with the oracle on one tag set (the oracle's, passed to both)."""
+import os
+
 import numpy as np
 import pytest
 
-from gpu_cases import plume_case, rel_err
+from gpu_cases import oracle_targets, plume_case, rel_err, tags_on_device
 
 pytestmark = pytest.mark.gpu
 
@@ -33,8 +40,22 @@ def _gpu_tags(fr, ctx, shape, origin, h, cams, targets, thresh):
     return tags.cpu().numpy().view(np.uint32)
 
 
+def _compare_tags(got, ref, undecided, what):
+    """Exact on decided bits; on undecided bits the GPU's answer is free."""
+    wrong = (got ^ ref) & ~undecided
+    n_und = int(np.count_nonzero(undecided))
+    n_diff = int(np.count_nonzero((got ^ ref) & undecided))
+    print(f"{what}: {n_und} of {got.size} nodes with undecided bits ({n_und / got.size:.2e}), "
+          f"{n_diff} of them answered the other way")
+    assert not np.any(wrong), np.argwhere(wrong)[:5]
+    return n_und
+
+
 @pytest.mark.parametrize("seed", [0, 1])
-def test_hull_tags_bit_exact_random_masks(orc, fr_ctx, seed):
+def test_hull_tags_match_oracle_random_masks(orc, fr_ctx, seed):
+    """Random masks seen by 7 cameras with odd image widths: the volume's
+    centre node projects exactly onto a pixel centre in every view, so this
+    case holds exact ties (undecided by construction)."""
     fr, ctx = fr_ctx
     from paper_1809_06417_gb300 import synth
     rng = np.random.default_rng(seed)
@@ -45,28 +66,31 @@ def test_hull_tags_bit_exact_random_masks(orc, fr_ctx, seed):
     targets = rng.random((7, 38, 45, 3)) * (rng.random((7, 38, 45, 1)) < 0.2)
     thresh = 0.3
     mask = (targets.max(axis=-1) > thresh).astype(np.uint8)
-    ref = orc.visual_hull(orc.Scene(shape, origin, h, cams), mask)
+    ref, und = orc.visual_hull(orc.Scene(shape, origin, h, cams), mask, with_undecided=True)
     got = _gpu_tags(fr, ctx, shape, origin, h, cams, targets.astype(np.float32), thresh)
-    assert np.array_equal(got, ref), np.argwhere(got != ref)[:5]
+    n_und = _compare_tags(got, ref, und, f"random masks seed {seed}")
+    assert n_und < 0.06 * got.size
 
 
-def test_hull_tags_bit_exact_full_size(orc, fr_ctx):
+def test_hull_tags_match_oracle_full_size(orc, fr_ctx):
+    """128^3 nodes, 8 views of 512^2: masks from the oracle's render of the
+    full-RTE plume; at most 1e-3 of the nodes hold an undecided bit."""
     fr, ctx = fr_ctx
     from paper_1809_06417_gb300 import synth
+    orc.set_threads(os.cpu_count() or 1)
     n, views, side = 128, 8, 512
     shape, origin, h = synth.unit_grid(n)
     cams = synth.ring_cameras(views, side, side, elevation_jitter_deg=10.0, seed=2)
     gt, _ = synth.plume_volume(n, 2)
-    g = torch.as_tensor(gt, dtype=torch.float32, device="cuda").contiguous()
-    img = torch.zeros((views, side, side, 3), device="cuda")
-    ctx.fr_render(fr.volume(g, origin, h), fr.cameras(cams), fr.params(step=0.5), img)
-    img /= img.max()
-    targets = img.cpu().numpy()
+    sc = orc.Scene(shape, origin, h, cams)
+    img, _ = orc.render(sc, gt, orc.make_params(step=0.5))
+    targets = img / img.max()
     thresh = 30 / 255
     mask = (targets.max(axis=-1) > thresh).astype(np.uint8)
-    ref = orc.visual_hull(orc.Scene(shape, origin, h, cams), mask)
+    ref, und = orc.visual_hull(sc, mask, with_undecided=True)
     got = _gpu_tags(fr, ctx, shape, origin, h, cams, targets, thresh)
-    assert np.array_equal(got, ref)
+    n_und = _compare_tags(got, ref, und, "full size")
+    assert n_und < 1e-3 * got.size
     inside = (got == (1 << views) - 1).mean()
     print(f"hull fraction of the volume: {inside:.3f}")
     assert 0.01 < inside < 0.6
@@ -74,15 +98,13 @@ def test_hull_tags_bit_exact_full_size(orc, fr_ctx):
 
 @pytest.mark.parametrize("scatter", [False, True])
 def test_reconstruct_with_hull_follows_oracle(orc, fr_ctx, scatter):
-    """The hull-restricted loop follows the oracle; with in-scattering its
-    sweeps also skip the loads of line chunks in bricks outside the hull."""
+    """The hull-restricted loop follows the oracle on the oracle's tags; with
+    in-scattering its sweeps also skip the loads of line chunks in bricks
+    outside the hull."""
     fr, ctx = fr_ctx
     case = plume_case(n=36, views=6, side=64)
-    sc = orc.Scene(case.shape, case.origin, case.h, case.cams)
     P = orc.make_params(step=case.step, alpha_l=3e-3)
-    img, _ = orc.render(sc, case.vol, P)
-    img /= img.max()
-    t_ref, mask, bbox_ref = orc.prepare_targets(img, 30 / 255)
+    sc, img, t_ref, mask, bbox_ref = oracle_targets(orc, case)
     hull = orc.visual_hull(sc, mask)
     v0 = case.vol.copy()
     v0[..., :3] = 0.01
@@ -95,7 +117,8 @@ def test_reconstruct_with_hull_follows_oracle(orc, fr_ctx, scatter):
     rmse = np.zeros((4, 3), dtype=np.float32)
     alb = torch.as_tensor(case.albedo, dtype=torch.float32, device="cuda").contiguous() if scatter else None
     ctx.fr_reconstruct(fr.volume(v, case.origin, case.h), fr.cameras(case.cams), t_dev, bbox, 4,
-                       fr.params(step=case.step, alpha_l=3e-3, use_hull=1), albedo=alb, rmse=rmse)
+                       fr.params(step=case.step, alpha_l=3e-3, use_hull=1, hull_tags=tags_on_device(torch, hull)),
+                       albedo=alb, rmse=rmse)
     torch.cuda.synchronize()
     got = v.cpu().numpy()
     outside = hull != (1 << len(case.cams)) - 1

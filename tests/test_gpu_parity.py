@@ -13,7 +13,7 @@ Tolerances (float32 arithmetic against float64):
 import numpy as np
 import pytest
 
-from gpu_cases import plume_case, ragged_case, rel_err, tiny_case
+from gpu_cases import oracle_lut, plume_case, ragged_case, rel_err, tiny_case
 
 pytestmark = pytest.mark.gpu
 
@@ -227,10 +227,7 @@ def test_temperature_render_and_gradient(orc, fr, ctx):
     vol = synth.temperature_volume(n, 3)
     case = tiny_case(n=n, views=3, side=40, step=0.5, jitter=7.0)
     case.vol = vol
-    m = 4096
-    lut = torch.zeros((m, 4), device="cuda")
-    ctx.fr_planck_lut(800.0, 2000.0, lut)
-    lut_ref = lut.cpu().numpy()[:, :3].astype(np.float64)  # both sides use the same table values
+    lut, lut_ref = oracle_lut(orc, torch, 800.0, 2000.0, 4096)   # one table for both sides
     sc = oracle_scene(orc, case)
     P = orc.make_params(step=case.step)
     ref, _ = orc.render_temp(sc, vol, lut_ref, 800.0, 2000.0, P)

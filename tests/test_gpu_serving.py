@@ -137,3 +137,38 @@ def test_budget_admission_refusal_cancel_and_wait(env):
         _submit(small, jobs[2], 3, "f32")
     small.close()
     srv.close()
+
+
+@pytest.mark.parametrize("dtype,use_hull", [("f32", 0), ("f32", 1), ("bf16", 1)])
+def test_served_job_follows_oracle(orc, env, dtype, use_hull):
+    """One served job (raw frames prepared by the server at admission) against
+    orc.reconstruct on targets the oracle rendered: float32 storage at the
+    loop tolerance, BF16 storage against the oracle keeping BF16 records at
+    the storage tolerance; with the hull the job carries the oracle's tags."""
+    fr, ctx, _ = env
+    from gpu_cases import Case, oracle_targets
+    from paper_1809_06417_gb300 import synth
+    n, views, side, seed, iters = 24, 6, 40, 22, 6
+    shape, origin, h = synth.unit_grid(n)
+    cams = synth.ring_cameras(views, side, side, elevation_jitter_deg=8.0, seed=seed)
+    case = Case(shape, cams, synth.plume_volume(n, seed)[0], 0.5)
+    sc, img, t_ref, mask, bbox_ref = oracle_targets(orc, case)
+    tags = orc.visual_hull(sc, mask) if use_hull else None
+    init = case.vol.copy()
+    init[..., :3] = 0.0
+    storage = "bf16" if dtype == "bf16" else None
+    if storage:
+        init = orc.round_storage(init, storage)
+    P = orc.make_params(step=0.5, alpha_l=2e-3, storage=storage)
+    ref, r_ref, _ = orc.reconstruct(sc, init, P, t_ref, mask, bbox_ref, iters, hull=tags)
+    srv = fr.Server(ctx, fr.params(step=0.5, alpha_l=2e-3, use_hull=use_hull),
+                    dtype=fr.FR_F32 if dtype == "f32" else fr.FR_BF16)
+    job = srv.submit(shape, origin, h, cams, iters, _records(init, dtype), img.astype(np.float32), hull_tags=tags)
+    job.wait()
+    srv.close()
+    got = _as_float(job.result, dtype)
+    tol = 1e-3 if dtype == "f32" else 1e-2
+    e = rel_err(got[..., :3], ref[..., :3])
+    print(f"served {dtype} hull={use_hull}: volume vs oracle {e.max():.2e}; rmse {job.rmse[-1]} vs {r_ref[-1]}")
+    assert e.max() < tol
+    np.testing.assert_allclose(job.rmse, r_ref, rtol=tol)

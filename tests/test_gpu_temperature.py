@@ -31,8 +31,9 @@ def test_green_to_temperature_follows_oracle(orc, setup):
     table: the segment found can differ only at a node, where both segments
     give that node's temperature, and the fraction carries about 1e-7 of a
     table step (1.2 K), so 1e-3 K bounds the difference."""
-    fr, synth, ctx, lut = setup
-    lut_np = lut.cpu().numpy().astype(np.float64)
+    fr, synth, ctx, _ = setup
+    from gpu_cases import oracle_lut
+    lut, lut_np = oracle_lut(orc, torch, T_MIN, T_MAX, 1024)   # one table for both sides
     rng = np.random.default_rng(5)
     n = 40
     g = rng.uniform(-0.1, 1.2, size=(n, n, n)) * rng.choice([1.0, 1e-4, 1e-7], size=(n, n, n))
@@ -46,7 +47,7 @@ def test_green_to_temperature_follows_oracle(orc, setup):
     ctx.fr_temperature_from_green(fr.volume(src, origin, h), p, fr.volume(out, origin, h, kind=fr.FR_KIND_TEMP))
     torch.cuda.synchronize()
     got = out.cpu().numpy()
-    ref = orc.green_to_temp(rgb[..., 1].astype(np.float64), lut_np[:, :3], T_MIN, T_MAX)
+    ref = orc.green_to_temp(rgb[..., 1].astype(np.float64), lut_np, T_MIN, T_MAX)
     print("max |dT|", np.abs(got[..., 0] - ref).max())
     np.testing.assert_allclose(got[..., 0], ref, rtol=0, atol=1e-3)
     assert np.array_equal(got[..., 1], rgb[..., 3])

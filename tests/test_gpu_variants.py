@@ -4,7 +4,7 @@ vanishing asymmetry the per-view loop matches the standard one."""
 import numpy as np
 import pytest
 
-from gpu_cases import plume_case, rel_err
+from gpu_cases import plume_case, rel_err, tags_on_device
 
 pytestmark = pytest.mark.gpu
 
@@ -51,7 +51,10 @@ def test_variant_follows_oracle(orc, fr_ctx, variant):
     t_dev = torch.as_tensor(img, dtype=torch.float32, device="cuda").contiguous()
     bbox = torch.zeros((len(case.cams), 4), dtype=torch.int32, device="cuda")
     ctx.fr_prepare_targets(t_dev, 30 / 255, bbox)
-    got, rmse = _run_gpu(fr, ctx, case, t_dev, bbox, v0, 3, **variant)
+    kw = dict(variant)
+    if hull is not None:
+        kw["hull_tags"] = tags_on_device(torch, hull)   # one tag set for both sides
+    got, rmse = _run_gpu(fr, ctx, case, t_dev, bbox, v0, 3, **kw)
     e = rel_err(got[..., :3], ref[..., :3])
     print(f"{variant}: max {e.max():.2e}, rmse {rmse[-1]} vs {r_ref[-1]}")
     np.testing.assert_allclose(rmse, r_ref, rtol=1e-3)

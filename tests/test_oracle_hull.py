@@ -196,3 +196,92 @@ def test_volume_rmse_in_hull(orc):
     assert n3 == a.size // 4 and np.allclose(r3, 0.5, atol=1e-15)
     r4, n4 = orc.volume_rmse(a, b, np.zeros_like(tags), full)
     assert n4 == 0 and np.all(r4 == 0.0)
+
+
+def _numpy_hull(shape, origin, h, cams, mask, dt):
+    """The hull rule evaluated independently, vectorised over nodes: every
+    lattice point projected once (in float64, or in float32 with one rounding
+    per operation in the order a float32 kernel takes), each node's rectangle
+    the extremes over its box's eight corners, flame pixels counted with a
+    summed-area table.  Returns (tags, u and v of every lattice point)."""
+    nx, ny, nz = shape
+    tags = np.zeros((nz, ny, nx), dtype=np.uint32)
+    K, J, I = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    lo = [np.maximum(a - 1, 0) for a in (I, J, K)]
+    hi = [np.minimum(a + 1, n - 1) for a, n in zip((I, J, K), (nx, ny, nz))]
+    uvs = []
+    for v, c in enumerate(cams):
+        W, H = c["width"], c["height"]
+        if dt == np.float32:
+            f = np.float32
+            o = [(f(c["pos"][a]) - f(origin[a])) * (f(1.0) / f(h)) for a in range(3)]
+            X = [np.arange(n, dtype=f) - o[a] for a, n in enumerate((nx, ny, nz))]
+            Xk, Xj, Xi = np.meshgrid(X[2], X[1], X[0], indexing="ij")
+
+            def dot(r):
+                return (Xi * f(r[0]) + Xj * f(r[1])) + Xk * f(r[2])
+            xc, yc, zc = dot(c["right"]), dot(c["up"]), dot(c["fwd"])
+            ty = f(c["tan_half_fov"])
+            tx = ty * f(W) / f(H)
+            u = ((xc / zc) / tx + f(1.0)) * (f(0.5) * f(W)) - f(0.5)
+            w = (f(1.0) - (yc / zc) / ty) * (f(0.5) * f(H)) - f(0.5)
+        else:
+            o = (np.asarray(c["pos"]) - np.asarray(origin)) / h
+            P = np.stack([I - o[0], J - o[1], K - o[2]], axis=-1)
+            xc, yc, zc = P @ np.asarray(c["right"]), P @ np.asarray(c["up"]), P @ np.asarray(c["fwd"])
+            ty = c["tan_half_fov"]
+            tx = ty * W / H
+            u = (xc / zc / tx + 1.0) * 0.5 * W - 0.5
+            w = (1.0 - yc / zc / ty) * 0.5 * H - 0.5
+        assert np.all(zc > 0)
+        uvs.append((u.astype(np.float64), w.astype(np.float64)))
+        corners = [(ci, cj, ck) for ck in (lo[2], hi[2]) for cj in (lo[1], hi[1]) for ci in (lo[0], hi[0])]
+        us = np.stack([u[ck, cj, ci] for ci, cj, ck in corners])
+        ws = np.stack([w[ck, cj, ci] for ci, cj, ck in corners])
+        x0 = np.clip(np.ceil(us.min(0)), 0, W).astype(np.int64)
+        x1 = np.clip(np.floor(us.max(0)), -1, W - 1).astype(np.int64)
+        y0 = np.clip(np.ceil(ws.min(0)), 0, H).astype(np.int64)
+        y1 = np.clip(np.floor(ws.max(0)), -1, H - 1).astype(np.int64)
+        sat = np.zeros((H + 1, W + 1), dtype=np.int64)
+        sat[1:, 1:] = np.cumsum(np.cumsum(mask[v].astype(np.int64), axis=0), axis=1)
+        ok = (x0 <= x1) & (y0 <= y1)
+        cnt = (sat[np.where(ok, y1 + 1, 0), np.where(ok, x1 + 1, 0)] - sat[np.where(ok, y0, 0), np.where(ok, x1 + 1, 0)]
+               - sat[np.where(ok, y1 + 1, 0), np.where(ok, x0, 0)] + sat[np.where(ok, y0, 0), np.where(ok, x0, 0)])
+        tags |= np.where(ok & (cnt > 0), np.uint32(1 << v), np.uint32(0))
+    return tags, uvs
+
+
+@pytest.mark.parametrize("n,views,side,seed", [(7, 3, 13, 0), (16, 5, 41, 1), (24, 8, 64, 2)])
+def test_undecided_bits_cover_every_precision_dependent_decision(orc, n, views, side, seed):
+    """An independent evaluation of the rule agrees with the oracle on every
+    decided bit, in float64 and in float32 alike; the undecided bits (edge
+    within HULL_EPS of a flame pixel centre) are few; and the float32
+    projection's error is far inside the margin."""
+    rng = np.random.default_rng(seed)
+    shape, origin, h = synth.unit_grid(n)
+    cams = synth.ring_cameras(views, side, side - 2, elevation_jitter_deg=15, seed=seed)
+    mask = (rng.random((views, side - 2, side)) < 0.3).astype(np.uint8)
+    tags, und = orc.visual_hull(orc.Scene(shape, origin, h, cams), mask, with_undecided=True)
+    t64, uv64 = _numpy_hull(shape, origin, h, cams, mask, np.float64)
+    t32, uv32 = _numpy_hull(shape, origin, h, cams, mask, np.float32)
+    assert not np.any((t64 ^ tags) & ~und)
+    assert not np.any((t32 ^ tags) & ~und)
+    assert np.count_nonzero(und) < 0.1 * und.size
+    err = max(np.abs(a - b).max() for p, q in zip(uv32, uv64) for a, b in zip(p, q))
+    assert err < orc.HULL_EPS / 4, err
+
+
+def test_float32_projection_error_at_the_benchmark_sizes(orc):
+    """The margin holds at the sizes the GPU tests and the benchmark use: the
+    float32 projection of every lattice point stays within a quarter of
+    HULL_EPS of the float64 one (128^3 with 8 views of 512^2; 192^3 with 12
+    views of 768^2, the largest serving job)."""
+    for n, views, side, seed in ((128, 8, 512, 2), (192, 12, 768, 5)):
+        shape, origin, h = synth.unit_grid(n)
+        cams = synth.ring_cameras(views, side, side, elevation_jitter_deg=10.0, seed=seed)
+        mask = np.zeros((views, side, side), dtype=np.uint8)
+        _, uv64 = _numpy_hull(shape, origin, h, cams[:2], mask[:2], np.float64)
+        _, uv32 = _numpy_hull(shape, origin, h, cams[:2], mask[:2], np.float32)
+        err = max(np.abs(a - b).max() for p, q in zip(uv32, uv64) for a, b in zip(p, q))
+        print(f"{n}^3, {side}^2: float32 projection error {err:.2e} pixel")
+        assert err < orc.HULL_EPS / 4
