@@ -46,6 +46,8 @@ KERNELS_PER_STEP = 9
 # this workload (None where the kernel changed since)
 NCU_TRAFFIC = {("fwd", "f32"): None, ("adj", "f32"): 19.64e6 + 0.0}
 NCU_INST = {("fwd", "f32"): None, ("adj", "f32"): 201.39e6}
+# iterations of the step that `--profile` runs for the ncu captures
+PROFILE_ITERS = 3
 # instruction issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock
 # at the 2070 MHz maximum SM clock, in warp instructions per second
 ISSUE_PEAK = 152 * 4 * 2.07e9
@@ -60,12 +62,14 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the video-batch and serving sections")
-    ap.add_argument("--serving-jobs", type=int, default=40)
+    ap.add_argument("--storage-section", action="store_true",
+                    help="run the float32 / BF16 comparison even with --no-extras")
+    ap.add_argument("--serving-jobs", type=int, default=500)
     ap.add_argument("--no-hull", action="store_true",
                     help="reconstruct the whole box instead of the visual hull (Sec. 4.3.1)")
     ap.add_argument("--no-skip", action="store_true", help="march empty bricks too (same result, slower)")
     ap.add_argument("--profile", action="store_true",
-                    help="one untimed iteration plus one forward and one adjustment launch, for ncu")
+                    help="untimed iterations of the step, for ncu captures")
     return ap.parse_args()
 
 
@@ -257,23 +261,38 @@ def run_ours(args, ws, rank, local):
 
     t_fwd, t_adj = phase_ms["forward"] / 1e3, phase_ms["adjust"] / 1e3
 
-    # end to end through the C ABI with host buffers: pinned targets in, rmse out
+    # end to end through the C ABI with host buffers, every step: the volume
+    # (float32 records, pinned host memory) uploaded into a library-held volume
+    # of the storage type, the pinned host targets copied in by fr_reconstruct,
+    # the RMSE and the updated volume read back (the next step uploads it
+    # again).  The job's constants (albedo, flame boxes, hull tags) stay on the
+    # device.
+    vol_host = torch.as_tensor(I["vol0"].float().cpu()).pin_memory()
+    vol_host_np = vol_host.numpy()
     tgt_host = I["targets"].cpu().pin_memory()
     rmse_host = np.zeros((1, 3), dtype=np.float32)
-    vol_e2e = I["vol0"].clone()
-    fe = fr.volume(vol_e2e, I["origin"], I["h"])
-    for it in range(2):
-        ctx.fr_reconstruct(fe, cams, tgt_host, I["bbox"], 1, p, albedo=I["albedo"], first_iteration=it,
+    lv = ctx.fr_volume_create((w["n"],) * 3, I["origin"], I["h"],
+                              dtype=fr.FR_F32 if args.storage == "f32" else fr.FR_BF16)
+
+    def e2e_step(it):
+        ctx.fr_volume_upload(lv, vol_host_np)
+        ctx.fr_reconstruct(lv, cams, tgt_host, I["bbox"], 1, p, albedo=I["albedo"], first_iteration=it,
                            rmse=rmse_host, targets_are_host=True)
+        ctx.fr_volume_download(lv, vol_host_np)
+
+    for it in range(2):
+        e2e_step(it)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     t0 = time.perf_counter()
     for it in range(args.steps):
-        ctx.fr_reconstruct(fe, cams, tgt_host, I["bbox"], 1, p, albedo=I["albedo"], first_iteration=2 + it,
-                           rmse=rmse_host, targets_are_host=True)
+        e2e_step(2 + it)
     torch.cuda.synchronize()
     t_e2e = dist_max(time.perf_counter() - t0)
+    ctx.fr_volume_free(lv)
+    e2e_h2d = int(vol_host.numel() * 4 + I["targets"].numel() * 4)
+    e2e_d2h = int(vol_host.numel() * 4 + 12)
 
     # reconstruction quality after the timed iterations (context for the number)
     rmse_now = np.zeros((1, 3), dtype=np.float32)
@@ -342,6 +361,9 @@ def run_ours(args, ws, rank, local):
              "rmse_last": [float(x) for x in r_u[max(n_u - 1, 0)]],
              "note": "wall time of one fr_reconstruct_until call, graph instantiation included"}
 
+    storage_cmp = run_storage_comparison(fr, ctx, I, args) if not args.no_extras or args.storage_section else None
+    ablation = run_ablation(fr, ctx, I, args)
+
     samples_step = n_fwd + n_adj
     value = weak_value(ws, samples_step, args.steps, t_dev)
     peaks = {}
@@ -350,18 +372,59 @@ def run_ours(args, ws, rank, local):
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    # Roofline of the dominant march.  Algorithmic bytes per sample: the
-    # forward gathers the 8 corner records of its cell; the adjustment gathers
-    # the 8 corners' extinction and reduces a 16-byte update into each of them.
+    # Roofline of the two marches.  Compulsory DRAM bytes per launch (the
+    # least each must move, one pass over what it reads and writes): the
+    # forward reads the records and the targets and writes the residual; the
+    # adjustment reads the records and the residual and writes the update
+    # (three float32 per node).  The per-sample gather (8 corner records for
+    # the forward; 8 extinctions plus one 16-byte reduction per key point for
+    # the adjustment) is served by L1/L2 and reported separately.
     rec = 16 if args.storage == "f32" else 8
     sig = 4 if args.storage == "f32" else 2
-    kernels = {"fwd": dict(per_sample=8 * rec, samples=n_fwd, seconds=t_fwd,
-                           traffic=NCU_TRAFFIC.get(("fwd", args.storage)), inst=NCU_INST.get(("fwd", args.storage))),
-               "adj": dict(per_sample=8 * sig + 8 * 16, samples=n_adj, seconds=t_adj,
-                           traffic=NCU_TRAFFIC.get(("adj", args.storage)), inst=NCU_INST.get(("adj", args.storage)))}
+    nodes = w["n"] ** 3
+    img_bytes = w["views"] * w["side"] ** 2 * 12
+    kernels = {
+        "fwd": dict(name="fwd_single (forward march + residual)", seconds=t_fwd, samples=n_fwd,
+                    compulsory={"records_read": nodes * rec, "targets_read": img_bytes,
+                                "residual_written": img_bytes},
+                    gather_per_sample=8 * rec, traffic=NCU_TRAFFIC.get(("fwd", args.storage)),
+                    inst=NCU_INST.get(("fwd", args.storage))),
+        "adj": dict(name="adj_list (paper-rule adjustment over half rays)", seconds=t_adj, samples=n_adj,
+                    compulsory={"records_read": nodes * rec, "residual_read": img_bytes,
+                                "update_written": nodes * 12},
+                    gather_per_sample=8 * sig + 8 * 16, traffic=NCU_TRAFFIC.get(("adj", args.storage)),
+                    inst=NCU_INST.get(("adj", args.storage))),
+    }
+    for K in kernels.values():
+        K["compulsory_bytes"] = sum(K["compulsory"].values())
+        K["hbm_frac"] = K["compulsory_bytes"] / K["seconds"] / 1e9 / hbm_peak
+        K["issue_frac"] = None if K["inst"] is None else K["inst"] / K["seconds"] / ISSUE_PEAK
     dom = max(kernels, key=lambda k: kernels[k]["seconds"])
     K = kernels[dom]
-    achieved = K["per_sample"] * K["samples"] / K["seconds"] / 1e9
+    achieved = K["compulsory_bytes"] / K["seconds"] / 1e9
+    roofline = {
+        "bound": "hbm", "kernel": K["name"], "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+        "frac": achieved / hbm_peak, "traffic": K["traffic"],
+        "algorithmic_bytes_per_launch": K["compulsory_bytes"], "algorithmic_bytes": K["compulsory"],
+        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s",
+        "limiter": None if K["inst"] is None else {
+            "bound": "issue", "frac": K["issue_frac"], "warp_instructions_per_launch": K["inst"],
+            "achieved_per_s": K["inst"] / K["seconds"], "peak_per_s": ISSUE_PEAK,
+            "source": "smsp__inst_executed.sum of one ncu capture (profiles/); peak 152 SMs x 4 schedulers x "
+                      "2070 MHz"},
+        "l1_l2_gather": {"bytes_per_launch": K["gather_per_sample"] * K["samples"],
+                         "bytes_per_sample": K["gather_per_sample"], "samples_per_launch": K["samples"],
+                         "achieved_GBps": K["gather_per_sample"] * K["samples"] / K["seconds"] / 1e9},
+        "other_kernel": {"name": kernels["fwd" if dom == "adj" else "adj"]["name"],
+                         "hbm_frac": kernels["fwd" if dom == "adj" else "adj"]["hbm_frac"],
+                         "issue_frac": kernels["fwd" if dom == "adj" else "adj"]["issue_frac"]},
+        "note": "achieved = compulsory DRAM bytes of one launch over its event-timed duration; the 128^3 "
+                "records, the images and the update stay in the 129 MB L2 between kernels, so the DRAM "
+                "traffic ncu measures per launch (`traffic`) is below even those bytes, and the marches are "
+                "bound by instruction issue (`limiter`), not by HBM; the per-sample gathers (`l1_l2_gather`) "
+                "are served by L1 and L2",
+    }
+
     out = {
         "metric": METRIC,
         "value": value,
@@ -386,35 +449,105 @@ def run_ours(args, ws, rank, local):
         "phase_ms_per_step": phase_ms,
         "traced_ms_per_step": traced_ms,
         "e2e": {"value": weak_value(ws, samples_step, args.steps, t_e2e), "unit": "samples/s",
-                "h2d_bytes_per_step": int(I["targets"].numel() * 4), "d2h_bytes_per_step": 12},
+                "h2d_bytes_per_step": e2e_h2d, "d2h_bytes_per_step": e2e_d2h,
+                "ms_per_step": 1e3 * t_e2e / args.steps,
+                "path": "fr_volume_upload (float32 host records) -> fr_reconstruct (host targets, host rmse) "
+                        "-> fr_volume_download (float32 host records), pinned host memory, every step"},
         "gpu_launches": KERNELS_PER_STEP * args.steps,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": K["traffic"],
-                     "algorithmic_bytes_per_launch": K["per_sample"] * K["samples"],
-                     "bytes_per_sample": K["per_sample"], "samples_per_launch": K["samples"],
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
-                     else "fallback 6.8 TB/s",
-                     "note": "gather bytes are served by L1/L2 (the volume stays in the 129 MB L2; DRAM "
-                             "traffic per launch is `traffic`, far below them) and the adjustment's key-point "
-                             "window issues one reduction per key point a ray leaves, not one per sample-corner, "
-                             "so frac can exceed 1; the binding limit is instruction issue (`issue`)",
-                     "issue": None if K["inst"] is None else {
-                         "warp_instructions_per_launch": K["inst"], "achieved_per_s": K["inst"] / K["seconds"],
-                         "peak_per_s": ISSUE_PEAK, "frac": K["inst"] / K["seconds"] / ISSUE_PEAK,
-                         "source": "smsp__inst_executed.sum of one ncu capture; peak 152 SMs x 4 schedulers x "
-                                   "2070 MHz"}},
+        "roofline": roofline,
         "clocks": clk.summary(),
         "rmse_after": [float(x) for x in rmse_now[0]],
         "until_converged": until,
         "visual_hull": {"ms": hull_ms, "views": w["views"], "grid": [w["n"]] * 3, "image": [w["side"]] * 2,
                         "same_tags_as_setup": hull_same},
         "variants": variants,
+        "storage_f32_vs_bf16": storage_cmp,
+        "ablation": ablation,
         "volume_rmse_in_hull": {"rmse": [float(x) for x in v_rmse], "key_points": v_n,
                                 "relative_to_max": [float(x) / ref_max for x in v_rmse],
                                 "after_iterations": args.warmup + 2 * args.steps + 1},
         "wall_s": t_wall,
     }
     ctx.close()
+    return out
+
+
+def run_storage_comparison(fr, ctx, I, args, iters=50):
+    """The full-RTE configuration as stated: `iters` iterations from the zero
+    start with float32 records and with BF16 records (float32 arithmetic), on
+    the same targets, hull and parameters, each run as one fr_reconstruct call
+    timed with CUDA events; per storage the per-iteration time, the image error
+    of the first and last iteration, and the volume data error inside the hull
+    against the ground truth on the targets' scale (Sec. 5.1)."""
+    import torch
+    w = WORKLOAD
+    stream = torch.cuda.current_stream()
+    ref = torch.as_tensor(I["gt"], dtype=torch.float32, device="cuda")
+    ref[..., :3] /= I["scale"]
+    fref = fr.volume(ref.contiguous(), I["origin"], I["h"])
+    ref_max = float(ref[..., :3].max())
+    full = (1 << w["views"]) - 1
+    p = method_params(args, I)
+    out, vols = {}, {}
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        warm = I["vol0"].float().to(dt).contiguous()
+        ctx.fr_reconstruct(fr.volume(warm, I["origin"], I["h"]), I["fcams"], I["targets"], I["bbox"], 2, p,
+                           albedo=I["albedo"])
+        vol = I["vol0"].float().to(dt).contiguous()
+        fv = fr.volume(vol, I["origin"], I["h"])
+        rmse = torch.zeros((iters, 3), device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.fr_reconstruct(fv, I["fcams"], I["targets"], I["bbox"], iters, p, albedo=I["albedo"], rmse=rmse)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        r = rmse.cpu().numpy()
+        v_rmse, _ = ctx.fr_volume_rmse(fv, fref, I["tags"], full)
+        out[name] = {"ms_per_iteration": e0.elapsed_time(e1) / iters, "rmse_first": [float(x) for x in r[0]],
+                     "rmse_last": [float(x) for x in r[-1]],
+                     "volume_rmse_in_hull": [float(x) for x in v_rmse],
+                     "volume_rmse_in_hull_relative_to_max": [float(x) / ref_max for x in v_rmse]}
+        vols[name] = (vol, fv)
+        del warm
+    d, _ = ctx.fr_volume_rmse(vols["f32"][1], vols["bf16"][1], I["tags"], full)
+    out["bf16_minus_f32_volume_rmse_in_hull_relative_to_max"] = [float(x) / ref_max for x in d]
+    out["iterations"] = iters
+    out["speedup_bf16"] = out["f32"]["ms_per_iteration"] / out["bf16"]["ms_per_iteration"]
+    return out
+
+
+def run_ablation(fr, ctx, I, args, iters=20):
+    """Per-iteration time of the step with parts of the method's restrictions
+    turned off, beside the headline: without empty-brick skipping (same
+    result, every sample in the box evaluated) and without the visual hull
+    (the whole box reconstructed).  One fr_reconstruct call of `iters`
+    iterations each from the zero start, timed with CUDA events."""
+    import torch
+    w = WORKLOAD
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, kw in (("default", {}), ("no_skip", dict(skip_empty=0)), ("no_hull", dict(use_hull=0)),
+                     ("no_hull_no_skip", dict(use_hull=0, skip_empty=0))):
+        p = fr.params(step=w["step"], alpha_l=w["alpha_l"], use_hull=1, hull_tags=I["tags"], skip_empty=1)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        if not p.use_hull:
+            p.hull_tags = None
+        vol = I["vol0"].clone()
+        fv = fr.volume(vol, I["origin"], I["h"])
+        ctx.fr_reconstruct(fv, I["fcams"], I["targets"], I["bbox"], 2, p, albedo=I["albedo"])
+        vol.copy_(I["vol0"])
+        rmse = np.zeros((iters, 3), dtype=np.float32)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.fr_reconstruct(fv, I["fcams"], I["targets"], I["bbox"], iters, p, albedo=I["albedo"], rmse=rmse)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_iteration": e0.elapsed_time(e1) / iters, "rmse_last": [float(x) for x in rmse[-1]]}
+        del vol
+    out["iterations"] = iters
     return out
 
 
@@ -469,19 +602,29 @@ def run_video(fr, ctx, frames=64, n=96, views=8, side=384, iters=20, step=0.5, s
             "final_rmse_mean": [float(x) for x in final.mean(axis=0)], "launches_per_iteration": 7}
 
 
-def run_serving(fr, ctx, jobs=40, rate=20.0, seed=5, step=0.5):
-    """Serving stream: seeded Poisson arrivals at `rate` jobs/s, mixed grids,
-    views, image sizes and iteration counts, bf16 volumes, through the
-    continuous-batching server (p50 / p99 latency, jobs/s).  The same jobs are
-    then run offline twice to compare throughput at matched error: all at once
-    through the server (bf16) and one after another through fr_reconstruct
-    (float32, the plain single-job path)."""
+def run_serving(fr, ctx, jobs=500, rate=20.0, seed=5, step=0.5, warmup_s=10.0, pool=64):
+    """The serving configuration: reconstruction jobs arrive as a seeded
+    Poisson stream at `rate` jobs/s -- `warmup_s` seconds of warm-up jobs, then
+    `jobs` measured ones -- each with a grid from {64, 96, 128, 192}^3, 4-12
+    views, image side 256-768 and 20-50 iterations, BF16 records, its own
+    visual hull, through the continuous-batching server.  A job's scene (grid,
+    cameras, targets) comes from a pool of `pool` seeded scenes drawn from the
+    same distribution, rendered once up front (host memory); its arrival time
+    and iteration count are its own.
+
+    Reported: p50 / p99 latency from arrival (the loop's clock, so waiting for
+    a step in flight counts) and service time on the server, throughput while
+    the measured jobs were in the system, and, on the measured jobs alone: the
+    capacity (all submitted at once to a fresh server) against the plain
+    single-job float32 path (fr_reconstruct, one job after another, frames and
+    records from host memory as for the server), with each arm's final image
+    error (green, 0-255) to compare them at matched error."""
     import torch
     from paper_1809_06417_gb300 import serving, synth
-    stream = synth.serving_stream(jobs, seed=seed, rate=rate)
-    plumes = {}
-    specs = []
-    for js in stream:
+    n_warm = int(round(warmup_s * rate))
+    stream = synth.serving_stream(n_warm + jobs, seed=seed, rate=rate)
+    plumes, scenes = {}, []
+    for js in stream[:pool]:
         n, K, side = js["n"], js["views"], js["side"]
         if n not in plumes:
             plumes[n] = synth.plume_volume(n, seed + n)[0]
@@ -494,11 +637,13 @@ def run_serving(fr, ctx, jobs=40, rate=20.0, seed=5, step=0.5):
         img /= img.max()
         init = gt.copy()
         init[..., :3] = 0.0
-        specs.append(dict(js=js, shape=shape, origin=origin, h=h, cams=cams, targets=img.cpu().numpy(),
-                          init32=init.astype(np.float32),
-                          init16=torch.as_tensor(init, dtype=torch.float32).to(torch.bfloat16)
-                          .view(torch.int16).numpy().view(np.uint16).copy(),
-                          alpha=alpha_for(n, K, side, step)))
+        scenes.append(dict(n=n, shape=shape, origin=origin, h=h, cams=cams, targets=img.cpu().numpy(),
+                           init32=init.astype(np.float32),
+                           init16=torch.as_tensor(init, dtype=torch.float32).to(torch.bfloat16)
+                           .view(torch.int16).numpy().view(np.uint16).copy(),
+                           alpha=alpha_for(n, K, side, step)))
+        del g, img
+    specs = [dict(js=js, **scenes[i % pool]) for i, js in enumerate(stream)]
     p = fr.params(step=step, alpha_l=2e-4, use_hull=1)   # each job in its own visual hull
 
     def submitter(sp):
@@ -507,26 +652,29 @@ def run_serving(fr, ctx, jobs=40, rate=20.0, seed=5, step=0.5):
 
     # online: Poisson arrivals, continuous batching
     srv = fr.Server(ctx, p, dtype=fr.FR_BF16)
-    warm = srv.submit(specs[0]["shape"], specs[0]["origin"], specs[0]["h"], specs[0]["cams"], 2,
-                      specs[0]["init16"], specs[0]["targets"], alpha_l=specs[0]["alpha"])
-    warm.wait()
-    reqs = [serving.Request(arrival=sp["js"]["arrival"] - stream[0]["arrival"], submit=submitter(sp)) for sp in specs]
+    reqs = [serving.Request(arrival=sp["js"]["arrival"] - stream[0]["arrival"], submit=submitter(sp),
+                            warmup=i < n_warm) for i, sp in enumerate(specs)]
     res = serving.run_requests(srv, reqs)
-    online_rmse = np.mean([r.job.rmse[-1, 1] for r in reqs])
+    measured = [r for r in reqs if not r.warmup]
+    online_rmse = np.mean([r.job.rmse[-1, 1] for r in measured])
     srv.close()
-    # offline: all jobs at once through the server (bf16)
+    meas_specs = specs[n_warm:]
+    # capacity: the measured jobs all submitted at once to a fresh server (bf16)
     srv = fr.Server(ctx, p, dtype=fr.FR_BF16)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    handles = [submitter(sp)(srv) for sp in specs]
+    handles = [submitter(sp)(srv) for sp in meas_specs]
     for j in handles:
-        j.wait(timeout_ms=600000)
+        j.wait(timeout_ms=1800000)
     t_batched = time.perf_counter() - t0
-    rmse_batched = np.mean([j.rmse[-1, 1] for j in handles])
+    rmse_batched = np.array([j.rmse[-1, 1] for j in handles])
     srv.close()
-    # offline: one job after another through fr_reconstruct (float32)
+    del handles
+    # the plain single-job path: one job after another through fr_reconstruct
+    # (float32), frames and records from host memory, the result read back
     t0 = time.perf_counter()
     rmse_single = []
-    for sp in specs:
+    for sp in meas_specs:
         K, side = len(sp["cams"]), sp["cams"][0]["width"]
         v = torch.as_tensor(sp["init32"], device="cuda").contiguous()
         t = torch.as_tensor(sp["targets"], device="cuda").contiguous()
@@ -535,16 +683,25 @@ def run_serving(fr, ctx, jobs=40, rate=20.0, seed=5, step=0.5):
         rm = np.zeros((sp["js"]["iters"], 3), dtype=np.float32)
         ctx.fr_reconstruct(fr.volume(v, sp["origin"], sp["h"]), fr.cameras(sp["cams"]), t, bbox, sp["js"]["iters"],
                            fr.params(step=step, alpha_l=sp["alpha"], use_hull=1), rmse=rm)
+        v.cpu()
         rmse_single.append(rm[-1, 1])
     torch.cuda.synchronize()
     t_single = time.perf_counter() - t0
-    return {"workload": f"serving_poisson{rate:g}_jobs{jobs}", "jobs": jobs, "rate_jobs_per_s": rate,
+    rmse_single = np.array(rmse_single)
+    return {"workload": f"serving_poisson{rate:g}_jobs{jobs}_warmup{warmup_s:g}s", "jobs": jobs,
+            "warmup_jobs": n_warm, "rate_jobs_per_s": rate, "scene_pool": pool,
             "p50_latency_s": res.percentile(50), "p99_latency_s": res.percentile(99),
-            "jobs_per_s": jobs / res.wall, "max_resident": res.max_running, "steps": res.steps,
+            "p50_service_s": res.percentile(50, res.services), "p99_service_s": res.percentile(99, res.services),
+            "jobs_per_s_in_system": res.throughput(), "max_resident": res.max_running, "steps": res.steps,
             "online_final_rmse_green_mean": float(online_rmse),
-            "offline": {"batched_bf16_jobs_per_s": jobs / t_batched, "single_f32_jobs_per_s": jobs / t_single,
-                        "speedup": t_single / t_batched, "final_rmse_green_mean_batched": float(rmse_batched),
-                        "final_rmse_green_mean_single": float(np.mean(rmse_single))},
+            "latency_note": "latency from each job's arrival to the end of the server step that completed it "
+                            "(loop clock); service from submission to completion (server clock)",
+            "capacity": {"batched_bf16_jobs_per_s": jobs / t_batched, "single_f32_jobs_per_s": jobs / t_single,
+                         "speedup": t_single / t_batched,
+                         "final_rmse_green_mean_batched_bf16": float(rmse_batched.mean()),
+                         "final_rmse_green_mean_single_f32": float(rmse_single.mean()),
+                         "rmse_ratio_bf16_over_f32": float(rmse_batched.mean() / rmse_single.mean()),
+                         "note": "the measured jobs all submitted at t = 0 (saturating arrivals)"},
             "storage": "bf16", "visual_hull": True,
             "mix": "grids {64,96,128,192}^3, 4-12 views, side 256-768, 20-50 iterations"}
 
@@ -690,109 +847,142 @@ def run_differentiable(fr, ctx, n=128, views=8, side=512, step=0.5, seed=3, reps
             "note": "backward includes the loss and torch's reduction kernels around fr_render_backward"}
 
 
-class OracleSample:
-    """The oracle on bounded samples of the workload: a band of image rows of
-    one view, one iteration (in-scattering source, render of those pixels,
-    residual, adjustment).  The scene, ground truth and the sample's targets
-    are prepared outside the timed region."""
+class OracleWorkload:
+    """The oracle on the benchmarked workload itself: the same seeded plume,
+    cameras, noise, hull and parameters, targets rendered by the oracle, the
+    volume starting at zero emission and advanced one fr_reconstruct-like
+    iteration per step (in-scattering source, render, residual, adjustment,
+    update inside the hull).  Set-up runs outside the timed steps."""
 
-    def __init__(self):
+    def __init__(self, threads):
         import oracle as orc
         from paper_1809_06417_gb300 import synth
         self.orc = orc
         w = WORKLOAD
         n = w["n"]
-        self.shape, self.origin, self.h = synth.unit_grid(n)
-        self.gt, self.albedo = synth.plume_volume(n, w["seed"])
-        self.cams = synth.ring_cameras(w["views"], w["side"], w["side"], elevation_jitter_deg=10.0, seed=w["seed"])
+        orc.set_threads(threads)
+        shape, origin, h = synth.unit_grid(n)
+        gt, self.albedo = synth.plume_volume(n, w["seed"])
+        cams = synth.ring_cameras(w["views"], w["side"], w["side"], elevation_jitter_deg=10.0, seed=w["seed"])
+        self.sc = orc.Scene(shape, origin, h, cams)
         self.P = orc.make_params(step=w["step"], alpha_l=w["alpha_l"])
-        sc = orc.Scene(self.shape, self.origin, self.h, self.cams[:1])
-        self.src_gt = orc.scatter_source(self.gt, self.albedo, orc.scatter_J(sc, self.gt))
-        self.vol0 = self.gt.copy()
-        self.vol0[..., :3] = 0.0
+        src = orc.scatter_source(gt, self.albedo, orc.scatter_J(self.sc, gt))
+        img, _ = orc.render(self.sc, src, self.P)
+        img = synth.add_noise(img / img.max(), w["noise"], w["seed"])
+        self.targets, self.mask, self.bbox = orc.prepare_targets(img, 30 / 255)
+        self.tags = orc.visual_hull(self.sc, self.mask)
+        self.vol = gt.copy()
+        self.vol[..., :3] = 0.0
+        self.it = 0
 
-    def run(self, rows, view=0):
-        orc, w = self.orc, WORKLOAD
-        S = w["side"]
-        sc = orc.Scene(self.shape, self.origin, self.h, [self.cams[view]])
-        y0 = S // 2 - rows // 2
-        px = [(0, x, y) for y in range(y0, y0 + rows) for x in range(S)]
-        tgt, _ = orc.render_pixels(sc, self.src_gt, self.P, px)
-        tgt /= max(tgt.max(), 1e-30)
+    def step(self, threads):
+        """One iteration on `threads` threads: (samples, seconds)."""
+        self.orc.set_threads(threads)
         t0 = time.perf_counter()
-        src0 = orc.scatter_source(self.vol0, self.albedo, orc.scatter_J(sc, self.vol0))
-        ren, n_f = orc.render_pixels(sc, src0, self.P, px)
-        res = np.zeros((1, S, S, 3))
-        mask = np.zeros((1, S, S), dtype=np.uint8)
-        flame = (tgt.max(axis=1) > 30 / 255).reshape(rows, S)
-        res[0, y0:y0 + rows] = (tgt - ren).reshape(rows, S, 3) * flame[..., None]
-        mask[0, y0:y0 + rows] = flame
-        _, n_a = orc.update_paper(sc, src0, self.P, res, mask, 0)
+        self.vol, _, (nf, na) = self.orc.reconstruct(self.sc, self.vol, self.P, self.targets, self.mask, self.bbox, 1,
+                                                     albedo=self.albedo, first_iteration=self.it, hull=self.tags)
         dt = time.perf_counter() - t0
-        return n_f + n_a, dt, f"view {view}, rows {y0}-{y0 + rows - 1} of {S}, one iteration"
+        self.it += 1
+        return nf + na, dt
 
 
-def cpu_baseline(views=6):
-    """The oracle on `views` whole views of one iteration (about 2 s each)."""
-    sample = OracleSample()
-    n = dt = 0
-    for v in range(views):
-        nv, tv, _ = sample.run(WORKLOAD["side"], view=v)
-        n += nv
-        dt += tv
-    return {"value": n / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
-            "sample": f"views 0-{views - 1}, all {WORKLOAD['side']} rows each, one iteration (scatter source, "
-                      f"render, residual, adjust) of {WORKLOAD['name']} without the hull; "
-                      f"{n} samples in {dt:.1f} s"}
+def oracle_tiny(threads, iters=10):
+    """The tiny configuration (32^3, 4 views of 64^2, step 1, 10 iterations)
+    through the oracle, timed in full: (samples, seconds)."""
+    import oracle as orc
+    from paper_1809_06417_gb300 import synth
+    orc.set_threads(threads)
+    n = 32
+    shape, origin, h = synth.unit_grid(n)
+    cams = synth.ring_cameras(4, 64, 64, seed=1)
+    gt = synth.blobs_volume(n, 1)
+    sc = orc.Scene(shape, origin, h, cams)
+    P = orc.make_params(step=1.0, alpha_l=0.01)
+    img, _ = orc.render(sc, gt, P)
+    t, mask, bbox = orc.prepare_targets(synth.add_noise(img / img.max(), 1e-3, 1), 30 / 255)
+    v0 = gt.copy()
+    v0[..., :3] = 0.0
+    t0 = time.perf_counter()
+    _, _, (nf, na) = orc.reconstruct(sc, v0, P, t, mask, bbox, iters)
+    return nf + na, time.perf_counter() - t0
+
+
+def cpu_baseline(full_iters=3):
+    """The oracle, as it stands, on the machine's host cores: the benchmarked
+    workload over `full_iters` whole iterations on every core (OpenMP), one
+    whole iteration on one core, and the tiny configuration's 10 iterations on
+    both."""
+    cores = os.cpu_count() or 1
+    wl = OracleWorkload(cores)
+    n_all = t_all = 0
+    for _ in range(full_iters):
+        n_, t_ = wl.step(cores)
+        n_all += n_
+        t_all += t_
+    n_one, t_one = wl.step(1)
+    tn_all, tt_all = oracle_tiny(cores)
+    tn_one, tt_one = oracle_tiny(1)
+    import oracle as orc
+    orc.set_threads(1)
+    return {"value": n_all / t_all, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{WORKLOAD['name']}: {full_iters} whole iterations (in-scattering source, render of every "
+                      f"pixel, residual, adjustment of every flame ray, update inside the hull) on {cores} threads, "
+                      f"{n_all} samples in {t_all:.1f} s",
+            "iterations_per_s": full_iters / t_all,
+            "single_core": {"value": n_one / t_one, "unit": "samples/s", "cores": 1,
+                            "sample": f"one whole iteration, {n_one} samples in {t_one:.1f} s",
+                            "iterations_per_s": 1.0 / t_one},
+            "tiny_10_iterations": {"all_cores_s": tt_all, "single_core_s": tt_one, "samples": tn_all,
+                                   "cores": cores}}
 
 
 def run_profile(args):
-    """One warm-up iteration, then one launch each of the forward march
-    (fused residual) and the adjustment, with no timing or L2 flush: the
-    command the ncu captures use."""
+    """The command the ncu captures use: the workload's inputs, then
+    PROFILE_ITERS iterations of the benchmarked step (one fr_reconstruct
+    iteration each, the same launches as a timed step), no timing or L2 flush.
+    Launches: make_inputs renders the ground truth once (fwd_single) and
+    computes the hull; each iteration then launches KERNELS_PER_STEP kernels."""
     import torch
     from paper_1809_06417_gb300 import flamerec as fr
-    w = WORKLOAD
     ctx, I = make_inputs(args.storage, 0, 0)
     p = method_params(args, I)
     vol = I["vol0"].clone()
     fv = fr.volume(vol, I["origin"], I["h"])
-    ctx.fr_reconstruct(fv, I["fcams"], I["targets"], I["bbox"], 1, p, albedo=I["albedo"])
-    src = torch.empty_like(vol)
-    J = torch.empty(vol.shape[:3] + (4,), device="cuda")
-    ctx.fr_scatter_source(fv, I["albedo"], J, fr.volume(src, I["origin"], I["h"]))
-    fs = fr.volume(src, I["origin"], I["h"])
-    res = torch.empty_like(I["targets"])
-    sq = torch.zeros(4, device="cuda")
-    dV = torch.zeros(vol.shape[:3] + (4,), device="cuda")
-    ctx.fr_render_residual(fs, I["fcams"], p, I["targets"], I["bbox"], None, res, sq)
-    ctx.fr_adjust(fs, I["fcams"], p, res, 1, dV)
+    rmse = np.zeros((1, 3), dtype=np.float32)
+    for it in range(PROFILE_ITERS):
+        ctx.fr_reconstruct(fv, I["fcams"], I["targets"], I["bbox"], 1, p, albedo=I["albedo"], first_iteration=it,
+                           rmse=rmse)
     torch.cuda.synchronize()
-    print(json.dumps({"profile": "ok", "sq_err": [float(x) for x in sq.cpu()]}))
+    print(json.dumps({"profile": "ok", "iterations": PROFILE_ITERS, "rmse_last": [float(x) for x in rmse[0]]}))
     ctx.close()
 
 
 def run_reference(args, ws, rank):
+    """The reference arm: the oracle (the paper ships no code) on the same
+    workload, metric and unit, every host core, one whole iteration per step."""
     if rank != 0:
         return None
-    rows = 8
+    cores = os.cpu_count() or 1
+    wl = OracleWorkload(cores)
     tot_n, tot_t = 0, 0.0
-    sample = OracleSample()
     for i in range(args.warmup + args.steps):
-        n, dt, what = sample.run(rows, view=i % WORKLOAD["views"])
+        n, dt = wl.step(cores)
         if i >= args.warmup:
             tot_n += n
             tot_t += dt
     v = tot_n / tot_t
+    w = WORKLOAD
     return {"metric": METRIC, "value": v, "unit": "samples/s", "impl": "reference", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"], "grid": [WORKLOAD["n"]] * 3, "views": WORKLOAD["views"],
-                       "image": [WORKLOAD["side"]] * 2, "step_vox": WORKLOAD["step"], "storage": "f64",
-                       "rule": "paper", "scattering": True, "parallelism": "cpu1"},
-            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
-                             "sample": f"per step {rows} rows of one view, one iteration"},
+            "config": {"workload": w["name"], "grid": [w["n"]] * 3, "views": w["views"], "image": [w["side"]] * 2,
+                       "step_vox": w["step"], "storage": "f64", "rule": "paper", "scattering": True,
+                       "visual_hull": True, "parallelism": f"cpu{cores}"},
+            "recon_iters_per_s": args.steps / tot_t,
+            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                             "sample": "one whole iteration of the workload per step (every pixel rendered, every "
+                                       "flame ray adjusted), OpenMP over pixel rows"},
             "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -421,6 +421,55 @@ fr_status fr_camera_from_projection(const double P[12], int width, int height, f
 fr_status fr_volume_dims(const fr_camera *cams, int ncam, const float box_min[3], const float box_max[3],
                          float alpha, int32_t dims[3], float *h, float n[3]);
 
+/* ---- Volumes held by the library ---- */
+
+/* A volume whose records the library allocates on the context's device:
+ * nx x ny x nz key points (Sec. 3.3: the voxel vertices) of `kind` stored as
+ * `dtype`, kept in GPU memory across calls as the paper keeps its volume
+ * (Sec. 4.3.2).  *out receives the descriptor every other entry point takes;
+ * its data (device, 256-byte aligned) is owned by the library, zeroed, and
+ * freed by fr_volume_free or fr_destroy.  FR_ENOMEM when the device cannot
+ * hold it. */
+fr_status fr_volume_create(fr_ctx *ctx, int nx, int ny, int nz, const float origin[3], float h, int kind,
+                           int dtype, fr_volume *out);
+/* Frees a volume from fr_volume_create on this context (after the context's
+ * queued work is done) and sets vol->data to NULL; FR_EINVAL for any other
+ * volume. */
+fr_status fr_volume_free(fr_ctx *ctx, fr_volume *vol);
+/* Writes a volume's records from float32 values in record layout (nodes x 4
+ * {S_r, S_g, S_b, sigma} for RGB, nodes x 2 {T, sigma} for TEMP), rounded to
+ * the storage type to nearest even.  src: host memory when src_is_host (copied
+ * in stream order: pinned memory must stay unchanged until the context's
+ * stream has passed the copy), else device memory, 16-byte aligned.  16-bit
+ * volumes need 8-byte-aligned data.  Asynchronous. */
+fr_status fr_volume_upload(fr_ctx *ctx, fr_volume *vol, const float *src, int src_is_host);
+/* Reads a volume's records as float32 values in record layout into dst (host
+ * when dst_is_host: filled when the call returns, which synchronises the
+ * context's stream; else device, 16-byte aligned, asynchronous). */
+fr_status fr_volume_download(fr_ctx *ctx, const fr_volume *vol, float *dst, int dst_is_host);
+
+/* ---- Camera sets (host memory owned by the library, no device) ---- */
+
+typedef struct fr_cams fr_cams;
+
+/* k calibrated cameras from 3x4 projections (P: k x 12 doubles, row-major,
+ * each as fr_camera_from_projection takes it; wh: k x {width, height}), the
+ * calibration output of Sec. 4.1.  FR_EINVAL when a projection is not a
+ * pinhole of fr_camera's model or the images differ in size. */
+fr_status fr_cams_create(int k, const double *P, const int32_t *wh, fr_cams **out);
+/* k cameras on a ring around `center` (world units), as the paper's simulated
+ * cameras surround the fire looking at it (Sec. 5.1): camera i at azimuth
+ * phase + 2 pi i / k (radians, measured from +x towards +z) and elevation
+ * elevation_deg[i] (degrees, NULL: 0), at `radius` from the centre, looking at
+ * it with +y up, vertical field of view fov_deg, images width x height. */
+fr_status fr_cams_ring(int k, int width, int height, const float center[3], float radius, float fov_deg,
+                       const float *elevation_deg, float phase, fr_cams **out);
+/* The number of cameras, and the array the other entry points take (valid
+ * until fr_cams_destroy). */
+int32_t fr_cams_count(const fr_cams *cams);
+const fr_camera *fr_cams_data(const fr_cams *cams);
+fr_status fr_cams_destroy(fr_cams *cams);
+
 /* ---- Tracing: device time per phase of fr_reconstruct ---- */
 
 typedef enum {

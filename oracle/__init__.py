@@ -97,14 +97,15 @@ def _load():
             "orc_prepare_targets": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
                                            ctypes.c_double, _P, _P]),
             "orc_residual": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]),
-            "orc_update_paper": (_I64, [_P, _P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]),
+            "orc_update_paper": (_I64, [_P, _P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, _P]),
+            "orc_set_undecided_margins": (None, [ctypes.c_double, ctypes.c_double]),
             "orc_apply_update": (None, [_I64, _P, _P, ctypes.c_int]),
             "orc_grad": (None, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P]),
             "orc_grad_temp": (None, [_P, _P, _P, _P, ctypes.c_int, _P, _P, _P, _P]),
             "orc_scatter_J": (None, [_P, _P, _P]),
             "orc_scatter_source": (None, [_I64, _P, _P, _P, _P]),
             "orc_reconstruct": (None, [_P, _P, _P, _P, ctypes.c_int, _P, _P, _P, _P,
-                                       ctypes.c_int, ctypes.c_int, _P, _P, _P, ctypes.c_double, _P]),
+                                       ctypes.c_int, ctypes.c_int, _P, _P, _P, ctypes.c_double, _P, _P]),
             "orc_visual_hull": (None, [_P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_double, ctypes.c_double]),
             "orc_set_threads": (None, [ctypes.c_int]),
             "orc_threads": (ctypes.c_int, []),
@@ -316,17 +317,37 @@ def residual(rendered, targets, bbox):
     return res, rmse
 
 
-def update_paper(scene: Scene, vol, params: Params, res, mask, iteration):
-    """Eqs. 10-12: the accumulated adjustment dV (nz,ny,nx,3) and samples visited."""
+def update_paper(scene: Scene, vol, params: Params, res, mask, iteration, with_undecided=False):
+    """Eqs. 10-12: the accumulated adjustment dV (nz,ny,nx,3) and samples
+    visited; with_undecided: also the per-node bound (nz,ny,nx) on what the
+    samples whose cell or existence is undecided at float32-rounding margins
+    can move (see set_undecided_margins)."""
     lib = _load()
     vol = _check_vol(vol, scene.shape, 4)
     res = _f64(res)
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
     nx, ny, nz = scene.shape
     dV = np.zeros((nz, ny, nx, 3))
+    und = np.zeros((nz, ny, nx)) if with_undecided else None
     n = lib.orc_update_paper(ctypes.byref(scene.grid), _ptr(vol), scene.cams, scene.ncam,
-                             ctypes.byref(params), _ptr(res), _ptr(mask), int(iteration), _ptr(dV))
-    return dV, int(n)
+                             ctypes.byref(params), _ptr(res), _ptr(mask), int(iteration), _ptr(dV),
+                             _ptr(und) if und is not None else None)
+    return (dV, int(n), und) if with_undecided else (dV, int(n))
+
+
+# Margins of the adjustment's undecided samples: a sample within FACE_EPS
+# voxels of a cell face, or a ray whose chord / step lies within COUNT_EPS of
+# an integer.  A float32 evaluation of the sample positions differs from the
+# double-precision one by about 3e-5 voxels at 250 voxels from the camera
+# (one unit in the last place there, plus the direction's rounding times the
+# distance travelled), and chord / step by a few units in the last place of
+# values below 1000.
+FACE_EPS = 2e-4
+COUNT_EPS = 1e-3
+
+
+def set_undecided_margins(face_voxels=FACE_EPS, count_segments=COUNT_EPS):
+    _load().orc_set_undecided_margins(float(face_voxels), float(count_segments))
 
 
 def apply_update(vol, dV, clamp_nonneg=True):
@@ -392,11 +413,12 @@ def visual_hull(scene: Scene, mask, with_undecided=False, eps=HULL_EPS, eps_z=HU
 
 
 def reconstruct(scene: Scene, vol, params: Params, targets, mask, bbox, iters,
-                albedo=None, first_iteration=0, hull=None, stop_delta=None):
+                albedo=None, first_iteration=0, hull=None, stop_delta=None, with_undecided=False):
     """Algorithm 2 repeated `iters` times with the paper rule; with `hull`
     (visual-hull tags) the records outside the hull are held at 0; with
     stop_delta, stops once the image error changes by less than it (Sec. 3).
-    Returns (volume, rmse per iteration run (rows x 3), (forward, adjust) samples)."""
+    Returns (volume, rmse per iteration run (rows x 3), (forward, adjust)
+    samples[, the adjustments' undecided budget summed over the iterations])."""
     lib = _load()
     vol = _check_vol(vol, scene.shape, 4).copy()
     targets = _f64(targets)
@@ -407,12 +429,16 @@ def reconstruct(scene: Scene, vol, params: Params, targets, mask, bbox, iters,
     alb = _f64(albedo) if albedo is not None else None
     hl = np.ascontiguousarray(hull, dtype=np.uint32) if hull is not None else None
     done = ctypes.c_int(0)
+    nx, ny, nz = scene.shape
+    und = np.zeros((nz, ny, nx)) if with_undecided else None
     lib.orc_reconstruct(ctypes.byref(scene.grid), _ptr(vol), _ptr(alb) if alb is not None else None,
                         scene.cams, scene.ncam, ctypes.byref(params), _ptr(targets), _ptr(mask),
                         _ptr(bbox), int(iters), int(first_iteration), _ptr(rmse), _ptr(samples),
                         _ptr(hl) if hl is not None else None,
-                        float(stop_delta) if stop_delta is not None else -1.0, ctypes.byref(done))
-    return vol, rmse[:done.value], (int(samples[0]), int(samples[1]))
+                        float(stop_delta) if stop_delta is not None else -1.0, ctypes.byref(done),
+                        _ptr(und) if und is not None else None)
+    out = (vol, rmse[:done.value], (int(samples[0]), int(samples[1])))
+    return out + (und,) if with_undecided else out
 
 
 def scatter_L6(scene: Scene, vol):

@@ -611,34 +611,76 @@ void orc_residual(int ncam, int height, int width, const double *rendered,
  * where T(s, s_e) is the transmittance between the eye and the sample (Eq. 12
  * in constant-tau mode, exp(-sum of preceding optical depths) in field mode)
  * and D the Euclidean key-point distance in voxel edge lengths.  All views
- * accumulate into one dV (N^3 x 3).  Returns the number of samples visited. */
+ * accumulate into one dV (N^3 x 3).  Returns the number of samples visited.
+ *
+ * Which eight key points a sample has is an integer decision (its cell), and
+ * so is the number of samples on a ray (ceil(chord / step)): an evaluation in
+ * another precision may take either when the sample lies within its rounding
+ * error of a cell face, or chord / step within it of an integer.  undecided
+ * (nullable, one value per node) then receives, for each such sample, its
+ * largest possible contribution G alpha_l T max_c |dL_c| (exp(-alpha_d D) <= 1)
+ * at every node of the cells it may belong to: a bound on how much that
+ * decision can move the node's sum.  The margins are set by
+ * orc_set_undecided_margins. */
+static double g_face_eps = 2e-4;    /* voxels */
+static double g_count_eps = 1e-3;   /* segments */
+
+void orc_set_undecided_margins(double face_voxels, double count_segments)
+{
+    g_face_eps = face_voxels;
+    g_count_eps = count_segments;
+}
+
+/* w added to every node of the cells [c + lo, c + hi] (clamped to the grid). */
+static void add_to_cells(const orc_grid *g, const int c[3], const int lo[3], const int hi[3], double w,
+                         double *und)
+{
+    const int n[3] = {g->nx, g->ny, g->nz};
+    int a0[3], a1[3];
+    for (int a = 0; a < 3; ++a) {
+        a0[a] = c[a] + lo[a] < 0 ? 0 : c[a] + lo[a];
+        a1[a] = c[a] + hi[a] + 1 > n[a] - 1 ? n[a] - 1 : c[a] + hi[a] + 1;
+    }
+    for (int k = a0[2]; k <= a1[2]; ++k)
+        for (int j = a0[1]; j <= a1[1]; ++j)
+            for (int i = a0[0]; i <= a1[0]; ++i) und[node_index(g, i, j, k)] += w;
+}
+
 static int64_t update_paper_views(const orc_grid *g, const double *vol, const orc_cam *cams,
                                   int ncam, const orc_params *P, const double *residual,
-                                  const uint8_t *mask, int iteration, int view_base, double *dV);
+                                  const uint8_t *mask, int iteration, int view_base, double *dV,
+                                  double *undecided);
 
 int64_t orc_update_paper(const orc_grid *g, const double *vol, const orc_cam *cams,
                          int ncam, const orc_params *P, const double *residual,
-                         const uint8_t *mask, int iteration, double *dV)
+                         const uint8_t *mask, int iteration, double *dV, double *undecided)
 {
-    return update_paper_views(g, vol, cams, ncam, P, residual, mask, iteration, 0, dV);
+    return update_paper_views(g, vol, cams, ncam, P, residual, mask, iteration, 0, dV, undecided);
 }
 
 /* The views of cams are views view_base, view_base + 1, ... of the problem:
  * their index keys the G(s) stream. */
 static int64_t update_paper_views(const orc_grid *g, const double *vol, const orc_cam *cams,
                                   int ncam, const orc_params *P, const double *residual,
-                                  const uint8_t *mask, int iteration, int view_base, double *dV)
+                                  const uint8_t *mask, int iteration, int view_base, double *dV,
+                                  double *undecided)
 {
     orc_field F = {ORC_RGB, vol, NULL};
+    const int n_ax[3] = {g->nx, g->ny, g->nz};
     const int64_t nodes = (int64_t)g->nx * g->ny * g->nz;
     /* one accumulator per thread (the first is dV itself), added in thread
-     * order at the end */
+     * order at the end; the same for the undecided budget */
     int nt = orc_threads();
     double **acc = malloc(sizeof(double *) * (size_t)nt);
+    double **und = malloc(sizeof(double *) * (size_t)nt);
     acc[0] = dV;
+    und[0] = undecided;
     for (int t = 1; t < nt; ++t) {
         acc[t] = calloc((size_t)(3 * nodes), sizeof(double));
-        if (!acc[t]) {   /* out of memory: the remaining work runs on fewer threads */
+        und[t] = undecided ? calloc((size_t)nodes, sizeof(double)) : NULL;
+        if (!acc[t] || (undecided && !und[t])) {   /* out of memory: the work runs on fewer threads */
+            free(acc[t]);
+            free(und[t]);
             nt = t;
             break;
         }
@@ -650,16 +692,20 @@ static int64_t update_paper_views(const orc_grid *g, const double *vol, const or
 #pragma omp parallel for num_threads(nt) schedule(static, 1) reduction(+ : view_total)
         for (int py = 0; py < c->height; ++py) {
             double *dst = acc[ORC_THREAD()];
+            double *ust = und[ORC_THREAD()];
             for (int px = 0; px < c->width; ++px) {
                 int64_t pix = off + (int64_t)py * c->width + px;
                 if (!mask[pix]) continue;
                 const double *dL = residual + 3 * pix;
+                double dl_max = fabs(dL[0]);
+                if (fabs(dL[1]) > dl_max) dl_max = fabs(dL[1]);
+                if (fabs(dL[2]) > dl_max) dl_max = fabs(dL[2]);
                 double o[3], d[3], t0, t1;
                 camera_ray(g, c, px, py, o, d);
                 if (!clip_ray(g, o, d, &t0, &t1)) continue;
                 int64_t n = segment_count(t0, t1, P->step);
                 view_total += n;
-                double T = 1.0;
+                double T = 1.0, T_last = 1.0;
                 for (int64_t k = 0; k < n; ++k) {
                     double len, p[3];
                     orc_sample s;
@@ -675,10 +721,39 @@ static int64_t update_paper_views(const orc_grid *g, const double *vol, const or
                         double a = G * P->alpha_l * T * exp(-P->alpha_d * D);
                         for (int ch = 0; ch < 3; ++ch) dst[3 * j + ch] += a * dL[ch];
                     }
+                    if (ust) {
+                        /* a sample within the margin of a face may belong to the cell beyond it */
+                        int cc[3], lo[3], hi[3], near = 0;
+                        double f[3];
+                        locate(g, p, cc, f);
+                        for (int a = 0; a < 3; ++a) {
+                            lo[a] = f[a] < g_face_eps && cc[a] > 0 ? -1 : 0;
+                            hi[a] = f[a] > 1.0 - g_face_eps && cc[a] < n_ax[a] - 2 ? 1 : 0;
+                            near |= lo[a] | hi[a];
+                        }
+                        if (near) add_to_cells(g, cc, lo, hi, fabs(G) * P->alpha_l * T * dl_max, ust);
+                    }
+                    T_last = T;
                     if (P->tau > 0.0)
                         T *= 1.0 - P->tau;
                     else
                         T *= exp(-s.sigma * len);
+                }
+                if (ust) {
+                    /* chord / step within the margin of an integer m: a sample at the
+                     * exit point (index m, a segment of almost no length) may be
+                     * added or dropped */
+                    const double x = (t1 - t0) / P->step, m = nearbyint(x);
+                    if (fabs(x - m) < g_count_eps && m >= 1.0) {
+                        double pe[3], f[3];
+                        int cc[3];
+                        const int lo[3] = {-1, -1, -1}, hi[3] = {1, 1, 1};
+                        for (int a = 0; a < 3; ++a) pe[a] = o[a] + t1 * d[a];
+                        locate(g, pe, cc, f);
+                        const double G = orc_g_draw(P->seed, P->g_std, iteration, view_base + v,
+                                                    (int64_t)py * c->width + px, (int64_t)m);
+                        add_to_cells(g, cc, lo, hi, fabs(G) * P->alpha_l * T_last * dl_max, ust);
+                    }
                 }
             }
         }
@@ -687,9 +762,13 @@ static int64_t update_paper_views(const orc_grid *g, const double *vol, const or
     }
     for (int t = 1; t < nt; ++t) {
         for (int64_t i = 0; i < 3 * nodes; ++i) dV[i] += acc[t][i];
+        if (undecided)
+            for (int64_t i = 0; i < nodes; ++i) undecided[i] += und[t][i];
         free(acc[t]);
+        free(und[t]);
     }
     free(acc);
+    free(und);
     return total;
 }
 
@@ -1130,6 +1209,8 @@ static int64_t view_residual(int height, int width, const double *rendered, cons
  * each iteration.  targets must have been through orc_prepare_targets (mask,
  * bbox).  rmse (iters x 3) gets the error of the images rendered in each
  * iteration.  samples[0..1] accumulate forward and adjustment sample counts.
+ * undecided (nullable, one value per node) accumulates over the iterations
+ * the adjustment's undecided budget (see update_paper_views).
  * P->storage != 0 keeps the records in a 16-bit type: the volume is rounded
  * to it on entry and after every update, the in-scattering source each time it
  * is formed (orc_round_storage).
@@ -1146,7 +1227,7 @@ void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
                      const orc_cam *cams, int ncam, const orc_params *P,
                      const double *targets, const uint8_t *mask, const int32_t *bbox,
                      int iters, int first_iteration, double *rmse, int64_t *samples,
-                     const uint32_t *hull, double stop_delta, int *iters_done)
+                     const uint32_t *hull, double stop_delta, int *iters_done, double *undecided)
 {
     int64_t nodes = (int64_t)g->nx * g->ny * g->nz;
     int64_t npix = 0;
@@ -1181,7 +1262,7 @@ void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
             samples[0] += orc_render(g, rvol, cams, ncam, P, img, NULL);
             orc_residual(ncam, cams[0].height, cams[0].width, img, targets, bbox, res, rmse + 3 * it);
             memset(dV, 0, sizeof(double) * 3 * (size_t)nodes);
-            samples[1] += orc_update_paper(g, rvol, cams, ncam, P, res, mask, first_iteration + it, dV);
+            samples[1] += orc_update_paper(g, rvol, cams, ncam, P, res, mask, first_iteration + it, dV, undecided);
             orc_apply_update(nodes, vol, dV, P->clamp_nonneg);
             orc_round_storage(4 * nodes, vol, P->storage);
             if (hull)
@@ -1213,7 +1294,7 @@ void orc_reconstruct(const orc_grid *g, double *vol, const double *albedo,
                 count += view_residual(c->height, c->width, img + 3 * off, targets + 3 * off, bbox + 4 * v,
                                        res + 3 * off, acc);
                 samples[1] += update_paper_views(g, rvol, c, 1, P, res + 3 * off, mask + off,
-                                                 first_iteration + it, v, dV);
+                                                 first_iteration + it, v, dV, undecided);
                 if (P->sequential) {
                     orc_apply_update(nodes, vol, dV, P->clamp_nonneg);
                     orc_round_storage(4 * nodes, vol, P->storage);

@@ -47,6 +47,8 @@ struct fr_ctx {
     Buf verr;                        // volume-error partials and result
     Buf L6;                          // directional radiances for anisotropic in-scattering
     Buf hull, sat;                   // visual hull tags, flame-mask tables
+    Buf vol_stage;                   // float32 staging of fr_volume_upload / fr_volume_download
+    std::vector<void*> owned;        // volume records allocated by fr_volume_create
     unsigned long long* host_counter = nullptr;  // pinned host scratch of kHostScratchBytes
     void* staging = nullptr;         // pinned host staging of batch tables
     size_t staging_bytes = 0;

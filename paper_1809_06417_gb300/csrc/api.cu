@@ -64,8 +64,10 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     cudaStreamSynchronize(c->stream);
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
                    &c->rmse, &c->J, &c->src, &c->flame_cnt, &c->flame_list, &c->batch, &c->pairs,
-                   &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr, &c->L6, &c->fin, &c->flame_tm})
+                   &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr, &c->L6, &c->fin, &c->flame_tm,
+                   &c->vol_stage})
         if (b->p) cudaFree(b->p);
+    for (void* p : c->owned) cudaFree(p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
     if (c->staging) cudaFreeHost(c->staging);
     if (c->staging_done) cudaEventDestroy(c->staging_done);
@@ -319,6 +321,194 @@ extern "C" fr_status fr_planck_lut(fr_ctx* c, float t_min, float t_max, int m, f
     FR_TRY(check_align(c, lut, 16, "lut"));
     FR_TRY(check_dev(c, lut, (size_t)m * 16, "lut"));
     FR_CUDA(c, launch_planck_lut(t_min, t_max, m, lut, c->stream));
+    return FR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Volumes owned by the library
+// ---------------------------------------------------------------------------
+
+extern "C" fr_status fr_volume_create(fr_ctx* c, int nx, int ny, int nz, const float origin[3], float h, int kind,
+                                      int dtype, fr_volume* out)
+{
+    FR_BEGIN(c);
+    if (!out || !origin) return fail(c, FR_EINVAL, "out and origin must not be NULL");
+    fr_volume v{};
+    v.nx = nx; v.ny = ny; v.nz = nz;
+    v.kind = kind;
+    v.dtype = dtype;
+    for (int a = 0; a < 3; ++a) v.origin[a] = origin[a];
+    v.h = h;
+    if (nx < 2 || ny < 2 || nz < 2 || nx > 8192 || ny > 8192 || nz > 8192)
+        return fail(c, FR_EINVAL, "extents must be in [2, 8192], got %d x %d x %d", nx, ny, nz);
+    if (node_count(&v) >= (1LL << 31)) return fail(c, FR_EINVAL, "at most 2^31 - 1 nodes");
+    if (kind != FR_KIND_RGB && kind != FR_KIND_TEMP) return fail(c, FR_EINVAL, "bad kind %d", kind);
+    if (dtype != FR_F32 && dtype != FR_BF16 && dtype != FR_F16) return fail(c, FR_EINVAL, "bad dtype %d", dtype);
+    if (!(h > 0.0f) || !std::isfinite(h) || !finite3(origin))
+        return fail(c, FR_EINVAL, "spacing must be positive and origin finite");
+    const size_t bytes = (size_t)node_count(&v) * rec_bytes(&v);
+    void* data = nullptr;
+    if (cudaMalloc(&data, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, FR_ENOMEM, "cannot allocate %zu bytes of volume records", bytes);
+    }
+    cudaError_t e = cudaMemsetAsync(data, 0, bytes, c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(data);
+        return cuda_fail(c, e, "cudaMemsetAsync");
+    }
+    c->owned.push_back(data);
+    v.data = data;
+    *out = v;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_volume_free(fr_ctx* c, fr_volume* vol)
+{
+    FR_BEGIN(c);
+    if (!vol) return fail(c, FR_EINVAL, "vol is NULL");
+    auto it = std::find(c->owned.begin(), c->owned.end(), vol->data);
+    if (!vol->data || it == c->owned.end())
+        return fail(c, FR_EINVAL, "vol was not created by fr_volume_create on this context");
+    FR_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->owned.erase(it);
+    FR_CUDA(c, cudaFree(vol->data));
+    vol->data = nullptr;
+    return FR_OK;
+}
+
+// float32 values of a volume's records (nodes x components)
+static size_t volume_values(const fr_volume* v) { return (size_t)node_count(v) * rec_components(v->kind); }
+
+extern "C" fr_status fr_volume_upload(fr_ctx* c, fr_volume* vol, const float* src, int src_is_host)
+{
+    FR_BEGIN(c);
+    FR_TRY(check_volume(c, vol, "vol"));
+    if (!src) return fail(c, FR_EINVAL, "src is NULL");
+    const size_t n = volume_values(vol), bytes = n * sizeof(float);
+    if (!src_is_host) {
+        FR_TRY(check_align(c, src, 16, "src"));
+        FR_TRY(check_dev(c, src, bytes, "src"));
+    }
+    const cudaMemcpyKind kind = src_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (vol->dtype == FR_F32) {
+        FR_CUDA(c, cudaMemcpyAsync(vol->data, src, bytes, kind, c->stream));
+        return FR_OK;
+    }
+    FR_TRY(check_align(c, vol->data, 8, "vol"));
+    const float* d = src;
+    if (src_is_host) {
+        FR_TRY(ensure(c, c->vol_stage, bytes, "volume staging"));
+        FR_CUDA(c, cudaMemcpyAsync(c->vol_stage.p, src, bytes, kind, c->stream));
+        d = static_cast<const float*>(c->vol_stage.p);
+    }
+    FR_CUDA(c, launch_to_storage(d, vol->data, vol->dtype, (long long)n, c->stream));
+    return FR_OK;
+}
+
+extern "C" fr_status fr_volume_download(fr_ctx* c, const fr_volume* vol, float* dst, int dst_is_host)
+{
+    FR_BEGIN(c);
+    FR_TRY(check_volume(c, vol, "vol"));
+    if (!dst) return fail(c, FR_EINVAL, "dst is NULL");
+    const size_t n = volume_values(vol), bytes = n * sizeof(float);
+    if (!dst_is_host) {
+        FR_TRY(check_align(c, dst, 16, "dst"));
+        FR_TRY(check_dev(c, dst, bytes, "dst"));
+    }
+    const cudaMemcpyKind kind = dst_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (vol->dtype == FR_F32) {
+        FR_CUDA(c, cudaMemcpyAsync(dst, vol->data, bytes, kind, c->stream));
+    } else {
+        FR_TRY(check_align(c, vol->data, 8, "vol"));
+        float* d = dst;
+        if (dst_is_host) {
+            FR_TRY(ensure(c, c->vol_stage, bytes, "volume staging"));
+            d = static_cast<float*>(c->vol_stage.p);
+        }
+        FR_CUDA(c, launch_from_storage(vol->data, d, vol->dtype, (long long)n, c->stream));
+        if (dst_is_host) FR_CUDA(c, cudaMemcpyAsync(dst, d, bytes, kind, c->stream));
+    }
+    if (dst_is_host) FR_CUDA(c, cudaStreamSynchronize(c->stream));
+    return FR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Camera sets (host memory owned by the library)
+// ---------------------------------------------------------------------------
+
+struct fr_cams {
+    std::vector<fr_camera> cams;
+};
+
+static fr_status cams_finish(std::vector<fr_camera>& v, fr_cams** out)
+{
+    fr_ctx probe;   // validation messages are not kept: a host-only call has no context
+    if (check_cams(&probe, v.data(), (int)v.size()) != FR_OK) return FR_EINVAL;
+    fr_cams* c = new (std::nothrow) fr_cams();
+    if (!c) return FR_ENOMEM;
+    c->cams.swap(v);
+    *out = c;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_cams_create(int k, const double* P, const int32_t* wh, fr_cams** out)
+{
+    if (!out) return FR_EINVAL;
+    *out = nullptr;
+    if (k < 1 || k > FR_MAX_VIEWS || !P || !wh) return FR_EINVAL;
+    std::vector<fr_camera> v((size_t)k);
+    for (int i = 0; i < k; ++i) {
+        const fr_status s = fr_camera_from_projection(P + 12 * i, wh[2 * i], wh[2 * i + 1], &v[(size_t)i]);
+        if (s != FR_OK) return s;
+    }
+    return cams_finish(v, out);
+}
+
+extern "C" fr_status fr_cams_ring(int k, int width, int height, const float center[3], float radius, float fov_deg,
+                                  const float* elevation_deg, float phase, fr_cams** out)
+{
+    if (!out) return FR_EINVAL;
+    *out = nullptr;
+    if (k < 1 || k > FR_MAX_VIEWS || !center || !finite3(center) || !(radius > 0.0f) || !std::isfinite(radius) ||
+        !(fov_deg > 0.0f && fov_deg < 180.0f) || !std::isfinite(phase))
+        return FR_EINVAL;
+    const double pi = 3.14159265358979323846;
+    std::vector<fr_camera> v((size_t)k);
+    for (int i = 0; i < k; ++i) {
+        const double th = phase + 2.0 * pi * i / k;
+        const double el = elevation_deg ? elevation_deg[i] * pi / 180.0 : 0.0;
+        if (!std::isfinite(el) || std::fabs(el) >= 0.5 * pi) return FR_EINVAL;
+        const double off[3] = {std::cos(el) * std::cos(th), std::sin(el), std::cos(el) * std::sin(th)};
+        // looking at the centre, right = fwd x world up (+y), up = right x fwd
+        const double f[3] = {-off[0], -off[1], -off[2]};
+        double r[3] = {-f[2], 0.0, f[0]};
+        const double rn = std::sqrt(r[0] * r[0] + r[2] * r[2]);
+        for (double& x : r) x /= rn;
+        const double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+        fr_camera& c = v[(size_t)i];
+        memset(&c, 0, sizeof c);
+        for (int a = 0; a < 3; ++a) {
+            c.pos[a] = (float)(center[a] + radius * off[a]);
+            c.right[a] = (float)r[a];
+            c.up[a] = (float)u[a];
+            c.fwd[a] = (float)f[a];
+        }
+        c.tan_half_fov = (float)std::tan(0.5 * fov_deg * pi / 180.0);
+        c.width = width;
+        c.height = height;
+    }
+    return cams_finish(v, out);
+}
+
+extern "C" int32_t fr_cams_count(const fr_cams* c) { return c ? (int32_t)c->cams.size() : 0; }
+
+extern "C" const fr_camera* fr_cams_data(const fr_cams* c) { return c ? c->cams.data() : nullptr; }
+
+extern "C" fr_status fr_cams_destroy(fr_cams* c)
+{
+    if (!c) return FR_EINVAL;
+    delete c;
     return FR_OK;
 }
 

@@ -105,6 +105,10 @@ struct HgWeights {
 cudaError_t launch_source_hg(const void* emission, int dt, const float* albedo, const float* L6, HgWeights w,
                              void* out, long long nodes, cudaStream_t s);
 cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t s);
+// n float32 values (even; 8-byte aligned source, 16-byte aligned for the
+// vector path) to and from the 16-bit storage type dt, rounding to nearest even
+cudaError_t launch_to_storage(const float* src, void* dst, int dt, long long n, cudaStream_t s);
+cudaError_t launch_from_storage(const void* src, float* dst, int dt, long long n, cudaStream_t s);
 // visual hull: sat needs ncam (H+1)(W+1) uint32, tags one uint32 per node
 cudaError_t launch_visual_hull(const CamDev* cams, int ncam, int W, int H, int nx, int ny, int nz,
                                const float* targets, float thresh, unsigned* sat, unsigned* tags, cudaStream_t s);

@@ -1616,6 +1616,87 @@ cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Storage conversion of a volume's records (fr_volume_upload / download):
+// float32 values to and from the 16-bit storage types, rounding to nearest
+// even.  Streaming: four values (16 bytes of float32) per thread and step;
+// a count that is not a multiple of 4 leaves two values for the last thread.
+// ---------------------------------------------------------------------------
+
+template <int DT>
+__device__ __forceinline__ uint32_t pack2(float a, float b)
+{
+    if constexpr (DT == DT_BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    } else {
+        const __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ float2 unpack2(uint32_t u)
+{
+    if constexpr (DT == DT_BF16) return make_float2(bf16_lo(u), bf16_hi(u));
+    else return f16x2(u);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) to_storage_kernel(const float* __restrict__ src, void* dst, long long n)
+{
+    const long long quads = n >> 2;
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    uint2* d4 = reinterpret_cast<uint2*>(dst);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < quads; i += stride) {
+        const float4 v = __ldg(s4 + i);
+        d4[i] = make_uint2(pack2<DT>(v.x, v.y), pack2<DT>(v.z, v.w));
+    }
+    if ((n & 3) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const long long at = quads * 4;
+        reinterpret_cast<uint32_t*>(dst)[at >> 1] = pack2<DT>(src[at], src[at + 1]);
+    }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) from_storage_kernel(const void* src, float* __restrict__ dst, long long n)
+{
+    const long long quads = n >> 2;
+    const uint2* s4 = reinterpret_cast<const uint2*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < quads; i += stride) {
+        const uint2 u = __ldg(s4 + i);
+        const float2 a = unpack2<DT>(u.x), b = unpack2<DT>(u.y);
+        d4[i] = make_float4(a.x, a.y, b.x, b.y);
+    }
+    if ((n & 3) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const long long at = quads * 4;
+        const float2 a = unpack2<DT>(reinterpret_cast<const uint32_t*>(src)[at >> 1]);
+        dst[at] = a.x;
+        dst[at + 1] = a.y;
+    }
+}
+
+cudaError_t launch_to_storage(const float* src, void* dst, int dt, long long n, cudaStream_t s)
+{
+    const int g = grid_for((n + 3) / 4, 256);
+    if (dt == DT_BF16) to_storage_kernel<DT_BF16><<<g, 256, 0, s>>>(src, dst, n);
+    else if (dt == DT_F16) to_storage_kernel<DT_F16><<<g, 256, 0, s>>>(src, dst, n);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_storage(const void* src, float* dst, int dt, long long n, cudaStream_t s)
+{
+    const int g = grid_for((n + 3) / 4, 256);
+    if (dt == DT_BF16) from_storage_kernel<DT_BF16><<<g, 256, 0, s>>>(src, dst, n);
+    else if (dt == DT_F16) from_storage_kernel<DT_F16><<<g, 256, 0, s>>>(src, dst, n);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 cudaError_t check_word_volume(unsigned* word, bool reset)
 {
 #ifdef FR_CHECKED

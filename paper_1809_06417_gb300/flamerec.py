@@ -126,6 +126,15 @@ SIGNATURES = {
     "fr_phase_times": (_S, [_P, _P, _I, _P]),
     "fr_render_residual_noalloc": (_S, [_I, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, ctypes.c_char_p,
                                         ctypes.c_size_t]),
+    "fr_volume_create": (_S, [_P, _I, _I, _I, _P, _F, _I, _I, _P]),
+    "fr_volume_free": (_S, [_P, _P]),
+    "fr_volume_upload": (_S, [_P, _P, _P, _I]),
+    "fr_volume_download": (_S, [_P, _P, _P, _I]),
+    "fr_cams_create": (_S, [_I, _P, _P, _P]),
+    "fr_cams_ring": (_S, [_I, _I, _I, _P, _F, _F, _P, _F, _P]),
+    "fr_cams_count": (ctypes.c_int32, [_P]),
+    "fr_cams_data": (_P, [_P]),
+    "fr_cams_destroy": (_S, [_P]),
 }
 
 _lib = None
@@ -220,6 +229,66 @@ def volume(t, origin, h, kind=FR_KIND_RGB) -> fr_volume:
     v.h = float(h)
     v.data = t.data_ptr()
     return v
+
+
+class Cams:
+    """A camera set held by the library (fr_cams).  .array is the fr_camera
+    array the entry points take; len() is its count."""
+
+    def __init__(self, handle):
+        self.lib, self.h = load(), handle
+        n = self.lib.fr_cams_count(handle)
+        ptr = self.lib.fr_cams_data(handle)
+        self.array = ctypes.cast(ptr, ctypes.POINTER(fr_camera * n)).contents
+
+    def __len__(self):
+        return len(self.array)
+
+    def as_dicts(self):
+        return [dict(pos=list(c.pos), right=list(c.right), up=list(c.up), fwd=list(c.fwd),
+                     tan_half_fov=c.tan_half_fov, width=c.width, height=c.height) for c in self.array]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fr_cams_destroy(self.h)
+            self.h = None
+            self.array = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cams_create(projections, sizes) -> Cams:
+    """fr_cams_create: cameras from 3x4 projection matrices and (width, height) pairs."""
+    P = np.ascontiguousarray(projections, dtype=np.float64).reshape(-1, 12)
+    wh = np.ascontiguousarray(sizes, dtype=np.int32).reshape(-1, 2)
+    if len(P) != len(wh):
+        raise FrError(FR_EINVAL, "one size per projection")
+    h = ctypes.c_void_p()
+    st = load().fr_cams_create(len(P), P.ctypes.data, wh.ctypes.data, ctypes.byref(h))
+    if st != FR_OK:
+        raise FrError(st, "fr_cams_create rejected the projections")
+    return Cams(h)
+
+
+def cams_ring(k, width, height, center=(0.0, 0.0, 0.0), radius=2.0, fov_deg=60.0, elevation_deg=None,
+              phase=0.0) -> Cams:
+    """fr_cams_ring: k cameras on a ring around `center` looking at it."""
+    c = (ctypes.c_float * 3)(*[float(x) for x in center])
+    el = None
+    if elevation_deg is not None:
+        el = np.ascontiguousarray(elevation_deg, dtype=np.float32)
+        if el.shape != (k,):
+            raise FrError(FR_EINVAL, "one elevation per camera")
+    h = ctypes.c_void_p()
+    st = load().fr_cams_ring(int(k), int(width), int(height), c, float(radius), float(fov_deg),
+                             el.ctypes.data if el is not None else None, float(phase), ctypes.byref(h))
+    if st != FR_OK:
+        raise FrError(st, "fr_cams_ring rejected its arguments")
+    return Cams(h)
 
 
 def camera_from_projection(P, width, height):
@@ -439,6 +508,36 @@ class Context:
 
     def fr_synchronize(self):
         self.check(self.lib.fr_synchronize(self.h))
+
+    def fr_volume_create(self, shape, origin, h, kind=FR_KIND_RGB, dtype=FR_F32) -> fr_volume:
+        """A volume whose records the library allocates (zeroed); shape (nx, ny, nz)."""
+        v = fr_volume()
+        o = (ctypes.c_float * 3)(*[float(x) for x in origin])
+        nx, ny, nz = shape
+        self.check(self.lib.fr_volume_create(self.h, int(nx), int(ny), int(nz), o, float(h), int(kind), int(dtype),
+                                             ctypes.byref(v)))
+        return v
+
+    def fr_volume_free(self, vol):
+        self.check(self.lib.fr_volume_free(self.h, ctypes.byref(vol)))
+
+    @_nvtx
+    def fr_volume_upload(self, vol, src):
+        """src: float32 records, a host numpy array or a CUDA tensor."""
+        host = isinstance(src, np.ndarray)
+        if host:
+            src = np.ascontiguousarray(src, dtype=np.float32)
+        self.check(self.lib.fr_volume_upload(self.h, ctypes.byref(vol), _ptr(src), int(host)))
+        return src
+
+    @_nvtx
+    def fr_volume_download(self, vol, dst):
+        """dst: float32 records, a host numpy array (filled on return) or a CUDA tensor."""
+        host = isinstance(dst, np.ndarray)
+        if host and (dst.dtype != np.float32 or not dst.flags["C_CONTIGUOUS"]):
+            raise FrError(FR_EINVAL, "dst must be a contiguous float32 array")
+        self.check(self.lib.fr_volume_download(self.h, ctypes.byref(vol), _ptr(dst), int(host)))
+        return dst
 
 
 class Job:

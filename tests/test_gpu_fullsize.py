@@ -100,17 +100,20 @@ def test_full_size_render_residual_follows_oracle(orc, full):
 
 def test_full_size_reconstruct_iterations_follow_oracle(orc, full):
     """fr_reconstruct as the benchmark calls it (hull tags given, empty bricks
-    skipped, half-ray adjustment, in-scattering) for two iterations.  The
-    adjustment's key-point set changes where a sample crosses a cell face,
-    and float32 sample positions (about 1e-5 voxels off at 250 voxels from the
-    camera) put a few of the 2e7 samples on the other side of a face; each
-    such sample moves a few parts in 1e5 of a node's sum, so the volume is
-    compared relative to its maximum at 1e-3, as in the small loop tests."""
+    skipped, half-ray adjustment, in-scattering) for two iterations.  Which
+    eight key points a sample updates (Eq. 10) is an integer decision: of the
+    7e7 adjustment samples, those within float32 rounding of a cell face (or
+    the last sample of a ray whose chord is within rounding of a whole number
+    of steps) may update the neighbouring cell's key points on one side only.
+    The oracle bounds, per node, what those samples can move (its undecided
+    budget); every node must lie within 1e-4 of the volume's maximum plus its
+    budget."""
     fr, ctx, sc, P = full["fr"], full["ctx"], full["sc"], full["P"]
     v0 = _start(full)
     iters = 2
-    vol_ref, rmse_ref, samples = orc.reconstruct(sc, v0, P, full["t_ref"], full["mask"], full["bbox_ref"], iters,
-                                                 albedo=full["alb"], hull=full["tags"])
+    vol_ref, rmse_ref, samples, und = orc.reconstruct(sc, v0, P, full["t_ref"], full["mask"], full["bbox_ref"],
+                                                      iters, albedo=full["alb"], hull=full["tags"],
+                                                      with_undecided=True)
     v = torch.as_tensor(v0, dtype=torch.float32, device="cuda").contiguous()
     alb = torch.as_tensor(full["alb"], dtype=torch.float32, device="cuda").contiguous()
     p = fr.params(step=STEP, alpha_l=ALPHA_L, use_hull=1, hull_tags=tags_on_device(torch, full["tags"]),
@@ -120,21 +123,21 @@ def test_full_size_reconstruct_iterations_follow_oracle(orc, full):
                        full["bbox"], iters, p, albedo=alb, rmse=rmse)
     torch.cuda.synchronize()
     got = v.cpu().numpy().astype(np.float64)
-    e = rel_err(got[..., :3], vol_ref[..., :3])
-    moved = np.abs(vol_ref[..., :3] - v0[..., :3]).max() / np.abs(vol_ref[..., :3]).max()
+    scale = np.abs(vol_ref[..., :3]).max()
+    err = np.abs(got[..., :3] - vol_ref[..., :3]).max(axis=-1)
+    bound = 1e-4 * scale + und
+    flagged = und > 0
+    moved = np.abs(vol_ref[..., :3] - v0[..., :3]).max() / scale
     print(f"oracle samples (forward, adjustment) {samples}; rmse gpu {rmse.tolist()} oracle {rmse_ref.tolist()}")
-    print(f"full-size volume after {iters} iterations: max error / max {e.max():.3e}, "
-          f"p99.99 {np.quantile(e, 0.9999):.3e}; the update moved the volume by {moved:.3e} of its max")
+    print(f"full-size volume after {iters} iterations (the update moved it by {moved:.3e} of its max): "
+          f"max error / max {err.max() / scale:.3e}; nodes with an undecided budget {flagged.sum()} "
+          f"({flagged.mean():.2e}); max error / max off them {err[~flagged].max() / scale:.3e}; "
+          f"worst error / bound {np.max(err / bound):.3f}")
     # the first row is the error of the render of v0; the next ones follow updates
     np.testing.assert_allclose(rmse[0], rmse_ref[0], rtol=1e-4)
     np.testing.assert_allclose(rmse, rmse_ref, rtol=1e-3)
-    assert e.max() < 1e-3
-    # the change itself, relative to its largest magnitude: face flips move
-    # single samples' weights, so the bound holds for all but 1e-3 of the nodes
-    eu = rel_err(got[..., :3] - v0[..., :3], vol_ref[..., :3] - v0[..., :3])
-    print(f"update error / max update: max {eu.max():.3e}, p99.9 {np.quantile(eu, 0.999):.3e}")
-    assert np.quantile(eu, 0.999) < 1e-3
-    assert eu.max() < 2e-2
+    assert np.all(err <= bound)
+    assert flagged.mean() < 0.05
     outside = full["tags"] != (1 << VIEWS) - 1
     assert np.all(got[outside] == 0.0)
     assert np.array_equal(got[..., 3], v0[..., 3].astype(np.float32))

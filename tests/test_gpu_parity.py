@@ -168,9 +168,9 @@ def _adjust(fr, ctx, case, vol, residual, iteration=0, **kw):
 def test_adjust_paper_rule(orc, fr, ctx, tau, g_std):
     """Eq. 10 accumulated over all flame rays.  The key-point set of a sample
     changes when the sample crosses a cell face, so samples within float32
-    rounding (about 1e-5 voxels) of a face may land in the neighbouring cell on
-    one side only; the bound therefore applies to all but a small fraction of
-    nodes, and every node stays within the weight of a few samples."""
+    rounding of a face may land in the neighbouring cell on one side only; the
+    oracle bounds per node what such samples can move (its undecided budget),
+    and every node must lie within 1e-5 of the largest node plus that budget."""
     case = tiny_case(seed=4, jitter=8.0, step=0.5)
     img, t_ref, mask, bbox_ref, t_dev, bbox = _prepared(orc, fr, ctx, case)
     vol = case.vol.copy()
@@ -180,13 +180,16 @@ def test_adjust_paper_rule(orc, fr, ctx, tau, g_std):
     ren, _ = orc.render(sc, vol, P)
     res, _ = orc.residual(ren, t_ref, bbox_ref)
     res *= mask[..., None]
-    dV_ref, _ = orc.update_paper(sc, vol, P, res, mask, 3)
+    dV_ref, _, und = orc.update_paper(sc, vol, P, res, mask, 3, with_undecided=True)
     got = _adjust(fr, ctx, case, vol, res, iteration=3, alpha_l=0.01, tau=tau, g_std=g_std, seed=99)
     assert np.all(got[..., 3] == 0.0)
-    e = rel_err(got[..., :3], dV_ref)
-    print(f"adjust tau={tau} g={g_std}: max {e.max():.3e}, p99.9 {np.quantile(e, 0.999):.3e}")
-    assert np.quantile(e, 0.999) < 1e-4
-    assert e.max() < 2e-2
+    scale = np.abs(dV_ref).max()
+    err = np.abs(got[..., :3] - dV_ref).max(axis=-1)
+    bound = 1e-5 * scale + und
+    print(f"adjust tau={tau} g={g_std}: max error / max {err.max() / scale:.3e}, off undecided nodes "
+          f"{err[und == 0].max() / scale:.3e}; {np.count_nonzero(und)} nodes with a budget; "
+          f"worst error / bound {np.max(err / bound):.3f}")
+    assert np.all(err <= bound)
 
 
 def test_backward_matches_oracle_gradient(orc, fr, ctx):

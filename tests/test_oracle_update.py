@@ -178,3 +178,49 @@ def test_rmse_over_boxes(orc):
     np.testing.assert_allclose(res, t - r, rtol=0, atol=0)
     d = np.concatenate([(t - r)[0, 1:3, 1:4].reshape(-1, 3), (t - r)[1].reshape(-1, 3)])
     np.testing.assert_allclose(rmse, 255.0 * np.sqrt((d ** 2).mean(axis=0)), rtol=1e-13)
+
+
+def _shifted(cams, delta_world):
+    out = []
+    for c in cams:
+        c = dict(c)
+        c["pos"] = [x + delta_world for x in c["pos"]]
+        out.append(c)
+    return out
+
+
+def test_undecided_budget_covers_every_flip_of_a_small_shift(orc):
+    """Moving every sample by 5e-5 voxels (inside the face margin) moves a
+    node's adjustment by at most its undecided budget plus the continuous part
+    of the change (distances and transmittances move by that much, about 1e-4
+    of the largest node sum); with the margins at zero the same shift exceeds
+    the budget at some node -- the budget is what covers the face crossings."""
+    from paper_1809_06417_gb300 import synth
+    n, views, side = 16, 4, 48
+    shape, origin, h = synth.unit_grid(n)
+    cams = synth.ring_cameras(views, side, side, elevation_jitter_deg=12.0, seed=5)
+    vol = synth.blobs_volume(n, 5, radius_range=(2.0, 4.0))
+    P = orc.make_params(step=0.5, alpha_l=0.01)
+    sc = orc.Scene(shape, origin, h, cams)
+    img, _ = orc.render(sc, vol, P)
+    targets, mask, bbox = orc.prepare_targets(img / img.max(), 30 / 255)
+    v0 = vol.copy()
+    v0[..., :3] *= 0.3
+    ren, _ = orc.render(sc, v0, P)
+    res, _ = orc.residual(ren, targets, bbox)
+    res *= mask[..., None]
+    shifted = orc.Scene(shape, origin, h, _shifted(cams, 5e-5 * h))
+    dV2, _ = orc.update_paper(shifted, v0, P, res, mask, 0)
+    try:
+        dV, _, und = orc.update_paper(sc, v0, P, res, mask, 0, with_undecided=True)
+        diff = np.abs(dV2 - dV).max(axis=-1)
+        cont = 1e-4 * np.abs(dV).max()
+        assert np.count_nonzero(und) > 0
+        assert np.count_nonzero(und) < 0.2 * und.size
+        assert np.all(diff <= und + cont)
+        assert np.any(diff > cont)                          # the shift does cross faces
+        orc.set_undecided_margins(0.0, 0.0)
+        _, _, und0 = orc.update_paper(sc, v0, P, res, mask, 0, with_undecided=True)
+        assert np.any(diff > und0 + cont)
+    finally:
+        orc.set_undecided_margins()

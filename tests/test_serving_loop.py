@@ -1,7 +1,8 @@
 """Host-side logic of the request loop (no GPU): arrivals are honoured on the
-loop's clock, every request completes, latency is measured from submission to
-completion on the server's clock, and a job that the server refuses surfaces
-as an error."""
+loop's clock, every request completes, latency runs from a job's arrival to the
+end of the step that completed it (time spent waiting for a step in flight
+counts), warm-up requests stay out of the statistics, and a job that the
+server refuses surfaces as an error."""
 import pytest
 
 from paper_1809_06417_gb300.serving import Request, run_requests
@@ -88,3 +89,29 @@ def test_refused_job_raises():
 
     with pytest.raises(MemoryError):
         run_requests(srv, [Request(arrival=0.0, submit=refuse)], clock=clk, sleep=clk.sleep)
+
+
+def test_latency_counts_the_wait_for_a_step_in_flight():
+    """A job arriving while a long step runs is submitted only after it: its
+    latency includes that wait, its service time on the server does not."""
+    clk = FakeClock()
+    srv = FakeServer(clk, dt=0.05, slots=4)
+    reqs = [Request(arrival=0.0, submit=lambda s: s.submit(2)),
+            Request(arrival=0.01, submit=lambda s: s.submit(1))]
+    res = run_requests(srv, reqs, clock=clk, sleep=clk.sleep)
+    # the second job arrives at 0.01 during the first step (0 -> 0.05), is
+    # submitted at 0.05 and done after the second step, at 0.10
+    assert reqs[1].latency == pytest.approx(0.09, abs=1e-9)
+    assert reqs[1].service == pytest.approx(0.05, abs=1e-9)
+    assert len(res.latencies) == 2
+
+
+def test_warmup_requests_are_not_measured():
+    clk = FakeClock()
+    srv = FakeServer(clk, dt=0.01, slots=8)
+    reqs = [Request(arrival=0.01 * k, submit=lambda s: s.submit(3), warmup=k < 5) for k in range(12)]
+    res = run_requests(srv, reqs, clock=clk, sleep=clk.sleep)
+    assert len(res.latencies) == 7
+    assert all(r.latency is not None for r in reqs)
+    assert res.measured_start == pytest.approx(0.05)
+    assert res.throughput() == pytest.approx(7 / (res.measured_end - 0.05))
