@@ -490,10 +490,10 @@ def run_storage_comparison(fr, ctx, I, args, iters=50):
     p = method_params(args, I)
     out, vols = {}, {}
     for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
-        warm = I["vol0"].float().to(dt).contiguous()
+        warm = I["vol0"].float().to(dt).clone()
         ctx.fr_reconstruct(fr.volume(warm, I["origin"], I["h"]), I["fcams"], I["targets"], I["bbox"], 2, p,
                            albedo=I["albedo"])
-        vol = I["vol0"].float().to(dt).contiguous()
+        vol = I["vol0"].float().to(dt).clone()    # (a copy: I["vol0"] itself stays the start)
         fv = fr.volume(vol, I["origin"], I["h"])
         rmse = torch.zeros((iters, 3), device="cuda")
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -707,7 +707,7 @@ def run_serving(fr, ctx, jobs=500, rate=20.0, seed=5, step=0.5, warmup_s=10.0, p
 
 
 def run_temperature_views(fr, ctx, n=128, side=512, step=0.5, iters=50, seed=3, view_counts=(4, 16, 28),
-                          t_min=1000.0, t_max=2300.0):
+                          t_min=1000.0, t_max=2300.0, alpha_scale=1.0):
     """Paper-literal temperature path (Sec. 3.3.3) against the number of cameras
     (Sec. 5.2: 4, 16 and 28 cameras, temperatures in 1000-2300 K):
     targets rendered from a seeded temperature field through the colour-
@@ -736,8 +736,8 @@ def run_temperature_views(fr, ctx, n=128, side=512, step=0.5, iters=50, seed=3, 
         fv = fr.volume(rec, origin, h)
         tags = torch.zeros((n, n, n), dtype=torch.int32, device="cuda")
         ctx.fr_visual_hull(fv, fc, img, fr.params(flame_thresh=thresh), tags)
-        p = fr.params(step=step, alpha_l=alpha_for(n, views, side, step), flame_thresh=thresh, use_hull=1,
-                      hull_tags=tags)
+        p = fr.params(step=step, alpha_l=alpha_scale * alpha_for(n, views, side, step), flame_thresh=thresh,
+                      use_hull=1, hull_tags=tags)
         rmse = np.zeros((iters, 3), dtype=np.float32)
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -1323,6 +1323,18 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
     // visual hull per problem (from its own targets) and exact empty-brick skipping
     const bool hull = p->use_hull != 0;
     const bool skip = p->skip_empty && !(p->tau > 0.0f);
+    // the adjustment over ray parts (as in fr_reconstruct) when every
+    // problem's pixel index leaves the list entries' top two bits free
+#if FR_ADJ_SPLIT > 1
+    int parts = FR_ADJ_SPLIT;
+    for (int i = 0; i < nprob; ++i) {
+        const fr_problem& q = probs[i];
+        if (q.cams && q.ncam > 0 && (long long)q.ncam * q.cams[0].width * q.cams[0].height >= (1LL << 30) - 1)
+            parts = 1;
+    }
+#else
+    const int parts = 1;
+#endif
     // sizes and validation
     size_t arena = 0, cams_total = 0;
     long long tiles_total = 0;
@@ -1345,7 +1357,9 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         const int nt = tiles_of(q.cams[0].width, q.cams[0].height, q.ncam);
         arena += align256(ib) + align256((size_t)node_count(&q.vol) * 16) + align256((size_t)nt * 16) +
                  align256((size_t)std::max(iters, 1) * 16) + align256(flame_list_buf_entries(nt) * 4) +
-                 align256((size_t)nt * kTileThreads * 4) + align256((size_t)node_count(&q.vol) * 2 * rec_bytes(&q.vol));
+                 align256((size_t)nt * kTileThreads * 4 * parts) +
+                 align256((size_t)node_count(&q.vol) * 2 * rec_bytes(&q.vol)) +
+                 align256((size_t)npix * 4 * (parts - 1));
         const size_t tb = align256(brick_table_bytes(q.vol.nx, q.vol.ny, q.vol.nz));
         if (hull) arena += align256((size_t)node_count(&q.vol) * 4);
         if (skip) arena += tb;
@@ -1353,7 +1367,7 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         tiles_total += nt;
         cams_total += (size_t)q.ncam;
     }
-    if (tiles_total >= (1LL << 31)) return fail(c, FR_EINVAL, "too many tiles in one batch");
+    if (tiles_total * parts >= (1LL << 31)) return fail(c, FR_EINVAL, "too many tiles in one batch");
     if (iters == 0) return FR_OK;
     const size_t tab_probs = align256(sizeof(ProbDev) * nprob);
     const size_t tab_cams = align256(sizeof(CamDev) * cams_total);
@@ -1397,9 +1411,13 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         float* partials = reinterpret_cast<float*>(dbase + off); off += align256((size_t)nt * 16);
         float* sqerr = reinterpret_cast<float*>(dbase + off); off += align256((size_t)iters * 16);
         unsigned* fbuf = reinterpret_cast<unsigned*>(dbase + off); off += align256(flame_list_buf_entries(nt) * 4);
-        // (runs padded to whole warps: at most a tile's worth of entries per tile)
-        unsigned* flist = reinterpret_cast<unsigned*>(dbase + off); off += align256((size_t)nt * kTileThreads * 4);
+        // (runs padded to whole warps: at most a tile's worth of entries per tile and part)
+        unsigned* flist = reinterpret_cast<unsigned*>(dbase + off);
+        off += align256((size_t)nt * kTileThreads * 4 * parts);
         void* pairs = dbase + off; off += align256((size_t)nodes * 2 * rec_bytes(&q.vol));
+        const size_t npix_q = (size_t)q.ncam * q.cams[0].width * q.cams[0].height;
+        float* tpart = parts > 1 ? reinterpret_cast<float*>(dbase + off) : nullptr;
+        off += align256(npix_q * 4 * (parts - 1));
         const size_t tb = align256(brick_table_bytes(q.vol.nx, q.vol.ny, q.vol.nz));
         unsigned* tags = nullptr;
         unsigned char *occ = nullptr, *hb = nullptr;
@@ -1441,11 +1459,12 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         P.iteration = first_iteration;
         P.sq_slot = 0;
         P.pairs = pairs;
+        P.tpart = tpart;
         h_probs[i] = P;
         for (int v = 0; v < q.ncam; ++v) h_cams[cam_off + v] = a.cams[v];
         h_tiles[i] = tile_off;
         FR_CUDA(c, cudaMemsetAsync(dV, 0, (size_t)nodes * 16, s));
-        FR_CUDA(c, launch_flame_list(a, nt, fbuf, flist, s));
+        FR_CUDA(c, launch_flame_list(a, nt, fbuf, flist, s, parts));
         cam_off += (size_t)q.ncam;
         tile_off += nt;
     }
@@ -1464,7 +1483,7 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
                 e = launch_fwd_batch(d_probs, d_tiles, nprob, tile_off, dt, KIND_RGB, tau, true, st, skip);
             if (e == cudaSuccess) e = launch_finalize_batch(d_probs, nprob, it, st);
             if (e == cudaSuccess)
-                e = launch_adjust_list_batch(d_probs, d_tiles, nprob, tile_off, dt, tau, it, st, hull && skip);
+                e = launch_adjust_list_batch(d_probs, d_tiles, nprob, tile_off, dt, tau, it, st, hull && skip, parts);
             if (e == cudaSuccess) e = launch_apply_batch(d_probs, nprob, dt, p->clamp_nonneg, st);   // + hull clear
         }
         return e;

@@ -116,6 +116,11 @@ struct ProbDev {
     const unsigned char* adj_occ;
     const unsigned* adj_box;     // box of those bricks
     int nbx, nby, nbz;           // bricks along x, y and z
+    // batched launches with ray parts: per pixel, the transmittance at the
+    // start of parts 1 .. FR_ADJ_SPLIT - 1 (part-major: [(j - 1) npix + pixel]),
+    // written by the forward march for flame pixels; the flame-ray list then
+    // holds one entry per part (the part in an entry's top two bits)
+    float* tpart;
 };
 
 // Bricks of 4^3 cells: finer bricks follow the flame's surface more tightly

@@ -33,8 +33,11 @@ cudaError_t launch_fwd_batch(const ProbDev* probs, const int* tile_start, int np
 // x-pair records of every problem's volume (vol_rw -> pairs), RGB records
 cudaError_t launch_pair_pack_batch(const ProbDev* probs, int nprob, int dt, cudaStream_t s);
 cudaError_t launch_adjust(const SingleArgs& a, int dt, int ntiles, cudaStream_t s);
+// parts > 1: every problem's flame list holds that many entries per ray
+// (launch_flame_list with the same parts) and ProbDev::tpart is set
 cudaError_t launch_adjust_list_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
-                                     int dt, bool tau, int iteration, cudaStream_t s, bool skip = false);
+                                     int dt, bool tau, int iteration, cudaStream_t s, bool skip = false,
+                                     int parts = 1);
 cudaError_t launch_finalize_batch(const ProbDev* probs, int nprob, int iteration, cudaStream_t s);
 cudaError_t launch_apply_batch(const ProbDev* probs, int nprob, int dt, int clamp_nonneg, cudaStream_t s);
 // batched brick tables (P.occ: flags cleared, then their box); the batched
@@ -57,10 +60,13 @@ cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cuda
                             void* scratch = nullptr, float* rmse3 = nullptr);
 // flame-ray list of a problem with prepared targets: buf needs
 // flame_list_buf_entries(ntiles) entries, the total lands at
-// buf[flame_list_total_at(ntiles)]; list needs one entry per pixel at most
+// buf[flame_list_total_at(ntiles)]; list needs parts entries per pixel at
+// most (parts > 1: one entry per part of each ray, the part in the top two
+// bits, each tile's run one padded block per part)
 inline size_t flame_list_buf_entries(int ntiles) { return (size_t)ntiles * (kTileThreads / 32 + 1) + 1; }
 inline size_t flame_list_total_at(int ntiles) { return (size_t)ntiles * (kTileThreads / 32 + 1); }
-cudaError_t launch_flame_list(const SingleArgs& a, int ntiles, unsigned* buf, unsigned* list, cudaStream_t s);
+cudaError_t launch_flame_list(const SingleArgs& a, int ntiles, unsigned* buf, unsigned* list, cudaStream_t s,
+                              int parts = 1);
 // tm (nullable): the list holds both halves of every flame ray (ProbDev::flist_tm)
 cudaError_t launch_adjust_list(const SingleArgs& a, int dt, int ntiles, const unsigned* list,
                                const unsigned* count, cudaStream_t s, const float* tm = nullptr);

@@ -378,6 +378,15 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
             for (unsigned j = 0; j < parts; ++j) P.flist[run_at + j * padded + threadIdx.x] = kNoPixel;
         }
     }
+    if constexpr (SPLIT && FR_ADJ_SPLIT > 1) {
+        // batched problems: the transmittance at each part boundary of a
+        // flame pixel, read by the adjustment of that part
+        if (P.tpart && flame) {
+            const long long npix = (long long)P.ncam * P.H * P.W;
+#pragma unroll
+            for (int j = 0; j < kTm; ++j) P.tpart[j * npix + pix] = Tm[j];
+        }
+    }
     if (P.partials) {
         __shared__ float red[4][kTileThreads / 32];
         a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2); cnt = warp_sum(cnt);
@@ -416,7 +425,7 @@ __global__ void FR_FWD_BATCH_BOUNDS fwd_batch(const ProbDev* __restrict__ probs,
 {
     const int p = find_problem(tile_start, nprob, blockIdx.x);
     const ProbDev& P = probs[p];
-    fwd_body<DT, KIND, TAU, MODE>(P, P.cams, blockIdx.x - __ldg(tile_start + p));
+    fwd_body<DT, KIND, TAU, MODE, true>(P, P.cams, blockIdx.x - __ldg(tile_start + p));
 }
 
 // ---------------------------------------------------------------------------
@@ -573,26 +582,38 @@ __global__ void FR_ADJ_LIST_BOUNDS adj_list(const __grid_constant__ SingleArgs a
 }
 
 // Batched form, one warp per CTA like adj_list: CTA b covers list entries
-// [n b', n b' + n) of the problem whose tile range holds tile b / (128 / n),
-// b' counted from that problem's first CTA (n = FR_ADJ_THREADS).  The G(s)
-// stream index is the problem's own iteration plus `iteration`.
+// [n b', n b' + n) of the problem whose tile range holds tile
+// b / (parts 128 / n), b' counted from that problem's first CTA
+// (n = FR_ADJ_THREADS).  With parts > 1 every problem's list holds `parts`
+// entries per flame ray (ProbDev::tpart), part j starting from the
+// transmittance the forward stored for it.  The G(s) stream index is the
+// problem's own iteration plus `iteration`.
 template <int DT, bool TAU, bool SKIP>
 __global__ void FR_ADJ_LIST_BOUNDS adj_list_batch(const ProbDev* __restrict__ probs,
-                                                  const int* __restrict__ tile_start, int nprob, int iteration)
+                                                  const int* __restrict__ tile_start, int nprob, int iteration,
+                                                  unsigned parts)
 {
-    constexpr unsigned kPer = kTileThreads / FR_ADJ_THREADS;   // CTAs per tile
-    const int p = find_problem(tile_start, nprob, (int)(blockIdx.x / kPer));
+    const unsigned per = parts * (unsigned)(kTileThreads / FR_ADJ_THREADS);   // CTAs per tile
+    const int p = find_problem(tile_start, nprob, (int)(blockIdx.x / per));
     const ProbDev& P = probs[p];
-    const unsigned i = (blockIdx.x - (unsigned)__ldg(tile_start + p) * kPer) * (unsigned)FR_ADJ_THREADS + threadIdx.x;
+    const unsigned i = (blockIdx.x - (unsigned)__ldg(tile_start + p) * per) * (unsigned)FR_ADJ_THREADS + threadIdx.x;
     if (i >= __ldg(P.list_count)) return;
-    const unsigned pix = __ldg(P.list + i);
-    if (pix == kNoPixel) return;
+    unsigned e = __ldg(P.list + i);
+    if (e == kNoPixel) return;
+    int part = -1;
+    float T0 = 1.0f;
+    if (parts > 1u) {
+        part = (int)(e >> 30);
+        e &= 0x3fffffffu;
+    }
     const unsigned per_view = (unsigned)P.W * (unsigned)P.H;
+    const unsigned pix = (unsigned)FR_CHK(e, (long long)P.ncam * per_view, 8u);
+    if (part > 0) T0 = __ldg(P.tpart + (size_t)(part - 1) * P.ncam * per_view + pix);
     const int view = (int)(pix / per_view);
     const unsigned r = pix - (unsigned)view * per_view;
     const int py = (int)(r / (unsigned)P.W), px = (int)(r - (unsigned)py * (unsigned)P.W);
-    if (P.g_std > 0.0f) adj_ray<DT, TAU, SKIP, true>(P, P.cams, view, px, py, P.iteration + iteration);
-    else adj_ray<DT, TAU, SKIP, false>(P, P.cams, view, px, py, P.iteration + iteration);
+    if (P.g_std > 0.0f) adj_ray<DT, TAU, SKIP, true>(P, P.cams, view, px, py, P.iteration + iteration, part, T0);
+    else adj_ray<DT, TAU, SKIP, false>(P, P.cams, view, px, py, P.iteration + iteration, part, T0);
 }
 
 template <int DT, bool TAU>
@@ -860,7 +881,8 @@ __device__ __forceinline__ bool is_flame(const ProbDev& P, int view, int px, int
 constexpr int kWarpsPerTile = kTileThreads / 32;
 
 __global__ void __launch_bounds__(kTileThreads) flame_count_kernel(const __grid_constant__ SingleArgs a,
-                                                                   unsigned* __restrict__ buf, int ntiles)
+                                                                   unsigned* __restrict__ buf, int ntiles,
+                                                                   unsigned parts)
 {
     __shared__ unsigned wc[kWarpsPerTile];
     int view, px, py;
@@ -875,7 +897,8 @@ __global__ void __launch_bounds__(kTileThreads) flame_count_kernel(const __grid_
     if (threadIdx.x == 0) {
         unsigned t = 0;
         for (int i = 0; i < kWarpsPerTile; ++i) t += wc[i];
-        buf[(size_t)kWarpsPerTile * ntiles + blockIdx.x] = (t + 31u) & ~31u;   // the run padded to whole warps
+        // the run padded to whole warps, once per part of the rays
+        buf[(size_t)kWarpsPerTile * ntiles + blockIdx.x] = parts * ((t + 31u) & ~31u);
     }
 }
 
@@ -919,7 +942,7 @@ __global__ void __launch_bounds__(1024) flame_scan_kernel(unsigned* __restrict__
 
 __global__ void __launch_bounds__(kTileThreads) flame_list_kernel(const __grid_constant__ SingleArgs a,
                                                                   const unsigned* __restrict__ buf, int ntiles,
-                                                                  unsigned* __restrict__ list)
+                                                                  unsigned* __restrict__ list, unsigned parts)
 {
     const ProbDev& P = a.p;
     int view, px, py;
@@ -927,17 +950,21 @@ __global__ void __launch_bounds__(kTileThreads) flame_list_kernel(const __grid_c
     const bool f = is_flame(P, view, px, py);
     const unsigned m = __ballot_sync(0xffffffffu, f);
     const unsigned run_at = buf[(size_t)kWarpsPerTile * ntiles + blockIdx.x];
+    unsigned len = 0;
+    for (int i = 0; i < kWarpsPerTile; ++i) len += buf[blockIdx.x * kWarpsPerTile + i];
+    const unsigned padded = (len + 31u) & ~31u;
     if (f) {
         const int w = threadIdx.x >> 5;
         unsigned at = run_at;
         for (int i = 0; i < w; ++i) at += buf[blockIdx.x * kWarpsPerTile + i];
         at += __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
-        list[at] = (unsigned)(((long long)view * P.H + py) * P.W + px);
+        const unsigned pix = (unsigned)(((long long)view * P.H + py) * P.W + px);
+        // part j's block of the run: the pixel tagged j in the top two bits
+        for (unsigned j = 0; j < parts; ++j) list[at + j * padded] = pix | (j << 30);
     }
     // the run's padding to whole warps names no pixel
-    unsigned len = 0;
-    for (int i = 0; i < kWarpsPerTile; ++i) len += buf[blockIdx.x * kWarpsPerTile + i];
-    if ((unsigned)threadIdx.x >= len && (unsigned)threadIdx.x < ((len + 31u) & ~31u)) list[run_at + threadIdx.x] = kNoPixel;
+    if ((unsigned)threadIdx.x >= len && (unsigned)threadIdx.x < padded)
+        for (unsigned j = 0; j < parts; ++j) list[run_at + j * padded + threadIdx.x] = kNoPixel;
 }
 
 // Per-problem sums of the squared-error partials (one CTA per problem), into
@@ -1046,13 +1073,14 @@ cudaError_t launch_adjust(const SingleArgs& a, int dt, int ntiles, cudaStream_t 
 }
 
 cudaError_t launch_adjust_list_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
-                                     int dt, bool tau, int iteration, cudaStream_t s, bool skip)
+                                     int dt, bool tau, int iteration, cudaStream_t s, bool skip, int parts)
 {
-    dim3 grid((unsigned)total_tiles * (kTileThreads / FR_ADJ_THREADS)), block(FR_ADJ_THREADS);
+    const unsigned np = parts > 1 ? (unsigned)parts : 1u;
+    dim3 grid((unsigned)total_tiles * (kTileThreads / FR_ADJ_THREADS) * np), block(FR_ADJ_THREADS);
     FR_DISPATCH_DT(dt, D, {
-        if (tau) adj_list_batch<D, true, false><<<grid, block, 0, s>>>(probs, tile_start, nprob, iteration);
-        else if (skip) adj_list_batch<D, false, true><<<grid, block, 0, s>>>(probs, tile_start, nprob, iteration);
-        else adj_list_batch<D, false, false><<<grid, block, 0, s>>>(probs, tile_start, nprob, iteration);
+        if (tau) adj_list_batch<D, true, false><<<grid, block, 0, s>>>(probs, tile_start, nprob, iteration, np);
+        else if (skip) adj_list_batch<D, false, true><<<grid, block, 0, s>>>(probs, tile_start, nprob, iteration, np);
+        else adj_list_batch<D, false, false><<<grid, block, 0, s>>>(probs, tile_start, nprob, iteration, np);
     });
     return cudaGetLastError();
 }
@@ -1114,11 +1142,13 @@ cudaError_t launch_finalize(const float* partials, int ntiles, float* out4, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_flame_list(const SingleArgs& a, int ntiles, unsigned* buf, unsigned* list, cudaStream_t s)
+cudaError_t launch_flame_list(const SingleArgs& a, int ntiles, unsigned* buf, unsigned* list, cudaStream_t s,
+                              int parts)
 {
-    flame_count_kernel<<<ntiles, kTileThreads, 0, s>>>(a, buf, ntiles);
+    const unsigned np = parts > 1 ? (unsigned)parts : 1u;
+    flame_count_kernel<<<ntiles, kTileThreads, 0, s>>>(a, buf, ntiles, np);
     flame_scan_kernel<<<1, 1024, 0, s>>>(buf + (size_t)kWarpsPerTile * ntiles, ntiles);
-    flame_list_kernel<<<ntiles, kTileThreads, 0, s>>>(a, buf, ntiles, list);
+    flame_list_kernel<<<ntiles, kTileThreads, 0, s>>>(a, buf, ntiles, list, np);
     return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@ struct fr_job {
     float* sqerr = nullptr;
     unsigned* fbuf = nullptr;
     unsigned* flist = nullptr;
+    float* tpart = nullptr;             // transmittance at the ray parts' starts (flame pixels)
     void* pairs = nullptr;
     unsigned* tags = nullptr;           // visual hull tags (server with use_hull)
     unsigned char* occ = nullptr;       // brick table of the non-empty records (skip_empty)
@@ -56,8 +57,17 @@ struct fr_server {
 namespace {
 
 struct JobLayout {
-    size_t vol, targets, bbox, residual, dV, partials, sqerr, fbuf, flist, pairs, tags, occ, hull_bricks, total;
+    size_t vol, targets, bbox, residual, dV, partials, sqerr, fbuf, flist, tpart, pairs, tags, occ, hull_bricks, total;
 };
+
+// Parts each flame ray is adjusted in (as in fr_reconstruct): the list
+// entries carry the part in their top two bits, so jobs stay below 2^30 - 1
+// pixels (fr_server_submit refuses larger ones).
+#if FR_ADJ_SPLIT > 1
+constexpr int kServerParts = FR_ADJ_SPLIT;
+#else
+constexpr int kServerParts = 1;
+#endif
 
 bool server_hull(const fr_server* s) { return s->p.use_hull != 0; }
 bool server_skip(const fr_server* s) { return s->p.skip_empty && !(s->p.tau > 0.0f); }
@@ -77,7 +87,8 @@ JobLayout job_layout(const fr_job_desc& d, int dtype, const fr_camera* cams, boo
     L.partials = o; o += align256((size_t)nt * 16);
     L.sqerr = o; o += align256((size_t)std::max(d.iters, 1) * 16);
     L.fbuf = o; o += align256(flame_list_buf_entries(nt) * 4);
-    L.flist = o; o += align256((size_t)nt * kTileThreads * 4);   // runs padded to whole warps
+    L.flist = o; o += align256((size_t)nt * kTileThreads * 4 * kServerParts);   // runs padded to whole warps
+    L.tpart = o; o += align256((size_t)d.ncam * cams[0].width * cams[0].height * 4 * (kServerParts - 1));
     L.pairs = o; o += align256((size_t)nodes * 8 * dtype_bytes(dtype));
     const size_t tb = align256(brick_table_bytes(d.nx, d.ny, d.nz));
     L.tags = o; if (hull) o += align256((size_t)nodes * 4);
@@ -133,6 +144,7 @@ fr_status job_admit(fr_server* s, fr_job* j)
     j->sqerr = reinterpret_cast<float*>(j->mem + L.sqerr);
     j->fbuf = reinterpret_cast<unsigned*>(j->mem + L.fbuf);
     j->flist = reinterpret_cast<unsigned*>(j->mem + L.flist);
+    j->tpart = kServerParts > 1 ? reinterpret_cast<float*>(j->mem + L.tpart) : nullptr;
     j->pairs = j->mem + L.pairs;
     j->tags = hull ? reinterpret_cast<unsigned*>(j->mem + L.tags) : nullptr;
     j->occ = skip ? reinterpret_cast<unsigned char*>(j->mem + L.occ) : nullptr;
@@ -150,7 +162,7 @@ fr_status job_admit(fr_server* s, fr_job* j)
     fr_volume v = job_volume(j, s->dtype);
     fill_problem(&v, j->cams.data(), j->d.ncam, &s->p, a);
     a.p.targets = j->targets;
-    FR_CUDA(c, launch_flame_list(a, j->ntiles, j->fbuf, j->flist, st));
+    FR_CUDA(c, launch_flame_list(a, j->ntiles, j->fbuf, j->flist, st, kServerParts));
     if (hull) {
         // the job's visual hull from its prepared frames; records outside it cleared
         const unsigned full = j->d.ncam >= 32 ? 0xffffffffu : ((1u << j->d.ncam) - 1u);
@@ -270,7 +282,7 @@ extern "C" fr_status fr_server_submit(fr_server* s, const fr_job_desc* d, fr_job
     if (!std::isfinite(d->alpha_l)) return fail(c, FR_EINVAL, "alpha_l must be finite");
     if (!d->init_records || !d->targets || !d->result_records) return fail(c, FR_EINVAL, "NULL host buffer");
     const long long npix = (long long)d->ncam * d->cams[0].width * d->cams[0].height;
-    if (npix >= (1LL << 32)) return fail(c, FR_EINVAL, "at most 2^32 pixels per job");
+    if (npix >= (1LL << 30) - 1) return fail(c, FR_EINVAL, "at most 2^30 - 2 pixels per job");
     const size_t fp = job_layout(*d, s->dtype, d->cams, server_hull(s), server_skip(s)).total;
     if (fp > s->budget) return fail(c, FR_ENOMEM, "job needs %zu bytes, the budget is %zu", fp, s->budget);
     fr_job* j = new (std::nothrow) fr_job();
@@ -376,6 +388,7 @@ extern "C" fr_status fr_server_step(fr_server* s, int* running, int* queued)
             P.sq_slot = j->iters_done;
             if (j->d.alpha_l != 0.0f) P.alpha_l = j->d.alpha_l;
             P.pairs = j->pairs;
+            P.tpart = j->tpart;
             P.nbx = bricks_along(j->d.nx);
             P.nby = bricks_along(j->d.ny);
             P.nbz = bricks_along(j->d.nz);
@@ -401,7 +414,8 @@ extern "C" fr_status fr_server_step(fr_server* s, int* running, int* queued)
         if (skip) FR_CUDA(c, launch_brick_box_batch(dp, n, st));
         FR_CUDA(c, launch_fwd_batch(dp, dtl, n, tile_off, s->dtype, KIND_RGB, tau, true, st, skip));
         FR_CUDA(c, launch_finalize_batch(dp, n, 0, st));
-        FR_CUDA(c, launch_adjust_list_batch(dp, dtl, n, tile_off, s->dtype, tau, 0, st, hull && skip));
+        FR_CUDA(c, launch_adjust_list_batch(dp, dtl, n, tile_off, s->dtype, tau, 0, st, hull && skip,
+                                            kServerParts));
         FR_CUDA(c, launch_apply_batch(dp, n, s->dtype, s->p.clamp_nonneg, st));   // with the hull clear
         FR_CUDA(c, cudaStreamSynchronize(st));
         // advance and retire

@@ -69,8 +69,14 @@ def test_refusals(fr_ctx):
     with pytest.raises(fr.FrError, match="FR_EINVAL"):
         ctx.fr_volume_create((4, 4, 4), (0, 0, 0), 0.0)
     vol = ctx.fr_volume_create((4, 4, 4), (0, 0, 0), 1.0, dtype=fr.FR_BF16)
-    with pytest.raises(fr.FrError, match="FR_EINVAL"):
-        ctx.fr_volume_upload(vol, torch.zeros(10, device="cuda"))    # too short
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    big = torch.zeros(16 * 2 ** 20 // 4, device="cuda")   # its own 16 MiB allocation
+    tail = big[-64:]                                      # 256 bytes before it ends; 1 KiB are read
+    with pytest.raises(fr.FrError, match="FR_EINVAL.*allocation ends"):
+        ctx.fr_volume_upload(vol, tail)
+    with pytest.raises(fr.FrError, match="FR_EINVAL.*aligned"):
+        ctx.fr_volume_upload(vol, big[1:257])              # 4-byte offset
     ctx.fr_volume_free(vol)
 
 
