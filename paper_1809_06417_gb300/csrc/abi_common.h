@@ -48,6 +48,7 @@ struct fr_ctx {
     Buf L6;                          // directional radiances for anisotropic in-scattering
     Buf hull, sat;                   // visual hull tags, flame-mask tables
     Buf vol_stage;                   // float32 staging of fr_volume_upload / fr_volume_download
+    Buf probe;                       // measurement builds only (FR_ADJ_GATHER_PROBE)
     std::vector<void*> owned;        // volume records allocated by fr_volume_create
     unsigned long long* host_counter = nullptr;  // pinned host scratch of kHostScratchBytes
     void* staging = nullptr;         // pinned host staging of batch tables

@@ -65,7 +65,7 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
                    &c->rmse, &c->J, &c->src, &c->flame_cnt, &c->flame_list, &c->batch, &c->pairs,
                    &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr, &c->L6, &c->fin, &c->flame_tm,
-                   &c->vol_stage})
+                   &c->vol_stage, &c->probe})
         if (b->p) cudaFree(b->p);
     for (void* p : c->owned) cudaFree(p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
@@ -1073,6 +1073,16 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
             u.p.iteration = first_iteration + slot;
             FR_CUDA(c, launch_adjust_list(u, vol->dtype, nt, flame_list, flame_cnt + slot, st, flame_tm));
             FR_TRY(trace_mark(c, FR_PHASE_ADJUST));
+#ifdef FR_ADJ_GATHER_PROBE
+            // (measurement build: a gather's set-up work, timed as the finish phase)
+            if (hull) {
+                FR_TRY(ensure(c, c->probe, (size_t)nodes * 8 + 256, "gather probe"));
+                unsigned* pl = static_cast<unsigned*>(c->probe.p);
+                FR_CUDA(c, launch_gather_probe(u, hull, full, nodes, pl, pl + 2 * nodes,
+                                               reinterpret_cast<float*>(pl + nodes), st));
+                FR_TRY(trace_mark(c, FR_PHASE_FINISH));
+            }
+#endif
             FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg, 1,
                                     st, hull, full));
         } else {
@@ -1323,10 +1333,10 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
     // visual hull per problem (from its own targets) and exact empty-brick skipping
     const bool hull = p->use_hull != 0;
     const bool skip = p->skip_empty && !(p->tau > 0.0f);
-    // the adjustment over ray parts (as in fr_reconstruct) when every
-    // problem's pixel index leaves the list entries' top two bits free
-#if FR_ADJ_SPLIT > 1
-    int parts = FR_ADJ_SPLIT;
+    // the adjustment over ray parts (FR_BATCH_PARTS; whole rays by default)
+    // when every problem's pixel index leaves the list entries' top two bits free
+#if FR_BATCH_PARTS > 1
+    int parts = FR_BATCH_PARTS;
     for (int i = 0; i < nprob; ++i) {
         const fr_problem& q = probs[i];
         if (q.cams && q.ncam > 0 && (long long)q.ncam * q.cams[0].width * q.cams[0].height >= (1LL << 30) - 1)

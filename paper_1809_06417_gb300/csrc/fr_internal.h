@@ -33,6 +33,11 @@ cudaError_t launch_fwd_batch(const ProbDev* probs, const int* tile_start, int np
 // x-pair records of every problem's volume (vol_rw -> pairs), RGB records
 cudaError_t launch_pair_pack_batch(const ProbDev* probs, int nprob, int dt, cudaStream_t s);
 cudaError_t launch_adjust(const SingleArgs& a, int dt, int ntiles, cudaStream_t s);
+// Parts a batched problem's flame rays are adjusted in (march.cu: 1 unless
+// built with -DFR_BATCH_PARTS=FR_ADJ_SPLIT)
+#ifndef FR_BATCH_PARTS
+#define FR_BATCH_PARTS 1
+#endif
 // parts > 1: every problem's flame list holds that many entries per ray
 // (launch_flame_list with the same parts) and ProbDev::tpart is set
 cudaError_t launch_adjust_list_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
@@ -67,6 +72,12 @@ inline size_t flame_list_buf_entries(int ntiles) { return (size_t)ntiles * (kTil
 inline size_t flame_list_total_at(int ntiles) { return (size_t)ntiles * (kTileThreads / 32 + 1); }
 cudaError_t launch_flame_list(const SingleArgs& a, int ntiles, unsigned* buf, unsigned* list, cudaStream_t s,
                               int parts = 1);
+#ifdef FR_ADJ_GATHER_PROBE
+// lower-bound measurement of a gather adjustment (march.cu): list and sink
+// hold one entry per node, count one word
+cudaError_t launch_gather_probe(const SingleArgs& a, const unsigned* tags, unsigned full, long long nodes,
+                                unsigned* list, unsigned* count, float* sink, cudaStream_t s);
+#endif
 // tm (nullable): the list holds both halves of every flame ray (ProbDev::flist_tm)
 cudaError_t launch_adjust_list(const SingleArgs& a, int dt, int ntiles, const unsigned* list,
                                const unsigned* count, cudaStream_t s, const float* tm = nullptr);

@@ -419,13 +419,23 @@ __global__ void FR_FWD_BOUNDS fwd_single(const __grid_constant__ SingleArgs a)
 #else
 #define FR_FWD_BATCH_BOUNDS FR_MARCH_BOUNDS
 #endif
+// FR_BATCH_PARTS: parts each flame ray of a batch (and of the server) is
+// adjusted in.  1 (whole rays): the split, which makes the single-problem
+// adjustment 6% faster, measured 8% slower on the video batch (64 frames of
+// 96^3, 8 views of 384^2) and 10% lower in serving capacity, where many short
+// problems already fill the GPU's last wave and the forward's part bookkeeping
+// spills.
+#ifndef FR_BATCH_PARTS
+#define FR_BATCH_PARTS 1
+#endif
+static_assert(FR_BATCH_PARTS == 1 || FR_BATCH_PARTS == FR_ADJ_SPLIT, "batched parts: 1 or FR_ADJ_SPLIT");
 template <int DT, int KIND, bool TAU, int MODE>
 __global__ void FR_FWD_BATCH_BOUNDS fwd_batch(const ProbDev* __restrict__ probs, const int* __restrict__ tile_start,
                                               int nprob)
 {
     const int p = find_problem(tile_start, nprob, blockIdx.x);
     const ProbDev& P = probs[p];
-    fwd_body<DT, KIND, TAU, MODE, true>(P, P.cams, blockIdx.x - __ldg(tile_start + p));
+    fwd_body<DT, KIND, TAU, MODE, (FR_BATCH_PARTS > 1)>(P, P.cams, blockIdx.x - __ldg(tile_start + p));
 }
 
 // ---------------------------------------------------------------------------
@@ -437,9 +447,43 @@ __global__ void FR_FWD_BATCH_BOUNDS fwd_batch(const ProbDev* __restrict__ probs,
 // receives that sum times dL when the ray leaves it.
 // RG: G(s) drawn per sample (g_std > 0); false: G = 1 (a compile-time
 // constant, 1.6% faster than a per-sample test of g_std).
-template <int DT, bool TAU, bool SKIP, bool RG>
+// Accumulator of the key points' sums a ray releases, for the comparison of
+// FR_ADJ_ACCUM = 1 (see adj_list_tab): an open-addressing table of one CTA's
+// key points in shared memory, flushed with vector reductions when the CTA's
+// rays are done.
+#ifndef FR_ADJ_TAB_BITS
+#define FR_ADJ_TAB_BITS 10
+#endif
+constexpr int kTab = 1 << FR_ADJ_TAB_BITS;
+struct KeyTable {
+    int key[kTab];           // node index, -1 while free
+    float v[kTab][3];
+};
+
+// Adds {a, b, c} to node's entry (claimed with a compare-and-swap on its
+// first visit); after 8 occupied probes the sum goes straight to dV.
+__device__ __forceinline__ void tab_add(KeyTable& T, unsigned node, float a, float b, float c, float* dV)
+{
+    unsigned h = (node * 2654435761u) >> (32 - FR_ADJ_TAB_BITS);
+    const volatile int* keys = T.key;
+#pragma unroll 1
+    for (int probe = 0; probe < 8; ++probe) {
+        int k = keys[h];
+        if (k == -1) k = atomicCAS(&T.key[h], -1, (int)node);
+        if (k == -1 || k == (int)node) {
+            atomicAdd(&T.v[h][0], a);
+            atomicAdd(&T.v[h][1], b);
+            atomicAdd(&T.v[h][2], c);
+            return;
+        }
+        h = (h + 1) & (kTab - 1);
+    }
+    red_add_v4(dV + 4 * (size_t)node, a, b, c, 0.0f);
+}
+
+template <int DT, bool TAU, bool SKIP, bool RG, int ACC = 0>
 __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, int view, int px, int py,
-                                        int iteration, int part = -1, float T0 = 1.0f)
+                                        int iteration, int part = -1, float T0 = 1.0f, KeyTable* tab = nullptr)
 {
     // SKIP: samples in bricks with no key point inside the visual hull are
     // skipped.  Their records are zero (no extinction: T is unchanged) and
@@ -470,9 +514,13 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
     // without testing the weight (a zero test per slot measured 5% slower).
     // (Reloading all eight corner sigmas on every cell change instead of the
     // entering slots' measured 16% slower.)
-    auto leave = [&acc, dV, dl0, dl1, dl2, nodes](int t, int node, bool p) {
+    auto leave = [&acc, dV, dl0, dl1, dl2, nodes, tab](int t, int node, bool p) {
         const float w = acc[t];
-        red_add_v4_if(dV + 4 * (unsigned)FR_CHK(node, nodes, 2u), w * dl0, w * dl1, w * dl2, 0.0f, p);
+        if constexpr (ACC == 0) {
+            red_add_v4_if(dV + 4 * (unsigned)FR_CHK(node, nodes, 2u), w * dl0, w * dl1, w * dl2, 0.0f, p);
+        } else {
+            if (p) tab_add(*tab, (unsigned)FR_CHK(node, nodes, 2u), w * dl0, w * dl1, w * dl2, dV);
+        }
         acc[t] = p ? 0.0f : w;
     };
     auto enter = [&sg, vol, nodes](int t, int node, bool p) {
@@ -579,6 +627,54 @@ __global__ void FR_ADJ_LIST_BOUNDS adj_list(const __grid_constant__ SingleArgs a
     const int it = P.iteration + (P.iter_dev ? __ldg(P.iter_dev) : 0);
     if (P.g_std > 0.0f) adj_ray<DT, TAU, SKIP, true>(P, a.cams, view, px, py, it, part, T0);
     else adj_ray<DT, TAU, SKIP, false>(P, a.cams, view, px, py, it, part, T0);
+}
+
+// adj_list with each CTA's key-point sums gathered in a shared-memory table
+// (KeyTable) and flushed with one vector reduction per key point the CTA's
+// rays touched, instead of one per key point a ray leaves (FR_ADJ_ACCUM = 1;
+// a comparison variant, one warp per CTA).
+#ifndef FR_ADJ_ACCUM
+#define FR_ADJ_ACCUM 0
+#endif
+template <int DT, bool TAU, bool SKIP>
+__global__ void FR_ADJ_LIST_BOUNDS adj_list_tab(const __grid_constant__ SingleArgs a,
+                                                const unsigned* __restrict__ list,
+                                                const unsigned* __restrict__ count, const float* __restrict__ tm)
+{
+    static_assert(FR_ADJ_THREADS == 32, "one warp per CTA");
+    __shared__ KeyTable tab;
+    const unsigned n = __ldg(count);
+    const unsigned i = blockIdx.x * 32u + threadIdx.x;
+    if (blockIdx.x * 32u >= n) return;                 // the whole CTA past the list's end
+    for (int j = threadIdx.x; j < kTab; j += 32) {
+        tab.key[j] = -1;
+        tab.v[j][0] = tab.v[j][1] = tab.v[j][2] = 0.0f;
+    }
+    __syncwarp();
+    const ProbDev& P = a.p;
+    unsigned e = i < n ? __ldg(list + i) : kNoPixel;
+    if (e != kNoPixel) {
+        int part = -1;
+        float T0 = 1.0f;
+        if (tm) {
+            part = (int)(e >> 30);
+            e &= 0x3fffffffu;
+            if (part) T0 = __ldg(tm + i);
+        }
+        const unsigned pix = (unsigned)FR_CHK(e, (long long)P.ncam * P.W * P.H, 8u);
+        const unsigned per_view = (unsigned)P.W * (unsigned)P.H;
+        const int view = (int)(pix / per_view);
+        const unsigned r = pix - (unsigned)view * per_view;
+        const int py = (int)(r / (unsigned)P.W), px = (int)(r - (unsigned)py * (unsigned)P.W);
+        const int it = P.iteration + (P.iter_dev ? __ldg(P.iter_dev) : 0);
+        if (P.g_std > 0.0f) adj_ray<DT, TAU, SKIP, true, 1>(P, a.cams, view, px, py, it, part, T0, &tab);
+        else adj_ray<DT, TAU, SKIP, false, 1>(P, a.cams, view, px, py, it, part, T0, &tab);
+    }
+    __syncwarp();
+    for (int j = threadIdx.x; j < kTab; j += 32) {
+        const int k = tab.key[j];
+        if (k >= 0) red_add_v4(P.dV + 4 * (size_t)k, tab.v[j][0], tab.v[j][1], tab.v[j][2], 0.0f);
+    }
 }
 
 // Batched form, one warp per CTA like adj_list: CTA b covers list entries
@@ -1164,13 +1260,118 @@ cudaError_t launch_adjust_list(const SingleArgs& a, int dt, int ntiles, const un
 #endif
     dim3 grid((unsigned)ntiles * (kTileThreads / FR_ADJ_THREADS) * parts), block(FR_ADJ_THREADS);
     const bool skip = a.p.adj_occ != nullptr && !tau;
+#if FR_ADJ_ACCUM == 1
+    FR_DISPATCH_DT(dt, D, {
+        if (tau) adj_list_tab<D, true, false><<<grid, block, 0, s>>>(a, list, count, tm);
+        else if (skip) adj_list_tab<D, false, true><<<grid, block, 0, s>>>(a, list, count, tm);
+        else adj_list_tab<D, false, false><<<grid, block, 0, s>>>(a, list, count, tm);
+    });
+#else
     FR_DISPATCH_DT(dt, D, {
         if (tau) adj_list<D, true, false><<<grid, block, 0, s>>>(a, list, count, tm);
         else if (skip) adj_list<D, false, true><<<grid, block, 0, s>>>(a, list, count, tm);
         else adj_list<D, false, false><<<grid, block, 0, s>>>(a, list, count, tm);
     });
+#endif
     return cudaGetLastError();
 }
+
+#ifdef FR_ADJ_GATHER_PROBE
+// Measurement of the gather form of the adjustment (one thread per key point
+// summing over the rays that sample its eight cells), built only with
+// -DFR_ADJ_GATHER_PROBE.  A gather evaluates the same (sample, key point)
+// pairs as the scatter, but before any of them it must find, per key point
+// and view, the flame pixels whose rays can cross the box of its eight cells
+// and each such ray's samples inside that box.  gather_probe_kernel does that
+// set-up work alone -- the box's projection, the residual test of every pixel
+// in its rectangle, the ray and its clip to the box -- and none of the
+// per-sample work (positions, cells, distance weights, the transmittance a
+// gather would have to read from a store the forward march wrote): its time is
+// a lower bound on any gather's.  Its output (a sample count weighted by the
+// red residual per key point) is discarded.
+__global__ void __launch_bounds__(256) hull_nodes_kernel(const unsigned* __restrict__ tags, long long nodes,
+                                                         unsigned full, unsigned* __restrict__ list,
+                                                         unsigned* __restrict__ count)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const bool in = i < nodes && __ldg(tags + i) == full;
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if (lane == 0 && m) base = atomicAdd(count, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (in) list[base + __popc(m & ((1u << lane) - 1u))] = (unsigned)i;
+}
+
+__global__ void __launch_bounds__(128) gather_probe_kernel(const __grid_constant__ SingleArgs a,
+                                                           const unsigned* __restrict__ list,
+                                                           const unsigned* __restrict__ count,
+                                                           float* __restrict__ sink)
+{
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= __ldg(count)) return;
+    const ProbDev& P = a.p;
+    const unsigned node = __ldg(list + t);
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const int i = (int)(node % (unsigned)nx), j = (int)((node / (unsigned)nx) % (unsigned)ny),
+              k = (int)(node / ((unsigned)nx * (unsigned)ny));
+    const float lo[3] = {(float)max(i - 1, 0), (float)max(j - 1, 0), (float)max(k - 1, 0)};
+    const float hi[3] = {(float)min(i + 1, nx - 1), (float)min(j + 1, ny - 1), (float)min(k + 1, nz - 1)};
+    float sum = 0.0f;
+    for (int v = 0; v < P.ncam; ++v) {
+        const CamDev& c = a.cams[v];
+        float umin = INFINITY, umax = -INFINITY, wmin = INFINITY, wmax = -INFINITY;
+        bool behind = false;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const float X = ((b & 1) ? hi[0] : lo[0]) - c.o[0], Y = ((b & 2) ? hi[1] : lo[1]) - c.o[1],
+                        Z = ((b & 4) ? hi[2] : lo[2]) - c.o[2];
+            const float xc = X * c.r[0] + Y * c.r[1] + Z * c.r[2], yc = X * c.u[0] + Y * c.u[1] + Z * c.u[2];
+            const float zc = X * c.f[0] + Y * c.f[1] + Z * c.f[2];
+            behind |= !(zc > 0.0f);
+            const float u = (xc / zc / c.tx + 1.0f) * 0.5f * (float)c.W - 0.5f;
+            const float w = (1.0f - yc / zc / c.ty) * 0.5f * (float)c.H - 0.5f;
+            umin = fminf(umin, u); umax = fmaxf(umax, u); wmin = fminf(wmin, w); wmax = fmaxf(wmax, w);
+        }
+        if (behind) continue;
+        const int x0 = max((int)ceilf(umin), 0), x1 = min((int)floorf(umax), c.W - 1);
+        const int y0 = max((int)ceilf(wmin), 0), y1 = min((int)floorf(wmax), c.H - 1);
+        for (int py = y0; py <= y1; ++py)
+            for (int px = x0; px <= x1; ++px) {
+                const long long pix = ((long long)v * c.H + py) * c.W + px;
+                const float r0 = __ldg(P.img_in + 3 * pix), r1 = __ldg(P.img_in + 3 * pix + 1),
+                            r2 = __ldg(P.img_in + 3 * pix + 2);
+                if (r0 == 0.0f && r1 == 0.0f && r2 == 0.0f) continue;
+                Ray R;
+                if (!make_ray(c, px, py, nx, ny, nz, P.step, R)) continue;
+                const float o[3] = {R.p0x, R.p0y, R.p0z}, id[3] = {R.idx, R.idy, R.idz}, d[3] = {R.dx, R.dy, R.dz};
+                float tin = 0.0f, tout = R.chord;
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) {
+                    if (d[ax] == 0.0f) continue;
+                    const float t0 = (lo[ax] - o[ax]) * id[ax], t1 = (hi[ax] - o[ax]) * id[ax];
+                    tin = fmaxf(tin, fminf(t0, t1));
+                    tout = fminf(tout, fmaxf(t0, t1));
+                }
+                if (tout < tin) continue;
+                const int ka = max(0, (int)ceilf(tin / P.step - 0.5f) - 1);
+                const int kb = min(R.n - 1, (int)floorf(tout / P.step) + 1);
+                sum += (float)(kb - ka + 1) * r0;
+            }
+    }
+    sink[node] = sum;
+}
+
+cudaError_t launch_gather_probe(const SingleArgs& a, const unsigned* tags, unsigned full, long long nodes,
+                                unsigned* list, unsigned* count, float* sink, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    hull_nodes_kernel<<<(unsigned)((nodes + 255) / 256), 256, 0, s>>>(tags, nodes, full, list, count);
+    gather_probe_kernel<<<(unsigned)((nodes + 127) / 128), 128, 0, s>>>(a, list, count, sink);
+    return cudaGetLastError();
+}
+#endif
 
 // The check word of this translation unit (0 in the normal build).
 cudaError_t check_word_march(unsigned* word, bool reset)

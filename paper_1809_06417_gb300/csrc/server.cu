@@ -60,14 +60,10 @@ struct JobLayout {
     size_t vol, targets, bbox, residual, dV, partials, sqerr, fbuf, flist, tpart, pairs, tags, occ, hull_bricks, total;
 };
 
-// Parts each flame ray is adjusted in (as in fr_reconstruct): the list
-// entries carry the part in their top two bits, so jobs stay below 2^30 - 1
-// pixels (fr_server_submit refuses larger ones).
-#if FR_ADJ_SPLIT > 1
-constexpr int kServerParts = FR_ADJ_SPLIT;
-#else
-constexpr int kServerParts = 1;
-#endif
+// Parts each flame ray is adjusted in (FR_BATCH_PARTS, whole rays by
+// default); with parts the list entries carry the part in their top two bits,
+// so jobs stay below 2^30 - 1 pixels (fr_server_submit refuses larger ones).
+constexpr int kServerParts = FR_BATCH_PARTS;
 
 bool server_hull(const fr_server* s) { return s->p.use_hull != 0; }
 bool server_skip(const fr_server* s) { return s->p.skip_empty && !(s->p.tau > 0.0f); }
