@@ -141,6 +141,40 @@ __device__ __forceinline__ void load8_pairs(const void* pairs, long long base, i
     Rec::pair(pairs, base + nxy + nx, v[6], v[7]);
 }
 
+// Staged forward gathers (FR_FWD_STAGE = 1, a comparison variant of the
+// FP32 x-pair path): the next sample's cell records are copied asynchronously
+// (cp.async) into the thread's own shared-memory slot one sample ahead, so the
+// global load latency overlaps the current sample's arithmetic without a
+// second set of records in registers.
+#ifndef FR_FWD_STAGE
+#define FR_FWD_STAGE 0
+#endif
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" :: "r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// The four x-pair records of the cell at `base` into this thread's slot
+// (stage[q][thread], q = 2 pair + half), as one cp.async group.
+__device__ __forceinline__ void stage_cell(const void* pairs, long long base, int nx, long long nxy,
+                                           float4 (*stage)[kTileThreads])
+{
+    const float* p = reinterpret_cast<const float*>(pairs);
+    const long long idx[4] = {base, base + nx, base + nxy, base + nxy + nx};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        cp_async16(&stage[2 * q][threadIdx.x], p + 8 * idx[q]);
+        cp_async16(&stage[2 * q + 1][threadIdx.x], p + 8 * idx[q] + 4);
+    }
+    cp_async_commit();
+}
+
 // Skipping of flagged-off bricks along one ray.  A brick is the box of kBrick^3
 // cells [B b, min(B b + B, n - 1)] per axis (B = kBrick); `flags` holds one byte per brick
 // (non-zero: the samples in it are evaluated).
@@ -255,6 +289,9 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
 #pragma unroll
             for (int q = 0; q < 8; ++q) v[q] = RT{};
             long long vbase = -1;
+#if FR_FWD_STAGE
+            long long staged = -1;   // the cell whose records are in flight to (or in) the thread's slot
+#endif
             float T = 1.0f;
             BrickSkip skip;
             int k0 = 0, k1 = R.n;
@@ -272,6 +309,33 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
                 }
                 const Cell c = cell_of(x, y, z, P.nx, P.ny, P.nz);
                 if constexpr (PAIRS && KIND == KIND_RGB && DT == DT_F32) {
+#if FR_FWD_STAGE
+                    __shared__ float4 stage[8][kTileThreads];
+                    const long long lim = nxy * P.nz - nxy - P.nx - 1;   // largest cell base
+                    (void)lim;
+                    if (c.base != vbase) {
+                        // the staged cell, or (after a skip) this one, staged now
+                        if (staged != c.base) {
+                            cp_async_wait_all();
+                            stage_cell(P.pairs, FR_CHK(c.base, lim, 1u), P.nx, nxy, stage);
+                        }
+                        cp_async_wait_all();
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) v[q] = stage[q][threadIdx.x];
+                        staged = -1;
+                        vbase = c.base;
+                    }
+                    // the next sample's cell, one sample ahead
+                    if (k + 1 < k1 && staged < 0) {
+                        float l2, x2, y2, z2;
+                        segment(R, P.step, k + 1, l2, x2, y2, z2);
+                        const long long nb = cell_of(x2, y2, z2, P.nx, P.ny, P.nz).base;
+                        if (nb != vbase) {
+                            stage_cell(P.pairs, FR_CHK(nb, lim, 1u), P.nx, nxy, stage);
+                            staged = nb;
+                        }
+                    }
+#else
                     // The four pair loads predicated on a cell change rather
                     // than branched on it: the lanes, which enter cells at
                     // different samples, stay converged (2.4% faster).
@@ -282,6 +346,7 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
                     const long long idx[4] = {b, b + P.nx, b + nxy, b + nxy + P.nx};
 #pragma unroll
                     for (int q = 0; q < 4; ++q) load_rgb_pair_f32_if(P.pairs, idx[q], need, v[2 * q], v[2 * q + 1]);
+#endif
                 } else
                 if (c.base != vbase) {
                     vbase = c.base;
@@ -309,6 +374,10 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
                     for (int j = 0; j < kTm; ++j) Tm[j] = k < kb[j] ? T : Tm[j];
                 }
             }
+#if FR_FWD_STAGE
+            // a copy for a cell the ray did not reach lands before the thread moves on
+            cp_async_wait_all();
+#endif
         }
     }
     // pixel epilogue: image, residual of the colour constraint, error sums

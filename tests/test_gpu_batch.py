@@ -99,3 +99,53 @@ def test_batch_follows_oracle(orc, use_hull):
         assert e.max() < 1e-3
         np.testing.assert_allclose(rm.cpu().numpy(), rmse_ref, rtol=1e-3)
     ctx.close()
+
+
+def test_video_size_batch_follows_oracle(orc):
+    """Two frames of the video setting at full size (96^3, 8 views of 384^2,
+    the plume advected between them), each in its own hull (the oracle's tags),
+    two batched iterations captured in a CUDA graph, against orc.reconstruct
+    frame by frame; node by node within 1e-4 of the frame's maximum plus the
+    oracle's undecided budget."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    from gpu_cases import Case, oracle_targets, tags_on_device
+    from paper_1809_06417_gb300 import flamerec as fr, synth
+    orc.set_threads(os.cpu_count() or 1)
+    ctx = fr.Context(0)
+    n, views, side, step, iters = 96, 8, 384, 0.5, 2
+    shape, origin, h = synth.unit_grid(n)
+    cams = synth.ring_cameras(views, side, side, elevation_jitter_deg=10.0, seed=4)
+    frames = synth.video_frames(8, n, 4)[3:5]
+    alpha = 2e-4 * (n / 128.0) * (512.0 / side) ** 2
+    P = orc.make_params(step=step, alpha_l=alpha)
+    p = fr.params(step=step, alpha_l=alpha, use_hull=1)
+    refs, batch, keep = [], [], []
+    for gt in frames:
+        case = Case(shape, cams, gt, step)
+        sc, img, t_ref, mask, bbox_ref = oracle_targets(orc, case)
+        tags = orc.visual_hull(sc, mask)
+        v0 = gt.copy()
+        v0[..., :3] = 0.0
+        refs.append(orc.reconstruct(sc, v0, P, t_ref, mask, bbox_ref, iters, hull=tags, with_undecided=True))
+        v = torch.as_tensor(v0, dtype=torch.float32, device="cuda").contiguous()
+        t_dev = torch.as_tensor(img, dtype=torch.float32, device="cuda").contiguous()
+        bbox = torch.zeros((views, 4), dtype=torch.int32, device="cuda")
+        ctx.fr_prepare_targets(t_dev, 30 / 255, bbox)
+        rm = torch.zeros((iters, 3), device="cuda")
+        tg = tags_on_device(torch, tags)
+        keep.append((v, rm, t_dev, bbox, tg))
+        batch.append((fr.volume(v, origin, h), fr.cameras(cams), t_dev, bbox, rm, tg))
+    ctx.fr_reconstruct_batch(batch, iters, p, use_graph=True)
+    torch.cuda.synchronize()
+    for (vol_ref, rmse_ref, _, und), (v, rm, *_) in zip(refs, keep):
+        got = v.cpu().numpy().astype(np.float64)
+        scale = np.abs(vol_ref[..., :3]).max()
+        err = np.abs(got[..., :3] - vol_ref[..., :3]).max(axis=-1)
+        bound = 1e-4 * scale + und
+        print(f"video frame vs oracle: max error / max {err.max() / scale:.2e}, worst error / bound "
+              f"{np.max(err / bound):.3f}, rmse {rm.cpu().numpy()[-1]} vs {rmse_ref[-1]}")
+        assert np.all(err <= bound)
+        np.testing.assert_allclose(rm.cpu().numpy(), rmse_ref, rtol=1e-3)
+    ctx.close()

@@ -144,3 +144,32 @@ def test_full_size_reconstruct_iterations_follow_oracle(orc, full):
     outside = full["tags"] != (1 << VIEWS) - 1
     assert np.all(got[outside] == 0.0)
     assert np.array_equal(got[..., 3], v0[..., 3].astype(np.float32))
+
+
+def test_full_size_bf16_records_follow_the_16bit_oracle(orc, full):
+    """The benchmarked workload with BF16 records (FP32 arithmetic): two
+    iterations against the oracle keeping BF16 records, at the storage
+    tolerance of 1e-2 of the volume's maximum; the error against the FP64
+    loop with double-precision records is printed beside it."""
+    fr, ctx, sc, P = full["fr"], full["ctx"], full["sc"], full["P"]
+    v0 = orc.round_storage(_start(full), "bf16")
+    iters = 2
+    P16 = orc.make_params(step=STEP, alpha_l=ALPHA_L, storage="bf16")
+    ref16, r16, _ = orc.reconstruct(sc, v0, P16, full["t_ref"], full["mask"], full["bbox_ref"], iters,
+                                    albedo=full["alb"], hull=full["tags"])
+    ref64, _, _ = orc.reconstruct(sc, v0, P, full["t_ref"], full["mask"], full["bbox_ref"], iters,
+                                  albedo=full["alb"], hull=full["tags"])
+    v = torch.as_tensor(v0, dtype=torch.float32, device="cuda").to(torch.bfloat16).contiguous()
+    alb = torch.as_tensor(full["alb"], dtype=torch.float32, device="cuda").contiguous()
+    p = fr.params(step=STEP, alpha_l=ALPHA_L, use_hull=1, hull_tags=tags_on_device(torch, full["tags"]))
+    rmse = np.zeros((iters, 3), dtype=np.float32)
+    ctx.fr_reconstruct(fr.volume(v, full["origin"], full["h"]), fr.cameras(full["cams"]), full["t_dev"],
+                       full["bbox"], iters, p, albedo=alb, rmse=rmse)
+    torch.cuda.synchronize()
+    got = v.float().cpu().numpy().astype(np.float64)
+    e16 = rel_err(got[..., :3], ref16[..., :3])
+    e64 = rel_err(got[..., :3], ref64[..., :3])
+    print(f"full-size BF16: volume vs BF16 oracle max {e16.max():.2e} (p99.99 {np.quantile(e16, 0.9999):.2e}); "
+          f"vs FP64 records {e64.max():.2e}; rmse gpu {rmse[-1]} oracle {r16[-1]}")
+    assert e16.max() < 1e-2
+    np.testing.assert_allclose(rmse, r16, rtol=1e-2)
