@@ -16,6 +16,10 @@
  *    its own scratch, which it owns and frees in fr_destroy.
  *  - Ordering: all device work is queued on the context's stream, in call
  *    order.  Calls do not synchronise the host except where stated.
+ *    fr_reconstruct runs the adjustments of an iteration's views on a second
+ *    stream the context owns, ordered after the call's earlier work on the
+ *    context's stream and before its later work (events), so to the caller
+ *    the call behaves as if all of it were queued on the context's stream.
  *  - Geometry: the volume is a node-centred grid.  Node (i, j, k) is a key
  *    point (a voxel vertex, Sec. 3.3 definitions) at world position
  *    origin + h (i, j, k); records are stored x fastest: index

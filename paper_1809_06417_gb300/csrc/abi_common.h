@@ -28,6 +28,12 @@ struct Buf {
 
 constexpr size_t kHostScratchBytes = 64;
 
+// Forward and adjustment of an iteration pipelined view by view over two
+// streams (fr_reconstruct); 0 launches each over all views at once.
+#ifndef FR_PIPELINE_VIEWS
+#define FR_PIPELINE_VIEWS 1
+#endif
+
 struct fr_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;   // where work is queued (borrowed; 0 = default stream)
@@ -55,6 +61,8 @@ struct fr_ctx {
     size_t staging_bytes = 0;
     cudaEvent_t staging_done = nullptr;
     cudaStream_t capture = nullptr;  // stream used to capture CUDA graphs
+    cudaStream_t aux = nullptr;      // second stream of the pipelined views (adjustments)
+    cudaEvent_t pipe_ev[kMaxViews + 1] = {};  // per-view forward done; [kMaxViews]: adjustments done
     // device scratch held in Bufs, and the most the context may hold
     size_t scratch_bytes = 0;
     size_t scratch_limit = SIZE_MAX;

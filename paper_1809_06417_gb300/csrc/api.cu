@@ -62,6 +62,7 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     if (!c) return FR_EINVAL;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->aux) cudaStreamSynchronize(c->aux);   // (adjustments of pipelined views)
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
                    &c->rmse, &c->J, &c->src, &c->flame_cnt, &c->flame_list, &c->batch, &c->pairs,
                    &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr, &c->L6, &c->fin, &c->flame_tm,
@@ -72,6 +73,9 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     if (c->staging) cudaFreeHost(c->staging);
     if (c->staging_done) cudaEventDestroy(c->staging_done);
     if (c->capture) cudaStreamDestroy(c->capture);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    for (cudaEvent_t e : c->pipe_ev)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : c->trace_pool) cudaEventDestroy(e);
     delete c;
     return FR_OK;
@@ -127,6 +131,7 @@ extern "C" fr_status fr_synchronize(fr_ctx* c)
 {
     if (!c) return FR_EINVAL;
     FR_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->aux) FR_CUDA(c, cudaStreamSynchronize(c->aux));
     return FR_OK;
 }
 
@@ -843,7 +848,16 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     }
     const long long npix = (long long)ncam * cams[0].width * cams[0].height;
     if (npix >= (1LL << 32)) return fail(c, FR_EINVAL, "at most 2^32 pixels per reconstruction");
-    const int count_slots = per_view ? ncam : 1;   // flame-ray counts per iteration
+    // Views pipelined (FR_PIPELINE_VIEWS): the forward march of each view on
+    // the context's stream, the adjustment of its flame rays on a second
+    // stream as soon as that view's forward is done, so that the forward
+    // (latency-bound) and the adjustment (issue-bound) of different views share
+    // the SMs.  The adjustment of a view depends on that view's forward alone;
+    // the update waits for all of them.  Not with phase tracing (whose events
+    // time the kernels one after another) nor inside the stop-criterion graph.
+    const bool pipe = FR_PIPELINE_VIEWS && !until && !c->trace_on && !per_view && ncam > 1 &&
+                      p->rule == FR_RULE_PAPER;
+    const int count_slots = per_view || pipe ? ncam : 1;   // flame-ray counts per iteration
     FR_TRY(ensure(c, c->flame_cnt, (size_t)iters * count_slots * sizeof(unsigned), "flame counts"));
     const bool hg = per_view && p->hg_g != 0.0f && albedo;
     if (hg) FR_TRY(ensure(c, c->L6, (size_t)nodes * 6 * 16, "directional radiances"));
@@ -875,6 +889,11 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
         FR_TRY(ensure(c, c->hull_bricks, brick_table_bytes(vol->nx, vol->ny, vol->nz), "hull bricks"));
     }
     cudaStream_t s = c->stream;
+    if (pipe) {
+        if (!c->aux) FR_CUDA(c, cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+        for (int v = 0; v <= kMaxViews; ++v)
+            if (!c->pipe_ev[v]) FR_CUDA(c, cudaEventCreateWithFlags(&c->pipe_ev[v], cudaEventDisableTiming));
+    }
     const float* tg = targets;
     if (targets_are_host) {
         FR_CUDA(c, cudaMemcpyAsync(c->targets.p, targets, ib, cudaMemcpyHostToDevice, s));
@@ -1050,6 +1069,28 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
         }
         return FR_OK;
     };
+    // The forward and adjustment of an iteration view by view, the
+    // adjustments on the second stream (see `pipe`); each view's flame rays in
+    // their own region of the list, counted at their own slot.
+    const size_t view_region = (size_t)nt1 * kTileThreads * parts;
+    auto pipelined_views = [&](cudaStream_t st, int slot) -> fr_status {
+        for (int v = 0; v < ncam; ++v) {
+            view_problem(v, slot);
+            fv.p.flist = flame_list + v * view_region;
+            fv.p.flist_tm = split ? static_cast<float*>(c->flame_tm.p) + v * view_region : nullptr;
+            FR_CUDA(c, launch_fwd(fv, vol->dtype, vol->kind, nt1, st));
+            FR_CUDA(c, launch_finalize(fv.p.partials, nt1, sq + 4 * slot, st, v > 0, fin,
+                                       v == ncam - 1 ? rmse_dev + 3 * slot : nullptr));
+            FR_CUDA(c, cudaEventRecord(c->pipe_ev[v], st));
+            FR_CUDA(c, cudaStreamWaitEvent(c->aux, c->pipe_ev[v], 0));
+            uv.p.iteration = first_iteration + slot;
+            FR_CUDA(c, launch_adjust_list(uv, vol->dtype, nt1, fv.p.flist, fv.p.flist_count, c->aux,
+                                          fv.p.flist_tm));
+        }
+        FR_CUDA(c, cudaEventRecord(c->pipe_ev[kMaxViews], c->aux));
+        FR_CUDA(c, cudaStreamWaitEvent(st, c->pipe_ev[kMaxViews], 0));
+        return FR_OK;
+    };
     auto one_iteration = [&](cudaStream_t st, int it) -> fr_status {
         if (per_view) return per_view_iteration(st, it);
         const int slot = it < 0 ? 0 : it;
@@ -1061,6 +1102,12 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
         FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, occ,
                                     st, pack_keep));
         FR_TRY(trace_mark(c, FR_PHASE_PACK));
+        if (pipe) {
+            FR_TRY(pipelined_views(st, slot));
+            FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg, 1,
+                                    st, hull, full));
+            return FR_OK;
+        }
         f.p.flist_count = f.p.flist ? flame_cnt + slot : nullptr;
         FR_CUDA(c, launch_fwd(f, vol->dtype, vol->kind, nt, st));
         FR_TRY(trace_mark(c, FR_PHASE_FORWARD));
