@@ -1108,6 +1108,31 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
                                     st, hull, full));
             return FR_OK;
         }
+#if FR_FUSED
+        if (p->rule == FR_RULE_PAPER && f.p.pairs && occ && !(p->tau > 0.0f) && vol->kind == FR_KIND_RGB) {
+            // (comparison build: the forward and the adjustment in one kernel)
+            static thread_local SingleArgs fu;
+            fu = f;
+            fu.p.flist = nullptr;
+            fu.p.flist_tm = nullptr;
+            fu.p.flist_count = nullptr;
+            fu.p.residual = nullptr;
+            fu.p.dV = u.p.dV;
+            fu.p.adj_occ = u.p.adj_occ;
+            fu.p.adj_box = u.p.adj_box;
+            fu.p.iteration = first_iteration + slot;
+            fu.p.iter_dev = u.p.iter_dev;
+            FR_CUDA(c, launch_fused(fu, vol->dtype, nt, st));
+            FR_TRY(trace_mark(c, FR_PHASE_FORWARD));
+            FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * slot, st, 0, fin,
+                                       it < 0 ? nullptr : rmse_dev + 3 * slot));
+            FR_TRY(trace_mark(c, FR_PHASE_REDUCE));
+            FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg, 1,
+                                    st, hull, full));
+            FR_TRY(trace_mark(c, FR_PHASE_APPLY));
+            return FR_OK;
+        }
+#endif
         f.p.flist_count = f.p.flist ? flame_cnt + slot : nullptr;
         FR_CUDA(c, launch_fwd(f, vol->dtype, vol->kind, nt, st));
         FR_TRY(trace_mark(c, FR_PHASE_FORWARD));

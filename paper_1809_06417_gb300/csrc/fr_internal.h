@@ -23,6 +23,16 @@ inline int tiles_of(int W, int H, int ncam)
 
 // march.cu
 cudaError_t launch_fwd(const SingleArgs& a, int dt, int kind, int ntiles, cudaStream_t s);
+#ifndef FR_FUSED
+#define FR_FUSED 0
+#endif
+#if FR_FUSED
+// forward march and paper-rule adjustment of each tile in one kernel (RGB
+// x-pair records with brick skipping; a.p carries the forward's and the
+// adjustment's fields, no residual image and no flame list; the comparison
+// variant of march.cu's fwd_single + adj_list)
+cudaError_t launch_fused(const SingleArgs& a, int dt, int ntiles, cudaStream_t s);
+#endif
 // Loads the kernels the allocation-free render launches (the forward march
 // gathering records one by one, every storage type, kind and opacity mode,
 // and the one-CTA error reduction) on the current device, so that their first

@@ -266,8 +266,16 @@ struct BrickSkip {
 // transmittance unchanged, so skipping it does not change the result).
 // SPLIT: track the transmittance at the ray's part boundaries for a flame list
 // of ray parts (the single-problem forward; the batched one lists no rays).
+// One ray's results that a fused adjustment needs (fused_single).
+struct FwdOut {
+    bool flame;
+    unsigned pix;
+    float dl[3];   // residual of the colour constraint
+    float tm;      // transmittance at the start of the ray's second part
+};
+
 template <int DT, int KIND, bool TAU, int MODE, bool SPLIT = false>
-__device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, int tile)
+__device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, int tile, FwdOut* out = nullptr)
 {
     constexpr bool PAIRS = MODE >= 1;
     constexpr bool SKIP = MODE == 2 && KIND == KIND_RGB && !TAU;
@@ -382,6 +390,7 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
     }
     // pixel epilogue: image, residual of the colour constraint, error sums
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, cnt = 0.0f;
+    float fl0 = 0.0f, fl1 = 0.0f, fl2 = 0.0f;   // the residual (kept for a fused adjustment)
     const long long pix = valid ? FR_CHK(((long long)view * P.H + py) * P.W + px, (long long)P.ncam * P.H * P.W, 4u)
                                 : 0;
     bool flame = false;
@@ -395,10 +404,13 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
             const float t0 = t[0], t1 = t[1], t2 = t[2];
             const float d0 = t0 - L0, d1 = t1 - L1, d2 = t2 - L2;
             flame = fmaxf(t0, fmaxf(t1, t2)) > P.thresh;
-            float* r = P.residual + 3 * pix;
-            r[0] = flame ? d0 : 0.0f;
-            r[1] = flame ? d1 : 0.0f;
-            r[2] = flame ? d2 : 0.0f;
+            if (P.residual) {
+                float* r = P.residual + 3 * pix;
+                r[0] = flame ? d0 : 0.0f;
+                r[1] = flame ? d1 : 0.0f;
+                r[2] = flame ? d2 : 0.0f;
+            }
+            fl0 = d0; fl1 = d1; fl2 = d2;
             const int* bb = P.bbox + 4 * view;
             if (px >= bb[0] && px <= bb[2] && py >= bb[1] && py <= bb[3]) {
                 a0 = d0 * d0; a1 = d1 * d1; a2 = d2 * d2; cnt = 1.0f;
@@ -468,6 +480,12 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
             for (int i = 0; i < kTileThreads / 32; ++i) s += red[threadIdx.x][i];
             P.partials[4 * (long long)tile + threadIdx.x] = s;
         }
+    }
+    if (out) {
+        out->flame = flame;
+        out->pix = (unsigned)pix;
+        out->dl[0] = fl0; out->dl[1] = fl1; out->dl[2] = fl2;
+        out->tm = Tm[0];
     }
 }
 
@@ -552,15 +570,18 @@ __device__ __forceinline__ void tab_add(KeyTable& T, unsigned node, float a, flo
 
 template <int DT, bool TAU, bool SKIP, bool RG, int ACC = 0>
 __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, int view, int px, int py,
-                                        int iteration, int part = -1, float T0 = 1.0f, KeyTable* tab = nullptr)
+                                        int iteration, int part = -1, float T0 = 1.0f, KeyTable* tab = nullptr,
+                                        const float* dl_in = nullptr)
 {
     // SKIP: samples in bricks with no key point inside the visual hull are
     // skipped.  Their records are zero (no extinction: T is unchanged) and
     // their key points' updates are discarded after the update, so the
-    // result is the same.
+    // result is the same.  dl_in (nullable): the ray's residual, else read
+    // from P.img_in.
     const long long pix = ((long long)view * P.H + py) * P.W + px;
-    const float* g = P.img_in + 3 * pix;
-    const float dl0 = g[0] * P.img_scale, dl1 = g[1] * P.img_scale, dl2 = g[2] * P.img_scale;
+    const float* g = dl_in ? dl_in : P.img_in + 3 * pix;
+    const float sc = dl_in ? 1.0f : P.img_scale;
+    const float dl0 = g[0] * sc, dl1 = g[1] * sc, dl2 = g[2] * sc;
     if (dl0 == 0.0f && dl1 == 0.0f && dl2 == 0.0f) return;
     Ray R;
     if (!make_ray(cams[view], px, py, P.nx, P.ny, P.nz, P.step, R)) return;
@@ -697,6 +718,67 @@ __global__ void FR_ADJ_LIST_BOUNDS adj_list(const __grid_constant__ SingleArgs a
     if (P.g_std > 0.0f) adj_ray<DT, TAU, SKIP, true>(P, a.cams, view, px, py, it, part, T0);
     else adj_ray<DT, TAU, SKIP, false>(P, a.cams, view, px, py, it, part, T0);
 }
+
+// Forward march and paper-rule adjustment of one tile in one kernel
+// (FR_FUSED = 1, a comparison variant of the loop's fwd_single + adj_list):
+// the tile's rays march forward (fwd_body: image sums, error partials), its
+// flame pixels' index, residual and transmittance at the ray's middle sample
+// go to shared memory instead of a flame-ray list in global memory, and the
+// CTA's warps then adjust those rays in FR_ADJ_SPLIT parts while the records
+// they gathered are still in the SM's L1.  No residual image is written.
+#ifndef FR_FUSED
+#define FR_FUSED 0
+#endif
+#ifndef FR_FUSED_MINB
+#define FR_FUSED_MINB 5
+#endif
+#if FR_FUSED
+template <int DT, bool SKIP_ADJ>
+__global__ void __launch_bounds__(kTileThreads, FR_FUSED_MINB) fused_single(const __grid_constant__ SingleArgs a)
+{
+    static_assert(FR_ADJ_SPLIT <= 2, "the fused form keeps one part boundary per ray");
+    FwdOut o;
+    fwd_body<DT, KIND_RGB, false, 2, true>(a.p, a.cams, blockIdx.x, &o);
+    __shared__ unsigned f_pix[kTileThreads];
+    __shared__ float f_dl[3][kTileThreads];
+    __shared__ float f_tm[kTileThreads];
+    __shared__ unsigned f_wc[kTileThreads / 32];
+    const unsigned m = __ballot_sync(0xffffffffu, o.flame);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) f_wc[w] = (unsigned)__popc(m);
+    __syncthreads();
+    unsigned at = (unsigned)__popc(m & ((1u << lane) - 1u)), F = 0;
+#pragma unroll
+    for (int i = 0; i < kTileThreads / 32; ++i) {
+        if (i < w) at += f_wc[i];
+        F += f_wc[i];
+    }
+    if (o.flame) {
+        f_pix[at] = o.pix;
+        f_dl[0][at] = o.dl[0];
+        f_dl[1][at] = o.dl[1];
+        f_dl[2][at] = o.dl[2];
+        f_tm[at] = o.tm;
+    }
+    __syncthreads();
+    const ProbDev& P = a.p;
+    const unsigned parts = (unsigned)FR_ADJ_SPLIT, items = F * parts;
+    const int it = P.iteration + (P.iter_dev ? __ldg(P.iter_dev) : 0);
+    const unsigned per_view = (unsigned)P.W * (unsigned)P.H;
+    for (unsigned item = threadIdx.x; item < items; item += kTileThreads) {
+        const unsigned part = item / F, idx = item - part * F;
+        const unsigned pix = f_pix[idx];
+        const float dl[3] = {f_dl[0][idx], f_dl[1][idx], f_dl[2][idx]};
+        const int view = (int)(pix / per_view);
+        const unsigned r = pix - (unsigned)view * per_view;
+        const int py = (int)(r / (unsigned)P.W), px = (int)(r - (unsigned)py * (unsigned)P.W);
+        const int pp = parts > 1u ? (int)part : -1;
+        const float T0 = part ? f_tm[idx] : 1.0f;
+        if (P.g_std > 0.0f) adj_ray<DT, false, SKIP_ADJ, true>(P, a.cams, view, px, py, it, pp, T0, nullptr, dl);
+        else adj_ray<DT, false, SKIP_ADJ, false>(P, a.cams, view, px, py, it, pp, T0, nullptr, dl);
+    }
+}
+#endif
 
 // adj_list with each CTA's key-point sums gathered in a shared-memory table
 // (KeyTable) and flushed with one vector reduction per key point the CTA's
@@ -1205,6 +1287,21 @@ cudaError_t preload_noalloc_kernels()
 #undef FR_PRELOAD
     return e;
 }
+
+#if FR_FUSED
+cudaError_t launch_fused(const SingleArgs& a, int dt, int ntiles, cudaStream_t s)
+{
+    // the forward's mode 2: x-pair records, brick skipping, no constant tau
+    if (a.p.pairs == nullptr || a.p.occ == nullptr || a.p.tau > 0.0f || a.p.flist || a.p.residual)
+        return cudaErrorInvalidValue;
+    dim3 grid(ntiles), block(kTileThreads);
+    FR_DISPATCH_DT(dt, D, {
+        if (a.p.adj_occ) fused_single<D, true><<<grid, block, 0, s>>>(a);
+        else fused_single<D, false><<<grid, block, 0, s>>>(a);
+    });
+    return cudaGetLastError();
+}
+#endif
 
 cudaError_t launch_fwd_batch(const ProbDev* probs, const int* tile_start, int nprob, int total_tiles,
                              int dt, int kind, bool tau, bool pairs, cudaStream_t s, bool skip)
