@@ -707,19 +707,22 @@ def run_serving(fr, ctx, jobs=500, rate=20.0, seed=5, step=0.5, warmup_s=10.0, p
 
 
 def run_temperature_views(fr, ctx, n=128, side=512, step=0.5, iters=50, seed=3, view_counts=(4, 16, 28),
-                          t_min=1000.0, t_max=2300.0, alpha_scale=1.0):
+                          t_min=1000.0, t_max=2300.0, alpha_scale=1.0, sigma=None):
     """Paper-literal temperature path (Sec. 3.3.3) against the number of cameras
     (Sec. 5.2: 4, 16 and 28 cameras, temperatures in 1000-2300 K):
     targets rendered from a seeded temperature field through the colour-
     temperature table, the green channel reconstructed with the paper rule
     inside the visual hull, the temperature read off the table; errors inside
-    the hull (Sec. 5.1), and on the key points inside every camera set's hull."""
+    the hull (Sec. 5.1), and on the key points inside every camera set's hull.
+    sigma: the constant extinction per voxel length (default the paper's
+    tau = 0.05 at a one-voxel step)."""
     import torch
     from paper_1809_06417_gb300 import synth
+    sigma = synth.SIGMA_PAPER if sigma is None else sigma
     lut = torch.zeros((1024, 4), device="cuda")
     ctx.fr_planck_lut(t_min, t_max, lut)
     pt = dict(lut=lut, lut_t_min=t_min, lut_t_max=t_max)
-    gt = synth.temperature_volume(n, seed, t_min=t_min, t_max=t_max)
+    gt = synth.temperature_volume(n, seed, t_min=t_min, t_max=t_max, sigma=sigma)
     shape, origin, h = synth.unit_grid(n)
     g = torch.as_tensor(gt, dtype=torch.float32, device="cuda").contiguous()
     out, temps, hulls = {}, {}, {}
@@ -758,7 +761,7 @@ def run_temperature_views(fr, ctx, n=128, side=512, step=0.5, iters=50, seed=3, 
         out[views]["temperature_rmse_in_all_hulls_K"] = float(
             np.sqrt(np.mean((temps[views][common] - gt[..., 0][common]) ** 2)))
     return {"workload": f"temperature_green_{n}^3_{side}^2_{iters}it", "range_K": [t_min, t_max],
-            "common_key_points": int(common.sum()),
+            "sigma_per_voxel": sigma, "common_key_points": int(common.sum()),
             "views": {str(k): v for k, v in out.items()}}
 
 
@@ -1007,11 +1010,13 @@ def main():
         cpu = cpu_baseline()  # before any GPU work: the oracle never forks after CUDA init
     out = run_ours(args, ws, rank, local)
     if rank == 0 and not args.no_extras:
-        from paper_1809_06417_gb300 import flamerec as fr
+        from paper_1809_06417_gb300 import flamerec as fr, synth
         ctx = fr.Context(local)
         out["video"] = run_video(fr, ctx, storage=args.storage)
         out["serving"] = run_serving(fr, ctx, jobs=args.serving_jobs)
         out["temperature_views"] = run_temperature_views(fr, ctx)
+        # the same at the optical depth the paper's extinction gives a 48^3 grid
+        out["temperature_views_thin"] = run_temperature_views(fr, ctx, sigma=synth.SIGMA_PAPER * 48.0 / 128.0)
         out["held_out_view"] = run_held_out(fr, ctx)
         out["differentiable"] = run_differentiable(fr, ctx)
         ctx.close()
