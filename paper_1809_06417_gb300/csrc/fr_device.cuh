@@ -498,9 +498,67 @@ __device__ __forceinline__ void load_ts_pair(const void* pairs, long long idx, f
 
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
 
+// Packed FP32 pairs: sm_100-family GPUs execute add/sub/mul/fma on two floats
+// held in a 64-bit register pair as one instruction (.f32x2), each half
+// rounded to nearest exactly as the scalar operation.  Used for the
+// trilinear blends and the adjustment's distance weights: the forward march
+// measured 6.5% faster (0.268 against 0.287 ms on the 128^3 x 8 x 512^2
+// step), the adjustment 0.5%.  FR_PACKED = 0 keeps the scalar forms.
+#ifndef FR_PACKED
+#define FR_PACKED 1
+#endif
+struct F2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ F2 f2(float lo, float hi)
+{
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 f2_get(F2 a)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
+{
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_sub(F2 a, F2 b)
+{
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b)
+{
+    F2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c)
+{
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+// lerpf on both halves with one weight t (the same two roundings per half)
+__device__ __forceinline__ F2 f2_lerp(F2 a, F2 b, F2 t) { return f2_fma(t, f2_sub(b, a), a); }
+
 __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t)
 {
+#if FR_PACKED
+    const F2 tt = f2(t, t);
+    const float2 lo = f2_get(f2_lerp(f2(a.x, a.y), f2(b.x, b.y), tt));
+    const float2 hi = f2_get(f2_lerp(f2(a.z, a.w), f2(b.z, b.w), tt));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+#else
     return make_float4(lerpf(a.x, b.x, t), lerpf(a.y, b.y, t), lerpf(a.z, b.z, t), lerpf(a.w, b.w, t));
+#endif
 }
 
 __device__ __forceinline__ float2 lerp2(float2 a, float2 b, float t)

@@ -70,9 +70,19 @@ __device__ __forceinline__ float2 slot_blend<float2>(const float2* v, float gx, 
 template <>
 __device__ __forceinline__ float slot_blend<float>(const float* v, float gx, float gy, float gz)
 {
+#if FR_PACKED
+    // the same lerps, slots t and t + 4 side by side: (a, c), (b, d), then
+    // (lerp(a, b), lerp(c, d)) and the z lerp
+    const F2 tx = f2(gx, gx), ty = f2(gy, gy);
+    const F2 ac = f2_lerp(f2(v[0], v[4]), f2(v[1], v[5]), tx);
+    const F2 bd = f2_lerp(f2(v[2], v[6]), f2(v[3], v[7]), tx);
+    const float2 e = f2_get(f2_lerp(ac, bd, ty));
+    return lerpf(e.x, e.y, gz);
+#else
     float a = lerpf(v[0], v[1], gx), b = lerpf(v[2], v[3], gx);
     float c = lerpf(v[4], v[5], gx), d = lerpf(v[6], v[7], gx);
     return lerpf(lerpf(a, b, gy), lerpf(c, d, gy), gz);
+#endif
 }
 
 template <int DT, int KIND>
@@ -659,8 +669,24 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
         const float ey[2] = {gy * gy, (1.0f - gy) * (1.0f - gy)};
         const float ez[2] = {gz * gz, (1.0f - gz) * (1.0f - gz)};
         const float exy[4] = {ex[0] + ey[0], ex[1] + ey[0], ex[0] + ey[1], ex[1] + ey[1]};
+#if FR_PACKED
+        // slots t and t + 4 side by side (the same operations per slot)
+        const F2 ezz = f2(ez[0], ez[1]), bb = f2(base, base), cc = f2(dcoef, dcoef);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float2 d = f2_get(f2_add(f2(exy[t], exy[t]), ezz));
+            float r0, r1;
+            asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(d.x));
+            asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(d.y));
+            const float2 e = f2_get(f2_mul(cc, f2(r0, r1)));
+            const float2 a2 = f2_get(f2_fma(bb, f2(ex2_approx(e.x), ex2_approx(e.y)), f2(acc[t], acc[t + 4])));
+            acc[t] = a2.x;
+            acc[t + 4] = a2.y;
+        }
+#else
 #pragma unroll
         for (int t = 0; t < 8; ++t) acc[t] = fmaf(base, dist_weight(dcoef, exy[t & 3] + ez[t >> 2]), acc[t]);
+#endif
         if constexpr (TAU) T *= 1.0f - P.tau;
         else T *= __expf(-slot_blend<float>(sg, gx, gy, gz) * len);
     }
