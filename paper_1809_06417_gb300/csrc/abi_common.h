@@ -32,6 +32,9 @@ constexpr size_t kHostScratchBytes = 64;
 // streams (fr_reconstruct) when 1; 0 (the default) launches each once over all
 // views (the pipelined form measured 1.19 ms against 0.714 ms per iteration of
 // the full-RTE workload).
+#ifndef FR_NODE_BOX
+#define FR_NODE_BOX 1
+#endif
 #ifndef FR_PIPELINE_VIEWS
 #define FR_PIPELINE_VIEWS 0
 #endif

@@ -967,6 +967,10 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     // box of the non-zero bricks is not recomputed every iteration.
     const unsigned char* pack_keep = occ ? u.p.adj_occ : nullptr;
     if (pack_keep) f.p.occ_box = u.p.adj_box;
+    // The same box bounds the in-scattering sweeps and the update: every record
+    // outside it is zero (the hull clear) and no adjustment reaches it
+    // (FR_NODE_BOX = 0: the whole grid).
+    const NodeBox nbox = FR_NODE_BOX && pack_keep ? NodeBox{u.p.adj_box, nbx, nby, nbz} : NodeBox{};
     void* fin = nullptr;
     FR_TRY(fin_scratch(c, &fin));
     float* rmse_dev = static_cast<float*>(c->rmse.p);
@@ -1033,13 +1037,13 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
                 } else if (v == 0 || seq) {
                     FR_CUDA(c, launch_scatter_source(vol->data, vol->dtype, albedo, static_cast<float*>(c->J.p),
                                                      c->src.p, vol->dtype, vol->nx, vol->ny, vol->nz, st,
-                                                     p->skip_empty != 0));
+                                                     p->skip_empty != 0, nbox));
                 }
                 FR_TRY(trace_mark(c, FR_PHASE_SCATTER));
             }
             if (v == 0 || seq || hg) {
                 FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz,
-                                            occ, st, pack_keep));
+                                            occ, st, pack_keep, nbox));
                 FR_TRY(trace_mark(c, FR_PHASE_PACK));
             }
             view_problem(v, slot);
@@ -1059,8 +1063,8 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
             if (seq || v == ncam - 1) {
                 // the update, with the hull clear fused in
                 if (p->rule == FR_RULE_PAPER)
-                    FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg,
-                                            1, st, hull, full));
+                    FR_CUDA(c, launch_apply_box(vol->data, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, u.p.dV,
+                                                1.0f, 0, p->clamp_nonneg, 1, st, hull, full, nbox));
                 else
                     FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, -p->grad_step,
                                             p->update_sigma, p->clamp_nonneg, 1, st, hull, full));
@@ -1096,16 +1100,16 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
         const int slot = it < 0 ? 0 : it;
         if (albedo) {
             FR_CUDA(c, launch_scatter_source(vol->data, vol->dtype, albedo, static_cast<float*>(c->J.p), c->src.p,
-                                             vol->dtype, vol->nx, vol->ny, vol->nz, st, p->skip_empty != 0));
+                                             vol->dtype, vol->nx, vol->ny, vol->nz, st, p->skip_empty != 0, nbox));
             FR_TRY(trace_mark(c, FR_PHASE_SCATTER));
         }
         FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, occ,
-                                    st, pack_keep));
+                                    st, pack_keep, nbox));
         FR_TRY(trace_mark(c, FR_PHASE_PACK));
         if (pipe) {
             FR_TRY(pipelined_views(st, slot));
-            FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg, 1,
-                                    st, hull, full));
+            FR_CUDA(c, launch_apply_box(vol->data, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, u.p.dV, 1.0f,
+                                        0, p->clamp_nonneg, 1, st, hull, full, nbox));
             return FR_OK;
         }
 #if FR_FUSED
@@ -1127,8 +1131,8 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
             FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * slot, st, 0, fin,
                                        it < 0 ? nullptr : rmse_dev + 3 * slot));
             FR_TRY(trace_mark(c, FR_PHASE_REDUCE));
-            FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg, 1,
-                                    st, hull, full));
+            FR_CUDA(c, launch_apply_box(vol->data, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, u.p.dV, 1.0f,
+                                        0, p->clamp_nonneg, 1, st, hull, full, nbox));
             FR_TRY(trace_mark(c, FR_PHASE_APPLY));
             return FR_OK;
         }
@@ -1155,8 +1159,8 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
                 FR_TRY(trace_mark(c, FR_PHASE_FINISH));
             }
 #endif
-            FR_CUDA(c, launch_apply(vol->data, vol->dtype, vol->kind, nodes, u.p.dV, 1.0f, 0, p->clamp_nonneg, 1,
-                                    st, hull, full));
+            FR_CUDA(c, launch_apply_box(vol->data, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, u.p.dV, 1.0f,
+                                        0, p->clamp_nonneg, 1, st, hull, full, nbox));
         } else {
             // d(0.5 sum m dL^2)/d(rendered) = -m dL: the residual scaled by -1
             u.p.img_scale = -1.0f;

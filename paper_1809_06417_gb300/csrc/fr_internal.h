@@ -96,12 +96,27 @@ cudaError_t launch_adjust_list(const SingleArgs& a, int dt, int ntiles, const un
 cudaError_t launch_apply(void* vol, int dt, int kind, long long nodes, float* dV, float scale,
                          int with_sigma, int clamp_nonneg, int zero_dV, cudaStream_t s,
                          const unsigned* hull = nullptr, unsigned hull_full = 0);
+// The box of a brick table's flagged bricks (brick-table layout, on the
+// device; see brick_box) taken as the range of nodes that are corners of
+// their cells.  box == nullptr: the whole grid.
+struct NodeBox {
+    const unsigned* box = nullptr;
+    int nbx = 0, nby = 0, nbz = 0;
+};
+// launch_apply over the nodes of `box` only (the whole grid without one): the
+// caller guarantees that every record and every update outside it is zero.
+cudaError_t launch_apply_box(void* vol, int dt, int kind, int nx, int ny, int nz, float* dV, float scale,
+                             int with_sigma, int clamp_nonneg, int zero_dV, cudaStream_t s, const unsigned* hull,
+                             unsigned hull_full, NodeBox box);
 // skip_empty: chunks of a grid line whose records are all zero skip their
 // walks; J is then left undefined at their nodes (their source is 0 anyway),
 // so only the reconstruction loop, which reads the source alone, asks for it.
+// box: every record outside it is zero, and J and the source are computed at
+// its nodes only (left undefined elsewhere; grids whose lines run the
+// register-held chunks, the others in full).
 cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* albedo, float* J,
                                   void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s,
-                                  bool skip_empty = false);
+                                  bool skip_empty = false, NodeBox box = NodeBox{});
 cudaError_t launch_planck_lut(float t_min, float t_max, int m, float* lut, cudaStream_t s);
 cudaError_t launch_prepare_targets(float* targets, int ncam, int H, int W, float thresh, int* bbox,
                                    cudaStream_t s);
@@ -166,7 +181,10 @@ __host__ __device__ inline unsigned* brick_box(unsigned char* table, int nbx, in
 // (nullable, brick-table layout): only nodes of flagged bricks are packed and
 // their box is the one the forward clips to, so occ's own box is not computed
 // (for the visual hull's table, whose flagged-off bricks hold zero records).
+// box (with keep): the records are known inside it only (launch_scatter_source
+// with that box) and are zero outside; nodes outside are not packed.
 cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int nx, int ny, int nz,
-                             unsigned char* occ, cudaStream_t s, const unsigned char* keep = nullptr);
+                             unsigned char* occ, cudaStream_t s, const unsigned char* keep = nullptr,
+                             NodeBox box = NodeBox{});
 
 }  // namespace frk

@@ -72,6 +72,46 @@ __global__ void __launch_bounds__(256) apply_kernel(void* vol, long long nodes, 
         apply_node<DT, KIND>(vol, i, dV, scale, with_sigma, clamp_nonneg, zero_dV, hull, hull_full);
 }
 
+// Node range [lo, hi] per axis of a NodeBox (false: no flagged brick); the
+// same box arithmetic as the marches' BrickSkip::box_range.
+__device__ __forceinline__ bool node_range(const NodeBox& B, int nx, int ny, int nz, int lo[3], int hi[3])
+{
+    const int n[3] = {nx, ny, nz}, nb[3] = {B.nbx, B.nby, B.nbz};
+    if (!B.box) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { lo[a] = 0; hi[a] = n[a] - 1; }
+        return true;
+    }
+    if (__ldg(B.box + 3) == 0u) return false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (nb[a] - (int)__ldg(B.box + a)) * kBrick;
+        hi[a] = min((int)__ldg(B.box + 3 + a) * kBrick, n[a] - 1);
+    }
+    return true;
+}
+
+// apply_kernel over the nodes of a NodeBox.
+template <int DT, int KIND>
+__global__ void __launch_bounds__(256) apply_box_kernel(void* vol, int nx, int ny, int nz, float* dV, float scale,
+                                                        int with_sigma, int clamp_nonneg, int zero_dV,
+                                                        const unsigned* __restrict__ hull, unsigned hull_full,
+                                                        NodeBox B)
+{
+    int lo[3], hi[3];
+    if (!node_range(B, nx, ny, nz, lo, hi)) return;
+    const unsigned ex = (unsigned)(hi[0] - lo[0] + 1), ey = (unsigned)(hi[1] - lo[1] + 1);
+    const unsigned total = ex * ey * (unsigned)(hi[2] - lo[2] + 1);   // volumes hold < 2^31 nodes
+    const long long nodes = (long long)nx * ny * nz;   // bounds of the checked build
+    (void)nodes;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const unsigned row = t / ex, x = t - row * ex, z = row / ey, y = row - z * ey;
+        const long long i = ((long long)(z + lo[2]) * ny + (y + lo[1])) * nx + (x + lo[0]);
+        apply_node<DT, KIND>(vol, FR_CHK(i, nodes, 41u), dV, scale, with_sigma, clamp_nonneg, zero_dV, hull,
+                             hull_full);
+    }
+}
+
 static int grid_for(long long n, int block)
 {
     long long g = (n + block - 1) / block;
@@ -86,6 +126,30 @@ cudaError_t launch_apply(void* vol, int dt, int kind, long long nodes, float* dV
     int g = grid_for(nodes, 256);
 #define FR_APPLY(D, KD) \
     apply_kernel<D, KD><<<g, 256, 0, s>>>(vol, nodes, dV, scale, with_sigma, clamp_nonneg, zero_dV, hull, hull_full)
+    if (kind == KIND_RGB) {
+        if (dt == DT_F32) FR_APPLY(DT_F32, KIND_RGB);
+        else if (dt == DT_BF16) FR_APPLY(DT_BF16, KIND_RGB);
+        else FR_APPLY(DT_F16, KIND_RGB);
+    } else {
+        if (dt == DT_F32) FR_APPLY(DT_F32, KIND_TEMP);
+        else if (dt == DT_BF16) FR_APPLY(DT_BF16, KIND_TEMP);
+        else FR_APPLY(DT_F16, KIND_TEMP);
+    }
+#undef FR_APPLY
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_box(void* vol, int dt, int kind, int nx, int ny, int nz, float* dV, float scale,
+                             int with_sigma, int clamp_nonneg, int zero_dV, cudaStream_t s, const unsigned* hull,
+                             unsigned hull_full, NodeBox box)
+{
+    const long long nodes = (long long)nx * ny * nz;
+    if (!box.box)
+        return launch_apply(vol, dt, kind, nodes, dV, scale, with_sigma, clamp_nonneg, zero_dV, s, hull, hull_full);
+    const int g = grid_for(nodes, 256);
+#define FR_APPLY(D, KD)                                                                                          \
+    apply_box_kernel<D, KD><<<g, 256, 0, s>>>(vol, nx, ny, nz, dV, scale, with_sigma, clamp_nonneg, zero_dV, hull, \
+                                              hull_full, box)
     if (kind == KIND_RGB) {
         if (dt == DT_F32) FR_APPLY(DT_F32, KIND_RGB);
         else if (dt == DT_BF16) FR_APPLY(DT_BF16, KIND_RGB);
@@ -297,13 +361,14 @@ __device__ __forceinline__ OwnedNodes owned_nodes(const KeepBricks& K, int nz, i
     return o;
 }
 
-// Pair i = {record i, record of its +x neighbour} (itself on the last x) of
-// node (x, y, z), and the brick marks of the non-zero records.
+// Pair i = {record i, record of its +x neighbour} (itself from x = x_last
+// on: the grid's last x, or the last x of the box the records are known in)
+// of node (x, y, z), and the brick marks of the non-zero records.
 template <int DT, int KIND>
-__device__ __forceinline__ void pack_node(const void* src, void* dst, long long i, int x, int y, int z, int nx,
+__device__ __forceinline__ void pack_node(const void* src, void* dst, long long i, int x, int y, int z, int x_last,
                                           unsigned char* occ, int nbx, int nby, int nbz)
 {
-    const long long j = x < nx - 1 ? i + 1 : i;
+    const long long j = x < x_last ? i + 1 : i;
     if constexpr (KIND == KIND_RGB) {
         bool nonzero;
         if constexpr (DT == DT_F32) {
@@ -344,26 +409,35 @@ __global__ void __launch_bounds__(256) pair_pack_kernel(const void* src, void* d
         const int x = (int)((unsigned)i - row * (unsigned)nx);
         const unsigned z = row / (unsigned)ny;
         const int y = (int)(row - z * (unsigned)ny);
-        pack_node<DT, KIND>(src, dst, i, x, y, (int)z, nx, occ, nbx, nby, nbz);
+        pack_node<DT, KIND>(src, dst, i, x, y, (int)z, nx - 1, occ, nbx, nby, nbz);
     }
 }
 
 // Over the owned nodes of the active bricks of `keep` only, one warp per brick
-// (a node of an inactive brick is read by no forward sample).
+// (a node of an inactive brick is read by no forward sample).  With a
+// NodeBox, the records are known inside it only (the sweeps computed no more;
+// every record outside it is zero): nodes outside are left out, and the pair
+// of the box's last x node repeats that node, zero like its neighbour -- the
+// same pairs and brick marks as over the whole grid, for the cells the
+// forward can evaluate.
 template <int DT, int KIND>
 __global__ void __launch_bounds__(256) pair_pack_bricks_kernel(const void* src, void* dst, int nz, unsigned char* occ,
-                                                               KeepBricks keep)
+                                                               KeepBricks keep, NodeBox B)
 {
     const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (b >= keep.nbx * keep.nby * keep.nbz) return;
     const OwnedNodes o = owned_nodes(keep, nz, b);
     if (!o.active) return;
+    int lo[3], hi[3];
+    if (!node_range(B, keep.nx, keep.ny, nz, lo, hi)) return;
+    const int x_last = min(keep.nx - 1, hi[0]);
     const int exy = o.ex * o.ey, cnt = exy * o.ez;
     for (int t = lane; t < cnt; t += 32) {
         const int dz = t / exy, r = t - dz * exy, dy = r / o.ex, dx = r - dy * o.ex;
         const int x = o.x0 + dx, y = o.y0 + dy, z = o.z0 + dz;
+        if (x < lo[0] || x > hi[0] || y < lo[1] || y > hi[1] || z < lo[2] || z > hi[2]) continue;
         const long long i = ((long long)z * keep.ny + y) * keep.nx + x;
-        pack_node<DT, KIND>(src, dst, i, x, y, z, keep.nx, occ, keep.nbx, keep.nby, keep.nbz);
+        pack_node<DT, KIND>(src, dst, i, x, y, z, x_last, occ, keep.nbx, keep.nby, keep.nbz);
     }
 }
 
@@ -410,7 +484,7 @@ cudaError_t launch_pair_pack_batch(const ProbDev* probs, int nprob, int dt, cuda
 }
 
 cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int nx, int ny, int nz,
-                             unsigned char* occ, cudaStream_t s, const unsigned char* keep)
+                             unsigned char* occ, cudaStream_t s, const unsigned char* keep, NodeBox box)
 {
     const long long nodes = (long long)nx * ny * nz;
     const int g = grid_for(nodes, 256);
@@ -422,7 +496,7 @@ cudaError_t launch_pair_pack(const void* src, void* dst, int dt, int kind, int n
     const KeepBricks KB{keep, nx, ny, nbx, nby, nbz};
     const unsigned gb = (unsigned)(((long long)nbx * nby * nbz * 32 + 255) / 256);
 #define FR_PACK(D, K)                                                                        \
-    if (keep) pair_pack_bricks_kernel<D, K><<<gb, 256, 0, s>>>(src, dst, nz, occ, KB);      \
+    if (keep) pair_pack_bricks_kernel<D, K><<<gb, 256, 0, s>>>(src, dst, nz, occ, KB, box); \
     else pair_pack_kernel<D, K><<<g, 256, 0, s>>>(src, dst, nodes, nx, ny, occ, nbx, nby, nbz)
     if (kind == KIND_RGB) {
         if (dt == DT_F32) FR_PACK(DT_F32, KIND_RGB);
@@ -637,10 +711,15 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const
 // are bitwise equal.  rec[0] is node max(s0 - 1, 0), rec[1 + q] node s0 + q,
 // rec[cnt + 1] node min(s1, n - 1); segment j joins rec[j] and rec[j + 1] and
 // leads into node s0 + j.
+//
+// With a NodeBox, only the lines through the box run, over the box's nodes:
+// every record outside it is zero, so the light reaching the box along a line
+// is zero and the segment into its first node (from a zero record) is part of
+// the first chunk, as without the box.
 template <int DT, int AXIS, bool LAST, int CM>
 __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_reg_kernel(const void* em, const float* albedo,
                                                                                 float* J, void* out, int nx, int ny,
-                                                                                int nz, bool skip_empty)
+                                                                                int nz, bool skip_empty, NodeBox B)
 {
     __shared__ float4 fwd[kSweepChunks][kSweepLines];
     __shared__ float4 bwd[kSweepChunks][kSweepLines];
@@ -648,12 +727,16 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_reg_kernel(c
     const long long lines = AXIS == 1 ? (long long)nx * nz : (long long)nx * ny;
     const long long line = blockIdx.x * (long long)kSweepLines + threadIdx.x;
     const int ch = threadIdx.y;
-    const bool live = line < lines;
+    int lo[3], hi[3];
+    bool live = line < lines && node_range(B, nx, ny, nz, lo, hi);
     long long start = 0, stride = 1;
     if (live) {
+        // the line's two other coordinates: (x, z) for y lines, (x, y) for z lines
+        const int c = (int)(line / nx), x = (int)(line - (long long)c * nx);
+        const int ca = AXIS == 1 ? 2 : 1;
+        live = x >= lo[0] && x <= hi[0] && c >= lo[ca] && c <= hi[ca];
         if constexpr (AXIS == 1) {
-            const long long z = line / nx, x = line - z * nx;
-            start = z * (long long)nx * ny + x;
+            start = (long long)c * nx * ny + x;      // line = z * nx + x
             stride = nx;
         } else {
             start = line;                            // line = y * nx + x
@@ -662,8 +745,9 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_reg_kernel(c
     }
     const long long nodes = (long long)nx * ny * nz;   // bounds of the checked build
     (void)nodes;
-    const int m = (n_line + kSweepChunks - 1) / kSweepChunks;
-    const int s0 = min(ch * m, n_line), s1 = min(s0 + m, n_line), cnt = s1 - s0;   // cnt <= CM
+    const int alo = live ? lo[AXIS] : 0, ahi = live ? hi[AXIS] : -1;   // the nodes [alo, ahi] of the line
+    const int m = (ahi - alo + 1 + kSweepChunks - 1) / kSweepChunks;
+    const int s0 = min(alo + ch * m, ahi + 1), s1 = min(s0 + m, ahi + 1), cnt = s1 - s0;   // cnt <= CM
     float4 rec[CM + 2];
     float Ef = 1.0f, F0 = 0.0f, F1 = 0.0f, F2 = 0.0f;
     float Eb = 1.0f, B0 = 0.0f, B1 = 0.0f, B2 = 0.0f;
@@ -884,19 +968,26 @@ __global__ void __launch_bounds__(256) sweep_x_kernel(const void* em, float* J, 
 
 // The x sweep with a chunk of at most CM nodes held in registers (see
 // sweep_reg_kernel; the same arithmetic as sweep_x_kernel in the same order).
+// With a NodeBox, the lines through the box over its nodes (as in sweep_reg_kernel).
 template <int DT, int CM>
 __global__ void __launch_bounds__(256) sweep_x_reg_kernel(const void* em, float* J, int nx, int ny, int nz,
-                                                          bool skip_empty)
+                                                          bool skip_empty, NodeBox B)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const long long line = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (line >= (long long)ny * nz) return;   // whole warps leave together
+    int lo[3], hi[3];
+    if (!node_range(B, nx, ny, nz, lo, hi)) return;
+    {
+        const int z = (int)(line / ny), y = (int)(line - (long long)z * ny);   // line = z * ny + y
+        if (y < lo[1] || y > hi[1] || z < lo[2] || z > hi[2]) return;
+    }
     const long long start = line * nx;
     const long long nodes = (long long)nx * ny * nz;   // bounds of the checked build
     (void)nodes;
-    const int m = (nx + 31) / 32;
-    const int s0 = min(lane * m, nx), s1 = min(s0 + m, nx), cnt = s1 - s0;   // cnt <= CM
+    const int m = (hi[0] - lo[0] + 1 + 31) / 32;
+    const int s0 = min(lo[0] + lane * m, hi[0] + 1), s1 = min(s0 + m, hi[0] + 1), cnt = s1 - s0;   // cnt <= CM
     float4 rec[CM + 2];
     float Ef = 1.0f, F0 = 0.0f, F1 = 0.0f, F2 = 0.0f;
     float Eb = 1.0f, B0 = 0.0f, B1 = 0.0f, B2 = 0.0f;
@@ -990,13 +1081,13 @@ __global__ void __launch_bounds__(256) sweep_x_reg_kernel(const void* em, float*
 
 template <int DT, int AXIS, bool LAST>
 static cudaError_t launch_sweep_yz(int m, unsigned grid, const void* em, const float* albedo, float* J, void* out,
-                                   int nx, int ny, int nz, cudaStream_t s, bool skip_empty)
+                                   int nx, int ny, int nz, cudaStream_t s, bool skip_empty, NodeBox box)
 {
     const dim3 B(kSweepLines, kSweepChunks);
     if (FR_SWEEP_REG_MAX >= 4 && m <= 4)
-        sweep_reg_kernel<DT, AXIS, LAST, 4><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, skip_empty);
+        sweep_reg_kernel<DT, AXIS, LAST, 4><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, skip_empty, box);
     else if (FR_SWEEP_REG_MAX >= 8 && m <= 8)
-        sweep_reg_kernel<DT, AXIS, LAST, 8><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, skip_empty);
+        sweep_reg_kernel<DT, AXIS, LAST, 8><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, skip_empty, box);
     else
         sweep_kernel<DT, AXIS, LAST><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, nullptr, skip_empty);
     return cudaSuccess;
@@ -1004,34 +1095,38 @@ static cudaError_t launch_sweep_yz(int m, unsigned grid, const void* em, const f
 
 template <int DT>
 static cudaError_t launch_sweeps(const void* em, const float* albedo, float* J, void* out, int nx, int ny, int nz,
-                                 cudaStream_t s, bool skip_empty)
+                                 cudaStream_t s, bool skip_empty, NodeBox box)
 {
     const long long lx = (long long)ny * nz, ly = (long long)nx * nz, lz = (long long)nx * ny;
     const unsigned gxw = (unsigned)((lx + 7) / 8);  // one warp per x line, 8 warps per CTA
     const unsigned gy = (unsigned)((ly + kSweepLines - 1) / kSweepLines);
     const unsigned gz = (unsigned)((lz + kSweepLines - 1) / kSweepLines);
     const int mx = (nx + 31) / 32;
+    const int my = (ny + kSweepChunks - 1) / kSweepChunks, mz = (nz + kSweepChunks - 1) / kSweepChunks;
+    // the box applies when every sweep runs register-held chunks (it is a
+    // restriction of work, never needed for the result)
+    const int cm = FR_SWEEP_REG_MAX >= 8 ? 8 : FR_SWEEP_REG_MAX;
+    if (!(mx <= cm && my <= cm && mz <= cm)) box = NodeBox{};
     if (FR_SWEEP_REG_MAX >= 4 && mx <= 4)
-        sweep_x_reg_kernel<DT, 4><<<gxw, 256, 0, s>>>(em, J, nx, ny, nz, skip_empty);
+        sweep_x_reg_kernel<DT, 4><<<gxw, 256, 0, s>>>(em, J, nx, ny, nz, skip_empty, box);
     else if (FR_SWEEP_REG_MAX >= 8 && mx <= 8)
-        sweep_x_reg_kernel<DT, 8><<<gxw, 256, 0, s>>>(em, J, nx, ny, nz, skip_empty);
+        sweep_x_reg_kernel<DT, 8><<<gxw, 256, 0, s>>>(em, J, nx, ny, nz, skip_empty, box);
     else
         sweep_x_kernel<DT><<<gxw, 256, 0, s>>>(em, J, nx, ny, nz, nullptr, skip_empty);
-    cudaError_t e = launch_sweep_yz<DT, 1, false>((ny + kSweepChunks - 1) / kSweepChunks, gy, em, albedo, J, out, nx,
-                                                  ny, nz, s, skip_empty);
+    cudaError_t e = launch_sweep_yz<DT, 1, false>(my, gy, em, albedo, J, out, nx, ny, nz, s, skip_empty, box);
     if (e != cudaSuccess) return e;
-    return launch_sweep_yz<DT, 2, true>((nz + kSweepChunks - 1) / kSweepChunks, gz, em, albedo, J, out, nx, ny, nz,
-                                        s, skip_empty);
+    return launch_sweep_yz<DT, 2, true>(mz, gz, em, albedo, J, out, nx, ny, nz, s, skip_empty, box);
 }
 
 cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* albedo, float* J,
-                                  void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s, bool skip_empty)
+                                  void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s, bool skip_empty,
+                                  NodeBox box)
 {
     if (dt_in != dt_out) return cudaErrorInvalidValue;
     cudaError_t e;
-    if (dt_in == DT_F32) e = launch_sweeps<DT_F32>(emission, albedo, J, out, nx, ny, nz, s, skip_empty);
-    else if (dt_in == DT_BF16) e = launch_sweeps<DT_BF16>(emission, albedo, J, out, nx, ny, nz, s, skip_empty);
-    else e = launch_sweeps<DT_F16>(emission, albedo, J, out, nx, ny, nz, s, skip_empty);
+    if (dt_in == DT_F32) e = launch_sweeps<DT_F32>(emission, albedo, J, out, nx, ny, nz, s, skip_empty, box);
+    else if (dt_in == DT_BF16) e = launch_sweeps<DT_BF16>(emission, albedo, J, out, nx, ny, nz, s, skip_empty, box);
+    else e = launch_sweeps<DT_F16>(emission, albedo, J, out, nx, ny, nz, s, skip_empty, box);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
