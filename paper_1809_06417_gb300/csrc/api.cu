@@ -971,6 +971,9 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     // outside it is zero (the hull clear) and no adjustment reaches it
     // (FR_NODE_BOX = 0: the whole grid).
     const NodeBox nbox = FR_NODE_BOX && pack_keep ? NodeBox{u.p.adj_box, nbx, nby, nbz} : NodeBox{};
+    // the forward clips to the adjustment's box: the half rays divide the
+    // samples inside it (FR_SPLIT_BOX = 0: the whole chord)
+    if (FR_SPLIT_BOX && pack_keep) f.p.split_box = u.p.split_box = 1;
     void* fin = nullptr;
     FR_TRY(fin_scratch(c, &fin));
     float* rmse_dev = static_cast<float*>(c->rmse.p);

@@ -75,7 +75,10 @@ struct ProbDev {
     float step, alpha_l, alpha_d, tau, g_std, thresh;
     unsigned long long seed;
     int iteration;
-    int pad_;
+    // 1: a flame ray's parts (FR_ADJ_SPLIT) divide the samples its box range
+    // keeps -- the forward's occ_box and the adjustment's adj_box, the same
+    // box -- instead of its whole chord (both marches split the same way)
+    int split_box;
     unsigned long long* counter; // sample counter, nullable
     // batched launches only
     const unsigned* list;        // flame-ray list (linear pixel indices)

@@ -317,8 +317,12 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
                 if (!BrickSkip::box_range(P, P.occ_box, R, P.step, k0, k1)) k1 = 0;
             }
             int kb[kTm];
+            {
+                const bool in_box = SKIP && P.split_box;
+                const int sa = in_box ? k0 : 0, sn = in_box ? max(k1 - k0, 0) : R.n;
 #pragma unroll
-            for (int j = 0; j < kTm; ++j) kb[j] = R.n * (j + 1) / FR_ADJ_SPLIT;
+                for (int j = 0; j < kTm; ++j) kb[j] = sa + sn * (j + 1) / FR_ADJ_SPLIT;
+            }
             for (int k = k0; k < k1; ++k) {
                 float len, x, y, z;
                 segment(R, P.step, k, len, x, y, z);
@@ -644,11 +648,15 @@ __device__ __forceinline__ void adj_ray(const ProbDev& P, const CamDev* cams, in
         if (!BrickSkip::box_range(P, P.adj_box, R, P.step, k0, k1)) return;
     }
 #if FR_ADJ_SPLIT > 1
-    // part j: samples [R.n j / n, R.n (j + 1) / n) of the ray, starting from the
-    // transmittance the forward march reached there
+    // part j: samples [a + m j / n, a + m (j + 1) / n) of the ray -- [a, a + m)
+    // the box range (P.split_box), else the whole chord [0, R.n) -- starting
+    // from the transmittance the forward march reached there
     if (part >= 0) {
-        k0 = max(k0, R.n * part / FR_ADJ_SPLIT);
-        k1 = min(k1, R.n * (part + 1) / FR_ADJ_SPLIT);
+        const bool in_box = SKIP && P.split_box;
+        const int sa = in_box ? k0 : 0, sn = in_box ? k1 - k0 : R.n;
+        const int a0 = sa + sn * part / FR_ADJ_SPLIT, a1 = sa + sn * (part + 1) / FR_ADJ_SPLIT;
+        k0 = max(k0, a0);
+        k1 = min(k1, a1);
     }
 #endif
     for (int k = k0; k < k1; ++k) {
