@@ -36,11 +36,11 @@ METRIC = "ray samples/s (fwd+adjoint) and recon iters/s at 128^3×8 views; p50/p
 WORKLOAD = dict(name="full_rte_128^3_8x512^2", n=128, views=8, side=512, step=0.5, seed=2,
                 alpha_l=2e-4, noise=1e-3, hull=True)
 # kernels one step (one fr_reconstruct iteration) launches: hull clear with
-# brick marks and their box, in-scatter sweeps (3), pair pack (inside the
-# hull's bricks; the forward clips to their box), forward (which lists the
-# flame rays), error reduction (which also writes the rmse), adjustment,
-# update (with the hull clear)
-KERNELS_PER_STEP = 9
+# brick marks and their box, in-scatter sweeps (3, over the box of the hull's
+# bricks; the last also writes the x-pair records and the brick marks),
+# forward (which lists the flame rays), error reduction (which also writes the
+# rmse), adjustment, update (with the hull clear, over the same box)
+KERNELS_PER_STEP = 8
 # dram__bytes_read.sum + dram__bytes_write.sum and smsp__inst_executed.sum
 # (warp instructions) per launch from ncu captures of the current kernels at
 # this workload (None where the kernel changed since)

@@ -38,6 +38,9 @@ constexpr size_t kHostScratchBytes = 64;
 #ifndef FR_SPLIT_BOX
 #define FR_SPLIT_BOX 1
 #endif
+#ifndef FR_SWEEP_PACK
+#define FR_SWEEP_PACK 1
+#endif
 #ifndef FR_PIPELINE_VIEWS
 #define FR_PIPELINE_VIEWS 0
 #endif

@@ -974,6 +974,13 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     // the forward clips to the adjustment's box: the half rays divide the
     // samples inside it (FR_SPLIT_BOX = 0: the whole chord)
     if (FR_SPLIT_BOX && pack_keep) f.p.split_box = u.p.split_box = 1;
+    // With the box, the last in-scattering sweep writes the x-pair records and
+    // the brick marks itself (the pair pack folded into it; FR_SWEEP_PACK = 0:
+    // a separate pack)
+    const bool fold_pack = FR_SWEEP_PACK && albedo && !hg && nbox.box && occ &&
+                           sweeps_take_box(vol->nx, vol->ny, vol->nz);
+    const PackOut pk = fold_pack ? PackOut{c->pairs.p, occ} : PackOut{};
+    const size_t occ_bytes = brick_table_bytes(vol->nx, vol->ny, vol->nz);
     void* fin = nullptr;
     FR_TRY(fin_scratch(c, &fin));
     float* rmse_dev = static_cast<float*>(c->rmse.p);
@@ -1038,13 +1045,14 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
                     FR_CUDA(c, launch_source_hg(vol->data, vol->dtype, albedo, static_cast<const float*>(c->L6.p),
                                                 hg_weights(v), c->src.p, nodes, st));
                 } else if (v == 0 || seq) {
+                    if (fold_pack) FR_CUDA(c, cudaMemsetAsync(occ, 0, occ_bytes, st));
                     FR_CUDA(c, launch_scatter_source(vol->data, vol->dtype, albedo, static_cast<float*>(c->J.p),
                                                      c->src.p, vol->dtype, vol->nx, vol->ny, vol->nz, st,
-                                                     p->skip_empty != 0, nbox));
+                                                     p->skip_empty != 0, nbox, pk));
                 }
                 FR_TRY(trace_mark(c, FR_PHASE_SCATTER));
             }
-            if (v == 0 || seq || hg) {
+            if ((v == 0 || seq || hg) && !fold_pack) {
                 FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz,
                                             occ, st, pack_keep, nbox));
                 FR_TRY(trace_mark(c, FR_PHASE_PACK));
@@ -1102,13 +1110,16 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
         if (per_view) return per_view_iteration(st, it);
         const int slot = it < 0 ? 0 : it;
         if (albedo) {
+            if (fold_pack) FR_CUDA(c, cudaMemsetAsync(occ, 0, occ_bytes, st));
             FR_CUDA(c, launch_scatter_source(vol->data, vol->dtype, albedo, static_cast<float*>(c->J.p), c->src.p,
-                                             vol->dtype, vol->nx, vol->ny, vol->nz, st, p->skip_empty != 0, nbox));
+                                             vol->dtype, vol->nx, vol->ny, vol->nz, st, p->skip_empty != 0, nbox, pk));
             FR_TRY(trace_mark(c, FR_PHASE_SCATTER));
         }
-        FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, occ,
-                                    st, pack_keep, nbox));
-        FR_TRY(trace_mark(c, FR_PHASE_PACK));
+        if (!fold_pack) {
+            FR_CUDA(c, launch_pair_pack(render_vol, c->pairs.p, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, occ,
+                                        st, pack_keep, nbox));
+            FR_TRY(trace_mark(c, FR_PHASE_PACK));
+        }
         if (pipe) {
             FR_TRY(pipelined_views(st, slot));
             FR_CUDA(c, launch_apply_box(vol->data, vol->dtype, vol->kind, vol->nx, vol->ny, vol->nz, u.p.dV, 1.0f,

@@ -103,6 +103,16 @@ struct NodeBox {
     const unsigned* box = nullptr;
     int nbx = 0, nby = 0, nbz = 0;
 };
+// x-pair records and brick marks written by the last in-scattering sweep
+// (the pair pack folded into it): pair i = {source i, source of its +x
+// neighbour}, the second half repeating the first on the box's last x; occ
+// (cleared beforehand) flags the bricks of every non-zero source record.
+struct PackOut {
+    void* pairs = nullptr;
+    unsigned char* occ = nullptr;
+};
+// Whether launch_scatter_source honours a NodeBox (and a PackOut) for this grid.
+bool sweeps_take_box(int nx, int ny, int nz);
 // launch_apply over the nodes of `box` only (the whole grid without one): the
 // caller guarantees that every record and every update outside it is zero.
 cudaError_t launch_apply_box(void* vol, int dt, int kind, int nx, int ny, int nz, float* dV, float scale,
@@ -114,9 +124,12 @@ cudaError_t launch_apply_box(void* vol, int dt, int kind, int nx, int ny, int nz
 // box: every record outside it is zero, and J and the source are computed at
 // its nodes only (left undefined elsewhere; grids whose lines run the
 // register-held chunks, the others in full).
+// pk (with a box the sweeps honour): the pairs and brick marks of the source
+// records at the box's nodes, as launch_pair_pack with that box would write
+// them for the forward march.
 cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* albedo, float* J,
                                   void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s,
-                                  bool skip_empty = false, NodeBox box = NodeBox{});
+                                  bool skip_empty = false, NodeBox box = NodeBox{}, PackOut pk = PackOut{});
 cudaError_t launch_planck_lut(float t_min, float t_max, int m, float* lut, cudaStream_t s);
 cudaError_t launch_prepare_targets(float* targets, int ncam, int H, int W, float thresh, int* bbox,
                                    cudaStream_t s);

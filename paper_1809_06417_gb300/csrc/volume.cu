@@ -704,6 +704,55 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const
     }
 }
 
+// A source record in its storage form (the bits store_rgb writes) and
+// whether it is non-zero as stored (+0 and -0 read as empty, as in the pack).
+template <int DT>
+__device__ __forceinline__ bool stored_form(float4 v, float4& f, uint2& u)
+{
+    if constexpr (DT == DT_F32) {
+        f = v;
+        return v.x != 0.0f || v.y != 0.0f || v.z != 0.0f || v.w != 0.0f;
+    } else {
+        if constexpr (DT == DT_BF16) {
+            __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+            u.x = *reinterpret_cast<uint32_t*>(&a);
+            u.y = *reinterpret_cast<uint32_t*>(&b);
+        } else {
+            __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+            u.x = *reinterpret_cast<uint32_t*>(&a);
+            u.y = *reinterpret_cast<uint32_t*>(&b);
+        }
+        return ((u.x | u.y) & 0x7fff7fffu) != 0u;
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void put_stored(void* dst, long long i, const float4& f, const uint2& u)
+{
+    if constexpr (DT == DT_F32) reinterpret_cast<float4*>(dst)[i] = f;
+    else reinterpret_cast<uint2*>(dst)[i] = u;
+}
+
+// Source record of node `node` at (x, y, z) written to `out` and, with pk, to
+// the two x-pairs that hold it (its own first half, the -x neighbour's second
+// half inside the box, its own second half on the box's last x), with the
+// brick marks of a non-zero record.
+template <int DT>
+__device__ __forceinline__ void put_source(void* out, long long node, float4 v, const PackOut& pk, int x, int y, int z,
+                                           int x_lo, int x_last, int nbx, int nby, int nbz)
+{
+    float4 f;
+    uint2 u;
+    const bool nz = stored_form<DT>(v, f, u);
+    put_stored<DT>(out, node, f, u);
+    if (pk.pairs) {
+        put_stored<DT>(pk.pairs, 2 * node, f, u);
+        if (x > x_lo) put_stored<DT>(pk.pairs, 2 * node - 1, f, u);
+        if (x == x_last) put_stored<DT>(pk.pairs, 2 * node + 1, f, u);
+        if (nz && pk.occ) mark_bricks(pk.occ, x, y, z, nbx, nby, nbz);
+    }
+}
+
 // The y / z sweep with a chunk of at most CM nodes held in registers: the
 // chunk's records (and its nodes' J, albedo) are loaded together at the start,
 // where the kernel above reloads them in three dependent walks; J is stored
@@ -719,8 +768,10 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_kernel(const
 template <int DT, int AXIS, bool LAST, int CM>
 __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_reg_kernel(const void* em, const float* albedo,
                                                                                 float* J, void* out, int nx, int ny,
-                                                                                int nz, bool skip_empty, NodeBox B)
+                                                                                int nz, bool skip_empty, NodeBox B,
+                                                                                PackOut pk)
 {
+    static_assert(!LAST || AXIS == 2, "the source (and its pairs) is written by the z sweep");
     __shared__ float4 fwd[kSweepChunks][kSweepLines];
     __shared__ float4 bwd[kSweepChunks][kSweepLines];
     const int n_line = AXIS == 1 ? ny : nz;
@@ -730,9 +781,11 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_reg_kernel(c
     int lo[3], hi[3];
     bool live = line < lines && node_range(B, nx, ny, nz, lo, hi);
     long long start = 0, stride = 1;
+    int lx = 0, lc = 0;   // the line's x and its other coordinate (z for y lines, y for z lines)
     if (live) {
-        // the line's two other coordinates: (x, z) for y lines, (x, y) for z lines
         const int c = (int)(line / nx), x = (int)(line - (long long)c * nx);
+        lx = x;
+        lc = c;
         const int ca = AXIS == 1 ? 2 : 1;
         live = x >= lo[0] && x <= hi[0] && c >= lo[ca] && c <= hi[ca];
         if constexpr (AXIS == 1) {
@@ -798,10 +851,12 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_reg_kernel(c
     bwd[ch][threadIdx.x] = make_float4(Eb, B0, B1, B2);
     __syncthreads();
     if (!live || cnt <= 0) return;
+    const int x_last = min(nx - 1, hi[0]);   // (pk: lines through the box only, so lo/hi are set)
     if (skip_empty && !occupied) {
         if constexpr (LAST) {
             for (int q = 0; q < cnt; ++q)
-                store_rgb<DT>(out, FR_CHK(start + (s0 + q) * stride, nodes, 36u), make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+                put_source<DT>(out, FR_CHK(start + (s0 + q) * stride, nodes, 36u), make_float4(0.0f, 0.0f, 0.0f, 0.0f),
+                               pk, lx, lc, s0 + q, lo[0], x_last, B.nbx, B.nby, B.nbz);
         }
         return;
     }
@@ -844,8 +899,8 @@ __global__ void __launch_bounds__(kSweepLines * kSweepChunks) sweep_reg_kernel(c
             if constexpr (LAST) {
                 const float4 cur = rec[q + 1];
                 const float as = alb[q] * cur.w;
-                store_rgb<DT>(out, node, make_float4(fmaf(as, jx, cur.x), fmaf(as, jy, cur.y), fmaf(as, jz, cur.z),
-                                                     cur.w));
+                put_source<DT>(out, node, make_float4(fmaf(as, jx, cur.x), fmaf(as, jy, cur.y), fmaf(as, jz, cur.z), cur.w),
+                               pk, lx, lc, i, lo[0], x_last, B.nbx, B.nby, B.nbz);
                 if (!skip_empty) J4[node] = make_float4(jx, jy, jz, 0.0f);
             } else {
                 J4[node] = make_float4(jx, jy, jz, 0.0f);
@@ -1081,21 +1136,28 @@ __global__ void __launch_bounds__(256) sweep_x_reg_kernel(const void* em, float*
 
 template <int DT, int AXIS, bool LAST>
 static cudaError_t launch_sweep_yz(int m, unsigned grid, const void* em, const float* albedo, float* J, void* out,
-                                   int nx, int ny, int nz, cudaStream_t s, bool skip_empty, NodeBox box)
+                                   int nx, int ny, int nz, cudaStream_t s, bool skip_empty, NodeBox box, PackOut pk)
 {
     const dim3 B(kSweepLines, kSweepChunks);
     if (FR_SWEEP_REG_MAX >= 4 && m <= 4)
-        sweep_reg_kernel<DT, AXIS, LAST, 4><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, skip_empty, box);
+        sweep_reg_kernel<DT, AXIS, LAST, 4><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, skip_empty, box, pk);
     else if (FR_SWEEP_REG_MAX >= 8 && m <= 8)
-        sweep_reg_kernel<DT, AXIS, LAST, 8><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, skip_empty, box);
+        sweep_reg_kernel<DT, AXIS, LAST, 8><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, skip_empty, box, pk);
     else
         sweep_kernel<DT, AXIS, LAST><<<grid, B, 0, s>>>(em, albedo, J, out, nx, ny, nz, nullptr, skip_empty);
     return cudaSuccess;
 }
 
+bool sweeps_take_box(int nx, int ny, int nz)
+{
+    const int cm = FR_SWEEP_REG_MAX >= 8 ? 8 : FR_SWEEP_REG_MAX;
+    return (nx + 31) / 32 <= cm && (ny + kSweepChunks - 1) / kSweepChunks <= cm &&
+           (nz + kSweepChunks - 1) / kSweepChunks <= cm;
+}
+
 template <int DT>
 static cudaError_t launch_sweeps(const void* em, const float* albedo, float* J, void* out, int nx, int ny, int nz,
-                                 cudaStream_t s, bool skip_empty, NodeBox box)
+                                 cudaStream_t s, bool skip_empty, NodeBox box, PackOut pk)
 {
     const long long lx = (long long)ny * nz, ly = (long long)nx * nz, lz = (long long)nx * ny;
     const unsigned gxw = (unsigned)((lx + 7) / 8);  // one warp per x line, 8 warps per CTA
@@ -1104,29 +1166,32 @@ static cudaError_t launch_sweeps(const void* em, const float* albedo, float* J, 
     const int mx = (nx + 31) / 32;
     const int my = (ny + kSweepChunks - 1) / kSweepChunks, mz = (nz + kSweepChunks - 1) / kSweepChunks;
     // the box applies when every sweep runs register-held chunks (it is a
-    // restriction of work, never needed for the result)
-    const int cm = FR_SWEEP_REG_MAX >= 8 ? 8 : FR_SWEEP_REG_MAX;
-    if (!(mx <= cm && my <= cm && mz <= cm)) box = NodeBox{};
+    // restriction of work, never needed for the result); so do the pairs
+    if (!sweeps_take_box(nx, ny, nz)) {
+        if (pk.pairs) return cudaErrorInvalidValue;
+        box = NodeBox{};
+    }
+    if (pk.pairs && !box.box) return cudaErrorInvalidValue;
     if (FR_SWEEP_REG_MAX >= 4 && mx <= 4)
         sweep_x_reg_kernel<DT, 4><<<gxw, 256, 0, s>>>(em, J, nx, ny, nz, skip_empty, box);
     else if (FR_SWEEP_REG_MAX >= 8 && mx <= 8)
         sweep_x_reg_kernel<DT, 8><<<gxw, 256, 0, s>>>(em, J, nx, ny, nz, skip_empty, box);
     else
         sweep_x_kernel<DT><<<gxw, 256, 0, s>>>(em, J, nx, ny, nz, nullptr, skip_empty);
-    cudaError_t e = launch_sweep_yz<DT, 1, false>(my, gy, em, albedo, J, out, nx, ny, nz, s, skip_empty, box);
+    cudaError_t e = launch_sweep_yz<DT, 1, false>(my, gy, em, albedo, J, out, nx, ny, nz, s, skip_empty, box, PackOut{});
     if (e != cudaSuccess) return e;
-    return launch_sweep_yz<DT, 2, true>(mz, gz, em, albedo, J, out, nx, ny, nz, s, skip_empty, box);
+    return launch_sweep_yz<DT, 2, true>(mz, gz, em, albedo, J, out, nx, ny, nz, s, skip_empty, box, pk);
 }
 
 cudaError_t launch_scatter_source(const void* emission, int dt_in, const float* albedo, float* J,
                                   void* out, int dt_out, int nx, int ny, int nz, cudaStream_t s, bool skip_empty,
-                                  NodeBox box)
+                                  NodeBox box, PackOut pk)
 {
     if (dt_in != dt_out) return cudaErrorInvalidValue;
     cudaError_t e;
-    if (dt_in == DT_F32) e = launch_sweeps<DT_F32>(emission, albedo, J, out, nx, ny, nz, s, skip_empty, box);
-    else if (dt_in == DT_BF16) e = launch_sweeps<DT_BF16>(emission, albedo, J, out, nx, ny, nz, s, skip_empty, box);
-    else e = launch_sweeps<DT_F16>(emission, albedo, J, out, nx, ny, nz, s, skip_empty, box);
+    if (dt_in == DT_F32) e = launch_sweeps<DT_F32>(emission, albedo, J, out, nx, ny, nz, s, skip_empty, box, pk);
+    else if (dt_in == DT_BF16) e = launch_sweeps<DT_BF16>(emission, albedo, J, out, nx, ny, nz, s, skip_empty, box, pk);
+    else e = launch_sweeps<DT_F16>(emission, albedo, J, out, nx, ny, nz, s, skip_empty, box, pk);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -1,6 +1,8 @@
 """Phase tracing of fr_reconstruct: the library's events split the device time
 of a call into its phases; their sum matches the time measured around the call
-and each phase that ran has a positive share."""
+and each phase that ran has a positive share.  With in-scattering and the
+visual hull the pair pack runs inside the last sweep (no pack phase); without
+in-scattering it is a phase of its own."""
 import numpy as np
 import pytest
 
@@ -44,13 +46,19 @@ def test_phase_times_cover_the_call():
         total = e0.elapsed_time(e1)
         print({k: round(x, 4) for k, x in ms.items()}, "calls", calls, "total", round(total, 4))
         assert calls == 2
-        for k in ("setup", "scatter", "pack", "forward", "reduce", "adjust", "apply", "finish"):
+        for k in ("setup", "scatter", "forward", "reduce", "adjust", "apply", "finish"):
             assert ms[k] > 0.0, k
+        assert ms["pack"] == 0.0
         assert sum(ms.values()) <= total * 1.001
         assert sum(ms.values()) > 0.8 * total
         # read again: the record was dropped
         ms2, calls2 = ctx.fr_phase_times()
         assert calls2 == 0 and sum(ms2.values()) == 0.0
+        # without in-scattering: a pack phase of its own, no sweeps
+        ctx.fr_reconstruct(fv, fc, img, bbox, 2, p)
+        torch.cuda.synchronize()
+        ms4, calls4 = ctx.fr_phase_times()
+        assert calls4 == 1 and ms4["pack"] > 0.0 and ms4["scatter"] == 0.0 and ms4["forward"] > 0.0
         # tracing off: nothing is recorded
         ctx.fr_trace_phases(False)
         ctx.fr_reconstruct(fv, fc, img, bbox, 1, p, albedo=alb)
