@@ -22,23 +22,38 @@
 #endif
 // Resident CTAs per SM asked for the forward march: 6 caps it at 80
 // registers without spills (20% more warps than the 96 it takes unbounded;
-// measured 3% faster; 7 or 8 spill and are slower).
+// measured 3% faster).  The FP32 RGB field march with x-pair records and
+// skipping (the reconstruction loop's) takes 7 (72 registers, 8 bytes
+// spilled; 1% faster than 6 with the packed-pair blend); 8 spills 72 bytes.
 #ifndef FR_FWD_MINB
 #define FR_FWD_MINB 6
 #endif
+#ifndef FR_FWD_MINB_LOOP
+#define FR_FWD_MINB_LOOP 7
+#endif
 #define FR_FWD_BOUNDS __launch_bounds__(frk::kTileThreads, FR_FWD_MINB)
+#define FR_FWD_BOUNDS_T(DT, KIND, TAU, MODE) \
+    __launch_bounds__(frk::kTileThreads, (DT) == DT_F32 && (KIND) == KIND_RGB && !(TAU) && (MODE) == 2 \
+                                             ? FR_FWD_MINB_LOOP : FR_FWD_MINB)
 // The adjustment over the flame-ray list runs one warp per CTA: a CTA's
 // resources return as soon as its 32 rays end, where a 4-warp CTA waits for
 // its longest ray (measured 6% faster).  FR_ADJ_MINB resident CTAs per SM
-// leave the compiler 96 registers (20 warps per SM); asking for 24 (80
-// registers) measures the same, 28 (72 registers) 2% slower.
+// leave the compiler 96 registers (20 warps per SM); 28 (72 registers)
+// measured 2% slower.  The FP32 field adjustment with skipping (the
+// reconstruction loop's) takes 24 (80 registers, no spill; 1% faster with
+// the packed-pair weights), the others, which would spill there, 20.
 #ifndef FR_ADJ_THREADS
 #define FR_ADJ_THREADS 32
 #endif
 #ifndef FR_ADJ_MINB
 #define FR_ADJ_MINB 20
 #endif
+#ifndef FR_ADJ_MINB_LOOP
+#define FR_ADJ_MINB_LOOP 24
+#endif
 #define FR_ADJ_LIST_BOUNDS __launch_bounds__(FR_ADJ_THREADS, FR_ADJ_MINB)
+#define FR_ADJ_LIST_BOUNDS_T(DT, TAU, SKIP) \
+    __launch_bounds__(FR_ADJ_THREADS, (DT) == DT_F32 && !(TAU) && (SKIP) ? FR_ADJ_MINB_LOOP : FR_ADJ_MINB)
 
 
 namespace frk {
@@ -504,7 +519,7 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
 }
 
 template <int DT, int KIND, bool TAU, int MODE>
-__global__ void FR_FWD_BOUNDS fwd_single(const __grid_constant__ SingleArgs a)
+__global__ void FR_FWD_BOUNDS_T(DT, KIND, TAU, MODE) fwd_single(const __grid_constant__ SingleArgs a)
 {
     fwd_body<DT, KIND, TAU, MODE, true>(a.p, a.cams, blockIdx.x);
 }
@@ -728,7 +743,8 @@ __device__ __forceinline__ void adj_body(const ProbDev& P, const CamDev* cams, i
 // past the list's end, which exit at once, cost less than a warp's wait for
 // its next chunk.)
 template <int DT, bool TAU, bool SKIP>
-__global__ void FR_ADJ_LIST_BOUNDS adj_list(const __grid_constant__ SingleArgs a, const unsigned* __restrict__ list,
+__global__ void FR_ADJ_LIST_BOUNDS_T(DT, TAU, SKIP) adj_list(const __grid_constant__ SingleArgs a,
+                                                          const unsigned* __restrict__ list,
                                          const unsigned* __restrict__ count, const float* __restrict__ tm)
 {
     const unsigned i = blockIdx.x * (unsigned)FR_ADJ_THREADS + threadIdx.x;
