@@ -973,7 +973,10 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     const NodeBox nbox = FR_NODE_BOX && pack_keep ? NodeBox{u.p.adj_box, nbx, nby, nbz} : NodeBox{};
     // the forward clips to the adjustment's box: the half rays divide the
     // samples inside it (FR_SPLIT_BOX = 0: the whole chord)
-    if (FR_SPLIT_BOX && pack_keep) f.p.split_box = u.p.split_box = 1;
+    if (FR_SPLIT_BOX && pack_keep) {
+        f.p.split_box = u.p.split_box = 1;
+        f.p.adj_box = u.p.adj_box;
+    }
     // With the box, the last in-scattering sweep writes the x-pair records and
     // the brick marks itself (the pair pack folded into it; FR_SWEEP_PACK = 0:
     // a separate pack)
@@ -1542,6 +1545,8 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         P.hull_full = full;
         P.adj_occ = hb;
         P.adj_box = hb ? brick_box(hb, nbx, nby, nbz) : nullptr;
+        // ray parts divide the samples inside the hull's box (see fr_reconstruct)
+        P.split_box = FR_SPLIT_BOX && FR_BATCH_PARTS > 1 && hb && !(p->tau > 0.0f) ? 1 : 0;
         P.cams = d_cams + cam_off;
         P.targets = q.targets;
         P.bbox = q.bbox;

@@ -75,9 +75,10 @@ struct ProbDev {
     float step, alpha_l, alpha_d, tau, g_std, thresh;
     unsigned long long seed;
     int iteration;
-    // 1: a flame ray's parts (FR_ADJ_SPLIT) divide the samples its box range
-    // keeps -- the forward's occ_box and the adjustment's adj_box, the same
-    // box -- instead of its whole chord (both marches split the same way)
+    // 1: a flame ray's parts (FR_ADJ_SPLIT) divide the samples the
+    // adjustment's box range over adj_box keeps instead of its whole chord
+    // (set only where the adjustment skips by adj_occ; the forward computes
+    // the same range to place the part boundaries)
     int split_box;
     unsigned long long* counter; // sample counter, nullable
     // batched launches only

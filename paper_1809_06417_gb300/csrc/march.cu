@@ -332,9 +332,17 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
                 if (!BrickSkip::box_range(P, P.occ_box, R, P.step, k0, k1)) k1 = 0;
             }
             int kb[kTm];
-            {
-                const bool in_box = SKIP && P.split_box;
-                const int sa = in_box ? k0 : 0, sn = in_box ? max(k1 - k0, 0) : R.n;
+            if constexpr (SPLIT && FR_ADJ_SPLIT > 1) {
+                // the part boundaries the adjustment uses: its box range
+                // (P.split_box, the adjustment's own box_range over adj_box),
+                // else the whole chord
+                int sa = 0, sn = R.n;
+                if (P.split_box) {
+                    int a0 = 0, a1 = R.n;
+                    const bool any = BrickSkip::box_range(P, P.adj_box, R, P.step, a0, a1);
+                    sa = any ? a0 : 0;
+                    sn = any ? a1 - a0 : 0;
+                }
 #pragma unroll
                 for (int j = 0; j < kTm; ++j) kb[j] = sa + sn * (j + 1) / FR_ADJ_SPLIT;
             }

@@ -394,6 +394,7 @@ extern "C" fr_status fr_server_step(fr_server* s, int* running, int* queued)
             P.hull_full = j->d.ncam >= 32 ? 0xffffffffu : ((1u << j->d.ncam) - 1u);
             P.adj_occ = j->hull_bricks;
             P.adj_box = j->hull_bricks ? brick_box(j->hull_bricks, P.nbx, P.nby, P.nbz) : nullptr;
+            P.split_box = FR_SPLIT_BOX && kServerParts > 1 && j->hull_bricks && !(P.tau > 0.0f) ? 1 : 0;
             hp[i] = P;
             for (int k = 0; k < j->d.ncam; ++k) hc[cam_off + k] = a.cams[k];
             ht[i] = tile_off;
