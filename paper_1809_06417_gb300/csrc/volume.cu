@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) apply_box_kernel(void* vol, int nx, int n
     for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const unsigned row = t / ex, x = t - row * ex, z = row / ey, y = row - z * ey;
         const long long i = ((long long)(z + lo[2]) * ny + (y + lo[1])) * nx + (x + lo[0]);
-        apply_node<DT, KIND>(vol, FR_CHK(i, nodes, 41u), dV, scale, with_sigma, clamp_nonneg, zero_dV, hull,
+        apply_node<DT, KIND>(vol, FR_CHK(i, nodes, 32u), dV, scale, with_sigma, clamp_nonneg, zero_dV, hull,
                              hull_full);
     }
 }
@@ -165,14 +165,26 @@ cudaError_t launch_apply_box(void* vol, int dt, int kind, int nx, int ny, int nz
 
 // Batched apply (paper rule, RGB records): blockIdx.y is the problem; each
 // problem's nodes are covered grid-stride.
+// FR_BATCH_BOX = 1: with the hull's brick table (the adjustment skipping by
+// it), only the nodes of its box (NodeBox): every record outside is zero and
+// no adjustment reaches it (the same restriction as the single loop's).
+#ifndef FR_BATCH_BOX
+#define FR_BATCH_BOX 1
+#endif
 template <int DT>
 __global__ void __launch_bounds__(256) apply_batch_kernel(const ProbDev* __restrict__ probs, int clamp_nonneg)
 {
     const ProbDev& P = probs[blockIdx.y];
     void* vol = P.vol_rw;
     float4* dV = reinterpret_cast<float4*>(P.dV);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P.nodes;
-         i += (long long)gridDim.x * blockDim.x) {
+    int lo[3], hi[3];
+    const NodeBox B = FR_BATCH_BOX && P.adj_occ ? NodeBox{P.adj_box, P.nbx, P.nby, P.nbz} : NodeBox{};
+    if (!node_range(B, P.nx, P.ny, P.nz, lo, hi)) return;
+    const unsigned ex = (unsigned)(hi[0] - lo[0] + 1), ey = (unsigned)(hi[1] - lo[1] + 1);
+    const unsigned total = ex * ey * (unsigned)(hi[2] - lo[2] + 1);   // volumes hold < 2^31 nodes
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const unsigned row = t / ex, xo = t - row * ex, zo = row / ey, yo = row - zo * ey;
+        const long long i = FR_CHK(((long long)(zo + lo[2]) * P.ny + (yo + lo[1])) * P.nx + (xo + lo[0]), P.nodes, 32u);
         if (P.hull && __ldg(P.hull + i) != P.hull_full) {   // outside the problem's hull: held at 0
             store_rgb<DT>(vol, i, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
             dV[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -446,15 +458,24 @@ template <int DT>
 __global__ void __launch_bounds__(256) pair_pack_batch_kernel(const ProbDev* __restrict__ probs)
 {
     const ProbDev& P = probs[blockIdx.y];
-    const long long rows = (long long)P.ny * P.nz;
     const int nx = P.nx;
     const void* src = P.vol_rw;
     void* dst = const_cast<void*>(P.pairs);
     unsigned char* occ = const_cast<unsigned char*>(P.occ);   // brick flags (cleared beforehand), or null
-    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-        const long long r0 = row * nx;
-        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-            const long long i = r0 + x, j = x < nx - 1 ? i + 1 : i;
+    // with the hull's brick table, the rows and nodes of its box only (see
+    // apply_batch_kernel): the records outside are zero, so are their pairs
+    // and marks, and the forward evaluates no cell there; the pair of the
+    // box's last x node repeats that node, zero like its neighbour
+    int lo[3], hi[3];
+    const NodeBox B = FR_BATCH_BOX && P.adj_occ ? NodeBox{P.adj_box, P.nbx, P.nby, P.nbz} : NodeBox{};
+    if (!node_range(B, P.nx, P.ny, P.nz, lo, hi)) return;
+    const int ey = hi[1] - lo[1] + 1, x_last = min(nx - 1, hi[0]);
+    const long long rows = (long long)ey * (hi[2] - lo[2] + 1);
+    for (long long rb = blockIdx.x; rb < rows; rb += gridDim.x) {
+        const int yy = lo[1] + (int)(rb % ey), zz = lo[2] + (int)(rb / ey);
+        const long long row = (long long)zz * P.ny + yy, r0 = row * nx;
+        for (int x = lo[0] + threadIdx.x; x <= hi[0]; x += blockDim.x) {
+            const long long i = FR_CHK(r0 + x, P.nodes, 32u), j = x < x_last ? i + 1 : i;
             bool nonzero;
             if constexpr (DT == DT_F32) {
                 const float4* s4 = reinterpret_cast<const float4*>(src);
