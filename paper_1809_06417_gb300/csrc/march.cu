@@ -542,14 +542,18 @@ __global__ void FR_FWD_BOUNDS_T(DT, KIND, TAU, MODE) fwd_single(const __grid_con
     fwd_body<DT, KIND, TAU, MODE, true>(a.p, a.cams, blockIdx.x);
 }
 
-// (Batched forward: capped at 80 registers like fwd_single it spills 40 bytes
-// and is still 3% faster on the video batch than with 96 registers;
-// FR_FWD_BATCH_CAP=0 leaves the registers unbounded.)
+// (Batched forward: capped at 80 registers (6 CTAs per SM) it spills and is
+// still 3% faster on the video batch than with 96 registers, and 1% faster
+// than at 72 (7 CTAs, 136 bytes spilled); FR_FWD_BATCH_CAP=0 leaves the
+// registers unbounded.)
 #ifndef FR_FWD_BATCH_CAP
 #define FR_FWD_BATCH_CAP 1
 #endif
+#ifndef FR_FWD_BATCH_MINB
+#define FR_FWD_BATCH_MINB FR_FWD_MINB
+#endif
 #if FR_FWD_BATCH_CAP
-#define FR_FWD_BATCH_BOUNDS FR_FWD_BOUNDS
+#define FR_FWD_BATCH_BOUNDS __launch_bounds__(frk::kTileThreads, FR_FWD_BATCH_MINB)
 #else
 #define FR_FWD_BATCH_BOUNDS FR_MARCH_BOUNDS
 #endif
