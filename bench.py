@@ -46,6 +46,9 @@ KERNELS_PER_STEP = 8
 # this workload (None where the kernel changed since)
 NCU_TRAFFIC = {("fwd", "f32"): 39.51e6 + 2.24e6, ("adj", "f32"): 19.64e6 + 0.0}
 NCU_INST = {("fwd", "f32"): 143.75e6, ("adj", "f32"): 192.76e6}
+# lts__throughput.avg.pct_of_peak_sustained_elapsed and
+# l1tex__throughput.avg.pct_of_peak_sustained_active of the same captures
+NCU_L2_L1 = {("fwd", "f32"): (0.0607, 0.6698), ("adj", "f32"): (0.6336, 0.7052)}
 # iterations of the step that `--profile` runs for the ncu captures
 PROFILE_ITERS = 3
 # instruction issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock
@@ -388,12 +391,12 @@ def run_ours(args, ws, rank, local):
                     compulsory={"records_read": nodes * rec, "targets_read": img_bytes,
                                 "residual_written": img_bytes},
                     gather_per_sample=8 * rec, traffic=NCU_TRAFFIC.get(("fwd", args.storage)),
-                    inst=NCU_INST.get(("fwd", args.storage))),
+                    inst=NCU_INST.get(("fwd", args.storage)), l2_l1=NCU_L2_L1.get(("fwd", args.storage))),
         "adj": dict(name="adj_list (paper-rule adjustment over half rays)", seconds=t_adj, samples=n_adj,
                     compulsory={"records_read": nodes * rec, "residual_read": img_bytes,
                                 "update_written": nodes * 12},
                     gather_per_sample=8 * sig + 8 * 16, traffic=NCU_TRAFFIC.get(("adj", args.storage)),
-                    inst=NCU_INST.get(("adj", args.storage))),
+                    inst=NCU_INST.get(("adj", args.storage)), l2_l1=NCU_L2_L1.get(("adj", args.storage))),
     }
     for K in kernels.values():
         K["compulsory_bytes"] = sum(K["compulsory"].values())
@@ -414,7 +417,11 @@ def run_ours(args, ws, rank, local):
                       "2070 MHz"},
         "l1_l2_gather": {"bytes_per_launch": K["gather_per_sample"] * K["samples"],
                          "bytes_per_sample": K["gather_per_sample"], "samples_per_launch": K["samples"],
-                         "achieved_GBps": K["gather_per_sample"] * K["samples"] / K["seconds"] / 1e9},
+                         "achieved_GBps": K["gather_per_sample"] * K["samples"] / K["seconds"] / 1e9,
+                         "l2_frac": None if K["l2_l1"] is None else K["l2_l1"][0],
+                         "l1_frac": None if K["l2_l1"] is None else K["l2_l1"][1],
+                         "source": "lts__throughput / l1tex__throughput, fractions of their peaks in the same "
+                                   "ncu capture (profiles/)"},
         "other_kernel": {"name": kernels["fwd" if dom == "adj" else "adj"]["name"],
                          "hbm_frac": kernels["fwd" if dom == "adj" else "adj"]["hbm_frac"],
                          "issue_frac": kernels["fwd" if dom == "adj" else "adj"]["issue_frac"]},
