@@ -66,7 +66,7 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
                    &c->rmse, &c->J, &c->src, &c->flame_cnt, &c->flame_list, &c->batch, &c->pairs,
                    &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr, &c->L6, &c->fin, &c->flame_tm,
-                   &c->vol_stage, &c->probe})
+                   &c->vol_stage, &c->probe, &c->flame_dl})
         if (b->p) cudaFree(b->p);
     for (void* p : c->owned) cudaFree(p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
@@ -875,6 +875,10 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
 #endif
     FR_TRY(ensure(c, c->flame_list, (size_t)nt * kTileThreads * parts * sizeof(unsigned), "flame list"));
     if (split) FR_TRY(ensure(c, c->flame_tm, (size_t)nt * kTileThreads * parts * sizeof(float), "flame list"));
+    // the flame rays' residuals beside their list entries instead of the
+    // residual image (the loop over all views at once, paper rule)
+    const bool list_dl = FR_LIST_DL && p->rule == FR_RULE_PAPER && !per_view && !pipe;
+    if (list_dl) FR_TRY(ensure(c, c->flame_dl, (size_t)nt * kTileThreads * parts * 3 * sizeof(float), "flame list"));
     FR_TRY(ensure(c, c->pairs, (size_t)nodes * 2 * rec_bytes(vol), "pairs"));
     const int nbx = bricks_along(vol->nx), nby = bricks_along(vol->ny), nbz = bricks_along(vol->nz);
     unsigned char* occ = nullptr;
@@ -943,6 +947,11 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
         FR_CUDA(c, cudaMemsetAsync(flame_cnt, 0, (size_t)iters * count_slots * sizeof(unsigned), s));
         f.p.flist = flame_list;
         f.p.flist_tm = split ? static_cast<float*>(c->flame_tm.p) : nullptr;
+        if (list_dl) {
+            f.p.flist_dl = static_cast<float*>(c->flame_dl.p);
+            f.p.residual = nullptr;
+            u.p.flist_dl = f.p.flist_dl;
+        }
     }
     const float* flame_tm = split ? static_cast<const float*>(c->flame_tm.p) : nullptr;
     const unsigned* hull = nullptr;

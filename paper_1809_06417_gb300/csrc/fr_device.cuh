@@ -115,6 +115,10 @@ struct ProbDev {
     // the transmittance at the start of the part is stored at the same list
     // position here
     float* flist_tm;
+    // when set (with flist), the residual of each listed flame ray, three
+    // floats at its list position (every part's entry), which the adjustment
+    // reads instead of the residual image
+    float* flist_dl;
     // bricks holding a key point inside the visual hull; when set, the
     // adjustment skips the others (their key points' updates are discarded)
     const unsigned char* adj_occ;

@@ -493,11 +493,19 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
             unsigned at = run_at + (unsigned)__popc(m & ((1u << lane) - 1u));
             for (int i = 0; i < w; ++i) at += wcount[i];
             P.flist[at] = (unsigned)pix;
+            if (P.flist_dl) {
+                float* q = P.flist_dl + 3 * (size_t)at;
+                q[0] = fl0; q[1] = fl1; q[2] = fl2;
+            }
             if (parts > 1u) {
 #pragma unroll
                 for (int j = 1; j <= kTm; ++j) {
                     P.flist[at + j * padded] = (unsigned)pix | ((unsigned)j << 30);
                     P.flist_tm[at + j * padded] = Tm[j - 1];
+                    if (P.flist_dl) {
+                        float* q = P.flist_dl + 3 * (size_t)(at + j * padded);
+                        q[0] = fl0; q[1] = fl1; q[2] = fl2;
+                    }
                 }
             }
         }
@@ -787,8 +795,9 @@ __global__ void FR_ADJ_LIST_BOUNDS_T(DT, TAU, SKIP) adj_list(const __grid_consta
     const unsigned r = pix - (unsigned)view * per_view;
     const int py = (int)(r / (unsigned)P.W), px = (int)(r - (unsigned)py * (unsigned)P.W);
     const int it = P.iteration + (P.iter_dev ? __ldg(P.iter_dev) : 0);
-    if (P.g_std > 0.0f) adj_ray<DT, TAU, SKIP, true>(P, a.cams, view, px, py, it, part, T0);
-    else adj_ray<DT, TAU, SKIP, false>(P, a.cams, view, px, py, it, part, T0);
+    const float* dl = P.flist_dl ? P.flist_dl + 3 * (size_t)i : nullptr;
+    if (P.g_std > 0.0f) adj_ray<DT, TAU, SKIP, true>(P, a.cams, view, px, py, it, part, T0, nullptr, dl);
+    else adj_ray<DT, TAU, SKIP, false>(P, a.cams, view, px, py, it, part, T0, nullptr, dl);
 }
 
 // Forward march and paper-rule adjustment of one tile in one kernel
@@ -890,8 +899,9 @@ __global__ void FR_ADJ_LIST_BOUNDS adj_list_tab(const __grid_constant__ SingleAr
         const unsigned r = pix - (unsigned)view * per_view;
         const int py = (int)(r / (unsigned)P.W), px = (int)(r - (unsigned)py * (unsigned)P.W);
         const int it = P.iteration + (P.iter_dev ? __ldg(P.iter_dev) : 0);
-        if (P.g_std > 0.0f) adj_ray<DT, TAU, SKIP, true, 1>(P, a.cams, view, px, py, it, part, T0, &tab);
-        else adj_ray<DT, TAU, SKIP, false, 1>(P, a.cams, view, px, py, it, part, T0, &tab);
+        const float* dl = P.flist_dl ? P.flist_dl + 3 * (size_t)i : nullptr;
+        if (P.g_std > 0.0f) adj_ray<DT, TAU, SKIP, true, 1>(P, a.cams, view, px, py, it, part, T0, &tab, dl);
+        else adj_ray<DT, TAU, SKIP, false, 1>(P, a.cams, view, px, py, it, part, T0, &tab, dl);
     }
     __syncwarp();
     for (int j = threadIdx.x; j < kTab; j += 32) {
