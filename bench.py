@@ -44,11 +44,11 @@ KERNELS_PER_STEP = 8
 # dram__bytes_read.sum + dram__bytes_write.sum and smsp__inst_executed.sum
 # (warp instructions) per launch from ncu captures of the current kernels at
 # this workload (None where the kernel changed since)
-NCU_TRAFFIC = {("fwd", "f32"): 39.51e6 + 2.24e6, ("adj", "f32"): 19.64e6 + 0.0}
-NCU_INST = {("fwd", "f32"): 143.75e6, ("adj", "f32"): 192.76e6}
+NCU_TRAFFIC = {("fwd", "f32"): 39.50e6 + 0.12e6, ("adj", "f32"): 21.44e6 + 0.0}
+NCU_INST = {("fwd", "f32"): 144.29e6, ("adj", "f32"): 192.75e6}
 # lts__throughput.avg.pct_of_peak_sustained_elapsed and
 # l1tex__throughput.avg.pct_of_peak_sustained_active of the same captures
-NCU_L2_L1 = {("fwd", "f32"): (0.0607, 0.6698), ("adj", "f32"): (0.6336, 0.7052)}
+NCU_L2_L1 = {("fwd", "f32"): (0.0535, 0.6588), ("adj", "f32"): (0.6273, 0.7070)}
 # iterations of the step that `--profile` runs for the ncu captures
 PROFILE_ITERS = 3
 # instruction issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock
@@ -377,23 +377,26 @@ def run_ours(args, ws, rank, local):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     # Roofline of the two marches.  Compulsory DRAM bytes per launch (the
     # least each must move, one pass over what it reads and writes): the
-    # forward reads the records and the targets and writes the residual; the
-    # adjustment reads the records and the residual and writes the update
-    # (three float32 per node).  The per-sample gather (8 corner records for
-    # the forward; 8 extinctions plus one 16-byte reduction per key point for
-    # the adjustment) is served by L1/L2 and reported separately.
+    # forward reads the records and the targets and writes the residual of
+    # the flame rays (the only rays the adjustment reads); the adjustment
+    # reads the records and those residuals and writes the update (three
+    # float32 per node).  The per-sample gather (8 corner records for the
+    # forward; 8 extinctions plus one 16-byte reduction per key point for the
+    # adjustment) is served by L1/L2 and reported separately.
     rec = 16 if args.storage == "f32" else 8
     sig = 4 if args.storage == "f32" else 2
     nodes = w["n"] ** 3
     img_bytes = w["views"] * w["side"] ** 2 * 12
+    flame_rays = int((I["targets"].amax(dim=-1) > p.flame_thresh).sum())
+    res_bytes = flame_rays * 12
     kernels = {
         "fwd": dict(name="fwd_single (forward march + residual)", seconds=t_fwd, samples=n_fwd,
                     compulsory={"records_read": nodes * rec, "targets_read": img_bytes,
-                                "residual_written": img_bytes},
+                                "flame_residuals_written": res_bytes},
                     gather_per_sample=8 * rec, traffic=NCU_TRAFFIC.get(("fwd", args.storage)),
                     inst=NCU_INST.get(("fwd", args.storage)), l2_l1=NCU_L2_L1.get(("fwd", args.storage))),
         "adj": dict(name="adj_list (paper-rule adjustment over half rays)", seconds=t_adj, samples=n_adj,
-                    compulsory={"records_read": nodes * rec, "residual_read": img_bytes,
+                    compulsory={"records_read": nodes * rec, "flame_residuals_read": res_bytes,
                                 "update_written": nodes * 12},
                     gather_per_sample=8 * sig + 8 * 16, traffic=NCU_TRAFFIC.get(("adj", args.storage)),
                     inst=NCU_INST.get(("adj", args.storage)), l2_l1=NCU_L2_L1.get(("adj", args.storage))),
