@@ -185,3 +185,42 @@ def test_volume_rmse_follows_oracle(orc, fr_ctx, dtype):
     # no key point compared
     got, n = ctx.fr_volume_rmse(va, vb, torch.zeros_like(tt), 3)
     assert n == 0 and np.all(got == 0.0)
+
+
+@pytest.mark.parametrize("shape", ["empty", "corner"])
+def test_reconstruct_with_degenerate_hull_follows_oracle(orc, fr_ctx, shape):
+    """Hulls at the edges of the box logic: no key point at all (the hull's box
+    is empty: the sweeps, the pack and the update have no node to cover and
+    the marches no sample) and a 3^3 block of key points at the grid's upper
+    corner (the box reaches the last node on every axis), with in-scattering,
+    against the oracle on the same tags."""
+    fr, ctx = fr_ctx
+    case = plume_case(n=36, views=6, side=64)
+    n = case.vol.shape[0]
+    P = orc.make_params(step=case.step, alpha_l=3e-3)
+    sc, img, t_ref, mask, bbox_ref = oracle_targets(orc, case)
+    full = (1 << len(case.cams)) - 1
+    hull = np.zeros(case.vol.shape[:3], dtype=np.uint32)
+    if shape == "corner":
+        hull[n - 3:, n - 3:, n - 3:] = full
+    v0 = case.vol.copy()
+    v0[..., :3] = 0.01
+    vol_ref, rmse_ref, _ = orc.reconstruct(sc, v0, P, t_ref, mask, bbox_ref, 3, hull=hull, albedo=case.albedo)
+    t_dev = torch.as_tensor(img, dtype=torch.float32, device="cuda").contiguous()
+    bbox = torch.zeros((len(case.cams), 4), dtype=torch.int32, device="cuda")
+    ctx.fr_prepare_targets(t_dev, 30 / 255, bbox)
+    v = torch.as_tensor(v0, dtype=torch.float32, device="cuda").contiguous()
+    rmse = np.zeros((3, 3), dtype=np.float32)
+    alb = torch.as_tensor(case.albedo, dtype=torch.float32, device="cuda").contiguous()
+    ctx.fr_reconstruct(fr.volume(v, case.origin, case.h), fr.cameras(case.cams), t_dev, bbox, 3,
+                       fr.params(step=case.step, alpha_l=3e-3, use_hull=1, hull_tags=tags_on_device(torch, hull)),
+                       albedo=alb, rmse=rmse)
+    torch.cuda.synchronize()
+    got = v.cpu().numpy()
+    outside = hull != full
+    assert np.all(got[outside] == 0.0)
+    np.testing.assert_allclose(rmse, rmse_ref, rtol=1e-3)
+    if shape == "corner":
+        e = rel_err(got[..., :3], vol_ref[..., :3])
+        print(f"corner hull: max {e.max():.3e}, key points {int((~outside).sum())}")
+        assert e.max() < 1e-3
