@@ -149,3 +149,48 @@ def test_video_size_batch_follows_oracle(orc):
         assert np.all(err <= bound)
         np.testing.assert_allclose(rm.cpu().numpy(), rmse_ref, rtol=1e-3)
     ctx.close()
+
+
+def test_batch_with_an_empty_hull_follows_oracle(orc):
+    """A batch whose middle problem has no key point in its hull (its box is
+    empty: the batched pack and update cover no node of it) beside two with
+    their hulls: each against orc.reconstruct on the same tags."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_cases import Case, oracle_targets, tags_on_device
+    from paper_1809_06417_gb300 import flamerec as fr, synth
+    ctx = fr.Context(0)
+    specs = [(24, 3, 40, 11), (32, 5, 56, 12), (20, 4, 33, 13)]
+    iters = 3
+    P = orc.make_params(step=0.5, alpha_l=2e-3)
+    p = fr.params(step=0.5, alpha_l=2e-3, use_hull=1)
+    refs, batch, keep = [], [], []
+    for i, (n, views, side, seed) in enumerate(specs):
+        shape, origin, h = synth.unit_grid(n)
+        cams = synth.ring_cameras(views, side, side, elevation_jitter_deg=8.0, seed=seed)
+        case = Case(shape, cams, synth.plume_volume(n, seed)[0], 0.5)
+        sc, img, t_ref, mask, bbox_ref = oracle_targets(orc, case)
+        tags = orc.visual_hull(sc, mask)
+        if i == 1:
+            tags = np.zeros_like(tags)
+        v0 = case.vol.copy()
+        v0[..., :3] *= 0.2
+        refs.append(orc.reconstruct(sc, v0, P, t_ref, mask, bbox_ref, iters, hull=tags)[:2])
+        v = torch.as_tensor(v0, dtype=torch.float32, device="cuda").contiguous()
+        t_dev = torch.as_tensor(img, dtype=torch.float32, device="cuda").contiguous()
+        bbox = torch.zeros((views, 4), dtype=torch.int32, device="cuda")
+        ctx.fr_prepare_targets(t_dev, 30 / 255, bbox)
+        rm = torch.zeros((iters, 3), device="cuda")
+        tg = tags_on_device(torch, tags)
+        keep.append((v, rm, t_dev, bbox, tg))
+        batch.append((fr.volume(v, origin, h), fr.cameras(cams), t_dev, bbox, rm, tg))
+    ctx.fr_reconstruct_batch(batch, iters, p, use_graph=True)
+    torch.cuda.synchronize()
+    for i, ((vol_ref, rmse_ref), (v, rm, *_)) in enumerate(zip(refs, keep)):
+        got = v.cpu().numpy().astype(np.float64)
+        if i == 1:
+            assert np.all(got == 0.0) and np.all(vol_ref == 0.0)
+        else:
+            assert rel_err(got[..., :3], vol_ref[..., :3]).max() < 1e-3
+        np.testing.assert_allclose(rm.cpu().numpy(), rmse_ref, rtol=1e-3)
+    ctx.close()
