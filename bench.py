@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--no-hull", action="store_true",
                     help="reconstruct the whole box instead of the visual hull (Sec. 4.3.1)")
     ap.add_argument("--no-skip", action="store_true", help="march empty bricks too (same result, slower)")
+    ap.add_argument("--profile-video", action="store_true",
+                    help="run the video batch once with the profiler range around its timed graph only "
+                         "(for ncu --profile-from-start off)")
     ap.add_argument("--profile", action="store_true",
                     help="untimed iterations of the step, for ncu captures")
     return ap.parse_args()
@@ -561,7 +564,8 @@ def run_ablation(fr, ctx, I, args, iters=20):
     return out
 
 
-def run_video(fr, ctx, frames=64, n=96, views=8, side=384, iters=20, step=0.5, seed=4, storage="f32"):
+def run_video(fr, ctx, frames=64, n=96, views=8, side=384, iters=20, step=0.5, seed=4, storage="f32",
+              profile=False):
     """Batched video frames: every frame reconstructed from its own targets,
     all frames in one batched launch per phase, the 20 iterations captured in
     one CUDA graph."""
@@ -598,10 +602,14 @@ def run_video(fr, ctx, frames=64, n=96, views=8, side=384, iters=20, step=0.5, s
     flush.fill_(1.0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()
+    if profile:
+        torch.cuda.profiler.start()
     e0.record(stream)
     ctx.fr_reconstruct_batch(probs, iters, p, use_graph=True)
     e1.record(stream)
     torch.cuda.synchronize()
+    if profile:
+        torch.cuda.profiler.stop()
     t = e0.elapsed_time(e1) / 1e3
     final = np.stack([rm[-1].cpu().numpy() for *_, rm in vols])
     return {"workload": f"video_{frames}x{n}^3_{views}x{side}^2", "frames": frames, "iters_per_frame": iters,
@@ -1004,6 +1012,13 @@ def main():
     ws, rank, local = dist_setup()
     if args.profile:
         run_profile(args)
+        return
+    if args.profile_video:
+        from paper_1809_06417_gb300 import flamerec as fr
+        ctx = fr.Context(local)
+        r = run_video(fr, ctx, storage=args.storage, profile=True)
+        print(json.dumps({"frames_per_s": r["frames_per_s"], "seconds": r["seconds"]}))
+        ctx.close()
         return
     if args.impl == "reference":
         out = run_reference(args, ws, rank)
