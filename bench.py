@@ -3,12 +3,15 @@
 Workload (default): the full-RTE setting -- a 128^3 float32 volume holding RGB
 emission, extinction and scattering albedo (seeded 8-blob plume with 4-octave
 value noise), 8 ring cameras at 512 x 512, a 0.5-voxel ray step, the paper's
-adjustment rule.  One step is one iteration of the loop: in-scattering source,
-forward march with fused residual, error reduction, adjustment, update.
+adjustment rule.  One step is one whole reconstruction of that setting: 50
+iterations (in-scattering source, rendering with fused residual, error
+reduction, adjustment, update) from the zero start in one fr_reconstruct call,
+which builds the ray weight tables first and streams them every iteration.
 
-Metric: ray samples per second, forward + adjustment, i.e. the samples both
-marches process per iteration over the iteration's device time; iterations per
-second are reported beside it.
+Metric: ray samples per second, forward + adjustment: the samples the
+iterations stand for (those the marches evaluate per iteration, times the
+iterations) over the step's device time; iterations per second are reported
+beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--storage f32|bf16]
@@ -35,22 +38,22 @@ sys.path.insert(0, ROOT)
 METRIC = "ray samples/s (fwd+adjoint) and recon iters/s at 128^3×8 views; p50/p99 job latency"
 WORKLOAD = dict(name="full_rte_128^3_8x512^2", n=128, views=8, side=512, step=0.5, seed=2,
                 alpha_l=2e-4, noise=1e-3, hull=True)
-# kernels one step (one fr_reconstruct iteration) launches: hull clear with
-# brick marks and their box, in-scatter sweeps (3, over the box of the hull's
-# bricks; the last also writes the x-pair records and the brick marks),
-# forward (which lists the flame rays), error reduction (which also writes the
-# rmse), adjustment, update (with the hull clear, over the same box)
-KERNELS_PER_STEP = 8
-# dram__bytes_read.sum + dram__bytes_write.sum and smsp__inst_executed.sum
-# (warp instructions) per launch from ncu captures of the current kernels at
-# this workload (None where the kernel changed since)
-NCU_TRAFFIC = {("fwd", "f32"): 39.50e6 + 0.12e6, ("adj", "f32"): 21.44e6 + 0.0}
-NCU_INST = {("fwd", "f32"): 144.29e6, ("adj", "f32"): 192.75e6}
+# iterations of one step (the full-RTE setting runs 50)
+ITERS_PER_STEP = 50
+# kernels one step launches: hull clear with the hull's brick marks and box;
+# the tables' build (count march, four scans of three kernels, fill march,
+# entry ends, entry sort); then per iteration the in-scatter sweeps (3, over
+# the box of the hull's bricks), the forward table's render with the
+# residual, the error reduction (which also writes the rmse) and the
+# adjustment table's update
+KERNELS_SETUP = 1 + 16
+KERNELS_PER_ITERATION = 6
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures of
+# the current kernels at this workload (None where the kernel changed since)
+NCU_TRAFFIC = {("fwd", "f32"): None, ("adj", "f32"): None}
 # lts__throughput.avg.pct_of_peak_sustained_elapsed and
 # l1tex__throughput.avg.pct_of_peak_sustained_active of the same captures
-NCU_L2_L1 = {("fwd", "f32"): (0.0535, 0.6588), ("adj", "f32"): (0.6273, 0.7070)}
-# iterations of the step that `--profile` runs for the ncu captures
-PROFILE_ITERS = 3
+NCU_L2_L1 = {("fwd", "f32"): None, ("adj", "f32"): None}
 # instruction issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock
 # at the 2070 MHz maximum SM clock, in warp instructions per second
 ISSUE_PEAK = 152 * 4 * 2.07e9
@@ -213,6 +216,7 @@ def run_ours(args, ws, rank, local):
     from paper_1809_06417_gb300 import flamerec as fr
     torch.cuda.set_device(local)
     w = WORKLOAD
+    K_IT = ITERS_PER_STEP
     ctx, I = make_inputs(args.storage, rank, local)
     p = method_params(args, I)
     vol = I["vol0"].clone()
@@ -220,17 +224,24 @@ def run_ours(args, ws, rank, local):
     cams = I["fcams"]
     stream = torch.cuda.current_stream()
     n_adj = ctx.fr_count_samples(fv, cams, p, residual=I["targets"])
-    flush = torch.empty(384 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
-
-    def step(it):
-        ctx.fr_reconstruct(fv, cams, I["targets"], I["bbox"], 1, p, albedo=I["albedo"], first_iteration=it)
-
-    for it in range(args.warmup):
-        step(it)
-    # forward samples evaluated (empty bricks of the current volume skipped),
-    # counted before and after the timed steps
+    # forward samples the marches evaluate at the zero start (empty bricks skipped)
     n_fwd_before = ctx.fr_count_samples(fv, cams, p)
+    flush = torch.empty(384 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+    rmse_dev = torch.zeros((K_IT, 3), device="cuda")
+
+    def reset(i):
+        # the job's start volume and an L2 flush, queued before the step's start event
+        vol.copy_(I["vol0"])
+        flush.fill_(float(i))
+
+    def step():
+        ctx.fr_reconstruct(fv, cams, I["targets"], I["bbox"], K_IT, p, albedo=I["albedo"], rmse=rmse_dev)
+
+    for i in range(args.warmup):
+        reset(i)
+        step()
     torch.cuda.synchronize()
+    stats = ctx.fr_table_stats()
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -238,9 +249,9 @@ def run_ours(args, ws, rank, local):
     with Clocks(local) as clk:
         t_wall = time.perf_counter()
         for i in range(args.steps):
-            flush.fill_(float(i))
+            reset(i)
             ev[i][0].record(stream)
-            step(args.warmup + i)
+            step()
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
@@ -248,63 +259,91 @@ def run_ours(args, ws, rank, local):
         dist.barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
     t_dev = dist_max(sum(ms) / 1e3)
+    rmse_step = rmse_dev.cpu().numpy()
+    n_fwd_after = ctx.fr_count_samples(fv, cams, p)
+    n_fwd = (n_fwd_before + n_fwd_after) // 2
+    n_fwd_box = ctx.fr_count_samples(fv, cams, fr.params(step=w["step"], skip_empty=0))
     # per-phase device time from a second pass of as many steps, with the
     # events the library records on this stream between its launches (kept
-    # out of the timed steps above: they cost about 2% of a step)
+    # out of the timed steps above)
     ctx.fr_trace_phases(True)
     for i in range(args.steps):
-        flush.fill_(float(i))
-        step(args.warmup + args.steps + i)
+        reset(i)
+        step()
     torch.cuda.synchronize()
     phase_ms, calls = ctx.fr_phase_times()
     ctx.fr_trace_phases(False)
     assert calls == args.steps, (calls, args.steps)
     phase_ms = {k: v / args.steps for k, v in phase_ms.items()}
     traced_ms = sum(phase_ms.values())
-    n_fwd_after = ctx.fr_count_samples(fv, cams, p)
-    n_fwd = (n_fwd_before + n_fwd_after) // 2
-    n_fwd_box = ctx.fr_count_samples(fv, cams, fr.params(step=w["step"], skip_empty=0))
+    t_fwd, t_adj = phase_ms["forward"] / K_IT / 1e3, phase_ms["adjust"] / K_IT / 1e3
+    t_setup = phase_ms["setup"] / 1e3
 
-    t_fwd, t_adj = phase_ms["forward"] / 1e3, phase_ms["adjust"] / 1e3
+    # the same job marching every iteration (fr_params.tables = 1), one timed
+    # call after a warm-up, with its phases
+    pm = method_params(args, I)
+    pm.tables = 1
+    reset(0)
+    ctx.fr_reconstruct(fv, cams, I["targets"], I["bbox"], 2, pm, albedo=I["albedo"])
+    reset(1)
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    ctx.fr_reconstruct(fv, cams, I["targets"], I["bbox"], K_IT, pm, albedo=I["albedo"])
+    m1.record(stream)
+    torch.cuda.synchronize()
+    march_ms = m0.elapsed_time(m1)
+    reset(2)
+    ctx.fr_trace_phases(True)
+    ctx.fr_reconstruct(fv, cams, I["targets"], I["bbox"], K_IT, pm, albedo=I["albedo"])
+    torch.cuda.synchronize()
+    march_phase, _ = ctx.fr_phase_times()
+    ctx.fr_trace_phases(False)
+    marching = {"ms_per_step": march_ms, "ms_per_iteration": march_ms / K_IT,
+                "phase_ms_per_iteration": {k: v / K_IT for k, v in march_phase.items()},
+                "note": "the same 50-iteration job with fr_params.tables = 1: the forward march and the "
+                        "paper-rule adjustment over half rays every iteration"}
 
-    # end to end through the C ABI with host buffers, every step: the volume
-    # (float32 records, pinned host memory) uploaded into a library-held volume
-    # of the storage type, the pinned host targets copied in by fr_reconstruct,
-    # the RMSE and the updated volume read back (the next step uploads it
-    # again).  The job's constants (albedo, flame boxes, hull tags) stay on the
-    # device.
+    # end to end through the C ABI with host buffers, every step: the start
+    # volume (float32 records, pinned host memory) uploaded into a
+    # library-held volume of the storage type, the pinned host targets copied
+    # in by fr_reconstruct, the per-iteration RMSE and the reconstructed volume
+    # read back.  The job's constants (albedo, flame boxes, hull tags) stay on
+    # the device.
     vol_host = torch.as_tensor(I["vol0"].float().cpu()).pin_memory()
     vol_host_np = vol_host.numpy()
+    out_host = torch.empty_like(vol_host).pin_memory()
+    out_host_np = out_host.numpy()
     tgt_host = I["targets"].cpu().pin_memory()
-    rmse_host = np.zeros((1, 3), dtype=np.float32)
+    rmse_host = np.zeros((K_IT, 3), dtype=np.float32)
     lv = ctx.fr_volume_create((w["n"],) * 3, I["origin"], I["h"],
                               dtype=fr.FR_F32 if args.storage == "f32" else fr.FR_BF16)
 
-    def e2e_step(it):
+    def e2e_step():
         ctx.fr_volume_upload(lv, vol_host_np)
-        ctx.fr_reconstruct(lv, cams, tgt_host, I["bbox"], 1, p, albedo=I["albedo"], first_iteration=it,
-                           rmse=rmse_host, targets_are_host=True)
-        ctx.fr_volume_download(lv, vol_host_np)
+        ctx.fr_reconstruct(lv, cams, tgt_host, I["bbox"], K_IT, p, albedo=I["albedo"], rmse=rmse_host,
+                           targets_are_host=True)
+        ctx.fr_volume_download(lv, out_host_np)
 
-    for it in range(2):
-        e2e_step(it)
+    for _ in range(2):
+        e2e_step()
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     t0 = time.perf_counter()
-    for it in range(args.steps):
-        e2e_step(2 + it)
+    for _ in range(args.steps):
+        e2e_step()
     torch.cuda.synchronize()
     t_e2e = dist_max(time.perf_counter() - t0)
+    e2e_same = bool(np.allclose(out_host_np, vol.float().cpu().numpy(), rtol=0, atol=1e-4 * float(vol.abs().max())))
     ctx.fr_volume_free(lv)
     e2e_h2d = int(vol_host.numel() * 4 + I["targets"].numel() * 4)
-    e2e_d2h = int(vol_host.numel() * 4 + 12)
+    e2e_d2h = int(vol_host.numel() * 4 + K_IT * 12)
 
-    # reconstruction quality after the timed iterations (context for the number)
-    rmse_now = np.zeros((1, 3), dtype=np.float32)
-    ctx.fr_reconstruct(fv, cams, I["targets"], I["bbox"], 1, p, albedo=I["albedo"],
-                       first_iteration=args.warmup + 2 * args.steps, rmse=rmse_now)
+    # reconstruction quality after the job (context for the number)
+    reset(0)
+    step()
     torch.cuda.synchronize()
+    rmse_now = rmse_dev.cpu().numpy()[-1:]
 
     # volume data error inside the hull (Sec. 5.1) against the ground truth's
     # emission on the targets' scale (the targets were divided by `scale`)
@@ -370,7 +409,7 @@ def run_ours(args, ws, rank, local):
     storage_cmp = run_storage_comparison(fr, ctx, I, args) if not args.no_extras or args.storage_section else None
     ablation = run_ablation(fr, ctx, I, args)
 
-    samples_step = n_fwd + n_adj
+    samples_step = (n_fwd + n_adj) * K_IT
     value = weak_value(ws, samples_step, args.steps, t_dev)
     peaks = {}
     try:
@@ -378,65 +417,52 @@ def run_ours(args, ws, rank, local):
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    # Roofline of the two marches.  Compulsory DRAM bytes per launch (the
-    # least each must move, one pass over what it reads and writes): the
-    # forward reads the records and the targets and writes the residual of
-    # the flame rays (the only rays the adjustment reads); the adjustment
-    # reads the records and those residuals and writes the update (three
-    # float32 per node).  The per-sample gather (8 corner records for the
-    # forward; 8 extinctions plus one 16-byte reduction per key point for the
-    # adjustment) is served by L1/L2 and reported separately.
+    # Roofline of the two per-iteration kernels.  Algorithmic bytes per launch
+    # (one pass over what each must read and write): the forward reads its
+    # table (8-byte entries, 0.4 GB: it cannot stay in L2 and streams from
+    # HBM every iteration), the source records and the targets, and writes
+    # each flame ray's residual (16 bytes); the adjustment reads its table,
+    # the residuals, the hull's entry ends and key points (8 bytes each) and
+    # reads and writes the hull's records.
     rec = 16 if args.storage == "f32" else 8
-    sig = 4 if args.storage == "f32" else 2
     nodes = w["n"] ** 3
     img_bytes = w["views"] * w["side"] ** 2 * 12
-    flame_rays = int((I["targets"].amax(dim=-1) > p.flame_thresh).sum())
-    res_bytes = flame_rays * 12
+    f_ent, a_ent, n_flame, n_hull = (stats["forward_entries"], stats["adjustment_entries"], stats["flame_rays"],
+                                     stats["hull_key_points"])
     kernels = {
-        "fwd": dict(name="fwd_single (forward march + residual)", seconds=t_fwd, samples=n_fwd,
-                    compulsory={"records_read": nodes * rec, "targets_read": img_bytes,
-                                "flame_residuals_written": res_bytes},
-                    gather_per_sample=8 * rec, traffic=NCU_TRAFFIC.get(("fwd", args.storage)),
-                    inst=NCU_INST.get(("fwd", args.storage)), l2_l1=NCU_L2_L1.get(("fwd", args.storage))),
-        "adj": dict(name="adj_list (paper-rule adjustment over half rays)", seconds=t_adj, samples=n_adj,
-                    compulsory={"records_read": nodes * rec, "flame_residuals_read": res_bytes,
-                                "update_written": nodes * 12},
-                    gather_per_sample=8 * sig + 8 * 16, traffic=NCU_TRAFFIC.get(("adj", args.storage)),
-                    inst=NCU_INST.get(("adj", args.storage)), l2_l1=NCU_L2_L1.get(("adj", args.storage))),
+        "fwd": dict(name="tab_forward_kernel (forward table: render + residual)", seconds=t_fwd,
+                    compulsory={"forward_table_read": 8 * f_ent, "records_read": nodes * rec,
+                                "targets_read": img_bytes, "flame_residuals_written": 16 * n_flame},
+                    traffic=NCU_TRAFFIC.get(("fwd", args.storage)), l2_l1=NCU_L2_L1.get(("fwd", args.storage))),
+        "adj": dict(name="tab_adjust_kernel (adjustment table: paper-rule update, Eqs. 10-11)", seconds=t_adj,
+                    compulsory={"adjustment_table_read": 8 * a_ent, "flame_residuals_read": 16 * n_flame,
+                                "hull_lists_read": 8 * n_hull, "hull_records_read_written": 2 * rec * n_hull},
+                    traffic=NCU_TRAFFIC.get(("adj", args.storage)), l2_l1=NCU_L2_L1.get(("adj", args.storage))),
     }
     for K in kernels.values():
         K["compulsory_bytes"] = sum(K["compulsory"].values())
-        K["hbm_frac"] = K["compulsory_bytes"] / K["seconds"] / 1e9 / hbm_peak
-        K["issue_frac"] = None if K["inst"] is None else K["inst"] / K["seconds"] / ISSUE_PEAK
+        K["hbm_frac"] = K["compulsory_bytes"] / K["seconds"] / 1e9 / hbm_peak if K["seconds"] > 0 else None
     dom = max(kernels, key=lambda k: kernels[k]["seconds"])
     K = kernels[dom]
+    other = kernels["fwd" if dom == "adj" else "adj"]
     achieved = K["compulsory_bytes"] / K["seconds"] / 1e9
     roofline = {
         "bound": "hbm", "kernel": K["name"], "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
         "frac": achieved / hbm_peak, "traffic": K["traffic"],
         "algorithmic_bytes_per_launch": K["compulsory_bytes"], "algorithmic_bytes": K["compulsory"],
+        "launch_ms": 1e3 * K["seconds"], "launches_per_step": K_IT,
         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s",
-        "limiter": None if K["inst"] is None else {
-            "bound": "issue", "frac": K["issue_frac"], "warp_instructions_per_launch": K["inst"],
-            "achieved_per_s": K["inst"] / K["seconds"], "peak_per_s": ISSUE_PEAK,
-            "source": "smsp__inst_executed.sum of one ncu capture (profiles/); peak 152 SMs x 4 schedulers x "
-                      "2070 MHz"},
-        "l1_l2_gather": {"bytes_per_launch": K["gather_per_sample"] * K["samples"],
-                         "bytes_per_sample": K["gather_per_sample"], "samples_per_launch": K["samples"],
-                         "achieved_GBps": K["gather_per_sample"] * K["samples"] / K["seconds"] / 1e9,
-                         "l2_frac": None if K["l2_l1"] is None else K["l2_l1"][0],
-                         "l1_frac": None if K["l2_l1"] is None else K["l2_l1"][1],
-                         "source": "lts__throughput / l1tex__throughput, fractions of their peaks in the same "
-                                   "ncu capture (profiles/)"},
-        "other_kernel": {"name": kernels["fwd" if dom == "adj" else "adj"]["name"],
-                         "hbm_frac": kernels["fwd" if dom == "adj" else "adj"]["hbm_frac"],
-                         "issue_frac": kernels["fwd" if dom == "adj" else "adj"]["issue_frac"]},
-        "note": "achieved = compulsory DRAM bytes of one launch over its event-timed duration; the 128^3 "
-                "records, the images and the update stay in the 129 MB L2 between kernels, so the DRAM "
-                "traffic ncu measures per launch (`traffic`) is below even those bytes, and the marches are "
-                "bound by instruction issue (`limiter`), not by HBM; the per-sample gathers (`l1_l2_gather`) "
-                "are served by L1 and L2",
+        "l2_l1_frac": K["l2_l1"],
+        "other_kernel": {"name": other["name"], "hbm_frac": other["hbm_frac"], "launch_ms": 1e3 * other["seconds"],
+                         "algorithmic_bytes_per_launch": other["compulsory_bytes"], "traffic": other["traffic"]},
+        "tables": {"forward_entries": f_ent, "adjustment_entries": a_ent, "flame_rays": n_flame,
+                   "hull_key_points": n_hull, "bytes": 8 * (f_ent + a_ent) + 16 * n_flame,
+                   "build_ms_per_step": 1e3 * t_setup},
+        "note": "achieved = algorithmic bytes of one launch (tables, records, images, residuals) over its "
+                "event-timed duration against the measured HBM copy bandwidth; the tables stream from HBM "
+                "every iteration, the 128^3 records stay in the 129 MB L2",
     }
+    launches = KERNELS_SETUP + KERNELS_PER_ITERATION * K_IT if f_ent else None
 
     out = {
         "metric": METRIC,
@@ -454,21 +480,29 @@ def run_ours(args, ws, rank, local):
         "config": {"workload": w["name"], "grid": [w["n"]] * 3, "views": w["views"], "image": [w["side"]] * 2,
                    "step_vox": w["step"], "storage": args.storage, "rule": "paper", "scattering": True,
                    "visual_hull": bool(p.use_hull), "skip_empty_bricks": bool(p.skip_empty),
-                   "l2": "flushed before every timed step (384 MiB write)", "parallelism": f"replicas{ws}"},
-        "recon_iters_per_s": ws * args.steps / t_dev,
-        "samples_per_step": {"fwd": n_fwd, "adj": n_adj, "fwd_before": n_fwd_before, "fwd_after": n_fwd_after,
-                             "fwd_all_in_box": n_fwd_box},
-        "kernel_ms": {"fwd_residual": 1e3 * t_fwd, "adjust": 1e3 * t_adj},
+                   "iterations_per_step": K_IT, "ray_weight_tables": bool(f_ent),
+                   "l2": "flushed before every timed step (384 MiB write); inside a step the ray weight tables "
+                         "(larger than L2) stream from HBM every iteration",
+                   "parallelism": f"replicas{ws}"},
+        "recon_iters_per_s": ws * args.steps * K_IT / t_dev,
+        "ms_per_iteration": 1e3 * t_dev / args.steps / K_IT,
+        "samples_per_iteration": {"fwd": n_fwd, "adj": n_adj, "fwd_before": n_fwd_before, "fwd_after": n_fwd_after,
+                                  "fwd_all_in_box": n_fwd_box,
+                                  "note": "the samples the marches evaluate per iteration (empty bricks skipped); "
+                                          "the tables hold the same samples' weights per ray and key point"},
+        "kernel_ms": {"fwd_residual": 1e3 * t_fwd, "adjust_update": 1e3 * t_adj, "tables_build": 1e3 * t_setup},
         "phase_ms_per_step": phase_ms,
         "traced_ms_per_step": traced_ms,
+        "marching": marching,
         "e2e": {"value": weak_value(ws, samples_step, args.steps, t_e2e), "unit": "samples/s",
                 "h2d_bytes_per_step": e2e_h2d, "d2h_bytes_per_step": e2e_d2h,
-                "ms_per_step": 1e3 * t_e2e / args.steps,
-                "path": "fr_volume_upload (float32 host records) -> fr_reconstruct (host targets, host rmse) "
-                        "-> fr_volume_download (float32 host records), pinned host memory, every step"},
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
+                "ms_per_step": 1e3 * t_e2e / args.steps, "same_volume_as_device_path": e2e_same,
+                "path": "fr_volume_upload (float32 host records) -> fr_reconstruct (50 iterations, host targets, "
+                        "host rmse) -> fr_volume_download (float32 host records), pinned host memory, every step"},
+        "gpu_launches": None if launches is None else launches * args.steps,
         "roofline": roofline,
         "clocks": clk.summary(),
+        "rmse_first": [float(x) for x in rmse_step[0]],
         "rmse_after": [float(x) for x in rmse_now[0]],
         "until_converged": until,
         "visual_hull": {"ms": hull_ms, "views": w["views"], "grid": [w["n"]] * 3, "image": [w["side"]] * 2,
@@ -478,7 +512,7 @@ def run_ours(args, ws, rank, local):
         "ablation": ablation,
         "volume_rmse_in_hull": {"rmse": [float(x) for x in v_rmse], "key_points": v_n,
                                 "relative_to_max": [float(x) / ref_max for x in v_rmse],
-                                "after_iterations": args.warmup + 2 * args.steps + 1},
+                                "after_iterations": K_IT},
         "wall_s": t_wall,
     }
     ctx.close()
@@ -530,18 +564,20 @@ def run_storage_comparison(fr, ctx, I, args, iters=50):
     return out
 
 
-def run_ablation(fr, ctx, I, args, iters=20):
-    """Per-iteration time of the step with parts of the method's restrictions
-    turned off, beside the headline: without empty-brick skipping (same
-    result, every sample in the box evaluated) and without the visual hull
-    (the whole box reconstructed).  One fr_reconstruct call of `iters`
-    iterations each from the zero start, timed with CUDA events."""
+def run_ablation(fr, ctx, I, args, iters=ITERS_PER_STEP):
+    """Per-iteration time of the step with parts of the method turned off,
+    beside the headline: marching every iteration instead of the ray weight
+    tables (same result up to float32 rounding), without empty-brick skipping
+    (the marches then evaluate every sample in the box; the tables need the
+    hull's bricks) and without the visual hull (the whole box reconstructed).
+    One fr_reconstruct call of `iters` iterations each from the zero start,
+    timed with CUDA events."""
     import torch
     w = WORKLOAD
     stream = torch.cuda.current_stream()
     out = {}
-    for name, kw in (("default", {}), ("no_skip", dict(skip_empty=0)), ("no_hull", dict(use_hull=0)),
-                     ("no_hull_no_skip", dict(use_hull=0, skip_empty=0))):
+    for name, kw in (("default", {}), ("no_tables", dict(tables=1)), ("no_skip", dict(skip_empty=0)),
+                     ("no_hull", dict(use_hull=0)), ("no_hull_no_skip", dict(use_hull=0, skip_empty=0))):
         p = fr.params(step=w["step"], alpha_l=w["alpha_l"], use_hull=1, hull_tags=I["tags"], skip_empty=1)
         for k, v in kw.items():
             setattr(p, k, v)
@@ -958,23 +994,23 @@ def cpu_baseline(full_iters=3):
 
 
 def run_profile(args):
-    """The command the ncu captures use: the workload's inputs, then
-    PROFILE_ITERS iterations of the benchmarked step (one fr_reconstruct
-    iteration each, the same launches as a timed step), no timing or L2 flush.
-    Launches: make_inputs renders the ground truth once (fwd_single) and
-    computes the hull; each iteration then launches KERNELS_PER_STEP kernels."""
+    """The command the ncu captures use: the workload's inputs, then one
+    benchmarked step (one fr_reconstruct call of ITERS_PER_STEP iterations,
+    the same launches as a timed step), no timing or L2 flush.  Launches:
+    make_inputs renders the ground truth once (fwd_single) and computes the
+    hull; the step then launches KERNELS_SETUP kernels and
+    KERNELS_PER_ITERATION per iteration."""
     import torch
     from paper_1809_06417_gb300 import flamerec as fr
     ctx, I = make_inputs(args.storage, 0, 0)
     p = method_params(args, I)
     vol = I["vol0"].clone()
     fv = fr.volume(vol, I["origin"], I["h"])
-    rmse = np.zeros((1, 3), dtype=np.float32)
-    for it in range(PROFILE_ITERS):
-        ctx.fr_reconstruct(fv, I["fcams"], I["targets"], I["bbox"], 1, p, albedo=I["albedo"], first_iteration=it,
-                           rmse=rmse)
+    rmse = np.zeros((ITERS_PER_STEP, 3), dtype=np.float32)
+    ctx.fr_reconstruct(fv, I["fcams"], I["targets"], I["bbox"], ITERS_PER_STEP, p, albedo=I["albedo"], rmse=rmse)
     torch.cuda.synchronize()
-    print(json.dumps({"profile": "ok", "iterations": PROFILE_ITERS, "rmse_last": [float(x) for x in rmse[0]]}))
+    print(json.dumps({"profile": "ok", "iterations": ITERS_PER_STEP, "rmse_last": [float(x) for x in rmse[-1]],
+                      "tables": ctx.fr_table_stats()}))
     ctx.close()
 
 

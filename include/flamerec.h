@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define FR_ABI_VERSION 2
+#define FR_ABI_VERSION 3
 #define FR_MAX_VIEWS 32          /* cameras per problem */
 
 typedef enum fr_status {
@@ -121,7 +121,20 @@ typedef struct fr_params {
                             from the volume's centre to its camera */
     int32_t sequential_views; /* fr_reconstruct: 1 = update the volume after each view in turn
                             (Kaczmarz order; the source is recomputed before each view) */
+    int32_t tables;      /* fr_reconstruct, paper rule with the visual hull, skip_empty, field mode
+                            (tau <= 0), g_std = 0, all views at once: the extinction stays fixed and
+                            G(s) = 1, so rendering (Eqs. 5-8) and the adjustment (Eq. 10) are linear
+                            maps whose weights do not change between iterations.  0: build them once
+                            per call (two marches over every ray) and stream them each iteration when
+                            the call runs at least FR_TABLES_MIN_ITERS iterations; 1: never (march
+                            every iteration); 2: whenever they apply.  Where they do not apply, or
+                            their device memory would pass the scratch limit, the marches run.  The
+                            results are those of the marches up to float32 rounding (summation order) */
 } fr_params;
+
+/* Iterations from which fr_reconstruct builds the ray weight tables when
+ * fr_params.tables is 0. */
+#define FR_TABLES_MIN_ITERS 4
 
 typedef struct fr_ctx fr_ctx;
 
@@ -498,6 +511,15 @@ fr_status fr_trace_phases(fr_ctx *ctx, int on);
  * number of those calls; then drops the record.  FR_ERANGE when more than
  * 65536 events went unread (the later ones were not recorded). */
 fr_status fr_phase_times(fr_ctx *ctx, float *ms, int n, int32_t *calls);
+
+/* Sizes of the ray weight tables the context's last fr_reconstruct or
+ * fr_reconstruct_until call built (fr_params.tables; all 0 when that call
+ * marched): stats[0] forward entries (one per ray and key point of the hull
+ * it samples, padded to whole rows of 32 rays; 8 bytes each), stats[1]
+ * adjustment entries (one per flame ray and key point; 8 bytes each),
+ * stats[2] flame rays, stats[3] key points inside the hull.  Host only; no
+ * device work. */
+fr_status fr_table_stats(const fr_ctx *ctx, uint64_t stats[4]);
 
 /* Number of samples (segments) the rays of `cams` take through the volume's
  * box: all rays when residual is NULL (one render; when p->skip_empty applies,

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libflamerec.so")
 # the checked build (bounds checks recorded in a device word): its own objects and library
 LIB_CHECKED = os.path.join(BUILD, "checked", "libflamerec_checked.so")
-SOURCES = ["march.cu", "volume.cu", "api.cu", "server.cu"]
+SOURCES = ["march.cu", "volume.cu", "api.cu", "server.cu", "tables.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

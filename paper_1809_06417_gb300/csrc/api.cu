@@ -66,7 +66,7 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
                    &c->rmse, &c->J, &c->src, &c->flame_cnt, &c->flame_list, &c->batch, &c->pairs,
                    &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr, &c->L6, &c->fin, &c->flame_tm,
-                   &c->vol_stage, &c->probe, &c->flame_dl})
+                   &c->vol_stage, &c->probe, &c->flame_dl, &c->tab_small, &c->tab_fwd, &c->tab_adj, &c->tab_dl})
         if (b->p) cudaFree(b->p);
     for (void* p : c->owned) cudaFree(p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
@@ -100,7 +100,9 @@ extern "C" fr_status fr_check_word(fr_ctx* c, uint32_t* word, int reset)
     unsigned a = 0, b = 0;
     FR_CUDA(c, check_word_march(&a, reset != 0));
     FR_CUDA(c, check_word_volume(&b, reset != 0));
-    *word = a | b;
+    unsigned t = 0;
+    FR_CUDA(c, check_word_tables(&t, reset != 0));
+    *word = a | b | t;
     return FR_OK;
 }
 
@@ -726,6 +728,13 @@ extern "C" fr_status fr_phase_times(fr_ctx* c, float* ms, int n, int32_t* calls)
     return FR_OK;
 }
 
+extern "C" fr_status fr_table_stats(const fr_ctx* c, uint64_t stats[4])
+{
+    if (!c || !stats) return FR_EINVAL;
+    for (int i = 0; i < 4; ++i) stats[i] = c->tab_stats[i];
+    return FR_OK;
+}
+
 extern "C" fr_status fr_count_samples(fr_ctx* c, const fr_volume* vol, const fr_camera* cams, int ncam,
                                       const fr_params* p, const float* residual, int64_t* samples)
 {
@@ -799,6 +808,96 @@ extern "C" fr_status fr_visual_hull(fr_ctx* c, const fr_volume* vol, const fr_ca
 // The loop of fr_reconstruct (stop_delta < 0: exactly `iters` iterations) and
 // of fr_reconstruct_until (stop_delta >= 0: at most `iters` iterations, ended
 // on the device by the stop criterion inside a conditional CUDA graph).
+// The ray weight tables of a reconstruction (tables.cu): the count pass, the
+// scans (whose totals the host reads, to size the entries), the fill pass.
+// f: the problem (cameras, targets) with the hull's brick table; records: the
+// volume whose extinction fixes the transmittance.  built stays false, with
+// nothing launched after the count pass's scratch, when the tables would
+// pass the context's scratch limit or 2^32 entries (the marches then run).
+static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* vol, const unsigned* tags,
+                              unsigned full, int nt, TabIter& it, bool& built)
+{
+    built = false;
+    const long long nodes = node_count(vol);
+    const long long nw = (long long)nt * (kTileThreads / 32);
+    const size_t nb = tab_scan_blocks(nodes > nw ? nodes : nw);
+    size_t at = 0;
+    auto carve = [&](size_t bytes) {
+        const size_t o = at;
+        at += align256(bytes);
+        return o;
+    };
+    const size_t o_wrows = carve(nw * 4), o_woff = carve(nw * 4), o_tfl = carve((size_t)nt * 4),
+                 o_tfoff = carve((size_t)nt * 4), o_ncnt = carve((size_t)nodes * 4),
+                 o_hnode = carve((size_t)nodes * 4), o_hend = carve((size_t)nodes * 4), o_bsum = carve(nb * 8),
+                 o_tot = carve(4 * 8);
+    fr_status st = ensure(c, c->tab_small, at, "table counts");
+    if (st == FR_ENOMEM) {
+        c->err[0] = '\0';
+        return FR_OK;
+    }
+    FR_TRY(st);
+    char* base = static_cast<char*>(c->tab_small.p);
+    TabBuild b{};
+    b.tags = tags;
+    b.full = full;
+    b.wrows = reinterpret_cast<unsigned*>(base + o_wrows);
+    b.woff = reinterpret_cast<unsigned*>(base + o_woff);
+    b.tfl = reinterpret_cast<unsigned*>(base + o_tfl);
+    b.tfoff = reinterpret_cast<unsigned*>(base + o_tfoff);
+    b.ncnt = reinterpret_cast<unsigned*>(base + o_ncnt);
+    b.hnode = reinterpret_cast<unsigned*>(base + o_hnode);
+    unsigned* hend = reinterpret_cast<unsigned*>(base + o_hend);
+    unsigned long long* totals = reinterpret_cast<unsigned long long*>(base + o_tot);
+    static thread_local SingleArgs bf;
+    bf = f;
+    bf.p.vol = vol->data;
+    cudaStream_t s = c->stream;
+    FR_CUDA(c, cudaMemsetAsync(b.ncnt, 0, (size_t)nodes * 4, s));
+    FR_CUDA(c, launch_tab_count(bf, b, vol->dtype, nt, s));
+    FR_CUDA(c, launch_tab_scans(b, nt, nodes, reinterpret_cast<unsigned long long*>(base + o_bsum), totals, s));
+    static_assert(kHostScratchBytes >= 32, "host scratch holds the four totals");
+    FR_CUDA(c, cudaMemcpyAsync(c->host_counter, totals, 32, cudaMemcpyDeviceToHost, s));
+    FR_CUDA(c, cudaStreamSynchronize(s));
+    unsigned long long tot[4];
+    memcpy(tot, c->host_counter, sizeof tot);
+    const unsigned long long rows = tot[0], nflame = tot[1], nadj = tot[2], nhull = tot[3];
+    if (rows * 32 >= (1ull << 32) || nadj >= (1ull << 32)) return FR_OK;
+    st = ensure(c, c->tab_fwd, (size_t)rows * 32 * 8, "forward table");
+    if (st == FR_OK) st = ensure(c, c->tab_adj, (size_t)nadj * 8, "adjustment table");
+    if (st == FR_OK) st = ensure(c, c->tab_dl, (size_t)nflame * 16, "flame residuals");
+    if (st == FR_ENOMEM) {
+        c->err[0] = '\0';
+        return FR_OK;
+    }
+    FR_TRY(st);
+    b.efwd = static_cast<uint2*>(c->tab_fwd.p);
+    b.eadj = static_cast<uint2*>(c->tab_adj.p);
+    b.nadj = nadj;
+    b.nhull = (unsigned)nhull;
+    FR_CUDA(c, launch_tab_fill(bf, b, vol->dtype, nt, s));
+    FR_CUDA(c, launch_tab_hend(b.hnode, b.ncnt, (unsigned)nhull, hend, s));
+    FR_CUDA(c, launch_tab_sort(b.eadj, hend, (unsigned)nhull, s));
+    it = TabIter{};
+    it.wrows = b.wrows;
+    it.woff = b.woff;
+    it.tfoff = b.tfoff;
+    it.efwd = b.efwd;
+    it.eadj = b.eadj;
+    it.hnode = b.hnode;
+    it.hend = hend;
+    it.dl = static_cast<float4*>(c->tab_dl.p);
+    it.nhull = (unsigned)nhull;
+    it.nflame = (unsigned)nflame;
+    it.nadj = (unsigned)nadj;
+    c->tab_stats[0] = rows * 32;
+    c->tab_stats[1] = nadj;
+    c->tab_stats[2] = nflame;
+    c->tab_stats[3] = nhull;
+    built = true;
+    return FR_OK;
+}
+
 static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo, const fr_camera* cams, int ncam,
                                   const float* targets, int targets_are_host, const int32_t* bbox, int iters,
                                   int first_iteration, const fr_params* p, float* rmse, int rmse_is_host,
@@ -993,6 +1092,22 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
                            sweeps_take_box(vol->nx, vol->ny, vol->nz);
     const PackOut pk = fold_pack ? PackOut{c->pairs.p, occ} : PackOut{};
     const size_t occ_bytes = brick_table_bytes(vol->nx, vol->ny, vol->nz);
+    // The ray weight tables in place of the two marches (fr_params.tables):
+    // paper rule, RGB records, the hull's brick table (skip_empty, field
+    // mode), G(s) = 1 and all views at once.
+    TabIter tab{};
+    bool tables = false;
+    memset(c->tab_stats, 0, sizeof c->tab_stats);
+    if (!FR_FUSED && p->tables != 1 && p->rule == FR_RULE_PAPER && vol->kind == FR_KIND_RGB && hull &&
+        u.p.adj_occ && !(p->g_std > 0.0f) && !per_view && !pipe &&
+        (p->tables == 2 || iters >= FR_TABLES_MIN_ITERS)) {
+        static thread_local SingleArgs tb;
+        tb = f;
+        tb.p.targets = tg;
+        tb.p.adj_occ = u.p.adj_occ;
+        tb.p.adj_box = u.p.adj_box;
+        FR_TRY(build_tables(c, tb, vol, hull, full, nt, tab, tables));
+    }
     void* fin = nullptr;
     FR_TRY(fin_scratch(c, &fin));
     float* rmse_dev = static_cast<float*>(c->rmse.p);
@@ -1121,6 +1236,26 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
     auto one_iteration = [&](cudaStream_t st, int it) -> fr_status {
         if (per_view) return per_view_iteration(st, it);
         const int slot = it < 0 ? 0 : it;
+        if (tables) {
+            // in-scattering source (no x-pairs: the forward table gathers
+            // the source records), rendering and residuals from the forward
+            // table, error sums, adjustment and update of the hull's key
+            // points from the adjustment table
+            if (albedo) {
+                FR_CUDA(c, launch_scatter_source(vol->data, vol->dtype, albedo, static_cast<float*>(c->J.p),
+                                                 c->src.p, vol->dtype, vol->nx, vol->ny, vol->nz, st,
+                                                 p->skip_empty != 0, nbox, PackOut{}));
+                FR_TRY(trace_mark(c, FR_PHASE_SCATTER));
+            }
+            FR_CUDA(c, launch_tab_forward(f, tab, vol->dtype, nt, st));
+            FR_TRY(trace_mark(c, FR_PHASE_FORWARD));
+            FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * slot, st, 0, fin,
+                                       it < 0 ? nullptr : rmse_dev + 3 * slot));
+            FR_TRY(trace_mark(c, FR_PHASE_REDUCE));
+            FR_CUDA(c, launch_tab_adjust(vol->data, vol->dtype, nodes, tab, p->clamp_nonneg, st));
+            FR_TRY(trace_mark(c, FR_PHASE_ADJUST));
+            return FR_OK;
+        }
         if (albedo) {
             if (fold_pack) FR_CUDA(c, cudaMemsetAsync(occ, 0, occ_bytes, st));
             FR_CUDA(c, launch_scatter_source(vol->data, vol->dtype, albedo, static_cast<float*>(c->J.p), c->src.p,

@@ -92,6 +92,56 @@ cudaError_t launch_gather_probe(const SingleArgs& a, const unsigned* tags, unsig
 cudaError_t launch_adjust_list(const SingleArgs& a, int dt, int ntiles, const unsigned* list,
                                const unsigned* count, cudaStream_t s, const float* tm = nullptr);
 
+// tables.cu: the paper-rule loop over a fixed extinction field as a forward
+// table (per ray: key point, A) and an adjustment table (per key point of the
+// hull: flame ray, W), built by two marches over every ray.
+struct TabBuild {
+    const unsigned* tags;   // visual hull tags; key points whose tag is `full` are inside
+    unsigned full;
+    unsigned* wrows;        // per warp of the tiles: rows of its forward entries
+    unsigned* woff;         // per warp: first row
+    unsigned* tfl;          // per tile: flame rays
+    unsigned* tfoff;        // per tile: number of its first flame ray
+    unsigned* ncnt;         // per node: adjustment entries (count pass), then the next free one (fill pass)
+    unsigned* hnode;        // the hull's key points in node order
+    uint2* efwd;            // forward entries {node, A}
+    uint2* eadj;            // adjustment entries {flame ray, W}
+    unsigned long long nadj;
+    unsigned nhull;         // key points inside the hull (fill pass)
+};
+struct TabIter {
+    const unsigned* wrows;
+    const unsigned* woff;
+    const unsigned* tfoff;
+    const uint2* efwd;
+    const uint2* eadj;
+    const unsigned* hnode;
+    const unsigned* hend;   // per key point of the hull: end of its entries
+    float4* dl;             // per flame ray: its residual {r, g, b, 0}
+    unsigned nhull, nflame, nadj;
+};
+// a.p: the problem with targets, cameras and the hull's brick table
+// (adj_occ, adj_box); a.p.vol the records whose extinction fixes T.
+cudaError_t launch_tab_count(const SingleArgs& a, const TabBuild& b, int dt, int ntiles, cudaStream_t s);
+// exclusive scans of the counts: totals[0] rows, [1] flame rays, [2]
+// adjustment entries, [3] key points inside the hull (bsum:
+// tab_scan_blocks(max(nodes, warps)) words)
+cudaError_t launch_tab_scans(const TabBuild& b, int ntiles, long long nodes, unsigned long long* bsum,
+                             unsigned long long* totals, cudaStream_t s);
+size_t tab_scan_blocks(long long n);
+cudaError_t launch_tab_fill(const SingleArgs& a, const TabBuild& b, int dt, int ntiles, cudaStream_t s);
+cudaError_t launch_tab_hend(const unsigned* hnode, const unsigned* cursor, unsigned nh, unsigned* hend,
+                            cudaStream_t s);
+// each key point's adjustment entries in increasing flame-ray order
+cudaError_t launch_tab_sort(uint2* eadj, const unsigned* hend, unsigned nh, cudaStream_t s);
+// a.p.vol: the source records; targets, bbox and partials as for the forward
+// march (rendered and residual images when set)
+cudaError_t launch_tab_forward(const SingleArgs& a, const TabIter& it, int dt, int ntiles, cudaStream_t s);
+// the adjustment added to the hull's key points of vol (RGB records)
+cudaError_t launch_tab_adjust(void* vol, int dt, long long nodes, const TabIter& it, int clamp_nonneg,
+                              cudaStream_t s);
+cudaError_t check_word_tables(unsigned* word, bool reset);
+
 // volume.cu
 cudaError_t launch_apply(void* vol, int dt, int kind, long long nodes, float* dV, float scale,
                          int with_sigma, int clamp_nonneg, int zero_dV, cudaStream_t s,

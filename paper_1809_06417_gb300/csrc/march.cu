@@ -68,44 +68,6 @@ namespace frk {
 // Shared pieces
 // ---------------------------------------------------------------------------
 
-// Trilinear blend of eight parity slots with mirrored fractions gx, gy, gz.
-template <class R>
-__device__ __forceinline__ R slot_blend(const R* v, float gx, float gy, float gz);
-
-template <>
-__device__ __forceinline__ float4 slot_blend<float4>(const float4* v, float gx, float gy, float gz)
-{
-    float4 a = lerp4(v[0], v[1], gx), b = lerp4(v[2], v[3], gx);
-    float4 c = lerp4(v[4], v[5], gx), d = lerp4(v[6], v[7], gx);
-    return lerp4(lerp4(a, b, gy), lerp4(c, d, gy), gz);
-}
-
-template <>
-__device__ __forceinline__ float2 slot_blend<float2>(const float2* v, float gx, float gy, float gz)
-{
-    float2 a = lerp2(v[0], v[1], gx), b = lerp2(v[2], v[3], gx);
-    float2 c = lerp2(v[4], v[5], gx), d = lerp2(v[6], v[7], gx);
-    return lerp2(lerp2(a, b, gy), lerp2(c, d, gy), gz);
-}
-
-template <>
-__device__ __forceinline__ float slot_blend<float>(const float* v, float gx, float gy, float gz)
-{
-#if FR_PACKED
-    // the same lerps, slots t and t + 4 side by side: (a, c), (b, d), then
-    // (lerp(a, b), lerp(c, d)) and the z lerp
-    const F2 tx = f2(gx, gx), ty = f2(gy, gy);
-    const F2 ac = f2_lerp(f2(v[0], v[4]), f2(v[1], v[5]), tx);
-    const F2 bd = f2_lerp(f2(v[2], v[6]), f2(v[3], v[7]), tx);
-    const float2 e = f2_get(f2_lerp(ac, bd, ty));
-    return lerpf(e.x, e.y, gz);
-#else
-    float a = lerpf(v[0], v[1], gx), b = lerpf(v[2], v[3], gx);
-    float c = lerpf(v[4], v[5], gx), d = lerpf(v[6], v[7], gx);
-    return lerpf(lerpf(a, b, gy), lerpf(c, d, gy), gz);
-#endif
-}
-
 template <int DT, int KIND>
 struct RecOf;
 template <int DT>
@@ -205,84 +167,6 @@ __device__ __forceinline__ void stage_cell(const void* pairs, long long base, in
     }
     cp_async_commit();
 }
-
-// Skipping of flagged-off bricks along one ray.  A brick is the box of kBrick^3
-// cells [B b, min(B b + B, n - 1)] per axis (B = kBrick); `flags` holds one byte per brick
-// (non-zero: the samples in it are evaluated).
-struct BrickSkip {
-    int brick = -1;         // the brick of the last tested sample
-    bool occupied = true;   // and its flag
-
-    // Samples [k0, k1) of the ray that can lie in the box of the flagged-on
-    // bricks (box: brick-table layout); false when there are none.  Samples
-    // outside the range have their midpoint (their start, for the last,
-    // shorter segment) beyond the box by more than a 1e-3 voxel margin.
-    static __device__ __forceinline__ bool box_range(const ProbDev& P, const unsigned* box, const Ray& R,
-                                                     float step, int& k0, int& k1)
-    {
-        const unsigned hx = __ldg(box + 3), hy = __ldg(box + 4), hz = __ldg(box + 5);
-        if (hx == 0u) return false;
-        const float lo[3] = {(float)((P.nbx - (int)__ldg(box)) * kBrick), (float)((P.nby - (int)__ldg(box + 1)) * kBrick),
-                             (float)((P.nbz - (int)__ldg(box + 2)) * kBrick)};
-        const float hi[3] = {(float)min((int)hx * kBrick, P.nx - 1), (float)min((int)hy * kBrick, P.ny - 1),
-                             (float)min((int)hz * kBrick, P.nz - 1)};
-        const float o[3] = {R.p0x, R.p0y, R.p0z}, d[3] = {R.dx, R.dy, R.dz}, id[3] = {R.idx, R.idy, R.idz};
-        float tin = 0.0f, tout = R.chord;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (d[a] == 0.0f) {
-                if (o[a] < lo[a] - 1e-3f || o[a] > hi[a] + 1e-3f) return false;
-                continue;
-            }
-            const float t0 = (lo[a] - o[a]) * id[a], t1 = (hi[a] - o[a]) * id[a];
-            tin = fmaxf(tin, fminf(t0, t1));
-            tout = fminf(tout, fmaxf(t0, t1));
-        }
-        // (the 1e-3 voxel margins cover the rounding of the products by
-        // 1 / step, a few ulp of at most a few hundred sample lengths)
-        const float is = 1.0f / step;
-        k0 = max(0, (int)ceilf((tin - 1e-3f) * is - 0.5f));
-        k1 = min(R.n, (int)floorf((tout + 1e-3f) * is) + 1);
-        return k0 < k1;
-    }
-
-    // True when sample k (midpoint x, y, z) lies in a flagged-off brick.  k
-    // then moves so that the loop's increment lands on the first sample whose
-    // midpoint may lie beyond that brick; a 1e-3 voxel margin on the exit
-    // keeps rounding on the safe side.
-    __device__ __forceinline__ bool empty(const unsigned char* flags, const ProbDev& P, const Ray& R, float step,
-                                          float x, float y, float z, int& k)
-    {
-        return empty_at(flags, P, R, step, cell_ijk(x, y, z, P.nx, P.ny, P.nz), k);
-    }
-
-    // The same for the sample's cell c.
-    __device__ __forceinline__ bool empty_at(const unsigned char* flags, const ProbDev& P, const Ray& R, float step,
-                                             const CellIJK& c, int& k)
-    {
-        const int b = ((c.k >> kBrickShift) * P.nby + (c.j >> kBrickShift)) * P.nbx + (c.i >> kBrickShift);
-        {
-            // the flag reloaded by a predicated load when the brick changes
-            // (no branch: 0.5-2% faster in the marches)
-            unsigned f = occupied ? 1u : 0u;
-            const unsigned need = b != brick ? 1u : 0u;
-            const unsigned char* fp = flags + FR_CHK(b, (long long)P.nbx * P.nby * P.nbz, 16u);
-            asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.u8 %0, [%1];\n\t}"
-                : "+r"(f) : "l"(fp), "r"(need));
-            brick = b;
-            occupied = f != 0u;
-        }
-        if (occupied) return false;
-        const int bx = c.i & ~(kBrick - 1), by = c.j & ~(kBrick - 1), bz = c.k & ~(kBrick - 1);
-        float te = INFINITY;
-        if (R.dx != 0.0f) te = fminf(te, ((R.dx > 0.0f ? (float)min(bx + kBrick, P.nx - 1) : (float)bx) - R.p0x) * R.idx);
-        if (R.dy != 0.0f) te = fminf(te, ((R.dy > 0.0f ? (float)min(by + kBrick, P.ny - 1) : (float)by) - R.p0y) * R.idy);
-        if (R.dz != 0.0f) te = fminf(te, ((R.dz > 0.0f ? (float)min(bz + kBrick, P.nz - 1) : (float)bz) - R.p0z) * R.idz);
-        const int kn = (int)ceilf((te - 1e-3f) / step - 0.5f);
-        k = max(k, kn - 1);
-        return true;
-    }
-};
 
 // Forward march of one ray.  Consecutive samples often share a cell (at half a
 // voxel step about 2 in 5 do), so the cell's eight records stay in registers

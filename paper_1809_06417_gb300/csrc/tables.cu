@@ -1,0 +1,578 @@
+// tables.cu -- the paper-rule loop over a fixed extinction field as two
+// sparse linear maps, built once per reconstruction call.
+//
+// The paper rule (Eqs. 10-11) adjusts the key points' colours only and keeps
+// sigma_t fixed (Sec. 3.3.1 takes it constant); with G(s) = 1 (Eq. 11) the
+// transmittance at every sample of every ray is then the same at every
+// iteration, and both halves of an iteration of Algorithm 2 are linear maps
+// whose coefficients do not change:
+//   * rendering (Eqs. 5-8): the radiance of pixel p is
+//       L_p = sum_j A_pj S_j,   A_pj = sum_s T(s) beta(s) w_j(s),
+//     over the samples s of p's ray, T(s) the transmittance in front of s,
+//     beta(s) = (1 - e^{-sigma l}) / sigma its segment weight and w_j(s) the
+//     trilinear weight of key point j at s (S_j: source record of j);
+//   * adjustment (Eq. 10): key point j moves by
+//       dV_j = sum_p W_pj dL_p,  W_pj = sum_s alpha_l T(s) e^{-alpha_d D(j, s)},
+//     over the flame rays p and their samples s whose cell has j as a corner.
+// One march over every ray fills both tables with an entry for each (ray, key
+// point inside the visual hull) pair -- records outside the hull are zero and
+// their updates are discarded (Sec. 4.3.1) -- and every iteration then streams
+// them: the forward table ray by ray (a gather of source records), the
+// adjustment table key point by key point (a gather of the flame rays'
+// residuals: the per-key-point gather form of the adjustment, no atomics).
+//
+// Layouts.  Forward table: warp w (one of the four 8 x 4 sub-tiles of a
+// 16 x 8 pixel tile, as in the marches) owns rows [woff[w], woff[w] + wrows[w]);
+// row r holds one entry per lane at 32 r + lane, {node, A as float bits}; a
+// lane's rows after its last entry hold the hull's first key point with
+// weight 0.  Flame rays are numbered in
+// tile order (the tile's offset tfoff plus the ray's rank among the tile's
+// flame pixels).  Adjustment table: key point h of the hull list (node
+// hnode[h], nodes in index order) owns entries [hend[h - 1], hend[h]) of
+// {flame-ray number, W as float bits}, in increasing flame-ray order (so
+// that neighbouring entries name neighbouring rays, whose residuals share
+// cache lines).
+#include "fr_device.cuh"
+#include "fr_internal.h"
+
+namespace frk {
+
+namespace {
+
+// One ray's march over the samples in bricks holding a key point inside the
+// hull (the adjustment's skipping, exact for both tables), with the
+// parity-slot window of the adjustment: emit(node, A, W) runs for each key
+// point of the hull the ray leaves, with its two sums (sums = false: the
+// same key points, the sums left at 0).  W is accumulated for flame rays
+// only.  The sample positions, cells and transmittance are those
+// of the paper-rule adjustment march (adj_ray), so the same key points
+// receive the same samples.
+template <int DT, class Emit>
+__device__ __forceinline__ void tab_march(const ProbDev& P, const CamDev& cam, int px, int py, bool flame,
+                                          const unsigned* __restrict__ tags, unsigned full, bool sums,
+                                          Emit&& emit)
+{
+    Ray R;
+    if (!make_ray(cam, px, py, P.nx, P.ny, P.nz, P.step, R)) return;
+    int k0 = 0, k1 = R.n;
+    if (!BrickSkip::box_range(P, P.adj_box, R, P.step, k0, k1)) return;
+    const long long nodes = (long long)P.nx * P.ny * P.nz;
+    (void)nodes;
+    const int nxy32 = P.nx * P.ny;
+    const float dcoef = -P.alpha_d * kLog2e;
+    float A[8], Wt[8], sg[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) { A[t] = 0.0f; Wt[t] = 0.0f; sg[t] = 0.0f; }
+    auto leave = [&](int t, int node, bool p) {
+        if (p) {
+            if (__ldg(tags + FR_CHK(node, nodes, 32u)) == full) emit(node, A[t], Wt[t]);
+            A[t] = 0.0f;
+            Wt[t] = 0.0f;
+        }
+    };
+    auto enter = [&](int t, int node, bool p) {
+        if (p && sums) sg[t] = load_rgb_sigma<DT>(P.vol, FR_CHK(node, nodes, 1u));
+    };
+    Win W;
+    W.live = false;
+    BrickSkip skip;
+    float T = 1.0f;
+    for (int k = k0; k < k1; ++k) {
+        float len, x, y, z;
+        segment(R, P.step, k, len, x, y, z);
+        const CellIJK c = cell_ijk(x, y, z, P.nx, P.ny, P.nz);
+        if (skip.empty_at(P.adj_occ, P, R, P.step, c, k)) continue;
+        win_move_pred(W, c.i, c.j, c.k, P.nx, P.ny, nxy32, leave, enter);
+        if (!sums) continue;   // (the count pass: which key points, not their sums)
+        const float gx = mirror_frac(c.i, c.fx), gy = mirror_frac(c.j, c.fy), gz = mirror_frac(c.k, c.fz);
+        const float sig = slot_blend<float>(sg, gx, gy, gz);
+        const float e = __expf(-sig * len);
+        const float beta = T * seg_weight(sig, len, e);
+        // trilinear weight of slot t: (t & 1 ? gx : 1 - gx) (t & 2 ? gy : 1 - gy) (t & 4 ? gz : 1 - gz)
+        const float wx[2] = {1.0f - gx, gx}, wy[2] = {1.0f - gy, gy}, wz[2] = {1.0f - gz, gz};
+#pragma unroll
+        for (int t = 0; t < 8; ++t) A[t] = fmaf(beta, wx[t & 1] * wy[(t >> 1) & 1] * wz[t >> 2], A[t]);
+        if (flame) {
+            const float base = P.alpha_l * T;
+            // squared distances (voxel units) from the sample to each slot's key point
+            const float ex[2] = {gx * gx, (1.0f - gx) * (1.0f - gx)};
+            const float ey[2] = {gy * gy, (1.0f - gy) * (1.0f - gy)};
+            const float ez[2] = {gz * gz, (1.0f - gz) * (1.0f - gz)};
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                Wt[t] = fmaf(base, dist_weight(dcoef, ex[t & 1] + ey[(t >> 1) & 1] + ez[t >> 2]), Wt[t]);
+        }
+        T *= e;
+    }
+    win_release(W, [&](int t, int node) { leave(t, node, true); });
+}
+
+__device__ __forceinline__ bool flame_pixel(const ProbDev& P, long long pix)
+{
+    const float* t = P.targets + 3 * pix;
+    return fmaxf(__ldg(t), fmaxf(__ldg(t + 1), __ldg(t + 2))) > P.thresh;
+}
+
+// One kernel for both passes, so that the two run the same instructions and
+// emit the same entries.  Count pass (fill = 0): entries per ray (their
+// warp's maximum: the warp's rows), flame rays per tile, and the adjustment
+// entries of every key point (ncnt, zeroed beforehand).  Fill pass (fill =
+// 1): the entries themselves, ncnt holding each key point's next free
+// adjustment entry; writes past the counted rows or entries are dropped.
+template <int DT>
+__global__ void __launch_bounds__(kTileThreads) tab_build_kernel(const __grid_constant__ SingleArgs a, TabBuild b,
+                                                                 int fill)
+{
+    const ProbDev& P = a.p;
+    int view, px, py;
+    tile_pixel(P, blockIdx.x, view, px, py);
+    const bool valid = px < P.W && py < P.H;
+    const long long pix = ((long long)view * P.H + py) * P.W + px;
+    const bool flame = valid && flame_pixel(P, pix);
+    __shared__ unsigned wc[kTileThreads / 32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned wi = blockIdx.x * (kTileThreads / 32) + w;
+    unsigned fid = 0, rows = 0;
+    uint2* out = nullptr;
+    if (fill) {
+        // the flame ray's number: the tile's offset and its rank in the tile
+        const unsigned m = __ballot_sync(0xffffffffu, flame);
+        if (lane == 0) wc[w] = (unsigned)__popc(m);
+        __syncthreads();
+        fid = __ldg(b.tfoff + blockIdx.x) + (unsigned)__popc(m & ((1u << lane) - 1u));
+        for (int i = 0; i < w; ++i) fid += wc[i];
+        rows = __ldg(b.wrows + wi);
+        out = b.efwd + (size_t)__ldg(b.woff + wi) * 32 + lane;
+    }
+    unsigned n = 0;
+    if (valid)
+        tab_march<DT>(P, a.cams[view], px, py, flame, b.tags, b.full, fill != 0, [&](int node, float A, float W) {
+            if (fill) {
+                if (n < rows) out[(size_t)n * 32] = make_uint2((unsigned)node, __float_as_uint(A));
+                if (flame) {
+                    const unsigned at = atomicAdd(b.ncnt + node, 1u);
+                    if (at < b.nadj) b.eadj[at] = make_uint2(fid, __float_as_uint(W));
+                }
+            } else if (flame) {
+                atomicAdd(b.ncnt + node, 1u);
+            }
+            ++n;
+        });
+    if (fill) {
+        // padding: a key point of the hull (whose source record is defined) with weight 0
+        const unsigned pad = b.nhull ? __ldg(b.hnode) : 0u;
+        for (; n < rows; ++n) out[(size_t)n * 32] = make_uint2(pad, 0u);
+    } else {
+        n = __reduce_max_sync(0xffffffffu, n);
+        const int nflame = __syncthreads_count(flame);
+        if (lane == 0) b.wrows[wi] = n;
+        if (threadIdx.x == 0) b.tfl[blockIdx.x] = (unsigned)nflame;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scans (block sums, a one-CTA scan of them, then each block's
+// items), 64-bit running sums
+// ---------------------------------------------------------------------------
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v, unsigned long long* total)
+{
+    __shared__ unsigned long long ws[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long s = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        ws[lane] = s;
+    }
+    __syncthreads();
+    const unsigned long long before = (w ? ws[w - 1] : 0ull) + x - v;
+    if (total) *total = ws[kScanThreads / 32 - 1];
+    __syncthreads();
+    return before;
+}
+
+// Scan inputs: the value of item i.
+struct GetU32 {
+    const unsigned* v;
+    __device__ unsigned operator()(long long i) const { return __ldg(v + i); }
+};
+struct GetInHull {
+    const unsigned* tags;
+    unsigned full;
+    __device__ unsigned operator()(long long i) const { return __ldg(tags + i) == full ? 1u : 0u; }
+};
+// Scan outputs: item i with its exclusive prefix `at` and value v.
+struct PutU32 {
+    unsigned* out;
+    __device__ void operator()(long long i, unsigned long long at, unsigned) const { out[i] = (unsigned)at; }
+};
+struct PutCompact {
+    unsigned* list;
+    __device__ void operator()(long long i, unsigned long long at, unsigned v) const
+    {
+        if (v) list[at] = (unsigned)i;
+    }
+};
+
+template <class Get>
+__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(Get get, long long n, unsigned long long* bsum)
+{
+    const long long i0 = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
+    unsigned long long s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q)
+        if (i0 + q < n) s += get(i0 + q);
+    unsigned long long total;
+    block_excl_scan(s, &total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// one CTA: bsum[0 .. nb) to exclusive prefixes, the sum to *total
+__global__ void __launch_bounds__(kScanThreads) scan_top_kernel(unsigned long long* bsum, int nb,
+                                                                unsigned long long* total)
+{
+    unsigned long long carry = 0;
+    for (int base = 0; base < nb; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const unsigned long long v = i < nb ? bsum[i] : 0ull;
+        unsigned long long t;
+        const unsigned long long before = block_excl_scan(v, &t);
+        if (i < nb) bsum[i] = carry + before;
+        carry += t;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+template <class Get, class Put>
+__global__ void __launch_bounds__(kScanThreads) scan_put_kernel(Get get, Put put, long long n,
+                                                                const unsigned long long* bsum)
+{
+    const long long i0 = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
+    unsigned v[kScanItems];
+    unsigned long long s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        v[q] = i0 + q < n ? get(i0 + q) : 0u;
+        s += v[q];
+    }
+    unsigned long long at = bsum[blockIdx.x] + block_excl_scan(s, nullptr);
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        if (i0 + q < n) put(i0 + q, at, v[q]);
+        at += v[q];
+    }
+}
+
+template <class Get, class Put>
+cudaError_t scan(Get get, Put put, long long n, unsigned long long* bsum, unsigned long long* total, cudaStream_t s)
+{
+    const int nb = (int)((n + kScanChunk - 1) / kScanChunk);
+    if (nb == 0) return cudaMemsetAsync(total, 0, sizeof *total, s);
+    scan_sums_kernel<<<nb, kScanThreads, 0, s>>>(get, n, bsum);
+    scan_top_kernel<<<1, kScanThreads, 0, s>>>(bsum, nb, total);
+    scan_put_kernel<<<nb, kScanThreads, 0, s>>>(get, put, n, bsum);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) hend_kernel(const unsigned* __restrict__ hnode, const unsigned* __restrict__ cursor,
+                                                   unsigned nh, unsigned* __restrict__ hend)
+{
+    const unsigned h = blockIdx.x * 256u + threadIdx.x;
+    if (h < nh) hend[h] = __ldg(cursor + __ldg(hnode + h));
+}
+
+// Each key point's adjustment entries in increasing flame-ray order (the fill
+// pass appends them in the order its atomics return): one warp per key point
+// ranks its entries in shared memory (a flame ray names a key point once:
+// the eight cells around it form a convex box, which a ray enters and leaves
+// once).  Key points with more than kSortMax entries keep their order.
+constexpr int kSortMax = 512;
+constexpr int kSortWarps = 8;
+__global__ void __launch_bounds__(32 * kSortWarps) tab_sort_kernel(uint2* __restrict__ eadj,
+                                                                  const unsigned* __restrict__ hend, unsigned nh)
+{
+    __shared__ uint2 buf[kSortWarps][kSortMax];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned g = blockIdx.x * (unsigned)kSortWarps + w;
+    if (g >= nh) return;
+    const unsigned b = g ? __ldg(hend + g - 1) : 0u, e = __ldg(hend + g), n = e - b;
+    if (n <= 1 || n > (unsigned)kSortMax) return;
+    for (unsigned i = lane; i < n; i += 32) buf[w][i] = eadj[b + i];
+    __syncwarp();
+    for (unsigned i = lane; i < n; i += 32) {
+        const uint2 x = buf[w][i];
+        unsigned rank = 0;
+        for (unsigned j = 0; j < n; ++j) rank += buf[w][j].x < x.x ? 1u : 0u;
+        eadj[b + rank] = x;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per iteration
+// ---------------------------------------------------------------------------
+
+#ifndef FR_TAB_UNROLL
+#define FR_TAB_UNROLL 4
+#endif
+constexpr int kTabUnroll = FR_TAB_UNROLL;
+
+// Forward: each lane sums its ray's entries, A times the entry's source record
+// (rows read once per iteration: streaming loads that leave the L2 to the
+// records), then the forward march's epilogue: rendered image and residual
+// image when asked for, each flame ray's residual at its number, the tile's
+// squared-error partials.
+template <int DT>
+__global__ void __launch_bounds__(kTileThreads) tab_forward_kernel(const __grid_constant__ SingleArgs a, TabIter it)
+{
+    const ProbDev& P = a.p;
+    int view, px, py;
+    tile_pixel(P, blockIdx.x, view, px, py);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned wi = blockIdx.x * (kTileThreads / 32) + w;
+    const unsigned rows = __ldg(it.wrows + wi);
+    const uint2* E = it.efwd + (size_t)__ldg(it.woff + wi) * 32 + lane;
+    const long long nodes = (long long)P.nx * P.ny * P.nz;
+    (void)nodes;
+    // rows streamed kTabUnroll at a time, the next group's entries loaded
+    // before this group's records are gathered (two dependent loads in
+    // flight per row instead of one after the other)
+    float L0 = 0.0f, L1 = 0.0f, L2 = 0.0f;
+    uint2 cur[kTabUnroll];
+#pragma unroll
+    for (int q = 0; q < kTabUnroll; ++q) cur[q] = (unsigned)q < rows ? __ldcs(E + (size_t)q * 32) : make_uint2(0u, 0u);
+    for (unsigned r = 0; r < rows; r += kTabUnroll) {
+        uint2 nxt[kTabUnroll];
+#pragma unroll
+        for (int q = 0; q < kTabUnroll; ++q) {
+            const unsigned rr = r + kTabUnroll + q;
+            nxt[q] = rr < rows ? __ldcs(E + (size_t)rr * 32) : make_uint2(0u, 0u);
+        }
+        float4 v[kTabUnroll];
+#pragma unroll
+        for (int q = 0; q < kTabUnroll; ++q)
+            v[q] = r + q < rows ? load_rgb<DT>(P.vol, FR_CHK(cur[q].x, nodes, 1u)) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int q = 0; q < kTabUnroll; ++q) {
+            const float A = __uint_as_float(cur[q].y);
+            L0 = fmaf(A, v[q].x, L0); L1 = fmaf(A, v[q].y, L1); L2 = fmaf(A, v[q].z, L2);
+            cur[q] = nxt[q];
+        }
+    }
+    const bool valid = px < P.W && py < P.H;
+    const long long pix = valid ? FR_CHK(((long long)view * P.H + py) * P.W + px, (long long)P.ncam * P.H * P.W, 4u)
+                                : 0;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, cnt = 0.0f;
+    float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
+    bool flame = false;
+    if (valid) {
+        if (P.rendered) {
+            float* o = P.rendered + 3 * pix;
+            o[0] = L0; o[1] = L1; o[2] = L2;
+        }
+        const float* t = P.targets + 3 * pix;
+        const float t0 = t[0], t1 = t[1], t2 = t[2];
+        d0 = t0 - L0; d1 = t1 - L1; d2 = t2 - L2;
+        flame = fmaxf(t0, fmaxf(t1, t2)) > P.thresh;
+        if (P.residual) {
+            float* o = P.residual + 3 * pix;
+            o[0] = flame ? d0 : 0.0f;
+            o[1] = flame ? d1 : 0.0f;
+            o[2] = flame ? d2 : 0.0f;
+        }
+        const int* bb = P.bbox + 4 * view;
+        if (px >= bb[0] && px <= bb[2] && py >= bb[1] && py <= bb[3]) {
+            a0 = d0 * d0; a1 = d1 * d1; a2 = d2 * d2; cnt = 1.0f;
+        }
+    }
+    // the flame ray's number: the tile's offset and its rank in the tile
+    __shared__ unsigned wc[kTileThreads / 32];
+    __shared__ float red[4][kTileThreads / 32];
+    const unsigned m = __ballot_sync(0xffffffffu, flame);
+    a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2); cnt = warp_sum(cnt);
+    if (lane == 0) {
+        wc[w] = (unsigned)__popc(m);
+        red[0][w] = a0; red[1][w] = a1; red[2][w] = a2; red[3][w] = cnt;
+    }
+    __syncthreads();
+    if (flame) {
+        unsigned fid = __ldg(it.tfoff + blockIdx.x) + (unsigned)__popc(m & ((1u << lane) - 1u));
+        for (int i = 0; i < w; ++i) fid += wc[i];
+        it.dl[FR_CHK(fid, it.nflame, 8u)] = make_float4(d0, d1, d2, 0.0f);
+    }
+    if (threadIdx.x < 4) {
+        float s = 0.0f;
+#pragma unroll
+        for (int i = 0; i < kTileThreads / 32; ++i) s += red[threadIdx.x][i];
+        P.partials[4 * (long long)blockIdx.x + threadIdx.x] = s;
+    }
+}
+
+// Adjustment and update of the hull's key points: kTabLanes lanes per key
+// point sum W times the flame ray's residual over its entries, then one lane
+// adds the sum to the record (Eq. 11), clamps it at 0 when asked and stores
+// it in the volume's type.  Every key point of the hull is visited each
+// iteration (as the update visits every node), entries or not.
+#ifndef FR_TAB_LANES
+#define FR_TAB_LANES 8
+#endif
+constexpr int kTabLanes = FR_TAB_LANES;
+static_assert(kTabLanes >= 1 && kTabLanes <= 32 && (kTabLanes & (kTabLanes - 1)) == 0, "FR_TAB_LANES: power of 2");
+constexpr int kTabAdjThreads = 256;
+
+template <int DT>
+__global__ void __launch_bounds__(kTabAdjThreads) tab_adjust_kernel(void* vol, TabIter it, int clamp_nonneg,
+                                                                    long long nodes)
+{
+    const unsigned g = (blockIdx.x * (unsigned)kTabAdjThreads + threadIdx.x) / (unsigned)kTabLanes;
+    const unsigned sub = threadIdx.x & (kTabLanes - 1);
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+    if (g < it.nhull) {
+        const unsigned b = g ? min(__ldg(it.hend + g - 1), it.nadj) : 0u, e = min(__ldg(it.hend + g), it.nadj);
+        // kTabUnroll entries per lane at a time, the next group's loaded
+        // before this group's residuals are gathered
+        unsigned i = b + sub;
+        uint2 cur[kTabUnroll];
+#pragma unroll
+        for (int q = 0; q < kTabUnroll; ++q) {
+            const unsigned k = i + q * kTabLanes;
+            cur[q] = k < e ? __ldcs(it.eadj + k) : make_uint2(0u, 0u);
+        }
+        for (; i < e; i += kTabUnroll * kTabLanes) {
+            uint2 nxt[kTabUnroll];
+#pragma unroll
+            for (int q = 0; q < kTabUnroll; ++q) {
+                const unsigned k = i + (kTabUnroll + q) * kTabLanes;
+                nxt[q] = k < e ? __ldcs(it.eadj + k) : make_uint2(0u, 0u);
+            }
+            float4 d[kTabUnroll];
+#pragma unroll
+            for (int q = 0; q < kTabUnroll; ++q)
+                d[q] = i + q * kTabLanes < e ? __ldg(it.dl + FR_CHK(cur[q].x, it.nflame, 8u))
+                                             : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+            for (int q = 0; q < kTabUnroll; ++q) {
+                const float W = __uint_as_float(cur[q].y);
+                a0 = fmaf(W, d[q].x, a0); a1 = fmaf(W, d[q].y, a1); a2 = fmaf(W, d[q].z, a2);
+                cur[q] = nxt[q];
+            }
+        }
+    }
+#pragma unroll
+    for (int o = kTabLanes / 2; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if (g < it.nhull && sub == 0) {
+        const long long node = FR_CHK(__ldg(it.hnode + g), nodes, 32u);
+        float4 v = load_rgb<DT>(vol, node);
+        v.x += a0; v.y += a1; v.z += a2;
+        if (clamp_nonneg) {
+            v.x = fmaxf(v.x, 0.0f); v.y = fmaxf(v.y, 0.0f); v.z = fmaxf(v.z, 0.0f);
+        }
+        store_rgb<DT>(vol, node, v);
+    }
+}
+
+}  // namespace
+
+static cudaError_t launch_tab_build(const SingleArgs& a, const TabBuild& b, int dt, int ntiles, int fill,
+                                    cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    if (dt == DT_F32) tab_build_kernel<DT_F32><<<ntiles, kTileThreads, 0, s>>>(a, b, fill);
+    else if (dt == DT_BF16) tab_build_kernel<DT_BF16><<<ntiles, kTileThreads, 0, s>>>(a, b, fill);
+    else tab_build_kernel<DT_F16><<<ntiles, kTileThreads, 0, s>>>(a, b, fill);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tab_count(const SingleArgs& a, const TabBuild& b, int dt, int ntiles, cudaStream_t s)
+{
+    return launch_tab_build(a, b, dt, ntiles, 0, s);
+}
+
+cudaError_t launch_tab_scans(const TabBuild& b, int ntiles, long long nodes, unsigned long long* bsum,
+                             unsigned long long* totals, cudaStream_t s)
+{
+    const long long nw = (long long)ntiles * (kTileThreads / 32);
+    cudaError_t e = scan(GetU32{b.wrows}, PutU32{b.woff}, nw, bsum, totals + 0, s);
+    if (e == cudaSuccess) e = scan(GetU32{b.tfl}, PutU32{b.tfoff}, ntiles, bsum, totals + 1, s);
+    if (e == cudaSuccess) e = scan(GetU32{b.ncnt}, PutU32{b.ncnt}, nodes, bsum, totals + 2, s);
+    if (e == cudaSuccess) e = scan(GetInHull{b.tags, b.full}, PutCompact{b.hnode}, nodes, bsum, totals + 3, s);
+    return e;
+}
+
+size_t tab_scan_blocks(long long n) { return (size_t)((n + kScanChunk - 1) / kScanChunk); }
+
+cudaError_t launch_tab_fill(const SingleArgs& a, const TabBuild& b, int dt, int ntiles, cudaStream_t s)
+{
+    return launch_tab_build(a, b, dt, ntiles, 1, s);
+}
+
+cudaError_t launch_tab_hend(const unsigned* hnode, const unsigned* cursor, unsigned nh, unsigned* hend, cudaStream_t s)
+{
+    if (nh == 0) return cudaSuccess;
+    hend_kernel<<<(nh + 255) / 256, 256, 0, s>>>(hnode, cursor, nh, hend);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tab_sort(uint2* eadj, const unsigned* hend, unsigned nh, cudaStream_t s)
+{
+    if (nh == 0) return cudaSuccess;
+    tab_sort_kernel<<<(nh + kSortWarps - 1) / kSortWarps, 32 * kSortWarps, 0, s>>>(eadj, hend, nh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tab_forward(const SingleArgs& a, const TabIter& it, int dt, int ntiles, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    if (dt == DT_F32) tab_forward_kernel<DT_F32><<<ntiles, kTileThreads, 0, s>>>(a, it);
+    else if (dt == DT_BF16) tab_forward_kernel<DT_BF16><<<ntiles, kTileThreads, 0, s>>>(a, it);
+    else tab_forward_kernel<DT_F16><<<ntiles, kTileThreads, 0, s>>>(a, it);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tab_adjust(void* vol, int dt, long long nodes, const TabIter& it, int clamp_nonneg, cudaStream_t s)
+{
+    if (it.nhull == 0) return cudaSuccess;
+    const unsigned per_cta = kTabAdjThreads / kTabLanes;
+    const unsigned g = (it.nhull + per_cta - 1) / per_cta;
+    if (dt == DT_F32) tab_adjust_kernel<DT_F32><<<g, kTabAdjThreads, 0, s>>>(vol, it, clamp_nonneg, nodes);
+    else if (dt == DT_BF16) tab_adjust_kernel<DT_BF16><<<g, kTabAdjThreads, 0, s>>>(vol, it, clamp_nonneg, nodes);
+    else tab_adjust_kernel<DT_F16><<<g, kTabAdjThreads, 0, s>>>(vol, it, clamp_nonneg, nodes);
+    return cudaGetLastError();
+}
+
+cudaError_t check_word_tables(unsigned* word, bool reset)
+{
+#ifdef FR_CHECKED
+    cudaError_t e = cudaMemcpyFromSymbol(word, g_fr_check_word, sizeof(unsigned));
+    if (e == cudaSuccess && reset) {
+        const unsigned zero = 0;
+        e = cudaMemcpyToSymbol(g_fr_check_word, &zero, sizeof(unsigned));
+    }
+    return e;
+#else
+    *word = 0;
+    (void)reset;
+    return cudaSuccess;
+#endif
+}
+
+}  // namespace frk

@@ -74,7 +74,7 @@ class fr_params(ctypes.Structure):
                 ("lut_t_min", ctypes.c_float), ("lut_t_max", ctypes.c_float), ("lut", ctypes.c_void_p),
                 ("lut_size", ctypes.c_int32), ("use_hull", ctypes.c_int32),
                 ("skip_empty", ctypes.c_int32), ("hull_tags", ctypes.c_void_p), ("hg_g", ctypes.c_float),
-                ("sequential_views", ctypes.c_int32)]
+                ("sequential_views", ctypes.c_int32), ("tables", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -124,6 +124,7 @@ SIGNATURES = {
     "fr_set_scratch_limit": (_S, [_P, ctypes.c_size_t]),
     "fr_scratch_bytes": (_S, [_P, _P]),
     "fr_phase_times": (_S, [_P, _P, _I, _P]),
+    "fr_table_stats": (_S, [_P, _P]),
     "fr_render_residual_noalloc": (_S, [_I, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, ctypes.c_char_p,
                                         ctypes.c_size_t]),
     "fr_volume_create": (_S, [_P, _I, _I, _I, _P, _F, _I, _I, _P]),
@@ -478,6 +479,13 @@ class Context:
         calls = ctypes.c_int32()
         self.check(self.lib.fr_phase_times(self.h, ms, FR_PHASE_COUNT, ctypes.byref(calls)))
         return dict(zip(PHASES, list(ms))), calls.value
+
+    def fr_table_stats(self):
+        """Sizes of the ray weight tables of the last reconstruction call: dict of
+        forward_entries, adjustment_entries, flame_rays, hull_key_points."""
+        st = (ctypes.c_uint64 * 4)()
+        self.check(self.lib.fr_table_stats(self.h, st))
+        return dict(zip(("forward_entries", "adjustment_entries", "flame_rays", "hull_key_points"), list(st)))
 
     def fr_count_samples(self, vol, cams, p, residual=None):
         n = ctypes.c_int64()

@@ -50,7 +50,8 @@ def main():
     bbox = torch.zeros((5, 4), dtype=torch.int32, device="cuda")
     ctx.fr_prepare_targets(img, 30 / 255, bbox)
     alb = torch.as_tensor(case.albedo, dtype=torch.float32, device="cuda").contiguous()
-    for kw in (dict(), dict(use_hull=1), dict(use_hull=1, hg_g=0.5), dict(use_hull=1, sequential_views=1)):
+    for kw in (dict(), dict(use_hull=1), dict(use_hull=1, tables=2), dict(use_hull=1, hg_g=0.5),
+               dict(use_hull=1, sequential_views=1)):
         v = g.clone()
         v[..., :3] = 0.0
         fv = fr.volume(v, case.origin, case.h)

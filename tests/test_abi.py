@@ -28,7 +28,7 @@ def test_library_exports_every_declared_symbol():
 def test_abi_version_and_defaults():
     from paper_1809_06417_gb300 import flamerec
     lib = flamerec.load()
-    assert lib.fr_abi_version() == 2
+    assert lib.fr_abi_version() == 3
     p = flamerec.params()
     # the paper's constants (Sec. 4.1, 4.2, 5.1)
     assert p.step == 1.0 and abs(p.alpha_l - 0.001) < 1e-9 and p.alpha_d == 1.0
@@ -44,7 +44,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(fr.fr_camera) == 64
     assert ctypes.sizeof(fr.fr_volume) == 48
     assert fr.fr_params.lut.offset % 8 == 0
-    fields = {"fr_params": ["lut", "hull_tags", "hg_g", "sequential_views"],
+    fields = {"fr_params": ["lut", "hull_tags", "hg_g", "sequential_views", "tables"],
               "fr_problem": ["targets", "rmse", "hull_tags"],
               "fr_job_desc": ["cams", "init_records", "rmse", "hull_tags"],
               "fr_job_info": ["t_submit", "footprint"]}

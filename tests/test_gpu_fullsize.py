@@ -7,8 +7,9 @@ ring cameras of 512 x 512, a half-voxel step.
   tolerance, residual and the error sums.
 * Two iterations of fr_reconstruct in the launch configuration the benchmark
   times -- in-scattering source, visual hull (the oracle's tags, given to both
-  sides), empty-brick skipping, the adjustment over half rays -- against
-  orc.reconstruct on the same tags: per-iteration error and the updated volume.
+  sides), empty-brick skipping, the ray weight tables (and, beside them, the
+  marches with the adjustment over half rays) -- against orc.reconstruct on
+  the same tags: per-iteration error and the updated volume.
 
 The oracle runs on every host core (its pixel loops are independent; see
 oracle.set_threads).
@@ -98,26 +99,36 @@ def test_full_size_render_residual_follows_oracle(orc, full):
     np.testing.assert_allclose(255.0 * np.sqrt(q[:3] / q[3]), rmse_ref, rtol=1e-4)
 
 
-def test_full_size_reconstruct_iterations_follow_oracle(orc, full):
-    """fr_reconstruct as the benchmark calls it (hull tags given, empty bricks
-    skipped, half-ray adjustment, in-scattering) for two iterations.  Which
-    eight key points a sample updates (Eq. 10) is an integer decision: of the
-    7e7 adjustment samples, those within float32 rounding of a cell face (or
-    the last sample of a ray whose chord is within rounding of a whole number
-    of steps) may update the neighbouring cell's key points on one side only.
-    The oracle bounds, per node, what those samples can move (its undecided
-    budget); every node must lie within 1e-4 of the volume's maximum plus its
-    budget."""
-    fr, ctx, sc, P = full["fr"], full["ctx"], full["sc"], full["P"]
+@pytest.fixture(scope="module")
+def ref2(orc, full):
+    """The oracle's two iterations from the mid-reconstruction start, with its
+    undecided budget (shared by the marching and the table runs)."""
     v0 = _start(full)
-    iters = 2
-    vol_ref, rmse_ref, samples, und = orc.reconstruct(sc, v0, P, full["t_ref"], full["mask"], full["bbox_ref"],
-                                                      iters, albedo=full["alb"], hull=full["tags"],
+    vol_ref, rmse_ref, samples, und = orc.reconstruct(full["sc"], v0, full["P"], full["t_ref"], full["mask"],
+                                                      full["bbox_ref"], 2, albedo=full["alb"], hull=full["tags"],
                                                       with_undecided=True)
+    return dict(v0=v0, vol=vol_ref, rmse=rmse_ref, samples=samples, und=und)
+
+
+@pytest.mark.parametrize("tables", [1, 2], ids=["march", "tables"])
+def test_full_size_reconstruct_iterations_follow_oracle(orc, full, ref2, tables):
+    """fr_reconstruct as the benchmark calls it (hull tags given, empty bricks
+    skipped, in-scattering) for two iterations, marching every iteration
+    (the adjustment over half rays) or streaming the ray weight tables built
+    at the start of the call.  Which eight key points a sample updates
+    (Eq. 10) is an integer decision: of the 7e7 adjustment samples, those
+    within float32 rounding of a cell face (or the last sample of a ray whose
+    chord is within rounding of a whole number of steps) may update the
+    neighbouring cell's key points on one side only.  The oracle bounds, per
+    node, what those samples can move (its undecided budget); every node must
+    lie within 1e-4 of the volume's maximum plus its budget."""
+    fr, ctx = full["fr"], full["ctx"]
+    v0, vol_ref, rmse_ref, samples, und = ref2["v0"], ref2["vol"], ref2["rmse"], ref2["samples"], ref2["und"]
+    iters = 2
     v = torch.as_tensor(v0, dtype=torch.float32, device="cuda").contiguous()
     alb = torch.as_tensor(full["alb"], dtype=torch.float32, device="cuda").contiguous()
     p = fr.params(step=STEP, alpha_l=ALPHA_L, use_hull=1, hull_tags=tags_on_device(torch, full["tags"]),
-                  skip_empty=1)
+                  skip_empty=1, tables=tables)
     rmse = np.zeros((iters, 3), dtype=np.float32)
     ctx.fr_reconstruct(fr.volume(v, full["origin"], full["h"]), fr.cameras(full["cams"]), full["t_dev"],
                        full["bbox"], iters, p, albedo=alb, rmse=rmse)
@@ -129,8 +140,8 @@ def test_full_size_reconstruct_iterations_follow_oracle(orc, full):
     flagged = und > 0
     moved = np.abs(vol_ref[..., :3] - v0[..., :3]).max() / scale
     print(f"oracle samples (forward, adjustment) {samples}; rmse gpu {rmse.tolist()} oracle {rmse_ref.tolist()}")
-    print(f"full-size volume after {iters} iterations (the update moved it by {moved:.3e} of its max): "
-          f"max error / max {err.max() / scale:.3e}; nodes with an undecided budget {flagged.sum()} "
+    print(f"full-size volume after {iters} iterations, tables={tables} (the update moved it by {moved:.3e} of its "
+          f"max): max error / max {err.max() / scale:.3e}; nodes with an undecided budget {flagged.sum()} "
           f"({flagged.mean():.2e}); max error / max off them {err[~flagged].max() / scale:.3e}; "
           f"worst error / bound {np.max(err / bound):.3f}")
     # the first row is the error of the render of v0; the next ones follow updates
@@ -146,22 +157,32 @@ def test_full_size_reconstruct_iterations_follow_oracle(orc, full):
     assert np.array_equal(got[..., 3], v0[..., 3].astype(np.float32))
 
 
-def test_full_size_bf16_records_follow_the_16bit_oracle(orc, full):
+@pytest.fixture(scope="module")
+def ref_bf16(orc, full):
+    """The oracle's two iterations keeping BF16 records, and with FP64 records."""
+    sc, P = full["sc"], full["P"]
+    v0 = orc.round_storage(_start(full), "bf16")
+    P16 = orc.make_params(step=STEP, alpha_l=ALPHA_L, storage="bf16")
+    ref16, r16, _ = orc.reconstruct(sc, v0, P16, full["t_ref"], full["mask"], full["bbox_ref"], 2,
+                                    albedo=full["alb"], hull=full["tags"])
+    ref64, _, _ = orc.reconstruct(sc, v0, P, full["t_ref"], full["mask"], full["bbox_ref"], 2,
+                                  albedo=full["alb"], hull=full["tags"])
+    return dict(v0=v0, ref16=ref16, r16=r16, ref64=ref64)
+
+
+@pytest.mark.parametrize("tables", [1, 2], ids=["march", "tables"])
+def test_full_size_bf16_records_follow_the_16bit_oracle(orc, full, ref_bf16, tables):
     """The benchmarked workload with BF16 records (FP32 arithmetic): two
     iterations against the oracle keeping BF16 records, at the storage
     tolerance of 1e-2 of the volume's maximum; the error against the FP64
     loop with double-precision records is printed beside it."""
-    fr, ctx, sc, P = full["fr"], full["ctx"], full["sc"], full["P"]
-    v0 = orc.round_storage(_start(full), "bf16")
+    fr, ctx = full["fr"], full["ctx"]
+    v0, ref16, r16, ref64 = ref_bf16["v0"], ref_bf16["ref16"], ref_bf16["r16"], ref_bf16["ref64"]
     iters = 2
-    P16 = orc.make_params(step=STEP, alpha_l=ALPHA_L, storage="bf16")
-    ref16, r16, _ = orc.reconstruct(sc, v0, P16, full["t_ref"], full["mask"], full["bbox_ref"], iters,
-                                    albedo=full["alb"], hull=full["tags"])
-    ref64, _, _ = orc.reconstruct(sc, v0, P, full["t_ref"], full["mask"], full["bbox_ref"], iters,
-                                  albedo=full["alb"], hull=full["tags"])
     v = torch.as_tensor(v0, dtype=torch.float32, device="cuda").to(torch.bfloat16).contiguous()
     alb = torch.as_tensor(full["alb"], dtype=torch.float32, device="cuda").contiguous()
-    p = fr.params(step=STEP, alpha_l=ALPHA_L, use_hull=1, hull_tags=tags_on_device(torch, full["tags"]))
+    p = fr.params(step=STEP, alpha_l=ALPHA_L, use_hull=1, hull_tags=tags_on_device(torch, full["tags"]),
+                  tables=tables)
     rmse = np.zeros((iters, 3), dtype=np.float32)
     ctx.fr_reconstruct(fr.volume(v, full["origin"], full["h"]), fr.cameras(full["cams"]), full["t_dev"],
                        full["bbox"], iters, p, albedo=alb, rmse=rmse)
@@ -169,7 +190,7 @@ def test_full_size_bf16_records_follow_the_16bit_oracle(orc, full):
     got = v.float().cpu().numpy().astype(np.float64)
     e16 = rel_err(got[..., :3], ref16[..., :3])
     e64 = rel_err(got[..., :3], ref64[..., :3])
-    print(f"full-size BF16: volume vs BF16 oracle max {e16.max():.2e} (p99.99 {np.quantile(e16, 0.9999):.2e}); "
+    print(f"full-size BF16 (tables={tables}): volume vs BF16 oracle max {e16.max():.2e} (p99.99 {np.quantile(e16, 0.9999):.2e}); "
           f"vs FP64 records {e64.max():.2e}; rmse gpu {rmse[-1]} oracle {r16[-1]}")
     assert e16.max() < 1e-2
     np.testing.assert_allclose(rmse, r16, rtol=1e-2)

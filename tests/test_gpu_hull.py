@@ -96,8 +96,9 @@ def test_hull_tags_match_oracle_full_size(orc, fr_ctx):
     assert 0.01 < inside < 0.6
 
 
+@pytest.mark.parametrize("tables", [1, 0], ids=["march", "auto"])
 @pytest.mark.parametrize("scatter", [False, True])
-def test_reconstruct_with_hull_follows_oracle(orc, fr_ctx, scatter):
+def test_reconstruct_with_hull_follows_oracle(orc, fr_ctx, scatter, tables):
     """The hull-restricted loop follows the oracle on the oracle's tags; with
     in-scattering its sweeps also skip the loads of line chunks in bricks
     outside the hull."""
@@ -117,7 +118,8 @@ def test_reconstruct_with_hull_follows_oracle(orc, fr_ctx, scatter):
     rmse = np.zeros((4, 3), dtype=np.float32)
     alb = torch.as_tensor(case.albedo, dtype=torch.float32, device="cuda").contiguous() if scatter else None
     ctx.fr_reconstruct(fr.volume(v, case.origin, case.h), fr.cameras(case.cams), t_dev, bbox, 4,
-                       fr.params(step=case.step, alpha_l=3e-3, use_hull=1, hull_tags=tags_on_device(torch, hull)),
+                       fr.params(step=case.step, alpha_l=3e-3, use_hull=1, hull_tags=tags_on_device(torch, hull),
+                                 tables=tables),
                        albedo=alb, rmse=rmse)
     torch.cuda.synchronize()
     got = v.cpu().numpy()
@@ -126,7 +128,7 @@ def test_reconstruct_with_hull_follows_oracle(orc, fr_ctx, scatter):
     assert np.array_equal(got[~outside][:, 3], v0[~outside][:, 3].astype(np.float32))
     np.testing.assert_allclose(rmse, rmse_ref, rtol=1e-3)
     e = rel_err(got[..., :3], vol_ref[..., :3])
-    print(f"reconstruct with hull (scatter={scatter}): max {e.max():.3e}, outside fraction {outside.mean():.3f}")
+    print(f"reconstruct with hull (scatter={scatter}, tables={tables}): max {e.max():.3e}, outside fraction {outside.mean():.3f}")
     assert e.max() < 1e-3
 
 
