@@ -73,7 +73,8 @@ struct fr_ctx {
     Buf hull, sat;                   // visual hull tags, flame-mask tables
     Buf vol_stage;                   // float32 staging of fr_volume_upload / fr_volume_download
     Buf probe;                       // measurement builds only (FR_ADJ_GATHER_PROBE)
-    Buf tab_small, tab_fwd, tab_adj, tab_dl;  // ray weight tables: counts and offsets, entries, residuals
+    Buf tab_small, tab_fwd, tab_adj, tab_dl, tab_hs;  // ray weight tables: counts and offsets, entries,
+                                                      // residuals, the hull's source records
     unsigned long long tab_stats[4] = {0, 0, 0, 0};  // sizes of the last call's tables (fr_table_stats)
     std::vector<void*> owned;        // volume records allocated by fr_volume_create
     unsigned long long* host_counter = nullptr;  // pinned host scratch of kHostScratchBytes

@@ -66,7 +66,8 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
                    &c->rmse, &c->J, &c->src, &c->flame_cnt, &c->flame_list, &c->batch, &c->pairs,
                    &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr, &c->L6, &c->fin, &c->flame_tm,
-                   &c->vol_stage, &c->probe, &c->flame_dl, &c->tab_small, &c->tab_fwd, &c->tab_adj, &c->tab_dl})
+                   &c->vol_stage, &c->probe, &c->flame_dl, &c->tab_small, &c->tab_fwd, &c->tab_adj, &c->tab_dl,
+                   &c->tab_hs})
         if (b->p) cudaFree(b->p);
     for (void* p : c->owned) cudaFree(p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
@@ -820,7 +821,18 @@ static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* v
     built = false;
     const long long nodes = node_count(vol);
     const long long nw = (long long)nt * (kTileThreads / 32);
-    const size_t nb = tab_scan_blocks(nodes > nw ? nodes : nw);
+    // the hull's key points in Morton order over the smallest cube of 2^m
+    // nodes per edge holding the grid, unless that cube has more than 8
+    // items per node (then node order)
+    KeyOrder order;
+    order.nx = vol->nx;
+    order.ny = vol->ny;
+    order.nz = vol->nz;
+    int m = 0;
+    while ((1 << m) < std::max(vol->nx, std::max(vol->ny, vol->nz))) ++m;
+    order.mbits = m <= 21 && (1LL << (3 * m)) <= 8 * nodes ? m : 0;
+    const long long nk = order.count();
+    const size_t nb = tab_scan_blocks(std::max(nk, nw));
     size_t at = 0;
     auto carve = [&](size_t bytes) {
         const size_t o = at;
@@ -829,8 +841,8 @@ static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* v
     };
     const size_t o_wrows = carve(nw * 4), o_woff = carve(nw * 4), o_tfl = carve((size_t)nt * 4),
                  o_tfoff = carve((size_t)nt * 4), o_ncnt = carve((size_t)nodes * 4),
-                 o_hnode = carve((size_t)nodes * 4), o_hend = carve((size_t)nodes * 4), o_bsum = carve(nb * 8),
-                 o_tot = carve(4 * 8);
+                 o_hnode = carve((size_t)nodes * 4), o_hend = carve((size_t)nodes * 4),
+                 o_hid = carve((size_t)nodes * 4), o_bsum = carve(nb * 8), o_tot = carve(4 * 8);
     fr_status st = ensure(c, c->tab_small, at, "table counts");
     if (st == FR_ENOMEM) {
         c->err[0] = '\0';
@@ -847,6 +859,9 @@ static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* v
     b.tfoff = reinterpret_cast<unsigned*>(base + o_tfoff);
     b.ncnt = reinterpret_cast<unsigned*>(base + o_ncnt);
     b.hnode = reinterpret_cast<unsigned*>(base + o_hnode);
+    b.hid = reinterpret_cast<unsigned*>(base + o_hid);
+    b.order = order;
+    b.nodes = nodes;
     unsigned* hend = reinterpret_cast<unsigned*>(base + o_hend);
     unsigned long long* totals = reinterpret_cast<unsigned long long*>(base + o_tot);
     static thread_local SingleArgs bf;
@@ -855,7 +870,7 @@ static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* v
     cudaStream_t s = c->stream;
     FR_CUDA(c, cudaMemsetAsync(b.ncnt, 0, (size_t)nodes * 4, s));
     FR_CUDA(c, launch_tab_count(bf, b, vol->dtype, nt, s));
-    FR_CUDA(c, launch_tab_scans(b, nt, nodes, reinterpret_cast<unsigned long long*>(base + o_bsum), totals, s));
+    FR_CUDA(c, launch_tab_scans(b, nt, reinterpret_cast<unsigned long long*>(base + o_bsum), totals, s));
     static_assert(kHostScratchBytes >= 32, "host scratch holds the four totals");
     FR_CUDA(c, cudaMemcpyAsync(c->host_counter, totals, 32, cudaMemcpyDeviceToHost, s));
     FR_CUDA(c, cudaStreamSynchronize(s));
@@ -866,6 +881,7 @@ static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* v
     st = ensure(c, c->tab_fwd, (size_t)rows * 32 * 8, "forward table");
     if (st == FR_OK) st = ensure(c, c->tab_adj, (size_t)nadj * 8, "adjustment table");
     if (st == FR_OK) st = ensure(c, c->tab_dl, (size_t)nflame * 16, "flame residuals");
+    if (st == FR_OK) st = ensure(c, c->tab_hs, (size_t)nhull * rec_bytes(vol), "hull records");
     if (st == FR_ENOMEM) {
         c->err[0] = '\0';
         return FR_OK;
@@ -886,6 +902,7 @@ static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* v
     it.eadj = b.eadj;
     it.hnode = b.hnode;
     it.hend = hend;
+    it.hs = c->tab_hs.p;
     it.dl = static_cast<float4*>(c->tab_dl.p);
     it.nhull = (unsigned)nhull;
     it.nflame = (unsigned)nflame;
@@ -1247,6 +1264,7 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
                                                  p->skip_empty != 0, nbox, PackOut{}));
                 FR_TRY(trace_mark(c, FR_PHASE_SCATTER));
             }
+            FR_CUDA(c, launch_tab_stage(render_vol, vol->dtype, tab, st));
             FR_CUDA(c, launch_tab_forward(f, tab, vol->dtype, nt, st));
             FR_TRY(trace_mark(c, FR_PHASE_FORWARD));
             FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * slot, st, 0, fin,

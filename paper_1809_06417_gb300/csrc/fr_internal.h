@@ -95,6 +95,47 @@ cudaError_t launch_adjust_list(const SingleArgs& a, int dt, int ntiles, const un
 // tables.cu: the paper-rule loop over a fixed extinction field as a forward
 // table (per ray: key point, A) and an adjustment table (per key point of the
 // hull: flame ray, W), built by two marches over every ray.
+// 3D Morton codes: bit i of a coordinate goes to bit 3 i (+0 x, +1 y, +2 z)
+// of the code; coordinates below 2^21.
+__host__ __device__ inline unsigned long long morton_spread(unsigned v)
+{
+    unsigned long long x = v & 0x1fffffull;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+__host__ __device__ inline unsigned morton_compact(unsigned long long x)
+{
+    x &= 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+    x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+    x = (x ^ (x >> 32)) & 0x1fffffull;
+    return (unsigned)x;
+}
+// The order the tables list key points in: item i of [0, count()) names
+// node(i), or -1 for an item outside the grid.  mbits > 0: Morton order over
+// a cube of 2^mbits nodes per edge; 0: node order.
+struct KeyOrder {
+    int nx = 0, ny = 0, nz = 0, mbits = 0;
+    __host__ __device__ long long count() const
+    {
+        return mbits ? 1LL << (3 * mbits) : (long long)nx * ny * nz;
+    }
+    __device__ long long node(long long i) const
+    {
+        if (!mbits) return i;
+        const unsigned long long c = (unsigned long long)i;
+        const unsigned x = morton_compact(c), y = morton_compact(c >> 1), z = morton_compact(c >> 2);
+        if (x >= (unsigned)nx || y >= (unsigned)ny || z >= (unsigned)nz) return -1;
+        return ((long long)z * ny + y) * nx + x;
+    }
+};
+
 struct TabBuild {
     const unsigned* tags;   // visual hull tags; key points whose tag is `full` are inside
     unsigned full;
@@ -103,8 +144,11 @@ struct TabBuild {
     unsigned* tfl;          // per tile: flame rays
     unsigned* tfoff;        // per tile: number of its first flame ray
     unsigned* ncnt;         // per node: adjustment entries (count pass), then the next free one (fill pass)
-    unsigned* hnode;        // the hull's key points in node order
-    uint2* efwd;            // forward entries {node, A}
+    unsigned* hnode;        // the hull's key points in the listing order
+    unsigned* hid;          // per node inside the hull: its place in that list
+    KeyOrder order;
+    long long nodes;
+    uint2* efwd;            // forward entries {place in the hull's list, A}
     uint2* eadj;            // adjustment entries {flame ray, W}
     unsigned long long nadj;
     unsigned nhull;         // key points inside the hull (fill pass)
@@ -117,6 +161,7 @@ struct TabIter {
     const uint2* eadj;
     const unsigned* hnode;
     const unsigned* hend;   // per key point of the hull: end of its entries
+    void* hs;               // per key point of the hull: its source record (the forward's gather)
     float4* dl;             // per flame ray: its residual {r, g, b, 0}
     unsigned nhull, nflame, nadj;
 };
@@ -125,15 +170,18 @@ struct TabIter {
 cudaError_t launch_tab_count(const SingleArgs& a, const TabBuild& b, int dt, int ntiles, cudaStream_t s);
 // exclusive scans of the counts: totals[0] rows, [1] flame rays, [2]
 // adjustment entries, [3] key points inside the hull (bsum:
-// tab_scan_blocks(max(nodes, warps)) words)
-cudaError_t launch_tab_scans(const TabBuild& b, int ntiles, long long nodes, unsigned long long* bsum,
-                             unsigned long long* totals, cudaStream_t s);
+// tab_scan_blocks(max(warps, b.order.count())) words); then b.hid of the
+// listed key points
+cudaError_t launch_tab_scans(const TabBuild& b, int ntiles, unsigned long long* bsum, unsigned long long* totals,
+                             cudaStream_t s);
 size_t tab_scan_blocks(long long n);
 cudaError_t launch_tab_fill(const SingleArgs& a, const TabBuild& b, int dt, int ntiles, cudaStream_t s);
 cudaError_t launch_tab_hend(const unsigned* hnode, const unsigned* cursor, unsigned nh, unsigned* hend,
                             cudaStream_t s);
-// each key point's adjustment entries in increasing flame-ray order
+// each key point's adjustment entries in increasing flame-ray order (FR_TAB_SORT builds)
 cudaError_t launch_tab_sort(uint2* eadj, const unsigned* hend, unsigned nh, cudaStream_t s);
+// it.hs[h] = records[it.hnode[h]] (records: the volume's storage type)
+cudaError_t launch_tab_stage(const void* records, int dt, const TabIter& it, cudaStream_t s);
 // a.p.vol: the source records; targets, bbox and partials as for the forward
 // march (rendered and residual images when set)
 cudaError_t launch_tab_forward(const SingleArgs& a, const TabIter& it, int dt, int ntiles, cudaStream_t s);

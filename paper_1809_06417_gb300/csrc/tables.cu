@@ -21,17 +21,19 @@
 // adjustment table key point by key point (a gather of the flame rays'
 // residuals: the per-key-point gather form of the adjustment, no atomics).
 //
-// Layouts.  Forward table: warp w (one of the four 8 x 4 sub-tiles of a
-// 16 x 8 pixel tile, as in the marches) owns rows [woff[w], woff[w] + wrows[w]);
-// row r holds one entry per lane at 32 r + lane, {node, A as float bits}; a
-// lane's rows after its last entry hold the hull's first key point with
-// weight 0.  Flame rays are numbered in
-// tile order (the tile's offset tfoff plus the ray's rank among the tile's
-// flame pixels).  Adjustment table: key point h of the hull list (node
-// hnode[h], nodes in index order) owns entries [hend[h - 1], hend[h]) of
-// {flame-ray number, W as float bits}, in increasing flame-ray order (so
-// that neighbouring entries name neighbouring rays, whose residuals share
-// cache lines).
+// Layouts.  The hull's key points are listed in Morton (Z) order of their
+// node coordinates (node order when the grid is far from cubic): hnode[h] is
+// the node of list entry h, and each iteration copies the source records of
+// the list into hs[h] first, so that the key points a bundle of neighbouring
+// rays samples lie close together in memory.  Forward table: warp w (one of
+// the four 8 x 4 sub-tiles of a 16 x 8 pixel tile, as in the marches) owns
+// rows [woff[w], woff[w] + wrows[w]); row r holds one entry per lane at
+// 32 r + lane, {h, A as float bits}; a lane's rows after its last entry hold
+// {0, 0}.  Flame rays are numbered in tile order (the tile's offset tfoff
+// plus the ray's rank among the tile's flame pixels).  Adjustment table: key
+// point h of the hull list owns entries [hend[h - 1], hend[h]) of
+// {flame-ray number, W as float bits}, in the order the fill pass's atomics
+// hand out (built with FR_TAB_SORT = 1: in increasing flame-ray order).
 #include "fr_device.cuh"
 #include "fr_internal.h"
 
@@ -119,9 +121,16 @@ __device__ __forceinline__ bool flame_pixel(const ProbDev& P, long long pix)
 // entries of every key point (ncnt, zeroed beforehand).  Fill pass (fill =
 // 1): the entries themselves, ncnt holding each key point's next free
 // adjustment entry; writes past the counted rows or entries are dropped.
+#ifndef FR_TAB_BUILD_MINB
+#define FR_TAB_BUILD_MINB 0
+#endif
+#if FR_TAB_BUILD_MINB
+#define FR_TAB_BUILD_BOUNDS __launch_bounds__(kTileThreads, FR_TAB_BUILD_MINB)
+#else
+#define FR_TAB_BUILD_BOUNDS __launch_bounds__(kTileThreads)
+#endif
 template <int DT>
-__global__ void __launch_bounds__(kTileThreads) tab_build_kernel(const __grid_constant__ SingleArgs a, TabBuild b,
-                                                                 int fill)
+__global__ void FR_TAB_BUILD_BOUNDS tab_build_kernel(const __grid_constant__ SingleArgs a, TabBuild b, int fill)
 {
     const ProbDev& P = a.p;
     int view, px, py;
@@ -148,7 +157,7 @@ __global__ void __launch_bounds__(kTileThreads) tab_build_kernel(const __grid_co
     if (valid)
         tab_march<DT>(P, a.cams[view], px, py, flame, b.tags, b.full, fill != 0, [&](int node, float A, float W) {
             if (fill) {
-                if (n < rows) out[(size_t)n * 32] = make_uint2((unsigned)node, __float_as_uint(A));
+                if (n < rows) out[(size_t)n * 32] = make_uint2(__ldg(b.hid + node), __float_as_uint(A));
                 if (flame) {
                     const unsigned at = atomicAdd(b.ncnt + node, 1u);
                     if (at < b.nadj) b.eadj[at] = make_uint2(fid, __float_as_uint(W));
@@ -159,9 +168,8 @@ __global__ void __launch_bounds__(kTileThreads) tab_build_kernel(const __grid_co
             ++n;
         });
     if (fill) {
-        // padding: a key point of the hull (whose source record is defined) with weight 0
-        const unsigned pad = b.nhull ? __ldg(b.hnode) : 0u;
-        for (; n < rows; ++n) out[(size_t)n * 32] = make_uint2(pad, 0u);
+        // padding: the hull's first key point with weight 0
+        for (; n < rows; ++n) out[(size_t)n * 32] = make_uint2(0u, 0u);
     } else {
         n = __reduce_max_sync(0xffffffffu, n);
         const int nflame = __syncthreads_count(flame);
@@ -212,21 +220,46 @@ struct GetU32 {
     const unsigned* v;
     __device__ unsigned operator()(long long i) const { return __ldg(v + i); }
 };
-struct GetInHull {
+// per key point in the listing order: its adjustment entries, whether it is inside the hull
+struct GetCountOrdered {
+    const unsigned* ncnt;
+    KeyOrder o;
+    __device__ unsigned operator()(long long i) const
+    {
+        const long long n = o.node(i);
+        return n < 0 ? 0u : __ldg(ncnt + n);
+    }
+};
+struct GetInHullOrdered {
     const unsigned* tags;
     unsigned full;
-    __device__ unsigned operator()(long long i) const { return __ldg(tags + i) == full ? 1u : 0u; }
+    KeyOrder o;
+    __device__ unsigned operator()(long long i) const
+    {
+        const long long n = o.node(i);
+        return n >= 0 && __ldg(tags + n) == full ? 1u : 0u;
+    }
 };
 // Scan outputs: item i with its exclusive prefix `at` and value v.
 struct PutU32 {
     unsigned* out;
     __device__ void operator()(long long i, unsigned long long at, unsigned) const { out[i] = (unsigned)at; }
 };
-struct PutCompact {
+struct PutCursorOrdered {
+    unsigned* ncnt;
+    KeyOrder o;
+    __device__ void operator()(long long i, unsigned long long at, unsigned) const
+    {
+        const long long n = o.node(i);
+        if (n >= 0) ncnt[n] = (unsigned)at;
+    }
+};
+struct PutCompactOrdered {
     unsigned* list;
+    KeyOrder o;
     __device__ void operator()(long long i, unsigned long long at, unsigned v) const
     {
-        if (v) list[at] = (unsigned)i;
+        if (v) list[at] = (unsigned)o.node(i);
     }
 };
 
@@ -290,6 +323,24 @@ cudaError_t scan(Get get, Put put, long long n, unsigned long long* bsum, unsign
     return cudaGetLastError();
 }
 
+// hid[hnode[h]] = h for the *count key points of the hull
+__global__ void __launch_bounds__(256) hid_kernel(const unsigned* __restrict__ hnode,
+                                                  const unsigned long long* __restrict__ count, unsigned* __restrict__ hid)
+{
+    const unsigned long long h = blockIdx.x * 256ull + threadIdx.x;
+    if (h < *count) hid[__ldg(hnode + h)] = (unsigned)h;
+}
+
+// The records the forward gathers, for the hull's key points in the list's
+// order: hs[h] = records[hnode[h]] (R: the record's bytes as one vector).
+template <class R>
+__global__ void __launch_bounds__(256) stage_kernel(const R* __restrict__ rec, const unsigned* __restrict__ hnode,
+                                                    unsigned nh, R* __restrict__ hs)
+{
+    const unsigned h = blockIdx.x * 256u + threadIdx.x;
+    if (h < nh) hs[h] = __ldg(rec + __ldg(hnode + h));
+}
+
 __global__ void __launch_bounds__(256) hend_kernel(const unsigned* __restrict__ hnode, const unsigned* __restrict__ cursor,
                                                    unsigned nh, unsigned* __restrict__ hend)
 {
@@ -299,9 +350,11 @@ __global__ void __launch_bounds__(256) hend_kernel(const unsigned* __restrict__ 
 
 // Each key point's adjustment entries in increasing flame-ray order (the fill
 // pass appends them in the order its atomics return): one warp per key point
-// ranks its entries in shared memory (a flame ray names a key point once:
-// the eight cells around it form a convex box, which a ray enters and leaves
-// once).  Key points with more than kSortMax entries keep their order.
+// sorts its entries in shared memory by a bitonic network over the next power
+// of two (padding keys sort last).  A flame ray names a key point once (the
+// eight cells around it form a convex box, which a ray enters and leaves
+// once), so the order is unique.  Key points with more than kSortMax entries
+// keep their order.
 constexpr int kSortMax = 512;
 constexpr int kSortWarps = 8;
 __global__ void __launch_bounds__(32 * kSortWarps) tab_sort_kernel(uint2* __restrict__ eadj,
@@ -313,14 +366,28 @@ __global__ void __launch_bounds__(32 * kSortWarps) tab_sort_kernel(uint2* __rest
     if (g >= nh) return;
     const unsigned b = g ? __ldg(hend + g - 1) : 0u, e = __ldg(hend + g), n = e - b;
     if (n <= 1 || n > (unsigned)kSortMax) return;
-    for (unsigned i = lane; i < n; i += 32) buf[w][i] = eadj[b + i];
+    unsigned P = 32;
+    while (P < n) P <<= 1;
+    uint2* B = buf[w];
+    for (unsigned i = lane; i < P; i += 32) B[i] = i < n ? eadj[b + i] : make_uint2(0xffffffffu, 0u);
     __syncwarp();
-    for (unsigned i = lane; i < n; i += 32) {
-        const uint2 x = buf[w][i];
-        unsigned rank = 0;
-        for (unsigned j = 0; j < n; ++j) rank += buf[w][j].x < x.x ? 1u : 0u;
-        eadj[b + rank] = x;
+    for (unsigned k = 2; k <= P; k <<= 1) {
+        for (unsigned j = k >> 1; j > 0; j >>= 1) {
+            for (unsigned i = lane; i < P; i += 32) {
+                const unsigned l = i ^ j;
+                if (l > i) {
+                    const uint2 x = B[i], y = B[l];
+                    const bool up = (i & k) == 0;
+                    if ((x.x > y.x) == up) {
+                        B[i] = y;
+                        B[l] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
     }
+    for (unsigned i = lane; i < n; i += 32) eadj[b + i] = B[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -331,6 +398,40 @@ __global__ void __launch_bounds__(32 * kSortWarps) tab_sort_kernel(uint2* __rest
 #define FR_TAB_UNROLL 4
 #endif
 constexpr int kTabUnroll = FR_TAB_UNROLL;
+#ifndef FR_TAB_ADJ_UNROLL
+#define FR_TAB_ADJ_UNROLL FR_TAB_UNROLL
+#endif
+constexpr int kTabAdjUnroll = FR_TAB_ADJ_UNROLL;
+// CTAs per SM the forward is compiled for (0: no bound)
+#ifndef FR_TAB_FWD_MINB
+#define FR_TAB_FWD_MINB 0
+#endif
+#if FR_TAB_FWD_MINB
+#define FR_TAB_FWD_BOUNDS __launch_bounds__(kTileThreads, FR_TAB_FWD_MINB)
+#else
+#define FR_TAB_FWD_BOUNDS __launch_bounds__(kTileThreads)
+#endif
+// rows ahead of the current group whose entries are prefetched into L2 (0: none)
+#ifndef FR_TAB_PREFETCH
+#define FR_TAB_PREFETCH 16
+#endif
+// rows per bulk L2 prefetch of a warp's forward entries (one
+// cp.async.bulk.prefetch per chunk, a chunk ahead; 0: none)
+#ifndef FR_TAB_BULK
+#define FR_TAB_BULK 0
+#endif
+// 1: each warp of the adjustment prefetches its key points' entries into L2
+// with one bulk prefetch before it starts
+#ifndef FR_TAB_ADJ_BULK
+#define FR_TAB_ADJ_BULK 0
+#endif
+
+// L2 prefetch of `bytes` (a multiple of 16) from a 16-byte aligned address by
+// the bulk-copy unit (no completion to wait for)
+__device__ __forceinline__ void bulk_prefetch_l2(const void* p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 // Forward: each lane sums its ray's entries, A times the entry's source record
 // (rows read once per iteration: streaming loads that leave the L2 to the
@@ -338,7 +439,7 @@ constexpr int kTabUnroll = FR_TAB_UNROLL;
 // image when asked for, each flame ray's residual at its number, the tile's
 // squared-error partials.
 template <int DT>
-__global__ void __launch_bounds__(kTileThreads) tab_forward_kernel(const __grid_constant__ SingleArgs a, TabIter it)
+__global__ void FR_TAB_FWD_BOUNDS tab_forward_kernel(const __grid_constant__ SingleArgs a, TabIter it)
 {
     const ProbDev& P = a.p;
     int view, px, py;
@@ -353,20 +454,38 @@ __global__ void __launch_bounds__(kTileThreads) tab_forward_kernel(const __grid_
     // before this group's records are gathered (two dependent loads in
     // flight per row instead of one after the other)
     float L0 = 0.0f, L1 = 0.0f, L2 = 0.0f;
+#if FR_TAB_BULK
+    static_assert(FR_TAB_BULK % FR_TAB_UNROLL == 0, "bulk prefetch chunks hold whole groups");
+    const char* Erow = reinterpret_cast<const char*>(it.efwd + (size_t)__ldg(it.woff + wi) * 32);
+    if (lane == 0 && rows) bulk_prefetch_l2(Erow, min(rows, 2u * FR_TAB_BULK) * 256u);
+#endif
     uint2 cur[kTabUnroll];
 #pragma unroll
     for (int q = 0; q < kTabUnroll; ++q) cur[q] = (unsigned)q < rows ? __ldcs(E + (size_t)q * 32) : make_uint2(0u, 0u);
     for (unsigned r = 0; r < rows; r += kTabUnroll) {
+#if FR_TAB_BULK
+        // at each chunk start, the chunk after the next one
+        if (lane == 0 && r % FR_TAB_BULK == 0 && r + 2u * FR_TAB_BULK < rows)
+            bulk_prefetch_l2(Erow + (size_t)(r + 2u * FR_TAB_BULK) * 256u,
+                             min(rows - (r + 2u * FR_TAB_BULK), (unsigned)FR_TAB_BULK) * 256u);
+#endif
         uint2 nxt[kTabUnroll];
 #pragma unroll
         for (int q = 0; q < kTabUnroll; ++q) {
             const unsigned rr = r + kTabUnroll + q;
             nxt[q] = rr < rows ? __ldcs(E + (size_t)rr * 32) : make_uint2(0u, 0u);
         }
+#if FR_TAB_PREFETCH
+#pragma unroll
+        for (int q = 0; q < kTabUnroll; ++q) {
+            const unsigned rr = r + FR_TAB_PREFETCH + q;
+            if (rr < rows) asm volatile("prefetch.global.L2 [%0];" ::"l"(E + (size_t)rr * 32));
+        }
+#endif
         float4 v[kTabUnroll];
 #pragma unroll
         for (int q = 0; q < kTabUnroll; ++q)
-            v[q] = r + q < rows ? load_rgb<DT>(P.vol, FR_CHK(cur[q].x, nodes, 1u)) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            v[q] = r + q < rows ? load_rgb<DT>(it.hs, FR_CHK(cur[q].x, it.nhull, 1u)) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
         for (int q = 0; q < kTabUnroll; ++q) {
             const float A = __uint_as_float(cur[q].y);
@@ -442,31 +561,45 @@ __global__ void __launch_bounds__(kTabAdjThreads) tab_adjust_kernel(void* vol, T
     const unsigned g = (blockIdx.x * (unsigned)kTabAdjThreads + threadIdx.x) / (unsigned)kTabLanes;
     const unsigned sub = threadIdx.x & (kTabLanes - 1);
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+#if FR_TAB_ADJ_BULK
+    {
+        // the warp's key points' entries are one contiguous range
+        constexpr unsigned per_warp = 32 / kTabLanes;
+        const unsigned g0 = g - (threadIdx.x & 31) / kTabLanes;
+        if ((threadIdx.x & 31) == 0 && g0 < it.nhull) {
+            const unsigned g1 = min(g0 + per_warp, it.nhull) - 1;
+            const unsigned lo = (g0 ? min(__ldg(it.hend + g0 - 1), it.nadj) : 0u) & ~1u;
+            // (rounded to whole 16-byte pairs inside the table)
+            const unsigned hi = min((min(__ldg(it.hend + g1), it.nadj) + 1u) & ~1u, it.nadj & ~1u);
+            if (hi > lo) bulk_prefetch_l2(it.eadj + lo, (hi - lo) * 8u);
+        }
+    }
+#endif
     if (g < it.nhull) {
         const unsigned b = g ? min(__ldg(it.hend + g - 1), it.nadj) : 0u, e = min(__ldg(it.hend + g), it.nadj);
-        // kTabUnroll entries per lane at a time, the next group's loaded
+        // kTabAdjUnroll entries per lane at a time, the next group's loaded
         // before this group's residuals are gathered
         unsigned i = b + sub;
-        uint2 cur[kTabUnroll];
+        uint2 cur[kTabAdjUnroll];
 #pragma unroll
-        for (int q = 0; q < kTabUnroll; ++q) {
+        for (int q = 0; q < kTabAdjUnroll; ++q) {
             const unsigned k = i + q * kTabLanes;
             cur[q] = k < e ? __ldcs(it.eadj + k) : make_uint2(0u, 0u);
         }
-        for (; i < e; i += kTabUnroll * kTabLanes) {
-            uint2 nxt[kTabUnroll];
+        for (; i < e; i += kTabAdjUnroll * kTabLanes) {
+            uint2 nxt[kTabAdjUnroll];
 #pragma unroll
-            for (int q = 0; q < kTabUnroll; ++q) {
-                const unsigned k = i + (kTabUnroll + q) * kTabLanes;
+            for (int q = 0; q < kTabAdjUnroll; ++q) {
+                const unsigned k = i + (kTabAdjUnroll + q) * kTabLanes;
                 nxt[q] = k < e ? __ldcs(it.eadj + k) : make_uint2(0u, 0u);
             }
-            float4 d[kTabUnroll];
+            float4 d[kTabAdjUnroll];
 #pragma unroll
-            for (int q = 0; q < kTabUnroll; ++q)
+            for (int q = 0; q < kTabAdjUnroll; ++q)
                 d[q] = i + q * kTabLanes < e ? __ldg(it.dl + FR_CHK(cur[q].x, it.nflame, 8u))
                                              : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
-            for (int q = 0; q < kTabUnroll; ++q) {
+            for (int q = 0; q < kTabAdjUnroll; ++q) {
                 const float W = __uint_as_float(cur[q].y);
                 a0 = fmaf(W, d[q].x, a0); a1 = fmaf(W, d[q].y, a1); a2 = fmaf(W, d[q].z, a2);
                 cur[q] = nxt[q];
@@ -507,14 +640,23 @@ cudaError_t launch_tab_count(const SingleArgs& a, const TabBuild& b, int dt, int
     return launch_tab_build(a, b, dt, ntiles, 0, s);
 }
 
-cudaError_t launch_tab_scans(const TabBuild& b, int ntiles, long long nodes, unsigned long long* bsum,
-                             unsigned long long* totals, cudaStream_t s)
+cudaError_t launch_tab_scans(const TabBuild& b, int ntiles, unsigned long long* bsum, unsigned long long* totals,
+                             cudaStream_t s)
 {
     const long long nw = (long long)ntiles * (kTileThreads / 32);
+    const long long nk = b.order.count();
     cudaError_t e = scan(GetU32{b.wrows}, PutU32{b.woff}, nw, bsum, totals + 0, s);
     if (e == cudaSuccess) e = scan(GetU32{b.tfl}, PutU32{b.tfoff}, ntiles, bsum, totals + 1, s);
-    if (e == cudaSuccess) e = scan(GetU32{b.ncnt}, PutU32{b.ncnt}, nodes, bsum, totals + 2, s);
-    if (e == cudaSuccess) e = scan(GetInHull{b.tags, b.full}, PutCompact{b.hnode}, nodes, bsum, totals + 3, s);
+    if (e == cudaSuccess)
+        e = scan(GetCountOrdered{b.ncnt, b.order}, PutCursorOrdered{b.ncnt, b.order}, nk, bsum, totals + 2, s);
+    if (e == cudaSuccess)
+        e = scan(GetInHullOrdered{b.tags, b.full, b.order}, PutCompactOrdered{b.hnode, b.order}, nk, bsum,
+                 totals + 3, s);
+    if (e == cudaSuccess && nk > 0) {
+        // hid: each key point's place in the hull's list (nodes outside the hull keep what they held)
+        hid_kernel<<<(unsigned)((b.nodes + 255) / 256), 256, 0, s>>>(b.hnode, totals + 3, b.hid);
+        e = cudaGetLastError();
+    }
     return e;
 }
 
@@ -532,9 +674,25 @@ cudaError_t launch_tab_hend(const unsigned* hnode, const unsigned* cursor, unsig
     return cudaGetLastError();
 }
 
+#ifndef FR_TAB_SORT
+#define FR_TAB_SORT 0
+#endif
+cudaError_t launch_tab_stage(const void* records, int dt, const TabIter& it, cudaStream_t s)
+{
+    if (it.nhull == 0) return cudaSuccess;
+    const unsigned g = (it.nhull + 255) / 256;
+    if (dt == DT_F32)
+        stage_kernel<uint4><<<g, 256, 0, s>>>(static_cast<const uint4*>(records), it.hnode, it.nhull,
+                                             static_cast<uint4*>(it.hs));
+    else
+        stage_kernel<uint2><<<g, 256, 0, s>>>(static_cast<const uint2*>(records), it.hnode, it.nhull,
+                                             static_cast<uint2*>(it.hs));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tab_sort(uint2* eadj, const unsigned* hend, unsigned nh, cudaStream_t s)
 {
-    if (nh == 0) return cudaSuccess;
+    if (nh == 0 || !FR_TAB_SORT) return cudaSuccess;
     tab_sort_kernel<<<(nh + kSortWarps - 1) / kSortWarps, 32 * kSortWarps, 0, s>>>(eadj, hend, nh);
     return cudaGetLastError();
 }
