@@ -42,18 +42,18 @@ WORKLOAD = dict(name="full_rte_128^3_8x512^2", n=128, views=8, side=512, step=0.
 ITERS_PER_STEP = 50
 # kernels one step launches: hull clear with the hull's brick marks and box;
 # the tables' build (count march, four scans of three kernels, fill march,
-# entry ends, entry sort); then per iteration the in-scatter sweeps (3, over
-# the box of the hull's bricks), the forward table's render with the
-# residual, the error reduction (which also writes the rmse) and the
-# adjustment table's update
+# entry ends); then per iteration the in-scatter sweeps (3, over the box of
+# the hull's bricks), the staging of the hull's source records, the forward
+# table's render with the residual, the error reduction (which also writes
+# the rmse) and the adjustment table's update
 KERNELS_SETUP = 1 + 16
-KERNELS_PER_ITERATION = 6
+KERNELS_PER_ITERATION = 7
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures of
 # the current kernels at this workload (None where the kernel changed since)
-NCU_TRAFFIC = {("fwd", "f32"): None, ("adj", "f32"): None}
+NCU_TRAFFIC = {("fwd", "f32"): 415.42e6 + 4.00e6, ("adj", "f32"): 347.49e6 + 4.82e6}
 # lts__throughput.avg.pct_of_peak_sustained_elapsed and
 # l1tex__throughput.avg.pct_of_peak_sustained_active of the same captures
-NCU_L2_L1 = {("fwd", "f32"): None, ("adj", "f32"): None}
+NCU_L2_L1 = {("fwd", "f32"): (0.2821, 0.8601), ("adj", "f32"): (0.3495, 0.8999)}
 # instruction issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock
 # at the 2070 MHz maximum SM clock, in warp instructions per second
 ISSUE_PEAK = 152 * 4 * 2.07e9
@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--no-hull", action="store_true",
                     help="reconstruct the whole box instead of the visual hull (Sec. 4.3.1)")
     ap.add_argument("--no-skip", action="store_true", help="march empty bricks too (same result, slower)")
+    ap.add_argument("--march", action="store_true",
+                    help="march every iteration instead of building the ray weight tables (fr_params.tables = 1)")
     ap.add_argument("--profile-video", action="store_true",
                     help="run the video batch once with the profiler range around its timed graph only "
                          "(for ncu --profile-from-start off)")
@@ -207,7 +209,8 @@ def method_params(args, I):
     w = WORKLOAD
     hull = w["hull"] and not args.no_hull
     return fr.params(step=w["step"], alpha_l=w["alpha_l"], use_hull=int(hull),
-                     hull_tags=I["tags"] if hull else None, skip_empty=int(not args.no_skip))
+                     hull_tags=I["tags"] if hull else None, skip_empty=int(not args.no_skip),
+                     tables=1 if args.march else 0)
 
 
 def run_ours(args, ws, rank, local):
