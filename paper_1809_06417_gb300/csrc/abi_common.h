@@ -76,6 +76,8 @@ struct fr_ctx {
     Buf tab_small, tab_fwd, tab_adj, tab_dl, tab_hs;  // ray weight tables: counts and offsets, entries,
                                                       // residuals, the hull's source records
     unsigned long long tab_stats[4] = {0, 0, 0, 0};  // sizes of the last call's tables (fr_table_stats)
+    void* tab_host = nullptr;        // pinned host scratch of the tables' build (warps' rows, tile order)
+    size_t tab_host_bytes = 0;
     std::vector<void*> owned;        // volume records allocated by fr_volume_create
     unsigned long long* host_counter = nullptr;  // pinned host scratch of kHostScratchBytes
     void* staging = nullptr;         // pinned host staging of batch tables

@@ -72,6 +72,7 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     for (void* p : c->owned) cudaFree(p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
     if (c->staging) cudaFreeHost(c->staging);
+    if (c->tab_host) cudaFreeHost(c->tab_host);
     if (c->staging_done) cudaEventDestroy(c->staging_done);
     if (c->capture) cudaStreamDestroy(c->capture);
     if (c->aux) cudaStreamDestroy(c->aux);
@@ -842,7 +843,8 @@ static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* v
     const size_t o_wrows = carve(nw * 4), o_woff = carve(nw * 4), o_tfl = carve((size_t)nt * 4),
                  o_tfoff = carve((size_t)nt * 4), o_ncnt = carve((size_t)nodes * 4),
                  o_hnode = carve((size_t)nodes * 4), o_hend = carve((size_t)nodes * 4),
-                 o_hid = carve((size_t)nodes * 4), o_bsum = carve(nb * 8), o_tot = carve(4 * 8);
+                 o_hid = carve((size_t)nodes * 4), o_order = carve((size_t)nt * 4), o_bsum = carve(nb * 8),
+                 o_tot = carve(4 * 8);
     fr_status st = ensure(c, c->tab_small, at, "table counts");
     if (st == FR_ENOMEM) {
         c->err[0] = '\0';
@@ -873,6 +875,20 @@ static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* v
     FR_CUDA(c, launch_tab_scans(b, nt, reinterpret_cast<unsigned long long*>(base + o_bsum), totals, s));
     static_assert(kHostScratchBytes >= 32, "host scratch holds the four totals");
     FR_CUDA(c, cudaMemcpyAsync(c->host_counter, totals, 32, cudaMemcpyDeviceToHost, s));
+    // the warps' rows too, for the forward's tile order (pinned: the order's
+    // upload below stays asynchronous)
+    const size_t host_need = (size_t)nw * 4 + (size_t)nt * 4;
+    if (c->tab_host_bytes < host_need) {
+        FR_CUDA(c, cudaStreamSynchronize(s));
+        if (c->tab_host) cudaFreeHost(c->tab_host);
+        c->tab_host = nullptr;
+        c->tab_host_bytes = 0;
+        FR_CUDA(c, cudaMallocHost(&c->tab_host, host_need));
+        c->tab_host_bytes = host_need;
+    }
+    unsigned* wrows_host = static_cast<unsigned*>(c->tab_host);
+    unsigned* order_host = wrows_host + nw;
+    FR_CUDA(c, cudaMemcpyAsync(wrows_host, b.wrows, (size_t)nw * 4, cudaMemcpyDeviceToHost, s));
     FR_CUDA(c, cudaStreamSynchronize(s));
     unsigned long long tot[4];
     memcpy(tot, c->host_counter, sizeof tot);
@@ -891,10 +907,16 @@ static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* v
     b.eadj = static_cast<uint2*>(c->tab_adj.p);
     b.nadj = nadj;
     b.nhull = (unsigned)nhull;
+    // the tiles, longest first, for the fill and for every iteration's forward
+    unsigned* order_dev = reinterpret_cast<unsigned*>(base + o_order);
+    tab_tile_order(wrows_host, nt, order_host);
+    FR_CUDA(c, cudaMemcpyAsync(order_dev, order_host, (size_t)nt * 4, cudaMemcpyHostToDevice, s));
+    b.torder = order_dev;
     FR_CUDA(c, launch_tab_fill(bf, b, vol->dtype, nt, s));
     FR_CUDA(c, launch_tab_hend(b.hnode, b.ncnt, (unsigned)nhull, hend, s));
     FR_CUDA(c, launch_tab_sort(b.eadj, hend, (unsigned)nhull, s));
     it = TabIter{};
+    it.torder = order_dev;
     it.wrows = b.wrows;
     it.woff = b.woff;
     it.tfoff = b.tfoff;

@@ -146,6 +146,7 @@ struct TabBuild {
     unsigned* ncnt;         // per node: adjustment entries (count pass), then the next free one (fill pass)
     unsigned* hnode;        // the hull's key points in the listing order
     unsigned* hid;          // per node inside the hull: its place in that list
+    const unsigned* torder; // the fill's tiles in launch order (nullable: tile order)
     KeyOrder order;
     long long nodes;
     uint2* efwd;            // forward entries {place in the hull's list, A}
@@ -163,6 +164,7 @@ struct TabIter {
     const unsigned* hend;   // per key point of the hull: end of its entries
     void* hs;               // per key point of the hull: its source record (the forward's gather)
     float4* dl;             // per flame ray: its residual {r, g, b, 0}
+    const unsigned* torder; // the forward's tiles in launch order (nullable: tile order)
     unsigned nhull, nflame, nadj;
 };
 // a.p: the problem with targets, cameras and the hull's brick table
@@ -189,6 +191,9 @@ cudaError_t launch_tab_forward(const SingleArgs& a, const TabIter& it, int dt, i
 cudaError_t launch_tab_adjust(void* vol, int dt, long long nodes, const TabIter& it, int clamp_nonneg,
                               cudaStream_t s);
 cudaError_t check_word_tables(unsigned* word, bool reset);
+// host: the forward's tiles in launch order from the warps' rows (the tile
+// with the most rows in one warp first; FR_TAB_LPT = 0: tile order)
+void tab_tile_order(const unsigned* wrows, int ntiles, unsigned* order);
 
 // volume.cu
 cudaError_t launch_apply(void* vol, int dt, int kind, long long nodes, float* dV, float scale,

@@ -34,6 +34,9 @@
 // point h of the hull list owns entries [hend[h - 1], hend[h]) of
 // {flame-ray number, W as float bits}, in the order the fill pass's atomics
 // hand out (built with FR_TAB_SORT = 1: in increasing flame-ray order).
+#include <algorithm>
+#include <vector>
+
 #include "fr_device.cuh"
 #include "fr_internal.h"
 
@@ -133,14 +136,16 @@ template <int DT>
 __global__ void FR_TAB_BUILD_BOUNDS tab_build_kernel(const __grid_constant__ SingleArgs a, TabBuild b, int fill)
 {
     const ProbDev& P = a.p;
+    // the fill takes the tiles longest first (b.torder), the count in tile order
+    const unsigned tile = fill && b.torder ? __ldg(b.torder + blockIdx.x) : blockIdx.x;
     int view, px, py;
-    tile_pixel(P, blockIdx.x, view, px, py);
+    tile_pixel(P, (int)tile, view, px, py);
     const bool valid = px < P.W && py < P.H;
     const long long pix = ((long long)view * P.H + py) * P.W + px;
     const bool flame = valid && flame_pixel(P, pix);
     __shared__ unsigned wc[kTileThreads / 32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned wi = blockIdx.x * (kTileThreads / 32) + w;
+    const unsigned wi = tile * (kTileThreads / 32) + w;
     unsigned fid = 0, rows = 0;
     uint2* out = nullptr;
     if (fill) {
@@ -148,7 +153,7 @@ __global__ void FR_TAB_BUILD_BOUNDS tab_build_kernel(const __grid_constant__ Sin
         const unsigned m = __ballot_sync(0xffffffffu, flame);
         if (lane == 0) wc[w] = (unsigned)__popc(m);
         __syncthreads();
-        fid = __ldg(b.tfoff + blockIdx.x) + (unsigned)__popc(m & ((1u << lane) - 1u));
+        fid = __ldg(b.tfoff + tile) + (unsigned)__popc(m & ((1u << lane) - 1u));
         for (int i = 0; i < w; ++i) fid += wc[i];
         rows = __ldg(b.wrows + wi);
         out = b.efwd + (size_t)__ldg(b.woff + wi) * 32 + lane;
@@ -174,7 +179,7 @@ __global__ void FR_TAB_BUILD_BOUNDS tab_build_kernel(const __grid_constant__ Sin
         n = __reduce_max_sync(0xffffffffu, n);
         const int nflame = __syncthreads_count(flame);
         if (lane == 0) b.wrows[wi] = n;
-        if (threadIdx.x == 0) b.tfl[blockIdx.x] = (unsigned)nflame;
+        if (threadIdx.x == 0) b.tfl[tile] = (unsigned)nflame;
     }
 }
 
@@ -443,9 +448,11 @@ __global__ void FR_TAB_FWD_BOUNDS tab_forward_kernel(const __grid_constant__ Sin
 {
     const ProbDev& P = a.p;
     int view, px, py;
-    tile_pixel(P, blockIdx.x, view, px, py);
+    // the tiles in the order of it.torder (longest first, so the grid ends on short ones)
+    const unsigned tile = it.torder ? __ldg(it.torder + blockIdx.x) : blockIdx.x;
+    tile_pixel(P, (int)tile, view, px, py);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned wi = blockIdx.x * (kTileThreads / 32) + w;
+    const unsigned wi = tile * (kTileThreads / 32) + w;
     const unsigned rows = __ldg(it.wrows + wi);
     const uint2* E = it.efwd + (size_t)__ldg(it.woff + wi) * 32 + lane;
     const long long nodes = (long long)P.nx * P.ny * P.nz;
@@ -530,7 +537,7 @@ __global__ void FR_TAB_FWD_BOUNDS tab_forward_kernel(const __grid_constant__ Sin
     }
     __syncthreads();
     if (flame) {
-        unsigned fid = __ldg(it.tfoff + blockIdx.x) + (unsigned)__popc(m & ((1u << lane) - 1u));
+        unsigned fid = __ldg(it.tfoff + tile) + (unsigned)__popc(m & ((1u << lane) - 1u));
         for (int i = 0; i < w; ++i) fid += wc[i];
         it.dl[FR_CHK(fid, it.nflame, 8u)] = make_float4(d0, d1, d2, 0.0f);
     }
@@ -538,7 +545,7 @@ __global__ void FR_TAB_FWD_BOUNDS tab_forward_kernel(const __grid_constant__ Sin
         float s = 0.0f;
 #pragma unroll
         for (int i = 0; i < kTileThreads / 32; ++i) s += red[threadIdx.x][i];
-        P.partials[4 * (long long)blockIdx.x + threadIdx.x] = s;
+        P.partials[4 * (long long)tile + threadIdx.x] = s;
     }
 }
 
@@ -715,6 +722,32 @@ cudaError_t launch_tab_adjust(void* vol, int dt, long long nodes, const TabIter&
     else if (dt == DT_BF16) tab_adjust_kernel<DT_BF16><<<g, kTabAdjThreads, 0, s>>>(vol, it, clamp_nonneg, nodes);
     else tab_adjust_kernel<DT_F16><<<g, kTabAdjThreads, 0, s>>>(vol, it, clamp_nonneg, nodes);
     return cudaGetLastError();
+}
+
+#ifndef FR_TAB_LPT
+#define FR_TAB_LPT 1
+#endif
+void tab_tile_order(const unsigned* wrows, int ntiles, unsigned* order)
+{
+    for (int t = 0; t < ntiles; ++t) order[t] = (unsigned)t;
+    if (!FR_TAB_LPT) return;
+    constexpr int wpt = kTileThreads / 32;
+    auto len = [wrows](unsigned t) {
+        unsigned m = 0;
+        for (int w = 0; w < wpt; ++w) m = std::max(m, wrows[(size_t)t * wpt + w]);
+        return m;
+    };
+    // counting sort by the length, longest first, tile order among equals
+    std::vector<unsigned> key(ntiles);
+    unsigned kmax = 0;
+    for (int t = 0; t < ntiles; ++t) {
+        key[t] = len((unsigned)t);
+        kmax = std::max(kmax, key[t]);
+    }
+    std::vector<unsigned> at((size_t)kmax + 2, 0u);
+    for (int t = 0; t < ntiles; ++t) ++at[kmax - key[t] + 1];
+    for (size_t k = 1; k < at.size(); ++k) at[k] += at[k - 1];
+    for (int t = 0; t < ntiles; ++t) order[at[kmax - key[t]]++] = (unsigned)t;
 }
 
 cudaError_t check_word_tables(unsigned* word, bool reset)
