@@ -121,7 +121,7 @@ typedef struct fr_params {
                             from the volume's centre to its camera */
     int32_t sequential_views; /* fr_reconstruct: 1 = update the volume after each view in turn
                             (Kaczmarz order; the source is recomputed before each view) */
-    int32_t tables;      /* fr_reconstruct, paper rule with the visual hull, skip_empty, field mode
+    int32_t tables;      /* fr_reconstruct and the server's jobs, paper rule with the visual hull, skip_empty, field mode
                             (tau <= 0), g_std = 0, all views at once: the extinction stays fixed and
                             G(s) = 1, so rendering (Eqs. 5-8) and the adjustment (Eq. 10) are linear
                             maps whose weights do not change between iterations.  0: build them once
@@ -333,7 +333,11 @@ fr_status fr_reconstruct_batch(fr_ctx *ctx, const fr_problem *probs, int nprob, 
  * every step advances all resident jobs by one iteration of the paper rule in
  * shared launches (their rays batched together); jobs join and leave at step
  * boundaries.  Volumes are held in the server's storage type with float32
- * arithmetic.  Calls on one server must not run concurrently.
+ * arithmetic.  With use_hull, skip_empty, field mode and g_std = 0 (and
+ * p->tables as for fr_reconstruct), a job builds its ray weight tables at
+ * admission (its footprint then grows by their size, inside the budget; a job
+ * with no room for them marches) and its iterations stream them in shared
+ * launches.  Calls on one server must not run concurrently.
  * ------------------------------------------------------------------------- */
 typedef struct fr_server fr_server;
 typedef struct fr_job fr_job;

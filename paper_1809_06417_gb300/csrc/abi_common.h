@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -73,8 +74,7 @@ struct fr_ctx {
     Buf hull, sat;                   // visual hull tags, flame-mask tables
     Buf vol_stage;                   // float32 staging of fr_volume_upload / fr_volume_download
     Buf probe;                       // measurement builds only (FR_ADJ_GATHER_PROBE)
-    Buf tab_small, tab_fwd, tab_adj, tab_dl, tab_hs;  // ray weight tables: counts and offsets, entries,
-                                                      // residuals, the hull's source records
+    Buf tab_small, tab_fwd;          // ray weight tables: counts, offsets and the hull's list; the tables
     unsigned long long tab_stats[4] = {0, 0, 0, 0};  // sizes of the last call's tables (fr_table_stats)
     void* tab_host = nullptr;        // pinned host scratch of the tables' build (warps' rows, tile order)
     size_t tab_host_bytes = 0;
@@ -358,3 +358,21 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Visual hull tags of one problem (api.cu): flame-mask tables in the
 // context's scratch, one tag per node into `tags` (device).
 fr_status hull_tags(fr_ctx* c, const SingleArgs& a, const float* targets, float thresh, unsigned* tags);
+
+// Where build_tables takes its device memory: `scratch` (counts, offsets and
+// the hull's list, used by every iteration too) and then `tables` (the two
+// tables, the flame rays' residuals and the hull's staged records in one
+// block); either returns nullptr when there is no room (the caller then
+// marches) and sets *status to another code than FR_ENOMEM on a real error.
+struct TabMemory {
+    std::function<void*(size_t)> scratch, tables;
+    fr_status* status = nullptr;
+};
+
+// The ray weight tables of one problem (api.cu): f the problem (cameras,
+// targets) with the hull's brick table (adj_occ, adj_box) and its
+// parameters; vol the volume whose extinction fixes the transmittance.
+// built = false (and FR_OK) when there was no room or the tables would need
+// 2^32 entries; *bytes: the device bytes taken from `mem`.
+fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* vol, const unsigned* tags, unsigned full,
+                       int nt, const TabMemory& mem, TabIter& it, bool& built, size_t* bytes = nullptr);

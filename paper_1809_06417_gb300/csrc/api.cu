@@ -66,8 +66,7 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
                    &c->rmse, &c->J, &c->src, &c->flame_cnt, &c->flame_list, &c->batch, &c->pairs,
                    &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr, &c->L6, &c->fin, &c->flame_tm,
-                   &c->vol_stage, &c->probe, &c->flame_dl, &c->tab_small, &c->tab_fwd, &c->tab_adj, &c->tab_dl,
-                   &c->tab_hs})
+                   &c->vol_stage, &c->probe, &c->flame_dl, &c->tab_small, &c->tab_fwd})
         if (b->p) cudaFree(b->p);
     for (void* p : c->owned) cudaFree(p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
@@ -810,16 +809,14 @@ extern "C" fr_status fr_visual_hull(fr_ctx* c, const fr_volume* vol, const fr_ca
 // The loop of fr_reconstruct (stop_delta < 0: exactly `iters` iterations) and
 // of fr_reconstruct_until (stop_delta >= 0: at most `iters` iterations, ended
 // on the device by the stop criterion inside a conditional CUDA graph).
-// The ray weight tables of a reconstruction (tables.cu): the count pass, the
-// scans (whose totals the host reads, to size the entries), the fill pass.
-// f: the problem (cameras, targets) with the hull's brick table; records: the
-// volume whose extinction fixes the transmittance.  built stays false, with
-// nothing launched after the count pass's scratch, when the tables would
-// pass the context's scratch limit or 2^32 entries (the marches then run).
-static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* vol, const unsigned* tags,
-                              unsigned full, int nt, TabIter& it, bool& built)
+// The ray weight tables of a problem (tables.cu): the count march, the scans
+// (whose totals and per-warp rows the host reads, to size the tables and to
+// order the tiles longest first), the fill march.
+fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* vol, const unsigned* tags, unsigned full,
+                       int nt, const TabMemory& mem, TabIter& it, bool& built, size_t* bytes)
 {
     built = false;
+    if (bytes) *bytes = 0;
     const long long nodes = node_count(vol);
     const long long nw = (long long)nt * (kTileThreads / 32);
     // the hull's key points in Morton order over the smallest cube of 2^m
@@ -835,9 +832,9 @@ static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* v
     const long long nk = order.count();
     const size_t nb = tab_scan_blocks(std::max(nk, nw));
     size_t at = 0;
-    auto carve = [&](size_t bytes) {
+    auto carve = [&](size_t n) {
         const size_t o = at;
-        at += align256(bytes);
+        at += align256(n);
         return o;
     };
     const size_t o_wrows = carve(nw * 4), o_woff = carve(nw * 4), o_tfl = carve((size_t)nt * 4),
@@ -845,13 +842,9 @@ static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* v
                  o_hnode = carve((size_t)nodes * 4), o_hend = carve((size_t)nodes * 4),
                  o_hid = carve((size_t)nodes * 4), o_order = carve((size_t)nt * 4), o_bsum = carve(nb * 8),
                  o_tot = carve(4 * 8);
-    fr_status st = ensure(c, c->tab_small, at, "table counts");
-    if (st == FR_ENOMEM) {
-        c->err[0] = '\0';
-        return FR_OK;
-    }
-    FR_TRY(st);
-    char* base = static_cast<char*>(c->tab_small.p);
+    const size_t scratch_bytes = at;
+    char* base = static_cast<char*>(mem.scratch(scratch_bytes));
+    if (!base) return mem.status && *mem.status != FR_ENOMEM ? *mem.status : FR_OK;
     TabBuild b{};
     b.tags = tags;
     b.full = full;
@@ -875,8 +868,9 @@ static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* v
     FR_CUDA(c, launch_tab_scans(b, nt, reinterpret_cast<unsigned long long*>(base + o_bsum), totals, s));
     static_assert(kHostScratchBytes >= 32, "host scratch holds the four totals");
     FR_CUDA(c, cudaMemcpyAsync(c->host_counter, totals, 32, cudaMemcpyDeviceToHost, s));
-    // the warps' rows too, for the forward's tile order (pinned: the order's
-    // upload below stays asynchronous)
+    // the warps' rows too, for the tile order (pinned: the order's upload
+    // below stays asynchronous; a later build writes the buffer only after
+    // its own synchronisation, when that upload is done)
     const size_t host_need = (size_t)nw * 4 + (size_t)nt * 4;
     if (c->tab_host_bytes < host_need) {
         FR_CUDA(c, cudaStreamSynchronize(s));
@@ -893,18 +887,16 @@ static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* v
     unsigned long long tot[4];
     memcpy(tot, c->host_counter, sizeof tot);
     const unsigned long long rows = tot[0], nflame = tot[1], nadj = tot[2], nhull = tot[3];
+    if (bytes) *bytes = scratch_bytes;
     if (rows * 32 >= (1ull << 32) || nadj >= (1ull << 32)) return FR_OK;
-    st = ensure(c, c->tab_fwd, (size_t)rows * 32 * 8, "forward table");
-    if (st == FR_OK) st = ensure(c, c->tab_adj, (size_t)nadj * 8, "adjustment table");
-    if (st == FR_OK) st = ensure(c, c->tab_dl, (size_t)nflame * 16, "flame residuals");
-    if (st == FR_OK) st = ensure(c, c->tab_hs, (size_t)nhull * rec_bytes(vol), "hull records");
-    if (st == FR_ENOMEM) {
-        c->err[0] = '\0';
-        return FR_OK;
-    }
-    FR_TRY(st);
-    b.efwd = static_cast<uint2*>(c->tab_fwd.p);
-    b.eadj = static_cast<uint2*>(c->tab_adj.p);
+    // the tables' block: forward entries, adjustment entries, residuals, staged records
+    const size_t t_fwd = align256((size_t)rows * 32 * 8), t_adj = align256((size_t)nadj * 8),
+                 t_dl = align256((size_t)nflame * 16), t_hs = align256((size_t)nhull * rec_bytes(vol));
+    char* tb = static_cast<char*>(mem.tables(t_fwd + t_adj + t_dl + t_hs));
+    if (!tb) return mem.status && *mem.status != FR_ENOMEM ? *mem.status : FR_OK;
+    if (bytes) *bytes += t_fwd + t_adj + t_dl + t_hs;
+    b.efwd = reinterpret_cast<uint2*>(tb);
+    b.eadj = reinterpret_cast<uint2*>(tb + t_fwd);
     b.nadj = nadj;
     b.nhull = (unsigned)nhull;
     // the tiles, longest first, for the fill and for every iteration's forward
@@ -924,8 +916,8 @@ static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* v
     it.eadj = b.eadj;
     it.hnode = b.hnode;
     it.hend = hend;
-    it.hs = c->tab_hs.p;
-    it.dl = static_cast<float4*>(c->tab_dl.p);
+    it.hs = tb + t_fwd + t_adj + t_dl;
+    it.dl = reinterpret_cast<float4*>(tb + t_fwd + t_adj);
     it.nhull = (unsigned)nhull;
     it.nflame = (unsigned)nflame;
     it.nadj = (unsigned)nadj;
@@ -935,6 +927,25 @@ static fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* v
     c->tab_stats[3] = nhull;
     built = true;
     return FR_OK;
+}
+
+// build_tables' memory from the context's scratch (held from call to call,
+// under the context's scratch limit)
+static TabMemory ctx_tab_memory(fr_ctx* c, fr_status* status)
+{
+    TabMemory m;
+    m.status = status;
+    m.scratch = [c, status](size_t n) -> void* {
+        *status = ensure(c, c->tab_small, n, "table counts");
+        if (*status == FR_ENOMEM) c->err[0] = '\0';
+        return *status == FR_OK ? c->tab_small.p : nullptr;
+    };
+    m.tables = [c, status](size_t n) -> void* {
+        *status = ensure(c, c->tab_fwd, n, "ray weight tables");
+        if (*status == FR_ENOMEM) c->err[0] = '\0';
+        return *status == FR_OK ? c->tab_fwd.p : nullptr;
+    };
+    return m;
 }
 
 static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo, const fr_camera* cams, int ncam,
@@ -1145,7 +1156,8 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
         tb.p.targets = tg;
         tb.p.adj_occ = u.p.adj_occ;
         tb.p.adj_box = u.p.adj_box;
-        FR_TRY(build_tables(c, tb, vol, hull, full, nt, tab, tables));
+        fr_status ms = FR_OK;
+        FR_TRY(build_tables(c, tb, vol, hull, full, nt, ctx_tab_memory(c, &ms), tab, tables));
     }
     void* fin = nullptr;
     FR_TRY(fin_scratch(c, &fin));

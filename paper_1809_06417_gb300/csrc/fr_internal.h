@@ -191,6 +191,16 @@ cudaError_t launch_tab_forward(const SingleArgs& a, const TabIter& it, int dt, i
 cudaError_t launch_tab_adjust(void* vol, int dt, long long nodes, const TabIter& it, int clamp_nonneg,
                               cudaStream_t s);
 cudaError_t check_word_tables(unsigned* word, bool reset);
+// Several problems' tables per launch (the server): tile_start / blk_start
+// ascending with the total last (blocks of the adjustment: tab_adjust_blocks
+// of a problem's key points); the batched adjustment updates each P.vol_rw
+// and writes the updated records to its.hs, the next iteration's staged
+// source (problems without in-scattering).
+unsigned tab_adjust_blocks(unsigned nh);
+cudaError_t launch_tab_forward_batch(const ProbDev* probs, const TabIter* its, const int* tile_start, int nprob,
+                                     int total_tiles, int dt, cudaStream_t s);
+cudaError_t launch_tab_adjust_batch(const ProbDev* probs, const TabIter* its, const int* blk_start, int nprob,
+                                    int total_blocks, int dt, int clamp_nonneg, cudaStream_t s);
 // host: the forward's tiles in launch order from the warps' rows (the tile
 // with the most rows in one warp first; FR_TAB_LPT = 0: tile order)
 void tab_tile_order(const unsigned* wrows, int ntiles, unsigned* order);

@@ -32,6 +32,13 @@ struct fr_job {
     unsigned char* occ = nullptr;       // brick table of the non-empty records (skip_empty)
     unsigned char* hull_bricks = nullptr;  // brick table of the hull (both)
     int ntiles = 0;
+    // ray weight tables (the paper rule in the visual hull with skipping, field
+    // mode, G = 1, jobs of FR_TABLES_MIN_ITERS iterations or more): built at
+    // admission in two more pool allocations, counted in the footprint
+    bool tabled = false;
+    TabIter tab{};
+    void* tab_scratch = nullptr;
+    void* tab_block = nullptr;
 };
 
 struct fr_server {
@@ -108,11 +115,45 @@ fr_volume job_volume(const fr_job* j, int dtype)
 
 void job_free(fr_server* s, fr_job* j)
 {
+    for (void** p : {&j->tab_scratch, &j->tab_block})
+        if (*p) {
+            cudaFreeAsync(*p, s->ctx->stream);
+            *p = nullptr;
+        }
+    j->tabled = false;
     if (j->mem) {
         cudaFreeAsync(j->mem, s->ctx->stream);
         j->mem = nullptr;
         s->used -= j->footprint;
     }
+}
+
+// Whether a job builds ray weight tables (fr_params.tables of the server).
+bool server_tables(const fr_server* s, const fr_job* j)
+{
+    const fr_params& p = s->p;
+    return !FR_FUSED && p.tables != 1 && p.rule == FR_RULE_PAPER && p.use_hull && p.skip_empty && !(p.tau > 0.0f) &&
+           !(p.g_std > 0.0f) && (p.tables == 2 || j->d.iters >= FR_TABLES_MIN_ITERS);
+}
+
+// A pool allocation for a job's tables inside the server's budget (nullptr
+// and *st = FR_ENOMEM when there is no room); counted in the job's footprint.
+void* job_tab_alloc(fr_server* s, fr_job* j, size_t n, void** slot, fr_status* st)
+{
+    if (s->used + n > s->budget) {
+        *st = FR_ENOMEM;
+        return nullptr;
+    }
+    void* p = nullptr;
+    if (cudaMallocFromPoolAsync(&p, n, s->pool, s->ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        *st = FR_ENOMEM;
+        return nullptr;
+    }
+    *slot = p;
+    s->used += n;
+    j->footprint += n;
+    return p;
 }
 
 // Admission: allocate, upload the initial volume and the frames, prepare the
@@ -167,6 +208,36 @@ fr_status job_admit(fr_server* s, fr_job* j)
         else
             FR_TRY(hull_tags(c, a, j->targets, s->p.flame_thresh, j->tags));
         FR_CUDA(c, launch_hull_clear(j->vol, s->dtype, j->d.nx, j->d.ny, j->d.nz, j->tags, full, j->hull_bricks, st));
+        if (j->hull_bricks && server_tables(s, j)) {
+            // the job's tables, then its first iteration's staged records
+            if (j->d.alpha_l != 0.0f) a.p.alpha_l = j->d.alpha_l;
+            a.p.nbx = bricks_along(j->d.nx);
+            a.p.nby = bricks_along(j->d.ny);
+            a.p.nbz = bricks_along(j->d.nz);
+            a.p.adj_occ = j->hull_bricks;
+            a.p.adj_box = brick_box(j->hull_bricks, a.p.nbx, a.p.nby, a.p.nbz);
+            fr_status ms = FR_OK;
+            TabMemory mem;
+            mem.status = &ms;
+            mem.scratch = [s, j, &ms](size_t n) { return job_tab_alloc(s, j, n, &j->tab_scratch, &ms); };
+            mem.tables = [s, j, &ms](size_t n) { return job_tab_alloc(s, j, n, &j->tab_block, &ms); };
+            bool built = false;
+            FR_TRY(build_tables(c, a, &v, j->tags, full, j->ntiles, mem, j->tab, built));
+            if (built) {
+                FR_CUDA(c, launch_tab_stage(j->vol, s->dtype, j->tab, st));
+                j->tabled = true;
+            } else {
+                // (no room: the job marches; what the build took goes back)
+                for (void** p : {&j->tab_scratch, &j->tab_block})
+                    if (*p) {
+                        cudaFreeAsync(*p, st);
+                        *p = nullptr;
+                    }
+                const size_t extra = j->footprint - job_layout(j->d, s->dtype, j->cams.data(), hull, skip).total;
+                s->used -= extra;
+                j->footprint -= extra;
+            }
+        }
     }
     j->state = FR_JOB_RUNNING;
     j->t_admit = s->now();
@@ -332,12 +403,21 @@ extern "C" fr_status fr_server_step(fr_server* s, int* running, int* queued)
     }
     const int n = (int)s->resident.size();
     if (n > 0) {
+        // the resident jobs with tables first, then the marching ones
+        std::vector<fr_job*> order;
+        order.reserve(n);
+        for (fr_job* j : s->resident)
+            if (j->tabled) order.push_back(j);
+        const int ntab = (int)order.size(), nm = n - ntab;
+        for (fr_job* j : s->resident)
+            if (!j->tabled) order.push_back(j);
         // tables of the resident jobs, with each job's own iteration
         size_t ncam = 0;
-        for (fr_job* j : s->resident) ncam += (size_t)j->d.ncam;
+        for (fr_job* j : order) ncam += (size_t)j->d.ncam;
         const size_t tp = align256(sizeof(ProbDev) * n), tc = align256(sizeof(CamDev) * ncam);
-        const size_t tt = align256(sizeof(int) * (n + 1));
-        const size_t tables = tp + tc + tt;
+        const size_t tt = align256(sizeof(int) * (nm + 1)), ttt = align256(sizeof(int) * (ntab + 1));
+        const size_t tbs = align256(sizeof(int) * (ntab + 1)), tit = align256(sizeof(TabIter) * (ntab + 1));
+        const size_t tables = tp + tc + tt + ttt + tbs + tit;
         FR_TRY(ensure(c, s->tables, tables, "server tables"));
         FR_CUDA(c, cudaEventSynchronize(s->staging_done));
         if (s->staging_bytes < tables) {
@@ -354,22 +434,28 @@ extern "C" fr_status fr_server_step(fr_server* s, int* running, int* queued)
         char* db = static_cast<char*>(s->tables.p);
         ProbDev* hp = reinterpret_cast<ProbDev*>(hb);
         CamDev* hc = reinterpret_cast<CamDev*>(hb + tp);
-        int* ht = reinterpret_cast<int*>(hb + tp + tc);
+        int* ht = reinterpret_cast<int*>(hb + tp + tc);                      // marching jobs' tile starts
+        int* htt = reinterpret_cast<int*>(hb + tp + tc + tt);                // tabled jobs' tile starts
+        int* hbs = reinterpret_cast<int*>(hb + tp + tc + tt + ttt);          // tabled jobs' adjustment blocks
+        TabIter* hit = reinterpret_cast<TabIter*>(hb + tp + tc + tt + ttt + tbs);
         ProbDev* dp = reinterpret_cast<ProbDev*>(db);
         CamDev* dc = reinterpret_cast<CamDev*>(db + tp);
         int* dtl = reinterpret_cast<int*>(db + tp + tc);
+        int* dtt = reinterpret_cast<int*>(db + tp + tc + tt);
+        int* dbs = reinterpret_cast<int*>(db + tp + tc + tt + ttt);
+        TabIter* dit = reinterpret_cast<TabIter*>(db + tp + tc + tt + ttt + tbs);
         static thread_local SingleArgs a;
         size_t cam_off = 0;
-        int tile_off = 0;
+        int tile_off = 0, tab_tiles = 0, tab_blocks = 0;
         for (int i = 0; i < n; ++i) {
-            fr_job* j = s->resident[i];
+            fr_job* j = order[i];
             fr_volume v = job_volume(j, s->dtype);
             fill_problem(&v, j->cams.data(), j->d.ncam, &s->p, a);
             ProbDev& P = a.p;
             P.cams = dc + cam_off;
             P.targets = j->targets;
             P.bbox = j->bbox;
-            P.residual = j->residual;
+            P.residual = j->tabled ? nullptr : j->residual;
             P.partials = j->partials;
             P.dV = j->dV;
             P.img_in = j->residual;
@@ -397,23 +483,41 @@ extern "C" fr_status fr_server_step(fr_server* s, int* running, int* queued)
             P.split_box = FR_SPLIT_BOX && kServerParts > 1 && j->hull_bricks && !(P.tau > 0.0f) ? 1 : 0;
             hp[i] = P;
             for (int k = 0; k < j->d.ncam; ++k) hc[cam_off + k] = a.cams[k];
-            ht[i] = tile_off;
+            if (i < ntab) {
+                htt[i] = tab_tiles;
+                hbs[i] = tab_blocks;
+                hit[i] = j->tab;
+                tab_tiles += j->ntiles;
+                tab_blocks += (int)tab_adjust_blocks(j->tab.nhull);
+            } else {
+                ht[i - ntab] = tile_off;
+                tile_off += j->ntiles;
+            }
             cam_off += (size_t)j->d.ncam;
-            tile_off += j->ntiles;
         }
-        ht[n] = tile_off;
+        ht[nm] = tile_off;
+        htt[ntab] = tab_tiles;
+        hbs[ntab] = tab_blocks;
         FR_CUDA(c, cudaMemcpyAsync(db, hb, tables, cudaMemcpyHostToDevice, st));
         FR_CUDA(c, cudaEventRecord(s->staging_done, st));
         const bool tau = s->p.tau > 0.0f;
         const bool hull = server_hull(s), skip = server_skip(s);
-        if (skip) FR_CUDA(c, launch_brick_reset_batch(dp, n, st));
-        FR_CUDA(c, launch_pair_pack_batch(dp, n, s->dtype, st));
-        if (skip) FR_CUDA(c, launch_brick_box_batch(dp, n, st));
-        FR_CUDA(c, launch_fwd_batch(dp, dtl, n, tile_off, s->dtype, KIND_RGB, tau, true, st, skip));
+        ProbDev* dpm = dp + ntab;   // the marching jobs
+        if (nm > 0) {
+            if (skip) FR_CUDA(c, launch_brick_reset_batch(dpm, nm, st));
+            FR_CUDA(c, launch_pair_pack_batch(dpm, nm, s->dtype, st));
+            if (skip) FR_CUDA(c, launch_brick_box_batch(dpm, nm, st));
+            FR_CUDA(c, launch_fwd_batch(dpm, dtl, nm, tile_off, s->dtype, KIND_RGB, tau, true, st, skip));
+        }
+        if (ntab > 0) FR_CUDA(c, launch_tab_forward_batch(dp, dit, dtt, ntab, tab_tiles, s->dtype, st));
         FR_CUDA(c, launch_finalize_batch(dp, n, 0, st));
-        FR_CUDA(c, launch_adjust_list_batch(dp, dtl, n, tile_off, s->dtype, tau, 0, st, hull && skip,
-                                            kServerParts));
-        FR_CUDA(c, launch_apply_batch(dp, n, s->dtype, s->p.clamp_nonneg, st));   // with the hull clear
+        if (nm > 0) {
+            FR_CUDA(c, launch_adjust_list_batch(dpm, dtl, nm, tile_off, s->dtype, tau, 0, st, hull && skip,
+                                                kServerParts));
+            FR_CUDA(c, launch_apply_batch(dpm, nm, s->dtype, s->p.clamp_nonneg, st));   // with the hull clear
+        }
+        if (ntab > 0)
+            FR_CUDA(c, launch_tab_adjust_batch(dp, dit, dbs, ntab, tab_blocks, s->dtype, s->p.clamp_nonneg, st));
         FR_CUDA(c, cudaStreamSynchronize(st));
         // advance and retire
         for (size_t i = 0; i < s->resident.size();) {

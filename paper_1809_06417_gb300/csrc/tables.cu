@@ -444,12 +444,11 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* p, unsigned bytes)
 // image when asked for, each flame ray's residual at its number, the tile's
 // squared-error partials.
 template <int DT>
-__global__ void FR_TAB_FWD_BOUNDS tab_forward_kernel(const __grid_constant__ SingleArgs a, TabIter it)
+__device__ __forceinline__ void tab_forward_body(const ProbDev& P, const TabIter& it, unsigned slot)
 {
-    const ProbDev& P = a.p;
     int view, px, py;
     // the tiles in the order of it.torder (longest first, so the grid ends on short ones)
-    const unsigned tile = it.torder ? __ldg(it.torder + blockIdx.x) : blockIdx.x;
+    const unsigned tile = it.torder ? __ldg(it.torder + slot) : slot;
     tile_pixel(P, (int)tile, view, px, py);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned wi = tile * (kTileThreads / 32) + w;
@@ -549,6 +548,23 @@ __global__ void FR_TAB_FWD_BOUNDS tab_forward_kernel(const __grid_constant__ Sin
     }
 }
 
+template <int DT>
+__global__ void FR_TAB_FWD_BOUNDS tab_forward_kernel(const __grid_constant__ SingleArgs a, TabIter it)
+{
+    tab_forward_body<DT>(a.p, it, blockIdx.x);
+}
+
+// The same over several problems: CTA b renders tile slot b - tile_start[i]
+// of problem i (tile_start ascending, its last entry the total).
+template <int DT>
+__global__ void FR_TAB_FWD_BOUNDS tab_forward_batch_kernel(const ProbDev* __restrict__ probs,
+                                                           const TabIter* __restrict__ its,
+                                                           const int* __restrict__ tile_start, int nprob)
+{
+    const int i = find_problem(tile_start, nprob, blockIdx.x);
+    tab_forward_body<DT>(probs[i], its[i], blockIdx.x - (unsigned)__ldg(tile_start + i));
+}
+
 // Adjustment and update of the hull's key points: kTabLanes lanes per key
 // point sum W times the flame ray's residual over its entries, then one lane
 // adds the sum to the record (Eq. 11), clamps it at 0 when asked and stores
@@ -561,11 +577,13 @@ constexpr int kTabLanes = FR_TAB_LANES;
 static_assert(kTabLanes >= 1 && kTabLanes <= 32 && (kTabLanes & (kTabLanes - 1)) == 0, "FR_TAB_LANES: power of 2");
 constexpr int kTabAdjThreads = 256;
 
+// stage_next: also write the stored record to it.hs[g], the next iteration's
+// staged source (loops without in-scattering, whose source is the volume).
 template <int DT>
-__global__ void __launch_bounds__(kTabAdjThreads) tab_adjust_kernel(void* vol, TabIter it, int clamp_nonneg,
-                                                                    long long nodes)
+__device__ __forceinline__ void tab_adjust_body(void* vol, const TabIter& it, int clamp_nonneg, long long nodes,
+                                                unsigned blk, bool stage_next)
 {
-    const unsigned g = (blockIdx.x * (unsigned)kTabAdjThreads + threadIdx.x) / (unsigned)kTabLanes;
+    const unsigned g = (blk * (unsigned)kTabAdjThreads + threadIdx.x) / (unsigned)kTabLanes;
     const unsigned sub = threadIdx.x & (kTabLanes - 1);
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
 #if FR_TAB_ADJ_BULK
@@ -627,7 +645,29 @@ __global__ void __launch_bounds__(kTabAdjThreads) tab_adjust_kernel(void* vol, T
             v.x = fmaxf(v.x, 0.0f); v.y = fmaxf(v.y, 0.0f); v.z = fmaxf(v.z, 0.0f);
         }
         store_rgb<DT>(vol, node, v);
+        if (stage_next) store_rgb<DT>(it.hs, g, v);
     }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kTabAdjThreads) tab_adjust_kernel(void* vol, TabIter it, int clamp_nonneg,
+                                                                    long long nodes)
+{
+    tab_adjust_body<DT>(vol, it, clamp_nonneg, nodes, blockIdx.x, false);
+}
+
+// The same over several problems: CTA b takes block b - blk_start[i] of
+// problem i's key points (blk_start ascending, its last entry the total),
+// updates P.vol_rw and stages the next iteration's records.
+template <int DT>
+__global__ void __launch_bounds__(kTabAdjThreads) tab_adjust_batch_kernel(const ProbDev* __restrict__ probs,
+                                                                          const TabIter* __restrict__ its,
+                                                                          const int* __restrict__ blk_start, int nprob,
+                                                                          int clamp_nonneg)
+{
+    const int i = find_problem(blk_start, nprob, blockIdx.x);
+    const ProbDev& P = probs[i];
+    tab_adjust_body<DT>(P.vol_rw, its[i], clamp_nonneg, P.nodes, blockIdx.x - (unsigned)__ldg(blk_start + i), true);
 }
 
 }  // namespace
@@ -721,6 +761,31 @@ cudaError_t launch_tab_adjust(void* vol, int dt, long long nodes, const TabIter&
     if (dt == DT_F32) tab_adjust_kernel<DT_F32><<<g, kTabAdjThreads, 0, s>>>(vol, it, clamp_nonneg, nodes);
     else if (dt == DT_BF16) tab_adjust_kernel<DT_BF16><<<g, kTabAdjThreads, 0, s>>>(vol, it, clamp_nonneg, nodes);
     else tab_adjust_kernel<DT_F16><<<g, kTabAdjThreads, 0, s>>>(vol, it, clamp_nonneg, nodes);
+    return cudaGetLastError();
+}
+
+unsigned tab_adjust_blocks(unsigned nh) { return (nh + kTabAdjThreads / kTabLanes - 1) / (kTabAdjThreads / kTabLanes); }
+
+cudaError_t launch_tab_forward_batch(const ProbDev* probs, const TabIter* its, const int* tile_start, int nprob,
+                                     int total_tiles, int dt, cudaStream_t s)
+{
+    if (nprob <= 0 || total_tiles <= 0) return cudaSuccess;
+    if (dt == DT_F32) tab_forward_batch_kernel<DT_F32><<<total_tiles, kTileThreads, 0, s>>>(probs, its, tile_start, nprob);
+    else if (dt == DT_BF16) tab_forward_batch_kernel<DT_BF16><<<total_tiles, kTileThreads, 0, s>>>(probs, its, tile_start, nprob);
+    else tab_forward_batch_kernel<DT_F16><<<total_tiles, kTileThreads, 0, s>>>(probs, its, tile_start, nprob);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tab_adjust_batch(const ProbDev* probs, const TabIter* its, const int* blk_start, int nprob,
+                                    int total_blocks, int dt, int clamp_nonneg, cudaStream_t s)
+{
+    if (nprob <= 0 || total_blocks <= 0) return cudaSuccess;
+    if (dt == DT_F32)
+        tab_adjust_batch_kernel<DT_F32><<<total_blocks, kTabAdjThreads, 0, s>>>(probs, its, blk_start, nprob, clamp_nonneg);
+    else if (dt == DT_BF16)
+        tab_adjust_batch_kernel<DT_BF16><<<total_blocks, kTabAdjThreads, 0, s>>>(probs, its, blk_start, nprob, clamp_nonneg);
+    else
+        tab_adjust_batch_kernel<DT_F16><<<total_blocks, kTabAdjThreads, 0, s>>>(probs, its, blk_start, nprob, clamp_nonneg);
     return cudaGetLastError();
 }
 

@@ -82,7 +82,7 @@ def main():
     jobs = []
     for v2, im2, b2, c2 in keep:
         init = v2.cpu().numpy()
-        jobs.append(srv.submit(c2.shape, c2.origin, c2.h, c2.cams, 3, init, im2.cpu().numpy()))
+        jobs.append(srv.submit(c2.shape, c2.origin, c2.h, c2.cams, 4, init, im2.cpu().numpy()))
     for j in jobs:
         j.wait()
     srv.close()
