@@ -68,6 +68,8 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
                    &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr, &c->L6, &c->fin, &c->flame_tm,
                    &c->vol_stage, &c->probe, &c->flame_dl, &c->tab_small, &c->tab_fwd})
         if (b->p) cudaFree(b->p);
+    for (Buf& b : c->tab_batch)
+        if (b.p) cudaFree(b.p);
     for (void* p : c->owned) cudaFree(p);
     if (c->host_counter) cudaFreeHost(c->host_counter);
     if (c->staging) cudaFreeHost(c->staging);
@@ -1668,11 +1670,17 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
     }
     if (tiles_total * parts >= (1LL << 31)) return fail(c, FR_EINVAL, "too many tiles in one batch");
     if (iters == 0) return FR_OK;
+    // ray weight tables for every problem (fr_params.tables, as in
+    // fr_reconstruct), or for none when one of them has no room
+    bool tabled = !FR_FUSED && p->tables != 1 && hull && skip && !(p->g_std > 0.0f) &&
+                  (p->tables == 2 || iters >= FR_TABLES_MIN_ITERS);
     const size_t tab_probs = align256(sizeof(ProbDev) * nprob);
     const size_t tab_cams = align256(sizeof(CamDev) * cams_total);
     const size_t tab_tiles = align256(sizeof(int) * (nprob + 1));
+    const size_t tab_blks = align256(sizeof(int) * (nprob + 1));
+    const size_t tab_its = align256(sizeof(TabIter) * nprob);
     const size_t rmse_all = align256(sizeof(float) * 3 * (size_t)nprob * iters);
-    const size_t tables = tab_probs + tab_cams + tab_tiles;
+    const size_t tables = tab_probs + tab_cams + tab_tiles + tab_blks + tab_its;
     FR_TRY(ensure(c, c->batch, arena + tables + rmse_all, "batch"));
     // host staging (pinned), reused once the previous copy out of it is done
     if (!c->staging_done) FR_CUDA(c, cudaEventCreateWithFlags(&c->staging_done, cudaEventDisableTiming));
@@ -1695,6 +1703,13 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
     ProbDev* h_probs = reinterpret_cast<ProbDev*>(c->staging);
     CamDev* h_cams = reinterpret_cast<CamDev*>(static_cast<char*>(c->staging) + tab_probs);
     int* h_tiles = reinterpret_cast<int*>(static_cast<char*>(c->staging) + tab_probs + tab_cams);
+    int* d_blks = reinterpret_cast<int*>(dbase + arena + tab_probs + tab_cams + tab_tiles);
+    int* h_blks = reinterpret_cast<int*>(static_cast<char*>(c->staging) + tab_probs + tab_cams + tab_tiles);
+    TabIter* d_its = reinterpret_cast<TabIter*>(dbase + arena + tab_probs + tab_cams + tab_tiles + tab_blks);
+    TabIter* h_its =
+        reinterpret_cast<TabIter*>(static_cast<char*>(c->staging) + tab_probs + tab_cams + tab_tiles + tab_blks);
+    if (tabled && c->tab_batch.size() < 2 * (size_t)nprob) c->tab_batch.resize(2 * (size_t)nprob);
+    fr_status tab_status = FR_OK;
     cudaStream_t s = c->stream;
     static thread_local SingleArgs a;
     size_t off = 0, cam_off = 0;
@@ -1761,6 +1776,32 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         P.sq_slot = 0;
         P.pairs = pairs;
         P.tpart = tpart;
+        if (tabled) {
+            // the problem's tables in its own two context buffers
+            TabMemory mem;
+            mem.status = &tab_status;
+            Buf* tb = &c->tab_batch[2 * (size_t)i];
+            mem.scratch = [c, tb, &tab_status](size_t n) -> void* {
+                tab_status = ensure(c, tb[0], n, "batch table counts");
+                if (tab_status == FR_ENOMEM) c->err[0] = '\0';
+                return tab_status == FR_OK ? tb[0].p : nullptr;
+            };
+            mem.tables = [c, tb, &tab_status](size_t n) -> void* {
+                tab_status = ensure(c, tb[1], n, "batch ray weight tables");
+                if (tab_status == FR_ENOMEM) c->err[0] = '\0';
+                return tab_status == FR_OK ? tb[1].p : nullptr;
+            };
+            bool built = false;
+            a.p.adj_occ = hb;
+            a.p.adj_box = P.adj_box;
+            a.p.nbx = nbx;
+            a.p.nby = nby;
+            a.p.nbz = nbz;
+            a.p.targets = q.targets;
+            FR_TRY(build_tables(c, a, &q.vol, tags, full, nt, mem, h_its[i], built));
+            if (!built) tabled = false;
+            h_blks[i] = i ? h_blks[i - 1] + (int)tab_adjust_blocks(h_its[i - 1].nhull) : 0;
+        }
         h_probs[i] = P;
         for (int v = 0; v < q.ncam; ++v) h_cams[cam_off + v] = a.cams[v];
         h_tiles[i] = tile_off;
@@ -1770,13 +1811,31 @@ extern "C" fr_status fr_reconstruct_batch(fr_ctx* c, const fr_problem* probs, in
         tile_off += nt;
     }
     h_tiles[nprob] = tile_off;
+    int blk_total = 0;
+    if (tabled) {
+        blk_total = h_blks[nprob - 1] + (int)tab_adjust_blocks(h_its[nprob - 1].nhull);
+        h_blks[nprob] = blk_total;
+        // the first iteration's staged records; the residual images are not needed
+        for (int i = 0; i < nprob; ++i) {
+            FR_CUDA(c, launch_tab_stage(probs[i].vol.data, dt, h_its[i], s));
+            h_probs[i].residual = nullptr;
+        }
+    }
     FR_CUDA(c, cudaMemcpyAsync(d_probs, h_probs, tables, cudaMemcpyHostToDevice, s));
     FR_CUDA(c, cudaEventRecord(c->staging_done, s));
     const bool tau = p->tau > 0.0f;
 
     auto iterate = [&](cudaStream_t st) -> cudaError_t {
         cudaError_t e = cudaSuccess;
-        for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+        for (int it = 0; it < iters && e == cudaSuccess && tabled; ++it) {
+            // rendering from the forward tables, error sums, the adjustment
+            // tables' update (which stages the next iteration's records)
+            e = launch_tab_forward_batch(d_probs, d_its, d_tiles, nprob, tile_off, dt, st);
+            if (e == cudaSuccess) e = launch_finalize_batch(d_probs, nprob, it, st);
+            if (e == cudaSuccess)
+                e = launch_tab_adjust_batch(d_probs, d_its, d_blks, nprob, blk_total, dt, p->clamp_nonneg, st);
+        }
+        for (int it = 0; it < iters && e == cudaSuccess && !tabled; ++it) {
             if (skip) e = launch_brick_reset_batch(d_probs, nprob, st);
             if (e == cudaSuccess) e = launch_pair_pack_batch(d_probs, nprob, dt, st);
             if (e == cudaSuccess && skip) e = launch_brick_box_batch(d_probs, nprob, st);

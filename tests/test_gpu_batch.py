@@ -101,12 +101,14 @@ def test_batch_follows_oracle(orc, use_hull):
     ctx.close()
 
 
-def test_video_size_batch_follows_oracle(orc):
+@pytest.mark.parametrize("tables", [1, 2], ids=["march", "tables"])
+def test_video_size_batch_follows_oracle(orc, tables):
     """Two frames of the video setting at full size (96^3, 8 views of 384^2,
     the plume advected between them), each in its own hull (the oracle's tags),
-    two batched iterations captured in a CUDA graph, against orc.reconstruct
-    frame by frame; node by node within 1e-4 of the frame's maximum plus the
-    oracle's undecided budget."""
+    two batched iterations captured in a CUDA graph, marching or on each
+    frame's ray weight tables, against orc.reconstruct frame by frame; node by
+    node within 1e-4 of the frame's maximum plus the oracle's undecided
+    budget."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import os
@@ -120,7 +122,7 @@ def test_video_size_batch_follows_oracle(orc):
     frames = synth.video_frames(8, n, 4)[3:5]
     alpha = 2e-4 * (n / 128.0) * (512.0 / side) ** 2
     P = orc.make_params(step=step, alpha_l=alpha)
-    p = fr.params(step=step, alpha_l=alpha, use_hull=1)
+    p = fr.params(step=step, alpha_l=alpha, use_hull=1, tables=tables)
     refs, batch, keep = [], [], []
     for gt in frames:
         case = Case(shape, cams, gt, step)
@@ -144,17 +146,19 @@ def test_video_size_batch_follows_oracle(orc):
         scale = np.abs(vol_ref[..., :3]).max()
         err = np.abs(got[..., :3] - vol_ref[..., :3]).max(axis=-1)
         bound = 1e-4 * scale + und
-        print(f"video frame vs oracle: max error / max {err.max() / scale:.2e}, worst error / bound "
+        print(f"video frame vs oracle (tables={tables}): max error / max {err.max() / scale:.2e}, worst error / bound "
               f"{np.max(err / bound):.3f}, rmse {rm.cpu().numpy()[-1]} vs {rmse_ref[-1]}")
         assert np.all(err <= bound)
         np.testing.assert_allclose(rm.cpu().numpy(), rmse_ref, rtol=1e-3)
     ctx.close()
 
 
-def test_batch_with_an_empty_hull_follows_oracle(orc):
+@pytest.mark.parametrize("tables", [1, 2], ids=["march", "tables"])
+def test_batch_with_an_empty_hull_follows_oracle(orc, tables):
     """A batch whose middle problem has no key point in its hull (its box is
-    empty: the batched pack and update cover no node of it) beside two with
-    their hulls: each against orc.reconstruct on the same tags."""
+    empty: the batched pack and update cover no node of it; its tables have no
+    entry and no adjustment block) beside two with their hulls: each against
+    orc.reconstruct on the same tags."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from gpu_cases import Case, oracle_targets, tags_on_device
@@ -163,7 +167,7 @@ def test_batch_with_an_empty_hull_follows_oracle(orc):
     specs = [(24, 3, 40, 11), (32, 5, 56, 12), (20, 4, 33, 13)]
     iters = 3
     P = orc.make_params(step=0.5, alpha_l=2e-3)
-    p = fr.params(step=0.5, alpha_l=2e-3, use_hull=1)
+    p = fr.params(step=0.5, alpha_l=2e-3, use_hull=1, tables=tables)
     refs, batch, keep = [], [], []
     for i, (n, views, side, seed) in enumerate(specs):
         shape, origin, h = synth.unit_grid(n)
