@@ -76,6 +76,7 @@ struct fr_ctx {
     Buf probe;                       // measurement builds only (FR_ADJ_GATHER_PROBE)
     Buf tab_small, tab_fwd;          // ray weight tables: counts, offsets and the hull's list; the tables
     std::vector<Buf> tab_batch;      // the same per problem of fr_reconstruct_batch (two each)
+    Buf torder;                      // marching loop: the forward's tile keys and launch order
     unsigned long long tab_stats[4] = {0, 0, 0, 0};  // sizes of the last call's tables (fr_table_stats)
     void* tab_host = nullptr;        // pinned host scratch of the tables' build (warps' rows, tile order)
     size_t tab_host_bytes = 0;

@@ -66,7 +66,7 @@ extern "C" fr_status fr_destroy(fr_ctx* c)
     for (Buf* b : {&c->partials, &c->counter, &c->residual, &c->rendered, &c->dV, &c->targets, &c->sqerr,
                    &c->rmse, &c->J, &c->src, &c->flame_cnt, &c->flame_list, &c->batch, &c->pairs,
                    &c->hull, &c->sat, &c->occ, &c->hull_bricks, &c->loop, &c->verr, &c->L6, &c->fin, &c->flame_tm,
-                   &c->vol_stage, &c->probe, &c->flame_dl, &c->tab_small, &c->tab_fwd})
+                   &c->vol_stage, &c->probe, &c->flame_dl, &c->tab_small, &c->tab_fwd, &c->torder})
         if (b->p) cudaFree(b->p);
     for (Buf& b : c->tab_batch)
         if (b.p) cudaFree(b.p);
@@ -1160,6 +1160,15 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
         tb.p.adj_box = u.p.adj_box;
         fr_status ms = FR_OK;
         FR_TRY(build_tables(c, tb, vol, hull, full, nt, ctx_tab_memory(c, &ms), tab, tables));
+    }
+    // Marching all views at once: the forward takes its tiles longest first
+    // (samples inside the hull's box per ray, else the whole chord), so the
+    // grid does not end on the longest tiles
+    if (!tables && !per_view && !pipe && !FR_FUSED && FR_MARCH_ORDER) {
+        FR_TRY(ensure(c, c->torder, (size_t)nt * 8, "tile order"));
+        unsigned* key = static_cast<unsigned*>(c->torder.p);
+        FR_CUDA(c, launch_tile_order(f, nt, pack_keep ? u.p.adj_box : nullptr, key, key + nt, s));
+        f.p.tile_order = key + nt;
     }
     void* fin = nullptr;
     FR_TRY(fin_scratch(c, &fin));

@@ -80,6 +80,8 @@ struct ProbDev {
     // (set only where the adjustment skips by adj_occ; the forward computes
     // the same range to place the part boundaries)
     int split_box;
+    // single-problem forward march: CTA b takes tile tile_order[b] (nullable: tile b)
+    const unsigned* tile_order;
     unsigned long long* counter; // sample counter, nullable
     // batched launches only
     const unsigned* list;        // flame-ray list (linear pixel indices)

@@ -23,6 +23,14 @@ inline int tiles_of(int W, int H, int ncam)
 
 // march.cu
 cudaError_t launch_fwd(const SingleArgs& a, int dt, int kind, int ntiles, cudaStream_t s);
+// The forward march's tiles longest first (for a.p.tile_order): key and order
+// hold ntiles words each; box (brick-table layout, nullable) bounds the
+// samples counted per ray.
+#ifndef FR_MARCH_ORDER
+#define FR_MARCH_ORDER 1
+#endif
+cudaError_t launch_tile_order(const SingleArgs& a, int ntiles, const unsigned* box, unsigned* key,
+                              unsigned* order, cudaStream_t s);
 #ifndef FR_FUSED
 #define FR_FUSED 0
 #endif

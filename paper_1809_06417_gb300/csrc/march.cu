@@ -431,7 +431,62 @@ __device__ __forceinline__ void fwd_body(const ProbDev& P, const CamDev* cams, i
 template <int DT, int KIND, bool TAU, int MODE>
 __global__ void FR_FWD_BOUNDS_T(DT, KIND, TAU, MODE) fwd_single(const __grid_constant__ SingleArgs a)
 {
-    fwd_body<DT, KIND, TAU, MODE, true>(a.p, a.cams, blockIdx.x);
+    const int tile = a.p.tile_order ? (int)__ldg(a.p.tile_order + blockIdx.x) : (int)blockIdx.x;
+    fwd_body<DT, KIND, TAU, MODE, true>(a.p, a.cams, tile);
+}
+
+// Launch order of the forward's tiles, longest first: per tile, the most
+// samples one of its rays takes inside the box (box_range over `box`, the
+// whole chord without one) as a key, then a counting sort by decreasing key
+// in one CTA (positions inside a key taken with atomics: any order).
+constexpr int kOrderKeys = 1024;
+__global__ void __launch_bounds__(kTileThreads) tile_work_kernel(const __grid_constant__ SingleArgs a,
+                                                                 const unsigned* box, unsigned* key)
+{
+    const ProbDev& P = a.p;
+    int view, px, py;
+    tile_pixel(P, blockIdx.x, view, px, py);
+    int n = 0;
+    if (px < P.W && py < P.H) {
+        Ray R;
+        if (make_ray(a.cams[view], px, py, P.nx, P.ny, P.nz, P.step, R)) {
+            int k0 = 0, k1 = R.n;
+            if (!box || BrickSkip::box_range(P, box, R, P.step, k0, k1)) n = max(k1 - k0, 0);
+            else n = 0;
+        }
+    }
+    __shared__ int wm[kTileThreads / 32];
+    n = __reduce_max_sync(0xffffffffu, n);
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int m = 0;
+        for (int i = 0; i < kTileThreads / 32; ++i) m = max(m, wm[i]);
+        key[blockIdx.x] = (unsigned)min(m / 2, kOrderKeys - 1);
+    }
+}
+
+__global__ void __launch_bounds__(1024) tile_order_kernel(const unsigned* __restrict__ key, int ntiles,
+                                                          unsigned* __restrict__ order)
+{
+    __shared__ unsigned cnt[kOrderKeys];
+    for (int i = threadIdx.x; i < kOrderKeys; i += 1024) cnt[i] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntiles; t += 1024) atomicAdd(&cnt[kOrderKeys - 1 - __ldg(key + t)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned run = 0;
+        for (int i = 0; i < kOrderKeys; ++i) {
+            const unsigned c = cnt[i];
+            cnt[i] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntiles; t += 1024) {
+        const unsigned at = atomicAdd(&cnt[kOrderKeys - 1 - __ldg(key + t)], 1u);
+        order[at] = (unsigned)t;
+    }
 }
 
 // (Batched forward: capped at 80 registers (6 CTAs per SM) it spills and is
@@ -1214,6 +1269,15 @@ __global__ void __launch_bounds__(1024) finalize_batch(const ProbDev* __restrict
         case DT_F16: { constexpr int DTC = DT_F16; __VA_ARGS__; break; }   \
         default: return cudaErrorInvalidValue;            \
     }
+
+cudaError_t launch_tile_order(const SingleArgs& a, int ntiles, const unsigned* box, unsigned* key,
+                              unsigned* order, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    tile_work_kernel<<<ntiles, kTileThreads, 0, s>>>(a, box, key);
+    tile_order_kernel<<<1, 1024, 0, s>>>(key, ntiles, order);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_fwd(const SingleArgs& a, int dt, int kind, int ntiles, cudaStream_t s)
 {
