@@ -197,6 +197,19 @@ extern "C" fr_status fr_prepare_targets(fr_ctx* c, int ncam, int height, int wid
     return FR_OK;
 }
 
+// Large single renders take their tiles longest first (the most samples a
+// ray of the tile takes through the box; brick skipping not counted).
+constexpr int kOrderMinTiles = 1024;
+static fr_status order_tiles(fr_ctx* c, SingleArgs& a, int nt)
+{
+    if (!FR_MARCH_ORDER || nt < kOrderMinTiles) return FR_OK;
+    FR_TRY(ensure(c, c->torder, (size_t)nt * 8, "tile order"));
+    unsigned* key = static_cast<unsigned*>(c->torder.p);
+    FR_CUDA(c, launch_tile_order(a, nt, nullptr, key, key + nt, c->stream));
+    a.p.tile_order = key + nt;
+    return FR_OK;
+}
+
 extern "C" fr_status fr_render(fr_ctx* c, const fr_volume* vol, const fr_camera* cams, int ncam,
                                const fr_params* p, float* out_rgb)
 {
@@ -210,6 +223,7 @@ extern "C" fr_status fr_render(fr_ctx* c, const fr_volume* vol, const fr_camera*
     a.p.rendered = out_rgb;
     FR_TRY(attach_pairs(c, vol, p, vol->data, a));
     int nt = tiles_of(a.p.W, a.p.H, ncam);
+    FR_TRY(order_tiles(c, a, nt));
     FR_CUDA(c, launch_fwd(a, vol->dtype, vol->kind, nt, c->stream));
     return FR_OK;
 }
@@ -240,6 +254,7 @@ extern "C" fr_status fr_render_residual(fr_ctx* c, const fr_volume* vol, const f
     FR_TRY(attach_pairs(c, vol, p, vol->data, a));
     void* fin = nullptr;
     FR_TRY(fin_scratch(c, &fin));
+    FR_TRY(order_tiles(c, a, nt));
     FR_CUDA(c, launch_fwd(a, vol->dtype, vol->kind, nt, c->stream));
     FR_CUDA(c, launch_finalize(a.p.partials, nt, sq_err, c->stream, 0, fin));
     return FR_OK;
@@ -299,7 +314,9 @@ extern "C" fr_status fr_render_backward(fr_ctx* c, const fr_volume* vol, const f
     a.p.img_in = grad_img;
     a.p.L_total = L_total;
     a.p.dV = grad;
-    FR_CUDA(c, launch_backward(a, vol->dtype, vol->kind, tiles_of(a.p.W, a.p.H, ncam), c->stream));
+    const int nt = tiles_of(a.p.W, a.p.H, ncam);
+    FR_TRY(order_tiles(c, a, nt));
+    FR_CUDA(c, launch_backward(a, vol->dtype, vol->kind, nt, c->stream));
     return FR_OK;
 }
 

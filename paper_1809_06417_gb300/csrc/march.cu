@@ -1003,7 +1003,8 @@ template <int DT, int KIND, bool TAU>
 __global__ void __launch_bounds__(kTileThreads, KIND == KIND_RGB ? FR_BWD_MINB_RGB : FR_BWD_MINB_TEMP)
     bwd_single(const __grid_constant__ SingleArgs a)
 {
-    bwd_body<DT, KIND, TAU>(a.p, a.cams, blockIdx.x);
+    const int tile = a.p.tile_order ? (int)__ldg(a.p.tile_order + blockIdx.x) : (int)blockIdx.x;
+    bwd_body<DT, KIND, TAU>(a.p, a.cams, tile);
 }
 
 template <int DT, int KIND, bool TAU>
