@@ -78,6 +78,7 @@ def main():
         keep.append((v2, im2, b2, c2))
         probs.append((fr.volume(v2, c2.origin, c2.h), fr.cameras(c2.cams), im2, b2, None))
     ctx.fr_reconstruct_batch(probs, 3, fr.params(step=0.5, alpha_l=2e-3, use_hull=1), use_graph=True)
+    ctx.fr_reconstruct_batch(probs, 3, fr.params(step=0.5, alpha_l=2e-3, use_hull=1, tables=2), use_graph=True)
     srv = fr.Server(ctx, fr.params(step=0.5, alpha_l=2e-3, use_hull=1), dtype=fr.FR_F32)
     jobs = []
     for v2, im2, b2, c2 in keep:
