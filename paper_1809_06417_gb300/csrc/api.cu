@@ -859,8 +859,8 @@ fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* vol, con
     const size_t o_wrows = carve(nw * 4), o_woff = carve(nw * 4), o_tfl = carve((size_t)nt * 4),
                  o_tfoff = carve((size_t)nt * 4), o_ncnt = carve((size_t)nodes * 4),
                  o_hnode = carve((size_t)nodes * 4), o_hend = carve((size_t)nodes * 4),
-                 o_hid = carve((size_t)nodes * 4), o_order = carve((size_t)nt * 4), o_bsum = carve(nb * 8),
-                 o_tot = carve(4 * 8);
+                 o_hid = carve((size_t)nodes * 4), o_order = carve((size_t)nt * 4), o_key = carve((size_t)nt * 4),
+                 o_bsum = carve(nb * 8), o_tot = carve(4 * 8);
     const size_t scratch_bytes = at;
     char* base = static_cast<char*>(mem.scratch(scratch_bytes));
     if (!base) return mem.status && *mem.status != FR_ENOMEM ? *mem.status : FR_OK;
@@ -883,6 +883,12 @@ fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* vol, con
     bf.p.vol = vol->data;
     cudaStream_t s = c->stream;
     FR_CUDA(c, cudaMemsetAsync(b.ncnt, 0, (size_t)nodes * 4, s));
+    // the count march's tiles longest first by the samples in the hull's box
+    unsigned* order_dev = reinterpret_cast<unsigned*>(base + o_order);
+    if (FR_MARCH_ORDER) {
+        FR_CUDA(c, launch_tile_order(bf, nt, bf.p.adj_box, reinterpret_cast<unsigned*>(base + o_key), order_dev, s));
+        b.torder = order_dev;
+    }
     FR_CUDA(c, launch_tab_count(bf, b, vol->dtype, nt, s));
     FR_CUDA(c, launch_tab_scans(b, nt, reinterpret_cast<unsigned long long*>(base + o_bsum), totals, s));
     static_assert(kHostScratchBytes >= 32, "host scratch holds the four totals");
@@ -919,7 +925,6 @@ fr_status build_tables(fr_ctx* c, const SingleArgs& f, const fr_volume* vol, con
     b.nadj = nadj;
     b.nhull = (unsigned)nhull;
     // the tiles, longest first, for the fill and for every iteration's forward
-    unsigned* order_dev = reinterpret_cast<unsigned*>(base + o_order);
     tab_tile_order(wrows_host, nt, order_host);
     FR_CUDA(c, cudaMemcpyAsync(order_dev, order_host, (size_t)nt * 4, cudaMemcpyHostToDevice, s));
     b.torder = order_dev;

@@ -136,8 +136,9 @@ template <int DT>
 __global__ void FR_TAB_BUILD_BOUNDS tab_build_kernel(const __grid_constant__ SingleArgs a, TabBuild b, int fill)
 {
     const ProbDev& P = a.p;
-    // the fill takes the tiles longest first (b.torder), the count in tile order
-    const unsigned tile = fill && b.torder ? __ldg(b.torder + blockIdx.x) : blockIdx.x;
+    // the tiles longest first (b.torder: estimated for the count, from the
+    // count's rows for the fill)
+    const unsigned tile = b.torder ? __ldg(b.torder + blockIdx.x) : blockIdx.x;
     int view, px, py;
     tile_pixel(P, (int)tile, view, px, py);
     const bool valid = px < P.W && py < P.H;
