@@ -41,12 +41,13 @@ WORKLOAD = dict(name="full_rte_128^3_8x512^2", n=128, views=8, side=512, step=0.
 # iterations of one step (the full-RTE setting runs 50)
 ITERS_PER_STEP = 50
 # kernels one step launches: hull clear with the hull's brick marks and box;
-# the tables' build (count march, four scans of three kernels, fill march,
-# entry ends); then per iteration the in-scatter sweeps (3, over the box of
+# the tables' build (the count march's tile order from each tile's samples
+# in the hull's box: 2, count march, four scans of three kernels, the hull's
+# list, fill march, entry ends); then per iteration the in-scatter sweeps (3, over the box of
 # the hull's bricks), the staging of the hull's source records, the forward
 # table's render with the residual, the error reduction (which also writes
 # the rmse) and the adjustment table's update
-KERNELS_SETUP = 1 + 16
+KERNELS_SETUP = 1 + 18
 KERNELS_PER_ITERATION = 7
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures of
 # the current kernels at this workload (None where the kernel changed since)
