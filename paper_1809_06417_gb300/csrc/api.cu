@@ -1334,10 +1334,14 @@ static fr_status reconstruct_impl(fr_ctx* c, fr_volume* vol, const float* albedo
             FR_CUDA(c, launch_tab_stage(render_vol, vol->dtype, tab, st));
             FR_CUDA(c, launch_tab_forward(f, tab, vol->dtype, nt, st));
             FR_TRY(trace_mark(c, FR_PHASE_FORWARD));
-            FR_CUDA(c, launch_finalize(f.p.partials, nt, sq + 4 * slot, st, 0, fin,
-                                       it < 0 ? nullptr : rmse_dev + 3 * slot));
-            FR_TRY(trace_mark(c, FR_PHASE_REDUCE));
-            FR_CUDA(c, launch_tab_adjust(vol->data, vol->dtype, nodes, tab, p->clamp_nonneg, st));
+            // the error sums run inside the adjustment's launch
+            const FinArgs fa{f.p.partials, nt, sq + 4 * slot, fin, it < 0 ? nullptr : rmse_dev + 3 * slot};
+            if (!FR_TAB_FIN_FUSED) {
+                FR_CUDA(c, launch_finalize(fa.partials, nt, fa.out4, st, 0, fin, fa.rmse3));
+                FR_TRY(trace_mark(c, FR_PHASE_REDUCE));
+            }
+            FR_CUDA(c, launch_tab_adjust(vol->data, vol->dtype, nodes, tab, p->clamp_nonneg, st,
+                                         FR_TAB_FIN_FUSED ? &fa : nullptr));
             FR_TRY(trace_mark(c, FR_PHASE_ADJUST));
             return FR_OK;
         }

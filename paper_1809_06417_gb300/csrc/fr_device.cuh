@@ -753,6 +753,62 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+// The error sums of one pass over nb CTAs of up to 256 threads: CTA b sums
+// its share of the tiles' partials (float4 per tile) into part_sums[b]; the
+// last CTA to finish (counted in *done, which it resets to 0) adds the shares
+// in order, so the result does not depend on which CTA ends last, writes
+// out4 (added to it when accumulate) and, with rmse3, the error measure of
+// Sec. 5.1, 255 sqrt(sum / count) per channel.
+__device__ __forceinline__ void finalize_parts_body(const float* __restrict__ partials, int ntiles,
+                                                    float* __restrict__ out4, int accumulate, float4* part_sums,
+                                                    unsigned* done, float* rmse3, unsigned b, unsigned nb)
+{
+    __shared__ float red[4][8];
+    __shared__ bool last;
+    __shared__ float sum4[4];
+    const int per = (ntiles + (int)nb - 1) / (int)nb;
+    const int b0 = (int)b * per, b1 = min(b0 + per, ntiles);
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    const float4* p4 = reinterpret_cast<const float4*>(partials);
+#pragma unroll 4
+    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        const float4 v = __ldg(p4 + i);
+        s0 += v.x; s1 += v.y; s2 += v.z; s3 += v.w;
+    }
+    s0 = warp_sum(s0); s1 = warp_sum(s1); s2 = warp_sum(s2); s3 = warp_sum(s3);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { red[0][w] = s0; red[1][w] = s1; red[2][w] = s2; red[3][w] = s3; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float4 t = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            t.x += red[0][i]; t.y += red[1][i]; t.z += red[2][i]; t.w += red[3][i];
+        }
+        part_sums[b] = t;
+        __threadfence();
+        last = atomicAdd(done, 1u) == nb - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    if (threadIdx.x < 4) {
+        __threadfence();
+        const volatile float* ps = reinterpret_cast<const volatile float*>(part_sums);
+        float t = 0.0f;
+        for (int i = 0; i < (int)nb; ++i) t += ps[4 * i + threadIdx.x];
+        t = accumulate ? out4[threadIdx.x] + t : t;
+        out4[threadIdx.x] = t;
+        sum4[threadIdx.x] = t;
+    }
+    if (threadIdx.x == 0) *done = 0u;
+    if (rmse3) {
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            const float cnt = sum4[3];
+            rmse3[threadIdx.x] = cnt > 0.0f ? 255.0f * sqrtf(sum4[threadIdx.x] / cnt) : 0.0f;
+        }
+    }
+}
+
 // View and pixel of the calling thread's ray in CTA tile `tile`.
 __device__ __forceinline__ void tile_pixel(const ProbDev& P, int tile, int& view, int& px, int& py)
 {

@@ -195,9 +195,27 @@ cudaError_t launch_tab_stage(const void* records, int dt, const TabIter& it, cud
 // a.p.vol: the source records; targets, bbox and partials as for the forward
 // march (rendered and residual images when set)
 cudaError_t launch_tab_forward(const SingleArgs& a, const TabIter& it, int dt, int ntiles, cudaStream_t s);
-// the adjustment added to the hull's key points of vol (RGB records)
+// The tables' iterations sum the forward's errors inside the adjustment's
+// launch (FR_TAB_FIN_FUSED = 0: a launch of their own between the two).
+#ifndef FR_TAB_FIN_FUSED
+#define FR_TAB_FIN_FUSED 1
+#endif
+// The error sums of a forward pass run by kFinParts extra CTAs of another
+// launch (finalize_parts_body): the tiles' partials, the sums written to out4
+// (not accumulated), the error measure to rmse3 (nullable); scratch as for
+// launch_finalize (kFinScratchBytes, its counter word 0).
+struct FinArgs {
+    const float* partials;
+    int ntiles;
+    float* out4;
+    void* scratch;
+    float* rmse3;
+};
+// the adjustment added to the hull's key points of vol (RGB records); fin
+// (nullable): the forward's error sums in the same launch, the update needing
+// only the residuals
 cudaError_t launch_tab_adjust(void* vol, int dt, long long nodes, const TabIter& it, int clamp_nonneg,
-                              cudaStream_t s);
+                              cudaStream_t s, const FinArgs* fin = nullptr);
 cudaError_t check_word_tables(unsigned* word, bool reset);
 // Several problems' tables per launch (the server): tile_start / blk_start
 // ascending with the total last (blocks of the adjustment: tab_adjust_blocks

@@ -1077,60 +1077,14 @@ __global__ void __launch_bounds__(1024) finalize_partials(const float* __restric
     }
 }
 
-// The same sum over kFinParts CTAs: CTA b sums its share of the tiles into
-// part_sums[b]; the last CTA to finish (counted in *done, which it resets to 0)
-// adds the shares in order, so the result does not depend on which CTA ends
-// last.  part_sums: kFinParts float4; *done must be 0 before the first launch.
+// The same sum over kFinParts CTAs (finalize_parts_body); *done must be 0
+// before the first launch.
 
 __global__ void __launch_bounds__(256) finalize_parts(const float* __restrict__ partials, int ntiles,
                                                       float* __restrict__ out4, int accumulate,
                                                       float4* part_sums, unsigned* done, float* rmse3)
 {
-    __shared__ float red[4][8];
-    __shared__ bool last;
-    const int per = (ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int b0 = blockIdx.x * per, b1 = min(b0 + per, ntiles);
-    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-    const float4* p4 = reinterpret_cast<const float4*>(partials);
-#pragma unroll 4
-    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-        const float4 v = __ldg(p4 + i);
-        s0 += v.x; s1 += v.y; s2 += v.z; s3 += v.w;
-    }
-    s0 = warp_sum(s0); s1 = warp_sum(s1); s2 = warp_sum(s2); s3 = warp_sum(s3);
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) { red[0][w] = s0; red[1][w] = s1; red[2][w] = s2; red[3][w] = s3; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float4 t = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-            t.x += red[0][i]; t.y += red[1][i]; t.z += red[2][i]; t.w += red[3][i];
-        }
-        part_sums[blockIdx.x] = t;
-        __threadfence();
-        last = atomicAdd(done, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __shared__ float sum4[4];
-    if (threadIdx.x < 4) {
-        __threadfence();
-        const volatile float* ps = reinterpret_cast<const volatile float*>(part_sums);
-        float t = 0.0f;
-        for (int i = 0; i < (int)gridDim.x; ++i) t += ps[4 * i + threadIdx.x];
-        t = accumulate ? out4[threadIdx.x] + t : t;
-        out4[threadIdx.x] = t;
-        sum4[threadIdx.x] = t;
-    }
-    if (threadIdx.x == 0) *done = 0u;
-    if (rmse3) {
-        // the error measure of Sec. 5.1, 255 sqrt(sum / count) per channel
-        __syncthreads();
-        if (threadIdx.x < 3) {
-            const float cnt = sum4[3];
-            rmse3[threadIdx.x] = cnt > 0.0f ? 255.0f * sqrtf(sum4[threadIdx.x] / cnt) : 0.0f;
-        }
-    }
+    finalize_parts_body(partials, ntiles, out4, accumulate, part_sums, done, rmse3, blockIdx.x, gridDim.x);
 }
 
 // Flame-ray list (pixels whose prepared target is non-zero), in tile order,

@@ -650,11 +650,20 @@ __device__ __forceinline__ void tab_adjust_body(void* vol, const TabIter& it, in
     }
 }
 
+// CTAs [0, nfin) sum the forward's error partials (finalize_parts_body), the
+// rest adjust blocks of key points; the sums are taken first so that they run
+// beside the adjustment instead of after it.
 template <int DT>
 __global__ void __launch_bounds__(kTabAdjThreads) tab_adjust_kernel(void* vol, TabIter it, int clamp_nonneg,
-                                                                    long long nodes)
+                                                                    long long nodes, FinArgs fin, unsigned nfin)
 {
-    tab_adjust_body<DT>(vol, it, clamp_nonneg, nodes, blockIdx.x, false);
+    if (blockIdx.x < nfin) {
+        float4* part_sums = reinterpret_cast<float4*>(fin.scratch);
+        finalize_parts_body(fin.partials, fin.ntiles, fin.out4, 0, part_sums,
+                            reinterpret_cast<unsigned*>(part_sums + kFinParts), fin.rmse3, blockIdx.x, nfin);
+        return;
+    }
+    tab_adjust_body<DT>(vol, it, clamp_nonneg, nodes, blockIdx.x - nfin, false);
 }
 
 // The same over several problems: CTA b takes block b - blk_start[i] of
@@ -754,14 +763,17 @@ cudaError_t launch_tab_forward(const SingleArgs& a, const TabIter& it, int dt, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_tab_adjust(void* vol, int dt, long long nodes, const TabIter& it, int clamp_nonneg, cudaStream_t s)
+cudaError_t launch_tab_adjust(void* vol, int dt, long long nodes, const TabIter& it, int clamp_nonneg, cudaStream_t s,
+                              const FinArgs* fin)
 {
-    if (it.nhull == 0) return cudaSuccess;
-    const unsigned per_cta = kTabAdjThreads / kTabLanes;
-    const unsigned g = (it.nhull + per_cta - 1) / per_cta;
-    if (dt == DT_F32) tab_adjust_kernel<DT_F32><<<g, kTabAdjThreads, 0, s>>>(vol, it, clamp_nonneg, nodes);
-    else if (dt == DT_BF16) tab_adjust_kernel<DT_BF16><<<g, kTabAdjThreads, 0, s>>>(vol, it, clamp_nonneg, nodes);
-    else tab_adjust_kernel<DT_F16><<<g, kTabAdjThreads, 0, s>>>(vol, it, clamp_nonneg, nodes);
+    const FinArgs f = fin ? *fin : FinArgs{};
+    const unsigned nfin = fin ? (unsigned)kFinParts : 0u;
+    const unsigned g = tab_adjust_blocks(it.nhull) + nfin;
+    if (g == 0) return cudaSuccess;
+    if (dt == DT_F32) tab_adjust_kernel<DT_F32><<<g, kTabAdjThreads, 0, s>>>(vol, it, clamp_nonneg, nodes, f, nfin);
+    else if (dt == DT_BF16)
+        tab_adjust_kernel<DT_BF16><<<g, kTabAdjThreads, 0, s>>>(vol, it, clamp_nonneg, nodes, f, nfin);
+    else tab_adjust_kernel<DT_F16><<<g, kTabAdjThreads, 0, s>>>(vol, it, clamp_nonneg, nodes, f, nfin);
     return cudaGetLastError();
 }
 
