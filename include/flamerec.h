@@ -494,12 +494,17 @@ fr_status fr_cams_destroy(fr_cams *cams);
 /* ---- Tracing: device time per phase of fr_reconstruct ---- */
 
 typedef enum {
-    FR_PHASE_SETUP = 0,   /* flame-ray list; visual hull tags, clear and bricks */
+    FR_PHASE_SETUP = 0,   /* flame-ray list; visual hull tags, clear and bricks;
+                             the ray weight tables' build */
     FR_PHASE_SCATTER = 1, /* in-scattering source (Sec. 3.2) */
     FR_PHASE_PACK = 2,    /* x-pair records and brick occupancy */
-    FR_PHASE_FORWARD = 3, /* forward march with the residual (Eqs. 5-8) */
-    FR_PHASE_REDUCE = 4,  /* squared-error reduction */
-    FR_PHASE_ADJUST = 5,  /* adjustment (Eqs. 10-12) or the exact gradient */
+    FR_PHASE_FORWARD = 3, /* forward march with the residual (Eqs. 5-8); on the
+                             tables, the staging of the records and the forward
+                             table */
+    FR_PHASE_REDUCE = 4,  /* squared-error reduction (0 on the tables, whose
+                             adjustment launch runs it) */
+    FR_PHASE_ADJUST = 5,  /* adjustment (Eqs. 10-12) or the exact gradient; on
+                             the tables also the update and the error sums */
     FR_PHASE_APPLY = 6,   /* update of the volume, hull clear */
     FR_PHASE_FINISH = 7,  /* error measure of the call */
     FR_PHASE_COUNT = 8
