@@ -129,6 +129,8 @@ typedef struct fr_params {
                             the call runs at least FR_TABLES_MIN_ITERS iterations; 1: never (march
                             every iteration); 2: whenever they apply.  Where they do not apply, or
                             their device memory would pass the scratch limit, the marches run.  The
+                            build synchronises the context's stream once (the host reads the tables'
+                            sizes and orders the tiles; fr_reconstruct_batch once per problem).  The
                             results are those of the marches up to float32 rounding (summation order) */
 } fr_params;
 
