@@ -395,6 +395,8 @@ extern "C" fr_status fr_server_step(fr_server* s, int* running, int* queued)
         s->queue.pop_front();
         fr_status r = job_admit(s, j);
         if (r != FR_OK) {
+            // what the admission took goes back to the pool and the budget
+            job_free(s, j);
             j->state = FR_JOB_CANCELED;
             j->t_done = s->now();
             return r;
