@@ -82,7 +82,7 @@ def test_adjustment_reads_no_emission(orc):
 @pytest.mark.parametrize("g_std", [0.0, 0.3])
 def test_weights_repeat_across_iterations_only_without_the_drawn_factor(orc, g_std):
     """With G(s) = 1 iteration 0 and iteration 5 adjust alike; with G(s)
-    drawn per iteration (Eq. 12) they do not, which is why the tables need
+    drawn per iteration (Eq. 11) they do not, which is why the tables need
     g_std = 0."""
     sc = _scene(orc)
     rng, (v,) = _volumes(sc.shape, 23, n=1)
